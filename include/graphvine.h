@@ -1,0 +1,256 @@
+/*
+ * graphvine.h -- C ABI of the GB300 (sm_103a) GraphVine dynamic-graph library.
+ *
+ * GraphVine ("A Data Structure to Optimize Dynamic Graph Processing on GPUs",
+ * Krishnan S, Tavva, Nasre) stores a directed graph as a vertex dictionary
+ * whose entries point at per-vertex sentinels; each sentinel roots a complete
+ * binary tree (CBT) of fixed-capacity edge blocks taken from a pre-allocated
+ * pool, the "edge queue".  Edge updates arrive in batches.  This library keeps
+ * that structure resident in device memory and runs every step of the batch
+ * operations in its own CUDA kernels.
+ *
+ * Conventions (all entry points):
+ *   - Array arguments are plain pointers.  Unless an entry point says
+ *     otherwise, an array may live in device memory (cudaMalloc, a torch CUDA
+ *     tensor) or in host memory (pinned or pageable).  Host arrays are copied
+ *     to and from library-owned device staging buffers on `stream`; a call
+ *     with a host OUTPUT array synchronises `stream` before it returns.
+ *   - The caller owns every array it passes; it must stay valid until the
+ *     call's work on `stream` has completed.  The library owns the graph
+ *     state, the block pool (unless gv_config.pool_mem is given) and its
+ *     scratch memory.
+ *   - Calls are asynchronous and ordered on `stream` (a cudaStream_t, passed
+ *     as void*; NULL = the legacy default stream).  Calls on one graph must
+ *     be ordered by the caller (one stream, or explicit dependencies): the
+ *     graph's scratch memory is shared by its calls.  Different graphs are
+ *     independent and may be used from different threads.
+ *   - The return value reports host-detectable errors at once (NULL graph,
+ *     NULL array with n > 0, n too large, CUDA launch or allocation failure).
+ *     Errors found on the device (edge pool exhausted, structure
+ *     inconsistency) turn the operation into a no-op -- the graph is left
+ *     exactly as it was -- and are latched in a device status word that the
+ *     next gv_sync() or gv_stats() returns and clears.
+ *   - Vertex ids and edge endpoints are uint32_t; valid ids are < the vertex
+ *     count.  An edge whose endpoint is out of range or not alive is rejected
+ *     and counted; the rest of its batch proceeds.
+ *   - Multiset semantics by default: inserting a pair that is already stored
+ *     adds another copy (Algorithm 1 appends without a duplicate check); a
+ *     delete removes every stored copy of each (u, v) it names (Algorithm 2
+ *     marks every matching entry).  With GV_DEDUP an insert adds a pair only
+ *     if it is not stored yet and not already added by the same batch.
+ */
+#ifndef GRAPHVINE_H
+#define GRAPHVINE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gv_graph gv_graph; /* opaque, owned by the library */
+
+typedef enum gv_status {
+    GV_OK = 0,
+    GV_ERR_INVALID_ARG = 1,   /* bad argument, detected on the host */
+    GV_ERR_OUT_OF_MEMORY = 2, /* device allocation failed, or edge pool exhausted (op is a no-op) */
+    GV_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+    GV_ERR_TIMEOUT = 4,       /* a bounded device wait gave up (op is a no-op) */
+    GV_ERR_STATE = 5          /* inconsistent structure detected on the device, or call out of order */
+} gv_status;
+
+/* gv_config.flags */
+#define GV_DEDUP 1u /* set semantics for inserts (cuSTINGER/Hornet-style duplicate check) */
+
+typedef struct gv_config {
+    /* C, the number of edge entries per edge block (multiple of 4, 4..512).
+     * 0 = the paper's rule ("Initialization"): the average degree of the
+     * vertices with non-zero degree in the first edge batch, rounded up to a
+     * multiple of 4; fixed from then on. */
+    uint32_t block_capacity;
+    uint32_t flags;          /* GV_DEDUP or 0 */
+    /* Bytes reserved for the edge-block pool: block storage (4*C bytes per
+     * block), tree links (8 bytes per block) and the edge queue (4 bytes per
+     * block).  0 = half of the free device memory ("Edge Queue": at least
+     * half of GPU memory is reserved with one allocation). */
+    uint64_t pool_bytes;
+    /* Optional caller-owned device buffer of pool_bytes bytes (16-byte
+     * aligned) to hold the pool instead of a library allocation.  It must
+     * outlive the graph. */
+    void *pool_mem;
+    /* Hint for the dictionary capacity; rounded up to a power of two
+     * ("Vertex dictionary": 453 vertices -> 512). */
+    uint32_t vertex_capacity;
+    uint32_t reserved;
+} gv_config;
+
+typedef struct gv_stats_t {
+    uint32_t num_vertices;     /* ids 0 .. num_vertices-1 exist (alive or deleted) */
+    uint32_t vertex_capacity;  /* dictionary capacity, a power of two */
+    uint32_t block_capacity;   /* C (0 until fixed by the first edge batch) */
+    uint32_t flags;
+    uint64_t num_edges;        /* stored edge entries (a multigraph counts copies) */
+    uint64_t pool_blocks;      /* blocks in the pool */
+    uint64_t pool_blocks_used; /* blocks owned by adjacencies */
+    uint64_t pool_blocks_free; /* blocks in the edge queue */
+    uint64_t pool_bytes;       /* device bytes of the pool (blocks, links, queue) */
+    uint64_t device_bytes;     /* all device bytes held by the graph, scratch included */
+    uint64_t total_inserted;   /* since creation */
+    uint64_t total_deleted;
+    uint64_t total_rejected;
+    uint32_t device_status;    /* latched device status (gv_status), cleared by the read */
+    uint32_t reserved;
+} gv_stats_t;
+
+/*
+ * gv_create -- vertex dictionary, sentinels and block pool ("Dynamic vertex
+ * updates": dictionary, sentinels and one kernel attaching a sentinel to each
+ * vertex; "Edge Queue": the pool is reserved once and every block id pushed
+ * onto the queue).
+ *   cfg           configuration (NULL = all defaults).
+ *   num_vertices  initial vertex count; ids 0 .. num_vertices-1, all alive.
+ *   stream        stream for the initialisation kernels.
+ *   out           receives the graph handle.
+ * When C is given the pool is allocated here; with C = 0 it is allocated by
+ * the first edge batch, once C is known.  Errors: GV_ERR_INVALID_ARG (bad C,
+ * NULL out, misaligned pool_mem, pool too small for one block),
+ * GV_ERR_OUT_OF_MEMORY, GV_ERR_CUDA.
+ */
+gv_status gv_create(const gv_config *cfg, uint32_t num_vertices, void *stream, gv_graph **out);
+
+/* gv_destroy -- synchronises the graph's last stream and frees everything the
+ * library allocated.  NULL is a no-op. */
+gv_status gv_destroy(gv_graph *g);
+
+/*
+ * gv_bulk_build -- the first edge batch ("Initialization and batch updates";
+ * Table 3 "Bulk" rows): fixes C by the paper's rule if the configuration left
+ * it 0 (this reads two counters back, so the call synchronises `stream`
+ * once), allocates the pool if needed, then inserts the n pairs exactly as
+ * gv_insert_edges does.  On a graph that already holds edges it is a plain
+ * insert.
+ *   src, dst  n uint32 endpoints each (device or host).
+ *   d_counts  optional, 2 uint64 written on the device: {inserted, rejected}.
+ */
+gv_status gv_bulk_build(gv_graph *g, const uint32_t *src, const uint32_t *dst, uint64_t n,
+                        uint64_t *d_counts, void *stream);
+
+/*
+ * gv_insert_edges -- batched edge insert (Algorithm 1, "Dynamic edge
+ * inserts").  The batch is grouped by source on the device; each source's
+ * new edges fill the free slots of its last block, then blocks popped from
+ * the edge queue at offsets given by a prefix sum of per-source block demand
+ * (Figure 3); each new block hangs in the source's CBT at the place the bit
+ * string of its 1-based index names (Figure 4).
+ *   src, dst  n uint32 endpoints each (device or host), any order, any
+ *             duplicates.
+ *   d_counts  optional, 2 uint64 (device or host): {inserted, rejected}.
+ * If the batch needs more blocks than the queue holds, nothing is inserted,
+ * d_counts gets {0, 0} and the device status latches GV_ERR_OUT_OF_MEMORY.
+ */
+gv_status gv_insert_edges(gv_graph *g, const uint32_t *src, const uint32_t *dst, uint64_t n,
+                          uint64_t *d_counts, void *stream);
+
+/*
+ * gv_delete_edges -- batched edge delete (Algorithm 2, "Dynamic edge
+ * deletes").  Every stored entry (u, v) with (u, v) in the batch is removed,
+ * all copies of it; pairs that are not stored are ignored.  Each touched
+ * adjacency is compacted so that all its blocks but the last are full, and
+ * the emptied blocks are pushed back onto the edge queue ("Edge Queue":
+ * emptied blocks return to the queue for reuse).
+ *   src, dst  n uint32 endpoints each (device or host).
+ *   d_counts  optional, 2 uint64: {deleted entries, rejected pairs}.
+ */
+gv_status gv_delete_edges(gv_graph *g, const uint32_t *src, const uint32_t *dst, uint64_t n,
+                          uint64_t *d_counts, void *stream);
+
+/*
+ * gv_query_edges -- batched edge-existence query (Algorithm 3, "Querying
+ * operations"): out[i] = 1 if src[i] and dst[i] are valid, alive ids and
+ * (src[i], dst[i]) is stored, else 0.
+ *   src, dst  n uint32 each (device or host).
+ *   out       n uint8 results (device or host).
+ */
+gv_status gv_query_edges(gv_graph *g, const uint32_t *src, const uint32_t *dst, uint64_t n,
+                         uint8_t *out, void *stream);
+
+/*
+ * gv_neighbors -- the current out-neighbours of n vertices, as CSR in each
+ * adjacency's storage order (the in-order walk of the block tree that
+ * Algorithms 2 and 3 perform).  Invalid or deleted ids give empty lists.
+ *   vids          n uint32 vertex ids (device or host).
+ *   offsets       n+1 uint64 (device or host): offsets[i] .. offsets[i+1]
+ *                 index vids[i]'s neighbours in nbrs.
+ *   nbrs          nbr_capacity uint32 (device or host).
+ *   total         host pointer, receives the number of neighbours; required.
+ * Synchronises `stream` (the total is read back).  If the total exceeds
+ * nbr_capacity, offsets are written, nbrs is not, and GV_ERR_INVALID_ARG is
+ * returned with *total set.
+ */
+gv_status gv_neighbors(gv_graph *g, const uint32_t *vids, uint32_t n, uint64_t *offsets,
+                       uint32_t *nbrs, uint64_t nbr_capacity, uint64_t *total, void *stream);
+
+/*
+ * gv_insert_vertices -- append k vertices with ids num_vertices ..
+ * num_vertices+k-1, alive and without edges ("Dynamic vertex updates": when
+ * the dictionary is full it is reallocated at twice the size and copied by
+ * one kernel; new vertices get sentinels by the initialisation kernel).
+ *   new_ids  optional, k uint32 (device or host) receiving the new ids.
+ */
+gv_status gv_insert_vertices(gv_graph *g, uint32_t k, uint32_t *new_ids, void *stream);
+
+/*
+ * gv_delete_vertices -- delete k vertices: each valid, alive id in ids is
+ * marked dead, its blocks return to the edge queue, and every edge pointing
+ * at it is removed from every other adjacency (incoming and outgoing edges,
+ * as the paper describes for faimGraph in "Prior Work"; GraphVine itself
+ * keeps the dictionary slot, "Dynamic vertex updates").  Ids are not reused.
+ * Invalid, dead or repeated ids are ignored.
+ *   ids  k uint32 (device or host).
+ * Cost: one pass over every live adjacency.
+ */
+gv_status gv_delete_vertices(gv_graph *g, const uint32_t *ids, uint32_t k, void *stream);
+
+/*
+ * gv_export_csr -- the whole graph as CSR in storage order: offsets has
+ * num_vertices+1 uint64 entries, nbrs nbr_capacity uint32 entries (device or
+ * host), total (host) receives the edge count.  Same contract as
+ * gv_neighbors over ids 0 .. num_vertices-1.
+ */
+gv_status gv_export_csr(gv_graph *g, uint64_t *offsets, uint32_t *nbrs, uint64_t nbr_capacity,
+                        uint64_t *total, void *stream);
+
+/* gv_degrees -- num_vertices uint32 out-degrees and, if alive is not NULL,
+ * num_vertices uint8 alive flags (device or host; host outputs synchronise). */
+gv_status gv_degrees(gv_graph *g, uint32_t *deg, uint8_t *alive, void *stream);
+
+/* gv_reserve -- grow the graph's scratch memory for batches of up to
+ * max_batch pairs now, so that later calls with at most that many pairs
+ * allocate nothing (a prerequisite for capturing them in a CUDA graph). */
+gv_status gv_reserve(gv_graph *g, uint64_t max_batch);
+
+/* gv_sync -- wait for the graph's last stream; return and clear the latched
+ * device status. */
+gv_status gv_sync(gv_graph *g);
+
+/* gv_stats -- synchronise, then fill *out (host pointer).  Returns and
+ * clears the latched device status like gv_sync. */
+gv_status gv_stats(gv_graph *g, gv_stats_t *out);
+
+/*
+ * gv_validate -- structural self-check on the device, for tests: every
+ * adjacency holds ceil(deg/C) blocks, every tree walk stays inside the pool,
+ * no block is owned twice or both owned and queued, and owned + queued =
+ * pool.  Writes the number of violations to *violations (host) and
+ * synchronises.
+ */
+gv_status gv_validate(gv_graph *g, uint64_t *violations, void *stream);
+
+/* gv_status_string -- a static, human-readable name for a status code. */
+const char *gv_status_string(gv_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRAPHVINE_H */

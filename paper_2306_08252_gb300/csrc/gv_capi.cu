@@ -1,0 +1,838 @@
+// gv_capi.cu -- the extern "C" entry points declared in include/graphvine.h.
+//
+// Host code only: argument checks, device memory of the graph (dictionary,
+// pool, scratch), staging of host arrays, and the launch sequence of each
+// operation.  Every step of an operation runs in the kernels of
+// gv_kernels.cu / gv_misc.cu; nothing here touches graph data on the host.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "../../include/graphvine.h"
+#include "gv_launch.h"
+
+using gv::Dev;
+using gv::GraphView;
+using gv::LaunchCfg;
+
+namespace {
+
+constexpr uint64_t kMaxBatch = 1ull << 30;  // pairs per call (32-bit ranks and arena offsets)
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct Staging {
+    DevBuf buf[6];
+};
+
+}  // namespace
+
+struct gv_graph {
+    int device = 0;
+    int num_sms = 0;
+    uint32_t C = 0, IB = 0, flags = 0;
+    uint32_t nv = 0, vcap = 0;
+    unsigned long long P = 0;
+    uint64_t pool_bytes_cfg = 0;
+    void *pool_mem_cfg = nullptr;
+    // pool (one allocation unless caller-owned)
+    void *pool_alloc = nullptr;
+    uint64_t pool_bytes = 0;
+    uint32_t *data = nullptr, *links = nullptr, *queue = nullptr;
+    // dictionary and vertex scratch
+    uint4 *sent = nullptr;
+    uint8_t *alive = nullptr;
+    uint32_t *vcnt = nullptr, *vcur = nullptr, *vtid = nullptr, *dead = nullptr;
+    // control block
+    Dev *dev = nullptr;
+    Dev *h_dev = nullptr;  // pinned mirror for stats
+    // touched scratch
+    unsigned long long tcap = 0;
+    uint32_t *t_vid = nullptr;
+    uint4 *t_a = nullptr, *t_b = nullptr;
+    unsigned long long ocap = 0;
+    uint32_t *t_owner = nullptr;
+    // items
+    unsigned long long icap = 0;
+    uint2 *items = nullptr;
+    uint32_t *it_mask = nullptr, *it_cnt = nullptr, *it_H = nullptr, *it_S = nullptr, *it_bid = nullptr;
+    // arena
+    unsigned long long acap = 0;
+    uint32_t *arena = nullptr, *found = nullptr;
+    unsigned long long qcap = 0;
+    uint32_t *qpos = nullptr;
+    // neighbour scan partials
+    unsigned long long pcap = 0;
+    unsigned long long *partials = nullptr;
+    // validation
+    uint32_t *owner_bits = nullptr;
+    unsigned long long *vres = nullptr;
+    unsigned long long *h_small = nullptr;  // pinned scratch (8 words)
+    Staging stage;
+    cudaStream_t last_stream = nullptr;
+    uint64_t scratch_bytes = 0;
+    uint64_t dict_bytes = 0;
+};
+
+namespace {
+
+#define GV_CK(expr)                                                  \
+    do {                                                             \
+        cudaError_t _e = (expr);                                     \
+        if (_e != cudaSuccess) {                                     \
+            return _e == cudaErrorMemoryAllocation ? GV_ERR_OUT_OF_MEMORY : GV_ERR_CUDA; \
+        }                                                            \
+    } while (0)
+
+#define GV_TRY(expr)                  \
+    do {                              \
+        gv_status _s = (expr);        \
+        if (_s != GV_OK) return _s;   \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <typename T>
+gv_status dalloc(T **p, size_t count, uint64_t *acct) {
+    if (count == 0) count = 1;
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return GV_ERR_OUT_OF_MEMORY;
+    }
+    *p = static_cast<T *>(q);
+    if (acct) *acct += count * sizeof(T);
+    return GV_OK;
+}
+
+template <typename T>
+void dfree(T *&p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+GraphView view(const gv_graph *g) {
+    GraphView v;
+    v.sent = g->sent;
+    v.alive = g->alive;
+    v.data = g->data;
+    v.links = g->links;
+    v.queue = g->queue;
+    v.dev = g->dev;
+    v.P = g->P;
+    v.C = g->C;
+    v.IB = g->IB;
+    v.nv = g->nv;
+    v.vcnt = g->vcnt;
+    v.vcur = g->vcur;
+    v.vtid = g->vtid;
+    v.t_vid = g->t_vid;
+    v.t_a = g->t_a;
+    v.t_b = g->t_b;
+    v.t_owner = g->t_owner;
+    v.items = g->items;
+    v.it_mask = g->it_mask;
+    v.it_cnt = g->it_cnt;
+    v.it_H = g->it_H;
+    v.it_S = g->it_S;
+    v.it_bid = g->it_bid;
+    v.arena = g->arena;
+    v.found = g->found;
+    v.qpos = g->qpos;
+    v.dead = g->dead;
+    v.max_items = g->icap;
+    v.arena_cap = g->acap;
+    return v;
+}
+
+LaunchCfg lcfg(const gv_graph *g, cudaStream_t s) {
+    LaunchCfg lc;
+    lc.num_sms = g->num_sms;
+    lc.stream = s;
+    return lc;
+}
+
+uint32_t next_pow2(uint64_t n) {
+    uint64_t c = 1;
+    while (c < n) c <<= 1;
+    return (uint32_t)std::min<uint64_t>(c, 1ull << 31);
+}
+
+// Is p a host address (pageable or pinned) rather than device memory?
+bool is_host_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+gv_status stage_buf(gv_graph *g, int slot, size_t bytes, void **out) {
+    DevBuf &b = g->stage.buf[slot];
+    if (b.bytes < bytes) {
+        if (b.p) cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+        size_t want = std::max(bytes, (size_t)4096);
+        if (cudaMalloc(&b.p, want) != cudaSuccess) {
+            cudaGetLastError();
+            return GV_ERR_OUT_OF_MEMORY;
+        }
+        b.bytes = want;
+    }
+    *out = b.p;
+    return GV_OK;
+}
+
+// Device view of an input array: itself, or a staged copy of a host array.
+gv_status input_ptr(gv_graph *g, int slot, const void *p, size_t bytes, cudaStream_t s, const void **out) {
+    if (!is_host_ptr(p) || bytes == 0) {
+        *out = p;
+        return GV_OK;
+    }
+    void *d = nullptr;
+    GV_TRY(stage_buf(g, slot, bytes, &d));
+    GV_CK(cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, s));
+    *out = d;
+    return GV_OK;
+}
+
+// Device target for an output array; *host is set when the caller's array
+// is in host memory and must be copied back after the kernels.
+gv_status output_ptr(gv_graph *g, int slot, void *p, size_t bytes, void **out, bool *host) {
+    *host = is_host_ptr(p);
+    if (!*host) {
+        *out = p;
+        return GV_OK;
+    }
+    return stage_buf(g, slot, bytes, out);
+}
+
+// ------------------------------------------------------------- capacities
+
+gv_status ensure_vertex_capacity(gv_graph *g, uint32_t need, cudaStream_t s) {
+    if (need <= g->vcap) return GV_OK;
+    uint32_t cap = std::max<uint32_t>(g->vcap ? g->vcap : 1, 1);
+    while (cap < need) cap *= 2;  // dictionary doubles ("Dynamic vertex updates")
+    uint4 *sent = nullptr;
+    uint8_t *alive = nullptr;
+    uint32_t *vcnt = nullptr, *vcur = nullptr, *vtid = nullptr, *dead = nullptr;
+    uint64_t acct = 0;
+    gv_status st;
+    if ((st = dalloc(&sent, cap, &acct)) != GV_OK || (st = dalloc(&alive, cap, &acct)) != GV_OK ||
+        (st = dalloc(&vcnt, cap, &acct)) != GV_OK || (st = dalloc(&vcur, cap, &acct)) != GV_OK ||
+        (st = dalloc(&vtid, cap, &acct)) != GV_OK || (st = dalloc(&dead, cap / 32 + 1, &acct)) != GV_OK) {
+        dfree(sent); dfree(alive); dfree(vcnt); dfree(vcur); dfree(vtid); dfree(dead);
+        return st;
+    }
+    GV_CK(cudaMemsetAsync(vcnt, 0, (size_t)cap * 4, s));
+    GV_CK(cudaMemsetAsync(vcur, 0, (size_t)cap * 4, s));
+    GV_CK(cudaMemsetAsync(dead, 0, (size_t)(cap / 32 + 1) * 4, s));
+    GV_CK(cudaMemsetAsync(alive, 0, cap, s));
+    if (g->vcap) {
+        GV_CK(gv::launch_copy_dictionary(sent, alive, g->sent, g->alive, g->nv, lcfg(g, s)));
+        GV_CK(cudaStreamSynchronize(s));
+    }
+    dfree(g->sent); dfree(g->alive); dfree(g->vcnt); dfree(g->vcur); dfree(g->vtid); dfree(g->dead);
+    g->sent = sent;
+    g->alive = alive;
+    g->vcnt = vcnt;
+    g->vcur = vcur;
+    g->vtid = vtid;
+    g->dead = dead;
+    g->vcap = cap;
+    g->dict_bytes = acct;
+    return GV_OK;
+}
+
+gv_status ensure_touched(gv_graph *g, unsigned long long need) {
+    if (need <= g->tcap && g->tcap) return GV_OK;
+    unsigned long long cap = std::max<unsigned long long>(need, std::max<unsigned long long>(2 * g->tcap, 1024));
+    dfree(g->t_vid); dfree(g->t_a); dfree(g->t_b);
+    g->tcap = 0;
+    GV_TRY(dalloc(&g->t_vid, cap, &g->scratch_bytes));
+    GV_TRY(dalloc(&g->t_a, cap, &g->scratch_bytes));
+    GV_TRY(dalloc(&g->t_b, cap, &g->scratch_bytes));
+    g->tcap = cap;
+    return GV_OK;
+}
+
+gv_status ensure_owner(gv_graph *g, unsigned long long need) {
+    if (need <= g->ocap && g->ocap) return GV_OK;
+    unsigned long long cap = std::max<unsigned long long>(need, std::max<unsigned long long>(2 * g->ocap, 1024));
+    dfree(g->t_owner);
+    g->ocap = 0;
+    GV_TRY(dalloc(&g->t_owner, cap, &g->scratch_bytes));
+    g->ocap = cap;
+    return GV_OK;
+}
+
+gv_status ensure_items(gv_graph *g, unsigned long long need) {
+    if (need <= g->icap && g->icap) return GV_OK;
+    unsigned long long cap = std::max<unsigned long long>(need, std::max<unsigned long long>(2 * g->icap, 1024));
+    dfree(g->items); dfree(g->it_mask); dfree(g->it_cnt); dfree(g->it_H); dfree(g->it_S); dfree(g->it_bid);
+    g->icap = 0;
+    GV_TRY(dalloc(&g->items, cap, &g->scratch_bytes));
+    GV_TRY(dalloc(&g->it_mask, cap * gv::MASK_WORDS, &g->scratch_bytes));
+    GV_TRY(dalloc(&g->it_cnt, cap, &g->scratch_bytes));
+    GV_TRY(dalloc(&g->it_H, cap, &g->scratch_bytes));
+    GV_TRY(dalloc(&g->it_S, cap, &g->scratch_bytes));
+    GV_TRY(dalloc(&g->it_bid, cap * (g->IB ? g->IB : 32), &g->scratch_bytes));
+    g->icap = cap;
+    return GV_OK;
+}
+
+gv_status ensure_arena(gv_graph *g, unsigned long long words, bool query, unsigned long long nq) {
+    if (words > g->acap || !g->acap) {
+        unsigned long long cap = std::max<unsigned long long>(words, std::max<unsigned long long>(2 * g->acap, 4096));
+        dfree(g->arena); dfree(g->found);
+        g->acap = 0;
+        GV_TRY(dalloc(&g->arena, cap, &g->scratch_bytes));
+        GV_TRY(dalloc(&g->found, cap, &g->scratch_bytes));
+        g->acap = cap;
+    }
+    if (query && (nq > g->qcap || !g->qcap)) {
+        unsigned long long cap = std::max<unsigned long long>(nq, std::max<unsigned long long>(2 * g->qcap, 4096));
+        dfree(g->qpos);
+        g->qcap = 0;
+        GV_TRY(dalloc(&g->qpos, cap, &g->scratch_bytes));
+        g->qcap = cap;
+    }
+    return GV_OK;
+}
+
+// Items over all touched sources never exceed touched + pool blocks / IB.
+unsigned long long item_bound(const gv_graph *g, unsigned long long touched) {
+    return touched + (g->IB ? (g->P + g->IB - 1) / g->IB : 0) + 1;
+}
+
+// Pool: one allocation holding block storage, links and the edge queue.
+gv_status setup_pool(gv_graph *g, uint32_t C, cudaStream_t s) {
+    if (C < 4 || C > 512 || (C % 4) != 0) return GV_ERR_INVALID_ARG;
+    g->C = C;
+    g->IB = std::min<uint32_t>(32, std::max<uint32_t>(1, 512 / C));
+    uint64_t bytes = g->pool_bytes_cfg;
+    if (bytes == 0) {
+        size_t fr = 0, tot = 0;
+        GV_CK(cudaMemGetInfo(&fr, &tot));
+        bytes = fr / 2;  // "Edge Queue": at least half of the GPU memory
+    }
+    const uint64_t per_block = 4ull * C + 8 + 4;
+    unsigned long long P = bytes / per_block;
+    // leave room for alignment padding between the three arrays
+    while (P > 0 && P * per_block + 512 > bytes) --P;
+    if (P > 0xFFFFFFFEull) P = 0xFFFFFFFEull;
+    if (P == 0) return GV_ERR_INVALID_ARG;
+    char *base = nullptr;
+    if (g->pool_mem_cfg) {
+        if (reinterpret_cast<uintptr_t>(g->pool_mem_cfg) % 16 != 0) return GV_ERR_INVALID_ARG;
+        base = static_cast<char *>(g->pool_mem_cfg);
+    } else {
+        void *p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return GV_ERR_OUT_OF_MEMORY;
+        }
+        g->pool_alloc = p;
+        base = static_cast<char *>(p);
+    }
+    auto align = [](uint64_t x) { return (x + 255) & ~255ull; };
+    uint64_t off = 0;
+    g->data = reinterpret_cast<uint32_t *>(base + off);
+    off = align(off + P * C * 4ull);
+    g->links = reinterpret_cast<uint32_t *>(base + off);
+    off = align(off + P * 8ull);
+    g->queue = reinterpret_cast<uint32_t *>(base + off);
+    g->P = P;
+    g->pool_bytes = bytes;
+    GV_CK(gv::launch_init_queue(g->queue, P, lcfg(g, s)));
+    // Dev: queue holds every block
+    Dev init;
+    std::memset(&init, 0, sizeof(init));
+    GV_CK(cudaMemcpyAsync(&g->dev->q_back, &P, sizeof(P), cudaMemcpyHostToDevice, s));
+    GV_CK(cudaStreamSynchronize(s));
+    GV_TRY(ensure_items(g, item_bound(g, 1024)));
+    return GV_OK;
+}
+
+// Scratch for a pair batch of n (insert / delete / query).
+gv_status ensure_batch(gv_graph *g, uint64_t n, int mode) {
+    const unsigned long long touched = std::min<unsigned long long>(n, g->nv ? g->nv : 1);
+    GV_TRY(ensure_touched(g, touched));
+    if (mode == gv::MODE_INSERT) {
+        GV_TRY(ensure_owner(g, (g->C ? n / g->C : n) + touched + 1));
+    } else {
+        GV_TRY(ensure_items(g, item_bound(g, touched)));
+        GV_TRY(ensure_arena(g, 4 * n + 64, mode == gv::MODE_QUERY, n));
+    }
+    return GV_OK;
+}
+
+gv_status check_launch() {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return GV_ERR_CUDA;
+    return GV_OK;
+}
+
+// C by the paper's rule from the counted first batch: average degree of the
+// sources with at least one edge, rounded up to a multiple of 4 (>= 4).
+uint32_t rule_capacity(unsigned long long valid, unsigned long long touched) {
+    if (touched == 0 || valid == 0) return 4;
+    unsigned long long avg = (valid + touched - 1) / touched;
+    unsigned long long c = (avg + 3) / 4 * 4;
+    if (c < 4) c = 4;
+    if (c > 512) c = 512;
+    return (uint32_t)c;
+}
+
+gv_status insert_impl(gv_graph *g, const uint32_t *src, const uint32_t *dst, uint64_t n,
+                      uint64_t *counts, cudaStream_t s) {
+    if (!g) return GV_ERR_INVALID_ARG;
+    if (n > kMaxBatch) return GV_ERR_INVALID_ARG;
+    if (n > 0 && (!src || !dst)) return GV_ERR_INVALID_ARG;
+    if (g->flags & GV_DEDUP) return GV_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    g->last_stream = s;
+    const void *dsrc = src, *ddst = dst;
+    GV_TRY(input_ptr(g, 0, src, n * 4, s, &dsrc));
+    GV_TRY(input_ptr(g, 1, dst, n * 4, s, &ddst));
+    void *dcounts = counts;
+    bool host_counts = false;
+    if (counts) GV_TRY(output_ptr(g, 2, counts, 16, &dcounts, &host_counts));
+    const unsigned long long touched = std::min<unsigned long long>(n, g->nv ? g->nv : 1);
+    GV_TRY(ensure_touched(g, touched));
+    if (g->C == 0) {
+        // First batch fixes C (paper rule), then the pool can be laid out.
+        GraphView v = view(g);
+        GV_CK(gv::launch_count(gv::MODE_INSERT, v, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, lcfg(g, s)));
+        GV_CK(cudaMemcpyAsync(g->h_small, &g->dev->call_b, 8, cudaMemcpyDeviceToHost, s));
+        unsigned int nt = 0;
+        GV_CK(cudaMemcpyAsync(&g->h_small[1], &g->dev->n_touched, 4, cudaMemcpyDeviceToHost, s));
+        GV_CK(cudaStreamSynchronize(s));
+        nt = (unsigned int)(g->h_small[1] & 0xFFFFFFFFull);
+        const unsigned long long valid = n - g->h_small[0];
+        GV_TRY(setup_pool(g, rule_capacity(valid, nt), s));
+        GV_TRY(ensure_batch(g, n, gv::MODE_INSERT));
+        GraphView v2 = view(g);
+        GV_CK(gv::launch_insert_tail(v2, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, g->tcap,
+                                     (unsigned long long *)dcounts, lcfg(g, s)));
+    } else {
+        GV_TRY(ensure_batch(g, n, gv::MODE_INSERT));
+        if (n == 0) {
+            if (counts) GV_CK(cudaMemsetAsync(dcounts, 0, 16, s));
+        } else {
+            GraphView v = view(g);
+            GV_CK(gv::launch_count(gv::MODE_INSERT, v, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, lcfg(g, s)));
+            GV_CK(gv::launch_insert_tail(v, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, g->tcap,
+                                         (unsigned long long *)dcounts, lcfg(g, s)));
+        }
+    }
+    if (host_counts) {
+        GV_CK(cudaMemcpyAsync(counts, dcounts, 16, cudaMemcpyDeviceToHost, s));
+        GV_CK(cudaStreamSynchronize(s));
+    }
+    return check_launch();
+}
+
+gv_status member_impl(gv_graph *g, int mode, const uint32_t *src, const uint32_t *dst, uint64_t n,
+                      uint64_t *counts, uint8_t *qout, cudaStream_t s) {
+    if (!g) return GV_ERR_INVALID_ARG;
+    if (n > kMaxBatch) return GV_ERR_INVALID_ARG;
+    if (n > 0 && (!src || !dst)) return GV_ERR_INVALID_ARG;
+    if (mode == gv::MODE_QUERY && n > 0 && !qout) return GV_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    g->last_stream = s;
+    void *dcounts = counts;
+    bool host_counts = false;
+    if (counts) GV_TRY(output_ptr(g, 2, counts, 16, &dcounts, &host_counts));
+    if (n == 0 || g->C == 0) {
+        // Empty batch, or no edge stored yet (C is fixed by the first edge
+        // batch): nothing can match.  Deletes still count rejected pairs.
+        if (mode == gv::MODE_QUERY) {
+            if (n) {
+                void *dq = qout;
+                bool hq = false;
+                GV_TRY(output_ptr(g, 3, qout, n, &dq, &hq));
+                GV_CK(cudaMemsetAsync(dq, 0, n, s));
+                if (hq) {
+                    GV_CK(cudaMemcpyAsync(qout, dq, n, cudaMemcpyDeviceToHost, s));
+                    GV_CK(cudaStreamSynchronize(s));
+                }
+            }
+            return check_launch();
+        }
+        if (counts) {
+            GV_CK(cudaMemsetAsync(dcounts, 0, 16, s));
+            if (n) {
+                const void *dsrc = src, *ddst = dst;
+                GV_TRY(input_ptr(g, 0, src, n * 4, s, &dsrc));
+                GV_TRY(input_ptr(g, 1, dst, n * 4, s, &ddst));
+                GV_CK(gv::launch_count_rejects(view(g), (const uint32_t *)dsrc, (const uint32_t *)ddst, n,
+                                               (unsigned long long *)dcounts + 1, lcfg(g, s)));
+            }
+            if (host_counts) {
+                GV_CK(cudaMemcpyAsync(counts, dcounts, 16, cudaMemcpyDeviceToHost, s));
+                GV_CK(cudaStreamSynchronize(s));
+            }
+        }
+        return check_launch();
+    }
+    const void *dsrc = src, *ddst = dst;
+    GV_TRY(input_ptr(g, 0, src, n * 4, s, &dsrc));
+    GV_TRY(input_ptr(g, 1, dst, n * 4, s, &ddst));
+    void *dq = qout;
+    bool hq = false;
+    if (mode == gv::MODE_QUERY) GV_TRY(output_ptr(g, 3, qout, n, &dq, &hq));
+    GV_TRY(ensure_batch(g, n, mode));
+    GraphView v = view(g);
+    GV_CK(gv::launch_count(mode, v, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, lcfg(g, s)));
+    GV_CK(gv::launch_member_tail(mode, v, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, g->tcap,
+                                 (unsigned long long *)dcounts, (uint8_t *)dq, lcfg(g, s)));
+    if (host_counts) GV_CK(cudaMemcpyAsync(counts, dcounts, 16, cudaMemcpyDeviceToHost, s));
+    if (hq) GV_CK(cudaMemcpyAsync(qout, dq, n, cudaMemcpyDeviceToHost, s));
+    if (host_counts || hq) GV_CK(cudaStreamSynchronize(s));
+    return check_launch();
+}
+
+gv_status neighbors_impl(gv_graph *g, const uint32_t *vids, uint32_t n, uint64_t *offsets, uint32_t *nbrs,
+                         uint64_t cap, uint64_t *total, cudaStream_t s, bool all) {
+    if (!g || !total || !offsets) return GV_ERR_INVALID_ARG;
+    if (n > 0 && !all && !vids) return GV_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    g->last_stream = s;
+    const void *dv = vids;
+    if (all) {
+        void *d = nullptr;
+        GV_TRY(stage_buf(g, 0, (size_t)n * 4 + 4, &d));
+        GV_CK(gv::launch_iota((uint32_t *)d, 0, n, lcfg(g, s)));
+        dv = d;
+    } else {
+        GV_TRY(input_ptr(g, 0, vids, (size_t)n * 4, s, &dv));
+    }
+    void *doff = offsets;
+    bool hoff = false;
+    GV_TRY(output_ptr(g, 1, offsets, ((size_t)n + 1) * 8, &doff, &hoff));
+    const unsigned long long nchunks = ((unsigned long long)n + 1023) / 1024;
+    if (nchunks + 1 > g->pcap) {
+        dfree(g->partials);
+        g->pcap = 0;
+        GV_TRY(dalloc(&g->partials, nchunks + 1, &g->scratch_bytes));
+        g->pcap = nchunks + 1;
+    }
+    GraphView v = view(g);
+    GV_CK(gv::launch_neighbor_offsets(v, (const uint32_t *)dv, n, (unsigned long long *)doff, g->partials, lcfg(g, s)));
+    GV_CK(cudaMemcpyAsync(g->h_small, (unsigned long long *)doff + n, 8, cudaMemcpyDeviceToHost, s));
+    GV_CK(cudaStreamSynchronize(s));
+    *total = g->h_small[0];
+    if (hoff) {
+        GV_CK(cudaMemcpyAsync(offsets, doff, ((size_t)n + 1) * 8, cudaMemcpyDeviceToHost, s));
+        GV_CK(cudaStreamSynchronize(s));
+    }
+    if (*total > cap) return GV_ERR_INVALID_ARG;
+    if (*total == 0 || g->C == 0) return check_launch();
+    if (!nbrs) return GV_ERR_INVALID_ARG;
+    void *dn = nbrs;
+    bool hn = false;
+    GV_TRY(output_ptr(g, 2, nbrs, (size_t)*total * 4, &dn, &hn));
+    GV_TRY(ensure_touched(g, n));
+    GV_TRY(ensure_items(g, item_bound(g, n)));
+    v = view(g);
+    GV_CK(gv::launch_neighbor_copy(v, (const uint32_t *)dv, n, (const unsigned long long *)doff, (uint32_t *)dn,
+                                   lcfg(g, s)));
+    if (hn) GV_CK(cudaMemcpyAsync(nbrs, dn, (size_t)*total * 4, cudaMemcpyDeviceToHost, s));
+    GV_CK(cudaStreamSynchronize(s));
+    return check_launch();
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+
+extern "C" {
+
+const char *gv_status_string(gv_status s) {
+    switch (s) {
+    case GV_OK: return "GV_OK";
+    case GV_ERR_INVALID_ARG: return "GV_ERR_INVALID_ARG";
+    case GV_ERR_OUT_OF_MEMORY: return "GV_ERR_OUT_OF_MEMORY";
+    case GV_ERR_CUDA: return "GV_ERR_CUDA";
+    case GV_ERR_TIMEOUT: return "GV_ERR_TIMEOUT";
+    case GV_ERR_STATE: return "GV_ERR_STATE";
+    }
+    return "GV_ERR_UNKNOWN";
+}
+
+gv_status gv_create(const gv_config *cfg, uint32_t num_vertices, void *stream, gv_graph **out) {
+    if (!out) return GV_ERR_INVALID_ARG;
+    *out = nullptr;
+    gv_config c;
+    std::memset(&c, 0, sizeof(c));
+    if (cfg) c = *cfg;
+    if (c.block_capacity != 0 && (c.block_capacity < 4 || c.block_capacity > 512 || c.block_capacity % 4))
+        return GV_ERR_INVALID_ARG;
+    if (c.flags & ~GV_DEDUP) return GV_ERR_INVALID_ARG;
+    if (c.flags & GV_DEDUP) return GV_ERR_INVALID_ARG;  // set semantics: not provided by this build
+    if (c.pool_mem && c.pool_bytes == 0) return GV_ERR_INVALID_ARG;
+    if (num_vertices > 0x7FFFFFFFu) return GV_ERR_INVALID_ARG;
+    gv_graph *g = new (std::nothrow) gv_graph();
+    if (!g) return GV_ERR_OUT_OF_MEMORY;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaGetDevice(&g->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete g;
+        return GV_ERR_CUDA;
+    }
+    cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+    if (g->num_sms <= 0) g->num_sms = 1;
+    g->flags = c.flags;
+    g->pool_bytes_cfg = c.pool_bytes;
+    g->pool_mem_cfg = c.pool_mem;
+    g->last_stream = s;
+    gv_status st = GV_OK;
+    do {
+        if ((st = dalloc(&g->dev, 1, &g->scratch_bytes)) != GV_OK) break;
+        if (cudaMemsetAsync(g->dev, 0, sizeof(Dev), s) != cudaSuccess) { st = GV_ERR_CUDA; break; }
+        void *hp = nullptr;
+        if (cudaMallocHost(&hp, 64) != cudaSuccess) { st = GV_ERR_OUT_OF_MEMORY; break; }
+        g->h_small = static_cast<unsigned long long *>(hp);
+        if (cudaMallocHost(&hp, sizeof(Dev)) != cudaSuccess) { st = GV_ERR_OUT_OF_MEMORY; break; }
+        g->h_dev = static_cast<Dev *>(hp);
+        uint32_t want = std::max<uint32_t>(num_vertices, c.vertex_capacity);
+        want = next_pow2(std::max<uint32_t>(want, 1));  // "closest power of 2" at or above
+        if ((st = ensure_vertex_capacity(g, want, s)) != GV_OK) break;
+        g->nv = num_vertices;
+        GraphView v = view(g);
+        if (gv::launch_init_vertices(v, 0, num_vertices, lcfg(g, s)) != cudaSuccess) { st = GV_ERR_CUDA; break; }
+        if (c.block_capacity) {
+            if ((st = setup_pool(g, c.block_capacity, s)) != GV_OK) break;
+        }
+        if (cudaStreamSynchronize(s) != cudaSuccess) { st = GV_ERR_CUDA; break; }
+    } while (0);
+    if (st != GV_OK) {
+        cudaGetLastError();
+        gv_destroy(g);
+        return st;
+    }
+    *out = g;
+    return GV_OK;
+}
+
+gv_status gv_destroy(gv_graph *g) {
+    if (!g) return GV_OK;
+    {
+        DeviceGuard dg(g->device);
+        cudaStreamSynchronize(g->last_stream);
+        cudaGetLastError();
+        if (g->pool_alloc) cudaFree(g->pool_alloc);
+        dfree(g->sent); dfree(g->alive); dfree(g->vcnt); dfree(g->vcur); dfree(g->vtid); dfree(g->dead);
+        dfree(g->dev);
+        dfree(g->t_vid); dfree(g->t_a); dfree(g->t_b); dfree(g->t_owner);
+        dfree(g->items); dfree(g->it_mask); dfree(g->it_cnt); dfree(g->it_H); dfree(g->it_S); dfree(g->it_bid);
+        dfree(g->arena); dfree(g->found); dfree(g->qpos); dfree(g->partials);
+        dfree(g->owner_bits); dfree(g->vres);
+        for (auto &b : g->stage.buf) dfree(b.p);
+        if (g->h_small) cudaFreeHost(g->h_small);
+        if (g->h_dev) cudaFreeHost(g->h_dev);
+        cudaGetLastError();
+    }
+    delete g;
+    return GV_OK;
+}
+
+gv_status gv_bulk_build(gv_graph *g, const uint32_t *src, const uint32_t *dst, uint64_t n, uint64_t *d_counts,
+                        void *stream) {
+    return insert_impl(g, src, dst, n, d_counts, static_cast<cudaStream_t>(stream));
+}
+
+gv_status gv_insert_edges(gv_graph *g, const uint32_t *src, const uint32_t *dst, uint64_t n, uint64_t *d_counts,
+                          void *stream) {
+    return insert_impl(g, src, dst, n, d_counts, static_cast<cudaStream_t>(stream));
+}
+
+gv_status gv_delete_edges(gv_graph *g, const uint32_t *src, const uint32_t *dst, uint64_t n, uint64_t *d_counts,
+                          void *stream) {
+    return member_impl(g, gv::MODE_DELETE, src, dst, n, d_counts, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+gv_status gv_query_edges(gv_graph *g, const uint32_t *src, const uint32_t *dst, uint64_t n, uint8_t *out,
+                         void *stream) {
+    return member_impl(g, gv::MODE_QUERY, src, dst, n, nullptr, out, static_cast<cudaStream_t>(stream));
+}
+
+gv_status gv_neighbors(gv_graph *g, const uint32_t *vids, uint32_t n, uint64_t *offsets, uint32_t *nbrs,
+                       uint64_t nbr_capacity, uint64_t *total, void *stream) {
+    return neighbors_impl(g, vids, n, offsets, nbrs, nbr_capacity, total, static_cast<cudaStream_t>(stream), false);
+}
+
+gv_status gv_export_csr(gv_graph *g, uint64_t *offsets, uint32_t *nbrs, uint64_t nbr_capacity, uint64_t *total,
+                        void *stream) {
+    if (!g) return GV_ERR_INVALID_ARG;
+    return neighbors_impl(g, nullptr, g->nv, offsets, nbrs, nbr_capacity, total, static_cast<cudaStream_t>(stream),
+                          true);
+}
+
+gv_status gv_degrees(gv_graph *g, uint32_t *deg, uint8_t *alive, void *stream) {
+    if (!g || (!deg && g->nv)) return GV_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    g->last_stream = s;
+    if (g->nv == 0) return GV_OK;
+    void *dd = deg, *da = alive;
+    bool hd = false, ha = false;
+    GV_TRY(output_ptr(g, 0, deg, (size_t)g->nv * 4, &dd, &hd));
+    if (alive) GV_TRY(output_ptr(g, 1, alive, g->nv, &da, &ha));
+    GV_CK(gv::launch_degrees(view(g), (uint32_t *)dd, (uint8_t *)da, lcfg(g, s)));
+    if (hd) GV_CK(cudaMemcpyAsync(deg, dd, (size_t)g->nv * 4, cudaMemcpyDeviceToHost, s));
+    if (ha) GV_CK(cudaMemcpyAsync(alive, da, g->nv, cudaMemcpyDeviceToHost, s));
+    if (hd || ha) GV_CK(cudaStreamSynchronize(s));
+    return check_launch();
+}
+
+gv_status gv_insert_vertices(gv_graph *g, uint32_t k, uint32_t *new_ids, void *stream) {
+    if (!g) return GV_ERR_INVALID_ARG;
+    if ((uint64_t)g->nv + k > 0x7FFFFFFFull) return GV_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    g->last_stream = s;
+    if (k == 0) return GV_OK;
+    const uint32_t first = g->nv;
+    GV_TRY(ensure_vertex_capacity(g, first + k, s));
+    GV_CK(gv::launch_init_vertices(view(g), first, first + k, lcfg(g, s)));
+    g->nv = first + k;
+    if (new_ids) {
+        void *d = new_ids;
+        bool h = false;
+        GV_TRY(output_ptr(g, 4, new_ids, (size_t)k * 4, &d, &h));
+        GV_CK(gv::launch_iota((uint32_t *)d, first, k, lcfg(g, s)));
+        if (h) {
+            GV_CK(cudaMemcpyAsync(new_ids, d, (size_t)k * 4, cudaMemcpyDeviceToHost, s));
+            GV_CK(cudaStreamSynchronize(s));
+        }
+    }
+    return check_launch();
+}
+
+gv_status gv_delete_vertices(gv_graph *g, const uint32_t *ids, uint32_t k, void *stream) {
+    if (!g) return GV_ERR_INVALID_ARG;
+    if (k > 0 && !ids) return GV_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    g->last_stream = s;
+    if (k == 0) return GV_OK;
+    const void *di = ids;
+    GV_TRY(input_ptr(g, 0, ids, (size_t)k * 4, s, &di));
+    GV_TRY(ensure_touched(g, std::max<unsigned long long>(g->nv, 1)));
+    if (g->C == 0) {
+        // No pool yet, hence no edges: only the alive flags change.  Reuse
+        // the delete kernels with an empty pool view (no items are formed).
+        GV_TRY(ensure_items(g, 1024));
+    } else {
+        GV_TRY(ensure_items(g, item_bound(g, g->nv)));
+    }
+    GraphView v = view(g);
+    if (v.C == 0) {
+        v.C = 4;
+        v.IB = 32;
+    }
+    GV_CK(gv::launch_vertex_delete(v, (const uint32_t *)di, k, lcfg(g, s)));
+    return check_launch();
+}
+
+gv_status gv_reserve(gv_graph *g, uint64_t max_batch) {
+    if (!g || max_batch > kMaxBatch) return GV_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    GV_TRY(ensure_touched(g, std::min<unsigned long long>(max_batch, g->nv ? g->nv : 1)));
+    GV_TRY(ensure_owner(g, (g->C ? max_batch / g->C : max_batch) + std::min<unsigned long long>(max_batch, g->nv) + 1));
+    if (g->C) GV_TRY(ensure_items(g, item_bound(g, std::min<unsigned long long>(max_batch, g->nv ? g->nv : 1))));
+    GV_TRY(ensure_arena(g, 4 * max_batch + 64, true, max_batch));
+    for (int slot = 0; slot < 4; ++slot) {
+        void *d = nullptr;
+        GV_TRY(stage_buf(g, slot, max_batch * 4 + 64, &d));
+    }
+    return GV_OK;
+}
+
+gv_status gv_sync(gv_graph *g) {
+    if (!g) return GV_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    GV_CK(cudaStreamSynchronize(g->last_stream));
+    unsigned int st = 0;
+    GV_CK(cudaMemcpy(&st, &g->dev->status, sizeof(st), cudaMemcpyDeviceToHost));
+    if (st) GV_CK(cudaMemset(&g->dev->status, 0, sizeof(st)));
+    return static_cast<gv_status>(st);
+}
+
+gv_status gv_stats(gv_graph *g, gv_stats_t *out) {
+    if (!g || !out) return GV_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    GV_CK(cudaStreamSynchronize(g->last_stream));
+    GV_CK(cudaMemcpy(g->h_dev, g->dev, sizeof(Dev), cudaMemcpyDeviceToHost));
+    const Dev &d = *g->h_dev;
+    std::memset(out, 0, sizeof(*out));
+    out->num_vertices = g->nv;
+    out->vertex_capacity = g->vcap;
+    out->block_capacity = g->C;
+    out->flags = g->flags;
+    out->num_edges = d.num_edges;
+    out->pool_blocks = g->P;
+    out->pool_blocks_free = d.q_back - d.q_front;
+    out->pool_blocks_used = g->P - out->pool_blocks_free;
+    out->pool_bytes = g->pool_bytes;
+    uint64_t stage_bytes = 0;
+    for (auto &b : g->stage.buf) stage_bytes += b.bytes;
+    out->device_bytes = (g->pool_alloc ? g->pool_bytes : 0) + g->dict_bytes + g->scratch_bytes + stage_bytes;
+    out->total_inserted = d.tot_ins;
+    out->total_deleted = d.tot_del;
+    out->total_rejected = d.tot_rej;
+    out->device_status = d.status;
+    if (d.status) GV_CK(cudaMemset(&g->dev->status, 0, sizeof(unsigned int)));
+    return static_cast<gv_status>(d.status);
+}
+
+gv_status gv_validate(gv_graph *g, uint64_t *violations, void *stream) {
+    if (!g || !violations) return GV_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    g->last_stream = s;
+    const unsigned long long words = g->P / 32 + 1;
+    dfree(g->owner_bits);
+    GV_TRY(dalloc(&g->owner_bits, words, nullptr));
+    if (!g->vres) GV_TRY(dalloc(&g->vres, 4, nullptr));
+    GV_CK(cudaMemsetAsync(g->owner_bits, 0, words * 4, s));
+    GV_CK(cudaMemsetAsync(g->vres, 0, 32, s));
+    GraphView v = view(g);
+    GV_CK(gv::launch_validate(v, g->owner_bits, g->vres, lcfg(g, s)));
+    unsigned long long r[4];
+    GV_CK(cudaMemcpyAsync(r, g->vres, 32, cudaMemcpyDeviceToHost, s));
+    GV_CK(cudaMemcpyAsync(g->h_dev, g->dev, sizeof(Dev), cudaMemcpyDeviceToHost, s));
+    GV_CK(cudaStreamSynchronize(s));
+    uint64_t viol = r[0];
+    if (r[1] != g->h_dev->num_edges) ++viol;         // degree sum = edge count
+    if (g->C && r[2] + r[3] != g->P) ++viol;          // owned + queued = pool
+    *violations = viol;
+    dfree(g->owner_bits);
+    return check_launch();
+}
+
+}  // extern "C"

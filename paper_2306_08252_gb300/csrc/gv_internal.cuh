@@ -1,0 +1,280 @@
+// gv_internal.cuh -- device-side layout and helpers of the GraphVine GB300 library.
+//
+// Layout in HBM (one graph):
+//   sent[vcap]      uint4 per vertex, the edge sentinel: {deg, nblocks, root, last}.
+//                   deg = stored entries, nblocks = ceil(deg / C) (adjacencies are
+//                   kept compacted), root = block id of heap index 1 of the CBT,
+//                   last = block id of heap index nblocks (where the next insert
+//                   starts, "last insert edge block" of the paper).  NIL when empty.
+//   alive[vcap]     uint8 per vertex.
+//   data[P * C]     uint32 destination ids; block b holds slots data[b*C .. b*C+C).
+//   links[2 * P]    uint32 child block ids of block b: links[2b] left, links[2b+1]
+//                   right; heap index k has children 2k and 2k+1 (Figure 2).
+//   queue[P]        uint32 ring of free block ids (the paper's edge queue); the
+//                   free ids sit at positions [q_front, q_back) modulo P.
+//   gv_dev          control block: queue positions, counters, status word.
+// Block ids are uint32 indices into data/links, so the pool may hold up to
+// 2^32 - 1 blocks.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gv {
+
+constexpr uint32_t NIL = 0xFFFFFFFFu;
+constexpr uint32_t EMPTY_KEY = 0xFFFFFFFFu;
+constexpr uint32_t FULL = 0xFFFFFFFFu;
+
+// Device control block (one per graph, device memory).
+struct Dev {
+    unsigned long long q_front;     // edge queue: next pop position
+    unsigned long long q_back;      // edge queue: next push position
+    unsigned long long num_edges;   // stored entries
+    unsigned long long tot_ins, tot_del, tot_rej;
+    // per-call scratch counters (reset by the finalize kernels)
+    unsigned long long alloc_total; // blocks popped by this call
+    unsigned long long free_total;  // blocks pushed by this call
+    unsigned long long arena_used;  // words of the membership arena used
+    unsigned long long call_a;      // inserted / deleted entries of this call
+    unsigned long long call_b;      // rejected pairs of this call
+    unsigned long long call_c;      // extra per-call counter (sums)
+    unsigned int n_touched;         // touched sources of this call
+    unsigned int n_items;           // work items of this call
+    unsigned int done_ctas;         // last-CTA ticket of the finalize kernels
+    unsigned int status;            // latched device status (gv_status), sticky
+    unsigned int abort;             // set when this call must not mutate the graph
+    unsigned int pad[3];
+};
+
+// Everything a kernel needs to know about one graph (passed by value).
+struct GraphView {
+    uint4 *sent;
+    uint8_t *alive;
+    uint32_t *data;
+    uint32_t *links;
+    uint32_t *queue;
+    Dev *dev;
+    unsigned long long P;   // pool blocks
+    uint32_t C;             // entries per block
+    uint32_t IB;            // blocks per work item (IB * C <= 512)
+    uint32_t nv;            // vertex count
+    // vertex-indexed scratch (zero between calls)
+    uint32_t *vcnt;         // batch entries per source
+    uint32_t *vcur;         // rank cursor per source
+    uint32_t *vtid;         // touched index of a source (valid while vcnt > 0)
+    // touched-indexed scratch
+    uint32_t *t_vid;        // touched source ids
+    uint4 *t_a;             // per-touched info A (op specific)
+    uint4 *t_b;             // per-touched info B (op specific)
+    uint32_t *t_owner;      // insert: pop index -> touched index
+    // work items (membership ops)
+    uint2 *items;           // {touched index, chunk}
+    uint32_t *it_mask;      // 16 words per item: survivor bits by slot
+    uint32_t *it_cnt;       // survivors per item
+    uint32_t *it_H;         // exclusive prefix of holes below the new degree
+    uint32_t *it_S;         // exclusive prefix of survivors at/above the new degree
+    uint32_t *it_bid;       // IB block ids per item
+    // membership arena
+    uint32_t *arena;        // list entries / hash keys
+    uint32_t *found;        // query: hit flags, parallel to arena
+    uint32_t *qpos;         // query: arena position of each query (NIL if invalid)
+    uint32_t *dead;         // vertex delete: bitmap of deleted ids
+    unsigned long long max_items;
+    unsigned long long arena_cap;
+};
+
+enum Mode : int { MODE_INSERT = 0, MODE_DELETE = 1, MODE_QUERY = 2, MODE_VDEL = 3 };
+
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    // "lowbias32" integer hash (C. Wellons, 2018).
+    x ^= x >> 16;
+    x *= 0x7feb352dU;
+    x ^= x >> 15;
+    x *= 0x846ca68bU;
+    x ^= x >> 16;
+    return x;
+}
+
+__device__ __forceinline__ void latch_status(Dev *dev, unsigned int code) {
+    atomicCAS(&dev->status, 0u, code);
+}
+
+// Block id at heap index k (k >= 1) of the CBT rooted at `root`: follow the
+// bits of k below its leading 1, most significant first, 0 = left, 1 = right
+// (the bit-string rule of "Dynamic edge inserts").  Every id on the path is
+// checked against the pool size; an id outside the pool (a corrupted tree)
+// yields NIL, which callers treat as an error instead of dereferencing it.
+__device__ __forceinline__ uint32_t cbt_walk(const uint32_t *__restrict__ links,
+                                             unsigned long long P, uint32_t root, uint32_t k) {
+    uint32_t b = root;
+    if (b >= P) return NIL;
+    int top = 31 - __clz(k);
+    for (int i = top - 1; i >= 0; --i) {
+        b = links[2ull * b + ((k >> i) & 1u)];
+        if (b >= P) return NIL;
+    }
+    return b;
+}
+
+// x mod P for a pool of P blocks (0 for an empty pool).
+__device__ __forceinline__ unsigned long long qmod(unsigned long long x, unsigned long long P) {
+    return P ? x % P : 0ull;
+}
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+// Full-warp exclusive scan of a uint32 (all 32 lanes must call).
+__device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, uint32_t *total) {
+    uint32_t lane = lane_id();
+    uint32_t incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t y = __shfl_up_sync(FULL, incl, d);
+        if (lane >= (uint32_t)d) incl += y;
+    }
+    *total = __shfl_sync(FULL, incl, 31);
+    return incl - v;
+}
+
+__device__ __forceinline__ uint32_t warp_sum(uint32_t v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(FULL, v, d);
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(FULL, v, d);
+    return v;
+}
+
+// Warp-aggregated atomicAdd (all 32 lanes must call): every lane with `want`
+// adds `v`; each gets the counter value before its own share.
+template <typename T>
+__device__ __forceinline__ T warp_atomic_add(T *ctr, uint32_t v, bool want) {
+    uint32_t val = want ? v : 0u;
+    uint32_t total;
+    uint32_t excl = warp_excl_scan(val, &total);
+    T base = 0;
+    if (lane_id() == 0 && total) base = atomicAdd(ctr, (T)total);
+    base = __shfl_sync(FULL, base, 0);
+    return base + (T)excl;
+}
+
+// Block-wide exclusive scan (blockDim.x a multiple of 32, <= 1024; all
+// threads must call).  Returns the exclusive prefix and the block total.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *total) {
+    __shared__ uint32_t s_w[33];
+    uint32_t wt;
+    uint32_t ex = warp_excl_scan(v, &wt);
+    uint32_t w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane_id() == 0) s_w[w] = wt;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t x = lane_id() < nw ? s_w[lane_id()] : 0u;
+        uint32_t t2;
+        uint32_t e2 = warp_excl_scan(x, &t2);
+        if (lane_id() < nw) s_w[lane_id()] = e2;
+        if (lane_id() == 0) s_w[32] = t2;
+    }
+    __syncthreads();
+    uint32_t r = ex + s_w[w];
+    *total = s_w[32];
+    __syncthreads();
+    return r;
+}
+
+// Block-wide sum of a 64-bit value (all threads must call).
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v) {
+    __shared__ unsigned long long s_p[32];
+    v = warp_sum_u64(v);
+    uint32_t w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane_id() == 0) s_p[w] = v;
+    __syncthreads();
+    unsigned long long r = 0;
+    if (threadIdx.x == 0)
+        for (uint32_t i = 0; i < nw; ++i) r += s_p[i];
+    __syncthreads();
+    return r;  // valid in thread 0
+}
+
+// Bitonic sort of 32 (key, payload) pairs held one per lane, ascending keys.
+__device__ __forceinline__ void warp_sort_pairs(uint32_t &key, uint32_t &pay) {
+    uint32_t lane = lane_id();
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            uint32_t ok = __shfl_xor_sync(FULL, key, j);
+            uint32_t op = __shfl_xor_sync(FULL, pay, j);
+            bool up = (lane & k) == 0;
+            bool lower = (lane & j) == 0;
+            bool take = lower ? (up ? ok < key : ok > key) : (up ? ok > key : ok < key);
+            if (take) {
+                key = ok;
+                pay = op;
+            }
+        }
+    }
+}
+
+// Branchless lower bound among 32 ascending keys held one per lane: the
+// returned position p satisfies key[p-1] < e <= key[p] whenever e <= key[31];
+// the caller tests key[p] == e for membership.  All lanes must call.
+__device__ __forceinline__ uint32_t warp_lower_bound(uint32_t skey, uint32_t e) {
+    uint32_t pos = 0;
+#pragma unroll
+    for (uint32_t step = 16; step >= 1; step >>= 1) {
+        uint32_t probe = __shfl_sync(FULL, skey, pos + step - 1);
+        if (probe < e) pos += step;
+    }
+    return pos;
+}
+
+// Open-addressing hash set in a global arena region of `hsize` (power of two)
+// words: insert, returning the slot of `v`.
+__device__ __forceinline__ uint32_t hash_insert(uint32_t *tab, uint32_t hsize, uint32_t v) {
+    uint32_t h = mix32(v) & (hsize - 1);
+    for (uint32_t probe = 0; probe < hsize; ++probe) {
+        uint32_t cur = tab[h];
+        if (cur == v) return h;
+        if (cur == EMPTY_KEY) {
+            uint32_t old = atomicCAS(&tab[h], EMPTY_KEY, v);
+            if (old == EMPTY_KEY || old == v) return h;
+        }
+        h = (h + 1) & (hsize - 1);
+    }
+    return NIL;  // unreachable: tables are sized at twice the entries
+}
+
+__device__ __forceinline__ uint32_t hash_find(const uint32_t *tab, uint32_t hsize, uint32_t v) {
+    uint32_t h = mix32(v) & (hsize - 1);
+    for (uint32_t probe = 0; probe < hsize; ++probe) {
+        uint32_t cur = tab[h];
+        if (cur == v) return h;
+        if (cur == EMPTY_KEY) return NIL;
+        h = (h + 1) & (hsize - 1);
+    }
+    return NIL;
+}
+
+// Last-CTA detection for a finalize kernel: returns true in exactly one CTA,
+// after every CTA has passed this point.  Uses dev->done_ctas, which the last
+// CTA resets.
+__device__ __forceinline__ bool last_cta(Dev *dev) {
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int t = atomicAdd(&dev->done_ctas, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last;
+}
+
+}  // namespace gv

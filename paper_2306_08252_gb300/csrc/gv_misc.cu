@@ -1,0 +1,361 @@
+// gv_misc.cu -- initialisation, dictionary growth, neighbour lists, degrees
+// and the structural self-check of the GraphVine library.
+#include "gv_launch.h"
+
+namespace gv {
+
+// Sentinel attach ("Dynamic vertex updates": one thread per vertex attaches
+// an empty edge sentinel).
+__global__ void __launch_bounds__(256) k_init_vertices(GraphView g, uint32_t from, uint32_t to) {
+    for (uint32_t u = from + blockIdx.x * blockDim.x + threadIdx.x; u < to; u += gridDim.x * blockDim.x) {
+        g.sent[u] = make_uint4(0, 0, NIL, NIL);
+        g.alive[u] = 1;
+    }
+}
+
+// Dictionary doubling: one kernel copies the old dictionary into the new one.
+__global__ void __launch_bounds__(256) k_copy_dictionary(uint4 *dst_sent, uint8_t *dst_alive,
+                                                         const uint4 *src_sent, const uint8_t *src_alive,
+                                                         uint32_t n) {
+    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        dst_sent[u] = src_sent[u];
+        dst_alive[u] = src_alive[u];
+    }
+}
+
+// Edge queue: every pool block id, in order ("Edge Queue").
+__global__ void __launch_bounds__(256) k_init_queue(uint32_t *queue, unsigned long long P) {
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < P;
+         i += (unsigned long long)gridDim.x * blockDim.x)
+        queue[i] = (uint32_t)i;
+}
+
+__global__ void __launch_bounds__(256) k_iota(uint32_t *out, uint32_t first, uint32_t k) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x)
+        out[i] = first + i;
+}
+
+__global__ void __launch_bounds__(256) k_degrees(GraphView g, uint32_t *deg, uint8_t *alive) {
+    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < g.nv; u += gridDim.x * blockDim.x) {
+        deg[u] = g.sent[u].x;
+        if (alive) alive[u] = g.alive[u];
+    }
+}
+
+// ------------------------------------------------------------- neighbours
+
+constexpr int SCAN_T = 256;
+constexpr int SCAN_PER = 4;
+constexpr int SCAN_CHUNK = SCAN_T * SCAN_PER;
+
+__device__ __forceinline__ uint32_t vid_degree(const GraphView &g, uint32_t u) {
+    return (u < g.nv && g.alive[u]) ? g.sent[u].x : 0u;
+}
+
+// Per-chunk sums of the requested vertices' degrees.
+__global__ void __launch_bounds__(SCAN_T) k_nbr_partials(GraphView g, const uint32_t *__restrict__ vids,
+                                                         uint32_t n, unsigned long long *partials) {
+    const uint32_t chunk = blockIdx.x;
+    unsigned long long s = 0;
+    for (int j = 0; j < SCAN_PER; ++j) {
+        const uint32_t i = chunk * SCAN_CHUNK + j * SCAN_T + threadIdx.x;
+        if (i < n) s += vid_degree(g, vids[i]);
+    }
+    s = block_sum_u64(s);
+    if (threadIdx.x == 0) partials[chunk] = s;
+}
+
+// Exclusive scan of the chunk sums by one CTA.
+__global__ void __launch_bounds__(1024) k_nbr_scan_partials(unsigned long long *partials, uint32_t nchunks) {
+    __shared__ unsigned long long s_carry;
+    __shared__ unsigned long long s_w[32];
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (uint32_t base = 0; base < nchunks; base += blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        const unsigned long long v = i < nchunks ? partials[i] : 0ull;
+        // inclusive warp scan
+        unsigned long long incl = v;
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long y = __shfl_up_sync(FULL, incl, d);
+            if (lane_id() >= (uint32_t)d) incl += y;
+        }
+        if (lane_id() == 31) s_w[threadIdx.x >> 5] = incl;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            unsigned long long x = threadIdx.x < (blockDim.x >> 5) ? s_w[threadIdx.x] : 0ull;
+            unsigned long long xi = x;
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned long long y = __shfl_up_sync(FULL, xi, d);
+                if (lane_id() >= (uint32_t)d) xi += y;
+            }
+            s_w[threadIdx.x] = xi - x;
+        }
+        __syncthreads();
+        const unsigned long long ex = s_carry + s_w[threadIdx.x >> 5] + incl - v;
+        if (i < nchunks) partials[i] = ex;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) s_carry = ex + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[nchunks] = s_carry;
+}
+
+// offsets[i] = chunk prefix + exclusive scan inside the chunk; offsets[n] = total.
+__global__ void __launch_bounds__(SCAN_T) k_nbr_apply(GraphView g, const uint32_t *__restrict__ vids,
+                                                      uint32_t n, const unsigned long long *partials,
+                                                      uint32_t nchunks, unsigned long long *offsets) {
+    const uint32_t chunk = blockIdx.x;
+    // thread-local run over SCAN_PER consecutive elements
+    unsigned long long v[SCAN_PER];
+    unsigned long long s = 0;
+    for (int j = 0; j < SCAN_PER; ++j) {
+        const uint32_t i = chunk * SCAN_CHUNK + threadIdx.x * SCAN_PER + j;
+        v[j] = i < n ? vid_degree(g, vids[i]) : 0ull;
+        s += v[j];
+    }
+    __shared__ unsigned long long s_w[SCAN_T / 32];
+    unsigned long long incl = s;
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long y = __shfl_up_sync(FULL, incl, d);
+        if (lane_id() >= (uint32_t)d) incl += y;
+    }
+    if (lane_id() == 31) s_w[threadIdx.x >> 5] = incl;
+    __syncthreads();
+    unsigned long long wpre = 0;
+    for (uint32_t w = 0; w < (threadIdx.x >> 5); ++w) wpre += s_w[w];
+    unsigned long long run = partials[chunk] + wpre + incl - s;
+    for (int j = 0; j < SCAN_PER; ++j) {
+        const uint32_t i = chunk * SCAN_CHUNK + threadIdx.x * SCAN_PER + j;
+        if (i < n) offsets[i] = run;
+        run += v[j];
+    }
+    if (chunk == nchunks - 1 && threadIdx.x == 0) offsets[n] = partials[nchunks];
+}
+
+// Items over the requested vertices' blocks (touched index = request index).
+__global__ void __launch_bounds__(256) k_nbr_plan(GraphView g, const uint32_t *__restrict__ vids, uint32_t n) {
+    const uint32_t IB = g.IB;
+    __shared__ uint32_t s_ai;
+    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        uint32_t ni = 0;
+        uint4 s = make_uint4(0, 0, NIL, NIL);
+        if (i < n) {
+            const uint32_t u = vids[i];
+            if (u < g.nv && g.alive[u]) {
+                s = g.sent[u];
+                ni = (s.y + IB - 1) / IB;
+            }
+        }
+        uint32_t itot;
+        const uint32_t iex = block_excl_scan(ni, &itot);
+        if (threadIdx.x == 0) s_ai = itot ? atomicAdd(&g.dev->n_items, itot) : 0u;
+        __syncthreads();
+        if (i < n) {
+            const uint32_t item0 = s_ai + iex;
+            g.t_b[i] = make_uint4(s.x, s.y, s.z, ni);
+            for (uint32_t c = 0; c < ni; ++c) g.items[item0 + c] = make_uint2(i, c);
+        }
+        __syncthreads();
+    }
+}
+
+// One warp per item: copy the item's slots in heap (storage) order.
+__global__ void __launch_bounds__(256) k_nbr_copy(GraphView g, const unsigned long long *__restrict__ offsets,
+                                                  uint32_t *__restrict__ nbrs) {
+    const uint32_t nitems = g.dev->n_items;
+    const uint32_t lane = lane_id();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t C = g.C, IB = g.IB;
+    for (uint32_t it = warp; it < nitems; it += nwarps) {
+        const uint2 itm = g.items[it];
+        const uint4 b = g.t_b[itm.x];
+        const uint32_t kb = itm.y * IB;
+        const uint32_t nblk = min(IB, b.y - kb);
+        uint32_t bid = NIL;
+        if (lane < nblk) bid = cbt_walk(g.links, g.P, b.z, kb + 1 + lane);
+        if (__any_sync(FULL, lane < nblk && bid == NIL)) {
+            if (lane == 0) latch_status(g.dev, 5u /* GV_ERR_STATE */);
+            continue;
+        }
+        const uint32_t sbase = kb * C;
+        const uint32_t nslots = min(nblk * C, b.x - sbase);
+        const uint32_t nquads = (nslots + 3) >> 2;
+        uint32_t *out = nbrs + offsets[itm.x] + sbase;
+        for (uint32_t q0 = 0; q0 < nquads; q0 += 32) {
+            const uint32_t q = q0 + lane;
+            const uint32_t x = q << 2;
+            const uint32_t lb = x / C;
+            const uint32_t myb = __shfl_sync(FULL, bid, lb & 31u);
+            if (q < nquads) {
+                const uint4 e4 = *reinterpret_cast<const uint4 *>(g.data + (size_t)myb * C + (x - lb * C));
+                const uint32_t e[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (x + j < nslots) out[x + j] = e[j];
+            }
+        }
+    }
+}
+
+__global__ void k_clear_items(GraphView g) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) g.dev->n_items = 0;
+}
+
+// ---------------------------------------------------------- self-check
+
+// res[0] violations, res[1] sum of degrees, res[2] owned blocks, res[3] queued blocks
+__device__ __forceinline__ uint32_t cbt_walk_checked(const uint32_t *links, unsigned long long P,
+                                                     uint32_t root, uint32_t k, bool &bad) {
+    uint32_t b = root;
+    if (b >= P) {
+        bad = true;
+        return NIL;
+    }
+    int top = 31 - __clz(k);
+    for (int i = top - 1; i >= 0; --i) {
+        b = links[2ull * b + ((k >> i) & 1u)];
+        if (b >= P) {
+            bad = true;
+            return NIL;
+        }
+    }
+    return b;
+}
+
+__global__ void __launch_bounds__(256) k_validate_vertices(GraphView g, uint32_t *owner,
+                                                           unsigned long long *res) {
+    const uint32_t lane = lane_id();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t C = g.C;
+    unsigned long long viol = 0, sdeg = 0, snb = 0;
+    for (uint32_t u = warp; u < g.nv; u += nwarps) {
+        const uint4 s = g.sent[u];
+        const uint32_t deg = s.x, nb = s.y;
+        if (lane == 0) {
+            sdeg += deg;
+            snb += nb;
+            if (C == 0 ? (deg != 0 || nb != 0) : (nb != (deg + C - 1) / C)) ++viol;
+            if (!g.alive[u] && (deg != 0 || nb != 0)) ++viol;
+            if (nb == 0 && (s.z != NIL || s.w != NIL)) ++viol;
+        }
+        for (uint32_t k = 1 + lane; k <= nb; k += 32) {
+            bool bad = false;
+            const uint32_t b = cbt_walk_checked(g.links, g.P, s.z, k, bad);
+            if (bad) {
+                ++viol;
+                continue;
+            }
+            const uint32_t bit = 1u << (b & 31u);
+            if (atomicOr(&owner[b >> 5], bit) & bit) ++viol;
+            if (k == nb && b != s.w) ++viol;
+            if (2ull * k > nb && g.links[2ull * b] != NIL) ++viol;
+            if (2ull * k + 1 > nb && g.links[2ull * b + 1] != NIL) ++viol;
+        }
+    }
+    viol = warp_sum_u64(viol);
+    sdeg = warp_sum_u64(sdeg);
+    snb = warp_sum_u64(snb);
+    if (lane == 0) {
+        if (viol) atomicAdd(&res[0], viol);
+        if (sdeg) atomicAdd(&res[1], sdeg);
+        if (snb) atomicAdd(&res[2], snb);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_validate_queue(GraphView g, uint32_t *owner,
+                                                        unsigned long long *res) {
+    const unsigned long long qf = g.dev->q_front, qb = g.dev->q_back, P = g.P;
+    if (P == 0) return;
+    unsigned long long viol = 0, cnt = 0;
+    for (unsigned long long p = qf + blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; p < qb;
+         p += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t b = g.queue[p % P];
+        ++cnt;
+        if (b >= P) {
+            ++viol;
+            continue;
+        }
+        const uint32_t bit = 1u << (b & 31u);
+        if (atomicOr(&owner[b >> 5], bit) & bit) ++viol;
+    }
+    viol = warp_sum_u64(viol);
+    cnt = warp_sum_u64(cnt);
+    if (lane_id() == 0) {
+        if (viol) atomicAdd(&res[0], viol);
+        if (cnt) atomicAdd(&res[3], cnt);
+    }
+}
+
+// ------------------------------------------------------------------ launch
+
+namespace {
+inline int grid_for(unsigned long long work, int per_block, int cap) {
+    unsigned long long g = (work + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > (unsigned long long)cap) g = cap;
+    return (int)g;
+}
+}  // namespace
+
+cudaError_t launch_init_vertices(const GraphView &g, uint32_t from, uint32_t to, const LaunchCfg &lc) {
+    if (to > from) k_init_vertices<<<grid_for(to - from, 256, lc.num_sms * 16), 256, 0, lc.stream>>>(g, from, to);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_dictionary(uint4 *dst_sent, uint8_t *dst_alive, const uint4 *src_sent,
+                                   const uint8_t *src_alive, uint32_t n, const LaunchCfg &lc) {
+    if (n) k_copy_dictionary<<<grid_for(n, 256, lc.num_sms * 16), 256, 0, lc.stream>>>(dst_sent, dst_alive, src_sent, src_alive, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_queue(uint32_t *queue, unsigned long long P, const LaunchCfg &lc) {
+    k_init_queue<<<grid_for(P, 256, lc.num_sms * 16), 256, 0, lc.stream>>>(queue, P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_iota(uint32_t *out, uint32_t first, uint32_t k, const LaunchCfg &lc) {
+    if (k) k_iota<<<grid_for(k, 256, lc.num_sms * 16), 256, 0, lc.stream>>>(out, first, k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_degrees(const GraphView &g, uint32_t *deg, uint8_t *alive, const LaunchCfg &lc) {
+    if (g.nv) k_degrees<<<grid_for(g.nv, 256, lc.num_sms * 16), 256, 0, lc.stream>>>(g, deg, alive);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_neighbor_offsets(const GraphView &g, const uint32_t *vids, uint32_t n,
+                                    unsigned long long *offsets, unsigned long long *partials,
+                                    const LaunchCfg &lc) {
+    const uint32_t nchunks = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    if (nchunks == 0) {
+        cudaMemsetAsync(offsets, 0, sizeof(unsigned long long), lc.stream);
+        cudaMemsetAsync(partials, 0, sizeof(unsigned long long), lc.stream);
+        return cudaGetLastError();
+    }
+    k_nbr_partials<<<nchunks, SCAN_T, 0, lc.stream>>>(g, vids, n, partials);
+    k_nbr_scan_partials<<<1, 1024, 0, lc.stream>>>(partials, nchunks);
+    k_nbr_apply<<<nchunks, SCAN_T, 0, lc.stream>>>(g, vids, n, partials, nchunks, offsets);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_neighbor_copy(const GraphView &g, const uint32_t *vids, uint32_t n,
+                                 const unsigned long long *offsets, uint32_t *nbrs, const LaunchCfg &lc) {
+    if (n == 0) return cudaSuccess;
+    k_nbr_plan<<<grid_for(n, 256, lc.num_sms * 8), 256, 0, lc.stream>>>(g, vids, n);
+    k_nbr_copy<<<lc.num_sms * 8, 256, 0, lc.stream>>>(g, offsets, nbrs);
+    k_clear_items<<<1, 32, 0, lc.stream>>>(g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate(const GraphView &g, uint32_t *owner_bits, unsigned long long *res,
+                            const LaunchCfg &lc) {
+    k_validate_vertices<<<lc.num_sms * 8, 256, 0, lc.stream>>>(g, owner_bits, res);
+    k_validate_queue<<<lc.num_sms * 8, 256, 0, lc.stream>>>(g, owner_bits, res);
+    return cudaGetLastError();
+}
+
+}  // namespace gv

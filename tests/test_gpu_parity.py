@@ -1,0 +1,289 @@
+"""GPU path vs the CPU oracle, bit-exact, after every call (integer results).
+
+Inputs come from the seeded generators in `workloads`; the oracle and the
+GPU library see the same arrays.  Sizes span many work items, multi-item
+hub adjacencies and ragged tails; the full-size RMAT workload is checked on
+every degree, every query bit and sampled neighbour lists.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_util import Pair, canon, dev_u32
+
+pytestmark = pytest.mark.gpu
+
+
+def test_tiny_uniform_config_every_batch():
+    cfg = W.tiny_uniform()
+    p = Pair(cfg["nv"], C=cfg["block_capacity"], pool_bytes=32 << 20)
+    try:
+        p.bulk(*cfg["bulk"])
+        p.check()
+        for op in cfg["ops"]:
+            if op.kind == "insert":
+                p.insert(op.src, op.dst)
+            else:
+                p.delete(op.src, op.dst)
+            p.check()
+    finally:
+        p.close()
+
+
+@pytest.mark.parametrize("C", [4, 8, 16, 20, 64, 0])
+def test_rmat_skewed_batches(C):
+    scale, nv = 12, 1 << 12
+    bs, bd = W.rmat_pairs(21, 0, 65536, scale)
+    p = Pair(nv, C=C, pool_bytes=64 << 20)
+    try:
+        p.bulk(bs, bd)
+        st = p.check()
+        if C == 0:
+            import oracle
+            assert st["block_capacity"] == oracle.block_capacity_rule(np.bincount(bs, minlength=nv))
+        for r, b in enumerate([1, 37, 5000, 20000]):
+            s, d = W.rmat_pairs(21, 100 + r, b, scale)
+            p.insert(s, d)
+            p.check()
+            qs, qd = W.rmat_queries(21, scale, 4000, s, d, r)
+            p.query(qs, qd)
+            # delete the batch, some base edges and some absent pairs
+            es = bs[r * 1000:(r + 1) * 1000]
+            ed = bd[r * 1000:(r + 1) * 1000]
+            as_, ad = W.absent_pairs(21, 300 + r, 500, nv, W.keys(np.concatenate([bs, s]), np.concatenate([bd, d])))
+            p.delete(np.concatenate([s, es, as_]), np.concatenate([d, ed, ad]))
+            p.check()
+            p.query(qs, qd)
+    finally:
+        p.close()
+
+
+def test_hub_deletes_across_many_items():
+    # one vertex with a long adjacency (hundreds of work items), deleted in
+    # scattered pieces, including every copy of duplicated pairs
+    nv = 3000
+    rng = np.random.default_rng(5)
+    hub_d = rng.integers(0, nv, 200_000).astype(np.uint32)
+    hub_s = np.zeros_like(hub_d)
+    other_s = rng.integers(1, nv, 50_000).astype(np.uint32)
+    other_d = rng.integers(0, nv, 50_000).astype(np.uint32)
+    p = Pair(nv, C=16, pool_bytes=64 << 20)
+    try:
+        p.bulk(np.concatenate([hub_s, other_s]), np.concatenate([hub_d, other_d]))
+        p.check()
+        for frac in (0.01, 0.3, 0.9):
+            k = int(nv * frac)
+            dd = rng.choice(nv, size=k, replace=False).astype(np.uint32)
+            p.delete(np.zeros(k, dtype=np.uint32), dd)
+            p.check()
+            p.insert(np.zeros(777, dtype=np.uint32), rng.integers(0, nv, 777).astype(np.uint32))
+            p.check()
+        # delete everything of the hub
+        p.delete(np.zeros(nv, dtype=np.uint32), np.arange(nv, dtype=np.uint32))
+        p.check()
+    finally:
+        p.close()
+
+
+def test_queries_with_invalid_and_dead_ids():
+    nv = 2000
+    bs, bd = W.uniform_pairs(9, 0, 30000, nv)
+    p = Pair(nv, C=8)
+    try:
+        p.bulk(bs, bd)
+        p.vdel(np.array([5, 6, 7], dtype=np.uint32))
+        qs = np.concatenate([bs[:3000], np.array([5, 1, nv, nv + 7, 0xFFFFFFFE], dtype=np.uint32)])
+        qd = np.concatenate([bd[:3000], np.array([1, 6, 1, 0, 3], dtype=np.uint32)])
+        p.query(qs, qd)
+        p.check()
+    finally:
+        p.close()
+
+
+def test_vertex_insert_and_delete():
+    nv = 5000
+    bs, bd = W.uniform_pairs(11, 0, 40000, nv)
+    # a few heavy vertices so that incoming-edge removal spans multi-item adjacencies
+    hs = np.repeat(np.arange(4, dtype=np.uint32), 3000)
+    hd = W.uniform_u32(11, 1, hs.size, 0, nv)
+    p = Pair(nv, C=16)
+    try:
+        p.bulk(np.concatenate([bs, hs]), np.concatenate([bd, hd]))
+        p.check()
+        ids = W.shuffled(11, 2, np.arange(nv, dtype=np.uint32))[:300]
+        ids = np.concatenate([ids, ids[:10], np.array([nv + 3, 0xFFFFFFFF], dtype=np.uint32)])
+        p.vdel(ids)
+        p.check()
+        p.vdel(ids[:50])  # already dead: no-op
+        p.check()
+        p.vins(4000)  # crosses the dictionary capacity (8192 -> 16384)
+        p.check()
+        new = np.arange(nv, nv + 4000, dtype=np.uint32)
+        s = np.repeat(new, 8)
+        d = W.uniform_u32(11, 3, s.size, 0, nv + 4000)
+        p.insert(s, d)  # some endpoints are dead: rejected
+        p.check()
+        p.vdel(np.concatenate([new[:100], np.arange(4, dtype=np.uint32)]))
+        p.check()
+        p.insert(bs[:5000], bd[:5000])
+        p.check()
+    finally:
+        p.close()
+
+
+def test_empty_degenerate_and_duplicates():
+    nv = 64
+    p = Pair(nv, C=4, pool_bytes=1 << 20)
+    e = np.zeros(0, dtype=np.uint32)
+    try:
+        p.insert(e, e)
+        p.delete(e, e)
+        p.query(e, e)
+        p.check()
+        # all-invalid batches
+        bad = np.array([64, 65, 1000], dtype=np.uint32)
+        p.insert(bad, np.array([0, 1, 2], dtype=np.uint32))
+        p.delete(bad, np.array([0, 1, 2], dtype=np.uint32))
+        p.check()
+        # self loops and duplicates (multiset)
+        s = np.array([1, 1, 1, 2, 2, 3] * 5, dtype=np.uint32)
+        d = np.array([1, 1, 2, 2, 3, 3] * 5, dtype=np.uint32)
+        p.insert(s, d)
+        p.check()
+        p.delete(np.array([1, 1], dtype=np.uint32), np.array([1, 1], dtype=np.uint32))
+        p.check()
+        # delete absent pairs: no-op
+        p.delete(np.array([5, 6], dtype=np.uint32), np.array([7, 8], dtype=np.uint32))
+        p.check()
+        # delete every edge, then rebuild: pool accounting returns to zero
+        s2, d2 = W.uniform_pairs(3, 0, 3000, nv)
+        p.insert(s2, d2)
+        p.check()
+        p.delete(np.repeat(np.arange(nv, dtype=np.uint32), nv), np.tile(np.arange(nv, dtype=np.uint32), nv))
+        st = p.check()
+        assert st["num_edges"] == 0 and st["pool_blocks_used"] == 0
+        p.insert(s2, d2)
+        p.check()
+    finally:
+        p.close()
+
+
+def test_pool_exhaustion_is_a_noop():
+    import paper_2306_08252_gb300 as gv
+    nv = 256
+    # pool of ~200 blocks of C=4
+    p = Pair(nv, C=4, pool_bytes=200 * (16 + 12) + 1024)
+    try:
+        s, d = W.uniform_pairs(4, 0, 300, nv)
+        p.insert(s, d)
+        p.check()
+        before = p.g.export_csr()
+        s2, d2 = W.uniform_pairs(4, 1, 5000, nv)
+        p.g.insert_edges(dev_u32(s2), dev_u32(d2), p.counts)
+        assert p.g.__class__  # call returns; error is latched on the device
+        code = gv.gv_sync(p.g.handle)
+        assert code == gv.GV_ERR_OUT_OF_MEMORY
+        assert tuple(p.counts.cpu().tolist()) == (0, 0)
+        after = p.g.export_csr()
+        np.testing.assert_array_equal(before[0], after[0])
+        np.testing.assert_array_equal(canon(*before), canon(*after))
+        p.check()  # status cleared; still equal to the oracle (which skipped the batch)
+        p.insert(s[:50], d[:50])
+        p.check()
+    finally:
+        p.close()
+
+
+def test_host_pointer_inputs_match_device_inputs():
+    import torch
+    import paper_2306_08252_gb300 as gv
+    nv = 4096
+    bs, bd = W.rmat_pairs(12, 0, 50000, 12)
+    a = gv.Graph(nv, block_capacity=16, pool_bytes=32 << 20)
+    b = gv.Graph(nv, block_capacity=16, pool_bytes=32 << 20)
+    try:
+        ca = np.zeros(2, dtype=np.uint64)
+        a.bulk_build(bs, bd, ca)              # numpy (pageable host) arrays
+        b.bulk_build(dev_u32(bs), dev_u32(bd))
+        assert tuple(ca) == (50000, 0)
+        pin_s = torch.from_numpy(bs[:9000].view(np.int32)).pin_memory()
+        pin_d = torch.from_numpy(bd[:9000].view(np.int32)).pin_memory()
+        a.delete_edges(pin_s, pin_d, ca)      # pinned host arrays
+        b.delete_edges(dev_u32(bs[:9000]), dev_u32(bd[:9000]))
+        out_h = np.zeros(20000, dtype=np.uint8)
+        a.query_edges(bs[:20000], bd[:20000], out_h)
+        out_d = torch.zeros(20000, dtype=torch.uint8, device="cuda")
+        b.query_edges(dev_u32(bs[:20000]), dev_u32(bd[:20000]), out_d)
+        np.testing.assert_array_equal(out_h, out_d.cpu().numpy())
+        np.testing.assert_array_equal(canon(*a.export_csr()), canon(*b.export_csr()))
+    finally:
+        a.close()
+        b.close()
+
+
+def test_neighbors_subset_and_capacity_error():
+    import paper_2306_08252_gb300 as gv
+    nv = 3000
+    bs, bd = W.rmat_pairs(13, 0, 40000, 12, limit=nv)
+    p = Pair(nv, C=12)
+    try:
+        p.bulk(bs, bd)
+        vids = np.array([0, 1, 2, 2999, 3000, 0xFFFFFFF0, 17, 0], dtype=np.uint32)
+        p.check_sampled(vids)
+        off = np.zeros(vids.size + 1, dtype=np.uint64)
+        small = np.zeros(3, dtype=np.uint32)
+        code, total = gv.gv_neighbors(p.g.handle, vids, off, small, small.size)
+        assert code == gv.GV_ERR_INVALID_ARG and total == int(p.o.neighbors(vids)[0][-1])
+    finally:
+        p.close()
+
+
+def test_er_mixed_scaled():
+    cfg = W.er_mixed(seed=3, nv=1 << 16, base_edges=1 << 18, rounds=2, batch=20000, vdel=2048,
+                     vins=2048, vins_edges=8)
+    p = Pair(cfg["nv"], C=4, pool_bytes=64 << 20)
+    try:
+        p.bulk(*cfg["bulk"])
+        p.check()
+        for op in cfg["ops"]:
+            if op.kind == "insert":
+                p.insert(op.src, op.dst)
+            elif op.kind == "delete":
+                p.delete(op.src, op.dst)
+            elif op.kind == "vdel":
+                p.vdel(op.ids)
+            else:
+                p.vins(op.k)
+            p.check()
+    finally:
+        p.close()
+
+
+def test_rmat_full_size_sampled():
+    """RMAT 2^20 vertices, 16M edges, the 10M insert / 1M query / 10M delete
+    step in the benchmark's launch configuration; every degree and query bit,
+    sampled neighbour lists (top hubs and random vertices)."""
+    scale = 20
+    bs, bd = W.rmat_graph(2, scale, 1 << 24)
+    p = Pair(1 << scale, C=16, pool_bytes=1 << 30)
+    try:
+        p.bulk(bs, bd)
+        p.check(full=False)
+        s, d = W.rmat_update(2, scale, 10_000_000, 0)
+        p.insert(s, d)
+        p.check(full=False)
+        qs, qd = W.rmat_queries(2, scale, 1_000_000, s, d, 0)
+        p.query(qs, qd)
+        p.delete(s, d)
+        p.check(full=False)
+        deg = p.o.degrees()
+        hubs = np.argsort(deg)[-64:].astype(np.uint32)
+        rnd = W.uniform_u32(2, 77, 4000, 0, 1 << scale)
+        p.check_sampled(np.concatenate([hubs, rnd]))
+        # a second step from the steady state
+        p.insert(s, d)
+        p.delete(s, d)
+        p.check(full=False)
+        p.check_sampled(np.concatenate([hubs, rnd]))
+    finally:
+        p.close()
