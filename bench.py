@@ -1,0 +1,431 @@
+"""Benchmark: batched edge updates on a power-law graph, one JSON line.
+
+Workload (the paper's batched-update experiment, Tables 3 and 4, on a
+synthetic stand-in for its co-paper graphs): RMAT graph with 2^20 vertices
+and 16,777,216 edges (a, b, c, d = .57, .19, .19, .05), edge-block capacity
+C = 16, bulk built once; one step = insert a 10,000,000-edge RMAT batch,
+answer 1,000,000 edge-existence queries (half present), delete the same
+10,000,000 edges.  metric = edge updates (inserted + deleted entries) per
+second.  Inputs live in HBM before the timed region; L2 is flushed before
+every timed step.
+
+`--impl reference` times the CPU oracle (the plain definition the GPU
+results are checked against) on a bounded sample of the same step.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "edge updates/s (batch insert+delete)"
+UNIT = "edges/s"
+SCALE = 20
+BASE_EDGES = 1 << 24
+BATCH = 10_000_000
+QUERIES = 1_000_000
+C = 16
+POOL_BYTES = 2 << 30
+SEED = 2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=BATCH)
+    ap.add_argument("--queries", type=int, default=QUERIES)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(batch, queries):
+    import workloads as W
+    bs, bd = W.rmat_graph(SEED, SCALE, BASE_EDGES)
+    s, d = W.rmat_update(SEED, SCALE, batch, 0)
+    qs, qd = W.rmat_queries(SEED, SCALE, queries, s, d, 0)
+    return (bs, bd), (s, d), (qs, qd)
+
+
+def config_dict(args, n):
+    return {
+        "workload": f"RMAT scale {SCALE} ({1 << SCALE} vertices, {BASE_EDGES} edges, a,b,c,d=.57,.19,.19,.05), "
+                    f"C={C}; step = insert {args.batch} + query {args.queries} + delete the {args.batch}",
+        "vertices": 1 << SCALE,
+        "base_edges": BASE_EDGES,
+        "batch": args.batch,
+        "queries": args.queries,
+        "block_capacity": C,
+        "l2": "flushed before every timed step (256 MiB write)",
+        "parallelism": f"replicas{n}" if n > 1 else "single",
+    }
+
+
+# ------------------------------------------------------------ CPU baseline
+
+def oracle_sample_rate(base, upd, qry, budget_s=12.0, sample=1_000_000, qsample=100_000, max_steps=None):
+    """The oracle (single thread, as it stands) on a bounded sample of the
+    step: insert `sample` edges of the batch, query `qsample`, delete them."""
+    import oracle
+    o = oracle.OracleGraph(1 << SCALE)
+    o.bulk_build(*base)
+    s, d = upd[0][:sample], upd[1][:sample]
+    qs, qd = qry[0][:qsample], qry[1][:qsample]
+    done = 0
+    t_total = 0.0
+    steps = 0
+    while (t_total < budget_s and (max_steps is None or steps < max_steps)) or steps == 0:
+        t0 = time.perf_counter()
+        ins, _ = o.insert_edges(s, d)
+        o.query_edges(qs, qd)
+        dele, _ = o.delete_edges(s, d)
+        t_total += time.perf_counter() - t0
+        done += ins + dele
+        steps += 1
+    o.close()
+    return done / t_total, steps, t_total
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for row in csv.reader(io.StringIO(out)):
+            if len(row) < 9:
+                continue
+            try:
+                sm.append(float(row[1]))
+                smax.append(float(row[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, row[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# -------------------------------------------------------------- byte model
+
+def byte_model(g, batch, qry, inserted, deleted, newblocks):
+    """Algorithmic bytes of one step (the minimum the method must move):
+    insert 12 B/edge + 32 B/touched source + 12 B/new block; query
+    9 B/query + 4 B per stored entry of each distinct queried source;
+    delete 8 B/edge + 4 B per stored entry of each touched source + 32 B per
+    touched source + 4 B per freed block (entries moved by compaction are
+    not counted: a lower bound)."""
+    s, d = batch
+    deg, _ = g.degrees()  # state after the insert = state the query and delete see
+    nv = deg.size
+    ok = (s < nv) & (d < nv)
+    us = np.unique(s[ok])
+    qs = np.unique(qry[0][qry[0] < nv])
+    ins_b = 12 * inserted + 32 * us.size + 12 * newblocks
+    qry_b = 9 * qry[0].size + 4 * int(deg[qs].astype(np.int64).sum())
+    del_b = 8 * s.size + 4 * int(deg[us].astype(np.int64).sum()) + 32 * us.size + 4 * newblocks
+    kernels = {
+        # per-launch algorithmic bytes of each timed phase
+        "insert.count": 8 * s.size,
+        "insert.scatter": 12 * inserted,
+        "delete.count": 8 * s.size,
+        "delete.scatter": 12 * s.size,
+        "delete.mark": 4 * int(deg[us].astype(np.int64).sum()) + 4 * s.size,
+        "query.count": 8 * qry[0].size,
+        "query.scatter": 12 * qry[0].size,
+        "query.mark": 4 * int(deg[qs].astype(np.int64).sum()) + 4 * qry[0].size,
+    }
+    return {"insert": ins_b, "query": qry_b, "delete": del_b, "step": ins_b + qry_b + del_b,
+            "touched_sources": int(us.size), "kernels": kernels}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2306_08252_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_phase):
+    """Per-launch DRAM bytes of the phase's kernel from the committed ncu
+    summary, or None if absent or taken on different kernel sources."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        data = json.load(open(p))
+    except Exception:
+        return None
+    ent = data.get(kernel_phase)
+    if not ent or ent.get("source_hash") != source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    import paper_2306_08252_gb300 as gv
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    gv.load()
+    base, upd, qry = workload(args.batch, args.queries)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(dev)
+    d_bs, d_bd = t(base[0]), t(base[1])
+    d_s, d_d = t(upd[0]), t(upd[1])
+    d_qs, d_qd = t(qry[0]), t(qry[1])
+    d_out = torch.zeros(args.queries, dtype=torch.uint8, device=dev)
+    counts = torch.zeros(4, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+    g = gv.Graph(1 << SCALE, block_capacity=C, pool_bytes=POOL_BYTES)
+    g.reserve(max(args.batch, BASE_EDGES))
+    g.bulk_build(d_bs, d_bs.new_empty(0) if False else d_bd, counts[:2])
+    g.sync()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        g.insert_edges(d_s, d_d, counts[:2])
+        g.query_edges(d_qs, d_qd, d_out)
+        g.delete_edges(d_s, d_d, counts[2:])
+
+    for _ in range(max(args.warmup, 3) if args.warmup >= 3 else args.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert g.sync() == 0
+
+    # byte model from the steady state (after an insert)
+    st0 = g.stats()
+    g.insert_edges(d_s, d_d, counts[:2])
+    torch.cuda.synchronize()
+    st1 = g.stats()
+    inserted = int(counts[0].item())
+    newblocks = st1["pool_blocks_used"] - st0["pool_blocks_used"]
+    g.delete_edges(d_s, d_d, counts[2:])
+    torch.cuda.synchronize()
+    deleted = int(counts[2].item())
+    # degrees as the query/delete of a step see them: re-insert, measure, delete
+    g.insert_edges(d_s, d_d, counts[:2])
+    model = byte_model(g, upd, qry, inserted, deleted, newblocks)
+    g.delete_edges(d_s, d_d, counts[2:])
+    torch.cuda.synchronize()
+
+    # ---------------- timed region (device time, CUDA events on the stream)
+    sampler = ClockSampler(local_rank)
+    g.profile_read()
+    g.profile(True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    upd_done = 0
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    g.profile(False)
+    phases = g.profile_read()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    upd_done = args.steps * (inserted + deleted)
+    if world > 1:
+        dist.barrier()
+    assert g.sync() == 0
+    gpu_launches = int(sum(c for _, c in phases.values()))
+
+    # ---------------- end to end: host (pinned) inputs and outputs, through the C ABI
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).pin_memory()
+        h_s, h_d, h_qs, h_qd = pin(upd[0]), pin(upd[1]), pin(qry[0]), pin(qry[1])
+        h_out = torch.zeros(args.queries, dtype=torch.uint8).pin_memory()
+        h_counts = torch.zeros(4, dtype=torch.int64).pin_memory()
+
+        def step_host():
+            g.insert_edges(h_s, h_d, h_counts[:2])
+            g.query_edges(h_qs, h_qd, h_out)
+            g.delete_edges(h_s, h_d, h_counts[2:])
+
+        step_host()
+        torch.cuda.synchronize()
+        e_ms = 0.0
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            step_host()
+            torch.cuda.synchronize()
+            e_ms += (time.perf_counter() - t0) * 1e3
+        assert g.sync() == 0
+        h2d = 2 * 4 * args.batch * 2 + 2 * 4 * args.queries
+        d2h = args.queries + 32
+        e2e = {"value": args.steps * (inserted + deleted) / (e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": e_ms / args.steps, "timer": "host wall clock around synchronised calls"}
+
+    # max over ranks
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+        if e2e:
+            te = torch.tensor([e2e["ms_per_step"]], device=dev)
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+            e2e["value"] = world * args.steps * (inserted + deleted) / (float(te.item()) * args.steps / 1e3)
+            e2e["ms_per_step"] = float(te.item())
+
+    value = world * upd_done / (total_ms / 1e3)
+    pk, pk_kind = peaks()
+    hbm = float(pk.get("hbm_gbs", 6800.0))
+    # dominant kernel phase = largest device time in the timed region
+    dom = max((k for k in phases if phases[k][1] > 0 and k in model["kernels"]), key=lambda k: phases[k][0])
+    dom_ms = phases[dom][0] / phases[dom][1]
+    dom_bytes = model["kernels"][dom]
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+    traffic = ncu_traffic(dom)
+    step_gbs = model["step"] / (total_ms / args.steps / 1e3) / 1e9
+    res = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32",
+        "data": "synthetic (seeded RMAT generator; stands in for the paper's DIMACS co-paper graphs)",
+        "config": config_dict(args, world),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "peak_kind": pk_kind, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": dom_bytes, "launch_ms": dom_ms},
+        "step_roofline": {"algorithmic_bytes": model["step"], "achieved_gbs": step_gbs, "frac_of_measured": step_gbs / hbm,
+                          "frac_of_8000": step_gbs / 8000.0},
+        "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items() if v[1]},
+        "gpu_launches": gpu_launches,
+        "clocks": clocks,
+        "e2e": e2e,
+        "counts_per_step": {"inserted": inserted, "deleted": deleted},
+    }
+    g.close()
+    return res, (base, upd, qry)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        base, upd, qry = workload(args.batch, args.queries)
+        import oracle
+        sample, qsample = 1_000_000, 100_000
+        o = oracle.OracleGraph(1 << SCALE)
+        o.bulk_build(*base)
+        s, d = upd[0][:sample], upd[1][:sample]
+        qs, qd = qry[0][:qsample], qry[1][:qsample]
+
+        def ostep():
+            a, _ = o.insert_edges(s, d)
+            o.query_edges(qs, qd)
+            b, _ = o.delete_edges(s, d)
+            return a + b
+
+        for _ in range(args.warmup):
+            ostep()
+        t0 = time.perf_counter()
+        done = 0
+        for _ in range(args.steps):
+            done += ostep()
+        dt = time.perf_counter() - t0
+        v = done / dt
+        a = argparse.Namespace(**vars(args))
+        res = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+               "data": "synthetic", "config": config_dict(a, world),
+               "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"per step: insert {sample} edges of the batch, query {qsample}, "
+                                          f"delete the {sample}, on the full bulk-built graph"},
+               "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(res), flush=True)
+        return 0
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    res, (base, upd, qry) = run_ours(args, rank, world, local_rank)
+    if rank == 0 and not args.no_cpu_baseline:
+        v, steps, secs = oracle_sample_rate(base, upd, qry)
+        res["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"{steps} steps of insert 1,000,000 edges of the batch + query 100,000 + "
+                                         f"delete them, on the full bulk-built graph ({secs:.1f} s)"}
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

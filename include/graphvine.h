@@ -246,6 +246,25 @@ gv_status gv_stats(gv_graph *g, gv_stats_t *out);
  */
 gv_status gv_validate(gv_graph *g, uint64_t *violations, void *stream);
 
+/*
+ * Per-phase device timing (tracing).  While enabled, the library records a
+ * CUDA event pair on the call's stream around every kernel it launches for
+ * this graph; each pair is attributed to a named phase (e.g.
+ * "insert.scatter", "delete.mark").  Off by default; costs one event record
+ * per launch when on.
+ *   gv_profile            enable (1) or disable (0).
+ *   gv_profile_read       synchronises the recorded events, writes for phases
+ *                         0 .. n-1 the summed device milliseconds (ms, may be
+ *                         NULL) and launch counts (launches, may be NULL)
+ *                         since the previous read, then resets them.
+ *   gv_profile_num_phases number of phases.
+ *   gv_profile_phase_name static name of a phase, NULL if out of range.
+ */
+gv_status gv_profile(gv_graph *g, int enable);
+gv_status gv_profile_read(gv_graph *g, double *ms, uint64_t *launches, uint32_t n);
+uint32_t gv_profile_num_phases(void);
+const char *gv_profile_phase_name(uint32_t phase);
+
 /* gv_status_string -- a static, human-readable name for a status code. */
 const char *gv_status_string(gv_status s);
 

@@ -79,6 +79,7 @@ struct gv_graph {
     cudaStream_t last_stream = nullptr;
     uint64_t scratch_bytes = 0;
     uint64_t dict_bytes = 0;
+    gv::Prof prof;
 };
 
 namespace {
@@ -167,6 +168,7 @@ LaunchCfg lcfg(const gv_graph *g, cudaStream_t s) {
     LaunchCfg lc;
     lc.num_sms = g->num_sms;
     lc.stream = s;
+    lc.prof = const_cast<gv::Prof *>(&g->prof);
     return lc;
 }
 
@@ -652,6 +654,11 @@ gv_status gv_destroy(gv_graph *g) {
         dfree(g->arena); dfree(g->found); dfree(g->qpos); dfree(g->partials);
         dfree(g->owner_bits); dfree(g->vres);
         for (auto &b : g->stage.buf) dfree(b.p);
+        for (auto &r : g->prof.recs) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        for (auto e : g->prof.pool) cudaEventDestroy(e);
         if (g->h_small) cudaFreeHost(g->h_small);
         if (g->h_dev) cudaFreeHost(g->h_dev);
         cudaGetLastError();
@@ -833,6 +840,49 @@ gv_status gv_validate(gv_graph *g, uint64_t *violations, void *stream) {
     *violations = viol;
     dfree(g->owner_bits);
     return check_launch();
+}
+
+static const char *kPhaseNames[gv::PH_COUNT] = {
+    "insert.count",   "insert.plan",    "insert.link",   "insert.scatter", "insert.finalize",
+    "delete.count",   "delete.plan",    "delete.arena",  "delete.scatter", "delete.mark",
+    "delete.vscan",   "delete.move",    "delete.finalize",
+    "query.count",    "query.plan",     "query.arena",   "query.scatter",  "query.mark",
+    "query.out",      "query.finalize", "vertex_delete", "neighbors",      "other"};
+
+uint32_t gv_profile_num_phases(void) { return gv::PH_COUNT; }
+
+const char *gv_profile_phase_name(uint32_t phase) {
+    return phase < gv::PH_COUNT ? kPhaseNames[phase] : nullptr;
+}
+
+gv_status gv_profile(gv_graph *g, int enable) {
+    if (!g) return GV_ERR_INVALID_ARG;
+    g->prof.on = enable != 0;
+    return GV_OK;
+}
+
+gv_status gv_profile_read(gv_graph *g, double *ms, uint64_t *launches, uint32_t n) {
+    if (!g) return GV_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    for (uint32_t i = 0; i < n; ++i) {
+        if (ms) ms[i] = 0.0;
+        if (launches) launches[i] = 0;
+    }
+    gv_status st = GV_OK;
+    for (auto &r : g->prof.recs) {
+        if (cudaEventSynchronize(r.b) != cudaSuccess) st = GV_ERR_CUDA;
+        float t = 0.f;
+        if (st == GV_OK && cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) st = GV_ERR_CUDA;
+        if ((uint32_t)r.phase < n) {
+            if (ms) ms[r.phase] += t;
+            if (launches) launches[r.phase] += 1;
+        }
+        g->prof.pool.push_back(r.a);
+        g->prof.pool.push_back(r.b);
+    }
+    g->prof.recs.clear();
+    cudaGetLastError();
+    return st;
 }
 
 }  // extern "C"

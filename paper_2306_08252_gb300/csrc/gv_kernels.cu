@@ -549,7 +549,12 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
             running += tot;
         }
         if (MODE == MODE_QUERY) {
-            if (listmode && lane < a.x && ((qfound >> lane) & 1u)) g.found[a.y + spay] = 1u;
+            if (listmode) {
+                // Hits were recorded at the first sorted position of each key;
+                // equal keys (repeated queries) share that position's bit.
+                const uint32_t first = warp_lower_bound(skey, skey);
+                if (lane < a.x && ((qfound >> first) & 1u)) g.found[a.y + spay] = 1u;
+            }
             continue;
         }
         if (single) {
@@ -940,6 +945,8 @@ inline int grid_for(unsigned long long work, int per_block, int cap) {
 cudaError_t launch_count(int mode, const GraphView &g, const uint32_t *src, const uint32_t *dst,
                          unsigned long long n, const LaunchCfg &lc) {
     const int grid = grid_for(n, AGG_TILE, lc.num_sms * 8);
+    const int ph = mode == MODE_INSERT ? PH_INS_COUNT : mode == MODE_DELETE ? PH_DEL_COUNT : PH_QRY_COUNT;
+    PhaseScope ps(lc, ph);
     switch (mode) {
     case MODE_INSERT: k_count<MODE_INSERT><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
     case MODE_DELETE: k_count<MODE_DELETE><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
@@ -960,11 +967,23 @@ cudaError_t launch_insert_tail(const GraphView &g, const uint32_t *src, const ui
                                unsigned long long *counts, const LaunchCfg &lc) {
     const int cap = lc.num_sms * 8;
     const int gt = grid_for(tcap, 256, cap);
-    k_plan_insert<<<gt, 256, 0, lc.stream>>>(g);
+    {
+        PhaseScope ps(lc, PH_INS_PLAN);
+        k_plan_insert<<<gt, 256, 0, lc.stream>>>(g);
+    }
     const unsigned long long max_pops = n / g.C + tcap + 1;
-    k_link_insert<<<grid_for(max_pops, 256, cap), 256, 0, lc.stream>>>(g);
-    k_scatter_insert<<<grid_for(n, AGG_TILE, cap), AGG_THREADS, 0, lc.stream>>>(g, src, dst, n);
-    k_finalize_insert<<<gt, 256, 0, lc.stream>>>(g, n, counts);
+    {
+        PhaseScope ps(lc, PH_INS_LINK);
+        k_link_insert<<<grid_for(max_pops, 256, cap), 256, 0, lc.stream>>>(g);
+    }
+    {
+        PhaseScope ps(lc, PH_INS_SCATTER);
+        k_scatter_insert<<<grid_for(n, AGG_TILE, cap), AGG_THREADS, 0, lc.stream>>>(g, src, dst, n);
+    }
+    {
+        PhaseScope ps(lc, PH_INS_FINALIZE);
+        k_finalize_insert<<<gt, 256, 0, lc.stream>>>(g, n, counts);
+    }
     return cudaGetLastError();
 }
 
@@ -975,17 +994,38 @@ static void member_tail(const GraphView &g, const uint32_t *src, const uint32_t 
     const int cap = lc.num_sms * 8;
     const int gt = grid_for(tcap, 256, cap);
     const int gi = lc.num_sms * 8;  // warp-per-item kernels: 8 warps per CTA
-    k_plan_member<MODE><<<gt, 256, 0, lc.stream>>>(g);
-    k_arena_init<MODE><<<grid_for(4 * n + 64, 256, cap), 256, 0, lc.stream>>>(g);
-    k_scatter_member<MODE><<<grid_for(n, AGG_TILE, cap), AGG_THREADS, 0, lc.stream>>>(g, src, dst, n);
-    k_mark<MODE><<<gi, 256, 0, lc.stream>>>(g);
-    if (MODE == MODE_DELETE) {
-        k_vscan<MODE><<<grid_for(tcap, 8, cap), 256, 0, lc.stream>>>(g);
+    const bool del = MODE == MODE_DELETE;
+    {
+        PhaseScope ps(lc, del ? PH_DEL_PLAN : PH_QRY_PLAN);
+        k_plan_member<MODE><<<gt, 256, 0, lc.stream>>>(g);
+    }
+    {
+        PhaseScope ps(lc, del ? PH_DEL_ARENA : PH_QRY_ARENA);
+        k_arena_init<MODE><<<grid_for(4 * n + 64, 256, cap), 256, 0, lc.stream>>>(g);
+    }
+    {
+        PhaseScope ps(lc, del ? PH_DEL_SCATTER : PH_QRY_SCATTER);
+        k_scatter_member<MODE><<<grid_for(n, AGG_TILE, cap), AGG_THREADS, 0, lc.stream>>>(g, src, dst, n);
+    }
+    {
+        PhaseScope ps(lc, del ? PH_DEL_MARK : PH_QRY_MARK);
+        k_mark<MODE><<<gi, 256, 0, lc.stream>>>(g);
+    }
+    if (del) {
+        {
+            PhaseScope ps(lc, PH_DEL_VSCAN);
+            k_vscan<MODE><<<grid_for(tcap, 8, cap), 256, 0, lc.stream>>>(g);
+        }
+        PhaseScope ps(lc, PH_DEL_MOVE);
         k_move<MODE><<<gi, 256, 0, lc.stream>>>(g);
     } else {
+        PhaseScope ps(lc, PH_QRY_OUT);
         k_query_out<<<grid_for(n, 256, cap), 256, 0, lc.stream>>>(g, n, qout);
     }
-    k_finalize_member<MODE><<<gt, 256, 0, lc.stream>>>(g, counts);
+    {
+        PhaseScope ps(lc, del ? PH_DEL_FINALIZE : PH_QRY_FINALIZE);
+        k_finalize_member<MODE><<<gt, 256, 0, lc.stream>>>(g, counts);
+    }
 }
 
 cudaError_t launch_member_tail(int mode, const GraphView &g, const uint32_t *src,
@@ -1000,6 +1040,7 @@ cudaError_t launch_vertex_delete(const GraphView &g, const uint32_t *ids, uint32
                                  const LaunchCfg &lc) {
     const int cap = lc.num_sms * 8;
     const int gi = lc.num_sms * 8;
+    PhaseScope ps(lc, PH_VDEL);
     k_vdel_mark<<<grid_for(k, 256, cap), 256, 0, lc.stream>>>(g, ids, k);
     k_plan_vfree<<<grid_for(k, 256, cap), 256, 0, lc.stream>>>(g);
     k_free_items<<<gi, 256, 0, lc.stream>>>(g);

@@ -3,13 +3,67 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "gv_internal.cuh"
 
 namespace gv {
 
+// Kernel phases timed by the optional per-graph profiler.
+enum Phase : int {
+    PH_INS_COUNT = 0, PH_INS_PLAN, PH_INS_LINK, PH_INS_SCATTER, PH_INS_FINALIZE,
+    PH_DEL_COUNT, PH_DEL_PLAN, PH_DEL_ARENA, PH_DEL_SCATTER, PH_DEL_MARK, PH_DEL_VSCAN, PH_DEL_MOVE,
+    PH_DEL_FINALIZE,
+    PH_QRY_COUNT, PH_QRY_PLAN, PH_QRY_ARENA, PH_QRY_SCATTER, PH_QRY_MARK, PH_QRY_OUT, PH_QRY_FINALIZE,
+    PH_VDEL, PH_NEIGHBORS, PH_OTHER,
+    PH_COUNT
+};
+
+// CUDA events recorded around each kernel launch while profiling is on.
+struct Prof {
+    bool on = false;
+    struct Rec {
+        int phase;
+        cudaEvent_t a, b;
+    };
+    std::vector<cudaEvent_t> pool;
+    std::vector<Rec> recs;
+    cudaEvent_t get() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+};
+
 struct LaunchCfg {
     int num_sms;
     cudaStream_t stream;
+    Prof *prof = nullptr;
+};
+
+// Records a start event now and a stop event when the scope ends.
+struct PhaseScope {
+    const LaunchCfg &lc;
+    int phase;
+    cudaEvent_t a = nullptr;
+    PhaseScope(const LaunchCfg &l, int ph) : lc(l), phase(ph) {
+        if (lc.prof && lc.prof->on) {
+            a = lc.prof->get();
+            cudaEventRecord(a, lc.stream);
+        }
+    }
+    ~PhaseScope() {
+        if (a) {
+            cudaEvent_t b = lc.prof->get();
+            cudaEventRecord(b, lc.stream);
+            lc.prof->recs.push_back({phase, a, b});
+        }
+    }
 };
 
 // Group-by-source counting pass over a pair batch (all modes).

@@ -336,6 +336,7 @@ cudaError_t launch_neighbor_offsets(const GraphView &g, const uint32_t *vids, ui
         cudaMemsetAsync(partials, 0, sizeof(unsigned long long), lc.stream);
         return cudaGetLastError();
     }
+    PhaseScope ps(lc, PH_NEIGHBORS);
     k_nbr_partials<<<nchunks, SCAN_T, 0, lc.stream>>>(g, vids, n, partials);
     k_nbr_scan_partials<<<1, 1024, 0, lc.stream>>>(partials, nchunks);
     k_nbr_apply<<<nchunks, SCAN_T, 0, lc.stream>>>(g, vids, n, partials, nchunks, offsets);
@@ -345,6 +346,7 @@ cudaError_t launch_neighbor_offsets(const GraphView &g, const uint32_t *vids, ui
 cudaError_t launch_neighbor_copy(const GraphView &g, const uint32_t *vids, uint32_t n,
                                  const unsigned long long *offsets, uint32_t *nbrs, const LaunchCfg &lc) {
     if (n == 0) return cudaSuccess;
+    PhaseScope ps(lc, PH_NEIGHBORS);
     k_nbr_plan<<<grid_for(n, 256, lc.num_sms * 8), 256, 0, lc.stream>>>(g, vids, n);
     k_nbr_copy<<<lc.num_sms * 8, 256, 0, lc.stream>>>(g, offsets, nbrs);
     k_clear_items<<<1, 32, 0, lc.stream>>>(g);

@@ -79,6 +79,10 @@ SIGNATURES = {
     "gv_stats": ([c_vp, ctypes.POINTER(gv_stats_t)], ctypes.c_int),
     "gv_validate": ([c_vp, ctypes.POINTER(c_u64), c_vp], ctypes.c_int),
     "gv_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "gv_profile": ([c_vp, ctypes.c_int], ctypes.c_int),
+    "gv_profile_read": ([c_vp, c_vp, c_vp, c_u32], ctypes.c_int),
+    "gv_profile_num_phases": ([], c_u32),
+    "gv_profile_phase_name": ([c_u32], ctypes.c_char_p),
 }
 
 _lib = None
@@ -234,6 +238,20 @@ def gv_validate(g, stream=None):
     return v.value
 
 
+def gv_profile(g, enable):
+    return check(load().gv_profile(g, 1 if enable else 0), "gv_profile")
+
+
+def gv_profile_read(g):
+    """{phase name: (device ms, launches)} since the previous read."""
+    lib = load()
+    n = lib.gv_profile_num_phases()
+    ms = np.zeros(n, dtype=np.float64)
+    cnt = np.zeros(n, dtype=np.uint64)
+    check(lib.gv_profile_read(g, ms.ctypes.data, cnt.ctypes.data, n), "gv_profile_read")
+    return {lib.gv_profile_phase_name(i).decode(): (float(ms[i]), int(cnt[i])) for i in range(n)}
+
+
 # -------------------------------------------------------------- convenience
 
 class Graph:
@@ -300,6 +318,12 @@ class Graph:
 
     def validate(self):
         return gv_validate(self.handle, self._s())
+
+    def profile(self, enable=True):
+        gv_profile(self.handle, enable)
+
+    def profile_read(self):
+        return gv_profile_read(self.handle)
 
     # ---- host-side results (numpy), for tests and tools
     def degrees(self):
