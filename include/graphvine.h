@@ -265,6 +265,35 @@ gv_status gv_profile_read(gv_graph *g, double *ms, uint64_t *launches, uint32_t 
 uint32_t gv_profile_num_phases(void);
 const char *gv_profile_phase_name(uint32_t phase);
 
+/*
+ * gv_degree_offsets_noalloc -- CSR offsets of the listed vertices' current
+ * out-degrees, computed without allocating any memory.  The paper has no
+ * counterpart; this entry point exists for callers that cannot allocate
+ * device memory at the point of the call: code that runs while a stream is
+ * being captured into a CUDA graph (cudaMalloc and cudaFree are not allowed
+ * there), serving loops that must not stall on an allocation (cudaFree
+ * synchronises the whole device), and processes whose device memory is
+ * owned by another allocator.
+ *   d_vids     n uint32 vertex ids, DEVICE memory only.
+ *   n          at most 67,108,864 (2^26); larger n returns GV_ERR_INVALID_ARG
+ *              and does nothing.
+ *   d_offsets  n+1 uint64, DEVICE memory only: offsets[i] = sum of the degrees
+ *              of vids[0 .. i-1], offsets[n] = the total.  Invalid or deleted
+ *              ids count 0.  The same offsets gv_neighbors returns.
+ * Host arrays are rejected with GV_ERR_INVALID_ARG (staging them would
+ * allocate).  Asynchronous on `stream`; nothing is read back.
+ * Scratch: the scan's chunk sums live in one fixed 512 KiB device array that
+ * every GPU loading this library holds until the process exits.  All calls
+ * on a device share it and it keeps the last call's contents (every call
+ * overwrites the part it uses, so nothing needs clearing); calls whose work
+ * overlaps on the GPU -- on different streams without ordering, from any
+ * graph -- race on it and must be serialised by the caller.  The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress),
+ * so make that first call before any stream capture begins.
+ */
+gv_status gv_degree_offsets_noalloc(gv_graph *g, const uint32_t *d_vids, uint32_t n, uint64_t *d_offsets,
+                                    void *stream);
+
 /* gv_status_string -- a static, human-readable name for a status code. */
 const char *gv_status_string(gv_status s);
 

@@ -842,6 +842,70 @@ gv_status gv_validate(gv_graph *g, uint64_t *violations, void *stream) {
     return check_launch();
 }
 
+// ----------------------------------------------------------------------------
+// Allocation-free degree offsets (gv_degree_offsets_noalloc).
+//
+// The chunk sums of the prefix scan live in a fixed device array instead of
+// library-allocated memory, so the call performs no allocation at all.  Every
+// GPU that loads this library holds the array (512 KiB) until the process
+// exits.  In host code `g_noalloc_partials` is only a host-side stand-in for
+// the symbol: its device address is taken once per device, with that device
+// current, by cudaGetSymbolAddress on the first call made on that device.
+
+}  // extern "C"
+
+namespace {
+constexpr uint32_t kNoAllocScanChunk = 1024;                           // ids per scan chunk (gv_misc.cu)
+constexpr uint32_t kNoAllocMaxVertices = 1u << 26;                     // ids per call
+constexpr uint32_t kNoAllocChunks = kNoAllocMaxVertices / kNoAllocScanChunk;
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kNoAllocMaxDevices] = {};
+}  // namespace
+
+static __device__ __align__(256) unsigned long long g_noalloc_partials[kNoAllocChunks + 1];
+
+namespace {
+// Device address of the scratch array on `dev` (which must be current).
+gv_status noalloc_scratch(int dev, unsigned long long **out) {
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return GV_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        if (e != cudaSuccess || p == nullptr) {
+            cudaGetLastError();
+            return GV_ERR_CUDA;
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    *out = static_cast<unsigned long long *>(g_noalloc_addr[dev]);
+    return GV_OK;
+}
+}  // namespace
+
+extern "C" {
+
+gv_status gv_degree_offsets_noalloc(gv_graph *g, const uint32_t *d_vids, uint32_t n, uint64_t *d_offsets,
+                                    void *stream) {
+    if (!g || !d_offsets || (n > 0 && !d_vids)) return GV_ERR_INVALID_ARG;
+    if (n > kNoAllocMaxVertices) return GV_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    // Host arrays would need staging buffers, i.e. an allocation.
+    if (is_host_ptr(d_offsets) || (n > 0 && is_host_ptr(d_vids))) return GV_ERR_INVALID_ARG;
+    unsigned long long *scratch = nullptr;
+    GV_TRY(noalloc_scratch(g->device, &scratch));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    g->last_stream = s;
+    gv::LaunchCfg lc;  // no profiler: event creation is avoided as well
+    lc.num_sms = g->num_sms;
+    lc.stream = s;
+    lc.prof = nullptr;
+    GV_CK(gv::launch_neighbor_offsets(view(g), d_vids, n, reinterpret_cast<unsigned long long *>(d_offsets),
+                                      scratch, lc));
+    return check_launch();
+}
+
 static const char *kPhaseNames[gv::PH_COUNT] = {
     "insert.count",   "insert.plan",    "insert.link",   "insert.scatter", "insert.finalize",
     "delete.count",   "delete.plan",    "delete.arena",  "delete.scatter", "delete.mark",

@@ -83,6 +83,7 @@ SIGNATURES = {
     "gv_profile_read": ([c_vp, c_vp, c_vp, c_u32], ctypes.c_int),
     "gv_profile_num_phases": ([], c_u32),
     "gv_profile_phase_name": ([c_u32], ctypes.c_char_p),
+    "gv_degree_offsets_noalloc": ([c_vp, c_vp, c_u32, c_vp, c_vp], ctypes.c_int),
 }
 
 _lib = None
@@ -236,6 +237,11 @@ def gv_validate(g, stream=None):
     v = c_u64(0)
     check(load().gv_validate(g, ctypes.byref(v), stream), "gv_validate")
     return v.value
+
+
+def gv_degree_offsets_noalloc(g, d_vids, d_offsets, stream=None):
+    """Degree offsets of the listed vertices with no allocation (device arrays only)."""
+    return load().gv_degree_offsets_noalloc(g, ptr(d_vids), _len(d_vids), ptr(d_offsets), stream)
 
 
 def gv_profile(g, enable):
