@@ -79,6 +79,7 @@ struct gv_graph {
     cudaStream_t last_stream = nullptr;
     uint64_t scratch_bytes = 0;
     uint64_t dict_bytes = 0;
+    bool any_vertex_deleted = false;
     gv::Prof prof;
 };
 
@@ -142,6 +143,7 @@ GraphView view(const gv_graph *g) {
     v.C = g->C;
     v.IB = g->IB;
     v.nv = g->nv;
+    v.all_alive = g->any_vertex_deleted ? 0u : 1u;
     v.vcnt = g->vcnt;
     v.vcur = g->vcur;
     v.vtid = g->vtid;
@@ -762,6 +764,8 @@ gv_status gv_delete_vertices(gv_graph *g, const uint32_t *ids, uint32_t k, void 
         v.C = 4;
         v.IB = 32;
     }
+    g->any_vertex_deleted = true;
+    v.all_alive = 0;
     GV_CK(gv::launch_vertex_delete(v, (const uint32_t *)di, k, lcfg(g, s)));
     return check_launch();
 }

@@ -59,6 +59,7 @@ struct GraphView {
     uint32_t C;             // entries per block
     uint32_t IB;            // blocks per work item (IB * C <= 512)
     uint32_t nv;            // vertex count
+    uint32_t all_alive;     // 1 while no vertex has ever been deleted (alive[] need not be read)
     // vertex-indexed scratch (zero between calls)
     uint32_t *vcnt;         // batch entries per source
     uint32_t *vcur;         // rank cursor per source

@@ -79,14 +79,90 @@ __device__ __forceinline__ unsigned long long ring(unsigned long long base, unsi
     return q >= P ? q - P : q;
 }
 
+// Freed block ids of one warp, staged in shared memory and pushed onto the
+// edge queue 32 at a time with one atomic on the call's free counter (the
+// queue positions are q_back + counter, published by the finalize kernel).
+struct FreeStage {
+    uint32_t *buf;  // 64 ids: this warp's slice of shared memory
+    uint32_t n;     // ids held (warp-uniform)
+
+    __device__ __forceinline__ void flush(uint32_t cnt, Dev *dev, uint32_t *queue, unsigned long long qbb,
+                                          unsigned long long P) {
+        unsigned long long base = 0;
+        if (lane_id() == 0 && cnt) base = atomicAdd(&dev->free_total, (unsigned long long)cnt);
+        base = __shfl_sync(FULL, base, 0);
+        if (lane_id() < cnt) queue[ring(qbb, base + lane_id(), P)] = buf[lane_id()];
+        __syncwarp();
+    }
+
+    // All 32 lanes call; lanes with `want` add `id`.
+    __device__ __forceinline__ void push(bool want, uint32_t id, Dev *dev, uint32_t *queue, unsigned long long qbb,
+                                         unsigned long long P) {
+        const uint32_t lane = lane_id();
+        const unsigned bal = __ballot_sync(FULL, want);
+        if (want) buf[n + __popc(bal & ((1u << lane) - 1u))] = id;
+        n += __popc(bal);
+        __syncwarp();
+        if (n >= 32) {
+            flush(32, dev, queue, qbb, P);
+            const uint32_t rem = n - 32;
+            const uint32_t x = lane < rem ? buf[32 + lane] : 0u;
+            __syncwarp();
+            if (lane < rem) buf[lane] = x;
+            __syncwarp();
+            n = rem;
+        }
+    }
+};
+
 // ---------------------------------------------------------------- grouping
 
-template <int MODE>
+// Loads one tile's pairs and their validity with every global load issued
+// before any of them is consumed (memory-level parallelism).  Pair e of this
+// thread is pair base + e * AGG_THREADS + threadIdx.x.
+__device__ __forceinline__ void load_tile(const GraphView &g, const uint32_t *__restrict__ src,
+                                          const uint32_t *__restrict__ dst, unsigned long long n,
+                                          unsigned long long base, uint32_t (&us)[AGG_EPT],
+                                          uint32_t (&vs)[AGG_EPT], uint32_t &okmask, uint32_t &inmask) {
+    okmask = 0;
+    inmask = 0;
+#pragma unroll
+    for (int e = 0; e < AGG_EPT; ++e) {
+        const unsigned long long i = base + (unsigned long long)e * AGG_THREADS + threadIdx.x;
+        const bool in = i < n;
+        us[e] = in ? __ldg(src + i) : NIL;
+        vs[e] = in ? __ldg(dst + i) : NIL;
+        if (in) inmask |= 1u << e;
+    }
+#pragma unroll
+    for (int e = 0; e < AGG_EPT; ++e)
+        if (us[e] < g.nv && vs[e] < g.nv) okmask |= 1u << e;
+    if (!g.all_alive) {
+        uint8_t au[AGG_EPT], av[AGG_EPT];
+#pragma unroll
+        for (int e = 0; e < AGG_EPT; ++e) {
+            const bool ok = (okmask >> e) & 1u;
+            au[e] = ok ? g.alive[us[e]] : 0;
+            av[e] = ok ? g.alive[vs[e]] : 0;
+        }
+#pragma unroll
+        for (int e = 0; e < AGG_EPT; ++e)
+            if (!(au[e] && av[e])) okmask &= ~(1u << e);
+    }
+    okmask &= inmask;
+}
+
+// Counting pass.  SPARSE: the tile that finds a source's count at zero lists
+// it as touched (atomics with return).  DENSE (large batches): counts use
+// atomics without return and the touched list is built afterwards by a
+// compaction over all vertices (k_touched_scan).
+template <int MODE, bool DENSE>
 __global__ void __launch_bounds__(AGG_THREADS) k_count(GraphView g, const uint32_t *__restrict__ src,
                                                        const uint32_t *__restrict__ dst,
                                                        unsigned long long n) {
     __shared__ uint32_t keys[AGG_H];
     __shared__ uint32_t cnt[AGG_H];
+    __shared__ uint32_t s_tbase;
     unsigned long long rej = 0;
     const unsigned long long ntiles = (n + AGG_TILE - 1) / AGG_TILE;
     for (unsigned long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -94,36 +170,55 @@ __global__ void __launch_bounds__(AGG_THREADS) k_count(GraphView g, const uint32
             keys[i] = EMPTY_KEY;
             cnt[i] = 0;
         }
+        uint32_t us[AGG_EPT], vs[AGG_EPT], okmask, inmask;
+        load_tile(g, src, dst, n, tile * AGG_TILE, us, vs, okmask, inmask);
+        rej += __popc(inmask & ~okmask);
         __syncthreads();
-        const unsigned long long base = tile * AGG_TILE;
-        uint32_t us[AGG_EPT], vs[AGG_EPT];
 #pragma unroll
         for (int e = 0; e < AGG_EPT; ++e) {
-            const unsigned long long i = base + (unsigned long long)e * AGG_THREADS + threadIdx.x;
-            us[e] = i < n ? __ldg(src + i) : NIL;
-            vs[e] = i < n ? __ldg(dst + i) : NIL;
-        }
-#pragma unroll
-        for (int e = 0; e < AGG_EPT; ++e) {
-            const unsigned long long i = base + (unsigned long long)e * AGG_THREADS + threadIdx.x;
-            if (i < n) {
-                if (valid_pair(g, us[e], vs[e])) {
-                    uint32_t r;
-                    agg_insert(keys, cnt, us[e], r);
-                } else {
-                    ++rej;
-                }
+            if ((okmask >> e) & 1u) {
+                uint32_t r;
+                agg_insert(keys, cnt, us[e], r);
             }
         }
         __syncthreads();
-        for (int s = threadIdx.x; s < AGG_H; s += AGG_THREADS) {
-            const uint32_t u = keys[s];
-            bool isnew = false;
-            if (u != EMPTY_KEY) isnew = atomicAdd(&g.vcnt[u], cnt[s]) == 0u;
-            const uint32_t t = warp_atomic_add<unsigned int>(&g.dev->n_touched, 1u, isnew);
-            if (isnew) {
+        if (DENSE) {
+#pragma unroll
+            for (int i = 0; i < AGG_SPT; ++i) {
+                const int s = threadIdx.x + i * AGG_THREADS;
+                const uint32_t u = keys[s];
+                if (u != EMPTY_KEY) atomicAdd(&g.vcnt[u], cnt[s]);
+            }
+        } else {
+            // One atomic per (tile, source), all issued back to back; the tile
+            // that finds a zero count lists the source as touched, and the
+            // tile's new entries take one atomic on the list length.
+            uint32_t fresh = 0;
+#pragma unroll
+            for (int h0 = 0; h0 < AGG_SPT; h0 += AGG_SPT / 2) {
+                uint32_t old[AGG_SPT / 2];
+#pragma unroll
+                for (int i = 0; i < AGG_SPT / 2; ++i) {
+                    const int s = threadIdx.x + (h0 + i) * AGG_THREADS;
+                    const uint32_t u = keys[s];
+                    old[i] = u != EMPTY_KEY ? atomicAdd(&g.vcnt[u], cnt[s]) : 1u;
+                }
+#pragma unroll
+                for (int i = 0; i < AGG_SPT / 2; ++i)
+                    if (old[i] == 0u) fresh |= 1u << (h0 + i);
+            }
+            uint32_t ntot;
+            const uint32_t ex = block_excl_scan(__popc(fresh), &ntot);
+            if (threadIdx.x == 0) s_tbase = ntot ? atomicAdd(&g.dev->n_touched, ntot) : 0u;
+            __syncthreads();
+            uint32_t t = s_tbase + ex;
+            while (fresh) {
+                const int i = __ffs(fresh) - 1;
+                fresh &= fresh - 1u;
+                const uint32_t u = keys[threadIdx.x + i * AGG_THREADS];
                 g.t_vid[t] = u;
                 g.vtid[u] = t;
+                ++t;
             }
         }
         __syncthreads();
@@ -131,6 +226,36 @@ __global__ void __launch_bounds__(AGG_THREADS) k_count(GraphView g, const uint32
     if (MODE != MODE_QUERY) {
         const unsigned long long r = warp_sum_u64(rej);
         if (lane_id() == 0 && r) atomicAdd(&g.dev->call_b, r);
+    }
+}
+
+// Touched list of a DENSE count: every vertex with a non-zero count, in
+// vertex order (one atomic per CTA chunk).
+__global__ void __launch_bounds__(256) k_touched_scan(GraphView g) {
+    const uint32_t nv = g.nv;
+    __shared__ uint32_t s_base;
+    for (uint32_t base = blockIdx.x * blockDim.x * 4; base < nv; base += gridDim.x * blockDim.x * 4) {
+        uint32_t flags = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t u = base + threadIdx.x * 4 + j;
+            if (u < nv && g.vcnt[u]) flags |= 1u << j;
+        }
+        uint32_t tot;
+        const uint32_t ex = block_excl_scan(__popc(flags), &tot);
+        if (threadIdx.x == 0) s_base = tot ? atomicAdd(&g.dev->n_touched, tot) : 0u;
+        __syncthreads();
+        uint32_t t = s_base + ex;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if ((flags >> j) & 1u) {
+                const uint32_t u = base + threadIdx.x * 4 + j;
+                g.t_vid[t] = u;
+                g.vtid[u] = t;
+                ++t;
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -222,7 +347,7 @@ __global__ void __launch_bounds__(256) k_link_insert(GraphView g) {
     }
 }
 
-__global__ void __launch_bounds__(AGG_THREADS) k_scatter_insert(GraphView g,
+__global__ void __launch_bounds__(AGG_THREADS, 3) k_scatter_insert(GraphView g,
                                                                 const uint32_t *__restrict__ src,
                                                                 const uint32_t *__restrict__ dst,
                                                                 unsigned long long n) {
@@ -239,45 +364,83 @@ __global__ void __launch_bounds__(AGG_THREADS) k_scatter_insert(GraphView g,
             keys[i] = EMPTY_KEY;
             cnt[i] = 0;
         }
+        uint32_t us[AGG_EPT], vs[AGG_EPT], okmask, inmask;
+        load_tile(g, src, dst, n, tile * AGG_TILE, us, vs, okmask, inmask);
         __syncthreads();
-        const unsigned long long base = tile * AGG_TILE;
-        uint32_t vs[AGG_EPT], slot[AGG_EPT], rank[AGG_EPT];
+        // slot (12 bits) and in-tile rank (11 bits) of each pair, packed
+        uint32_t sr[AGG_EPT];
 #pragma unroll
         for (int e = 0; e < AGG_EPT; ++e) {
-            const unsigned long long i = base + (unsigned long long)e * AGG_THREADS + threadIdx.x;
-            const uint32_t u = i < n ? __ldg(src + i) : NIL;
-            vs[e] = i < n ? __ldg(dst + i) : NIL;
-            slot[e] = NIL;
-            if (i < n && valid_pair(g, u, vs[e])) slot[e] = agg_insert(keys, cnt, u, rank[e]);
-        }
-        __syncthreads();
-        for (int s = threadIdx.x; s < AGG_H; s += AGG_THREADS) {
-            const uint32_t u = keys[s];
-            if (u != EMPTY_KEY) {
-                cnt[s] = atomicAdd(&g.vcur[u], cnt[s]);
-                tid[s] = g.vtid[u];
+            sr[e] = NIL;
+            if ((okmask >> e) & 1u) {
+                uint32_t r;
+                const uint32_t sl = agg_insert(keys, cnt, us[e], r);
+                sr[e] = sl | (r << 12);
             }
         }
         __syncthreads();
+        {
+            // rank cursors: independent atomics, issued back to back
+            // two halves of AGG_SPT / 2 slots: 8 atomics in flight per thread
+#pragma unroll
+            for (int h0 = 0; h0 < AGG_SPT; h0 += AGG_SPT / 2) {
+                uint32_t bs[AGG_SPT / 2], ts[AGG_SPT / 2];
+#pragma unroll
+                for (int i = 0; i < AGG_SPT / 2; ++i) {
+                    const int s = threadIdx.x + (h0 + i) * AGG_THREADS;
+                    const uint32_t u = keys[s];
+                    if (u != EMPTY_KEY) {
+                        bs[i] = atomicAdd(&g.vcur[u], cnt[s]);
+                        ts[i] = g.vtid[u];
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < AGG_SPT / 2; ++i) {
+                    const int s = threadIdx.x + (h0 + i) * AGG_THREADS;
+                    if (keys[s] != EMPTY_KEY) {
+                        cnt[s] = bs[i];
+                        tid[s] = ts[i];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // per pair: rank r, source info, then the queue slot of a new block,
+        // then the store -- each stage's loads issued for all pairs first
+        uint4 a[AGG_EPT];
 #pragma unroll
         for (int e = 0; e < AGG_EPT; ++e) {
-            if (slot[e] != NIL) {
-                const uint32_t r = cnt[slot[e]] + rank[e];
-                const uint4 a = g.t_a[tid[slot[e]]];
-                const uint32_t deg = a.x, last = a.y, off = a.z;
+            if (sr[e] != NIL) {
+                const uint32_t sl = sr[e] & 0xFFFu;
+                a[e] = g.t_a[tid[sl]];
+                a[e].w = cnt[sl] + (sr[e] >> 12);  // w: rank within the source's batch
+            }
+        }
+        uint32_t blk[AGG_EPT], lane[AGG_EPT];
+#pragma unroll
+        for (int e = 0; e < AGG_EPT; ++e) {
+            blk[e] = NIL;
+            lane[e] = 0;
+            if (sr[e] != NIL) {
+                const uint32_t r = a[e].w;
+                const uint32_t deg = a[e].x, off = a[e].z;
                 const uint32_t nb = (deg + C - 1) / C;
                 const uint32_t space = nb * C - deg;
-                uint32_t b, lane;
                 if (r < space) {
-                    b = last;
-                    lane = deg - (nb - 1) * C + r;
+                    blk[e] = a[e].y;
+                    lane[e] = deg - (nb - 1) * C + r;
                 } else {
                     const uint32_t q = r - space;
                     const uint32_t jb = q / C;
-                    lane = q - jb * C;
-                    b = g.queue[ring(qbase, off + jb, P)];
+                    lane[e] = q - jb * C;
+                    blk[e] = g.queue[ring(qbase, off + jb, P)];
                 }
-                if (b < P) g.data[(size_t)b * C + lane] = vs[e];
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < AGG_EPT; ++e) {
+            if (sr[e] != NIL) {
+                if (blk[e] < P) g.data[(size_t)blk[e] * C + lane[e]] = vs[e];
                 else latch_status(g.dev, 5u /* GV_ERR_STATE */);
             }
         }
@@ -400,7 +563,7 @@ __global__ void __launch_bounds__(256) k_arena_init(GraphView g) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(AGG_THREADS) k_scatter_member(GraphView g,
+__global__ void __launch_bounds__(AGG_THREADS, 3) k_scatter_member(GraphView g,
                                                                 const uint32_t *__restrict__ src,
                                                                 const uint32_t *__restrict__ dst,
                                                                 unsigned long long n) {
@@ -413,42 +576,91 @@ __global__ void __launch_bounds__(AGG_THREADS) k_scatter_member(GraphView g,
             keys[i] = EMPTY_KEY;
             cnt[i] = 0;
         }
-        __syncthreads();
         const unsigned long long base = tile * AGG_TILE;
-        uint32_t vs[AGG_EPT], slot[AGG_EPT], rank[AGG_EPT];
+        uint32_t us[AGG_EPT], vs[AGG_EPT], okmask, inmask;
+        load_tile(g, src, dst, n, base, us, vs, okmask, inmask);
+        __syncthreads();
+        uint32_t sr[AGG_EPT];
 #pragma unroll
         for (int e = 0; e < AGG_EPT; ++e) {
-            const unsigned long long i = base + (unsigned long long)e * AGG_THREADS + threadIdx.x;
-            const uint32_t u = i < n ? __ldg(src + i) : NIL;
-            vs[e] = i < n ? __ldg(dst + i) : NIL;
-            slot[e] = NIL;
-            if (i < n && valid_pair(g, u, vs[e])) slot[e] = agg_insert(keys, cnt, u, rank[e]);
-        }
-        __syncthreads();
-        for (int s = threadIdx.x; s < AGG_H; s += AGG_THREADS) {
-            const uint32_t u = keys[s];
-            if (u != EMPTY_KEY) {
-                cnt[s] = atomicAdd(&g.vcur[u], cnt[s]);
-                tid[s] = g.vtid[u];
+            sr[e] = NIL;
+            if ((okmask >> e) & 1u) {
+                uint32_t r;
+                const uint32_t sl = agg_insert(keys, cnt, us[e], r);
+                sr[e] = sl | (r << 12);
             }
         }
         __syncthreads();
+        {
+            // two halves of AGG_SPT / 2 slots: 8 atomics in flight per thread
+#pragma unroll
+            for (int h0 = 0; h0 < AGG_SPT; h0 += AGG_SPT / 2) {
+                uint32_t bs[AGG_SPT / 2], ts[AGG_SPT / 2];
+#pragma unroll
+                for (int i = 0; i < AGG_SPT / 2; ++i) {
+                    const int s = threadIdx.x + (h0 + i) * AGG_THREADS;
+                    const uint32_t u = keys[s];
+                    if (u != EMPTY_KEY) {
+                        bs[i] = atomicAdd(&g.vcur[u], cnt[s]);
+                        ts[i] = g.vtid[u];
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < AGG_SPT / 2; ++i) {
+                    const int s = threadIdx.x + (h0 + i) * AGG_THREADS;
+                    if (keys[s] != EMPTY_KEY) {
+                        cnt[s] = bs[i];
+                        tid[s] = ts[i];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // list entries: plain stores; hash entries: a first CAS at the home
+        // slot for every pair, issued back to back, then probing for the
+        // (rare) collisions
+        uint32_t aoff[AGG_EPT], hs[AGG_EPT], pos[AGG_EPT];
 #pragma unroll
         for (int e = 0; e < AGG_EPT; ++e) {
-            const unsigned long long i = base + (unsigned long long)e * AGG_THREADS + threadIdx.x;
-            if (slot[e] != NIL) {
-                const uint32_t r = cnt[slot[e]] + rank[e];
-                const uint4 a = g.t_a[tid[slot[e]]];
-                uint32_t pos;
-                if (a.z == 0) {
-                    pos = a.y + r;
-                    g.arena[pos] = vs[e];
+            if (sr[e] != NIL) {
+                const uint4 a = g.t_a[tid[sr[e] & 0xFFFu]];
+                aoff[e] = a.y;
+                hs[e] = a.z;
+            }
+        }
+        uint32_t old[AGG_EPT];
+#pragma unroll
+        for (int e = 0; e < AGG_EPT; ++e) {
+            pos[e] = NIL;
+            old[e] = EMPTY_KEY;
+            if (sr[e] != NIL) {
+                if (hs[e] == 0) {
+                    pos[e] = aoff[e] + cnt[sr[e] & 0xFFFu] + (sr[e] >> 12);
+                    g.arena[pos[e]] = vs[e];
                 } else {
-                    pos = a.y + hash_insert(g.arena + a.y, a.z, vs[e]);
+                    pos[e] = aoff[e] + (mix32(vs[e]) & (hs[e] - 1));
+                    old[e] = atomicCAS(&g.arena[pos[e]], EMPTY_KEY, vs[e]);
                 }
-                if (MODE == MODE_QUERY) g.qpos[i] = pos;
-            } else if (MODE == MODE_QUERY && i < n) {
-                g.qpos[i] = NIL;
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < AGG_EPT; ++e) {
+            if (sr[e] != NIL && hs[e] != 0 && old[e] != EMPTY_KEY && old[e] != vs[e]) {
+                uint32_t *tab = g.arena + aoff[e];
+                uint32_t h = (pos[e] - aoff[e] + 1) & (hs[e] - 1);
+                for (uint32_t probe = 1; probe < hs[e]; ++probe) {
+                    const uint32_t o = atomicCAS(&tab[h], EMPTY_KEY, vs[e]);
+                    if (o == EMPTY_KEY || o == vs[e]) break;
+                    h = (h + 1) & (hs[e] - 1);
+                }
+                pos[e] = aoff[e] + h;
+            }
+        }
+        if (MODE == MODE_QUERY) {
+#pragma unroll
+            for (int e = 0; e < AGG_EPT; ++e) {
+                const unsigned long long i = base + (unsigned long long)e * AGG_THREADS + threadIdx.x;
+                if (i < n) g.qpos[i] = pos[e];
             }
         }
         __syncthreads();
@@ -466,6 +678,12 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
     const uint32_t C = g.C, IB = g.IB;
     const unsigned long long P = g.P;
     const unsigned long long qbb = qmod(dev->q_back, P);
+    __shared__ uint32_t s_free[8][64];
+    __shared__ uint32_t s_bid[8][32];
+    __shared__ uint32_t s_hkey[8][64];
+    __shared__ uint32_t s_hfound[8][64];
+    FreeStage fs{s_free[threadIdx.x >> 5], 0u};
+    unsigned long long removed = 0;  // entries deleted by this warp (lane 0)
     for (uint32_t it = warp; it < nitems; it += nwarps) {
         const uint2 itm = g.items[it];
         const uint32_t t = itm.x, c = itm.y;
@@ -481,46 +699,77 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
             continue;
         }
 
+        // Block ids of the item, one per lane, mirrored in shared memory so
+        // that lanes can look up any block without a shuffle.
+        uint32_t *sb_ids = s_bid[threadIdx.x >> 5];
+        sb_ids[lane] = bid;
+        // Batch list of this source (<= 32 entries): a 64-slot shared hash
+        // set per warp; slot_of_mine = slot of list entry `lane`.
         bool listmode = false;
-        uint32_t skey = EMPTY_KEY, spay = lane;
+        uint32_t slot_of_mine = NIL;
+        uint32_t *hk = s_hkey[threadIdx.x >> 5];
+        uint32_t *hf = s_hfound[threadIdx.x >> 5];
         if (MODE == MODE_DELETE || MODE == MODE_QUERY) {
             listmode = (a.z == 0);
             if (listmode) {
-                if (lane < a.x) skey = g.arena[a.y + lane];
-                warp_sort_pairs(skey, spay);
+                hk[lane] = EMPTY_KEY;
+                hk[lane + 32] = EMPTY_KEY;
+                if (MODE == MODE_QUERY) {
+                    hf[lane] = 0u;
+                    hf[lane + 32] = 0u;
+                }
+                __syncwarp();
+                if (lane < a.x) {
+                    const uint32_t v = g.arena[a.y + lane];
+                    uint32_t h = mix32(v) & 63u;
+                    for (;;) {
+                        const uint32_t old = atomicCAS(&hk[h], EMPTY_KEY, v);
+                        if (old == EMPTY_KEY || old == v) break;
+                        h = (h + 1) & 63u;
+                    }
+                    slot_of_mine = h;
+                }
             }
         }
+        __syncwarp();
         const uint32_t sbase = kb * C;
         const uint32_t nslots = min(nblk * C, deg - sbase);
         const uint32_t nquads = (nslots + 3) >> 2;
         const bool single = (ni == 1);
         uint32_t running = 0;
-        uint32_t qfound = 0;
         for (uint32_t q0 = 0; q0 < nquads; q0 += 32) {
             const uint32_t q = q0 + lane;
             const bool qv = q < nquads;
             const uint32_t x = q << 2;
             const uint32_t lb = x / C;
-            const uint32_t myb = __shfl_sync(FULL, bid, lb & 31u);
             uint4 e4 = make_uint4(EMPTY_KEY, EMPTY_KEY, EMPTY_KEY, EMPTY_KEY);
-            if (qv) e4 = *reinterpret_cast<const uint4 *>(g.data + (size_t)myb * C + (x - lb * C));
+            if (qv) e4 = *reinterpret_cast<const uint4 *>(g.data + (size_t)sb_ids[lb] * C + (x - lb * C));
             const uint32_t e[4] = {e4.x, e4.y, e4.z, e4.w};
             uint32_t surv = 0;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const bool valid = qv && (x + j < nslots);
                 bool hit = false;
-                if (MODE == MODE_VDEL) {
-                    if (valid) hit = (g.dead[e[j] >> 5] >> (e[j] & 31u)) & 1u;
-                } else if (listmode) {
-                    const uint32_t pos = warp_lower_bound(skey, e[j]);
-                    const uint32_t kk = __shfl_sync(FULL, skey, pos);
-                    hit = valid && kk == e[j];
-                    if (MODE == MODE_QUERY) qfound |= __reduce_or_sync(FULL, hit ? (1u << pos) : 0u);
-                } else if (valid) {
-                    const uint32_t h = hash_find(g.arena + a.y, a.z, e[j]);
-                    hit = h != NIL;
-                    if (MODE == MODE_QUERY && hit) g.found[a.y + h] = 1u;
+                if (valid) {
+                    if (MODE == MODE_VDEL) {
+                        hit = (g.dead[e[j] >> 5] >> (e[j] & 31u)) & 1u;
+                    } else if (listmode) {
+                        uint32_t h = mix32(e[j]) & 63u;
+                        for (;;) {
+                            const uint32_t k = hk[h];
+                            if (k == e[j]) {
+                                hit = true;
+                                if (MODE == MODE_QUERY) hf[h] = 1u;
+                                break;
+                            }
+                            if (k == EMPTY_KEY) break;
+                            h = (h + 1) & 63u;
+                        }
+                    } else {
+                        const uint32_t h = hash_find(g.arena + a.y, a.z, e[j]);
+                        hit = h != NIL;
+                        if (MODE == MODE_QUERY && hit) g.found[a.y + h] = 1u;
+                    }
                 }
                 if (valid && !hit) surv |= 1u << j;
             }
@@ -533,11 +782,13 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
                 uint32_t w = running + ex;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const bool sj = (surv >> j) & 1u;
-                    const uint32_t tq = w / C;
-                    const uint32_t tb = __shfl_sync(FULL, bid, tq & 31u);
-                    if (sj && w != x + j) g.data[(size_t)tb * C + (w - tq * C)] = e[j];
-                    if (sj) ++w;
+                    if ((surv >> j) & 1u) {
+                        if (w != x + j) {
+                            const uint32_t tq = w / C;
+                            g.data[(size_t)sb_ids[tq] * C + (w - tq * C)] = e[j];
+                        }
+                        ++w;
+                    }
                 }
             } else {
                 uint32_t word = surv << (4u * (lane & 7u));
@@ -549,12 +800,10 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
             running += tot;
         }
         if (MODE == MODE_QUERY) {
-            if (listmode) {
-                // Hits were recorded at the first sorted position of each key;
-                // equal keys (repeated queries) share that position's bit.
-                const uint32_t first = warp_lower_bound(skey, skey);
-                if (lane < a.x && ((qfound >> first) & 1u)) g.found[a.y + spay] = 1u;
-            }
+            __syncwarp();
+            // every list entry (repeated queries included) reads its slot's flag
+            if (listmode && slot_of_mine != NIL && hf[slot_of_mine]) g.found[a.y + lane] = 1u;
+            __syncwarp();
             continue;
         }
         if (single) {
@@ -563,23 +812,24 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
                 const uint32_t nbn = (degn + C - 1) / C;
                 const uint32_t k = lane + 1;
                 const bool fr = lane < nblk && k > nbn;
-                const unsigned long long fpos = warp_atomic_add<unsigned long long>(&dev->free_total, 1u, fr);
+                fs.push(fr, bid, dev, g.queue, qbb, P);
                 const uint32_t p = k >> 1;
                 const uint32_t pb = __shfl_sync(FULL, bid, (p - 1) & 31u);
                 const uint32_t lastb = __shfl_sync(FULL, bid, (nbn - 1) & 31u);
-                if (fr) {
-                    g.queue[ring(qbb, fpos, P)] = bid;
-                    if (p >= 1 && p <= nbn) g.links[2ull * pb + (k & 1u)] = NIL;
-                }
+                if (fr && p >= 1 && p <= nbn) g.links[2ull * pb + (k & 1u)] = NIL;
                 if (lane == 0) {
                     g.sent[g.t_vid[t]] = make_uint4(degn, nbn, nbn ? root : NIL, nbn ? lastb : NIL);
-                    atomicAdd(&dev->call_a, (unsigned long long)(deg - degn));
+                    removed += deg - degn;
                 }
             }
         } else {
             if (lane < nblk) g.it_bid[(size_t)it * IB + lane] = bid;
             if (lane == 0) g.it_cnt[it] = running;
         }
+    }
+    if (MODE != MODE_QUERY) {
+        fs.flush(fs.n, dev, g.queue, qbb, P);
+        if (lane == 0 && removed) atomicAdd(&dev->call_a, removed);
     }
 }
 
@@ -592,6 +842,7 @@ __global__ void __launch_bounds__(256) k_vscan(GraphView g) {
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t C = g.C, IB = g.IB, SPI = IB * C;
+    unsigned long long removed = 0;
     for (uint32_t t = warp; t < nt; t += nwarps) {
         const uint4 b = g.t_b[t];
         const uint32_t ni = b.w;
@@ -646,9 +897,10 @@ __global__ void __launch_bounds__(256) k_vscan(GraphView g) {
                 lastb = g.it_bid[(size_t)(item0 + k / IB) * IB + (k % IB)];
             }
             g.sent[g.t_vid[t]] = make_uint4(degn, nbn, nbn ? root : NIL, lastb);
-            if (deg != degn) atomicAdd(&dev->call_a, (unsigned long long)(deg - degn));
+            removed += deg - degn;
         }
     }
+    if (lane == 0 && removed) atomicAdd(&dev->call_a, removed);
 }
 
 // One warp per item of a multi-item source.
@@ -662,6 +914,8 @@ __global__ void __launch_bounds__(256) k_move(GraphView g) {
     const uint32_t C = g.C, IB = g.IB, SPI = IB * C;
     const unsigned long long P = g.P;
     const unsigned long long qbb = qmod(dev->q_back, P);
+    __shared__ uint32_t s_free[8][64];
+    FreeStage fs{s_free[threadIdx.x >> 5], 0u};
     for (uint32_t it = warp; it < nitems; it += nwarps) {
         const uint2 itm = g.items[it];
         const uint32_t t = itm.x, c = itm.y;
@@ -731,9 +985,8 @@ __global__ void __launch_bounds__(256) k_move(GraphView g) {
         const uint32_t nblk = min(IB, nb - kb);
         const uint32_t k = kb + 1 + lane;
         const bool fr = lane < nblk && k > nbn;
-        const unsigned long long fpos = warp_atomic_add<unsigned long long>(&dev->free_total, 1u, fr);
+        fs.push(fr, fr ? bids[lane] : NIL, dev, g.queue, qbb, P);
         if (fr) {
-            g.queue[ring(qbb, fpos, P)] = bids[lane];
             const uint32_t p = k >> 1;
             if (p >= 1 && p <= nbn) {
                 const uint32_t pb = g.it_bid[(size_t)(item0 + (p - 1) / IB) * IB + (p - 1) % IB];
@@ -741,6 +994,7 @@ __global__ void __launch_bounds__(256) k_move(GraphView g) {
             }
         }
     }
+    fs.flush(fs.n, dev, g.queue, qbb, P);
 }
 
 __global__ void __launch_bounds__(256) k_query_out(GraphView g, unsigned long long n, uint8_t *out) {
@@ -848,6 +1102,8 @@ __global__ void __launch_bounds__(256) k_free_items(GraphView g) {
     const uint32_t IB = g.IB;
     const unsigned long long P = g.P;
     const unsigned long long qbb = qmod(dev->q_back, P);
+    __shared__ uint32_t s_free[8][64];
+    FreeStage fs{s_free[threadIdx.x >> 5], 0u};
     for (uint32_t it = warp; it < nitems; it += nwarps) {
         const uint2 itm = g.items[it];
         const uint4 b = g.t_b[itm.x];
@@ -857,9 +1113,9 @@ __global__ void __launch_bounds__(256) k_free_items(GraphView g) {
         uint32_t bid = NIL;
         if (fr) bid = cbt_walk(g.links, P, b.z, kb + 1 + lane);
         if (fr && bid == NIL) latch_status(dev, 5u /* GV_ERR_STATE */);
-        const unsigned long long fpos = warp_atomic_add<unsigned long long>(&dev->free_total, 1u, fr);
-        if (fr && bid != NIL) g.queue[ring(qbb, fpos, P)] = bid;
+        fs.push(fr && bid != NIL, bid, dev, g.queue, qbb, P);
     }
+    fs.flush(fs.n, dev, g.queue, qbb, P);
 }
 
 // Between the two phases of a vertex delete: the touched list and the item
@@ -947,10 +1203,22 @@ cudaError_t launch_count(int mode, const GraphView &g, const uint32_t *src, cons
     const int grid = grid_for(n, AGG_TILE, lc.num_sms * 8);
     const int ph = mode == MODE_INSERT ? PH_INS_COUNT : mode == MODE_DELETE ? PH_DEL_COUNT : PH_QRY_COUNT;
     PhaseScope ps(lc, ph);
-    switch (mode) {
-    case MODE_INSERT: k_count<MODE_INSERT><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
-    case MODE_DELETE: k_count<MODE_DELETE><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
-    default: k_count<MODE_QUERY><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
+    // Large batches touch a large share of the vertices: count without
+    // return values and list the touched vertices by one pass over all of them.
+    const bool dense = n >= (unsigned long long)g.nv / 8;
+    if (dense) {
+        switch (mode) {
+        case MODE_INSERT: k_count<MODE_INSERT, true><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
+        case MODE_DELETE: k_count<MODE_DELETE, true><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
+        default: k_count<MODE_QUERY, true><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
+        }
+        k_touched_scan<<<grid_for(g.nv, 1024, lc.num_sms * 8), 256, 0, lc.stream>>>(g);
+    } else {
+        switch (mode) {
+        case MODE_INSERT: k_count<MODE_INSERT, false><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
+        case MODE_DELETE: k_count<MODE_DELETE, false><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
+        default: k_count<MODE_QUERY, false><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
+        }
     }
     return cudaGetLastError();
 }

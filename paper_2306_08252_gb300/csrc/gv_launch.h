@@ -111,6 +111,7 @@ constexpr int AGG_THREADS = 256;
 constexpr int AGG_EPT = 8;
 constexpr int AGG_TILE = AGG_THREADS * AGG_EPT;  // pairs per tile
 constexpr int AGG_H = 4096;                      // shared hash slots per tile (>= 2 * tile)
+constexpr int AGG_SPT = AGG_H / AGG_THREADS;     // hash slots per thread
 constexpr int MASK_WORDS = 16;                   // survivor bits per item (512 slots)
 
 }  // namespace gv
