@@ -55,8 +55,10 @@ struct gv_graph {
     Dev *h_dev = nullptr;  // pinned mirror for stats
     // touched scratch
     unsigned long long tcap = 0;
-    uint32_t *t_vid = nullptr;
+    uint32_t *t_vid = nullptr, *t_tiny = nullptr;
     uint4 *t_a = nullptr, *t_b = nullptr;
+    unsigned long long rcap = 0;
+    uint32_t *prank = nullptr;
     unsigned long long ocap = 0;
     uint32_t *t_owner = nullptr;
     // items
@@ -151,6 +153,8 @@ GraphView view(const gv_graph *g) {
     v.t_a = g->t_a;
     v.t_b = g->t_b;
     v.t_owner = g->t_owner;
+    v.t_tiny = g->t_tiny;
+    v.prank = g->prank;
     v.items = g->items;
     v.it_mask = g->it_mask;
     v.it_cnt = g->it_cnt;
@@ -273,8 +277,9 @@ gv_status ensure_vertex_capacity(gv_graph *g, uint32_t need, cudaStream_t s) {
 gv_status ensure_touched(gv_graph *g, unsigned long long need) {
     if (need <= g->tcap && g->tcap) return GV_OK;
     unsigned long long cap = std::max<unsigned long long>(need, std::max<unsigned long long>(2 * g->tcap, 1024));
-    dfree(g->t_vid); dfree(g->t_a); dfree(g->t_b);
+    dfree(g->t_vid); dfree(g->t_a); dfree(g->t_b); dfree(g->t_tiny);
     g->tcap = 0;
+    GV_TRY(dalloc(&g->t_tiny, cap, &g->scratch_bytes));
     GV_TRY(dalloc(&g->t_vid, cap, &g->scratch_bytes));
     GV_TRY(dalloc(&g->t_a, cap, &g->scratch_bytes));
     GV_TRY(dalloc(&g->t_b, cap, &g->scratch_bytes));
@@ -380,10 +385,21 @@ gv_status setup_pool(gv_graph *g, uint32_t C, cudaStream_t s) {
     return GV_OK;
 }
 
+gv_status ensure_ranks(gv_graph *g, unsigned long long n) {
+    if (n <= g->rcap && g->rcap) return GV_OK;
+    unsigned long long cap = std::max<unsigned long long>(n, std::max<unsigned long long>(2 * g->rcap, 4096));
+    dfree(g->prank);
+    g->rcap = 0;
+    GV_TRY(dalloc(&g->prank, cap, &g->scratch_bytes));
+    g->rcap = cap;
+    return GV_OK;
+}
+
 // Scratch for a pair batch of n (insert / delete / query).
 gv_status ensure_batch(gv_graph *g, uint64_t n, int mode) {
     const unsigned long long touched = std::min<unsigned long long>(n, g->nv ? g->nv : 1);
     GV_TRY(ensure_touched(g, touched));
+    GV_TRY(ensure_ranks(g, n));
     if (mode == gv::MODE_INSERT) {
         GV_TRY(ensure_owner(g, (g->C ? n / g->C : n) + touched + 1));
     } else {
@@ -426,6 +442,7 @@ gv_status insert_impl(gv_graph *g, const uint32_t *src, const uint32_t *dst, uin
     if (counts) GV_TRY(output_ptr(g, 2, counts, 16, &dcounts, &host_counts));
     const unsigned long long touched = std::min<unsigned long long>(n, g->nv ? g->nv : 1);
     GV_TRY(ensure_touched(g, touched));
+    GV_TRY(ensure_ranks(g, n));
     if (g->C == 0) {
         // First batch fixes C (paper rule), then the pool can be laid out.
         GraphView v = view(g);
@@ -651,7 +668,7 @@ gv_status gv_destroy(gv_graph *g) {
         if (g->pool_alloc) cudaFree(g->pool_alloc);
         dfree(g->sent); dfree(g->alive); dfree(g->vcnt); dfree(g->vcur); dfree(g->vtid); dfree(g->dead);
         dfree(g->dev);
-        dfree(g->t_vid); dfree(g->t_a); dfree(g->t_b); dfree(g->t_owner);
+        dfree(g->t_vid); dfree(g->t_a); dfree(g->t_b); dfree(g->t_owner); dfree(g->t_tiny); dfree(g->prank);
         dfree(g->items); dfree(g->it_mask); dfree(g->it_cnt); dfree(g->it_H); dfree(g->it_S); dfree(g->it_bid);
         dfree(g->arena); dfree(g->found); dfree(g->qpos); dfree(g->partials);
         dfree(g->owner_bits); dfree(g->vres);
@@ -777,6 +794,7 @@ gv_status gv_reserve(gv_graph *g, uint64_t max_batch) {
     GV_TRY(ensure_owner(g, (g->C ? max_batch / g->C : max_batch) + std::min<unsigned long long>(max_batch, g->nv) + 1));
     if (g->C) GV_TRY(ensure_items(g, item_bound(g, std::min<unsigned long long>(max_batch, g->nv ? g->nv : 1))));
     GV_TRY(ensure_arena(g, 4 * max_batch + 64, true, max_batch));
+    GV_TRY(ensure_ranks(g, max_batch));
     for (int slot = 0; slot < 4; ++slot) {
         void *d = nullptr;
         GV_TRY(stage_buf(g, slot, max_batch * 4 + 64, &d));

@@ -44,7 +44,8 @@ struct Dev {
     unsigned int done_ctas;         // last-CTA ticket of the finalize kernels
     unsigned int status;            // latched device status (gv_status), sticky
     unsigned int abort;             // set when this call must not mutate the graph
-    unsigned int pad[3];
+    unsigned int n_tiny;            // touched sources handled one per thread
+    unsigned int pad[2];
 };
 
 // Everything a kernel needs to know about one graph (passed by value).
@@ -62,13 +63,15 @@ struct GraphView {
     uint32_t all_alive;     // 1 while no vertex has ever been deleted (alive[] need not be read)
     // vertex-indexed scratch (zero between calls)
     uint32_t *vcnt;         // batch entries per source
-    uint32_t *vcur;         // rank cursor per source
+    uint32_t *vcur;         // per-source offset set by the plan (queue or arena)
     uint32_t *vtid;         // touched index of a source (valid while vcnt > 0)
     // touched-indexed scratch
     uint32_t *t_vid;        // touched source ids
     uint4 *t_a;             // per-touched info A (op specific)
     uint4 *t_b;             // per-touched info B (op specific)
     uint32_t *t_owner;      // insert: pop index -> touched index
+    uint32_t *t_tiny;       // touched indices of tiny adjacencies (one thread each)
+    uint32_t *prank;        // per pair: rank among its source's batch pairs (NIL = rejected)
     // work items (membership ops)
     uint2 *items;           // {touched index, chunk}
     uint32_t *it_mask;      // 16 words per item: survivor bits by slot
@@ -86,6 +89,24 @@ struct GraphView {
 };
 
 enum Mode : int { MODE_INSERT = 0, MODE_DELETE = 1, MODE_QUERY = 2, MODE_VDEL = 3 };
+
+// A source's batch destinations are kept as a plain list up to LIST_MAX
+// entries (tested through a shared-memory hash set built per work item) and
+// as an open-addressing hash set in the arena above it.
+constexpr uint32_t LIST_MAX = 256;
+// Tiny adjacencies (one thread per source): at most TINY_DEG entries in at
+// most two blocks, at most TINY_M batch entries.
+constexpr uint32_t TINY_DEG = 32;
+constexpr uint32_t TINY_M = 16;
+
+// Arena words of a source with m batch entries: m (list) or the hash set
+// size, the power of two at or above 2m.
+__host__ __device__ __forceinline__ uint32_t member_words(uint32_t m) {
+    if (m <= LIST_MAX) return m;
+    uint32_t h = 2 * LIST_MAX;
+    while (h < 2 * m) h <<= 1;
+    return h;
+}
 
 // ------------------------------------------------------------------ helpers
 

@@ -152,11 +152,12 @@ __device__ __forceinline__ void load_tile(const GraphView &g, const uint32_t *__
     okmask &= inmask;
 }
 
-// Counting pass.  SPARSE: the tile that finds a source's count at zero lists
-// it as touched (atomics with return).  DENSE (large batches): counts use
-// atomics without return and the touched list is built afterwards by a
-// compaction over all vertices (k_touched_scan).
-template <int MODE, bool DENSE>
+// Counting pass.  Each (tile, source) adds its count with one atomic whose
+// return value is the tile's base rank for that source; every valid pair
+// records base + its rank inside the tile (prank, NIL for a rejected pair),
+// so the later passes need neither aggregation nor atomics to place it.
+// The tile that finds a source's count at zero lists the source as touched.
+template <int MODE>
 __global__ void __launch_bounds__(AGG_THREADS) k_count(GraphView g, const uint32_t *__restrict__ src,
                                                        const uint32_t *__restrict__ dst,
                                                        unsigned long long n) {
@@ -170,92 +171,64 @@ __global__ void __launch_bounds__(AGG_THREADS) k_count(GraphView g, const uint32
             keys[i] = EMPTY_KEY;
             cnt[i] = 0;
         }
+        const unsigned long long base = tile * AGG_TILE;
         uint32_t us[AGG_EPT], vs[AGG_EPT], okmask, inmask;
-        load_tile(g, src, dst, n, tile * AGG_TILE, us, vs, okmask, inmask);
+        load_tile(g, src, dst, n, base, us, vs, okmask, inmask);
         rej += __popc(inmask & ~okmask);
         __syncthreads();
+        uint32_t sr[AGG_EPT];  // slot (12 bits) | rank in tile (11 bits) << 12
 #pragma unroll
         for (int e = 0; e < AGG_EPT; ++e) {
+            sr[e] = NIL;
             if ((okmask >> e) & 1u) {
                 uint32_t r;
-                agg_insert(keys, cnt, us[e], r);
+                const uint32_t sl = agg_insert(keys, cnt, us[e], r);
+                sr[e] = sl | (r << 12);
             }
         }
         __syncthreads();
-        if (DENSE) {
+        // one atomic per (tile, source), 8 in flight per thread; the old
+        // count becomes the tile's base rank
+        uint32_t fresh = 0;
 #pragma unroll
-            for (int i = 0; i < AGG_SPT; ++i) {
-                const int s = threadIdx.x + i * AGG_THREADS;
+        for (int h0 = 0; h0 < AGG_SPT; h0 += AGG_SPT / 2) {
+            uint32_t old[AGG_SPT / 2];
+#pragma unroll
+            for (int i = 0; i < AGG_SPT / 2; ++i) {
+                const int s = threadIdx.x + (h0 + i) * AGG_THREADS;
                 const uint32_t u = keys[s];
-                if (u != EMPTY_KEY) atomicAdd(&g.vcnt[u], cnt[s]);
+                old[i] = u != EMPTY_KEY ? atomicAdd(&g.vcnt[u], cnt[s]) : 1u;
             }
-        } else {
-            // One atomic per (tile, source), all issued back to back; the tile
-            // that finds a zero count lists the source as touched, and the
-            // tile's new entries take one atomic on the list length.
-            uint32_t fresh = 0;
 #pragma unroll
-            for (int h0 = 0; h0 < AGG_SPT; h0 += AGG_SPT / 2) {
-                uint32_t old[AGG_SPT / 2];
-#pragma unroll
-                for (int i = 0; i < AGG_SPT / 2; ++i) {
-                    const int s = threadIdx.x + (h0 + i) * AGG_THREADS;
-                    const uint32_t u = keys[s];
-                    old[i] = u != EMPTY_KEY ? atomicAdd(&g.vcnt[u], cnt[s]) : 1u;
-                }
-#pragma unroll
-                for (int i = 0; i < AGG_SPT / 2; ++i)
-                    if (old[i] == 0u) fresh |= 1u << (h0 + i);
+            for (int i = 0; i < AGG_SPT / 2; ++i) {
+                const int s = threadIdx.x + (h0 + i) * AGG_THREADS;
+                if (keys[s] != EMPTY_KEY) cnt[s] = old[i];
+                if (old[i] == 0u) fresh |= 1u << (h0 + i);
             }
-            uint32_t ntot;
-            const uint32_t ex = block_excl_scan(__popc(fresh), &ntot);
-            if (threadIdx.x == 0) s_tbase = ntot ? atomicAdd(&g.dev->n_touched, ntot) : 0u;
-            __syncthreads();
-            uint32_t t = s_tbase + ex;
-            while (fresh) {
-                const int i = __ffs(fresh) - 1;
-                fresh &= fresh - 1u;
-                const uint32_t u = keys[threadIdx.x + i * AGG_THREADS];
-                g.t_vid[t] = u;
-                g.vtid[u] = t;
-                ++t;
-            }
+        }
+        uint32_t ntot;
+        const uint32_t ex = block_excl_scan(__popc(fresh), &ntot);
+        if (threadIdx.x == 0) s_tbase = ntot ? atomicAdd(&g.dev->n_touched, ntot) : 0u;
+        __syncthreads();
+        uint32_t t = s_tbase + ex;
+        while (fresh) {
+            const int i = __ffs(fresh) - 1;
+            fresh &= fresh - 1u;
+            const uint32_t u = keys[threadIdx.x + i * AGG_THREADS];
+            g.t_vid[t] = u;
+            g.vtid[u] = t;
+            ++t;
+        }
+#pragma unroll
+        for (int e = 0; e < AGG_EPT; ++e) {
+            const unsigned long long i = base + (unsigned long long)e * AGG_THREADS + threadIdx.x;
+            if (i < n) g.prank[i] = sr[e] == NIL ? NIL : cnt[sr[e] & 0xFFFu] + (sr[e] >> 12);
         }
         __syncthreads();
     }
     if (MODE != MODE_QUERY) {
         const unsigned long long r = warp_sum_u64(rej);
         if (lane_id() == 0 && r) atomicAdd(&g.dev->call_b, r);
-    }
-}
-
-// Touched list of a DENSE count: every vertex with a non-zero count, in
-// vertex order (one atomic per CTA chunk).
-__global__ void __launch_bounds__(256) k_touched_scan(GraphView g) {
-    const uint32_t nv = g.nv;
-    __shared__ uint32_t s_base;
-    for (uint32_t base = blockIdx.x * blockDim.x * 4; base < nv; base += gridDim.x * blockDim.x * 4) {
-        uint32_t flags = 0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const uint32_t u = base + threadIdx.x * 4 + j;
-            if (u < nv && g.vcnt[u]) flags |= 1u << j;
-        }
-        uint32_t tot;
-        const uint32_t ex = block_excl_scan(__popc(flags), &tot);
-        if (threadIdx.x == 0) s_base = tot ? atomicAdd(&g.dev->n_touched, tot) : 0u;
-        __syncthreads();
-        uint32_t t = s_base + ex;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if ((flags >> j) & 1u) {
-                const uint32_t u = base + threadIdx.x * 4 + j;
-                g.t_vid[t] = u;
-                g.vtid[u] = t;
-                ++t;
-            }
-        }
-        __syncthreads();
     }
 }
 
@@ -295,6 +268,7 @@ __global__ void __launch_bounds__(256) k_plan_insert(GraphView g) {
         const unsigned long long off = s_base + ex;
         if (t < nt) {
             g.t_a[t] = make_uint4(deg, last, (uint32_t)off, need);
+            g.vcur[g.t_vid[t]] = (uint32_t)off;
             for (uint32_t j = 0; j < need; ++j) g.t_owner[off + j] = t;
         }
         __syncthreads();
@@ -347,104 +321,66 @@ __global__ void __launch_bounds__(256) k_link_insert(GraphView g) {
     }
 }
 
-__global__ void __launch_bounds__(AGG_THREADS, 3) k_scatter_insert(GraphView g,
-                                                                const uint32_t *__restrict__ src,
-                                                                const uint32_t *__restrict__ dst,
-                                                                unsigned long long n) {
+// Pairs per thread per iteration of the streaming per-pair kernels.
+constexpr int PP = 4;
+
+// Insert scatter: one pass over the pairs, no aggregation and no atomics.
+// Pair i of source u with rank r goes to slot deg(u) + r: the free slots of
+// the last block first, then the new blocks popped for u at queue offset
+// vcur[u] (set by the plan).  Sentinels still hold the pre-call state.
+__global__ void __launch_bounds__(256) k_scatter_insert(GraphView g, const uint32_t *__restrict__ src,
+                                                        const uint32_t *__restrict__ dst,
+                                                        unsigned long long n) {
     if (g.dev->abort) return;
-    __shared__ uint32_t keys[AGG_H];
-    __shared__ uint32_t cnt[AGG_H];
-    __shared__ uint32_t tid[AGG_H];
     const unsigned long long P = g.P;
     const unsigned long long qbase = qmod(g.dev->q_front, P);
     const uint32_t C = g.C;
-    const unsigned long long ntiles = (n + AGG_TILE - 1) / AGG_TILE;
-    for (unsigned long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        for (int i = threadIdx.x; i < AGG_H; i += AGG_THREADS) {
-            keys[i] = EMPTY_KEY;
-            cnt[i] = 0;
-        }
-        uint32_t us[AGG_EPT], vs[AGG_EPT], okmask, inmask;
-        load_tile(g, src, dst, n, tile * AGG_TILE, us, vs, okmask, inmask);
-        __syncthreads();
-        // slot (12 bits) and in-tile rank (11 bits) of each pair, packed
-        uint32_t sr[AGG_EPT];
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i0 < n;
+         i0 += stride * PP) {
+        uint32_t r[PP], u[PP], v[PP];
 #pragma unroll
-        for (int e = 0; e < AGG_EPT; ++e) {
-            sr[e] = NIL;
-            if ((okmask >> e) & 1u) {
-                uint32_t r;
-                const uint32_t sl = agg_insert(keys, cnt, us[e], r);
-                sr[e] = sl | (r << 12);
+        for (int j = 0; j < PP; ++j) {
+            const unsigned long long i = i0 + j * stride;
+            r[j] = i < n ? g.prank[i] : NIL;
+            u[j] = i < n ? __ldg(src + i) : 0u;
+            v[j] = i < n ? __ldg(dst + i) : 0u;
+        }
+        uint4 sn[PP];
+        uint32_t off[PP];
+#pragma unroll
+        for (int j = 0; j < PP; ++j) {
+            if (r[j] != NIL) {
+                sn[j] = g.sent[u[j]];
+                off[j] = g.vcur[u[j]];
             }
         }
-        __syncthreads();
-        {
-            // rank cursors: independent atomics, issued back to back
-            // two halves of AGG_SPT / 2 slots: 8 atomics in flight per thread
+        uint32_t blk[PP], ln[PP];
 #pragma unroll
-            for (int h0 = 0; h0 < AGG_SPT; h0 += AGG_SPT / 2) {
-                uint32_t bs[AGG_SPT / 2], ts[AGG_SPT / 2];
-#pragma unroll
-                for (int i = 0; i < AGG_SPT / 2; ++i) {
-                    const int s = threadIdx.x + (h0 + i) * AGG_THREADS;
-                    const uint32_t u = keys[s];
-                    if (u != EMPTY_KEY) {
-                        bs[i] = atomicAdd(&g.vcur[u], cnt[s]);
-                        ts[i] = g.vtid[u];
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < AGG_SPT / 2; ++i) {
-                    const int s = threadIdx.x + (h0 + i) * AGG_THREADS;
-                    if (keys[s] != EMPTY_KEY) {
-                        cnt[s] = bs[i];
-                        tid[s] = ts[i];
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        // per pair: rank r, source info, then the queue slot of a new block,
-        // then the store -- each stage's loads issued for all pairs first
-        uint4 a[AGG_EPT];
-#pragma unroll
-        for (int e = 0; e < AGG_EPT; ++e) {
-            if (sr[e] != NIL) {
-                const uint32_t sl = sr[e] & 0xFFFu;
-                a[e] = g.t_a[tid[sl]];
-                a[e].w = cnt[sl] + (sr[e] >> 12);  // w: rank within the source's batch
-            }
-        }
-        uint32_t blk[AGG_EPT], lane[AGG_EPT];
-#pragma unroll
-        for (int e = 0; e < AGG_EPT; ++e) {
-            blk[e] = NIL;
-            lane[e] = 0;
-            if (sr[e] != NIL) {
-                const uint32_t r = a[e].w;
-                const uint32_t deg = a[e].x, off = a[e].z;
-                const uint32_t nb = (deg + C - 1) / C;
+        for (int j = 0; j < PP; ++j) {
+            blk[j] = NIL;
+            ln[j] = 0;
+            if (r[j] != NIL) {
+                const uint32_t deg = sn[j].x, nb = sn[j].y;
                 const uint32_t space = nb * C - deg;
-                if (r < space) {
-                    blk[e] = a[e].y;
-                    lane[e] = deg - (nb - 1) * C + r;
+                if (r[j] < space) {
+                    blk[j] = sn[j].w;
+                    ln[j] = deg - (nb - 1) * C + r[j];
                 } else {
-                    const uint32_t q = r - space;
+                    const uint32_t q = r[j] - space;
                     const uint32_t jb = q / C;
-                    lane[e] = q - jb * C;
-                    blk[e] = g.queue[ring(qbase, off + jb, P)];
+                    ln[j] = q - jb * C;
+                    blk[j] = g.queue[ring(qbase, off[j] + jb, P)];
                 }
             }
         }
 #pragma unroll
-        for (int e = 0; e < AGG_EPT; ++e) {
-            if (sr[e] != NIL) {
-                if (blk[e] < P) g.data[(size_t)blk[e] * C + lane[e]] = vs[e];
+        for (int j = 0; j < PP; ++j) {
+            if (r[j] != NIL) {
+                if (blk[j] < P) g.data[(size_t)blk[j] * C + ln[j]] = v[j];
                 else latch_status(g.dev, 5u /* GV_ERR_STATE */);
             }
         }
-        __syncthreads();
     }
 }
 
@@ -495,6 +431,7 @@ __global__ void __launch_bounds__(256) k_finalize_insert(GraphView g, unsigned l
         dev->call_a = dev->call_b = dev->call_c = 0;
         dev->n_touched = 0;
         dev->n_items = 0;
+        dev->n_tiny = 0;
         dev->arena_used = 0;
         dev->free_total = 0;
         dev->abort = 0;
@@ -511,41 +448,47 @@ __device__ __forceinline__ void emit_items(const GraphView &g, uint32_t t, uint3
     for (uint32_t c = 0; c < ni; ++c) g.items[item0 + c] = make_uint2(t, c);
 }
 
+// Per touched source: arena words for its batch destinations (a list up to
+// LIST_MAX entries, else a hash set), and either the tiny tier (one thread,
+// tiny adjacency and few batch entries) or work items of IB blocks.
 template <int MODE>
 __global__ void __launch_bounds__(256) k_plan_member(GraphView g) {
     const uint32_t nt = g.dev->n_touched;
     const uint32_t IB = g.IB;
+    const uint32_t tiny_deg = min(TINY_DEG, 2 * g.C);
     __shared__ unsigned long long s_aw;
-    __shared__ uint32_t s_ai;
+    __shared__ uint32_t s_ai, s_at;
     for (uint32_t base = blockIdx.x * blockDim.x; base < nt; base += gridDim.x * blockDim.x) {
         const uint32_t t = base + threadIdx.x;
-        uint32_t m = 0, words = 0, hs = 0, ni = 0;
+        uint32_t m = 0, words = 0, ni = 0, tiny = 0;
         uint4 s = make_uint4(0, 0, NIL, NIL);
         if (t < nt) {
             const uint32_t u = g.t_vid[t];
             m = g.vcnt[u];
             s = g.sent[u];
-            if (m <= 32) {
-                words = m;
-            } else {
-                hs = 64;
-                while (hs < 2 * m) hs <<= 1;
-                words = hs;
+            words = member_words(m);
+            if (s.y > 0) {
+                if (s.x <= tiny_deg && m <= TINY_M) tiny = 1;
+                else ni = (s.y + IB - 1) / IB;
             }
-            ni = (s.y + IB - 1) / IB;
         }
-        uint32_t wt, itot;
+        uint32_t wt, itot, ttot;
         const uint32_t wex = block_excl_scan(words, &wt);
         const uint32_t iex = block_excl_scan(ni, &itot);
+        const uint32_t tex = block_excl_scan(tiny, &ttot);
         if (threadIdx.x == 0) {
             s_aw = wt ? atomicAdd(&g.dev->arena_used, (unsigned long long)wt) : 0ull;
             s_ai = itot ? atomicAdd(&g.dev->n_items, itot) : 0u;
+            s_at = ttot ? atomicAdd(&g.dev->n_tiny, ttot) : 0u;
         }
         __syncthreads();
         if (t < nt) {
             const uint32_t item0 = s_ai + iex;
-            g.t_a[t] = make_uint4(m, (uint32_t)(s_aw + wex), hs, item0);
+            const uint32_t aoff = (uint32_t)(s_aw + wex);
+            g.t_a[t] = make_uint4(m, aoff, m <= LIST_MAX ? 0u : words, item0);
             g.t_b[t] = make_uint4(s.x, s.y, s.z, ni);
+            g.vcur[g.t_vid[t]] = aoff;
+            if (tiny) g.t_tiny[s_at + tex] = t;
             emit_items(g, t, item0, ni);
         }
         __syncthreads();
@@ -562,108 +505,68 @@ __global__ void __launch_bounds__(256) k_arena_init(GraphView g) {
     }
 }
 
+// Batch destinations into their source's list (plain store at the pair's
+// rank) or hash set (a CAS at the home slot, probing on collision); queries
+// record where their pair landed.  One pass over the pairs, no aggregation.
 template <int MODE>
-__global__ void __launch_bounds__(AGG_THREADS, 3) k_scatter_member(GraphView g,
-                                                                const uint32_t *__restrict__ src,
-                                                                const uint32_t *__restrict__ dst,
-                                                                unsigned long long n) {
-    __shared__ uint32_t keys[AGG_H];
-    __shared__ uint32_t cnt[AGG_H];
-    __shared__ uint32_t tid[AGG_H];
-    const unsigned long long ntiles = (n + AGG_TILE - 1) / AGG_TILE;
-    for (unsigned long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        for (int i = threadIdx.x; i < AGG_H; i += AGG_THREADS) {
-            keys[i] = EMPTY_KEY;
-            cnt[i] = 0;
-        }
-        const unsigned long long base = tile * AGG_TILE;
-        uint32_t us[AGG_EPT], vs[AGG_EPT], okmask, inmask;
-        load_tile(g, src, dst, n, base, us, vs, okmask, inmask);
-        __syncthreads();
-        uint32_t sr[AGG_EPT];
+__global__ void __launch_bounds__(256) k_scatter_member(GraphView g, const uint32_t *__restrict__ src,
+                                                        const uint32_t *__restrict__ dst,
+                                                        unsigned long long n) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i0 < n;
+         i0 += stride * PP) {
+        uint32_t r[PP], u[PP], v[PP];
 #pragma unroll
-        for (int e = 0; e < AGG_EPT; ++e) {
-            sr[e] = NIL;
-            if ((okmask >> e) & 1u) {
-                uint32_t r;
-                const uint32_t sl = agg_insert(keys, cnt, us[e], r);
-                sr[e] = sl | (r << 12);
+        for (int j = 0; j < PP; ++j) {
+            const unsigned long long i = i0 + j * stride;
+            r[j] = i < n ? g.prank[i] : NIL;
+            u[j] = i < n ? __ldg(src + i) : 0u;
+            v[j] = i < n ? __ldg(dst + i) : 0u;
+        }
+        uint32_t m[PP], aoff[PP];
+#pragma unroll
+        for (int j = 0; j < PP; ++j) {
+            if (r[j] != NIL) {
+                m[j] = g.vcnt[u[j]];
+                aoff[j] = g.vcur[u[j]];
             }
         }
-        __syncthreads();
-        {
-            // two halves of AGG_SPT / 2 slots: 8 atomics in flight per thread
+        uint32_t pos[PP], old[PP];
 #pragma unroll
-            for (int h0 = 0; h0 < AGG_SPT; h0 += AGG_SPT / 2) {
-                uint32_t bs[AGG_SPT / 2], ts[AGG_SPT / 2];
-#pragma unroll
-                for (int i = 0; i < AGG_SPT / 2; ++i) {
-                    const int s = threadIdx.x + (h0 + i) * AGG_THREADS;
-                    const uint32_t u = keys[s];
-                    if (u != EMPTY_KEY) {
-                        bs[i] = atomicAdd(&g.vcur[u], cnt[s]);
-                        ts[i] = g.vtid[u];
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < AGG_SPT / 2; ++i) {
-                    const int s = threadIdx.x + (h0 + i) * AGG_THREADS;
-                    if (keys[s] != EMPTY_KEY) {
-                        cnt[s] = bs[i];
-                        tid[s] = ts[i];
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        // list entries: plain stores; hash entries: a first CAS at the home
-        // slot for every pair, issued back to back, then probing for the
-        // (rare) collisions
-        uint32_t aoff[AGG_EPT], hs[AGG_EPT], pos[AGG_EPT];
-#pragma unroll
-        for (int e = 0; e < AGG_EPT; ++e) {
-            if (sr[e] != NIL) {
-                const uint4 a = g.t_a[tid[sr[e] & 0xFFFu]];
-                aoff[e] = a.y;
-                hs[e] = a.z;
-            }
-        }
-        uint32_t old[AGG_EPT];
-#pragma unroll
-        for (int e = 0; e < AGG_EPT; ++e) {
-            pos[e] = NIL;
-            old[e] = EMPTY_KEY;
-            if (sr[e] != NIL) {
-                if (hs[e] == 0) {
-                    pos[e] = aoff[e] + cnt[sr[e] & 0xFFFu] + (sr[e] >> 12);
-                    g.arena[pos[e]] = vs[e];
+        for (int j = 0; j < PP; ++j) {
+            pos[j] = NIL;
+            old[j] = EMPTY_KEY;
+            if (r[j] != NIL) {
+                if (m[j] <= LIST_MAX) {
+                    pos[j] = aoff[j] + r[j];
+                    g.arena[pos[j]] = v[j];
                 } else {
-                    pos[e] = aoff[e] + (mix32(vs[e]) & (hs[e] - 1));
-                    old[e] = atomicCAS(&g.arena[pos[e]], EMPTY_KEY, vs[e]);
+                    pos[j] = aoff[j] + (mix32(v[j]) & (member_words(m[j]) - 1));
+                    old[j] = atomicCAS(&g.arena[pos[j]], EMPTY_KEY, v[j]);
                 }
             }
         }
 #pragma unroll
-        for (int e = 0; e < AGG_EPT; ++e) {
-            if (sr[e] != NIL && hs[e] != 0 && old[e] != EMPTY_KEY && old[e] != vs[e]) {
-                uint32_t *tab = g.arena + aoff[e];
-                uint32_t h = (pos[e] - aoff[e] + 1) & (hs[e] - 1);
-                for (uint32_t probe = 1; probe < hs[e]; ++probe) {
-                    const uint32_t o = atomicCAS(&tab[h], EMPTY_KEY, vs[e]);
-                    if (o == EMPTY_KEY || o == vs[e]) break;
-                    h = (h + 1) & (hs[e] - 1);
+        for (int j = 0; j < PP; ++j) {
+            if (r[j] != NIL && m[j] > LIST_MAX && old[j] != EMPTY_KEY && old[j] != v[j]) {
+                const uint32_t hs = member_words(m[j]);
+                uint32_t *tab = g.arena + aoff[j];
+                uint32_t h = (pos[j] - aoff[j] + 1) & (hs - 1);
+                for (uint32_t probe = 1; probe < hs; ++probe) {
+                    const uint32_t o = atomicCAS(&tab[h], EMPTY_KEY, v[j]);
+                    if (o == EMPTY_KEY || o == v[j]) break;
+                    h = (h + 1) & (hs - 1);
                 }
-                pos[e] = aoff[e] + h;
+                pos[j] = aoff[j] + h;
             }
         }
         if (MODE == MODE_QUERY) {
 #pragma unroll
-            for (int e = 0; e < AGG_EPT; ++e) {
-                const unsigned long long i = base + (unsigned long long)e * AGG_THREADS + threadIdx.x;
-                if (i < n) g.qpos[i] = pos[e];
+            for (int j = 0; j < PP; ++j) {
+                const unsigned long long i = i0 + j * stride;
+                if (i < n) g.qpos[i] = pos[j];
             }
         }
-        __syncthreads();
     }
 }
 
@@ -680,8 +583,8 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
     const unsigned long long qbb = qmod(dev->q_back, P);
     __shared__ uint32_t s_free[8][64];
     __shared__ uint32_t s_bid[8][32];
-    __shared__ uint32_t s_hkey[8][64];
-    __shared__ uint32_t s_hfound[8][64];
+    __shared__ uint32_t s_hkey[8][2 * LIST_MAX];
+    __shared__ uint32_t s_hfound[8][(MODE == MODE_QUERY) ? 2 * LIST_MAX : 1];
     FreeStage fs{s_free[threadIdx.x >> 5], 0u};
     unsigned long long removed = 0;  // entries deleted by this warp (lane 0)
     for (uint32_t it = warp; it < nitems; it += nwarps) {
@@ -703,31 +606,29 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
         // that lanes can look up any block without a shuffle.
         uint32_t *sb_ids = s_bid[threadIdx.x >> 5];
         sb_ids[lane] = bid;
-        // Batch list of this source (<= 32 entries): a 64-slot shared hash
-        // set per warp; slot_of_mine = slot of list entry `lane`.
+        // Batch list of this source (<= LIST_MAX entries): a shared hash set
+        // of hmask + 1 slots (a power of two >= 2m, at least 64) per warp.
         bool listmode = false;
-        uint32_t slot_of_mine = NIL;
+        uint32_t hmask = 63;
         uint32_t *hk = s_hkey[threadIdx.x >> 5];
         uint32_t *hf = s_hfound[threadIdx.x >> 5];
         if (MODE == MODE_DELETE || MODE == MODE_QUERY) {
             listmode = (a.z == 0);
             if (listmode) {
-                hk[lane] = EMPTY_KEY;
-                hk[lane + 32] = EMPTY_KEY;
-                if (MODE == MODE_QUERY) {
-                    hf[lane] = 0u;
-                    hf[lane + 32] = 0u;
+                while (hmask + 1 < 2 * a.x) hmask = 2 * hmask + 1;
+                for (uint32_t j = lane; j <= hmask; j += 32) {
+                    hk[j] = EMPTY_KEY;
+                    if (MODE == MODE_QUERY) hf[j] = 0u;
                 }
                 __syncwarp();
-                if (lane < a.x) {
-                    const uint32_t v = g.arena[a.y + lane];
-                    uint32_t h = mix32(v) & 63u;
+                for (uint32_t j = lane; j < a.x; j += 32) {
+                    const uint32_t v = g.arena[a.y + j];
+                    uint32_t h = mix32(v) & hmask;
                     for (;;) {
                         const uint32_t old = atomicCAS(&hk[h], EMPTY_KEY, v);
                         if (old == EMPTY_KEY || old == v) break;
-                        h = (h + 1) & 63u;
+                        h = (h + 1) & hmask;
                     }
-                    slot_of_mine = h;
                 }
             }
         }
@@ -754,7 +655,7 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
                     if (MODE == MODE_VDEL) {
                         hit = (g.dead[e[j] >> 5] >> (e[j] & 31u)) & 1u;
                     } else if (listmode) {
-                        uint32_t h = mix32(e[j]) & 63u;
+                        uint32_t h = mix32(e[j]) & hmask;
                         for (;;) {
                             const uint32_t k = hk[h];
                             if (k == e[j]) {
@@ -763,7 +664,7 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
                                 break;
                             }
                             if (k == EMPTY_KEY) break;
-                            h = (h + 1) & 63u;
+                            h = (h + 1) & hmask;
                         }
                     } else {
                         const uint32_t h = hash_find(g.arena + a.y, a.z, e[j]);
@@ -801,8 +702,15 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
         }
         if (MODE == MODE_QUERY) {
             __syncwarp();
-            // every list entry (repeated queries included) reads its slot's flag
-            if (listmode && slot_of_mine != NIL && hf[slot_of_mine]) g.found[a.y + lane] = 1u;
+            // every list entry (repeated queries included) reads its key's flag
+            if (listmode) {
+                for (uint32_t j = lane; j < a.x; j += 32) {
+                    const uint32_t v = g.arena[a.y + j];
+                    uint32_t h = mix32(v) & hmask;
+                    while (hk[h] != v) h = (h + 1) & hmask;
+                    if (hf[h]) g.found[a.y + j] = 1u;
+                }
+            }
             __syncwarp();
             continue;
         }
@@ -830,6 +738,99 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
     if (MODE != MODE_QUERY) {
         fs.flush(fs.n, dev, g.queue, qbb, P);
         if (lane == 0 && removed) atomicAdd(&dev->call_a, removed);
+    }
+}
+
+// Tiny adjacencies, one thread per source: at most two blocks and
+// min(TINY_DEG, 2C) entries, at most TINY_M batch entries (held in
+// registers).  Delete / vertex delete compact in place (stable) and return
+// emptied blocks; query sets the hit flag of every matching batch entry.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
+    Dev *dev = g.dev;
+    const uint32_t ntiny = dev->n_tiny;
+    const uint32_t C = g.C;
+    const unsigned long long P = g.P;
+    const unsigned long long qbb = qmod(dev->q_back, P);
+    __shared__ uint32_t s_free[8][64];
+    FreeStage fs{s_free[threadIdx.x >> 5], 0u};
+    unsigned long long removed = 0;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    // the loop bound is uniform per warp: the queue staging needs all lanes
+    for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < ntiny; base += stride) {
+        const uint32_t k = base + lane_id();
+        bool act = k < ntiny;
+        uint32_t t = 0, deg = 0, nb = 0, root = NIL, m = 0, aoff = 0;
+        if (act) {
+            t = g.t_tiny[k];
+            const uint4 a = g.t_a[t];
+            const uint4 b = g.t_b[t];
+            deg = b.x;
+            nb = b.y;
+            root = b.z;
+            m = a.x;
+            aoff = a.y;
+        }
+        uint32_t b0 = root, b1 = NIL;
+        if (act && root < P && nb == 2) b1 = g.links[2ull * root];
+        if (act && (b0 >= P || (nb == 2 && b1 >= P))) {
+            latch_status(dev, 5u /* GV_ERR_STATE */);
+            act = false;
+        }
+        uint32_t d[TINY_M];
+#pragma unroll
+        for (int j = 0; j < (int)TINY_M; ++j)
+            d[j] = (MODE != MODE_VDEL && act && (uint32_t)j < m) ? g.arena[aoff + j] : EMPTY_KEY;
+        uint32_t qhit = 0;
+        uint32_t w = 0;
+        for (uint32_t x = 0; act && x < deg; x += 4) {
+            const uint32_t blk = x < C ? b0 : b1;
+            const uint32_t off = x < C ? x : x - C;
+            const uint4 e4 = *reinterpret_cast<const uint4 *>(g.data + (size_t)blk * C + off);
+            const uint32_t e[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                if (x + jj < deg) {
+                    bool hit;
+                    if (MODE == MODE_VDEL) {
+                        hit = (g.dead[e[jj] >> 5] >> (e[jj] & 31u)) & 1u;
+                    } else {
+                        uint32_t hm = 0;
+#pragma unroll
+                        for (int j = 0; j < (int)TINY_M; ++j) hm |= (uint32_t)(d[j] == e[jj]) << j;
+                        hit = hm != 0;
+                        if (MODE == MODE_QUERY) qhit |= hm;
+                    }
+                    if (MODE != MODE_QUERY && !hit) {
+                        if (w != x + jj) {
+                            const uint32_t tb = w < C ? b0 : b1;
+                            g.data[(size_t)tb * C + (w < C ? w : w - C)] = e[jj];
+                        }
+                        ++w;
+                    }
+                }
+            }
+        }
+        if (MODE == MODE_QUERY) {
+            if (act)
+                for (uint32_t j = 0; j < m; ++j)
+                    if ((qhit >> j) & 1u) g.found[aoff + j] = 1u;
+            continue;
+        }
+        const bool changed = act && w != deg;
+        const uint32_t nbn = (w + C - 1) / C;
+        fs.push(changed && nb == 2 && nbn < 2, b1, dev, g.queue, qbb, P);
+        fs.push(changed && nbn == 0, b0, dev, g.queue, qbb, P);
+        if (changed) {
+            if (nb == 2 && nbn == 1) g.links[2ull * b0] = NIL;  // heap 2 hangs left of heap 1
+            g.sent[g.t_vid[t]] = make_uint4(w, nbn, nbn ? root : NIL, nbn == 2 ? b1 : (nbn == 1 ? b0 : NIL));
+            removed += deg - w;
+        }
+    }
+    if (MODE != MODE_QUERY) {
+        fs.flush(fs.n, dev, g.queue, qbb, P);
+        removed = warp_sum_u64(removed);
+        if (lane_id() == 0 && removed) atomicAdd(&dev->call_a, removed);
     }
 }
 
@@ -1030,6 +1031,7 @@ __global__ void __launch_bounds__(256) k_finalize_member(GraphView g, unsigned l
         dev->call_a = dev->call_b = dev->call_c = 0;
         dev->n_touched = 0;
         dev->n_items = 0;
+        dev->n_tiny = 0;
         dev->arena_used = 0;
         dev->free_total = 0;
         dev->abort = 0;
@@ -1124,6 +1126,7 @@ __global__ void k_reset_lists(GraphView g) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         g.dev->n_touched = 0;
         g.dev->n_items = 0;
+        g.dev->n_tiny = 0;
     }
 }
 
@@ -1132,24 +1135,28 @@ __global__ void k_reset_lists(GraphView g) {
 __global__ void __launch_bounds__(256) k_plan_vdel_in(GraphView g) {
     const uint32_t nv = g.nv;
     const uint32_t IB = g.IB;
-    __shared__ uint32_t s_at, s_ai;
+    const uint32_t tiny_deg = min(TINY_DEG, 2 * g.C);
+    __shared__ uint32_t s_at, s_ai, s_an;
     for (uint32_t base = blockIdx.x * blockDim.x; base < nv; base += gridDim.x * blockDim.x) {
         const uint32_t u = base + threadIdx.x;
-        uint32_t take = 0, ni = 0;
+        uint32_t take = 0, ni = 0, tiny = 0;
         uint4 s = make_uint4(0, 0, NIL, NIL);
         if (u < nv && g.alive[u]) {
             s = g.sent[u];
             if (s.x) {
                 take = 1;
-                ni = (s.y + IB - 1) / IB;
+                if (s.x <= tiny_deg && s.y <= 2) tiny = 1;
+                else ni = (s.y + IB - 1) / IB;
             }
         }
-        uint32_t ttot, itot;
+        uint32_t ttot, itot, ntot;
         const uint32_t tex = block_excl_scan(take, &ttot);
         const uint32_t iex = block_excl_scan(ni, &itot);
+        const uint32_t nex = block_excl_scan(tiny, &ntot);
         if (threadIdx.x == 0) {
             s_at = ttot ? atomicAdd(&g.dev->n_touched, ttot) : 0u;
             s_ai = itot ? atomicAdd(&g.dev->n_items, itot) : 0u;
+            s_an = ntot ? atomicAdd(&g.dev->n_tiny, ntot) : 0u;
         }
         __syncthreads();
         if (take) {
@@ -1158,6 +1165,7 @@ __global__ void __launch_bounds__(256) k_plan_vdel_in(GraphView g) {
             g.t_vid[t] = u;
             g.t_b[t] = make_uint4(s.x, s.y, s.z, ni);
             g.t_a[t] = make_uint4(0, 0, 0, item0);
+            if (tiny) g.t_tiny[s_an + nex] = t;
             emit_items(g, t, item0, ni);
         }
         __syncthreads();
@@ -1180,6 +1188,7 @@ __global__ void __launch_bounds__(256) k_finalize_vdel(GraphView g, const uint32
         dev->call_a = dev->call_b = dev->call_c = 0;
         dev->n_touched = 0;
         dev->n_items = 0;
+        dev->n_tiny = 0;
         dev->arena_used = 0;
         dev->free_total = 0;
         dev->abort = 0;
@@ -1203,22 +1212,10 @@ cudaError_t launch_count(int mode, const GraphView &g, const uint32_t *src, cons
     const int grid = grid_for(n, AGG_TILE, lc.num_sms * 8);
     const int ph = mode == MODE_INSERT ? PH_INS_COUNT : mode == MODE_DELETE ? PH_DEL_COUNT : PH_QRY_COUNT;
     PhaseScope ps(lc, ph);
-    // Large batches touch a large share of the vertices: count without
-    // return values and list the touched vertices by one pass over all of them.
-    const bool dense = n >= (unsigned long long)g.nv / 8;
-    if (dense) {
-        switch (mode) {
-        case MODE_INSERT: k_count<MODE_INSERT, true><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
-        case MODE_DELETE: k_count<MODE_DELETE, true><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
-        default: k_count<MODE_QUERY, true><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
-        }
-        k_touched_scan<<<grid_for(g.nv, 1024, lc.num_sms * 8), 256, 0, lc.stream>>>(g);
-    } else {
-        switch (mode) {
-        case MODE_INSERT: k_count<MODE_INSERT, false><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
-        case MODE_DELETE: k_count<MODE_DELETE, false><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
-        default: k_count<MODE_QUERY, false><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
-        }
+    switch (mode) {
+    case MODE_INSERT: k_count<MODE_INSERT><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
+    case MODE_DELETE: k_count<MODE_DELETE><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
+    default: k_count<MODE_QUERY><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
     }
     return cudaGetLastError();
 }
@@ -1246,7 +1243,7 @@ cudaError_t launch_insert_tail(const GraphView &g, const uint32_t *src, const ui
     }
     {
         PhaseScope ps(lc, PH_INS_SCATTER);
-        k_scatter_insert<<<grid_for(n, AGG_TILE, cap), AGG_THREADS, 0, lc.stream>>>(g, src, dst, n);
+        k_scatter_insert<<<grid_for(n, 256 * PP, cap), 256, 0, lc.stream>>>(g, src, dst, n);
     }
     {
         PhaseScope ps(lc, PH_INS_FINALIZE);
@@ -1273,11 +1270,12 @@ static void member_tail(const GraphView &g, const uint32_t *src, const uint32_t 
     }
     {
         PhaseScope ps(lc, del ? PH_DEL_SCATTER : PH_QRY_SCATTER);
-        k_scatter_member<MODE><<<grid_for(n, AGG_TILE, cap), AGG_THREADS, 0, lc.stream>>>(g, src, dst, n);
+        k_scatter_member<MODE><<<grid_for(n, 256 * PP, cap), 256, 0, lc.stream>>>(g, src, dst, n);
     }
     {
         PhaseScope ps(lc, del ? PH_DEL_MARK : PH_QRY_MARK);
         k_mark<MODE><<<gi, 256, 0, lc.stream>>>(g);
+        k_mark_tiny<MODE><<<gt, 256, 0, lc.stream>>>(g);
     }
     if (del) {
         {
@@ -1315,6 +1313,7 @@ cudaError_t launch_vertex_delete(const GraphView &g, const uint32_t *ids, uint32
     k_reset_lists<<<1, 32, 0, lc.stream>>>(g);
     k_plan_vdel_in<<<grid_for(g.nv, 256, cap), 256, 0, lc.stream>>>(g);
     k_mark<MODE_VDEL><<<gi, 256, 0, lc.stream>>>(g);
+    k_mark_tiny<MODE_VDEL><<<grid_for(g.nv, 256, cap), 256, 0, lc.stream>>>(g);
     k_vscan<MODE_VDEL><<<grid_for(g.nv, 8, cap), 256, 0, lc.stream>>>(g);
     k_move<MODE_VDEL><<<gi, 256, 0, lc.stream>>>(g);
     k_finalize_vdel<<<grid_for(k, 256, cap), 256, 0, lc.stream>>>(g, ids, k);
