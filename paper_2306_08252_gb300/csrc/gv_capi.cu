@@ -146,6 +146,7 @@ GraphView view(const gv_graph *g) {
     v.IB = g->IB;
     v.nv = g->nv;
     v.all_alive = g->any_vertex_deleted ? 0u : 1u;
+    v.vmask = g->vcap ? g->vcap - 1 : 0;
     v.vcnt = g->vcnt;
     v.vcur = g->vcur;
     v.vtid = g->vtid;

@@ -61,7 +61,8 @@ struct GraphView {
     uint32_t IB;            // blocks per work item (IB * C <= 512)
     uint32_t nv;            // vertex count
     uint32_t all_alive;     // 1 while no vertex has ever been deleted (alive[] need not be read)
-    // vertex-indexed scratch (zero between calls)
+    uint32_t vmask;         // dictionary capacity - 1 (capacity is a power of two)
+    // vertex-indexed scratch (zero between calls), indexed by vslot(u)
     uint32_t *vcnt;         // batch entries per source
     uint32_t *vcur;         // per-source offset set by the plan (queue or arena)
     uint32_t *vtid;         // touched index of a source (valid while vcnt > 0)
@@ -119,6 +120,23 @@ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
     x ^= x >> 16;
     return x;
 }
+
+// Slot of vertex u in the per-call vertex scratch arrays: a bijection of
+// [0, capacity) (multiplication by an odd constant modulo the power-of-two
+// capacity).  Power-law graphs put most updates on a few low ids; without
+// the scramble their counters share a handful of L2 slices, whose atomic
+// units (about 1.5 G operations/s each) then serialise the whole batch.
+constexpr uint32_t VSCRAMBLE = 0x9E3779B1u;
+constexpr uint32_t inverse_odd(uint32_t a) {
+    uint32_t x = a;  // Newton iteration for the inverse modulo 2^32
+    for (int i = 0; i < 5; ++i) x *= 2u - a * x;
+    return x;
+}
+constexpr uint32_t VSCRAMBLE_INV = inverse_odd(VSCRAMBLE);
+static_assert(VSCRAMBLE * VSCRAMBLE_INV == 1u, "scramble inverse");
+
+__device__ __forceinline__ uint32_t vslot(uint32_t vmask, uint32_t u) { return (u * VSCRAMBLE) & vmask; }
+__device__ __forceinline__ uint32_t vslot_inv(uint32_t vmask, uint32_t i) { return (i * VSCRAMBLE_INV) & vmask; }
 
 __device__ __forceinline__ void latch_status(Dev *dev, unsigned int code) {
     atomicCAS(&dev->status, 0u, code);

@@ -176,14 +176,14 @@ __global__ void __launch_bounds__(AGG_THREADS) k_count(GraphView g, const uint32
         load_tile(g, src, dst, n, base, us, vs, okmask, inmask);
         rej += __popc(inmask & ~okmask);
         __syncthreads();
-        uint32_t sr[AGG_EPT];  // slot (12 bits) | rank in tile (11 bits) << 12
+        uint32_t sr[AGG_EPT];  // slot | rank in tile << AGG_HBITS
 #pragma unroll
         for (int e = 0; e < AGG_EPT; ++e) {
             sr[e] = NIL;
             if ((okmask >> e) & 1u) {
                 uint32_t r;
                 const uint32_t sl = agg_insert(keys, cnt, us[e], r);
-                sr[e] = sl | (r << 12);
+                sr[e] = sl | (r << AGG_HBITS);
             }
         }
         __syncthreads();
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(AGG_THREADS) k_count(GraphView g, const uint32
             for (int i = 0; i < AGG_SPT / 2; ++i) {
                 const int s = threadIdx.x + (h0 + i) * AGG_THREADS;
                 const uint32_t u = keys[s];
-                old[i] = u != EMPTY_KEY ? atomicAdd(&g.vcnt[u], cnt[s]) : 1u;
+                old[i] = u != EMPTY_KEY ? atomicAdd(&g.vcnt[vslot(g.vmask, u)], cnt[s]) : 1u;
             }
 #pragma unroll
             for (int i = 0; i < AGG_SPT / 2; ++i) {
@@ -216,19 +216,100 @@ __global__ void __launch_bounds__(AGG_THREADS) k_count(GraphView g, const uint32
             fresh &= fresh - 1u;
             const uint32_t u = keys[threadIdx.x + i * AGG_THREADS];
             g.t_vid[t] = u;
-            g.vtid[u] = t;
+            g.vtid[vslot(g.vmask, u)] = t;
             ++t;
         }
 #pragma unroll
         for (int e = 0; e < AGG_EPT; ++e) {
             const unsigned long long i = base + (unsigned long long)e * AGG_THREADS + threadIdx.x;
-            if (i < n) g.prank[i] = sr[e] == NIL ? NIL : cnt[sr[e] & 0xFFFu] + (sr[e] >> 12);
+            if (i < n) g.prank[i] = sr[e] == NIL ? NIL : cnt[sr[e] & (AGG_H - 1)] + (sr[e] >> AGG_HBITS);
         }
         __syncthreads();
     }
     if (MODE != MODE_QUERY) {
         const unsigned long long r = warp_sum_u64(rej);
         if (lane_id() == 0 && r) atomicAdd(&g.dev->call_b, r);
+    }
+}
+
+// Counting pass for large batches: one atomic per pair, whose return value
+// is the pair's rank among its source's pairs; no aggregation, no barriers.
+// The touched list is built afterwards by k_touched_scan.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_count_direct(GraphView g, const uint32_t *__restrict__ src,
+                                                      const uint32_t *__restrict__ dst,
+                                                      unsigned long long n) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    unsigned long long rej = 0;
+    for (unsigned long long i0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i0 < n;
+         i0 += stride * 8) {
+        uint32_t u[8], v[8];
+        uint32_t ok = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const unsigned long long i = i0 + j * stride;
+            u[j] = i < n ? __ldg(src + i) : NIL;
+            v[j] = i < n ? __ldg(dst + i) : NIL;
+            if (u[j] < g.nv && v[j] < g.nv) ok |= 1u << j;
+        }
+        if (!g.all_alive) {
+            uint8_t au[8], av[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                au[j] = ((ok >> j) & 1u) ? g.alive[u[j]] : 0;
+                av[j] = ((ok >> j) & 1u) ? g.alive[v[j]] : 0;
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (!(au[j] && av[j])) ok &= ~(1u << j);
+        }
+        uint32_t r[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) r[j] = ((ok >> j) & 1u) ? atomicAdd(&g.vcnt[vslot(g.vmask, u[j])], 1u) : NIL;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const unsigned long long i = i0 + j * stride;
+            if (i < n) {
+                g.prank[i] = r[j];
+                if (r[j] == NIL) ++rej;
+            }
+        }
+    }
+    if (MODE != MODE_QUERY) {
+        rej = warp_sum_u64(rej);
+        if (lane_id() == 0 && rej) atomicAdd(&g.dev->call_b, rej);
+    }
+}
+
+// Touched list after a direct count: every vertex with a non-zero count
+// (vertex order within each chunk; one atomic per CTA chunk).
+__global__ void __launch_bounds__(256) k_touched_scan(GraphView g) {
+    const uint32_t ncap = g.vmask + 1;
+    __shared__ uint32_t s_base;
+    for (uint32_t base = blockIdx.x * blockDim.x * 4; base < ncap; base += gridDim.x * blockDim.x * 4) {
+        uint32_t flags = 0;
+        const uint32_t u0 = base + threadIdx.x * 4;
+        if (u0 + 3 < ncap) {
+            const uint4 c = *reinterpret_cast<const uint4 *>(g.vcnt + u0);
+            flags = (c.x ? 1u : 0u) | (c.y ? 2u : 0u) | (c.z ? 4u : 0u) | (c.w ? 8u : 0u);
+        } else {
+            for (int j = 0; j < 4; ++j)
+                if (u0 + j < ncap && g.vcnt[u0 + j]) flags |= 1u << j;
+        }
+        uint32_t tot;
+        const uint32_t ex = block_excl_scan(__popc(flags), &tot);
+        if (threadIdx.x == 0) s_base = tot ? atomicAdd(&g.dev->n_touched, tot) : 0u;
+        __syncthreads();
+        uint32_t t = s_base + ex;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if ((flags >> j) & 1u) {
+                g.t_vid[t] = vslot_inv(g.vmask, u0 + j);
+                g.vtid[u0 + j] = t;
+                ++t;
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -254,7 +335,7 @@ __global__ void __launch_bounds__(256) k_plan_insert(GraphView g) {
         uint32_t need = 0, deg = 0, last = NIL;
         if (t < nt) {
             const uint32_t u = g.t_vid[t];
-            const uint32_t cnt = g.vcnt[u];
+            const uint32_t cnt = g.vcnt[vslot(g.vmask, u)];
             const uint4 s = g.sent[u];
             deg = s.x;
             last = s.w;
@@ -268,7 +349,7 @@ __global__ void __launch_bounds__(256) k_plan_insert(GraphView g) {
         const unsigned long long off = s_base + ex;
         if (t < nt) {
             g.t_a[t] = make_uint4(deg, last, (uint32_t)off, need);
-            g.vcur[g.t_vid[t]] = (uint32_t)off;
+            g.vcur[vslot(g.vmask, g.t_vid[t])] = (uint32_t)off;
             for (uint32_t j = 0; j < need; ++j) g.t_owner[off + j] = t;
         }
         __syncthreads();
@@ -321,9 +402,6 @@ __global__ void __launch_bounds__(256) k_link_insert(GraphView g) {
     }
 }
 
-// Pairs per thread per iteration of the streaming per-pair kernels.
-constexpr int PP = 4;
-
 // Insert scatter: one pass over the pairs, no aggregation and no atomics.
 // Pair i of source u with rank r goes to slot deg(u) + r: the free slots of
 // the last block first, then the new blocks popped for u at queue offset
@@ -352,7 +430,7 @@ __global__ void __launch_bounds__(256) k_scatter_insert(GraphView g, const uint3
         for (int j = 0; j < PP; ++j) {
             if (r[j] != NIL) {
                 sn[j] = g.sent[u[j]];
-                off[j] = g.vcur[u[j]];
+                off[j] = g.vcur[vslot(g.vmask, u[j])];
             }
         }
         uint32_t blk[PP], ln[PP];
@@ -394,7 +472,7 @@ __global__ void __launch_bounds__(256) k_finalize_insert(GraphView g, unsigned l
     const uint32_t C = g.C;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
         const uint32_t u = g.t_vid[t];
-        const uint32_t cnt = g.vcnt[u];
+        const uint32_t cnt = g.vcnt[vslot(g.vmask, u)];
         if (!abort) {
             const uint4 a = g.t_a[t];
             const uint32_t deg = a.x, off = a.z, need = a.w;
@@ -408,8 +486,8 @@ __global__ void __launch_bounds__(256) k_finalize_insert(GraphView g, unsigned l
             }
             g.sent[u] = s;
         }
-        g.vcnt[u] = 0;
-        g.vcur[u] = 0;
+        g.vcnt[vslot(g.vmask, u)] = 0;
+        g.vcur[vslot(g.vmask, u)] = 0;
     }
     if (last_cta(dev) && threadIdx.x == 0) {
         unsigned long long rej = dev->call_b;
@@ -464,7 +542,7 @@ __global__ void __launch_bounds__(256) k_plan_member(GraphView g) {
         uint4 s = make_uint4(0, 0, NIL, NIL);
         if (t < nt) {
             const uint32_t u = g.t_vid[t];
-            m = g.vcnt[u];
+            m = g.vcnt[vslot(g.vmask, u)];
             s = g.sent[u];
             words = member_words(m);
             if (s.y > 0) {
@@ -487,7 +565,7 @@ __global__ void __launch_bounds__(256) k_plan_member(GraphView g) {
             const uint32_t aoff = (uint32_t)(s_aw + wex);
             g.t_a[t] = make_uint4(m, aoff, m <= LIST_MAX ? 0u : words, item0);
             g.t_b[t] = make_uint4(s.x, s.y, s.z, ni);
-            g.vcur[g.t_vid[t]] = aoff;
+            g.vcur[vslot(g.vmask, g.t_vid[t])] = aoff;
             if (tiny) g.t_tiny[s_at + tex] = t;
             emit_items(g, t, item0, ni);
         }
@@ -527,8 +605,8 @@ __global__ void __launch_bounds__(256) k_scatter_member(GraphView g, const uint3
 #pragma unroll
         for (int j = 0; j < PP; ++j) {
             if (r[j] != NIL) {
-                m[j] = g.vcnt[u[j]];
-                aoff[j] = g.vcur[u[j]];
+                m[j] = g.vcnt[vslot(g.vmask, u[j])];
+                aoff[j] = g.vcur[vslot(g.vmask, u[j])];
             }
         }
         uint32_t pos[PP], old[PP];
@@ -646,34 +724,58 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
             uint4 e4 = make_uint4(EMPTY_KEY, EMPTY_KEY, EMPTY_KEY, EMPTY_KEY);
             if (qv) e4 = *reinterpret_cast<const uint4 *>(g.data + (size_t)sb_ids[lb] * C + (x - lb * C));
             const uint32_t e[4] = {e4.x, e4.y, e4.z, e4.w};
-            uint32_t surv = 0;
+            uint32_t vmask = 0;  // bit j: entry j is a stored entry of this item
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const bool valid = qv && (x + j < nslots);
-                bool hit = false;
-                if (valid) {
-                    if (MODE == MODE_VDEL) {
-                        hit = (g.dead[e[j] >> 5] >> (e[j] & 31u)) & 1u;
-                    } else if (listmode) {
+            for (int j = 0; j < 4; ++j)
+                if (qv && (x + j < nslots)) vmask |= 1u << j;
+            uint32_t hitm = 0;   // bit j: entry j is in the batch set
+            if (MODE == MODE_VDEL) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (((vmask >> j) & 1u) && ((g.dead[e[j] >> 5] >> (e[j] & 31u)) & 1u)) hitm |= 1u << j;
+            } else if (listmode) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if ((vmask >> j) & 1u) {
                         uint32_t h = mix32(e[j]) & hmask;
                         for (;;) {
                             const uint32_t k = hk[h];
                             if (k == e[j]) {
-                                hit = true;
+                                hitm |= 1u << j;
                                 if (MODE == MODE_QUERY) hf[h] = 1u;
                                 break;
                             }
                             if (k == EMPTY_KEY) break;
                             h = (h + 1) & hmask;
                         }
-                    } else {
-                        const uint32_t h = hash_find(g.arena + a.y, a.z, e[j]);
-                        hit = h != NIL;
-                        if (MODE == MODE_QUERY && hit) g.found[a.y + h] = 1u;
                     }
                 }
-                if (valid && !hit) surv |= 1u << j;
+            } else {
+                // global hash set: the home slots of all four entries are
+                // loaded together; only collisions probe further
+                const uint32_t *tab = g.arena + a.y;
+                const uint32_t hm = a.z - 1;
+                uint32_t hh[4], kk[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    hh[j] = mix32(e[j]) & hm;
+                    kk[j] = ((vmask >> j) & 1u) ? tab[hh[j]] : EMPTY_KEY;
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if ((vmask >> j) & 1u) {
+                        while (kk[j] != e[j] && kk[j] != EMPTY_KEY) {
+                            hh[j] = (hh[j] + 1) & hm;
+                            kk[j] = tab[hh[j]];
+                        }
+                        if (kk[j] == e[j]) {
+                            hitm |= 1u << j;
+                            if (MODE == MODE_QUERY) g.found[a.y + hh[j]] = 1u;
+                        }
+                    }
+                }
             }
+            const uint32_t surv = vmask & ~hitm;
             if (MODE == MODE_QUERY) continue;
             uint32_t tot;
             const uint32_t ex = warp_excl_scan(__popc(surv), &tot);
@@ -1012,8 +1114,8 @@ __global__ void __launch_bounds__(256) k_finalize_member(GraphView g, unsigned l
     const uint32_t nt = dev->n_touched;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
         const uint32_t u = g.t_vid[t];
-        g.vcnt[u] = 0;
-        g.vcur[u] = 0;
+        g.vcnt[vslot(g.vmask, u)] = 0;
+        g.vcur[vslot(g.vmask, u)] = 0;
     }
     if (last_cta(dev) && threadIdx.x == 0) {
         if (MODE == MODE_DELETE) {
@@ -1209,13 +1311,25 @@ inline int grid_for(unsigned long long work, int per_block, int cap) {
 
 cudaError_t launch_count(int mode, const GraphView &g, const uint32_t *src, const uint32_t *dst,
                          unsigned long long n, const LaunchCfg &lc) {
-    const int grid = grid_for(n, AGG_TILE, lc.num_sms * 8);
     const int ph = mode == MODE_INSERT ? PH_INS_COUNT : mode == MODE_DELETE ? PH_DEL_COUNT : PH_QRY_COUNT;
     PhaseScope ps(lc, ph);
-    switch (mode) {
-    case MODE_INSERT: k_count<MODE_INSERT><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
-    case MODE_DELETE: k_count<MODE_DELETE><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
-    default: k_count<MODE_QUERY><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
+    if (n >= (unsigned long long)g.nv / 8) {
+        // large batch: per-pair atomics, then a pass over all vertices
+        const int grid = grid_for(n, 256 * 8, lc.num_sms * GRID_MULT);
+        switch (mode) {
+        case MODE_INSERT: k_count_direct<MODE_INSERT><<<grid, 256, 0, lc.stream>>>(g, src, dst, n); break;
+        case MODE_DELETE: k_count_direct<MODE_DELETE><<<grid, 256, 0, lc.stream>>>(g, src, dst, n); break;
+        default: k_count_direct<MODE_QUERY><<<grid, 256, 0, lc.stream>>>(g, src, dst, n); break;
+        }
+        k_touched_scan<<<grid_for(g.vmask + 1ull, 1024, lc.num_sms * GRID_MULT), 256, 0, lc.stream>>>(g);
+    } else {
+        // small batch: per-tile aggregation, touched list appended on the fly
+        const int grid = grid_for(n, AGG_TILE, lc.num_sms * GRID_MULT);
+        switch (mode) {
+        case MODE_INSERT: k_count<MODE_INSERT><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
+        case MODE_DELETE: k_count<MODE_DELETE><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
+        default: k_count<MODE_QUERY><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
+        }
     }
     return cudaGetLastError();
 }
@@ -1223,14 +1337,14 @@ cudaError_t launch_count(int mode, const GraphView &g, const uint32_t *src, cons
 cudaError_t launch_count_rejects(const GraphView &g, const uint32_t *src, const uint32_t *dst,
                                  unsigned long long n, unsigned long long *rejected,
                                  const LaunchCfg &lc) {
-    k_count_rejects<<<grid_for(n, 256, lc.num_sms * 8), 256, 0, lc.stream>>>(g, src, dst, n, rejected);
+    k_count_rejects<<<grid_for(n, 256, lc.num_sms * GRID_MULT), 256, 0, lc.stream>>>(g, src, dst, n, rejected);
     return cudaGetLastError();
 }
 
 cudaError_t launch_insert_tail(const GraphView &g, const uint32_t *src, const uint32_t *dst,
                                unsigned long long n, unsigned long long tcap,
                                unsigned long long *counts, const LaunchCfg &lc) {
-    const int cap = lc.num_sms * 8;
+    const int cap = lc.num_sms * GRID_MULT;
     const int gt = grid_for(tcap, 256, cap);
     {
         PhaseScope ps(lc, PH_INS_PLAN);
@@ -1256,9 +1370,9 @@ template <int MODE>
 static void member_tail(const GraphView &g, const uint32_t *src, const uint32_t *dst,
                         unsigned long long n, unsigned long long tcap, unsigned long long *counts,
                         uint8_t *qout, const LaunchCfg &lc) {
-    const int cap = lc.num_sms * 8;
+    const int cap = lc.num_sms * GRID_MULT;
     const int gt = grid_for(tcap, 256, cap);
-    const int gi = lc.num_sms * 8;  // warp-per-item kernels: 8 warps per CTA
+    const int gi = lc.num_sms * GRID_MULT;  // warp-per-item kernels: 8 warps per CTA
     const bool del = MODE == MODE_DELETE;
     {
         PhaseScope ps(lc, del ? PH_DEL_PLAN : PH_QRY_PLAN);
@@ -1304,8 +1418,8 @@ cudaError_t launch_member_tail(int mode, const GraphView &g, const uint32_t *src
 
 cudaError_t launch_vertex_delete(const GraphView &g, const uint32_t *ids, uint32_t k,
                                  const LaunchCfg &lc) {
-    const int cap = lc.num_sms * 8;
-    const int gi = lc.num_sms * 8;
+    const int cap = lc.num_sms * GRID_MULT;
+    const int gi = lc.num_sms * GRID_MULT;
     PhaseScope ps(lc, PH_VDEL);
     k_vdel_mark<<<grid_for(k, 256, cap), 256, 0, lc.stream>>>(g, ids, k);
     k_plan_vfree<<<grid_for(k, 256, cap), 256, 0, lc.stream>>>(g);

@@ -106,12 +106,33 @@ cudaError_t launch_iota(uint32_t *out, uint32_t first, uint32_t k, const LaunchC
 cudaError_t launch_validate(const GraphView &g, uint32_t *owner_bits,
                             unsigned long long *violations, const LaunchCfg &lc);
 
-// Sizes shared with the host code.
-constexpr int AGG_THREADS = 256;
-constexpr int AGG_EPT = 8;
+// Sizes shared with the host code (overridable at build time for tuning).
+#ifndef GV_AGG_THREADS
+#define GV_AGG_THREADS 256
+#endif
+#ifndef GV_AGG_EPT
+#define GV_AGG_EPT 8
+#endif
+#ifndef GV_AGG_HBITS
+#define GV_AGG_HBITS 12
+#endif
+#ifndef GV_PP
+#define GV_PP 4
+#endif
+#ifndef GV_GRID_MULT
+#define GV_GRID_MULT 16
+#endif
+constexpr int AGG_THREADS = GV_AGG_THREADS;
+constexpr int AGG_EPT = GV_AGG_EPT;
 constexpr int AGG_TILE = AGG_THREADS * AGG_EPT;  // pairs per tile
-constexpr int AGG_H = 4096;                      // shared hash slots per tile (>= 2 * tile)
+constexpr int AGG_HBITS = GV_AGG_HBITS;
+constexpr int AGG_H = 1 << AGG_HBITS;            // shared hash slots per tile (>= 2 * tile)
 constexpr int AGG_SPT = AGG_H / AGG_THREADS;     // hash slots per thread
+constexpr int PP = GV_PP;                        // pairs per thread per step (streaming kernels)
+constexpr int GRID_MULT = GV_GRID_MULT;          // CTAs per SM of grid-stride kernels
 constexpr int MASK_WORDS = 16;                   // survivor bits per item (512 slots)
+static_assert(AGG_H >= 2 * AGG_TILE, "aggregation table must be at most half full");
+static_assert(AGG_SPT <= 32 && AGG_SPT % 2 == 0, "slots per thread");
+static_assert(AGG_TILE <= (1 << (32 - AGG_HBITS)), "slot and rank must pack into 32 bits");
 
 }  // namespace gv
