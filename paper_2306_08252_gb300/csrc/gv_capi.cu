@@ -49,7 +49,8 @@ struct gv_graph {
     // dictionary and vertex scratch
     uint4 *sent = nullptr;
     uint8_t *alive = nullptr;
-    uint32_t *vcnt = nullptr, *vcur = nullptr, *vtid = nullptr, *dead = nullptr;
+    uint32_t *vcnt = nullptr, *vtid = nullptr, *dead = nullptr;
+    uint4 *vinfo = nullptr;
     // control block
     Dev *dev = nullptr;
     Dev *h_dev = nullptr;  // pinned mirror for stats
@@ -148,7 +149,7 @@ GraphView view(const gv_graph *g) {
     v.all_alive = g->any_vertex_deleted ? 0u : 1u;
     v.vmask = g->vcap ? g->vcap - 1 : 0;
     v.vcnt = g->vcnt;
-    v.vcur = g->vcur;
+    v.vinfo = g->vinfo;
     v.vtid = g->vtid;
     v.t_vid = g->t_vid;
     v.t_a = g->t_a;
@@ -246,28 +247,28 @@ gv_status ensure_vertex_capacity(gv_graph *g, uint32_t need, cudaStream_t s) {
     while (cap < need) cap *= 2;  // dictionary doubles ("Dynamic vertex updates")
     uint4 *sent = nullptr;
     uint8_t *alive = nullptr;
-    uint32_t *vcnt = nullptr, *vcur = nullptr, *vtid = nullptr, *dead = nullptr;
+    uint32_t *vcnt = nullptr, *vtid = nullptr, *dead = nullptr;
+    uint4 *vinfo = nullptr;
     uint64_t acct = 0;
     gv_status st;
     if ((st = dalloc(&sent, cap, &acct)) != GV_OK || (st = dalloc(&alive, cap, &acct)) != GV_OK ||
-        (st = dalloc(&vcnt, cap, &acct)) != GV_OK || (st = dalloc(&vcur, cap, &acct)) != GV_OK ||
+        (st = dalloc(&vcnt, cap, &acct)) != GV_OK || (st = dalloc(&vinfo, cap, &acct)) != GV_OK ||
         (st = dalloc(&vtid, cap, &acct)) != GV_OK || (st = dalloc(&dead, cap / 32 + 1, &acct)) != GV_OK) {
-        dfree(sent); dfree(alive); dfree(vcnt); dfree(vcur); dfree(vtid); dfree(dead);
+        dfree(sent); dfree(alive); dfree(vcnt); dfree(vinfo); dfree(vtid); dfree(dead);
         return st;
     }
     GV_CK(cudaMemsetAsync(vcnt, 0, (size_t)cap * 4, s));
-    GV_CK(cudaMemsetAsync(vcur, 0, (size_t)cap * 4, s));
     GV_CK(cudaMemsetAsync(dead, 0, (size_t)(cap / 32 + 1) * 4, s));
     GV_CK(cudaMemsetAsync(alive, 0, cap, s));
     if (g->vcap) {
         GV_CK(gv::launch_copy_dictionary(sent, alive, g->sent, g->alive, g->nv, lcfg(g, s)));
         GV_CK(cudaStreamSynchronize(s));
     }
-    dfree(g->sent); dfree(g->alive); dfree(g->vcnt); dfree(g->vcur); dfree(g->vtid); dfree(g->dead);
+    dfree(g->sent); dfree(g->alive); dfree(g->vcnt); dfree(g->vinfo); dfree(g->vtid); dfree(g->dead);
     g->sent = sent;
     g->alive = alive;
     g->vcnt = vcnt;
-    g->vcur = vcur;
+    g->vinfo = vinfo;
     g->vtid = vtid;
     g->dead = dead;
     g->vcap = cap;
@@ -667,7 +668,7 @@ gv_status gv_destroy(gv_graph *g) {
         cudaStreamSynchronize(g->last_stream);
         cudaGetLastError();
         if (g->pool_alloc) cudaFree(g->pool_alloc);
-        dfree(g->sent); dfree(g->alive); dfree(g->vcnt); dfree(g->vcur); dfree(g->vtid); dfree(g->dead);
+        dfree(g->sent); dfree(g->alive); dfree(g->vcnt); dfree(g->vinfo); dfree(g->vtid); dfree(g->dead);
         dfree(g->dev);
         dfree(g->t_vid); dfree(g->t_a); dfree(g->t_b); dfree(g->t_owner); dfree(g->t_tiny); dfree(g->prank);
         dfree(g->items); dfree(g->it_mask); dfree(g->it_cnt); dfree(g->it_H); dfree(g->it_S); dfree(g->it_bid);

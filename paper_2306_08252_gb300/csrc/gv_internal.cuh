@@ -64,7 +64,7 @@ struct GraphView {
     uint32_t vmask;         // dictionary capacity - 1 (capacity is a power of two)
     // vertex-indexed scratch (zero between calls), indexed by vslot(u)
     uint32_t *vcnt;         // batch entries per source
-    uint32_t *vcur;         // per-source offset set by the plan (queue or arena)
+    uint4 *vinfo;           // per-source plan record read by the scatters (one 16-byte load per pair)
     uint32_t *vtid;         // touched index of a source (valid while vcnt > 0)
     // touched-indexed scratch
     uint32_t *t_vid;        // touched source ids
@@ -165,6 +165,12 @@ __device__ __forceinline__ unsigned long long qmod(unsigned long long x, unsigne
 }
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+// Loads of data read exactly once (batch pairs, ranks, adjacency entries
+// streamed by a scan): evict-first, so that they do not push the per-vertex
+// records and hash sets that many pairs share out of L2.
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t *p) { return __ldcs(p); }
+__device__ __forceinline__ uint4 ld_stream4(const uint4 *p) { return __ldcs(p); }
 
 // Full-warp exclusive scan of a uint32 (all 32 lanes must call).
 __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, uint32_t *total) {

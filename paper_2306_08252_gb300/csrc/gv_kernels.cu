@@ -248,8 +248,8 @@ __global__ void __launch_bounds__(256) k_count_direct(GraphView g, const uint32_
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const unsigned long long i = i0 + j * stride;
-            u[j] = i < n ? __ldg(src + i) : NIL;
-            v[j] = i < n ? __ldg(dst + i) : NIL;
+            u[j] = i < n ? ld_stream(src + i) : NIL;
+            v[j] = i < n ? ld_stream(dst + i) : NIL;
             if (u[j] < g.nv && v[j] < g.nv) ok |= 1u << j;
         }
         if (!g.all_alive) {
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(256) k_plan_insert(GraphView g) {
         const unsigned long long off = s_base + ex;
         if (t < nt) {
             g.t_a[t] = make_uint4(deg, last, (uint32_t)off, need);
-            g.vcur[vslot(g.vmask, g.t_vid[t])] = (uint32_t)off;
+            g.vinfo[vslot(g.vmask, g.t_vid[t])] = make_uint4(deg, last, (uint32_t)off, 0u);
             for (uint32_t j = 0; j < need; ++j) g.t_owner[off + j] = t;
         }
         __syncthreads();
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(256) k_link_insert(GraphView g) {
 // Insert scatter: one pass over the pairs, no aggregation and no atomics.
 // Pair i of source u with rank r goes to slot deg(u) + r: the free slots of
 // the last block first, then the new blocks popped for u at queue offset
-// vcur[u] (set by the plan).  Sentinels still hold the pre-call state.
+// recorded by the plan in the source's vinfo record.
 __global__ void __launch_bounds__(256) k_scatter_insert(GraphView g, const uint32_t *__restrict__ src,
                                                         const uint32_t *__restrict__ dst,
                                                         unsigned long long n) {
@@ -420,35 +420,31 @@ __global__ void __launch_bounds__(256) k_scatter_insert(GraphView g, const uint3
 #pragma unroll
         for (int j = 0; j < PP; ++j) {
             const unsigned long long i = i0 + j * stride;
-            r[j] = i < n ? g.prank[i] : NIL;
-            u[j] = i < n ? __ldg(src + i) : 0u;
-            v[j] = i < n ? __ldg(dst + i) : 0u;
+            r[j] = i < n ? ld_stream(g.prank + i) : NIL;
+            u[j] = i < n ? ld_stream(src + i) : 0u;
+            v[j] = i < n ? ld_stream(dst + i) : 0u;
         }
-        uint4 sn[PP];
-        uint32_t off[PP];
+        uint4 vi[PP];  // {deg, last block, queue offset of the new blocks, -}
 #pragma unroll
-        for (int j = 0; j < PP; ++j) {
-            if (r[j] != NIL) {
-                sn[j] = g.sent[u[j]];
-                off[j] = g.vcur[vslot(g.vmask, u[j])];
-            }
-        }
+        for (int j = 0; j < PP; ++j)
+            if (r[j] != NIL) vi[j] = g.vinfo[vslot(g.vmask, u[j])];
         uint32_t blk[PP], ln[PP];
 #pragma unroll
         for (int j = 0; j < PP; ++j) {
             blk[j] = NIL;
             ln[j] = 0;
             if (r[j] != NIL) {
-                const uint32_t deg = sn[j].x, nb = sn[j].y;
+                const uint32_t deg = vi[j].x;
+                const uint32_t nb = (deg + C - 1) / C;
                 const uint32_t space = nb * C - deg;
                 if (r[j] < space) {
-                    blk[j] = sn[j].w;
+                    blk[j] = vi[j].y;
                     ln[j] = deg - (nb - 1) * C + r[j];
                 } else {
                     const uint32_t q = r[j] - space;
                     const uint32_t jb = q / C;
                     ln[j] = q - jb * C;
-                    blk[j] = g.queue[ring(qbase, off[j] + jb, P)];
+                    blk[j] = g.queue[ring(qbase, vi[j].z + jb, P)];
                 }
             }
         }
@@ -487,7 +483,6 @@ __global__ void __launch_bounds__(256) k_finalize_insert(GraphView g, unsigned l
             g.sent[u] = s;
         }
         g.vcnt[vslot(g.vmask, u)] = 0;
-        g.vcur[vslot(g.vmask, u)] = 0;
     }
     if (last_cta(dev) && threadIdx.x == 0) {
         unsigned long long rej = dev->call_b;
@@ -565,7 +560,7 @@ __global__ void __launch_bounds__(256) k_plan_member(GraphView g) {
             const uint32_t aoff = (uint32_t)(s_aw + wex);
             g.t_a[t] = make_uint4(m, aoff, m <= LIST_MAX ? 0u : words, item0);
             g.t_b[t] = make_uint4(s.x, s.y, s.z, ni);
-            g.vcur[vslot(g.vmask, g.t_vid[t])] = aoff;
+            g.vinfo[vslot(g.vmask, g.t_vid[t])] = make_uint4(m, aoff, 0u, 0u);
             if (tiny) g.t_tiny[s_at + tex] = t;
             emit_items(g, t, item0, ni);
         }
@@ -597,16 +592,17 @@ __global__ void __launch_bounds__(256) k_scatter_member(GraphView g, const uint3
 #pragma unroll
         for (int j = 0; j < PP; ++j) {
             const unsigned long long i = i0 + j * stride;
-            r[j] = i < n ? g.prank[i] : NIL;
-            u[j] = i < n ? __ldg(src + i) : 0u;
-            v[j] = i < n ? __ldg(dst + i) : 0u;
+            r[j] = i < n ? ld_stream(g.prank + i) : NIL;
+            u[j] = i < n ? ld_stream(src + i) : 0u;
+            v[j] = i < n ? ld_stream(dst + i) : 0u;
         }
         uint32_t m[PP], aoff[PP];
 #pragma unroll
         for (int j = 0; j < PP; ++j) {
             if (r[j] != NIL) {
-                m[j] = g.vcnt[vslot(g.vmask, u[j])];
-                aoff[j] = g.vcur[vslot(g.vmask, u[j])];
+                const uint4 vi = g.vinfo[vslot(g.vmask, u[j])];
+                m[j] = vi.x;
+                aoff[j] = vi.y;
             }
         }
         uint32_t pos[PP], old[PP];
@@ -722,7 +718,7 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
             const uint32_t x = q << 2;
             const uint32_t lb = x / C;
             uint4 e4 = make_uint4(EMPTY_KEY, EMPTY_KEY, EMPTY_KEY, EMPTY_KEY);
-            if (qv) e4 = *reinterpret_cast<const uint4 *>(g.data + (size_t)sb_ids[lb] * C + (x - lb * C));
+            if (qv) e4 = ld_stream4(reinterpret_cast<const uint4 *>(g.data + (size_t)sb_ids[lb] * C + (x - lb * C)));
             const uint32_t e[4] = {e4.x, e4.y, e4.z, e4.w};
             uint32_t vmask = 0;  // bit j: entry j is a stored entry of this item
 #pragma unroll
@@ -1115,7 +1111,6 @@ __global__ void __launch_bounds__(256) k_finalize_member(GraphView g, unsigned l
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
         const uint32_t u = g.t_vid[t];
         g.vcnt[vslot(g.vmask, u)] = 0;
-        g.vcur[vslot(g.vmask, u)] = 0;
     }
     if (last_cta(dev) && threadIdx.x == 0) {
         if (MODE == MODE_DELETE) {
