@@ -148,6 +148,7 @@ GraphView view(const gv_graph *g) {
     v.nv = g->nv;
     v.all_alive = g->any_vertex_deleted ? 0u : 1u;
     v.vmask = g->vcap ? g->vcap - 1 : 0;
+    v.cmul = g->C ? ((1ull << 40) + g->C - 1) / g->C : 0ull;
     v.vcnt = g->vcnt;
     v.vinfo = g->vinfo;
     v.vtid = g->vtid;
@@ -782,6 +783,7 @@ gv_status gv_delete_vertices(gv_graph *g, const uint32_t *ids, uint32_t k, void 
     if (v.C == 0) {
         v.C = 4;
         v.IB = 32;
+        v.cmul = (1ull << 40) / 4;
     }
     g->any_vertex_deleted = true;
     v.all_alive = 0;

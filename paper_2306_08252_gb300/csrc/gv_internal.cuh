@@ -62,6 +62,7 @@ struct GraphView {
     uint32_t nv;            // vertex count
     uint32_t all_alive;     // 1 while no vertex has ever been deleted (alive[] need not be read)
     uint32_t vmask;         // dictionary capacity - 1 (capacity is a power of two)
+    unsigned long long cmul;  // ceil(2^40 / C): x / C == (x * cmul) >> 40 for x < 2^31
     // vertex-indexed scratch (zero between calls), indexed by vslot(u)
     uint32_t *vcnt;         // batch entries per source
     uint4 *vinfo;           // per-source plan record read by the scatters (one 16-byte load per pair)
@@ -96,8 +97,9 @@ enum Mode : int { MODE_INSERT = 0, MODE_DELETE = 1, MODE_QUERY = 2, MODE_VDEL = 
 // as an open-addressing hash set in the arena above it.
 constexpr uint32_t LIST_MAX = 256;
 // Tiny adjacencies (one thread per source): at most TINY_DEG entries in at
-// most two blocks, at most TINY_M batch entries.
-constexpr uint32_t TINY_DEG = 32;
+// most TINY_NB blocks, at most TINY_M batch entries.
+constexpr uint32_t TINY_DEG = 64;
+constexpr uint32_t TINY_NB = 4;
 constexpr uint32_t TINY_M = 16;
 
 // Arena words of a source with m batch entries: m (list) or the hash set
@@ -165,6 +167,13 @@ __device__ __forceinline__ unsigned long long qmod(unsigned long long x, unsigne
 }
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+// x / C by multiply and shift.  With M = ceil(2^40 / C) and e = M*C - 2^40
+// < C <= 512, floor(x*M / 2^40) = floor(x / C) whenever x*e < 2^40, i.e. for
+// every x < 2^31 (degrees and slot indices stay below that).
+__device__ __forceinline__ uint32_t divc(unsigned long long cmul, uint32_t x) {
+    return (uint32_t)(((unsigned long long)x * cmul) >> 40);
+}
 
 // Loads of data read exactly once (batch pairs, ranks, adjacency entries
 // streamed by a scan): evict-first, so that they do not push the per-vertex

@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(256) k_plan_insert(GraphView g) {
             deg = s.x;
             last = s.w;
             const uint32_t space = s.y * C - deg;
-            need = cnt > space ? (cnt - space + C - 1) / C : 0u;
+            need = cnt > space ? divc(g.cmul, cnt - space + C - 1) : 0u;
         }
         uint32_t tot;
         const uint32_t ex = block_excl_scan(need, &tot);
@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(256) k_link_insert(GraphView g) {
         const uint32_t t = g.t_owner[j];
         const uint4 a = g.t_a[t];
         const uint32_t deg = a.x, off = a.z, need = a.w;
-        const uint32_t nb = (deg + C - 1) / C;
+        const uint32_t nb = divc(g.cmul, deg + C - 1);
         const uint32_t k = nb + 1 + (uint32_t)(j - off);  // heap index of this block
         const uint32_t nbn = nb + need;
         const uint32_t id = g.queue[ring(qbase, j, P)];
@@ -435,14 +435,14 @@ __global__ void __launch_bounds__(256) k_scatter_insert(GraphView g, const uint3
             ln[j] = 0;
             if (r[j] != NIL) {
                 const uint32_t deg = vi[j].x;
-                const uint32_t nb = (deg + C - 1) / C;
+                const uint32_t nb = divc(g.cmul, deg + C - 1);
                 const uint32_t space = nb * C - deg;
                 if (r[j] < space) {
                     blk[j] = vi[j].y;
                     ln[j] = deg - (nb - 1) * C + r[j];
                 } else {
                     const uint32_t q = r[j] - space;
-                    const uint32_t jb = q / C;
+                    const uint32_t jb = divc(g.cmul, q);
                     ln[j] = q - jb * C;
                     blk[j] = g.queue[ring(qbase, vi[j].z + jb, P)];
                 }
@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(256) k_finalize_insert(GraphView g, unsigned l
         if (!abort) {
             const uint4 a = g.t_a[t];
             const uint32_t deg = a.x, off = a.z, need = a.w;
-            const uint32_t nb = (deg + C - 1) / C;
+            const uint32_t nb = divc(g.cmul, deg + C - 1);
             uint4 s = g.sent[u];
             s.x = deg + cnt;
             s.y = nb + need;
@@ -528,7 +528,7 @@ template <int MODE>
 __global__ void __launch_bounds__(256) k_plan_member(GraphView g) {
     const uint32_t nt = g.dev->n_touched;
     const uint32_t IB = g.IB;
-    const uint32_t tiny_deg = min(TINY_DEG, 2 * g.C);
+    const uint32_t tiny_deg = min(TINY_DEG, TINY_NB * g.C);
     __shared__ unsigned long long s_aw;
     __shared__ uint32_t s_ai, s_at;
     for (uint32_t base = blockIdx.x * blockDim.x; base < nt; base += gridDim.x * blockDim.x) {
@@ -541,7 +541,7 @@ __global__ void __launch_bounds__(256) k_plan_member(GraphView g) {
             s = g.sent[u];
             words = member_words(m);
             if (s.y > 0) {
-                if (s.x <= tiny_deg && m <= TINY_M) tiny = 1;
+                if (s.x <= tiny_deg && s.y <= TINY_NB && m <= TINY_M) tiny = 1;
                 else ni = (s.y + IB - 1) / IB;
             }
         }
@@ -716,7 +716,7 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
             const uint32_t q = q0 + lane;
             const bool qv = q < nquads;
             const uint32_t x = q << 2;
-            const uint32_t lb = x / C;
+            const uint32_t lb = divc(g.cmul, x);
             uint4 e4 = make_uint4(EMPTY_KEY, EMPTY_KEY, EMPTY_KEY, EMPTY_KEY);
             if (qv) e4 = ld_stream4(reinterpret_cast<const uint4 *>(g.data + (size_t)sb_ids[lb] * C + (x - lb * C)));
             const uint32_t e[4] = {e4.x, e4.y, e4.z, e4.w};
@@ -783,7 +783,7 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
                 for (int j = 0; j < 4; ++j) {
                     if ((surv >> j) & 1u) {
                         if (w != x + j) {
-                            const uint32_t tq = w / C;
+                            const uint32_t tq = divc(g.cmul, w);
                             g.data[(size_t)sb_ids[tq] * C + (w - tq * C)] = e[j];
                         }
                         ++w;
@@ -815,7 +815,7 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
         if (single) {
             const uint32_t degn = running;
             if (degn != deg) {
-                const uint32_t nbn = (degn + C - 1) / C;
+                const uint32_t nbn = divc(g.cmul, degn + C - 1);
                 const uint32_t k = lane + 1;
                 const bool fr = lane < nblk && k > nbn;
                 fs.push(fr, bid, dev, g.queue, qbb, P);
@@ -839,10 +839,14 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
     }
 }
 
-// Tiny adjacencies, one thread per source: at most two blocks and
-// min(TINY_DEG, 2C) entries, at most TINY_M batch entries (held in
+// Tiny adjacencies, one thread per source: at most TINY_NB blocks and
+// min(TINY_DEG, TINY_NB * C) entries, at most TINY_M batch entries (held in
 // registers).  Delete / vertex delete compact in place (stable) and return
 // emptied blocks; query sets the hit flag of every matching batch entry.
+__device__ __forceinline__ uint32_t pick4(uint32_t i, uint32_t b0, uint32_t b1, uint32_t b2, uint32_t b3) {
+    return i == 0 ? b0 : (i == 1 ? b1 : (i == 2 ? b2 : b3));
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
     Dev *dev = g.dev;
@@ -869,9 +873,14 @@ __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
             m = a.x;
             aoff = a.y;
         }
-        uint32_t b0 = root, b1 = NIL;
-        if (act && root < P && nb == 2) b1 = g.links[2ull * root];
-        if (act && (b0 >= P || (nb == 2 && b1 >= P))) {
+        // heap 1 = root, 2 and 3 = its children, 4 = left child of 2
+        uint32_t b0 = root, b1 = NIL, b2 = NIL, b3 = NIL;
+        if (act && root < P && nb >= 2) {
+            b1 = g.links[2ull * root];
+            if (nb >= 3) b2 = g.links[2ull * root + 1];
+        }
+        if (act && nb >= 4 && b1 < P) b3 = g.links[2ull * b1];
+        if (act && (b0 >= P || (nb >= 2 && b1 >= P) || (nb >= 3 && b2 >= P) || (nb >= 4 && b3 >= P))) {
             latch_status(dev, 5u /* GV_ERR_STATE */);
             act = false;
         }
@@ -882,9 +891,9 @@ __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
         uint32_t qhit = 0;
         uint32_t w = 0;
         for (uint32_t x = 0; act && x < deg; x += 4) {
-            const uint32_t blk = x < C ? b0 : b1;
-            const uint32_t off = x < C ? x : x - C;
-            const uint4 e4 = *reinterpret_cast<const uint4 *>(g.data + (size_t)blk * C + off);
+            const uint32_t bi = divc(g.cmul, x);
+            const uint32_t blk = pick4(bi, b0, b1, b2, b3);
+            const uint4 e4 = ld_stream4(reinterpret_cast<const uint4 *>(g.data + (size_t)blk * C + (x - bi * C)));
             const uint32_t e[4] = {e4.x, e4.y, e4.z, e4.w};
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj) {
@@ -901,8 +910,8 @@ __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
                     }
                     if (MODE != MODE_QUERY && !hit) {
                         if (w != x + jj) {
-                            const uint32_t tb = w < C ? b0 : b1;
-                            g.data[(size_t)tb * C + (w < C ? w : w - C)] = e[jj];
+                            const uint32_t wi = divc(g.cmul, w);
+                            g.data[(size_t)pick4(wi, b0, b1, b2, b3) * C + (w - wi * C)] = e[jj];
                         }
                         ++w;
                     }
@@ -916,12 +925,18 @@ __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
             continue;
         }
         const bool changed = act && w != deg;
-        const uint32_t nbn = (w + C - 1) / C;
-        fs.push(changed && nb == 2 && nbn < 2, b1, dev, g.queue, qbb, P);
+        const uint32_t nbn = divc(g.cmul, w + C - 1);
+        // blocks past the new count return to the queue; a freed block's
+        // parent (still owned) forgets it
+        fs.push(changed && nb >= 4 && nbn < 4, b3, dev, g.queue, qbb, P);
+        fs.push(changed && nb >= 3 && nbn < 3, b2, dev, g.queue, qbb, P);
+        fs.push(changed && nb >= 2 && nbn < 2, b1, dev, g.queue, qbb, P);
         fs.push(changed && nbn == 0, b0, dev, g.queue, qbb, P);
         if (changed) {
-            if (nb == 2 && nbn == 1) g.links[2ull * b0] = NIL;  // heap 2 hangs left of heap 1
-            g.sent[g.t_vid[t]] = make_uint4(w, nbn, nbn ? root : NIL, nbn == 2 ? b1 : (nbn == 1 ? b0 : NIL));
+            if (nb >= 4 && nbn >= 2 && nbn < 4) g.links[2ull * b1] = NIL;      // heap 4: left of heap 2
+            if (nb >= 3 && nbn >= 1 && nbn < 3) g.links[2ull * b0 + 1] = NIL;  // heap 3: right of heap 1
+            if (nb >= 2 && nbn == 1) g.links[2ull * b0] = NIL;                 // heap 2: left of heap 1
+            g.sent[g.t_vid[t]] = make_uint4(w, nbn, nbn ? root : NIL, nbn ? pick4(nbn - 1, b0, b1, b2, b3) : NIL);
             removed += deg - w;
         }
     }
@@ -989,7 +1004,7 @@ __global__ void __launch_bounds__(256) k_vscan(GraphView g) {
         }
         if (lane == 0) {
             g.t_a[t].x = degn;
-            const uint32_t nbn = (degn + C - 1) / C;
+            const uint32_t nbn = divc(g.cmul, degn + C - 1);
             uint32_t lastb = NIL;
             if (nbn) {
                 const uint32_t k = nbn - 1;
@@ -1023,7 +1038,7 @@ __global__ void __launch_bounds__(256) k_move(GraphView g) {
         if (ni <= 1) continue;
         const uint4 a = g.t_a[t];
         const uint32_t degn = a.x, item0 = a.w, deg = b.x, nb = b.y;
-        const uint32_t nbn = (degn + C - 1) / C;
+        const uint32_t nbn = divc(g.cmul, degn + C - 1);
         const uint32_t sb = c * SPI;
         const uint32_t len = min(SPI, deg - sb);
         const uint32_t *mk = g.it_mask + (size_t)it * MASK_WORDS;
@@ -1069,10 +1084,11 @@ __global__ void __launch_bounds__(256) k_move(GraphView g) {
                         r -= pc;
                     }
                     if (pos != NIL) {
-                        const uint32_t srcb = g.it_bid[(size_t)(item0 + cs) * IB + pos / C];
-                        const uint32_t val = g.data[(size_t)srcb * C + pos % C];
-                        const uint32_t dstb = bids[x / C];
-                        g.data[(size_t)dstb * C + x % C] = val;
+                        const uint32_t pq = divc(g.cmul, pos), xq = divc(g.cmul, x);
+                        const uint32_t srcb = g.it_bid[(size_t)(item0 + cs) * IB + pq];
+                        const uint32_t val = g.data[(size_t)srcb * C + (pos - pq * C)];
+                        const uint32_t dstb = bids[xq];
+                        g.data[(size_t)dstb * C + (x - xq * C)] = val;
                     } else {
                         latch_status(dev, 5u /* GV_ERR_STATE */);
                     }
@@ -1232,7 +1248,7 @@ __global__ void k_reset_lists(GraphView g) {
 __global__ void __launch_bounds__(256) k_plan_vdel_in(GraphView g) {
     const uint32_t nv = g.nv;
     const uint32_t IB = g.IB;
-    const uint32_t tiny_deg = min(TINY_DEG, 2 * g.C);
+    const uint32_t tiny_deg = min(TINY_DEG, TINY_NB * g.C);
     __shared__ uint32_t s_at, s_ai, s_an;
     for (uint32_t base = blockIdx.x * blockDim.x; base < nv; base += gridDim.x * blockDim.x) {
         const uint32_t u = base + threadIdx.x;
@@ -1242,7 +1258,7 @@ __global__ void __launch_bounds__(256) k_plan_vdel_in(GraphView g) {
             s = g.sent[u];
             if (s.x) {
                 take = 1;
-                if (s.x <= tiny_deg && s.y <= 2) tiny = 1;
+                if (s.x <= tiny_deg && s.y <= TINY_NB) tiny = 1;
                 else ni = (s.y + IB - 1) / IB;
             }
         }

@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(256) k_nbr_copy(GraphView g, const unsigned lo
         for (uint32_t q0 = 0; q0 < nquads; q0 += 32) {
             const uint32_t q = q0 + lane;
             const uint32_t x = q << 2;
-            const uint32_t lb = x / C;
+            const uint32_t lb = divc(g.cmul, x);
             const uint32_t myb = __shfl_sync(FULL, bid, lb & 31u);
             if (q < nquads) {
                 const uint4 e4 = *reinterpret_cast<const uint4 *>(g.data + (size_t)myb * C + (x - lb * C));

@@ -69,3 +69,16 @@ def test_product_path_does_not_import_oracle():
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
                 assert "gv_oracle" not in src, f
+
+
+def test_multiply_shift_division_by_block_capacity_is_exact():
+    # The kernels divide by C as (x * ceil(2^40 / C)) >> 40; exact for every
+    # x < 2^31 and every allowed C (multiple of 4, 4..512).
+    import random
+    rng = random.Random(7)
+    for C in range(4, 513, 4):
+        M = ((1 << 40) + C - 1) // C
+        xs = [0, 1, C - 1, C, C + 1, (1 << 31) - 1, (1 << 31) - C] + [rng.randrange(1 << 31) for _ in range(300)]
+        xs += [k * C + r for k in (1, 7, 1 << 20, (1 << 31) // C - 1) for r in (0, C - 1)]
+        for x in xs:
+            assert (x * M) >> 40 == x // C, (C, x)
