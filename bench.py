@@ -37,6 +37,7 @@ BASE_EDGES = 1 << 24
 BATCH = 10_000_000
 QUERIES = 1_000_000
 C = 16
+BLOCK = C
 POOL_BYTES = 2 << 30
 SEED = 2
 
@@ -149,31 +150,50 @@ class ClockSampler:
 # -------------------------------------------------------------- byte model
 
 def byte_model(g, batch, qry, inserted, deleted, newblocks):
-    """Algorithmic bytes of one step (the minimum the method must move):
-    insert 12 B/edge + 32 B/touched source + 12 B/new block; query
-    9 B/query + 4 B per stored entry of each distinct queried source;
-    delete 8 B/edge + 4 B per stored entry of each touched source + 32 B per
-    touched source + 4 B per freed block (entries moved by compaction are
-    not counted: a lower bound)."""
+    """Algorithmic bytes.
+
+    Per operation (the minimum the method must move): insert 12 B/edge +
+    32 B/touched source + 12 B/new block; query 9 B/query + 4 B per stored
+    entry of each distinct queried source; delete 8 B/edge + 4 B per stored
+    entry of each touched source + 32 B per touched source + 4 B per freed
+    block (entries moved by compaction are not counted: a lower bound).
+
+    Per kernel (its compulsory traffic): counting passes read the pairs and
+    write one rank per pair (12 B/pair); the touched scan reads the counter
+    array; scatters read pair + rank and write one 4-byte entry (16 B/pair);
+    mark kernels read every stored entry of the sources they own and their
+    batch entries (4 B each)."""
     s, d = batch
     deg, _ = g.degrees()  # state after the insert = state the query and delete see
     nv = deg.size
+    C = BLOCK
     ok = (s < nv) & (d < nv)
     us = np.unique(s[ok])
     qs = np.unique(qry[0][qry[0] < nv])
+    deg64 = deg.astype(np.int64)
     ins_b = 12 * inserted + 32 * us.size + 12 * newblocks
-    qry_b = 9 * qry[0].size + 4 * int(deg[qs].astype(np.int64).sum())
-    del_b = 8 * s.size + 4 * int(deg[us].astype(np.int64).sum()) + 32 * us.size + 4 * newblocks
+    qry_b = 9 * qry[0].size + 4 * int(deg64[qs].sum())
+    del_b = 8 * s.size + 4 * int(deg64[us].sum()) + 32 * us.size + 4 * newblocks
+
+    def tiers(src_ids):
+        m = np.bincount(src_ids, minlength=nv)
+        touched = m > 0
+        nb = (deg64 + C - 1) // C
+        tiny = touched & (deg64 > 0) & (deg64 <= min(64, 4 * C)) & (nb <= 4) & (m <= 16)
+        big = touched & (deg64 > 0) & ~tiny
+        return (4 * int(deg64[big].sum()) + 4 * int(m[big].sum()),
+                4 * int(deg64[tiny].sum()) + 4 * int(m[tiny].sum()))
+
+    dmark, dtiny = tiers(s[ok])
+    qok = (qry[0] < nv) & (qry[1] < nv)
+    qmark, qtiny = tiers(qry[0][qok])
+    scan = 4 * (1 << int(np.ceil(np.log2(max(nv, 1)))))
     kernels = {
-        # per-launch algorithmic bytes of each timed phase
-        "insert.count": 8 * s.size,
-        "insert.scatter": 12 * inserted,
-        "delete.count": 8 * s.size,
-        "delete.scatter": 12 * s.size,
-        "delete.mark": 4 * int(deg[us].astype(np.int64).sum()) + 4 * s.size,
-        "query.count": 8 * qry[0].size,
-        "query.scatter": 12 * qry[0].size,
-        "query.mark": 4 * int(deg[qs].astype(np.int64).sum()) + 4 * qry[0].size,
+        "insert.count": 12 * s.size, "insert.touched": scan, "insert.scatter": 16 * inserted,
+        "delete.count": 12 * s.size, "delete.touched": scan, "delete.scatter": 16 * s.size,
+        "delete.mark": dmark, "delete.mark_tiny": dtiny,
+        "query.count": 12 * qry[0].size, "query.touched": scan, "query.scatter": 16 * qry[0].size,
+        "query.mark": qmark, "query.mark_tiny": qtiny,
     }
     return {"insert": ins_b, "query": qry_b, "delete": del_b, "step": ins_b + qry_b + del_b,
             "touched_sources": int(us.size), "kernels": kernels}

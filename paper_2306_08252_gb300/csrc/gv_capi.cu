@@ -933,11 +933,13 @@ gv_status gv_degree_offsets_noalloc(gv_graph *g, const uint32_t *d_vids, uint32_
 }
 
 static const char *kPhaseNames[gv::PH_COUNT] = {
-    "insert.count",   "insert.plan",    "insert.link",   "insert.scatter", "insert.finalize",
-    "delete.count",   "delete.plan",    "delete.arena",  "delete.scatter", "delete.mark",
-    "delete.vscan",   "delete.move",    "delete.finalize",
-    "query.count",    "query.plan",     "query.arena",   "query.scatter",  "query.mark",
-    "query.out",      "query.finalize", "vertex_delete", "neighbors",      "other"};
+    "insert.count",   "insert.touched", "insert.plan",     "insert.link",      "insert.scatter",
+    "insert.finalize",
+    "delete.count",   "delete.touched", "delete.plan",     "delete.arena",     "delete.scatter",
+    "delete.mark",    "delete.mark_tiny", "delete.vscan",  "delete.move",      "delete.finalize",
+    "query.count",    "query.touched",  "query.plan",      "query.arena",      "query.scatter",
+    "query.mark",     "query.mark_tiny", "query.out",      "query.finalize",
+    "vertex_delete",  "neighbors",      "other"};
 
 uint32_t gv_profile_num_phases(void) { return gv::PH_COUNT; }
 

@@ -1323,18 +1323,22 @@ inline int grid_for(unsigned long long work, int per_block, int cap) {
 cudaError_t launch_count(int mode, const GraphView &g, const uint32_t *src, const uint32_t *dst,
                          unsigned long long n, const LaunchCfg &lc) {
     const int ph = mode == MODE_INSERT ? PH_INS_COUNT : mode == MODE_DELETE ? PH_DEL_COUNT : PH_QRY_COUNT;
-    PhaseScope ps(lc, ph);
     if (n >= (unsigned long long)g.nv / 8) {
         // large batch: per-pair atomics, then a pass over all vertices
         const int grid = grid_for(n, 256 * 8, lc.num_sms * GRID_MULT);
-        switch (mode) {
-        case MODE_INSERT: k_count_direct<MODE_INSERT><<<grid, 256, 0, lc.stream>>>(g, src, dst, n); break;
-        case MODE_DELETE: k_count_direct<MODE_DELETE><<<grid, 256, 0, lc.stream>>>(g, src, dst, n); break;
-        default: k_count_direct<MODE_QUERY><<<grid, 256, 0, lc.stream>>>(g, src, dst, n); break;
+        {
+            PhaseScope ps(lc, ph);
+            switch (mode) {
+            case MODE_INSERT: k_count_direct<MODE_INSERT><<<grid, 256, 0, lc.stream>>>(g, src, dst, n); break;
+            case MODE_DELETE: k_count_direct<MODE_DELETE><<<grid, 256, 0, lc.stream>>>(g, src, dst, n); break;
+            default: k_count_direct<MODE_QUERY><<<grid, 256, 0, lc.stream>>>(g, src, dst, n); break;
+            }
         }
+        PhaseScope ps(lc, ph + 1);  // the touched-list phase follows each count phase
         k_touched_scan<<<grid_for(g.vmask + 1ull, 1024, lc.num_sms * GRID_MULT), 256, 0, lc.stream>>>(g);
     } else {
         // small batch: per-tile aggregation, touched list appended on the fly
+        PhaseScope ps(lc, ph);
         const int grid = grid_for(n, AGG_TILE, lc.num_sms * GRID_MULT);
         switch (mode) {
         case MODE_INSERT: k_count<MODE_INSERT><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
@@ -1400,6 +1404,9 @@ static void member_tail(const GraphView &g, const uint32_t *src, const uint32_t 
     {
         PhaseScope ps(lc, del ? PH_DEL_MARK : PH_QRY_MARK);
         k_mark<MODE><<<gi, 256, 0, lc.stream>>>(g);
+    }
+    {
+        PhaseScope ps(lc, del ? PH_DEL_MARK_TINY : PH_QRY_MARK_TINY);
         k_mark_tiny<MODE><<<gt, 256, 0, lc.stream>>>(g);
     }
     if (del) {

@@ -11,10 +11,11 @@ namespace gv {
 
 // Kernel phases timed by the optional per-graph profiler.
 enum Phase : int {
-    PH_INS_COUNT = 0, PH_INS_PLAN, PH_INS_LINK, PH_INS_SCATTER, PH_INS_FINALIZE,
-    PH_DEL_COUNT, PH_DEL_PLAN, PH_DEL_ARENA, PH_DEL_SCATTER, PH_DEL_MARK, PH_DEL_VSCAN, PH_DEL_MOVE,
-    PH_DEL_FINALIZE,
-    PH_QRY_COUNT, PH_QRY_PLAN, PH_QRY_ARENA, PH_QRY_SCATTER, PH_QRY_MARK, PH_QRY_OUT, PH_QRY_FINALIZE,
+    PH_INS_COUNT = 0, PH_INS_TOUCHED, PH_INS_PLAN, PH_INS_LINK, PH_INS_SCATTER, PH_INS_FINALIZE,
+    PH_DEL_COUNT, PH_DEL_TOUCHED, PH_DEL_PLAN, PH_DEL_ARENA, PH_DEL_SCATTER, PH_DEL_MARK, PH_DEL_MARK_TINY,
+    PH_DEL_VSCAN, PH_DEL_MOVE, PH_DEL_FINALIZE,
+    PH_QRY_COUNT, PH_QRY_TOUCHED, PH_QRY_PLAN, PH_QRY_ARENA, PH_QRY_SCATTER, PH_QRY_MARK, PH_QRY_MARK_TINY,
+    PH_QRY_OUT, PH_QRY_FINALIZE,
     PH_VDEL, PH_NEIGHBORS, PH_OTHER,
     PH_COUNT
 };
