@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--queries", type=int, default=QUERIES)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "batched"],
+                    help="rmat: the single-graph step (default); batched: many member graphs, "
+                         "one captured launch sequence vs one launch sequence per graph")
+    ap.add_argument("--graphs", type=int, default=256)
     return ap.parse_args()
 
 
@@ -385,8 +389,136 @@ def run_ours(args, rank, world, local_rank):
     return res, (base, upd, qry)
 
 
+def run_batched(args):
+    """Many independent RMAT graphs (member sizes log-uniform in 2^10..2^18,
+    average degree 8, batches log-uniform in 1..1M): one graph set whose
+    insert + delete for all members is captured in one CUDA graph, against
+    one graph object per member driven call by call.  A step is every
+    member's insert batch then its delete batch; an untimed delete of the
+    insert batches restores the state between steps."""
+    import torch
+    import workloads as W
+    import paper_2306_08252_gb300 as gv
+    from paper_2306_08252_gb300 import autotune
+
+    torch.cuda.set_device(0)
+    members = W.batched_rmat(seed=4, graphs=args.graphs)
+    tuned = autotune.tune_set(members, log=lambda m: print(m, file=sys.stderr))
+    C, IBk, DS = tuned["block_capacity"], tuned["item_blocks"], tuned["dense_shift"]
+    dev = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).view(dt)).cuda()
+    bs, bd, bo = autotune.concat_member_batches(members, "bulk")
+    is_, id_, io = autotune.concat_member_batches(members, "insert")
+    ds, dd, do = autotune.concat_member_batches(members, "delete")
+    updates = int(is_.size + ds.size)
+    G = len(members)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    # ---- batched: one set, captured
+    blocks = (bs.size + 2 * is_.size) // C + sum(m["nv"] for m in members) + 4096
+    gs = gv.GraphSet([m["nv"] for m in members], block_capacity=C, pool_bytes=int(blocks * (4 * C + 12) * 1.5),
+                     item_blocks=IBk, dense_shift=DS)
+    cnt = torch.zeros(2 * G, dtype=torch.int64, device="cuda")
+    gs.insert_edges(dev(bs, np.int32), dev(bd, np.int32), dev(bo, np.int64), cnt)
+    gs.reserve(max(bs.size, is_.size, ds.size))
+    a = (dev(is_, np.int32), dev(id_, np.int32), dev(io, np.int64))
+    b = (dev(ds, np.int32), dev(dd, np.int32), dev(do, np.int64))
+    ci = torch.zeros(2 * G, dtype=torch.int64, device="cuda")
+    cd = torch.zeros(2 * G, dtype=torch.int64, device="cuda")
+    cr = torch.zeros(2 * G, dtype=torch.int64, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        gs.insert_edges(*a, ci)
+        gs.delete_edges(*b, cd)
+        gs.delete_edges(*a, cr)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    step_g, rest_g = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    with torch.cuda.graph(step_g, capture_error_mode="relaxed"):
+        gs.insert_edges(*a, ci)
+        gs.delete_edges(*b, cd)
+    with torch.cuda.graph(rest_g, capture_error_mode="relaxed"):
+        gs.delete_edges(*a, cr)
+    for _ in range(max(args.warmup, 1)):
+        step_g.replay()
+        rest_g.replay()
+    torch.cuda.synchronize()
+    t_b = 0.0
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step_g.replay()
+        e1.record()
+        rest_g.replay()
+        torch.cuda.synchronize()
+        t_b += e0.elapsed_time(e1)
+    assert gs.sync() == 0
+    batched_counts = (ci.cpu().numpy().reshape(-1, 2), cd.cpu().numpy().reshape(-1, 2))
+    gs.close()
+    del step_g, rest_g
+    # ---- plain: one graph per member, one launch sequence per call
+    plain = []
+    for m in members:
+        nb_ = (m["bulk"][0].size + 2 * m["insert"][0].size) // C + m["nv"] + 64
+        g = gv.Graph(m["nv"], block_capacity=C, pool_bytes=int(nb_ * (4 * C + 12) * 1.5) + (1 << 16),
+                     item_blocks=IBk, dense_shift=DS)
+        g.bulk_build(dev(m["bulk"][0], np.int32), dev(m["bulk"][1], np.int32))
+        plain.append((g, dev(m["insert"][0], np.int32), dev(m["insert"][1], np.int32),
+                      dev(m["delete"][0], np.int32), dev(m["delete"][1], np.int32)))
+    pc = torch.zeros(2 * G, dtype=torch.int64, device="cuda")
+    pd = torch.zeros(2 * G, dtype=torch.int64, device="cuda")
+
+    def plain_step(restore):
+        for i, (g, s_, d_, s2, d2) in enumerate(plain):
+            if restore:
+                g.delete_edges(s_, d_)
+            else:
+                g.insert_edges(s_, d_, pc[2 * i:2 * i + 2])
+                g.delete_edges(s2, d2, pd[2 * i:2 * i + 2])
+
+    for _ in range(max(args.warmup, 1)):
+        plain_step(False)
+        plain_step(True)
+    torch.cuda.synchronize()
+    t_p = 0.0
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plain_step(False)
+        e1.record()
+        torch.cuda.synchronize()
+        plain_step(True)
+        torch.cuda.synchronize()
+        t_p += e0.elapsed_time(e1)
+    same = (np.array_equal(pc.cpu().numpy().reshape(-1, 2), batched_counts[0]) and
+            np.array_equal(pd.cpu().numpy().reshape(-1, 2), batched_counts[1]))
+    for g, *_ in plain:
+        g.close()
+    vb = args.steps * updates / (t_b / 1e3)
+    vp = args.steps * updates / (t_p / 1e3)
+    res = {"metric": "edge updates/s (batched form: all members in one captured launch sequence)",
+           "value": vb, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": t_b / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "u32", "data": "synthetic (seeded RMAT members)",
+           "config": {"workload": f"{G} RMAT graphs, vertices log-uniform 2^10..2^18, average degree 8, "
+                                  f"insert + delete batches log-uniform 1..1M per member",
+                      "members": G, "vertices": int(sum(m["nv"] for m in members)), "base_edges": int(bs.size),
+                      "updates_per_step": updates, "tuned": {k: tuned[k] for k in ("block_capacity", "item_blocks",
+                                                                                      "dense_shift")},
+                      "l2": "flushed before every timed step"},
+           "plain": {"value": vp, "ms_per_step": t_p / args.steps,
+                     "form": "one graph object per member, insert + delete call per member"},
+           "speedup_vs_plain": vb / vp, "counts_match_plain": bool(same)}
+    print(json.dumps(res), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "batched":
+        return run_batched(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -81,6 +81,14 @@ typedef struct gv_config {
     /* Hint for the dictionary capacity; rounded up to a power of two
      * ("Vertex dictionary": 453 vertices -> 512). */
     uint32_t vertex_capacity;
+    /* Tuning (0 = default).  item_blocks: blocks of one adjacency that one
+     * warp handles per work item in deletes and queries (1 .. min(32, 512/C);
+     * default the maximum) -- fewer blocks put more warps on a long
+     * adjacency.  dense_shift: batches of n pairs with n >= vertices >> s
+     * are grouped with one atomic per pair plus a pass over all vertices,
+     * smaller ones with per-tile aggregation (default s = 3). */
+    uint32_t item_blocks;
+    uint32_t dense_shift;
     uint32_t reserved;
 } gv_config;
 
@@ -264,6 +272,42 @@ gv_status gv_profile(gv_graph *g, int enable);
 gv_status gv_profile_read(gv_graph *g, double *ms, uint64_t *launches, uint32_t n);
 uint32_t gv_profile_num_phases(void);
 const char *gv_profile_phase_name(uint32_t phase);
+
+/*
+ * Graph sets: many independent graphs ("members") in one device structure
+ * that shares one dictionary (members own consecutive vertex ranges), one
+ * block pool and one scratch area, so that an update touching every member
+ * runs as one launch sequence whatever the number of members (and can be
+ * captured in a CUDA graph once gv_reserve has sized the scratch).  Member
+ * batches use member-local vertex ids.  Vertex insert/delete is not
+ * available on a set; gv_stats, gv_validate, gv_sync, gv_reserve,
+ * gv_profile and gv_destroy work on it as on a graph.
+ *
+ * gv_set_create -- cfg must give C (block_capacity != 0) and no GV_DEDUP;
+ *   num_vertices is a host array of num_graphs (1 .. 1024) vertex counts.
+ * gv_set_insert_edges / gv_set_delete_edges / gv_set_query_edges -- the
+ *   members' batches concatenated: pairs d_offsets[i] .. d_offsets[i+1]-1 of
+ *   d_src/d_dst belong to member i (d_offsets: num_graphs+1 uint64, device;
+ *   n = d_offsets[num_graphs], given by the caller).  d_counts (device,
+ *   2*num_graphs uint64) receives per member {inserted, rejected} /
+ *   {deleted, rejected} / {0, rejected}; d_out (query, device, n uint8) the
+ *   answers.  All arrays must be device memory (GV_ERR_INVALID_ARG
+ *   otherwise): the calls allocate nothing once scratch is reserved and
+ *   never synchronise.  Semantics per member are those of the single-graph
+ *   calls (Algorithms 1-3).
+ * gv_set_member_neighbors -- member `member`'s CSR (member-local ids),
+ *   contract of gv_neighbors over all of its vertices.
+ */
+gv_status gv_set_create(const gv_config *cfg, uint32_t num_graphs, const uint32_t *num_vertices, void *stream,
+                        gv_graph **out);
+gv_status gv_set_insert_edges(gv_graph *set, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
+                              const uint64_t *d_offsets, uint64_t *d_counts, void *stream);
+gv_status gv_set_delete_edges(gv_graph *set, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
+                              const uint64_t *d_offsets, uint64_t *d_counts, void *stream);
+gv_status gv_set_query_edges(gv_graph *set, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
+                             const uint64_t *d_offsets, uint64_t *d_counts, uint8_t *d_out, void *stream);
+gv_status gv_set_member_neighbors(gv_graph *set, uint32_t member, uint64_t *offsets, uint32_t *nbrs,
+                                  uint64_t nbr_capacity, uint64_t *total, void *stream);
 
 /*
  * gv_degree_offsets_noalloc -- CSR offsets of the listed vertices' current

@@ -11,6 +11,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "../../include/graphvine.h"
 #include "gv_launch.h"
@@ -38,6 +39,7 @@ struct gv_graph {
     int device = 0;
     int num_sms = 0;
     uint32_t C = 0, IB = 0, flags = 0;
+    uint32_t item_blocks_cfg = 0, dense_shift = 3;
     uint32_t nv = 0, vcap = 0;
     unsigned long long P = 0;
     uint64_t pool_bytes_cfg = 0;
@@ -83,6 +85,12 @@ struct gv_graph {
     uint64_t scratch_bytes = 0;
     uint64_t dict_bytes = 0;
     bool any_vertex_deleted = false;
+    // graph set: members' vertex ranges (set_G == 0 for a plain graph)
+    uint32_t set_G = 0;
+    uint32_t *set_vbase = nullptr;          // device, G+1
+    std::vector<uint32_t> set_vbase_h;      // host copy
+    unsigned long long scap = 0;
+    uint32_t *set_src = nullptr, *set_dst = nullptr;  // remapped batch
     gv::Prof prof;
 };
 
@@ -149,6 +157,7 @@ GraphView view(const gv_graph *g) {
     v.all_alive = g->any_vertex_deleted ? 0u : 1u;
     v.vmask = g->vcap ? g->vcap - 1 : 0;
     v.cmul = g->C ? ((1ull << 40) + g->C - 1) / g->C : 0ull;
+    v.dense_shift = g->dense_shift;
     v.vcnt = g->vcnt;
     v.vinfo = g->vinfo;
     v.vtid = g->vtid;
@@ -170,6 +179,10 @@ GraphView view(const gv_graph *g) {
     v.dead = g->dead;
     v.max_items = g->icap;
     v.arena_cap = g->acap;
+    v.set_G = 0;
+    v.set_vbase = nullptr;
+    v.set_off = nullptr;
+    v.set_counts = nullptr;
     return v;
 }
 
@@ -344,6 +357,7 @@ gv_status setup_pool(gv_graph *g, uint32_t C, cudaStream_t s) {
     if (C < 4 || C > 512 || (C % 4) != 0) return GV_ERR_INVALID_ARG;
     g->C = C;
     g->IB = std::min<uint32_t>(32, std::max<uint32_t>(1, 512 / C));
+    if (g->item_blocks_cfg) g->IB = std::min<uint32_t>(g->IB, g->item_blocks_cfg);
     uint64_t bytes = g->pool_bytes_cfg;
     if (bytes == 0) {
         size_t fr = 0, tot = 0;
@@ -630,6 +644,8 @@ gv_status gv_create(const gv_config *cfg, uint32_t num_vertices, void *stream, g
     cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
     if (g->num_sms <= 0) g->num_sms = 1;
     g->flags = c.flags;
+    g->item_blocks_cfg = c.item_blocks;
+    if (c.dense_shift) g->dense_shift = std::min<uint32_t>(c.dense_shift, 31);
     g->pool_bytes_cfg = c.pool_bytes;
     g->pool_mem_cfg = c.pool_mem;
     g->last_stream = s;
@@ -675,6 +691,7 @@ gv_status gv_destroy(gv_graph *g) {
         dfree(g->items); dfree(g->it_mask); dfree(g->it_cnt); dfree(g->it_H); dfree(g->it_S); dfree(g->it_bid);
         dfree(g->arena); dfree(g->found); dfree(g->qpos); dfree(g->partials);
         dfree(g->owner_bits); dfree(g->vres);
+        dfree(g->set_vbase); dfree(g->set_src); dfree(g->set_dst);
         for (auto &b : g->stage.buf) dfree(b.p);
         for (auto &r : g->prof.recs) {
             cudaEventDestroy(r.a);
@@ -799,6 +816,14 @@ gv_status gv_reserve(gv_graph *g, uint64_t max_batch) {
     if (g->C) GV_TRY(ensure_items(g, item_bound(g, std::min<unsigned long long>(max_batch, g->nv ? g->nv : 1))));
     GV_TRY(ensure_arena(g, 4 * max_batch + 64, true, max_batch));
     GV_TRY(ensure_ranks(g, max_batch));
+    if (g->set_G && (max_batch > g->scap || !g->scap)) {
+        dfree(g->set_src);
+        dfree(g->set_dst);
+        g->scap = 0;
+        GV_TRY(dalloc(&g->set_src, std::max<uint64_t>(max_batch, 1), &g->scratch_bytes));
+        GV_TRY(dalloc(&g->set_dst, std::max<uint64_t>(max_batch, 1), &g->scratch_bytes));
+        g->scap = std::max<uint64_t>(max_batch, 1);
+    }
     for (int slot = 0; slot < 4; ++slot) {
         void *d = nullptr;
         GV_TRY(stage_buf(g, slot, max_batch * 4 + 64, &d));
@@ -930,6 +955,124 @@ gv_status gv_degree_offsets_noalloc(gv_graph *g, const uint32_t *d_vids, uint32_
     GV_CK(gv::launch_neighbor_offsets(view(g), d_vids, n, reinterpret_cast<unsigned long long *>(d_offsets),
                                       scratch, lc));
     return check_launch();
+}
+
+// ---------------------------------------------------------------- graph sets
+
+}  // extern "C"
+
+namespace {
+
+gv_status set_batch(gv_graph *g, int mode, const uint32_t *src, const uint32_t *dst, uint64_t n,
+                    const uint64_t *d_offsets, uint64_t *d_counts, uint8_t *out, cudaStream_t s) {
+    if (!g || g->set_G == 0) return GV_ERR_INVALID_ARG;
+    if (n > kMaxBatch || !d_offsets || !d_counts || (n > 0 && (!src || !dst))) return GV_ERR_INVALID_ARG;
+    if (mode == gv::MODE_QUERY && n > 0 && !out) return GV_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    // device arrays only: host staging would allocate and synchronise
+    if (is_host_ptr(d_offsets) || is_host_ptr(d_counts) || (n > 0 && (is_host_ptr(src) || is_host_ptr(dst))) ||
+        (out && is_host_ptr(out)))
+        return GV_ERR_INVALID_ARG;
+    g->last_stream = s;
+    GV_CK(cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * 2 * g->set_G, s));
+    if (n == 0) return check_launch();
+    if (n > g->scap || !g->scap) {
+        unsigned long long cap = std::max<unsigned long long>(n, 2 * g->scap);
+        dfree(g->set_src);
+        dfree(g->set_dst);
+        g->scap = 0;
+        GV_TRY(dalloc(&g->set_src, cap, &g->scratch_bytes));
+        GV_TRY(dalloc(&g->set_dst, cap, &g->scratch_bytes));
+        g->scap = cap;
+    }
+    GraphView v = view(g);
+    v.set_G = g->set_G;
+    v.set_vbase = g->set_vbase;
+    v.set_off = reinterpret_cast<const unsigned long long *>(d_offsets);
+    v.set_counts = reinterpret_cast<unsigned long long *>(d_counts);
+    GV_CK(gv::launch_set_remap(v, src, dst, n, g->set_src, g->set_dst, lcfg(g, s)));
+    if (mode == gv::MODE_INSERT) {
+        if (g->C == 0) return GV_ERR_STATE;  // sets are created with a fixed C
+        GV_TRY(ensure_batch(g, n, gv::MODE_INSERT));
+        GraphView w = view(g);
+        GV_CK(gv::launch_count(gv::MODE_INSERT, w, g->set_src, g->set_dst, n, lcfg(g, s)));
+        GV_CK(gv::launch_insert_tail(w, g->set_src, g->set_dst, n, g->tcap, nullptr, lcfg(g, s)));
+        GV_CK(gv::launch_set_insert_counts(v, lcfg(g, s)));
+    } else {
+        GV_TRY(ensure_batch(g, n, mode));
+        GraphView w = view(g);
+        w.set_G = v.set_G;
+        w.set_vbase = v.set_vbase;
+        w.set_off = v.set_off;
+        w.set_counts = v.set_counts;
+        GV_CK(gv::launch_count(mode, w, g->set_src, g->set_dst, n, lcfg(g, s)));
+        GV_CK(gv::launch_member_tail(mode, w, g->set_src, g->set_dst, n, g->tcap, nullptr, out, lcfg(g, s)));
+    }
+    return check_launch();
+}
+
+}  // namespace
+
+extern "C" {
+
+gv_status gv_set_create(const gv_config *cfg, uint32_t num_graphs, const uint32_t *num_vertices, void *stream,
+                        gv_graph **out) {
+    if (!out || num_graphs == 0 || num_graphs > gv::SET_MAX_G || !num_vertices) return GV_ERR_INVALID_ARG;
+    if (!cfg || cfg->block_capacity == 0 || (cfg->flags & GV_DEDUP)) return GV_ERR_INVALID_ARG;
+    std::vector<uint32_t> base(num_graphs + 1, 0);
+    uint64_t tot = 0;
+    for (uint32_t i = 0; i < num_graphs; ++i) {
+        base[i] = (uint32_t)tot;
+        tot += num_vertices[i];
+        if (tot > 0x7FFFFFFFull) return GV_ERR_INVALID_ARG;
+    }
+    base[num_graphs] = (uint32_t)tot;
+    gv_graph *g = nullptr;
+    GV_TRY(gv_create(cfg, (uint32_t)tot, stream, &g));
+    DeviceGuard dg(g->device);
+    gv_status st = dalloc(&g->set_vbase, num_graphs + 1, &g->scratch_bytes);
+    if (st == GV_OK &&
+        cudaMemcpy(g->set_vbase, base.data(), sizeof(uint32_t) * (num_graphs + 1), cudaMemcpyHostToDevice) != cudaSuccess)
+        st = GV_ERR_CUDA;
+    if (st != GV_OK) {
+        gv_destroy(g);
+        return st;
+    }
+    g->set_G = num_graphs;
+    g->set_vbase_h = base;
+    *out = g;
+    return GV_OK;
+}
+
+gv_status gv_set_insert_edges(gv_graph *set, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
+                              const uint64_t *d_offsets, uint64_t *d_counts, void *stream) {
+    return set_batch(set, gv::MODE_INSERT, d_src, d_dst, n, d_offsets, d_counts, nullptr,
+                     static_cast<cudaStream_t>(stream));
+}
+
+gv_status gv_set_delete_edges(gv_graph *set, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
+                              const uint64_t *d_offsets, uint64_t *d_counts, void *stream) {
+    return set_batch(set, gv::MODE_DELETE, d_src, d_dst, n, d_offsets, d_counts, nullptr,
+                     static_cast<cudaStream_t>(stream));
+}
+
+gv_status gv_set_query_edges(gv_graph *set, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
+                             const uint64_t *d_offsets, uint64_t *d_counts, uint8_t *d_out, void *stream) {
+    return set_batch(set, gv::MODE_QUERY, d_src, d_dst, n, d_offsets, d_counts, d_out,
+                     static_cast<cudaStream_t>(stream));
+}
+
+gv_status gv_set_member_neighbors(gv_graph *set, uint32_t member, uint64_t *offsets, uint32_t *nbrs,
+                                  uint64_t nbr_capacity, uint64_t *total, void *stream) {
+    if (!set || set->set_G == 0 || member >= set->set_G) return GV_ERR_INVALID_ARG;
+    DeviceGuard dg(set->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const uint32_t first = set->set_vbase_h[member];
+    const uint32_t cnt = set->set_vbase_h[member + 1] - first;
+    void *d = nullptr;
+    GV_TRY(stage_buf(set, 5, (size_t)cnt * 4 + 4, &d));
+    GV_CK(gv::launch_iota((uint32_t *)d, first, cnt, lcfg(set, s)));
+    return neighbors_impl(set, (const uint32_t *)d, cnt, offsets, nbrs, nbr_capacity, total, s, false);
 }
 
 static const char *kPhaseNames[gv::PH_COUNT] = {

@@ -63,6 +63,7 @@ struct GraphView {
     uint32_t all_alive;     // 1 while no vertex has ever been deleted (alive[] need not be read)
     uint32_t vmask;         // dictionary capacity - 1 (capacity is a power of two)
     unsigned long long cmul;  // ceil(2^40 / C): x / C == (x * cmul) >> 40 for x < 2^31
+    uint32_t dense_shift;   // batches with n >= nv >> dense_shift use per-pair counting
     // vertex-indexed scratch (zero between calls), indexed by vslot(u)
     uint32_t *vcnt;         // batch entries per source
     uint4 *vinfo;           // per-source plan record read by the scatters (one 16-byte load per pair)
@@ -88,7 +89,26 @@ struct GraphView {
     uint32_t *dead;         // vertex delete: bitmap of deleted ids
     unsigned long long max_items;
     unsigned long long arena_cap;
+    // graph sets (many member graphs in one structure); set_G == 0 otherwise
+    uint32_t set_G;                    // members
+    const uint32_t *set_vbase;         // G+1 first vertex of each member (device)
+    const unsigned long long *set_off; // G+1 first pair of each member's batch (device)
+    unsigned long long *set_counts;    // 2G per-member counts of this call (device)
 };
+
+// Largest number of members of a graph set (per-CTA shared histograms).
+constexpr uint32_t SET_MAX_G = 1024;
+
+// Member owning global vertex u: the last i with vbase[i] <= u.
+__device__ __forceinline__ uint32_t member_of(const uint32_t *vbase, uint32_t G, uint32_t u) {
+    uint32_t lo = 0, hi = G;  // vbase[lo] <= u < vbase[hi]
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (vbase[mid] <= u) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
 
 enum Mode : int { MODE_INSERT = 0, MODE_DELETE = 1, MODE_QUERY = 2, MODE_VDEL = 3 };
 

@@ -659,6 +659,11 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
     __shared__ uint32_t s_bid[8][32];
     __shared__ uint32_t s_hkey[8][2 * LIST_MAX];
     __shared__ uint32_t s_hfound[8][(MODE == MODE_QUERY) ? 2 * LIST_MAX : 1];
+    __shared__ uint32_t s_mhist[(MODE == MODE_QUERY) ? 1 : SET_MAX_G];
+    if (MODE != MODE_QUERY && g.set_G) {
+        for (uint32_t i = threadIdx.x; i < g.set_G; i += blockDim.x) s_mhist[i] = 0;
+        __syncthreads();
+    }
     FreeStage fs{s_free[threadIdx.x >> 5], 0u};
     unsigned long long removed = 0;  // entries deleted by this warp (lane 0)
     for (uint32_t it = warp; it < nitems; it += nwarps) {
@@ -824,8 +829,10 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
                 const uint32_t lastb = __shfl_sync(FULL, bid, (nbn - 1) & 31u);
                 if (fr && p >= 1 && p <= nbn) g.links[2ull * pb + (k & 1u)] = NIL;
                 if (lane == 0) {
-                    g.sent[g.t_vid[t]] = make_uint4(degn, nbn, nbn ? root : NIL, nbn ? lastb : NIL);
+                    const uint32_t u = g.t_vid[t];
+                    g.sent[u] = make_uint4(degn, nbn, nbn ? root : NIL, nbn ? lastb : NIL);
                     removed += deg - degn;
+                    if (g.set_G) atomicAdd(&s_mhist[member_of(g.set_vbase, g.set_G, u)], deg - degn);
                 }
             }
         } else {
@@ -836,6 +843,11 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
     if (MODE != MODE_QUERY) {
         fs.flush(fs.n, dev, g.queue, qbb, P);
         if (lane == 0 && removed) atomicAdd(&dev->call_a, removed);
+        if (g.set_G) {
+            __syncthreads();
+            for (uint32_t i = threadIdx.x; i < g.set_G; i += blockDim.x)
+                if (s_mhist[i]) atomicAdd(&g.set_counts[2 * i], (unsigned long long)s_mhist[i]);
+        }
     }
 }
 
@@ -855,6 +867,11 @@ __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
     const unsigned long long P = g.P;
     const unsigned long long qbb = qmod(dev->q_back, P);
     __shared__ uint32_t s_free[8][64];
+    __shared__ uint32_t s_mhist[(MODE == MODE_QUERY) ? 1 : SET_MAX_G];
+    if (MODE != MODE_QUERY && g.set_G) {
+        for (uint32_t i = threadIdx.x; i < g.set_G; i += blockDim.x) s_mhist[i] = 0;
+        __syncthreads();
+    }
     FreeStage fs{s_free[threadIdx.x >> 5], 0u};
     unsigned long long removed = 0;
     const uint32_t stride = gridDim.x * blockDim.x;
@@ -936,14 +953,21 @@ __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
             if (nb >= 4 && nbn >= 2 && nbn < 4) g.links[2ull * b1] = NIL;      // heap 4: left of heap 2
             if (nb >= 3 && nbn >= 1 && nbn < 3) g.links[2ull * b0 + 1] = NIL;  // heap 3: right of heap 1
             if (nb >= 2 && nbn == 1) g.links[2ull * b0] = NIL;                 // heap 2: left of heap 1
-            g.sent[g.t_vid[t]] = make_uint4(w, nbn, nbn ? root : NIL, nbn ? pick4(nbn - 1, b0, b1, b2, b3) : NIL);
+            const uint32_t u = g.t_vid[t];
+            g.sent[u] = make_uint4(w, nbn, nbn ? root : NIL, nbn ? pick4(nbn - 1, b0, b1, b2, b3) : NIL);
             removed += deg - w;
+            if (g.set_G) atomicAdd(&s_mhist[member_of(g.set_vbase, g.set_G, u)], deg - w);
         }
     }
     if (MODE != MODE_QUERY) {
         fs.flush(fs.n, dev, g.queue, qbb, P);
         removed = warp_sum_u64(removed);
         if (lane_id() == 0 && removed) atomicAdd(&dev->call_a, removed);
+        if (g.set_G) {
+            __syncthreads();
+            for (uint32_t i = threadIdx.x; i < g.set_G; i += blockDim.x)
+                if (s_mhist[i]) atomicAdd(&g.set_counts[2 * i], (unsigned long long)s_mhist[i]);
+        }
     }
 }
 
@@ -956,6 +980,11 @@ __global__ void __launch_bounds__(256) k_vscan(GraphView g) {
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t C = g.C, IB = g.IB, SPI = IB * C;
+    __shared__ uint32_t s_mhist[SET_MAX_G];
+    if (g.set_G) {
+        for (uint32_t i = threadIdx.x; i < g.set_G; i += blockDim.x) s_mhist[i] = 0;
+        __syncthreads();
+    }
     unsigned long long removed = 0;
     for (uint32_t t = warp; t < nt; t += nwarps) {
         const uint4 b = g.t_b[t];
@@ -1010,11 +1039,18 @@ __global__ void __launch_bounds__(256) k_vscan(GraphView g) {
                 const uint32_t k = nbn - 1;
                 lastb = g.it_bid[(size_t)(item0 + k / IB) * IB + (k % IB)];
             }
-            g.sent[g.t_vid[t]] = make_uint4(degn, nbn, nbn ? root : NIL, lastb);
+            const uint32_t u = g.t_vid[t];
+            g.sent[u] = make_uint4(degn, nbn, nbn ? root : NIL, lastb);
             removed += deg - degn;
+            if (g.set_G) atomicAdd(&s_mhist[member_of(g.set_vbase, g.set_G, u)], deg - degn);
         }
     }
     if (lane == 0 && removed) atomicAdd(&dev->call_a, removed);
+    if (g.set_G) {
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < g.set_G; i += blockDim.x)
+            if (s_mhist[i]) atomicAdd(&g.set_counts[2 * i], (unsigned long long)s_mhist[i]);
+    }
 }
 
 // One warp per item of a multi-item source.
@@ -1309,6 +1345,56 @@ __global__ void __launch_bounds__(256) k_finalize_vdel(GraphView g, const uint32
     }
 }
 
+// ---------------------------------------------------------------- graph sets
+
+// Concatenated member batches -> one batch over the set's shared dictionary:
+// the source becomes base(member) + u, the destination stays member-local
+// (stored entries of a member are its own ids).  A pair with an endpoint
+// outside its member's range is rejected here (source NIL) and counted for
+// its member.
+__global__ void __launch_bounds__(256) k_set_remap(GraphView g, const uint32_t *__restrict__ src,
+                                                   const uint32_t *__restrict__ dst, unsigned long long n,
+                                                   uint32_t *gsrc, uint32_t *gdst) {
+    __shared__ unsigned long long s_off[SET_MAX_G + 1];
+    __shared__ uint32_t s_base[SET_MAX_G + 1];
+    __shared__ uint32_t s_rej[SET_MAX_G];
+    const uint32_t G = g.set_G;
+    for (uint32_t i = threadIdx.x; i <= G; i += blockDim.x) {
+        s_off[i] = g.set_off[i];
+        s_base[i] = g.set_vbase[i];
+        if (i < G) s_rej[i] = 0;
+    }
+    __syncthreads();
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        uint32_t lo = 0, hi = G;  // s_off[lo] <= i < s_off[hi]
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (s_off[mid] <= i) lo = mid;
+            else hi = mid;
+        }
+        const uint32_t u = ld_stream(src + i), v = ld_stream(dst + i);
+        const uint32_t nvm = s_base[lo + 1] - s_base[lo];
+        const bool ok = u < nvm && v < nvm;
+        gsrc[i] = ok ? s_base[lo] + u : NIL;
+        gdst[i] = v;
+        if (!ok) atomicAdd(&s_rej[lo], 1u);
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < G; i += blockDim.x)
+        if (s_rej[i]) atomicAdd(&g.set_counts[2 * i + 1], (unsigned long long)s_rej[i]);
+}
+
+// Inserted pairs per member (multiset): its batch size minus its rejects.
+__global__ void k_set_insert_counts(GraphView g) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < g.set_G; i += gridDim.x * blockDim.x)
+        g.set_counts[2 * i] = (g.set_off[i + 1] - g.set_off[i]) - g.set_counts[2 * i + 1];
+}
+
+cudaError_t launch_set_remap(const GraphView &g, const uint32_t *src, const uint32_t *dst, unsigned long long n,
+                             uint32_t *gsrc, uint32_t *gdst, const LaunchCfg &lc);
+cudaError_t launch_set_insert_counts(const GraphView &g, const LaunchCfg &lc);
+
 // ------------------------------------------------------------------ launch
 
 namespace {
@@ -1323,7 +1409,7 @@ inline int grid_for(unsigned long long work, int per_block, int cap) {
 cudaError_t launch_count(int mode, const GraphView &g, const uint32_t *src, const uint32_t *dst,
                          unsigned long long n, const LaunchCfg &lc) {
     const int ph = mode == MODE_INSERT ? PH_INS_COUNT : mode == MODE_DELETE ? PH_DEL_COUNT : PH_QRY_COUNT;
-    if (n >= (unsigned long long)g.nv / 8) {
+    if (n >= ((unsigned long long)g.nv >> g.dense_shift)) {
         // large batch: per-pair atomics, then a pass over all vertices
         const int grid = grid_for(n, 256 * 8, lc.num_sms * GRID_MULT);
         {
@@ -1452,4 +1538,21 @@ cudaError_t launch_vertex_delete(const GraphView &g, const uint32_t *ids, uint32
     return cudaGetLastError();
 }
 
+}  // namespace gv
+
+namespace gv {
+cudaError_t launch_set_remap(const GraphView &g, const uint32_t *src, const uint32_t *dst, unsigned long long n,
+                             uint32_t *gsrc, uint32_t *gdst, const LaunchCfg &lc) {
+    if (n == 0) return cudaSuccess;
+    PhaseScope ps(lc, PH_OTHER);
+    unsigned long long blocks = (n + 2047) / 2048;
+    const unsigned long long cap = (unsigned long long)lc.num_sms * GRID_MULT;
+    if (blocks > cap) blocks = cap;
+    k_set_remap<<<(int)blocks, 256, 0, lc.stream>>>(g, src, dst, n, gsrc, gdst);
+    return cudaGetLastError();
+}
+cudaError_t launch_set_insert_counts(const GraphView &g, const LaunchCfg &lc) {
+    k_set_insert_counts<<<(g.set_G + 255) / 256, 256, 0, lc.stream>>>(g);
+    return cudaGetLastError();
+}
 }  // namespace gv

@@ -104,6 +104,10 @@ cudaError_t launch_neighbor_copy(const GraphView &g, const uint32_t *vids, uint3
 cudaError_t launch_degrees(const GraphView &g, uint32_t *deg, uint8_t *alive,
                            const LaunchCfg &lc);
 cudaError_t launch_iota(uint32_t *out, uint32_t first, uint32_t k, const LaunchCfg &lc);
+// Graph sets: member batches -> one global batch; per-member insert counts.
+cudaError_t launch_set_remap(const GraphView &g, const uint32_t *src, const uint32_t *dst, unsigned long long n,
+                             uint32_t *gsrc, uint32_t *gdst, const LaunchCfg &lc);
+cudaError_t launch_set_insert_counts(const GraphView &g, const LaunchCfg &lc);
 cudaError_t launch_validate(const GraphView &g, uint32_t *owner_bits,
                             unsigned long long *violations, const LaunchCfg &lc);
 

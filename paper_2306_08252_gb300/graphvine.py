@@ -34,6 +34,8 @@ class gv_config(ctypes.Structure):
         ("pool_bytes", c_u64),
         ("pool_mem", c_vp),
         ("vertex_capacity", c_u32),
+        ("item_blocks", c_u32),
+        ("dense_shift", c_u32),
         ("reserved", c_u32),
     ]
 
@@ -84,6 +86,11 @@ SIGNATURES = {
     "gv_profile_num_phases": ([], c_u32),
     "gv_profile_phase_name": ([c_u32], ctypes.c_char_p),
     "gv_degree_offsets_noalloc": ([c_vp, c_vp, c_u32, c_vp, c_vp], ctypes.c_int),
+    "gv_set_create": ([ctypes.POINTER(gv_config), c_u32, c_vp, c_vp, ctypes.POINTER(c_vp)], ctypes.c_int),
+    "gv_set_insert_edges": ([c_vp, c_vp, c_vp, c_u64, c_vp, c_vp, c_vp], ctypes.c_int),
+    "gv_set_delete_edges": ([c_vp, c_vp, c_vp, c_u64, c_vp, c_vp, c_vp], ctypes.c_int),
+    "gv_set_query_edges": ([c_vp, c_vp, c_vp, c_u64, c_vp, c_vp, c_vp, c_vp], ctypes.c_int),
+    "gv_set_member_neighbors": ([c_vp, c_u32, c_vp, c_vp, c_u64, ctypes.POINTER(c_u64), c_vp], ctypes.c_int),
 }
 
 _lib = None
@@ -158,8 +165,8 @@ def current_stream():
 # -------------------------------------------------------- C-named wrappers
 
 def gv_create(num_vertices, block_capacity=0, pool_bytes=0, pool_mem=None, flags=0, vertex_capacity=0,
-              stream=None):
-    cfg = gv_config(block_capacity, flags, pool_bytes, ptr(pool_mem), vertex_capacity, 0)
+              stream=None, item_blocks=0, dense_shift=0):
+    cfg = gv_config(block_capacity, flags, pool_bytes, ptr(pool_mem), vertex_capacity, item_blocks, dense_shift, 0)
     h = c_vp()
     check(load().gv_create(ctypes.byref(cfg), num_vertices, stream, ctypes.byref(h)), "gv_create")
     return h.value
@@ -258,17 +265,89 @@ def gv_profile_read(g):
     return {lib.gv_profile_phase_name(i).decode(): (float(ms[i]), int(cnt[i])) for i in range(n)}
 
 
+class GraphSet:
+    """Many member graphs in one device structure (gv_set_*)."""
+
+    def __init__(self, num_vertices, block_capacity, pool_bytes=0, stream=None, item_blocks=0, dense_shift=0):
+        nv = np.ascontiguousarray(num_vertices, dtype=np.uint32)
+        self.num_vertices = nv
+        self.stream = stream
+        cfg = gv_config(block_capacity, 0, pool_bytes, None, 0, item_blocks, dense_shift, 0)
+        h = c_vp()
+        check(load().gv_set_create(ctypes.byref(cfg), nv.size, nv.ctypes.data, self._s(), ctypes.byref(h)),
+              "gv_set_create")
+        self.handle = h.value
+
+    def _s(self):
+        return self.stream if self.stream is not None else current_stream()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            gv_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def insert_edges(self, d_src, d_dst, d_offsets, d_counts):
+        check(load().gv_set_insert_edges(self.handle, ptr(d_src), ptr(d_dst), _len(d_src), ptr(d_offsets),
+                                         ptr(d_counts), self._s()), "gv_set_insert_edges")
+
+    def delete_edges(self, d_src, d_dst, d_offsets, d_counts):
+        check(load().gv_set_delete_edges(self.handle, ptr(d_src), ptr(d_dst), _len(d_src), ptr(d_offsets),
+                                         ptr(d_counts), self._s()), "gv_set_delete_edges")
+
+    def query_edges(self, d_src, d_dst, d_offsets, d_counts, d_out):
+        check(load().gv_set_query_edges(self.handle, ptr(d_src), ptr(d_dst), _len(d_src), ptr(d_offsets),
+                                        ptr(d_counts), ptr(d_out), self._s()), "gv_set_query_edges")
+
+    def member_csr(self, member):
+        nv = int(self.num_vertices[member])
+        off = np.zeros(nv + 1, dtype=np.uint64)
+        total = c_u64(0)
+        lib = load()
+        code = lib.gv_set_member_neighbors(self.handle, member, off.ctypes.data, None, 0, ctypes.byref(total),
+                                           self._s())
+        nb = np.zeros(max(total.value, 1), dtype=np.uint32)
+        check(lib.gv_set_member_neighbors(self.handle, member, off.ctypes.data, nb.ctypes.data, nb.size,
+                                          ctypes.byref(total), self._s()), "gv_set_member_neighbors")
+        return off, nb[:total.value]
+
+    def reserve(self, max_batch):
+        gv_reserve(self.handle, max_batch)
+
+    def sync(self):
+        return check(gv_sync(self.handle), "device status")
+
+    def stats(self):
+        code, st = gv_stats(self.handle)
+        check(code, "device status")
+        return st
+
+    def validate(self):
+        return gv_validate(self.handle, self._s())
+
+    def profile(self, enable=True):
+        gv_profile(self.handle, enable)
+
+    def profile_read(self):
+        return gv_profile_read(self.handle)
+
+
 # -------------------------------------------------------------- convenience
 
 class Graph:
     """A device-resident GraphVine graph (see include/graphvine.h)."""
 
     def __init__(self, num_vertices, block_capacity=0, pool_bytes=0, pool_mem=None, flags=0,
-                 vertex_capacity=0, stream=None):
+                 vertex_capacity=0, stream=None, item_blocks=0, dense_shift=0):
         self.stream = stream
         self._pool_ref = pool_mem  # keep a caller-owned pool alive
         self.handle = gv_create(num_vertices, block_capacity, pool_bytes, pool_mem, flags, vertex_capacity,
-                                self._s())
+                                self._s(), item_blocks, dense_shift)
 
     def _s(self):
         if self.stream is not None:

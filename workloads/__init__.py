@@ -246,3 +246,46 @@ def er_mixed(seed: int = 3, nv: int = 1 << 22, base_edges: int = 16_777_216, rou
     ed = live[pick]
     ops.append(Batch("insert", es, ed))
     return {"nv": nv, "bulk": (bs, bd), "ops": ops}
+
+
+def batched_rmat(seed: int = 4, graphs: int = 256, xlo: float = 10.0, xhi: float = 18.0, avg_degree: int = 8,
+                 smax: float = 1e6, abcd=RMAT_ABCD):
+    """Many independent RMAT graphs with uneven update batches.
+
+    Member i: x ~ U(xlo, xhi), V = round(2^x) vertices (RMAT at scale
+    ceil(x), ids >= V redrawn), E = avg_degree * V base edges; an insert batch
+    of s fresh RMAT pairs and a delete batch of s pairs (half distinct pairs
+    of the base graph, half pairs absent from it and from the insert batch),
+    s = round(exp(U(0, ln smax))).  Returns a list of dicts with member-local
+    ids."""
+    xs = xlo + (xhi - xlo) * uniform_f64(seed, 0, graphs)
+    ls = np.log(smax) * uniform_f64(seed, 1, graphs)
+    out = []
+    for i in range(graphs):
+        x = float(xs[i])
+        nv = max(2, int(round(2.0 ** x)))
+        scale = int(np.ceil(np.log2(nv)))
+        e = avg_degree * nv
+        bs, bd = rmat_pairs(seed, 100 + i, e, scale, abcd, limit=nv)
+        s = max(1, int(round(np.exp(ls[i]))))
+        ins_s, ins_d = rmat_pairs(seed, 100_000 + i, s, scale, abcd, limit=nv)
+        base_keys = np.unique(keys(bs, bd))
+        ex = shuffled(seed, 200_000 + i, base_keys)[:s // 2]
+        es, ed = unkey(ex)
+        as_, ad = absent_pairs(seed, 300_000 + i, s - es.size, nv,
+                               np.concatenate([base_keys, keys(ins_s, ins_d)]))
+        ds = np.concatenate([es, as_])
+        dd = np.concatenate([ed, ad])
+        order = shuffled(seed, 400_000 + i, np.arange(ds.size, dtype=np.uint32))
+        out.append({"nv": nv, "bulk": (bs, bd), "insert": (ins_s, ins_d), "delete": (ds[order], dd[order])})
+    return out
+
+
+def concat_member_batches(members, key):
+    """Concatenate one batch kind over members: (src, dst, offsets[G+1])."""
+    parts = [m[key] for m in members]
+    off = np.zeros(len(parts) + 1, dtype=np.uint64)
+    off[1:] = np.cumsum([p[0].size for p in parts])
+    src = np.concatenate([p[0] for p in parts]).astype(np.uint32) if parts else np.zeros(0, np.uint32)
+    dst = np.concatenate([p[1] for p in parts]).astype(np.uint32) if parts else np.zeros(0, np.uint32)
+    return src, dst, off
