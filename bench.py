@@ -52,7 +52,9 @@ def parse():
     ap.add_argument("--queries", type=int, default=QUERIES)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="rmat", choices=["rmat", "batched"],
+    ap.add_argument("--requests", type=int, default=10_000)
+    ap.add_argument("--serve-scale", type=int, default=24)
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "batched", "serving"],
                     help="rmat: the single-graph step (default); batched: many member graphs, "
                          "one captured launch sequence vs one launch sequence per graph")
     ap.add_argument("--graphs", type=int, default=256)
@@ -515,10 +517,73 @@ def run_batched(args):
     return 0
 
 
+def run_serving(args):
+    """Serving: RMAT 2^24 vertices / 2^28 edges resident on the device;
+    requests of mixed kind (40% insert, 40% delete of base edges, 20% query),
+    sizes log-uniform in 1..1M, Poisson arrivals at 50% and 90% of the
+    measured saturated capacity; the first 10% of each stream is warm-up.
+    Latency = completion observed by the loop - arrival."""
+    import torch
+    import workloads as W
+    import paper_2306_08252_gb300 as gv
+    from paper_2306_08252_gb300 import serve
+
+    torch.cuda.set_device(0)
+    scale, C = args.serve_scale, 16
+    edges = 1 << (scale + 4)
+    t_gen = time.perf_counter()
+    bs, bd = W.rmat_pairs(5, 0, edges, scale)
+    reqs, gaps = W.serving_requests(5, bs, bd, scale, args.requests)
+    cap_reqs, _ = W.serving_requests(6, bs, bd, scale, max(args.requests // 10, 100))
+    t_gen = time.perf_counter() - t_gen
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
+    blocks = edges // C * 2 + (1 << scale) + (1 << 22)
+    g = gv.Graph(1 << scale, block_capacity=C, pool_bytes=int(blocks * (4 * C + 12)))
+    g.bulk_build(dev(bs), dev(bd))
+    g.sync()
+    server = serve.Server(g, C, slots=4, merge_pairs=2_000_000, max_reqs=1024)
+    # saturated capacity (all requests present at time 0)
+    crs = [serve.Request(k, a, b, 0.0) for k, a, b in cap_reqs]
+    t0 = time.perf_counter()
+    server.run(crs, realtime=False)
+    cap = len(crs) / (time.perf_counter() - t0)
+    levels = []
+    for load in (0.5, 0.9):
+        rate = load * cap
+        arrivals = np.cumsum(gaps) / rate
+        rs = [serve.Request(k, a, b, t) for (k, a, b), t in zip(reqs, arrivals)]
+        runs0, merged0 = server.runs, server.merged_requests
+        server.run(rs, realtime=True)
+        skip = len(rs) // 10
+        meas = [r for r in rs[skip:] if r.status == gv.GV_OK]
+        upd = sum(len(r) for r in meas if r.kind in (serve.INSERT, serve.DELETE))
+        span = max(r.done for r in meas) - min(r.arrival for r in meas)
+        lat = serve.latency_stats(rs, skip=skip)
+        levels.append({"load": load, "rate_req_per_s": rate, "p50_ms": lat["p50_ms"], "p99_ms": lat["p99_ms"],
+                       "mean_ms": lat["mean_ms"], "updates_per_s": upd / span, "requests": len(rs),
+                       "warmup_requests": skip, "runs": server.runs - runs0,
+                       "requests_per_run": (server.merged_requests - merged0) / max(server.runs - runs0, 1),
+                       "failed": sum(1 for r in rs if r.status != gv.GV_OK)})
+    assert g.sync() == 0
+    st = g.stats()
+    g.close()
+    res = {"metric": "serving: p50/p99 latency and edge updates/s under Poisson load",
+           "value": levels[-1]["updates_per_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+           "data": "synthetic (seeded RMAT graph and request stream)",
+           "config": {"workload": f"RMAT scale {scale} ({1 << scale} vertices, {edges} edges), C={C}; "
+                                  f"{args.requests} requests, 40/40/20 insert/delete/query, sizes log-uniform 1..1M",
+                      "slots": 4, "merge_pairs": 2_000_000, "generation_s": t_gen},
+           "capacity_req_per_s": cap, "levels": levels, "final_edges": st["num_edges"]}
+    print(json.dumps(res), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

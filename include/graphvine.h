@@ -274,6 +274,19 @@ uint32_t gv_profile_num_phases(void);
 const char *gv_profile_phase_name(uint32_t phase);
 
 /*
+ * gv_insert_edges_segmented -- gv_insert_edges on a batch made of nseg
+ * requests (pairs d_offsets[i] .. d_offsets[i+1]-1 belong to request i), with
+ * per-request counts: d_counts[2i] = inserted, d_counts[2i+1] = rejected.
+ * The result equals inserting the requests one after another (multiset
+ * inserts commute), which lets a server merge queued insert requests into
+ * one launch sequence.  nseg in 1 .. 1024; all arrays device memory; the
+ * graph's C must already be fixed (after gv_bulk_build or with a configured
+ * C).
+ */
+gv_status gv_insert_edges_segmented(gv_graph *g, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
+                                    const uint64_t *d_offsets, uint32_t nseg, uint64_t *d_counts, void *stream);
+
+/*
  * Graph sets: many independent graphs ("members") in one device structure
  * that shares one dictionary (members own consecutive vertex ranges), one
  * block pool and one scratch area, so that an update touching every member

@@ -1015,6 +1015,29 @@ gv_status set_batch(gv_graph *g, int mode, const uint32_t *src, const uint32_t *
 
 extern "C" {
 
+gv_status gv_insert_edges_segmented(gv_graph *g, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
+                                    const uint64_t *d_offsets, uint32_t nseg, uint64_t *d_counts, void *stream) {
+    if (!g || g->set_G || nseg == 0 || nseg > gv::SET_MAX_G || !d_offsets || !d_counts) return GV_ERR_INVALID_ARG;
+    if (n > kMaxBatch || (n > 0 && (!d_src || !d_dst))) return GV_ERR_INVALID_ARG;
+    if (g->flags & GV_DEDUP) return GV_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    if (is_host_ptr(d_offsets) || is_host_ptr(d_counts) || (n > 0 && (is_host_ptr(d_src) || is_host_ptr(d_dst))))
+        return GV_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    g->last_stream = s;
+    GV_CK(cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * 2 * nseg, s));
+    if (n == 0) return check_launch();
+    if (g->C == 0) return GV_ERR_STATE;  // the first edge batch fixes C: use gv_bulk_build
+    GraphView v = view(g);
+    v.set_G = nseg;
+    v.set_off = reinterpret_cast<const unsigned long long *>(d_offsets);
+    v.set_counts = reinterpret_cast<unsigned long long *>(d_counts);
+    GV_CK(gv::launch_segment_counts(v, d_src, d_dst, n, lcfg(g, s)));
+    GV_CK(gv::launch_set_insert_counts(v, lcfg(g, s)));
+    GV_TRY(insert_impl(g, d_src, d_dst, n, nullptr, s));
+    return check_launch();
+}
+
 gv_status gv_set_create(const gv_config *cfg, uint32_t num_graphs, const uint32_t *num_vertices, void *stream,
                         gv_graph **out) {
     if (!out || num_graphs == 0 || num_graphs > gv::SET_MAX_G || !num_vertices) return GV_ERR_INVALID_ARG;

@@ -1385,6 +1385,38 @@ __global__ void __launch_bounds__(256) k_set_remap(GraphView g, const uint32_t *
         if (s_rej[i]) atomicAdd(&g.set_counts[2 * i + 1], (unsigned long long)s_rej[i]);
 }
 
+// Per-segment counts of a batch made of several requests on one graph:
+// {valid pairs, rejected pairs} per segment (segments = consecutive pair
+// ranges, offsets in set_off; multiset inserts insert every valid pair).
+__global__ void __launch_bounds__(256) k_segment_counts(GraphView g, const uint32_t *__restrict__ src,
+                                                        const uint32_t *__restrict__ dst, unsigned long long n) {
+    __shared__ unsigned long long s_off[SET_MAX_G + 1];
+    __shared__ uint32_t s_rej[SET_MAX_G];
+    const uint32_t G = g.set_G;
+    for (uint32_t i = threadIdx.x; i <= G; i += blockDim.x) {
+        s_off[i] = g.set_off[i];
+        if (i < G) s_rej[i] = 0;
+    }
+    __syncthreads();
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t u = src[i], v = dst[i];
+        const bool ok = u < g.nv && v < g.nv && (g.all_alive || (g.alive[u] && g.alive[v]));
+        if (!ok) {
+            uint32_t lo = 0, hi = G;
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (s_off[mid] <= i) lo = mid;
+                else hi = mid;
+            }
+            atomicAdd(&s_rej[lo], 1u);
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < G; i += blockDim.x)
+        if (s_rej[i]) atomicAdd(&g.set_counts[2 * i + 1], (unsigned long long)s_rej[i]);
+}
+
 // Inserted pairs per member (multiset): its batch size minus its rejects.
 __global__ void k_set_insert_counts(GraphView g) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < g.set_G; i += gridDim.x * blockDim.x)
@@ -1549,6 +1581,15 @@ cudaError_t launch_set_remap(const GraphView &g, const uint32_t *src, const uint
     const unsigned long long cap = (unsigned long long)lc.num_sms * GRID_MULT;
     if (blocks > cap) blocks = cap;
     k_set_remap<<<(int)blocks, 256, 0, lc.stream>>>(g, src, dst, n, gsrc, gdst);
+    return cudaGetLastError();
+}
+cudaError_t launch_segment_counts(const GraphView &g, const uint32_t *src, const uint32_t *dst,
+                                  unsigned long long n, const LaunchCfg &lc) {
+    if (n == 0) return cudaSuccess;
+    unsigned long long blocks = (n + 2047) / 2048;
+    const unsigned long long cap = (unsigned long long)lc.num_sms * GRID_MULT;
+    if (blocks > cap) blocks = cap;
+    k_segment_counts<<<(int)blocks, 256, 0, lc.stream>>>(g, src, dst, n);
     return cudaGetLastError();
 }
 cudaError_t launch_set_insert_counts(const GraphView &g, const LaunchCfg &lc) {

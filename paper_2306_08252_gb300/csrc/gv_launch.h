@@ -108,6 +108,8 @@ cudaError_t launch_iota(uint32_t *out, uint32_t first, uint32_t k, const LaunchC
 cudaError_t launch_set_remap(const GraphView &g, const uint32_t *src, const uint32_t *dst, unsigned long long n,
                              uint32_t *gsrc, uint32_t *gdst, const LaunchCfg &lc);
 cudaError_t launch_set_insert_counts(const GraphView &g, const LaunchCfg &lc);
+cudaError_t launch_segment_counts(const GraphView &g, const uint32_t *src, const uint32_t *dst,
+                                  unsigned long long n, const LaunchCfg &lc);
 cudaError_t launch_validate(const GraphView &g, uint32_t *owner_bits,
                             unsigned long long *violations, const LaunchCfg &lc);
 

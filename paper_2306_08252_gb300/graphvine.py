@@ -86,6 +86,7 @@ SIGNATURES = {
     "gv_profile_num_phases": ([], c_u32),
     "gv_profile_phase_name": ([c_u32], ctypes.c_char_p),
     "gv_degree_offsets_noalloc": ([c_vp, c_vp, c_u32, c_vp, c_vp], ctypes.c_int),
+    "gv_insert_edges_segmented": ([c_vp, c_vp, c_vp, c_u64, c_vp, c_u32, c_vp, c_vp], ctypes.c_int),
     "gv_set_create": ([ctypes.POINTER(gv_config), c_u32, c_vp, c_vp, ctypes.POINTER(c_vp)], ctypes.c_int),
     "gv_set_insert_edges": ([c_vp, c_vp, c_vp, c_u64, c_vp, c_vp, c_vp], ctypes.c_int),
     "gv_set_delete_edges": ([c_vp, c_vp, c_vp, c_u64, c_vp, c_vp, c_vp], ctypes.c_int),
@@ -249,6 +250,11 @@ def gv_validate(g, stream=None):
 def gv_degree_offsets_noalloc(g, d_vids, d_offsets, stream=None):
     """Degree offsets of the listed vertices with no allocation (device arrays only)."""
     return load().gv_degree_offsets_noalloc(g, ptr(d_vids), _len(d_vids), ptr(d_offsets), stream)
+
+
+def gv_insert_edges_segmented(g, d_src, d_dst, d_offsets, nseg, d_counts, stream=None):
+    return check(load().gv_insert_edges_segmented(g, ptr(d_src), ptr(d_dst), _len(d_src), ptr(d_offsets), nseg,
+                                                  ptr(d_counts), stream), "gv_insert_edges_segmented")
 
 
 def gv_profile(g, enable):

@@ -289,3 +289,31 @@ def concat_member_batches(members, key):
     src = np.concatenate([p[0] for p in parts]).astype(np.uint32) if parts else np.zeros(0, np.uint32)
     dst = np.concatenate([p[1] for p in parts]).astype(np.uint32) if parts else np.zeros(0, np.uint32)
     return src, dst, off
+
+
+def serving_requests(seed: int, base_src, base_dst, scale: int, n_requests: int, smax: float = 1e6,
+                     mix=(0.4, 0.4, 0.2), abcd=RMAT_ABCD):
+    """Request stream for the serving loop: kinds drawn with probabilities
+    mix = (insert, delete, query); sizes s = round(exp(U(0, ln smax)));
+    inserts are fresh RMAT pairs, deletes pairs sampled from the base graph
+    (present unless an earlier request removed them), queries half base
+    pairs, half RMAT pairs.  Also returns unit-mean exponential gaps (scale
+    them by 1 / rate for Poisson arrivals)."""
+    u = uniform_f64(seed, 0, n_requests)
+    ls = np.log(smax) * uniform_f64(seed, 1, n_requests)
+    gaps = -np.log(1.0 - uniform_f64(seed, 2, n_requests))
+    reqs = []
+    for i in range(n_requests):
+        s = max(1, int(round(np.exp(ls[i]))))
+        if u[i] < mix[0]:
+            a, b = rmat_pairs(seed, 10_000 + i, s, scale, abcd)
+            reqs.append(("insert", a, b))
+        elif u[i] < mix[0] + mix[1]:
+            idx = sample_indices(seed, 20_000 + i, base_src.size, s)
+            reqs.append(("delete", base_src[idx], base_dst[idx]))
+        else:
+            h = s // 2
+            idx = sample_indices(seed, 30_000 + i, base_src.size, h)
+            a, b = rmat_pairs(seed, 40_000 + i, s - h, scale, abcd)
+            reqs.append(("query", np.concatenate([base_src[idx], a]), np.concatenate([base_dst[idx], b])))
+    return reqs, gaps
