@@ -22,7 +22,7 @@ using gv::LaunchCfg;
 
 namespace {
 
-constexpr uint64_t kMaxBatch = 1ull << 30;  // pairs per call (32-bit ranks and arena offsets)
+constexpr uint64_t kMaxBatch = 1ull << 29;  // pairs per call (32-bit ranks and arena offsets: 5n words)
 
 struct DevBuf {
     void *p = nullptr;
@@ -174,6 +174,7 @@ GraphView view(const gv_graph *g) {
     v.it_S = g->it_S;
     v.it_bid = g->it_bid;
     v.arena = g->arena;
+    v.hbase = 0;
     v.found = g->found;
     v.qpos = g->qpos;
     v.dead = g->dead;
@@ -421,7 +422,7 @@ gv_status ensure_batch(gv_graph *g, uint64_t n, int mode) {
         GV_TRY(ensure_owner(g, (g->C ? n / g->C : n) + touched + 1));
     } else {
         GV_TRY(ensure_items(g, item_bound(g, touched)));
-        GV_TRY(ensure_arena(g, 4 * n + 64, mode == gv::MODE_QUERY, n));
+        GV_TRY(ensure_arena(g, 5 * n + 128, mode == gv::MODE_QUERY, n));
     }
     return GV_OK;
 }
@@ -814,7 +815,7 @@ gv_status gv_reserve(gv_graph *g, uint64_t max_batch) {
     GV_TRY(ensure_touched(g, std::min<unsigned long long>(max_batch, g->nv ? g->nv : 1)));
     GV_TRY(ensure_owner(g, (g->C ? max_batch / g->C : max_batch) + std::min<unsigned long long>(max_batch, g->nv) + 1));
     if (g->C) GV_TRY(ensure_items(g, item_bound(g, std::min<unsigned long long>(max_batch, g->nv ? g->nv : 1))));
-    GV_TRY(ensure_arena(g, 4 * max_batch + 64, true, max_batch));
+    GV_TRY(ensure_arena(g, 5 * max_batch + 128, true, max_batch));
     GV_TRY(ensure_ranks(g, max_batch));
     if (g->set_G && (max_batch > g->scap || !g->scap)) {
         dfree(g->set_src);

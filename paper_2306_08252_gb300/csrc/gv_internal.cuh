@@ -46,6 +46,7 @@ struct Dev {
     unsigned int abort;             // set when this call must not mutate the graph
     unsigned int n_tiny;            // touched sources handled one per thread
     unsigned int pad[2];
+    unsigned long long harena_used; // words of the arena's hash region used
 };
 
 // Everything a kernel needs to know about one graph (passed by value).
@@ -83,7 +84,8 @@ struct GraphView {
     uint32_t *it_S;         // exclusive prefix of survivors at/above the new degree
     uint32_t *it_bid;       // IB block ids per item
     // membership arena
-    uint32_t *arena;        // list entries / hash keys
+    uint32_t *arena;        // list entries, then (from hbase) bucketed hash sets
+    uint32_t hbase;         // first word of the hash region (a multiple of 64)
     uint32_t *found;        // query: hit flags, parallel to arena
     uint32_t *qpos;         // query: arena position of each query (NIL if invalid)
     uint32_t *dead;         // vertex delete: bitmap of deleted ids
@@ -114,12 +116,15 @@ enum Mode : int { MODE_INSERT = 0, MODE_DELETE = 1, MODE_QUERY = 2, MODE_VDEL = 
 
 // A source's batch destinations are kept as a plain list up to LIST_MAX
 // entries (tested through a shared-memory hash set built per work item) and
-// as an open-addressing hash set in the arena above it.
+// as a bucketed hash set in the arena above it: buckets of HB = 8 words (one
+// 32-byte sector), so an insert or a lookup reads its whole bucket in one
+// round trip and only a full bucket sends it to the next one.
 constexpr uint32_t LIST_MAX = 256;
+constexpr uint32_t HB = 8;
 // Tiny adjacencies (one thread per source): at most TINY_DEG entries in at
 // most TINY_NB blocks, at most TINY_M batch entries.
-constexpr uint32_t TINY_DEG = 64;
-constexpr uint32_t TINY_NB = 4;
+constexpr uint32_t TINY_DEG = 128;
+constexpr uint32_t TINY_NB = 8;
 constexpr uint32_t TINY_M = 16;
 
 // Arena words of a source with m batch entries: m (list) or the hash set

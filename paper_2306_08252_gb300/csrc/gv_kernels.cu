@@ -506,6 +506,7 @@ __global__ void __launch_bounds__(256) k_finalize_insert(GraphView g, unsigned l
         dev->n_items = 0;
         dev->n_tiny = 0;
         dev->arena_used = 0;
+        dev->harena_used = 0;
         dev->free_total = 0;
         dev->abort = 0;
         dev->done_ctas = 0;
@@ -529,38 +530,43 @@ __global__ void __launch_bounds__(256) k_plan_member(GraphView g) {
     const uint32_t nt = g.dev->n_touched;
     const uint32_t IB = g.IB;
     const uint32_t tiny_deg = min(TINY_DEG, TINY_NB * g.C);
-    __shared__ unsigned long long s_aw;
+    __shared__ unsigned long long s_aw, s_hw;
     __shared__ uint32_t s_ai, s_at;
     for (uint32_t base = blockIdx.x * blockDim.x; base < nt; base += gridDim.x * blockDim.x) {
         const uint32_t t = base + threadIdx.x;
-        uint32_t m = 0, words = 0, ni = 0, tiny = 0;
+        uint32_t m = 0, lw = 0, hw = 0, ni = 0, tiny = 0;
         uint4 s = make_uint4(0, 0, NIL, NIL);
         if (t < nt) {
             const uint32_t u = g.t_vid[t];
             m = g.vcnt[vslot(g.vmask, u)];
             s = g.sent[u];
-            words = member_words(m);
+            if (m <= LIST_MAX) lw = m;
+            else hw = member_words(m);
             if (s.y > 0) {
                 if (s.x <= tiny_deg && s.y <= TINY_NB && m <= TINY_M) tiny = 1;
                 else ni = (s.y + IB - 1) / IB;
             }
         }
-        uint32_t wt, itot, ttot;
-        const uint32_t wex = block_excl_scan(words, &wt);
+        uint32_t lt, ht, itot, ttot;
+        const uint32_t lex = block_excl_scan(lw, &lt);
+        const uint32_t hex = block_excl_scan(hw, &ht);
         const uint32_t iex = block_excl_scan(ni, &itot);
         const uint32_t tex = block_excl_scan(tiny, &ttot);
         if (threadIdx.x == 0) {
-            s_aw = wt ? atomicAdd(&g.dev->arena_used, (unsigned long long)wt) : 0ull;
+            s_aw = lt ? atomicAdd(&g.dev->arena_used, (unsigned long long)lt) : 0ull;
+            s_hw = ht ? atomicAdd(&g.dev->harena_used, (unsigned long long)ht) : 0ull;
             s_ai = itot ? atomicAdd(&g.dev->n_items, itot) : 0u;
             s_at = ttot ? atomicAdd(&g.dev->n_tiny, ttot) : 0u;
         }
         __syncthreads();
         if (t < nt) {
             const uint32_t item0 = s_ai + iex;
-            const uint32_t aoff = (uint32_t)(s_aw + wex);
-            g.t_a[t] = make_uint4(m, aoff, m <= LIST_MAX ? 0u : words, item0);
+            // hash sets are powers of two >= 512 words, so their offsets stay
+            // multiples of 512 words: every bucket is sector-aligned
+            const uint32_t aoff = hw ? (uint32_t)(g.hbase + s_hw + hex) : (uint32_t)(s_aw + lex);
+            g.t_a[t] = make_uint4(m, aoff, hw, item0);
             g.t_b[t] = make_uint4(s.x, s.y, s.z, ni);
-            g.vinfo[vslot(g.vmask, g.t_vid[t])] = make_uint4(m, aoff, 0u, 0u);
+            g.vinfo[vslot(g.vmask, g.t_vid[t])] = make_uint4(m, aoff, hw, 0u);
             if (tiny) g.t_tiny[s_at + tex] = t;
             emit_items(g, t, item0, ni);
         }
@@ -570,11 +576,19 @@ __global__ void __launch_bounds__(256) k_plan_member(GraphView g) {
 
 template <int MODE>
 __global__ void __launch_bounds__(256) k_arena_init(GraphView g) {
-    const unsigned long long used = g.dev->arena_used;
-    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < used;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        g.arena[i] = EMPTY_KEY;
-        if (MODE == MODE_QUERY) g.found[i] = 0u;
+    // hash region -> EMPTY; query hit flags of both regions -> 0 (list
+    // entries are all overwritten by the scatter)
+    const unsigned long long lused = g.dev->arena_used, hused = g.dev->harena_used;
+    const unsigned long long tot = (MODE == MODE_QUERY ? lused : 0ull) + hused;
+    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < tot;
+         k += (unsigned long long)gridDim.x * blockDim.x) {
+        if (MODE == MODE_QUERY && k < lused) {
+            g.found[k] = 0u;
+        } else {
+            const unsigned long long i = g.hbase + (k - (MODE == MODE_QUERY ? lused : 0ull));
+            g.arena[i] = EMPTY_KEY;
+            if (MODE == MODE_QUERY) g.found[i] = 0u;
+        }
     }
 }
 
@@ -596,42 +610,73 @@ __global__ void __launch_bounds__(256) k_scatter_member(GraphView g, const uint3
             u[j] = i < n ? ld_stream(src + i) : 0u;
             v[j] = i < n ? ld_stream(dst + i) : 0u;
         }
-        uint32_t m[PP], aoff[PP];
+        uint32_t aoff[PP], hs[PP];
 #pragma unroll
         for (int j = 0; j < PP; ++j) {
             if (r[j] != NIL) {
                 const uint4 vi = g.vinfo[vslot(g.vmask, u[j])];
-                m[j] = vi.x;
                 aoff[j] = vi.y;
+                hs[j] = vi.z;  // 0: list
             }
         }
-        uint32_t pos[PP], old[PP];
+        uint32_t pos[PP];
 #pragma unroll
         for (int j = 0; j < PP; ++j) {
             pos[j] = NIL;
-            old[j] = EMPTY_KEY;
-            if (r[j] != NIL) {
-                if (m[j] <= LIST_MAX) {
-                    pos[j] = aoff[j] + r[j];
-                    g.arena[pos[j]] = v[j];
-                } else {
-                    pos[j] = aoff[j] + (mix32(v[j]) & (member_words(m[j]) - 1));
-                    old[j] = atomicCAS(&g.arena[pos[j]], EMPTY_KEY, v[j]);
-                }
+            if (r[j] != NIL && hs[j] == 0) {
+                pos[j] = aoff[j] + r[j];
+                g.arena[pos[j]] = v[j];
+            }
+        }
+        // bucketed hash sets: read the home bucket of every pair (L2, not a
+        // possibly stale L1 line), then claim a slot by CAS
+        uint4 b0[PP], b1[PP];
+        uint32_t bk[PP];
+#pragma unroll
+        for (int j = 0; j < PP; ++j) {
+            if (r[j] != NIL && hs[j] != 0) {
+                bk[j] = mix32(v[j]) & (hs[j] / HB - 1);
+                const uint4 *bp = reinterpret_cast<const uint4 *>(g.arena + aoff[j] + bk[j] * HB);
+                b0[j] = __ldcg(bp);
+                b1[j] = __ldcg(bp + 1);
             }
         }
 #pragma unroll
         for (int j = 0; j < PP; ++j) {
-            if (r[j] != NIL && m[j] > LIST_MAX && old[j] != EMPTY_KEY && old[j] != v[j]) {
-                const uint32_t hs = member_words(m[j]);
+            if (r[j] != NIL && hs[j] != 0) {
+                const uint32_t nbk = hs[j] / HB;
                 uint32_t *tab = g.arena + aoff[j];
-                uint32_t h = (pos[j] - aoff[j] + 1) & (hs - 1);
-                for (uint32_t probe = 1; probe < hs; ++probe) {
-                    const uint32_t o = atomicCAS(&tab[h], EMPTY_KEY, v[j]);
-                    if (o == EMPTY_KEY || o == v[j]) break;
-                    h = (h + 1) & (hs - 1);
+                uint32_t b = bk[j];
+                uint32_t w[HB] = {b0[j].x, b0[j].y, b0[j].z, b0[j].w, b1[j].x, b1[j].y, b1[j].z, b1[j].w};
+                // each pass either ends, moves to the next bucket, or follows a
+                // slot taken by another insert: (HB + 1) * nbk passes suffice
+                for (uint32_t probe = 0; probe < (HB + 1) * nbk; ++probe) {
+                    uint32_t hit = NIL, empty = NIL;
+#pragma unroll
+                    for (uint32_t k = 0; k < HB; ++k) {
+                        if (hit == NIL && w[k] == v[j]) hit = k;
+                        if (empty == NIL && w[k] == EMPTY_KEY) empty = k;
+                    }
+                    if (hit != NIL) {
+                        pos[j] = aoff[j] + b * HB + hit;
+                        break;
+                    }
+                    if (empty != NIL) {
+                        const uint32_t old = atomicCAS(&tab[b * HB + empty], EMPTY_KEY, v[j]);
+                        if (old == EMPTY_KEY || old == v[j]) {
+                            pos[j] = aoff[j] + b * HB + empty;
+                            break;
+                        }
+                        // lost the slot: reread this bucket
+                    } else {
+                        b = (b + 1) & (nbk - 1);
+                    }
+                    const uint4 *bp = reinterpret_cast<const uint4 *>(tab + b * HB);
+                    const uint4 x0 = __ldcg(bp), x1 = __ldcg(bp + 1);
+                    w[0] = x0.x; w[1] = x0.y; w[2] = x0.z; w[3] = x0.w;
+                    w[4] = x1.x; w[5] = x1.y; w[6] = x1.z; w[7] = x1.w;
                 }
-                pos[j] = aoff[j] + h;
+                if (pos[j] == NIL) latch_status(g.dev, 5u /* GV_ERR_STATE */);
             }
         }
         if (MODE == MODE_QUERY) {
@@ -752,26 +797,45 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
                     }
                 }
             } else {
-                // global hash set: the home slots of all four entries are
-                // loaded together; only collisions probe further
+                // global bucketed hash set: the home buckets of all four
+                // entries are loaded together; only a full bucket without the
+                // key sends a lookup on to the next bucket
                 const uint32_t *tab = g.arena + a.y;
-                const uint32_t hm = a.z - 1;
-                uint32_t hh[4], kk[4];
+                const uint32_t nbk = a.z / HB;
+                uint4 x0[4], x1[4];
+                uint32_t bk[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    hh[j] = mix32(e[j]) & hm;
-                    kk[j] = ((vmask >> j) & 1u) ? tab[hh[j]] : EMPTY_KEY;
+                    bk[j] = mix32(e[j]) & (nbk - 1);
+                    if ((vmask >> j) & 1u) {
+                        const uint4 *bp = reinterpret_cast<const uint4 *>(tab + bk[j] * HB);
+                        x0[j] = bp[0];
+                        x1[j] = bp[1];
+                    }
                 }
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     if ((vmask >> j) & 1u) {
-                        while (kk[j] != e[j] && kk[j] != EMPTY_KEY) {
-                            hh[j] = (hh[j] + 1) & hm;
-                            kk[j] = tab[hh[j]];
-                        }
-                        if (kk[j] == e[j]) {
-                            hitm |= 1u << j;
-                            if (MODE == MODE_QUERY) g.found[a.y + hh[j]] = 1u;
+                        for (uint32_t probe = 0; probe < nbk; ++probe) {
+                            const uint32_t w[HB] = {x0[j].x, x0[j].y, x0[j].z, x0[j].w,
+                                                    x1[j].x, x1[j].y, x1[j].z, x1[j].w};
+                            uint32_t hit = NIL;
+                            bool empty = false;
+#pragma unroll
+                            for (uint32_t k = 0; k < HB; ++k) {
+                                if (hit == NIL && w[k] == e[j]) hit = k;
+                                empty |= w[k] == EMPTY_KEY;
+                            }
+                            if (hit != NIL) {
+                                hitm |= 1u << j;
+                                if (MODE == MODE_QUERY) g.found[a.y + bk[j] * HB + hit] = 1u;
+                                break;
+                            }
+                            if (empty) break;
+                            bk[j] = (bk[j] + 1) & (nbk - 1);
+                            const uint4 *bp = reinterpret_cast<const uint4 *>(tab + bk[j] * HB);
+                            x0[j] = bp[0];
+                            x1[j] = bp[1];
                         }
                     }
                 }
@@ -851,13 +915,20 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
     }
 }
 
-// Tiny adjacencies, one thread per source: at most TINY_NB blocks and
+// Tiny adjacencies, one thread per source: at most TINY_NB (8) blocks and
 // min(TINY_DEG, TINY_NB * C) entries, at most TINY_M batch entries (held in
 // registers).  Delete / vertex delete compact in place (stable) and return
 // emptied blocks; query sets the hit flag of every matching batch entry.
-__device__ __forceinline__ uint32_t pick4(uint32_t i, uint32_t b0, uint32_t b1, uint32_t b2, uint32_t b3) {
-    return i == 0 ? b0 : (i == 1 ? b1 : (i == 2 ? b2 : b3));
-}
+struct Blocks8 {
+    uint32_t b[TINY_NB];
+    __device__ __forceinline__ uint32_t get(uint32_t i) const {
+        uint32_t r = b[0];
+#pragma unroll
+        for (uint32_t k = 1; k < TINY_NB; ++k)
+            if (i == k) r = b[k];
+        return r;
+    }
+};
 
 template <int MODE>
 __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
@@ -890,14 +961,22 @@ __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
             m = a.x;
             aoff = a.y;
         }
-        // heap 1 = root, 2 and 3 = its children, 4 = left child of 2
-        uint32_t b0 = root, b1 = NIL, b2 = NIL, b3 = NIL;
-        if (act && root < P && nb >= 2) {
-            b1 = g.links[2ull * root];
-            if (nb >= 3) b2 = g.links[2ull * root + 1];
+        // heap index h (1-based) lives in bl.b[h-1]; children of h are 2h, 2h+1
+        Blocks8 bl;
+#pragma unroll
+        for (uint32_t h = 0; h < TINY_NB; ++h) bl.b[h] = NIL;
+        bl.b[0] = root;
+        bool bad = act && root >= P;
+#pragma unroll
+        for (uint32_t h = 2; h <= TINY_NB; ++h) {
+            if (act && !bad && h <= nb) {
+                const uint32_t parent = bl.b[h / 2 - 1];
+                const uint32_t c = g.links[2ull * parent + (h & 1u)];
+                bl.b[h - 1] = c;
+                if (c >= P) bad = true;
+            }
         }
-        if (act && nb >= 4 && b1 < P) b3 = g.links[2ull * b1];
-        if (act && (b0 >= P || (nb >= 2 && b1 >= P) || (nb >= 3 && b2 >= P) || (nb >= 4 && b3 >= P))) {
+        if (bad) {
             latch_status(dev, 5u /* GV_ERR_STATE */);
             act = false;
         }
@@ -909,8 +988,7 @@ __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
         uint32_t w = 0;
         for (uint32_t x = 0; act && x < deg; x += 4) {
             const uint32_t bi = divc(g.cmul, x);
-            const uint32_t blk = pick4(bi, b0, b1, b2, b3);
-            const uint4 e4 = ld_stream4(reinterpret_cast<const uint4 *>(g.data + (size_t)blk * C + (x - bi * C)));
+            const uint4 e4 = ld_stream4(reinterpret_cast<const uint4 *>(g.data + (size_t)bl.get(bi) * C + (x - bi * C)));
             const uint32_t e[4] = {e4.x, e4.y, e4.z, e4.w};
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj) {
@@ -928,7 +1006,7 @@ __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
                     if (MODE != MODE_QUERY && !hit) {
                         if (w != x + jj) {
                             const uint32_t wi = divc(g.cmul, w);
-                            g.data[(size_t)pick4(wi, b0, b1, b2, b3) * C + (w - wi * C)] = e[jj];
+                            g.data[(size_t)bl.get(wi) * C + (w - wi * C)] = e[jj];
                         }
                         ++w;
                     }
@@ -944,17 +1022,16 @@ __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
         const bool changed = act && w != deg;
         const uint32_t nbn = divc(g.cmul, w + C - 1);
         // blocks past the new count return to the queue; a freed block's
-        // parent (still owned) forgets it
-        fs.push(changed && nb >= 4 && nbn < 4, b3, dev, g.queue, qbb, P);
-        fs.push(changed && nb >= 3 && nbn < 3, b2, dev, g.queue, qbb, P);
-        fs.push(changed && nb >= 2 && nbn < 2, b1, dev, g.queue, qbb, P);
-        fs.push(changed && nbn == 0, b0, dev, g.queue, qbb, P);
+        // parent, if still owned, forgets it
+#pragma unroll
+        for (uint32_t h = TINY_NB; h >= 1; --h) {
+            const bool fr = changed && h <= nb && h > nbn;
+            fs.push(fr, bl.b[h - 1], dev, g.queue, qbb, P);
+            if (fr && h >= 2 && h / 2 <= nbn) g.links[2ull * bl.b[h / 2 - 1] + (h & 1u)] = NIL;
+        }
         if (changed) {
-            if (nb >= 4 && nbn >= 2 && nbn < 4) g.links[2ull * b1] = NIL;      // heap 4: left of heap 2
-            if (nb >= 3 && nbn >= 1 && nbn < 3) g.links[2ull * b0 + 1] = NIL;  // heap 3: right of heap 1
-            if (nb >= 2 && nbn == 1) g.links[2ull * b0] = NIL;                 // heap 2: left of heap 1
             const uint32_t u = g.t_vid[t];
-            g.sent[u] = make_uint4(w, nbn, nbn ? root : NIL, nbn ? pick4(nbn - 1, b0, b1, b2, b3) : NIL);
+            g.sent[u] = make_uint4(w, nbn, nbn ? root : NIL, nbn ? bl.get(nbn - 1) : NIL);
             removed += deg - w;
             if (g.set_G) atomicAdd(&s_mhist[member_of(g.set_vbase, g.set_G, u)], deg - w);
         }
@@ -1182,6 +1259,7 @@ __global__ void __launch_bounds__(256) k_finalize_member(GraphView g, unsigned l
         dev->n_items = 0;
         dev->n_tiny = 0;
         dev->arena_used = 0;
+        dev->harena_used = 0;
         dev->free_total = 0;
         dev->abort = 0;
         dev->done_ctas = 0;
@@ -1339,6 +1417,7 @@ __global__ void __launch_bounds__(256) k_finalize_vdel(GraphView g, const uint32
         dev->n_items = 0;
         dev->n_tiny = 0;
         dev->arena_used = 0;
+        dev->harena_used = 0;
         dev->free_total = 0;
         dev->abort = 0;
         dev->done_ctas = 0;
@@ -1500,9 +1579,11 @@ cudaError_t launch_insert_tail(const GraphView &g, const uint32_t *src, const ui
 }
 
 template <int MODE>
-static void member_tail(const GraphView &g, const uint32_t *src, const uint32_t *dst,
+static void member_tail(const GraphView &g0, const uint32_t *src, const uint32_t *dst,
                         unsigned long long n, unsigned long long tcap, unsigned long long *counts,
                         uint8_t *qout, const LaunchCfg &lc) {
+    GraphView g = g0;
+    g.hbase = (uint32_t)((n + 63) / 64 * 64);  // lists below (at most n words), hash sets above
     const int cap = lc.num_sms * GRID_MULT;
     const int gt = grid_for(tcap, 256, cap);
     const int gi = lc.num_sms * GRID_MULT;  // warp-per-item kernels: 8 warps per CTA
@@ -1513,7 +1594,7 @@ static void member_tail(const GraphView &g, const uint32_t *src, const uint32_t 
     }
     {
         PhaseScope ps(lc, del ? PH_DEL_ARENA : PH_QRY_ARENA);
-        k_arena_init<MODE><<<grid_for(4 * n + 64, 256, cap), 256, 0, lc.stream>>>(g);
+        k_arena_init<MODE><<<grid_for(5 * n + 64, 256, cap), 256, 0, lc.stream>>>(g);
     }
     {
         PhaseScope ps(lc, del ? PH_DEL_SCATTER : PH_QRY_SCATTER);
