@@ -155,6 +155,11 @@ gv_status gv_bulk_build(gv_graph *g, const uint32_t *src, const uint32_t *dst, u
  *   d_counts  optional, 2 uint64 (device or host): {inserted, rejected}.
  * If the batch needs more blocks than the queue holds, nothing is inserted,
  * d_counts gets {0, 0} and the device status latches GV_ERR_OUT_OF_MEMORY.
+ * With GV_DEDUP a membership pass runs first (the batch's destinations per
+ * source in a hash set, every stored block of each touched source scanned as
+ * in gv_query_edges) and only pairs that are neither stored nor repeated
+ * within the batch are inserted; repeats count as neither inserted nor
+ * rejected.
  */
 gv_status gv_insert_edges(gv_graph *g, const uint32_t *src, const uint32_t *dst, uint64_t n,
                           uint64_t *d_counts, void *stream);

@@ -62,6 +62,10 @@ struct gv_graph {
     uint4 *t_a = nullptr, *t_b = nullptr;
     unsigned long long rcap = 0;
     uint32_t *prank = nullptr;
+    unsigned long long dcap = 0;
+    uint8_t *pflag = nullptr;      // set-semantics insert scratch
+    uint32_t *dsrc2 = nullptr;
+    unsigned long long *dtmp = nullptr;
     unsigned long long ocap = 0;
     uint32_t *t_owner = nullptr;
     // items
@@ -167,6 +171,7 @@ GraphView view(const gv_graph *g) {
     v.t_owner = g->t_owner;
     v.t_tiny = g->t_tiny;
     v.prank = g->prank;
+    v.pflag = g->pflag;
     v.items = g->items;
     v.it_mask = g->it_mask;
     v.it_cnt = g->it_cnt;
@@ -449,7 +454,6 @@ gv_status insert_impl(gv_graph *g, const uint32_t *src, const uint32_t *dst, uin
     if (!g) return GV_ERR_INVALID_ARG;
     if (n > kMaxBatch) return GV_ERR_INVALID_ARG;
     if (n > 0 && (!src || !dst)) return GV_ERR_INVALID_ARG;
-    if (g->flags & GV_DEDUP) return GV_ERR_INVALID_ARG;
     DeviceGuard dg(g->device);
     g->last_stream = s;
     const void *dsrc = src, *ddst = dst;
@@ -474,8 +478,41 @@ gv_status insert_impl(gv_graph *g, const uint32_t *src, const uint32_t *dst, uin
         GV_TRY(setup_pool(g, rule_capacity(valid, nt), s));
         GV_TRY(ensure_batch(g, n, gv::MODE_INSERT));
         GraphView v2 = view(g);
+        if (g->flags & GV_DEDUP) {
+            // the counting pass above only fixed C: clear it and run the
+            // set-semantics insert from the start
+            GV_CK(gv::launch_finalize_count_only(v2, lcfg(g, s)));
+            if (host_counts) {
+                GV_TRY(insert_impl(g, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, counts, s));
+                return check_launch();
+            }
+            return insert_impl(g, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, counts, s);
+        }
         GV_CK(gv::launch_insert_tail(v2, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, g->tcap,
                                      (unsigned long long *)dcounts, lcfg(g, s)));
+    } else if ((g->flags & GV_DEDUP) && n > 0) {
+        // set semantics: membership pass over the batch, mask of the pairs
+        // that add a new value, then the plain insert of the masked batch
+        GV_TRY(ensure_batch(g, n, gv::MODE_INSERT));
+        GV_TRY(ensure_batch(g, n, gv::MODE_QUERY));
+        if (n > g->dcap || !g->dcap) {
+            dfree(g->pflag);
+            dfree(g->dsrc2);
+            g->dcap = 0;
+            const unsigned long long cap = std::max<unsigned long long>(n, 2 * g->dcap);
+            GV_TRY(dalloc(&g->pflag, cap, &g->scratch_bytes));
+            GV_TRY(dalloc(&g->dsrc2, cap, &g->scratch_bytes));
+            g->dcap = cap;
+        }
+        if (!g->dtmp) GV_TRY(dalloc(&g->dtmp, 4, &g->scratch_bytes));
+        GV_CK(cudaMemsetAsync(g->dtmp, 0, 32, s));
+        GraphView v = view(g);
+        GV_CK(gv::launch_count(gv::MODE_DELETE, v, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, lcfg(g, s)));
+        GV_CK(gv::launch_dedup_insert_prepare(v, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, g->tcap,
+                                              g->dsrc2, g->dtmp, lcfg(g, s)));
+        GV_CK(gv::launch_count(gv::MODE_INSERT, v, g->dsrc2, (const uint32_t *)ddst, n, lcfg(g, s)));
+        GV_CK(gv::launch_insert_tail(v, g->dsrc2, (const uint32_t *)ddst, n, g->tcap, g->dtmp + 2, lcfg(g, s)));
+        GV_CK(gv::launch_dedup_counts(g->dev, g->dtmp, n, (unsigned long long *)dcounts, lcfg(g, s)));
     } else {
         GV_TRY(ensure_batch(g, n, gv::MODE_INSERT));
         if (n == 0) {
@@ -631,7 +668,6 @@ gv_status gv_create(const gv_config *cfg, uint32_t num_vertices, void *stream, g
     if (c.block_capacity != 0 && (c.block_capacity < 4 || c.block_capacity > 512 || c.block_capacity % 4))
         return GV_ERR_INVALID_ARG;
     if (c.flags & ~GV_DEDUP) return GV_ERR_INVALID_ARG;
-    if (c.flags & GV_DEDUP) return GV_ERR_INVALID_ARG;  // set semantics: not provided by this build
     if (c.pool_mem && c.pool_bytes == 0) return GV_ERR_INVALID_ARG;
     if (num_vertices > 0x7FFFFFFFu) return GV_ERR_INVALID_ARG;
     gv_graph *g = new (std::nothrow) gv_graph();
@@ -693,6 +729,7 @@ gv_status gv_destroy(gv_graph *g) {
         dfree(g->arena); dfree(g->found); dfree(g->qpos); dfree(g->partials);
         dfree(g->owner_bits); dfree(g->vres);
         dfree(g->set_vbase); dfree(g->set_src); dfree(g->set_dst);
+        dfree(g->pflag); dfree(g->dsrc2); dfree(g->dtmp);
         for (auto &b : g->stage.buf) dfree(b.p);
         for (auto &r : g->prof.recs) {
             cudaEventDestroy(r.a);

@@ -88,6 +88,7 @@ struct GraphView {
     uint32_t hbase;         // first word of the hash region (a multiple of 64)
     uint32_t *found;        // query: hit flags, parallel to arena
     uint32_t *qpos;         // query: arena position of each query (NIL if invalid)
+    uint8_t *pflag;         // set-semantics insert: 1 if the pair claimed its value's slot
     uint32_t *dead;         // vertex delete: bitmap of deleted ids
     unsigned long long max_items;
     unsigned long long arena_cap;
@@ -112,7 +113,7 @@ __device__ __forceinline__ uint32_t member_of(const uint32_t *vbase, uint32_t G,
     return lo;
 }
 
-enum Mode : int { MODE_INSERT = 0, MODE_DELETE = 1, MODE_QUERY = 2, MODE_VDEL = 3 };
+enum Mode : int { MODE_INSERT = 0, MODE_DELETE = 1, MODE_QUERY = 2, MODE_VDEL = 3, MODE_DEDUP = 4 };
 
 // A source's batch destinations are kept as a plain list up to LIST_MAX
 // entries (tested through a shared-memory hash set built per work item) and
@@ -121,6 +122,16 @@ enum Mode : int { MODE_INSERT = 0, MODE_DELETE = 1, MODE_QUERY = 2, MODE_VDEL = 
 // round trip and only a full bucket sends it to the next one.
 constexpr uint32_t LIST_MAX = 256;
 constexpr uint32_t HB = 8;
+
+// Arena words of a source under set-semantics inserts: every source gets a
+// bucketed hash set (which also merges repeated pairs of the batch), the
+// power of two at or above 2m, at least one bucket.
+__host__ __device__ __forceinline__ uint32_t dedup_words(uint32_t m) {
+    uint32_t h = HB;
+    while (h < 2 * m) h <<= 1;
+    return h;
+}
+
 // Tiny adjacencies (one thread per source): at most TINY_DEG entries in at
 // most TINY_NB blocks, at most TINY_M batch entries.
 constexpr uint32_t TINY_DEG = 128;

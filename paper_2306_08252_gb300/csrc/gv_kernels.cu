@@ -540,10 +540,11 @@ __global__ void __launch_bounds__(256) k_plan_member(GraphView g) {
             const uint32_t u = g.t_vid[t];
             m = g.vcnt[vslot(g.vmask, u)];
             s = g.sent[u];
-            if (m <= LIST_MAX) lw = m;
+            if (MODE == MODE_DEDUP) hw = dedup_words(m);
+            else if (m <= LIST_MAX) lw = m;
             else hw = member_words(m);
             if (s.y > 0) {
-                if (s.x <= tiny_deg && s.y <= TINY_NB && m <= TINY_M) tiny = 1;
+                if (MODE != MODE_DEDUP && s.x <= tiny_deg && s.y <= TINY_NB && m <= TINY_M) tiny = 1;
                 else ni = (s.y + IB - 1) / IB;
             }
         }
@@ -561,8 +562,8 @@ __global__ void __launch_bounds__(256) k_plan_member(GraphView g) {
         __syncthreads();
         if (t < nt) {
             const uint32_t item0 = s_ai + iex;
-            // hash sets are powers of two >= 512 words, so their offsets stay
-            // multiples of 512 words: every bucket is sector-aligned
+            // hash sets are powers of two >= HB words, so their offsets stay
+            // multiples of HB words: every bucket is sector-aligned
             const uint32_t aoff = hw ? (uint32_t)(g.hbase + s_hw + hex) : (uint32_t)(s_aw + lex);
             g.t_a[t] = make_uint4(m, aoff, hw, item0);
             g.t_b[t] = make_uint4(s.x, s.y, s.z, ni);
@@ -579,15 +580,16 @@ __global__ void __launch_bounds__(256) k_arena_init(GraphView g) {
     // hash region -> EMPTY; query hit flags of both regions -> 0 (list
     // entries are all overwritten by the scatter)
     const unsigned long long lused = g.dev->arena_used, hused = g.dev->harena_used;
-    const unsigned long long tot = (MODE == MODE_QUERY ? lused : 0ull) + hused;
+    constexpr bool Q = (MODE == MODE_QUERY || MODE == MODE_DEDUP);
+    const unsigned long long tot = (Q ? lused : 0ull) + hused;
     for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < tot;
          k += (unsigned long long)gridDim.x * blockDim.x) {
-        if (MODE == MODE_QUERY && k < lused) {
+        if (Q && k < lused) {
             g.found[k] = 0u;
         } else {
-            const unsigned long long i = g.hbase + (k - (MODE == MODE_QUERY ? lused : 0ull));
+            const unsigned long long i = g.hbase + (k - (Q ? lused : 0ull));
             g.arena[i] = EMPTY_KEY;
-            if (MODE == MODE_QUERY) g.found[i] = 0u;
+            if (Q) g.found[i] = 0u;
         }
     }
 }
@@ -632,6 +634,7 @@ __global__ void __launch_bounds__(256) k_scatter_member(GraphView g, const uint3
         // possibly stale L1 line), then claim a slot by CAS
         uint4 b0[PP], b1[PP];
         uint32_t bk[PP];
+        uint32_t rep = 0;  // set-semantics inserts: bit j = pair j claimed its slot
 #pragma unroll
         for (int j = 0; j < PP; ++j) {
             if (r[j] != NIL && hs[j] != 0) {
@@ -665,6 +668,7 @@ __global__ void __launch_bounds__(256) k_scatter_member(GraphView g, const uint3
                         const uint32_t old = atomicCAS(&tab[b * HB + empty], EMPTY_KEY, v[j]);
                         if (old == EMPTY_KEY || old == v[j]) {
                             pos[j] = aoff[j] + b * HB + empty;
+                            if (MODE == MODE_DEDUP && old == EMPTY_KEY) rep |= 1u << j;
                             break;
                         }
                         // lost the slot: reread this bucket
@@ -679,11 +683,14 @@ __global__ void __launch_bounds__(256) k_scatter_member(GraphView g, const uint3
                 if (pos[j] == NIL) latch_status(g.dev, 5u /* GV_ERR_STATE */);
             }
         }
-        if (MODE == MODE_QUERY) {
+        if (MODE == MODE_QUERY || MODE == MODE_DEDUP) {
 #pragma unroll
             for (int j = 0; j < PP; ++j) {
                 const unsigned long long i = i0 + j * stride;
-                if (i < n) g.qpos[i] = pos[j];
+                if (i < n) {
+                    g.qpos[i] = pos[j];
+                    if (MODE == MODE_DEDUP) g.pflag[i] = (uint8_t)((rep >> j) & 1u);
+                }
             }
         }
     }
@@ -1424,6 +1431,47 @@ __global__ void __launch_bounds__(256) k_finalize_vdel(GraphView g, const uint32
     }
 }
 
+// ------------------------------------------------------ set-semantics insert
+
+// After the membership pass over the batch (hit flags = value already
+// stored): pair i is inserted iff it claimed its value's slot (first of its
+// repeats in the batch) and the value is not stored yet; every other pair
+// gets source NIL so that the insert that follows skips it.
+__global__ void __launch_bounds__(256) k_dedup_select(GraphView g, const uint32_t *__restrict__ src,
+                                                      unsigned long long n, uint32_t *src2,
+                                                      unsigned long long *cnt) {
+    unsigned long long k = 0;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t p = g.qpos[i];
+        const bool take = p != NIL && g.pflag[i] && !g.found[p];
+        src2[i] = take ? src[i] : NIL;
+        k += take;
+    }
+    k = warp_sum_u64(k);
+    if (lane_id() == 0 && k) atomicAdd(cnt, k);
+}
+
+__global__ void k_copy_rejects(Dev *dev, unsigned long long *tmp) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) tmp[0] = dev->call_b;
+}
+
+// Final counts of a set-semantics insert: {inserted, rejected pairs of the
+// caller's batch}; the insert's own reject count (which includes the skipped
+// repeats) is taken back out of the running total.
+__global__ void k_dedup_counts(Dev *dev, const unsigned long long *tmp, unsigned long long n,
+                               unsigned long long *counts) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        // tmp[0] = rejected by the grouping pass, tmp[2..3] = {inserted, rejected} of the insert
+        const unsigned long long ins = tmp[2], rej2 = tmp[3], rej = tmp[0];
+        if (rej2 >= rej) dev->tot_rej -= rej2 - rej;
+        if (counts) {
+            counts[0] = ins;
+            counts[1] = (ins == 0 && rej2 == 0 && n != 0) ? 0ull : rej;  // {0, 0} when the insert aborted
+        }
+    }
+}
+
 // ---------------------------------------------------------------- graph sets
 
 // Concatenated member batches -> one batch over the set's shared dictionary:
@@ -1675,6 +1723,41 @@ cudaError_t launch_segment_counts(const GraphView &g, const uint32_t *src, const
 }
 cudaError_t launch_set_insert_counts(const GraphView &g, const LaunchCfg &lc) {
     k_set_insert_counts<<<(g.set_G + 255) / 256, 256, 0, lc.stream>>>(g);
+    return cudaGetLastError();
+}
+}  // namespace gv
+
+namespace gv {
+cudaError_t launch_dedup_insert_prepare(const GraphView &g0, const uint32_t *src, const uint32_t *dst,
+                                        unsigned long long n, unsigned long long tcap, uint32_t *src2,
+                                        unsigned long long *tmp, const LaunchCfg &lc) {
+    // tmp[0]: pairs rejected by the grouping pass; tmp[1]: pairs selected
+    GraphView g = g0;
+    g.hbase = (uint32_t)((n + 63) / 64 * 64);
+    const int cap = lc.num_sms * GRID_MULT;
+    const int gt = grid_for(tcap, 256, cap);
+    const int gi = lc.num_sms * GRID_MULT;
+    k_plan_member<MODE_DEDUP><<<gt, 256, 0, lc.stream>>>(g);
+    k_arena_init<MODE_DEDUP><<<grid_for(5 * n + 64, 256, cap), 256, 0, lc.stream>>>(g);
+    k_scatter_member<MODE_DEDUP><<<grid_for(n, 256 * PP, cap), 256, 0, lc.stream>>>(g, src, dst, n);
+    k_mark<MODE_QUERY><<<gi, 256, 0, lc.stream>>>(g);
+    k_dedup_select<<<grid_for(n, 256, cap), 256, 0, lc.stream>>>(g, src, n, src2, tmp + 1);
+    k_copy_rejects<<<1, 32, 0, lc.stream>>>(g.dev, tmp);
+    k_finalize_member<MODE_QUERY><<<gt, 256, 0, lc.stream>>>(g, nullptr);
+    return cudaGetLastError();
+}
+cudaError_t launch_dedup_counts(Dev *dev, const unsigned long long *tmp, unsigned long long n,
+                                unsigned long long *counts, const LaunchCfg &lc) {
+    k_dedup_counts<<<1, 32, 0, lc.stream>>>(dev, tmp, n, counts);
+    return cudaGetLastError();
+}
+}  // namespace gv
+
+namespace gv {
+// Clears the per-call state of a counting pass whose batch is not applied
+// (the first batch of a set-semantics graph, counted only to fix C).
+cudaError_t launch_finalize_count_only(const GraphView &g, const LaunchCfg &lc) {
+    k_finalize_member<MODE_QUERY><<<grid_for(g.nv, 256, lc.num_sms * GRID_MULT), 256, 0, lc.stream>>>(g, nullptr);
     return cudaGetLastError();
 }
 }  // namespace gv

@@ -110,6 +110,13 @@ cudaError_t launch_set_remap(const GraphView &g, const uint32_t *src, const uint
 cudaError_t launch_set_insert_counts(const GraphView &g, const LaunchCfg &lc);
 cudaError_t launch_segment_counts(const GraphView &g, const uint32_t *src, const uint32_t *dst,
                                   unsigned long long n, const LaunchCfg &lc);
+// Set-semantics insert: membership pass, then the mask of pairs to insert.
+cudaError_t launch_dedup_insert_prepare(const GraphView &g, const uint32_t *src, const uint32_t *dst,
+                                        unsigned long long n, unsigned long long tcap, uint32_t *src2,
+                                        unsigned long long *tmp, const LaunchCfg &lc);
+cudaError_t launch_dedup_counts(Dev *dev, const unsigned long long *tmp, unsigned long long n,
+                                unsigned long long *counts, const LaunchCfg &lc);
+cudaError_t launch_finalize_count_only(const GraphView &g, const LaunchCfg &lc);
 cudaError_t launch_validate(const GraphView &g, uint32_t *owner_bits,
                             unsigned long long *violations, const LaunchCfg &lc);
 

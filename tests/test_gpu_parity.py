@@ -287,3 +287,51 @@ def test_rmat_full_size_sampled():
         p.check_sampled(np.concatenate([hubs, rnd]))
     finally:
         p.close()
+
+
+@pytest.mark.parametrize("C", [4, 16, 0])
+def test_set_semantics_inserts(C):
+    # GV_DEDUP: a pair is added only when it is not stored and not already
+    # added by the same batch; duplicates within a batch, against the graph,
+    # hub sources with many work items, invalid ids and deletes in between
+    import paper_2306_08252_gb300 as gv
+    scale, nv = 12, 1 << 12
+    rng = np.random.default_rng(31)
+    bs, bd = W.rmat_pairs(23, 0, 60000, scale)
+    # repeat a slice of the bulk batch inside the batch itself
+    bs = np.concatenate([bs, bs[:5000]])
+    bd = np.concatenate([bd, bd[:5000]])
+    p = Pair(nv, C=C, pool_bytes=64 << 20, flags=gv.GV_DEDUP)
+    try:
+        p.bulk(bs, bd)
+        p.check()
+        for r, b in enumerate([1, 50, 3000, 40000]):
+            s, d = W.rmat_pairs(23, 10 + r, b, scale)
+            # a third of the batch repeats stored edges, some pairs twice
+            k = b // 3
+            pick = rng.integers(0, bs.size, k)
+            s = np.concatenate([s, bs[pick], s[: b // 4]])
+            d = np.concatenate([d, bd[pick], d[: b // 4]])
+            if r == 2:
+                s = np.concatenate([s, np.array([nv, 5, 0xFFFFFFFF], dtype=np.uint32)])
+                d = np.concatenate([d, np.array([1, nv + 3, 2], dtype=np.uint32)])
+            perm = rng.permutation(s.size)
+            p.insert(s[perm], d[perm])
+            p.check()
+            # the same batch again adds nothing
+            p.insert(s, d)
+            p.check()
+            es, ed = bs[r * 2000:(r + 1) * 2000], bd[r * 2000:(r + 1) * 2000]
+            p.delete(es, ed)
+            p.check()
+        # one hub source: a long adjacency, a batch that mixes stored and new
+        hub_d = rng.integers(0, nv, 30000).astype(np.uint32)
+        p.insert(np.zeros(hub_d.size, dtype=np.uint32), hub_d)
+        p.check()
+        hub_d2 = rng.integers(0, nv, 30000).astype(np.uint32)
+        p.insert(np.zeros(hub_d2.size, dtype=np.uint32), hub_d2)
+        p.check()
+        p.insert(np.zeros(0, dtype=np.uint32), np.zeros(0, dtype=np.uint32))
+        p.check()
+    finally:
+        p.close()
