@@ -159,7 +159,7 @@ gv_status gv_bulk_build(gv_graph *g, const uint32_t *src, const uint32_t *dst, u
  * source in a hash set, every stored block of each touched source scanned as
  * in gv_query_edges) and only pairs that are neither stored nor repeated
  * within the batch are inserted; repeats count as neither inserted nor
- * rejected.
+ * rejected.  Such a batch holds at most 2^28 pairs (GV_ERR_INVALID_ARG).
  */
 gv_status gv_insert_edges(gv_graph *g, const uint32_t *src, const uint32_t *dst, uint64_t n,
                           uint64_t *d_counts, void *stream);

@@ -495,6 +495,8 @@ gv_status insert_impl(gv_graph *g, const uint32_t *src, const uint32_t *dst, uin
         // that add a new value, then the plain insert of the masked batch
         GV_TRY(ensure_batch(g, n, gv::MODE_INSERT));
         GV_TRY(ensure_batch(g, n, gv::MODE_QUERY));
+        if (n > kMaxBatch / 2) return GV_ERR_INVALID_ARG;  // 8n arena words stay below 2^32
+        GV_TRY(ensure_arena(g, 8 * n + 128, true, n));       // one hash set per source
         if (n > g->dcap || !g->dcap) {
             dfree(g->pflag);
             dfree(g->dsrc2);

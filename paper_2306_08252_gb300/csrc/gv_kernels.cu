@@ -1732,13 +1732,15 @@ cudaError_t launch_dedup_insert_prepare(const GraphView &g0, const uint32_t *src
                                         unsigned long long n, unsigned long long tcap, uint32_t *src2,
                                         unsigned long long *tmp, const LaunchCfg &lc) {
     // tmp[0]: pairs rejected by the grouping pass; tmp[1]: pairs selected
+    // Every source gets a hash set (no list region): dedup_words(m) <= 8m
+    // words, so the arena needs at most 8n words from hbase = 0.
     GraphView g = g0;
-    g.hbase = (uint32_t)((n + 63) / 64 * 64);
+    g.hbase = 0;
     const int cap = lc.num_sms * GRID_MULT;
     const int gt = grid_for(tcap, 256, cap);
     const int gi = lc.num_sms * GRID_MULT;
     k_plan_member<MODE_DEDUP><<<gt, 256, 0, lc.stream>>>(g);
-    k_arena_init<MODE_DEDUP><<<grid_for(5 * n + 64, 256, cap), 256, 0, lc.stream>>>(g);
+    k_arena_init<MODE_DEDUP><<<grid_for(8 * n + 64, 256, cap), 256, 0, lc.stream>>>(g);
     k_scatter_member<MODE_DEDUP><<<grid_for(n, 256 * PP, cap), 256, 0, lc.stream>>>(g, src, dst, n);
     k_mark<MODE_QUERY><<<gi, 256, 0, lc.stream>>>(g);
     k_dedup_select<<<grid_for(n, 256, cap), 256, 0, lc.stream>>>(g, src, n, src2, tmp + 1);
