@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=10_000)
     ap.add_argument("--serve-scale", type=int, default=24)
-    ap.add_argument("--workload", default="rmat", choices=["rmat", "batched", "serving"],
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "batched", "serving", "rows"],
                     help="rmat: the single-graph step (default); batched: many member graphs, "
                          "one captured launch sequence vs one launch sequence per graph")
     ap.add_argument("--graphs", type=int, default=256)
@@ -578,8 +578,161 @@ def run_serving(args):
     return 0
 
 
+# ------------------------------------------------------- per-row sweep
+
+def run_rows(args):
+    """Each step of the path timed on its own with its algorithmic bytes:
+    create, bulk build, insert and delete at batch sizes 1K..10M, queries,
+    neighbours (RMAT 2^20 / 16M), vertex insert and delete (uniform 2^22 /
+    16M).  Device time by CUDA events on the call stream, median of the
+    repeats, L2 flushed before each timed call; restores are untimed."""
+    import torch
+    import paper_2306_08252_gb300 as gv
+    import workloads as W
+
+    pk, pk_kind = peaks()
+    hbm = float(pk.get("hbm_gbs", 6800.0))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
+    reps = max(args.steps, 3)
+    rows = []
+
+    def timed(fn, pre=None, post=None, n=reps):
+        ms = []
+        for i in range(n + 1):
+            if pre:
+                pre()
+            flush.fill_(i & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i:
+                ms.append(e0.elapsed_time(e1))
+            if post:
+                post()
+        return float(statistics.median(ms))
+
+    def row(name, what, units, unit_name, ms, nbytes, **extra):
+        gbs = nbytes / (ms / 1e3) / 1e9
+        r = {"row": name, "what": what, "units": units, "ms": ms, "rate": units / (ms / 1e3),
+             "rate_unit": unit_name + "/s", "algorithmic_bytes": int(nbytes), "achieved_gbs": gbs,
+             "frac_of_measured_hbm": gbs / hbm}
+        r.update(extra)
+        rows.append(r)
+        print(json.dumps(r), file=sys.stderr, flush=True)
+
+    nv = 1 << SCALE
+    (bs, bd), (us, ud), (qs, qd) = workload(BATCH, QUERIES)
+    d_bs, d_bd = t(bs), t(bd)
+    cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+
+    # a1: create (pool + dictionary); host wall clock, allocation included
+    ct = []
+    for i in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = gv.Graph(nv, block_capacity=C, pool_bytes=POOL_BYTES)
+        g.sync()
+        ct.append((time.perf_counter() - t0) * 1e3)
+        st = g.stats()
+        g.close()
+    P = st["pool_blocks"]
+    row("a1", "create: dictionary, sentinels, pool and edge queue", nv, "vertices", float(statistics.median(ct)),
+        17 * st["vertex_capacity"] + 4 * P, timer="host wall clock (allocation included)")
+
+    # a5: bulk build of the 16M-edge graph
+    holder = {}
+
+    def mk():
+        if "g" in holder:
+            holder["g"].close()
+        holder["g"] = gv.Graph(nv, block_capacity=C, pool_bytes=POOL_BYTES)
+        holder["g"].reserve(BATCH)
+        torch.cuda.synchronize()
+
+    ms = timed(lambda: holder["g"].bulk_build(d_bs, d_bd, cnt), pre=mk, n=3)
+    row("a5", "bulk build", bs.size, "edges", ms, 12 * bs.size + 16 * nv)
+    g = holder["g"]
+    deg0, _ = g.degrees()
+    deg0 = deg0.astype(np.int64)
+
+    # a2-a4 / a6: insert and delete sweeps
+    for B in (1_000, 10_000, 100_000, 1_000_000, 10_000_000):
+        s, d = t(us[:B]), t(ud[:B])
+        srcs = np.unique(us[:B])
+        st0 = g.stats()
+        ms_i = timed(lambda: g.insert_edges(s, d, cnt), post=lambda: g.delete_edges(s, d, cnt))
+        g.insert_edges(s, d, cnt)
+        torch.cuda.synchronize()
+        st1 = g.stats()
+        newb = st1["pool_blocks_used"] - st0["pool_blocks_used"]
+        deg1, _ = g.degrees()
+        g.delete_edges(s, d, cnt)
+        ms_d = timed(lambda: g.delete_edges(s, d, cnt), pre=lambda: g.insert_edges(s, d, cnt))
+        row("a2-a4", f"insert batch of {B}", B, "edges", ms_i, 12 * B + 32 * srcs.size + 12 * newb)
+        row("a6", f"delete batch of {B}", B, "edges", ms_d,
+            8 * B + 4 * int(deg1.astype(np.int64)[srcs].sum()) + 32 * srcs.size + 4 * newb)
+
+    # a7: 1M queries (half present) on the base graph
+    d_qs, d_qd = t(qs), t(qd)
+    out = torch.zeros(qs.size, dtype=torch.uint8, device="cuda")
+    qsrc = np.unique(qs[qs < nv])
+    ms = timed(lambda: g.query_edges(d_qs, d_qd, out))
+    row("a7", f"edge-existence queries ({qs.size})", qs.size, "queries", ms, 9 * qs.size + 4 * int(deg0[qsrc].sum()))
+
+    # a8: neighbours of every vertex (CSR of the whole graph)
+    vids = torch.arange(nv, dtype=torch.int32, device="cuda")
+    offs = torch.zeros(nv + 1, dtype=torch.int64, device="cuda")
+    E = int(deg0.sum())
+    nbrs = torch.zeros(E, dtype=torch.int32, device="cuda")
+    ms = timed(lambda: gv.gv_neighbors(g.handle, vids, offs, nbrs, E, stream.cuda_stream))
+    row("a8", f"neighbours of all {nv} vertices", E, "entries", ms, 8 * E + 4 * nv + 16 * nv + 8 * (nv + 1))
+    g.close()
+
+    # a9 / a10 on the uniform 2^22 graph
+    er = W.er_mixed(3, rounds=0)
+    nv2 = er["nv"]
+    es, ed = er["bulk"]
+    vdel = next(op for op in er["ops"] if op.kind == "vdel").ids
+    d_es, d_ed = t(es), t(ed)
+    d_ids = t(vdel)
+    holder2 = {}
+
+    def mk2():
+        if "g" in holder2:
+            holder2["g"].close()
+        holder2["g"] = gv.Graph(nv2, block_capacity=4, pool_bytes=1 << 30)
+        holder2["g"].bulk_build(d_es, d_ed, cnt)
+        torch.cuda.synchronize()
+
+    ms = timed(lambda: holder2["g"].delete_vertices(d_ids), pre=mk2, n=3)
+    E2 = int(es.size)
+    row("a10", f"delete {vdel.size} vertices (outgoing and incoming edges)", vdel.size, "vertices", ms,
+        4 * E2 + 16 * vdel.size + 16 * nv2 // 8)
+    k = 65_536
+    newids = torch.zeros(k, dtype=torch.int32, device="cuda")
+    ms = timed(lambda: holder2["g"].insert_vertices(k, newids), pre=mk2, n=3)
+    row("a9", f"insert {k} vertices (dictionary doubling from 2^22)", k, "vertices", ms,
+        2 * 17 * nv2 + 17 * k + 4 * k)
+    holder2["g"].close()
+
+    res = {"metric": "per-step device time and algorithmic bytes of each step of the path",
+           "value": None, "unit": None, "n_gpus": 1, "steps": reps, "warmup": 1, "higher_is_better": True,
+           "dtype": "u32", "data": "synthetic (seeded RMAT and uniform graphs)",
+           "config": {"workload": f"RMAT scale {SCALE} / {BASE_EDGES} edges, C={C}; uniform 2^22 / 16777216 "
+                                  "edges, C=4 for vertex operations", "l2": "flushed before every timed call"},
+           "peak_gbs": hbm, "peak_kind": pk_kind, "rows": rows}
+    print(json.dumps(res), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "rows":
+        return run_rows(args)
     if args.workload == "batched":
         return run_batched(args)
     if args.workload == "serving":

@@ -61,6 +61,15 @@ typedef enum gv_status {
 
 /* gv_config.flags */
 #define GV_DEDUP 1u /* set semantics for inserts (cuSTINGER/Hornet-style duplicate check) */
+/* Pool growth ("Edge Queue": when 80% of the pool is used it grows by 25%).
+ * Checked on the host before each insert against an upper bound of the
+ * blocks in use plus the insert's worst-case demand ceil(n/C) + min(n, |V|);
+ * when the bound passes 80% the call synchronises its stream once, reads the
+ * exact count and, if needed, moves the pool into an allocation 25% larger
+ * (repeatedly, until the exact count plus the demand is under 80%).  Block
+ * ids are kept.  Library-owned pools only (pool_mem must be NULL); a failed
+ * allocation keeps the old pool. */
+#define GV_GROW 2u
 
 typedef struct gv_config {
     /* C, the number of edge entries per edge block (multiple of 4, 4..512).
@@ -68,7 +77,7 @@ typedef struct gv_config {
      * vertices with non-zero degree in the first edge batch, rounded up to a
      * multiple of 4; fixed from then on. */
     uint32_t block_capacity;
-    uint32_t flags;          /* GV_DEDUP or 0 */
+    uint32_t flags;          /* GV_DEDUP | GV_GROW, or 0 */
     /* Bytes reserved for the edge-block pool: block storage (4*C bytes per
      * block), tree links (8 bytes per block) and the edge queue (4 bytes per
      * block).  0 = half of the free device memory ("Edge Queue": at least

@@ -89,6 +89,7 @@ struct gv_graph {
     uint64_t scratch_bytes = 0;
     uint64_t dict_bytes = 0;
     bool any_vertex_deleted = false;
+    unsigned long long used_ub = 0;  // upper bound of blocks in use (pool growth policy)
     // graph set: members' vertex ranges (set_G == 0 for a plain graph)
     uint32_t set_G = 0;
     uint32_t *set_vbase = nullptr;          // device, G+1
@@ -449,6 +450,75 @@ uint32_t rule_capacity(unsigned long long valid, unsigned long long touched) {
     return (uint32_t)c;
 }
 
+// Moves the pool into a larger allocation of P2 blocks: block storage and
+// tree links are copied (block ids keep their meaning), the queue ring is
+// rebuilt with the new ids behind the free ones.  qf/qb: queue counters read
+// after the stream was synchronised.
+gv_status grow_pool(gv_graph *g, unsigned long long P2, unsigned long long qf, unsigned long long qb,
+                    cudaStream_t s) {
+    auto align = [](uint64_t x) { return (x + 255) & ~255ull; };
+    const uint64_t C = g->C;
+    const uint64_t off_links = align(P2 * C * 4ull);
+    const uint64_t off_queue = align(off_links + P2 * 8ull);
+    const uint64_t bytes = off_queue + P2 * 4ull;
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return GV_ERR_OUT_OF_MEMORY;
+    }
+    char *base = static_cast<char *>(p);
+    uint32_t *data2 = reinterpret_cast<uint32_t *>(base);
+    uint32_t *links2 = reinterpret_cast<uint32_t *>(base + off_links);
+    uint32_t *queue2 = reinterpret_cast<uint32_t *>(base + off_queue);
+    const unsigned long long nfree = qb - qf;
+    GV_CK(cudaMemcpyAsync(data2, g->data, g->P * C * 4ull, cudaMemcpyDeviceToDevice, s));
+    GV_CK(cudaMemcpyAsync(links2, g->links, g->P * 8ull, cudaMemcpyDeviceToDevice, s));
+    GV_CK(gv::launch_grow_queue(g->queue, g->P, qf, nfree, queue2, P2, lcfg(g, s)));
+    g->h_small[2] = 0;
+    g->h_small[3] = nfree + (P2 - g->P);
+    GV_CK(cudaMemcpyAsync(&g->dev->q_front, &g->h_small[2], 8, cudaMemcpyHostToDevice, s));
+    GV_CK(cudaMemcpyAsync(&g->dev->q_back, &g->h_small[3], 8, cudaMemcpyHostToDevice, s));
+    GV_CK(cudaStreamSynchronize(s));
+    cudaFree(g->pool_alloc);
+    g->pool_alloc = p;
+    g->data = data2;
+    g->links = links2;
+    g->queue = queue2;
+    g->P = P2;
+    g->pool_bytes = bytes;
+    return GV_OK;
+}
+
+// Pool growth ("Edge Queue": once 80% of the pool is in use it grows by
+// 25%), checked on the host before an insert of n pairs.  The library keeps
+// an upper bound of the blocks in use (exact after a read, plus the
+// worst-case demand of every insert since, ceil(n / C) + min(n, |V|)); only
+// when that bound passes 80% does it synchronise to read the exact count,
+// then grows by 25% steps until the exact count plus this insert's
+// worst-case demand fits under 80%.  A failed allocation keeps the old pool
+// (the insert may then report pool exhaustion as usual).
+gv_status maybe_grow(gv_graph *g, uint64_t n, cudaStream_t s) {
+    if (!(g->flags & GV_GROW) || !g->C || n == 0) return GV_OK;
+    const unsigned long long demand = (n + g->C - 1) / g->C + std::min<unsigned long long>(n, g->nv);
+    if (5 * (g->used_ub + demand) <= 4 * g->P) {
+        g->used_ub += demand;
+        return GV_OK;
+    }
+    GV_CK(cudaMemcpyAsync(&g->h_small[0], &g->dev->q_front, 8, cudaMemcpyDeviceToHost, s));
+    GV_CK(cudaMemcpyAsync(&g->h_small[1], &g->dev->q_back, 8, cudaMemcpyDeviceToHost, s));
+    GV_CK(cudaStreamSynchronize(s));
+    const unsigned long long qf = g->h_small[0], qb = g->h_small[1];
+    const unsigned long long used = g->P - (qb - qf);
+    unsigned long long P2 = g->P;
+    while (5 * (used + demand) > 4 * P2 && P2 < 0xFFFFFFFEull) P2 = std::min<unsigned long long>(P2 + (P2 + 3) / 4, 0xFFFFFFFEull);
+    if (P2 > g->P) {
+        const gv_status st = grow_pool(g, P2, qf, qb, s);
+        if (st != GV_OK && st != GV_ERR_OUT_OF_MEMORY) return st;
+    }
+    g->used_ub = used + demand;
+    return GV_OK;
+}
+
 gv_status insert_impl(gv_graph *g, const uint32_t *src, const uint32_t *dst, uint64_t n,
                       uint64_t *counts, cudaStream_t s) {
     if (!g) return GV_ERR_INVALID_ARG;
@@ -465,6 +535,7 @@ gv_status insert_impl(gv_graph *g, const uint32_t *src, const uint32_t *dst, uin
     const unsigned long long touched = std::min<unsigned long long>(n, g->nv ? g->nv : 1);
     GV_TRY(ensure_touched(g, touched));
     GV_TRY(ensure_ranks(g, n));
+    GV_TRY(maybe_grow(g, n, s));
     if (g->C == 0) {
         // First batch fixes C (paper rule), then the pool can be laid out.
         GraphView v = view(g);
@@ -477,6 +548,7 @@ gv_status insert_impl(gv_graph *g, const uint32_t *src, const uint32_t *dst, uin
         const unsigned long long valid = n - g->h_small[0];
         GV_TRY(setup_pool(g, rule_capacity(valid, nt), s));
         GV_TRY(ensure_batch(g, n, gv::MODE_INSERT));
+        if (!(g->flags & GV_DEDUP)) GV_TRY(maybe_grow(g, n, s));  // set semantics: checked by the call below
         GraphView v2 = view(g);
         if (g->flags & GV_DEDUP) {
             // the counting pass above only fixed C: clear it and run the
@@ -669,7 +741,8 @@ gv_status gv_create(const gv_config *cfg, uint32_t num_vertices, void *stream, g
     if (cfg) c = *cfg;
     if (c.block_capacity != 0 && (c.block_capacity < 4 || c.block_capacity > 512 || c.block_capacity % 4))
         return GV_ERR_INVALID_ARG;
-    if (c.flags & ~GV_DEDUP) return GV_ERR_INVALID_ARG;
+    if (c.flags & ~(GV_DEDUP | GV_GROW)) return GV_ERR_INVALID_ARG;
+    if ((c.flags & GV_GROW) && c.pool_mem) return GV_ERR_INVALID_ARG;  // a caller-owned pool cannot grow
     if (c.pool_mem && c.pool_bytes == 0) return GV_ERR_INVALID_ARG;
     if (num_vertices > 0x7FFFFFFFu) return GV_ERR_INVALID_ARG;
     gv_graph *g = new (std::nothrow) gv_graph();

@@ -116,6 +116,8 @@ cudaError_t launch_dedup_insert_prepare(const GraphView &g, const uint32_t *src,
                                         unsigned long long *tmp, const LaunchCfg &lc);
 cudaError_t launch_dedup_counts(Dev *dev, const unsigned long long *tmp, unsigned long long n,
                                 unsigned long long *counts, const LaunchCfg &lc);
+cudaError_t launch_grow_queue(const uint32_t *q, unsigned long long P, unsigned long long qf,
+                              unsigned long long nfree, uint32_t *q2, unsigned long long P2, const LaunchCfg &lc);
 cudaError_t launch_finalize_count_only(const GraphView &g, const LaunchCfg &lc);
 cudaError_t launch_validate(const GraphView &g, uint32_t *owner_bits,
                             unsigned long long *violations, const LaunchCfg &lc);

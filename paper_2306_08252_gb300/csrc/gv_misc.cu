@@ -317,6 +317,23 @@ cudaError_t launch_init_queue(uint32_t *queue, unsigned long long P, const Launc
     return cudaGetLastError();
 }
 
+// Edge queue of a grown pool: the free ids in ring order at positions
+// 0 .. free-1, then the new ids P .. P2-1.
+__global__ void k_grow_queue(const uint32_t *__restrict__ q, unsigned long long P, unsigned long long qf,
+                             unsigned long long nfree, uint32_t *__restrict__ q2, unsigned long long P2) {
+    const unsigned long long tot = nfree + (P2 - P);
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < tot;
+         i += (unsigned long long)gridDim.x * blockDim.x)
+        q2[i] = i < nfree ? q[(qf + i) % P] : (uint32_t)(P + (i - nfree));
+}
+
+cudaError_t launch_grow_queue(const uint32_t *q, unsigned long long P, unsigned long long qf,
+                              unsigned long long nfree, uint32_t *q2, unsigned long long P2, const LaunchCfg &lc) {
+    const unsigned long long tot = nfree + (P2 - P);
+    if (tot) k_grow_queue<<<grid_for(tot, 256, lc.num_sms * 16), 256, 0, lc.stream>>>(q, P, qf, nfree, q2, P2);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_iota(uint32_t *out, uint32_t first, uint32_t k, const LaunchCfg &lc) {
     if (k) k_iota<<<grid_for(k, 256, lc.num_sms * 16), 256, 0, lc.stream>>>(out, first, k);
     return cudaGetLastError();

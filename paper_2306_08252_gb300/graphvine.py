@@ -23,6 +23,7 @@ GV_ERR_CUDA = 3
 GV_ERR_TIMEOUT = 4
 GV_ERR_STATE = 5
 GV_DEDUP = 1
+GV_GROW = 2
 
 c_u32, c_u64, c_vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p
 

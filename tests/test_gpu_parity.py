@@ -335,3 +335,43 @@ def test_set_semantics_inserts(C):
         p.check()
     finally:
         p.close()
+
+
+def test_pool_growth_policy():
+    # GV_GROW: a pool of ~2K blocks grows by 25% steps ahead of inserts that
+    # would take it past 80%; block ids survive the move (parity and the
+    # structural self-check after every call), deletes return blocks to the
+    # grown queue
+    import paper_2306_08252_gb300 as gv
+    scale, nv = 12, 1 << 12
+    C = 8
+    per_block = 4 * C + 12
+    p = Pair(nv, C=C, pool_bytes=2048 * per_block + 4096, flags=gv.GV_GROW)
+    try:
+        st0 = p.g.stats()
+        bs, bd = W.rmat_pairs(29, 0, 4000, scale)
+        p.bulk(bs, bd)
+        p.check()
+        sizes = []
+        for r, b in enumerate([3000, 20000, 70000, 5, 150000]):
+            s, d = W.rmat_pairs(29, 1 + r, b, scale)
+            p.insert(s, d)
+            st = p.check()
+            assert p.g.sync() == 0  # no exhaustion latched
+            assert 5 * st["pool_blocks_used"] <= 4 * st["pool_blocks"]
+            sizes.append(st["pool_blocks"])
+            if r % 2:
+                p.delete(s[: b // 2], d[: b // 2])
+                p.check()
+        assert sizes[-1] > st0["pool_blocks"] * 10
+        assert all(b2 >= b1 for b1, b2 in zip(sizes, sizes[1:]))
+    finally:
+        p.close()
+
+
+def test_pool_growth_rejects_caller_owned_pool():
+    import torch
+    import paper_2306_08252_gb300 as gv
+    buf = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    with pytest.raises(gv.GraphVineError):
+        gv.Graph(1024, block_capacity=16, pool_bytes=buf.numel(), pool_mem=buf, flags=gv.GV_GROW)
