@@ -56,6 +56,8 @@ def _get():
                 "orc_cbt_path": ([u64, ctypes.c_char_p], u32),
                 "orc_pop_ranges": ([p, u32, p, p], None),
                 "orc_insert_block_demand": ([u64, u64, u32], u64),
+                "orc_bfs": ([p, u32, p], u32),
+                "orc_pagerank": ([p, u32, ctypes.c_double, p], None),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -145,6 +147,17 @@ class OracleGraph:
         nb = np.zeros(max(tot, 1), dtype=np.uint32)
         self._lib.orc_neighbors(self._g, v.ctypes.data, v.size, off.ctypes.data, nb.ctypes.data, tot)
         return off, nb[:tot]
+
+    def bfs(self, source: int):
+        """(dist[nv] uint32, levels); unreached = 0xFFFFFFFF."""
+        dist = np.zeros(max(self.num_vertices, 1), dtype=np.uint32)
+        lv = int(self._lib.orc_bfs(self._g, source, dist.ctypes.data))
+        return dist[:self.num_vertices], lv
+
+    def pagerank(self, iterations: int, damping: float = 0.85) -> np.ndarray:
+        r = np.zeros(max(self.num_vertices, 1), dtype=np.float64)
+        self._lib.orc_pagerank(self._g, iterations, damping, r.ctypes.data)
+        return r[:self.num_vertices]
 
     def export_csr(self):
         nv = self.num_vertices

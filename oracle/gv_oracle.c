@@ -370,3 +370,77 @@ uint64_t orc_insert_block_demand(uint64_t deg, uint64_t cnt, uint32_t C) {
     if (cnt <= space) return 0;
     return (cnt - space + C - 1) / C;
 }
+
+/*
+ * Graph analytics over the stored structure.  The paper names analytics on
+ * the dynamic structure as future work ("Conclusion and future work") and
+ * defines none; these are the textbook definitions.
+ *
+ * orc_bfs: unweighted single-source distances (breadth-first search, level
+ * by level): dist[source] = 0 if the source is alive, dist[v] = 1 + min over
+ * stored entries (u, v) with u at distance dist[u]; unreached (and every
+ * vertex when the source is dead) = 0xFFFFFFFF.  Returns the number of
+ * levels (largest finite distance + 1; 0 when nothing is reached).
+ */
+uint32_t orc_bfs(const orc_graph *g, uint32_t source, uint32_t *dist) {
+    for (uint32_t v = 0; v < g->nv; ++v) dist[v] = 0xFFFFFFFFu;
+    if (source >= g->nv || !g->alive[source]) return 0;
+    uint32_t *cur = (uint32_t *)malloc(sizeof(uint32_t) * (g->nv + 1));
+    uint32_t *nxt = (uint32_t *)malloc(sizeof(uint32_t) * (g->nv + 1));
+    uint32_t ncur = 1, level = 0;
+    cur[0] = source;
+    dist[source] = 0;
+    while (ncur > 0) {
+        uint32_t nnxt = 0;
+        for (uint32_t i = 0; i < ncur; ++i) {
+            const orc_adj *a = &g->adj[cur[i]];
+            for (uint64_t j = 0; j < a->n; ++j) {
+                const uint32_t v = a->v[j];
+                if (dist[v] == 0xFFFFFFFFu) {
+                    dist[v] = level + 1;
+                    nxt[nnxt++] = v;
+                }
+            }
+        }
+        uint32_t *t = cur;
+        cur = nxt;
+        nxt = t;
+        ncur = nnxt;
+        ++level;
+    }
+    free(cur);
+    free(nxt);
+    return level;
+}
+
+/*
+ * orc_pagerank: power iteration of PageRank with damping d over the alive
+ * vertices (N of them), in fp64.  r_0 = 1/N; each iteration
+ *   r'(v) = (1 - d)/N + d * ( sum over stored entries (u, v) of r(u)/deg(u)
+ *                             + (sum of r(u) over alive u with deg(u) = 0)/N )
+ * (a stored entry counts once per copy, so a multigraph weights parallel
+ * edges by their multiplicity).  Dead vertices get 0.  N = 0: all 0.
+ */
+void orc_pagerank(const orc_graph *g, uint32_t iterations, double damping, double *rank) {
+    uint64_t N = 0;
+    for (uint32_t v = 0; v < g->nv; ++v) N += g->alive[v] ? 1u : 0u;
+    for (uint32_t v = 0; v < g->nv; ++v) rank[v] = (N && g->alive[v]) ? 1.0 / (double)N : 0.0;
+    if (N == 0) return;
+    double *acc = (double *)malloc(sizeof(double) * (g->nv + 1));
+    for (uint32_t it = 0; it < iterations; ++it) {
+        double dangling = 0.0;
+        for (uint32_t v = 0; v < g->nv; ++v) acc[v] = 0.0;
+        for (uint32_t u = 0; u < g->nv; ++u) {
+            if (!g->alive[u]) continue;
+            const orc_adj *a = &g->adj[u];
+            if (a->n == 0) {
+                dangling += rank[u];
+                continue;
+            }
+            for (uint64_t j = 0; j < a->n; ++j) acc[a->v[j]] += rank[u] / (double)a->n;
+        }
+        for (uint32_t v = 0; v < g->nv; ++v)
+            rank[v] = g->alive[v] ? (1.0 - damping) / (double)N + damping * (acc[v] + dangling / (double)N) : 0.0;
+    }
+    free(acc);
+}

@@ -137,6 +137,10 @@ __host__ __device__ __forceinline__ uint32_t dedup_words(uint32_t m) {
 constexpr uint32_t TINY_DEG = 128;
 constexpr uint32_t TINY_NB = 8;
 constexpr uint32_t TINY_M = 16;
+// Queries only read: their thread-per-source tier stops at four blocks (a
+// longer serial walk costs more than a warp item saves).
+constexpr uint32_t TINY_DEG_Q = 64;
+constexpr uint32_t TINY_NB_Q = 4;
 
 // Arena words of a source with m batch entries: m (list) or the hash set
 // size, the power of two at or above 2m.

@@ -544,7 +544,11 @@ __global__ void __launch_bounds__(256) k_plan_member(GraphView g) {
             else if (m <= LIST_MAX) lw = m;
             else hw = member_words(m);
             if (s.y > 0) {
-                if (MODE != MODE_DEDUP && s.x <= tiny_deg && s.y <= TINY_NB && m <= TINY_M) tiny = 1;
+                if (MODE == MODE_QUERY) {
+                    if (s.x <= min(TINY_DEG_Q, TINY_NB_Q * g.C) && s.y <= TINY_NB_Q && m <= TINY_M) tiny = 1;
+                } else if (MODE != MODE_DEDUP && s.x <= tiny_deg && s.y <= TINY_NB && m <= TINY_M) {
+                    tiny = 1;
+                }
                 else ni = (s.y + IB - 1) / IB;
             }
         }
@@ -630,18 +634,17 @@ __global__ void __launch_bounds__(256) k_scatter_member(GraphView g, const uint3
                 g.arena[pos[j]] = v[j];
             }
         }
-        // bucketed hash sets: read the home bucket of every pair (L2, not a
-        // possibly stale L1 line), then claim a slot by CAS
-        uint4 b0[PP], b1[PP];
+        // bucketed hash sets: read the first half of the home bucket of every
+        // pair (L2, not a possibly stale L1 line), then claim the first empty
+        // slot by CAS; occupied slots stay a prefix of each bucket
+        uint4 b0[PP];
         uint32_t bk[PP];
         uint32_t rep = 0;  // set-semantics inserts: bit j = pair j claimed its slot
 #pragma unroll
         for (int j = 0; j < PP; ++j) {
             if (r[j] != NIL && hs[j] != 0) {
                 bk[j] = mix32(v[j]) & (hs[j] / HB - 1);
-                const uint4 *bp = reinterpret_cast<const uint4 *>(g.arena + aoff[j] + bk[j] * HB);
-                b0[j] = __ldcg(bp);
-                b1[j] = __ldcg(bp + 1);
+                b0[j] = __ldcg(reinterpret_cast<const uint4 *>(g.arena + aoff[j] + bk[j] * HB));
             }
         }
 #pragma unroll
@@ -649,36 +652,36 @@ __global__ void __launch_bounds__(256) k_scatter_member(GraphView g, const uint3
             if (r[j] != NIL && hs[j] != 0) {
                 const uint32_t nbk = hs[j] / HB;
                 uint32_t *tab = g.arena + aoff[j];
-                uint32_t b = bk[j];
-                uint32_t w[HB] = {b0[j].x, b0[j].y, b0[j].z, b0[j].w, b1[j].x, b1[j].y, b1[j].z, b1[j].w};
-                // each pass either ends, moves to the next bucket, or follows a
-                // slot taken by another insert: (HB + 1) * nbk passes suffice
-                for (uint32_t probe = 0; probe < (HB + 1) * nbk; ++probe) {
-                    uint32_t hit = NIL, empty = NIL;
-#pragma unroll
-                    for (uint32_t k = 0; k < HB; ++k) {
-                        if (hit == NIL && w[k] == v[j]) hit = k;
-                        if (empty == NIL && w[k] == EMPTY_KEY) empty = k;
-                    }
+                uint32_t b = bk[j], half = 0;
+                uint4 w = b0[j];
+                // each pass ends, moves on by half a bucket, or rereads after
+                // losing a slot to another insert (which filled that slot):
+                // 2 * nbk * 5 passes bound the loop
+                for (uint32_t probe = 0; probe < 10 * nbk; ++probe) {
+                    const uint32_t hit = w.x == v[j] ? 0u : w.y == v[j] ? 1u : w.z == v[j] ? 2u
+                                       : w.w == v[j] ? 3u : NIL;
                     if (hit != NIL) {
-                        pos[j] = aoff[j] + b * HB + hit;
+                        pos[j] = aoff[j] + b * HB + half * 4 + hit;
                         break;
                     }
+                    const uint32_t empty = w.x == EMPTY_KEY ? 0u : w.y == EMPTY_KEY ? 1u : w.z == EMPTY_KEY ? 2u
+                                         : w.w == EMPTY_KEY ? 3u : NIL;
                     if (empty != NIL) {
-                        const uint32_t old = atomicCAS(&tab[b * HB + empty], EMPTY_KEY, v[j]);
+                        const uint32_t slot = b * HB + half * 4 + empty;
+                        const uint32_t old = atomicCAS(&tab[slot], EMPTY_KEY, v[j]);
                         if (old == EMPTY_KEY || old == v[j]) {
-                            pos[j] = aoff[j] + b * HB + empty;
+                            pos[j] = aoff[j] + slot;
                             if (MODE == MODE_DEDUP && old == EMPTY_KEY) rep |= 1u << j;
                             break;
                         }
-                        // lost the slot: reread this bucket
+                        // lost the slot: reread this half
+                    } else if (half == 0) {
+                        half = 1;
                     } else {
+                        half = 0;
                         b = (b + 1) & (nbk - 1);
                     }
-                    const uint4 *bp = reinterpret_cast<const uint4 *>(tab + b * HB);
-                    const uint4 x0 = __ldcg(bp), x1 = __ldcg(bp + 1);
-                    w[0] = x0.x; w[1] = x0.y; w[2] = x0.z; w[3] = x0.w;
-                    w[4] = x1.x; w[5] = x1.y; w[6] = x1.z; w[7] = x1.w;
+                    w = __ldcg(reinterpret_cast<const uint4 *>(tab + b * HB + half * 4));
                 }
                 if (pos[j] == NIL) latch_status(g.dev, 5u /* GV_ERR_STATE */);
             }
@@ -804,45 +807,41 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
                     }
                 }
             } else {
-                // global bucketed hash set: the home buckets of all four
-                // entries are loaded together; only a full bucket without the
-                // key sends a lookup on to the next bucket
+                // global bucketed hash set.  Occupied slots of a bucket are a
+                // prefix (inserts claim the first empty slot), so a lookup
+                // reads the first half-bucket of the home buckets of all four
+                // entries together and goes on to the second half, or the
+                // next bucket, only past four occupied slots without the key
                 const uint32_t *tab = g.arena + a.y;
                 const uint32_t nbk = a.z / HB;
-                uint4 x0[4], x1[4];
+                uint4 x0[4];
                 uint32_t bk[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     bk[j] = mix32(e[j]) & (nbk - 1);
-                    if ((vmask >> j) & 1u) {
-                        const uint4 *bp = reinterpret_cast<const uint4 *>(tab + bk[j] * HB);
-                        x0[j] = bp[0];
-                        x1[j] = bp[1];
-                    }
+                    if ((vmask >> j) & 1u) x0[j] = *reinterpret_cast<const uint4 *>(tab + bk[j] * HB);
                 }
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     if ((vmask >> j) & 1u) {
-                        for (uint32_t probe = 0; probe < nbk; ++probe) {
-                            const uint32_t w[HB] = {x0[j].x, x0[j].y, x0[j].z, x0[j].w,
-                                                    x1[j].x, x1[j].y, x1[j].z, x1[j].w};
-                            uint32_t hit = NIL;
-                            bool empty = false;
-#pragma unroll
-                            for (uint32_t k = 0; k < HB; ++k) {
-                                if (hit == NIL && w[k] == e[j]) hit = k;
-                                empty |= w[k] == EMPTY_KEY;
-                            }
-                            if (hit != NIL) {
+                        uint4 w = x0[j];
+                        uint32_t half = 0;  // 0: slots 0-3 of bucket bk[j]; 1: slots 4-7
+                        for (uint32_t probe = 0; probe < 2 * nbk; ++probe) {
+                            const uint32_t k = w.x == e[j] ? 0u : w.y == e[j] ? 1u : w.z == e[j] ? 2u
+                                             : w.w == e[j] ? 3u : NIL;
+                            if (k != NIL) {
                                 hitm |= 1u << j;
-                                if (MODE == MODE_QUERY) g.found[a.y + bk[j] * HB + hit] = 1u;
+                                if (MODE == MODE_QUERY) g.found[a.y + bk[j] * HB + half * 4 + k] = 1u;
                                 break;
                             }
-                            if (empty) break;
-                            bk[j] = (bk[j] + 1) & (nbk - 1);
-                            const uint4 *bp = reinterpret_cast<const uint4 *>(tab + bk[j] * HB);
-                            x0[j] = bp[0];
-                            x1[j] = bp[1];
+                            if (w.w == EMPTY_KEY) break;  // the prefix ended in this half
+                            if (half == 0) {
+                                half = 1;
+                            } else {
+                                half = 0;
+                                bk[j] = (bk[j] + 1) & (nbk - 1);
+                            }
+                            w = *reinterpret_cast<const uint4 *>(tab + bk[j] * HB + half * 4);
                         }
                     }
                 }
