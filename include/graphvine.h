@@ -368,6 +368,36 @@ gv_status gv_degree_offsets_noalloc(gv_graph *g, const uint32_t *d_vids, uint32_
 /* gv_status_string -- a static, human-readable name for a status code. */
 const char *gv_status_string(gv_status s);
 
+/*
+ * Graph analytics over the stored structure.  The paper lists analytics on
+ * the dynamic structure as future work ("Conclusion and future work") and
+ * defines none; both calls compute the textbook quantities, reading each
+ * adjacency through its tree of edge blocks as the delete and query paths do.
+ *
+ * gv_bfs -- unweighted single-source distances (level-synchronous
+ * breadth-first search over stored entries).
+ *   source    a vertex id < the vertex count (else GV_ERR_INVALID_ARG); a
+ *             deleted source reaches nothing.
+ *   dist      n uint32 (device or host), n = vertex count: dist[source] = 0,
+ *             dist[v] = length of a shortest path of stored edges, and
+ *             0xFFFFFFFF for unreached vertices.
+ *   h_levels  optional host uint32: number of distinct finite distances.
+ * Synchronises `stream` once per level (it reads the frontier size).
+ */
+gv_status gv_bfs(gv_graph *g, uint32_t source, uint32_t *dist, uint32_t *h_levels, void *stream);
+
+/*
+ * gv_pagerank -- `iterations` steps of PageRank power iteration in fp64 over
+ * the N live vertices: r_0 = 1/N; r'(v) = (1 - d)/N + d * (sum over stored
+ * entries (u, v) of r(u)/deg(u) + (sum of r(u) over live u with deg(u) = 0)/N),
+ * where every stored copy of a pair counts.  Deleted vertices get 0.
+ *   damping   d in [0, 1] (else GV_ERR_INVALID_ARG).
+ *   rank      n doubles (device or host), n = vertex count.
+ * The per-entry sums are fp64 atomic additions, so the summation order (and
+ * the last bits) can differ from run to run.
+ */
+gv_status gv_pagerank(gv_graph *g, uint32_t iterations, double damping, double *rank, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

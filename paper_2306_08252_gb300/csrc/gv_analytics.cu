@@ -1,0 +1,270 @@
+// Graph analytics over the stored structure: breadth-first search distances
+// and PageRank.  The paper names analytics on the dynamic structure as
+// future work ("Conclusion and future work"); the definitions are the
+// textbook ones (level-synchronous BFS; PageRank power iteration with
+// damping, dangling mass spread over all live vertices).
+//
+// Both read adjacencies the way the delete and query pipelines do: work
+// items of up to AIB blocks of one vertex, one warp per item, block ids by
+// lane-parallel walks of the vertex's complete binary tree ("Dynamic edge
+// inserts", bit-string rule), entries by 16-byte streaming loads.
+#include "gv_internal.cuh"
+#include "gv_launch.h"
+
+namespace gv {
+
+namespace {
+
+// Calls f(e4, vm) once per round of 32 quads of the item's stored entries
+// (all lanes call it: f may use warp collectives); vm bit j = entry j of the
+// lane's quad is a stored entry.  Returns false if a tree walk left the pool.
+template <typename F>
+__device__ __forceinline__ bool for_item_entries(const GraphView &g, uint32_t u, uint32_t c, uint32_t aib,
+                                                 uint32_t *sb, F &&f) {
+    const uint4 s = g.sent[u];
+    const uint32_t deg = s.x, nb = s.y, root = s.z;
+    const uint32_t kb = c * aib;
+    if (kb >= nb) return true;
+    const uint32_t nblk = min(aib, nb - kb);
+    const uint32_t lane = lane_id();
+    uint32_t bid = NIL;
+    if (lane < nblk) bid = cbt_walk(g.links, g.P, root, kb + 1 + lane);
+    if (__any_sync(FULL, lane < nblk && bid == NIL)) return false;
+    sb[lane] = bid;
+    __syncwarp();
+    const uint32_t C = g.C;
+    const uint32_t sbase = kb * C;
+    const uint32_t nslots = min(nblk * C, deg - sbase);
+    const uint32_t nquads = (nslots + 3) >> 2;
+    for (uint32_t q0 = 0; q0 < nquads; q0 += 32) {
+        const uint32_t q = q0 + lane;
+        uint4 e4 = make_uint4(NIL, NIL, NIL, NIL);
+        uint32_t vm = 0;
+        if (q < nquads) {
+            const uint32_t x = q << 2;
+            const uint32_t lb = divc(g.cmul, x);
+            e4 = ld_stream4(reinterpret_cast<const uint4 *>(g.data + (size_t)sb[lb] * C + (x - lb * C)));
+#pragma unroll
+            for (uint32_t j = 0; j < 4; ++j)
+                if (x + j < nslots) vm |= 1u << j;
+        }
+        f(e4, vm);
+    }
+    __syncwarp();
+    return true;
+}
+
+}  // namespace
+
+// Work items (vertex, chunk of aib blocks) for the live vertices of a list
+// (`*nlist` entries, read on the device) or of all vertices (list == NULL).
+__global__ void __launch_bounds__(256) k_an_items(GraphView g, const uint32_t *__restrict__ list,
+                                                  const uint32_t *nlist, uint32_t aib, uint2 *items,
+                                                  uint32_t *nitems) {
+    const uint32_t n = list ? *nlist : g.nv;
+    __shared__ uint32_t s_base;
+    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        uint32_t u = NIL, ni = 0;
+        if (i < n) {
+            u = list ? list[i] : i;
+            if (g.alive[u]) ni = (g.sent[u].y + aib - 1) / aib;
+        }
+        uint32_t tot;
+        const uint32_t ex = block_excl_scan(ni, &tot);
+        if (threadIdx.x == 0) s_base = tot ? atomicAdd(nitems, tot) : 0u;
+        __syncthreads();
+        for (uint32_t c = 0; c < ni; ++c) items[s_base + ex + c] = make_uint2(u, c);
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------- BFS
+
+// Source of the search: distance 0 and the first frontier, if alive.
+__global__ void k_bfs_seed(GraphView g, uint32_t source, uint32_t *dist, uint32_t *cur, uint32_t *ctr) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const bool live = source < g.nv && g.alive[source];
+        if (live) {
+            dist[source] = 0;
+            cur[0] = source;
+        }
+        ctr[0] = live ? 1u : 0u;  // frontier size
+        ctr[1] = 0;               // items
+        ctr[2] = 0;               // next frontier size
+    }
+}
+
+// One level: every stored entry v of a frontier vertex with no distance yet
+// is claimed by CAS (distance level + 1) and appended to the next frontier
+// (warp-aggregated append).
+__global__ void __launch_bounds__(256) k_bfs_expand(GraphView g, const uint2 *__restrict__ items,
+                                                    const uint32_t *nitems, uint32_t aib, uint32_t *dist,
+                                                    uint32_t level, uint32_t *next, uint32_t *nnext) {
+    __shared__ uint32_t s_bid[8][32];
+    const uint32_t n = *nitems;
+    const uint32_t lane = lane_id();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t nv = g.nv;
+    for (uint32_t it = warp; it < n; it += nwarps) {
+        const uint2 itm = items[it];
+        bool bad = false;
+        const bool ok = for_item_entries(g, itm.x, itm.y, aib, s_bid[threadIdx.x >> 5], [&](uint4 e4, uint32_t vm) {
+            const uint32_t e[4] = {e4.x, e4.y, e4.z, e4.w};
+            uint32_t push = 0;
+#pragma unroll
+            for (uint32_t j = 0; j < 4; ++j) {
+                if ((vm >> j) & 1u) {
+                    const uint32_t v = e[j];
+                    if (v >= nv) {
+                        bad = true;
+                    } else if (__ldcg(dist + v) == NIL && atomicCAS(dist + v, NIL, level + 1) == NIL) {
+                        push |= 1u << j;
+                    }
+                }
+            }
+            uint32_t tot;
+            const uint32_t ex = warp_excl_scan(__popc(push), &tot);
+            uint32_t base = 0;
+            if (lane == 0 && tot) base = atomicAdd(nnext, tot);
+            base = __shfl_sync(FULL, base, 0);
+            uint32_t w = base + ex;
+#pragma unroll
+            for (uint32_t j = 0; j < 4; ++j)
+                if ((push >> j) & 1u) next[w++] = e[j];
+        });
+        if ((!ok || bad) && lane == 0) latch_status(g.dev, 5u /* GV_ERR_STATE */);
+    }
+}
+
+// Next frontier becomes the current one: ctr = {frontier, items, next}.
+__global__ void k_bfs_advance(uint32_t *ctr) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        ctr[0] = ctr[2];
+        ctr[1] = 0;
+        ctr[2] = 0;
+    }
+}
+
+cudaError_t launch_bfs_seed(const GraphView &g, uint32_t source, uint32_t *dist, uint32_t *cur, uint32_t *ctr,
+                            const LaunchCfg &lc) {
+    PhaseScope ps(lc, PH_ANALYTICS);
+    if (g.nv) cudaMemsetAsync(dist, 0xFF, (size_t)g.nv * 4, lc.stream);
+    k_bfs_seed<<<1, 32, 0, lc.stream>>>(g, source, dist, cur, ctr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bfs_level(const GraphView &g, uint32_t aib, const uint32_t *cur, uint32_t *next, uint2 *items,
+                             uint32_t *ctr, uint32_t *dist, uint32_t level, const LaunchCfg &lc) {
+    PhaseScope ps(lc, PH_ANALYTICS);
+    const int grid = lc.num_sms * GRID_MULT;
+    k_an_items<<<grid, 256, 0, lc.stream>>>(g, cur, ctr, aib, items, ctr + 1);
+    k_bfs_expand<<<grid, 256, 0, lc.stream>>>(g, items, ctr + 1, aib, dist, level, next, ctr + 2);
+    k_bfs_advance<<<1, 32, 0, lc.stream>>>(ctr);
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------------------- PageRank
+
+// N = live vertices (64-bit counter, zeroed by the caller).
+__global__ void __launch_bounds__(256) k_pr_count(GraphView g, unsigned long long *N) {
+    unsigned long long k = 0;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < g.nv; v += gridDim.x * blockDim.x) k += g.alive[v];
+    k = block_sum_u64(k);
+    if (threadIdx.x == 0 && k) atomicAdd(N, k);
+}
+
+__global__ void __launch_bounds__(256) k_pr_start(GraphView g, double *r, const unsigned long long *N) {
+    const unsigned long long n = *N;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < g.nv; v += gridDim.x * blockDim.x)
+        r[v] = (n && g.alive[v]) ? 1.0 / (double)n : 0.0;
+}
+
+// Per vertex: its share r(u) / deg(u) (0 for dead or dangling vertices),
+// the accumulator cleared, and the dangling mass summed into *dang.
+__global__ void __launch_bounds__(256) k_pr_contrib(GraphView g, const double *__restrict__ r, double *c,
+                                                    double *acc, double *dang) {
+    __shared__ double s_p[8];
+    double dm = 0.0;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < g.nv; v += gridDim.x * blockDim.x) {
+        const uint32_t deg = g.sent[v].x;
+        const bool live = g.alive[v];
+        double share = 0.0;
+        if (live && deg) share = r[v] / (double)deg;
+        if (live && !deg) dm += r[v];
+        c[v] = share;
+        acc[v] = 0.0;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) dm += __shfl_xor_sync(FULL, dm, d);
+    if (lane_id() == 0) s_p[threadIdx.x >> 5] = dm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (uint32_t w = 0; w < (blockDim.x >> 5); ++w) t += s_p[w];
+        if (t != 0.0) atomicAdd(dang, t);
+    }
+}
+
+// Every stored entry (u, v) adds u's share to v's accumulator.
+__global__ void __launch_bounds__(256) k_pr_push(GraphView g, const uint2 *__restrict__ items, const uint32_t *nitems,
+                                                 uint32_t aib, const double *__restrict__ c, double *acc) {
+    __shared__ uint32_t s_bid[8][32];
+    const uint32_t n = *nitems;
+    const uint32_t lane = lane_id();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t nv = g.nv;
+    for (uint32_t it = warp; it < n; it += nwarps) {
+        const uint2 itm = items[it];
+        const double cu = c[itm.x];
+        bool bad = false;
+        const bool ok = for_item_entries(g, itm.x, itm.y, aib, s_bid[threadIdx.x >> 5], [&](uint4 e4, uint32_t vm) {
+            const uint32_t e[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+            for (uint32_t j = 0; j < 4; ++j) {
+                if ((vm >> j) & 1u) {
+                    if (e[j] < nv) atomicAdd(acc + e[j], cu);
+                    else bad = true;
+                }
+            }
+        });
+        if ((!ok || bad) && lane == 0) latch_status(g.dev, 5u /* GV_ERR_STATE */);
+    }
+}
+
+// r(v) = (1 - d)/N + d * (acc(v) + dangling/N) for live v, 0 otherwise; the
+// other dangling slot is cleared for the next iteration.
+__global__ void __launch_bounds__(256) k_pr_update(GraphView g, double *r, const double *__restrict__ acc,
+                                                   double *dang, uint32_t slot, const unsigned long long *N,
+                                                   double damping) {
+    const double n = (double)*N;
+    const double dm = dang[slot];
+    if (blockIdx.x == 0 && threadIdx.x == 0) dang[slot ^ 1u] = 0.0;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < g.nv; v += gridDim.x * blockDim.x)
+        r[v] = g.alive[v] ? (1.0 - damping) / n + damping * (acc[v] + dm / n) : 0.0;
+}
+
+cudaError_t launch_pagerank(const GraphView &g, uint32_t aib, uint32_t iterations, double damping, double *r,
+                            double *c, double *acc, double *scal, unsigned long long *N, uint2 *items,
+                            uint32_t *nitems, const LaunchCfg &lc) {
+    PhaseScope ps(lc, PH_ANALYTICS);
+    const int grid = lc.num_sms * GRID_MULT;
+    const int gnv = grid_for(g.nv ? g.nv : 1, 256, grid);
+    cudaMemsetAsync(N, 0, 8, lc.stream);
+    cudaMemsetAsync(nitems, 0, 4, lc.stream);
+    cudaMemsetAsync(scal, 0, 2 * sizeof(double), lc.stream);
+    k_pr_count<<<gnv, 256, 0, lc.stream>>>(g, N);
+    k_pr_start<<<gnv, 256, 0, lc.stream>>>(g, r, N);
+    k_an_items<<<grid, 256, 0, lc.stream>>>(g, nullptr, nullptr, aib, items, nitems);
+    for (uint32_t it = 0; it < iterations; ++it) {
+        const uint32_t slot = it & 1u;
+        k_pr_contrib<<<gnv, 256, 0, lc.stream>>>(g, r, c, acc, scal + slot);
+        k_pr_push<<<grid, 256, 0, lc.stream>>>(g, items, nitems, aib, c, acc);
+        k_pr_update<<<gnv, 256, 0, lc.stream>>>(g, r, acc, scal, slot, N, damping);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace gv

@@ -90,6 +90,12 @@ struct gv_graph {
     uint64_t dict_bytes = 0;
     bool any_vertex_deleted = false;
     unsigned long long used_ub = 0;  // upper bound of blocks in use (pool growth policy)
+    // analytics scratch: items, two frontiers, counters, PageRank vectors
+    unsigned long long an_icap = 0, an_vcap = 0;
+    uint2 *an_items = nullptr;
+    uint32_t *an_cur = nullptr, *an_next = nullptr, *an_ctr = nullptr;
+    double *pr_c = nullptr, *pr_acc = nullptr, *pr_scal = nullptr;
+    unsigned long long *pr_n = nullptr;
     // graph set: members' vertex ranges (set_G == 0 for a plain graph)
     uint32_t set_G = 0;
     uint32_t *set_vbase = nullptr;          // device, G+1
@@ -805,6 +811,8 @@ gv_status gv_destroy(gv_graph *g) {
         dfree(g->owner_bits); dfree(g->vres);
         dfree(g->set_vbase); dfree(g->set_src); dfree(g->set_dst);
         dfree(g->pflag); dfree(g->dsrc2); dfree(g->dtmp);
+        dfree(g->an_items); dfree(g->an_cur); dfree(g->an_next); dfree(g->an_ctr);
+        dfree(g->pr_c); dfree(g->pr_acc); dfree(g->pr_scal); dfree(g->pr_n);
         for (auto &b : g->stage.buf) dfree(b.p);
         for (auto &r : g->prof.recs) {
             cudaEventDestroy(r.a);
@@ -1211,6 +1219,95 @@ gv_status gv_set_member_neighbors(gv_graph *set, uint32_t member, uint64_t *offs
     return neighbors_impl(set, (const uint32_t *)d, cnt, offsets, nbrs, nbr_capacity, total, s, false);
 }
 
+// --------------------------------------------------------------- analytics
+
+namespace {
+
+// Blocks per analytics work item: up to 512 entries, at most 32 blocks.
+uint32_t analytics_item_blocks(const gv_graph *g) {
+    return g->C ? std::min<uint32_t>(32, std::max<uint32_t>(1, 512 / g->C)) : 32;
+}
+
+gv_status ensure_analytics(gv_graph *g, bool pagerank) {
+    const uint32_t aib = analytics_item_blocks(g);
+    const unsigned long long items = (unsigned long long)g->nv + (g->P + aib - 1) / aib + 1;
+    if (items > g->an_icap || !g->an_icap) {
+        dfree(g->an_items);
+        g->an_icap = 0;
+        GV_TRY(dalloc(&g->an_items, items, &g->scratch_bytes));
+        g->an_icap = items;
+    }
+    const unsigned long long nv = std::max<unsigned long long>(g->nv, 1);
+    if (nv > g->an_vcap || !g->an_vcap) {
+        dfree(g->an_cur); dfree(g->an_next); dfree(g->pr_c); dfree(g->pr_acc);
+        g->an_vcap = 0;
+        GV_TRY(dalloc(&g->an_cur, nv, &g->scratch_bytes));
+        GV_TRY(dalloc(&g->an_next, nv, &g->scratch_bytes));
+        g->an_vcap = nv;
+    }
+    if (!g->an_ctr) GV_TRY(dalloc(&g->an_ctr, 4, &g->scratch_bytes));
+    if (pagerank) {
+        if (!g->pr_c) GV_TRY(dalloc(&g->pr_c, g->an_vcap, &g->scratch_bytes));
+        if (!g->pr_acc) GV_TRY(dalloc(&g->pr_acc, g->an_vcap, &g->scratch_bytes));
+        if (!g->pr_scal) GV_TRY(dalloc(&g->pr_scal, 2, &g->scratch_bytes));
+        if (!g->pr_n) GV_TRY(dalloc(&g->pr_n, 1, &g->scratch_bytes));
+    }
+    return GV_OK;
+}
+
+}  // namespace
+
+gv_status gv_bfs(gv_graph *g, uint32_t source, uint32_t *dist, uint32_t *h_levels, void *stream) {
+    if (!g || !dist || source >= g->nv) return GV_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    g->last_stream = s;
+    GV_TRY(ensure_analytics(g, false));
+    void *dd = dist;
+    bool hd = false;
+    GV_TRY(output_ptr(g, 0, dist, (size_t)g->nv * 4, &dd, &hd));
+    const GraphView v = view(g);
+    const uint32_t aib = analytics_item_blocks(g);
+    GV_CK(gv::launch_bfs_seed(v, source, (uint32_t *)dd, g->an_cur, g->an_ctr, lcfg(g, s)));
+    uint32_t *cur = g->an_cur, *nxt = g->an_next;
+    uint32_t levels = 0;
+    for (uint32_t level = 0;; ++level) {
+        // frontier size of this level (one read per level)
+        GV_CK(cudaMemcpyAsync(g->h_small, g->an_ctr, 4, cudaMemcpyDeviceToHost, s));
+        GV_CK(cudaStreamSynchronize(s));
+        const uint32_t nf = (uint32_t)(g->h_small[0] & 0xFFFFFFFFull);
+        if (nf == 0) break;
+        levels = level + 1;
+        GV_CK(gv::launch_bfs_level(v, aib, cur, nxt, g->an_items, g->an_ctr, (uint32_t *)dd, level, lcfg(g, s)));
+        std::swap(cur, nxt);
+    }
+    if (hd) {
+        GV_CK(cudaMemcpyAsync(dist, dd, (size_t)g->nv * 4, cudaMemcpyDeviceToHost, s));
+        GV_CK(cudaStreamSynchronize(s));
+    }
+    if (h_levels) *h_levels = levels;
+    return check_launch();
+}
+
+gv_status gv_pagerank(gv_graph *g, uint32_t iterations, double damping, double *rank, void *stream) {
+    if (!g || (!rank && g->nv) || !(damping >= 0.0 && damping <= 1.0)) return GV_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    g->last_stream = s;
+    if (g->nv == 0) return GV_OK;
+    GV_TRY(ensure_analytics(g, true));
+    void *dr = rank;
+    bool hr = false;
+    GV_TRY(output_ptr(g, 0, rank, (size_t)g->nv * 8, &dr, &hr));
+    GV_CK(gv::launch_pagerank(view(g), analytics_item_blocks(g), iterations, damping, (double *)dr, g->pr_c,
+                              g->pr_acc, g->pr_scal, g->pr_n, g->an_items, g->an_ctr + 1, lcfg(g, s)));
+    if (hr) {
+        GV_CK(cudaMemcpyAsync(rank, dr, (size_t)g->nv * 8, cudaMemcpyDeviceToHost, s));
+        GV_CK(cudaStreamSynchronize(s));
+    }
+    return check_launch();
+}
+
 static const char *kPhaseNames[gv::PH_COUNT] = {
     "insert.count",   "insert.touched", "insert.plan",     "insert.link",      "insert.scatter",
     "insert.finalize",
@@ -1218,7 +1315,7 @@ static const char *kPhaseNames[gv::PH_COUNT] = {
     "delete.mark",    "delete.mark_tiny", "delete.vscan",  "delete.move",      "delete.finalize",
     "query.count",    "query.touched",  "query.plan",      "query.arena",      "query.scatter",
     "query.mark",     "query.mark_tiny", "query.out",      "query.finalize",
-    "vertex_delete",  "neighbors",      "other"};
+    "vertex_delete",  "neighbors",      "other",          "analytics"};
 
 uint32_t gv_profile_num_phases(void) { return gv::PH_COUNT; }
 

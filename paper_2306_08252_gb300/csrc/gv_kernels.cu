@@ -544,11 +544,10 @@ __global__ void __launch_bounds__(256) k_plan_member(GraphView g) {
             else if (m <= LIST_MAX) lw = m;
             else hw = member_words(m);
             if (s.y > 0) {
-                if (MODE == MODE_QUERY) {
-                    if (s.x <= min(TINY_DEG_Q, TINY_NB_Q * g.C) && s.y <= TINY_NB_Q && m <= TINY_M) tiny = 1;
-                } else if (MODE != MODE_DEDUP && s.x <= tiny_deg && s.y <= TINY_NB && m <= TINY_M) {
-                    tiny = 1;
-                }
+                const bool small = MODE == MODE_QUERY
+                    ? (s.x <= min(TINY_DEG_Q, TINY_NB_Q * g.C) && s.y <= TINY_NB_Q && m <= TINY_M)
+                    : (MODE != MODE_DEDUP && s.x <= tiny_deg && s.y <= TINY_NB && m <= TINY_M);
+                if (small) tiny = 1;
                 else ni = (s.y + IB - 1) / IB;
             }
         }
@@ -1555,14 +1554,6 @@ cudaError_t launch_set_insert_counts(const GraphView &g, const LaunchCfg &lc);
 
 // ------------------------------------------------------------------ launch
 
-namespace {
-inline int grid_for(unsigned long long work, int per_block, int cap) {
-    unsigned long long g = (work + per_block - 1) / per_block;
-    if (g < 1) g = 1;
-    if (g > (unsigned long long)cap) g = cap;
-    return (int)g;
-}
-}  // namespace
 
 cudaError_t launch_count(int mode, const GraphView &g, const uint32_t *src, const uint32_t *dst,
                          unsigned long long n, const LaunchCfg &lc) {

@@ -16,7 +16,7 @@ enum Phase : int {
     PH_DEL_VSCAN, PH_DEL_MOVE, PH_DEL_FINALIZE,
     PH_QRY_COUNT, PH_QRY_TOUCHED, PH_QRY_PLAN, PH_QRY_ARENA, PH_QRY_SCATTER, PH_QRY_MARK, PH_QRY_MARK_TINY,
     PH_QRY_OUT, PH_QRY_FINALIZE,
-    PH_VDEL, PH_NEIGHBORS, PH_OTHER,
+    PH_VDEL, PH_NEIGHBORS, PH_OTHER, PH_ANALYTICS,
     PH_COUNT
 };
 
@@ -68,6 +68,15 @@ struct PhaseScope {
 };
 
 // Group-by-source counting pass over a pair batch (all modes).
+// Blocks for `work` units at `per_block` units per block, at least 1 and at
+// most `cap` (grid-stride kernels cover the rest).
+inline int grid_for(unsigned long long work, int per_block, int cap) {
+    unsigned long long g = (work + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > (unsigned long long)cap) g = cap;
+    return (int)g;
+}
+
 cudaError_t launch_count(int mode, const GraphView &g, const uint32_t *src, const uint32_t *dst,
                          unsigned long long n, const LaunchCfg &lc);
 // Rejected-pair count only (batches that cannot match any stored edge).
@@ -118,6 +127,14 @@ cudaError_t launch_dedup_counts(Dev *dev, const unsigned long long *tmp, unsigne
                                 unsigned long long *counts, const LaunchCfg &lc);
 cudaError_t launch_grow_queue(const uint32_t *q, unsigned long long P, unsigned long long qf,
                               unsigned long long nfree, uint32_t *q2, unsigned long long P2, const LaunchCfg &lc);
+// graph analytics (gv_analytics.cu)
+cudaError_t launch_bfs_seed(const GraphView &g, uint32_t source, uint32_t *dist, uint32_t *cur, uint32_t *ctr,
+                            const LaunchCfg &lc);
+cudaError_t launch_bfs_level(const GraphView &g, uint32_t aib, const uint32_t *cur, uint32_t *next, uint2 *items,
+                             uint32_t *ctr, uint32_t *dist, uint32_t level, const LaunchCfg &lc);
+cudaError_t launch_pagerank(const GraphView &g, uint32_t aib, uint32_t iterations, double damping, double *r,
+                            double *c, double *acc, double *scal, unsigned long long *N, uint2 *items,
+                            uint32_t *nitems, const LaunchCfg &lc);
 cudaError_t launch_finalize_count_only(const GraphView &g, const LaunchCfg &lc);
 cudaError_t launch_validate(const GraphView &g, uint32_t *owner_bits,
                             unsigned long long *violations, const LaunchCfg &lc);

@@ -292,14 +292,6 @@ __global__ void __launch_bounds__(256) k_validate_queue(GraphView g, uint32_t *o
 
 // ------------------------------------------------------------------ launch
 
-namespace {
-inline int grid_for(unsigned long long work, int per_block, int cap) {
-    unsigned long long g = (work + per_block - 1) / per_block;
-    if (g < 1) g = 1;
-    if (g > (unsigned long long)cap) g = cap;
-    return (int)g;
-}
-}  // namespace
 
 cudaError_t launch_init_vertices(const GraphView &g, uint32_t from, uint32_t to, const LaunchCfg &lc) {
     if (to > from) k_init_vertices<<<grid_for(to - from, 256, lc.num_sms * 16), 256, 0, lc.stream>>>(g, from, to);

@@ -77,6 +77,8 @@ SIGNATURES = {
     "gv_delete_vertices": ([c_vp, c_vp, c_u32, c_vp], ctypes.c_int),
     "gv_export_csr": ([c_vp, c_vp, c_vp, c_u64, ctypes.POINTER(c_u64), c_vp], ctypes.c_int),
     "gv_degrees": ([c_vp, c_vp, c_vp, c_vp], ctypes.c_int),
+    "gv_bfs": ([c_vp, c_u32, c_vp, ctypes.POINTER(c_u32), c_vp], ctypes.c_int),
+    "gv_pagerank": ([c_vp, c_u32, ctypes.c_double, c_vp, c_vp], ctypes.c_int),
     "gv_reserve": ([c_vp, c_u64], ctypes.c_int),
     "gv_sync": ([c_vp], ctypes.c_int),
     "gv_stats": ([c_vp, ctypes.POINTER(gv_stats_t)], ctypes.c_int),
@@ -222,6 +224,18 @@ def gv_export_csr(g, offsets, nbrs, nbr_capacity, stream=None):
     total = c_u64(0)
     code = load().gv_export_csr(g, ptr(offsets), ptr(nbrs), nbr_capacity, ctypes.byref(total), stream)
     return code, total.value
+
+
+def gv_bfs(g, source, dist, stream=None):
+    """Distances from `source` into `dist` (uint32 per vertex); returns the
+    number of levels."""
+    levels = c_u32(0)
+    check(load().gv_bfs(g, source, ptr(dist), ctypes.byref(levels), stream), "gv_bfs")
+    return levels.value
+
+
+def gv_pagerank(g, iterations, damping, rank, stream=None):
+    return check(load().gv_pagerank(g, iterations, damping, ptr(rank), stream), "gv_pagerank")
 
 
 def gv_degrees(g, deg, alive=None, stream=None):
@@ -434,6 +448,20 @@ class Graph:
         code, total = gv_neighbors(self.handle, vids, off, nb, nb.size, self._s())
         check(code, "gv_neighbors")
         return off, nb[:total]
+
+    def bfs(self, source, dist=None):
+        """(dist, levels): uint32 distances (0xFFFFFFFF = unreached); `dist`
+        may be a device tensor or host array of vertex-count entries."""
+        if dist is None:
+            dist = np.zeros(max(self.stats()["num_vertices"], 1), dtype=np.uint32)
+        levels = gv_bfs(self.handle, source, dist, self._s())
+        return dist, levels
+
+    def pagerank(self, iterations, damping=0.85, rank=None):
+        if rank is None:
+            rank = np.zeros(max(self.stats()["num_vertices"], 1), dtype=np.float64)
+        gv_pagerank(self.handle, iterations, damping, rank, self._s())
+        return rank
 
     def export_csr(self):
         st = self.stats()
