@@ -690,6 +690,20 @@ def run_rows(args):
     nbrs = torch.zeros(E, dtype=torch.int32, device="cuda")
     ms = timed(lambda: gv.gv_neighbors(g.handle, vids, offs, nbrs, E, stream.cuda_stream))
     row("a8", f"neighbours of all {nv} vertices", E, "entries", ms, 8 * E + 4 * nv + 16 * nv + 8 * (nv + 1))
+
+    # next rows: BFS from the largest hub, PageRank (10 iterations)
+    dist = torch.zeros(nv, dtype=torch.int32, device="cuda")
+    src = int(np.argmax(deg0))
+    ms = timed(lambda: gv.gv_bfs(g.handle, src, dist, stream.cuda_stream), n=3)
+    reached = dist.cpu().numpy().view(np.uint32) != 0xFFFFFFFF
+    trav = int(deg0[reached].sum())
+    row("f2-bfs", f"BFS from vertex {src} ({int(reached.sum())} reached)", trav, "traversed edges", ms,
+        8 * trav + 16 * int(reached.sum()) + 4 * nv, timer="CUDA events (one host read per level)")
+    rank = torch.zeros(nv, dtype=torch.float64, device="cuda")
+    iters = 10
+    ms = timed(lambda: gv.gv_pagerank(g.handle, iters, 0.85, rank, stream.cuda_stream), n=3)
+    row("f2-pagerank", f"PageRank, {iters} iterations", iters * E, "edge visits", ms,
+        iters * (4 * E + 8 * E + 48 * nv))
     g.close()
 
     # a9 / a10 on the uniform 2^22 graph
