@@ -163,6 +163,14 @@ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
     return x;
 }
 
+// Home slot of key v in a table of `size` slots or buckets (a power of two):
+// the top bits of v times an odd constant (multiplicative hashing, Knuth,
+// TAOCP vol. 3, 6.4), two instructions where a full mixer takes seven; the
+// membership tables it indexes are probed once per stored entry.
+__device__ __forceinline__ uint32_t hidx(uint32_t v, uint32_t size) {
+    return __umulhi(v * 0x9E3779B1u, size);
+}
+
 // Slot of vertex u in the per-call vertex scratch arrays: a bijection of
 // [0, capacity) (multiplication by an odd constant modulo the power-of-two
 // capacity).  Power-law graphs put most updates on a few low ids; without

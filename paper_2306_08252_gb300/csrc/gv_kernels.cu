@@ -642,7 +642,7 @@ __global__ void __launch_bounds__(256) k_scatter_member(GraphView g, const uint3
 #pragma unroll
         for (int j = 0; j < PP; ++j) {
             if (r[j] != NIL && hs[j] != 0) {
-                bk[j] = mix32(v[j]) & (hs[j] / HB - 1);
+                bk[j] = hidx(v[j], hs[j] / HB);
                 b0[j] = __ldcg(reinterpret_cast<const uint4 *>(g.arena + aoff[j] + bk[j] * HB));
             }
         }
@@ -756,7 +756,7 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
                 __syncwarp();
                 for (uint32_t j = lane; j < a.x; j += 32) {
                     const uint32_t v = g.arena[a.y + j];
-                    uint32_t h = mix32(v) & hmask;
+                    uint32_t h = hidx(v, hmask + 1);
                     for (;;) {
                         const uint32_t old = atomicCAS(&hk[h], EMPTY_KEY, v);
                         if (old == EMPTY_KEY || old == v) break;
@@ -792,7 +792,7 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     if ((vmask >> j) & 1u) {
-                        uint32_t h = mix32(e[j]) & hmask;
+                        uint32_t h = hidx(e[j], hmask + 1);
                         for (;;) {
                             const uint32_t k = hk[h];
                             if (k == e[j]) {
@@ -817,7 +817,7 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
                 uint32_t bk[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    bk[j] = mix32(e[j]) & (nbk - 1);
+                    bk[j] = hidx(e[j], nbk);
                     if ((vmask >> j) & 1u) x0[j] = *reinterpret_cast<const uint4 *>(tab + bk[j] * HB);
                 }
 #pragma unroll
@@ -878,7 +878,7 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
             if (listmode) {
                 for (uint32_t j = lane; j < a.x; j += 32) {
                     const uint32_t v = g.arena[a.y + j];
-                    uint32_t h = mix32(v) & hmask;
+                    uint32_t h = hidx(v, hmask + 1);
                     while (hk[h] != v) h = (h + 1) & hmask;
                     if (hf[h]) g.found[a.y + j] = 1u;
                 }
