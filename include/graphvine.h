@@ -295,9 +295,30 @@ const char *gv_profile_phase_name(uint32_t phase);
  * inserts commute), which lets a server merge queued insert requests into
  * one launch sequence.  nseg in 1 .. 1024; all arrays device memory; the
  * graph's C must already be fixed (after gv_bulk_build or with a configured
- * C).
+ * C).  If the merged batch does not fit the pool, nothing is inserted and
+ * every request gets {0, 0}.
  */
 gv_status gv_insert_edges_segmented(gv_graph *g, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
+                                    const uint64_t *d_offsets, uint32_t nseg, uint64_t *d_counts, void *stream);
+
+/*
+ * gv_delete_edges_segmented -- one delete call for nseg consecutive batches
+ * (segments) of the same graph, with the result of applying them one call
+ * each, in segment order: segment s holds pairs d_offsets[s] ..
+ * d_offsets[s+1]-1.  The graph ends as after the nseg deletes (Algorithm 2
+ * removes every stored copy of each named pair, so a pair named again by a
+ * later segment finds nothing left); d_counts[2s] = stored entries removed
+ * for pairs whose key segment s is the first to name, d_counts[2s+1] = pairs
+ * of segment s rejected (endpoint out of range or dead).  A serving loop uses
+ * it to run queued delete requests as one batch.
+ *   d_offsets  nseg+1 uint64 (device), ascending, d_offsets[0] = 0,
+ *              d_offsets[nseg] = n.
+ *   nseg       1 .. 1024.
+ *   d_counts   2*nseg uint64 (device), written.
+ * Device arrays only; not on graph sets.  The paper has no segmented call
+ * (its batches are one call each).
+ */
+gv_status gv_delete_edges_segmented(gv_graph *g, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
                                     const uint64_t *d_offsets, uint32_t nseg, uint64_t *d_counts, void *stream);
 
 /*

@@ -154,7 +154,7 @@ void dfree(T *&p) {
 }
 
 GraphView view(const gv_graph *g) {
-    GraphView v;
+    GraphView v{};  // every field not set below is zero (NULL)
     v.sent = g->sent;
     v.alive = g->alive;
     v.data = g->data;
@@ -1155,7 +1155,38 @@ gv_status gv_insert_edges_segmented(gv_graph *g, const uint32_t *d_src, const ui
     v.set_counts = reinterpret_cast<unsigned long long *>(d_counts);
     GV_CK(gv::launch_segment_counts(v, d_src, d_dst, n, lcfg(g, s)));
     GV_CK(gv::launch_set_insert_counts(v, lcfg(g, s)));
-    GV_TRY(insert_impl(g, d_src, d_dst, n, nullptr, s));
+    if (!g->dtmp) GV_TRY(dalloc(&g->dtmp, 4, &g->scratch_bytes));
+    GV_TRY(insert_impl(g, d_src, d_dst, n, reinterpret_cast<uint64_t *>(g->dtmp), s));
+    // an insert that ran out of pool blocks is a no-op: every segment {0, 0}
+    GV_CK(gv::launch_segment_noop_check(v, g->dtmp, n, lcfg(g, s)));
+    return check_launch();
+}
+
+gv_status gv_delete_edges_segmented(gv_graph *g, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
+                                    const uint64_t *d_offsets, uint32_t nseg, uint64_t *d_counts, void *stream) {
+    if (!g || g->set_G || nseg == 0 || nseg > gv::SET_MAX_G || !d_offsets || !d_counts) return GV_ERR_INVALID_ARG;
+    if (n > kMaxBatch || (n > 0 && (!d_src || !d_dst))) return GV_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    if (is_host_ptr(d_offsets) || is_host_ptr(d_counts) || (n > 0 && (is_host_ptr(d_src) || is_host_ptr(d_dst))))
+        return GV_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    g->last_stream = s;
+    GV_CK(cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * 2 * nseg, s));
+    if (n == 0) return check_launch();
+    GraphView v = view(g);
+    v.set_G = nseg;
+    v.set_off = reinterpret_cast<const unsigned long long *>(d_offsets);
+    v.set_counts = reinterpret_cast<unsigned long long *>(d_counts);
+    GV_CK(gv::launch_segment_counts(v, d_src, d_dst, n, lcfg(g, s)));  // rejected pairs per segment
+    if (g->C == 0) return check_launch();                               // nothing stored: nothing to delete
+    GV_TRY(ensure_batch(g, n, gv::MODE_DELETE));
+    GraphView w = view(g);
+    w.set_G = nseg;
+    w.set_off = v.set_off;
+    w.set_counts = v.set_counts;
+    w.seg_own = g->found;  // owner segment per arena word (the delete leaves `found` unused)
+    GV_CK(gv::launch_count(gv::MODE_DELETE, w, d_src, d_dst, n, lcfg(g, s)));
+    GV_CK(gv::launch_member_tail(gv::MODE_DELETE, w, d_src, d_dst, n, g->tcap, nullptr, nullptr, lcfg(g, s)));
     return check_launch();
 }
 

@@ -97,7 +97,22 @@ struct GraphView {
     const uint32_t *set_vbase;         // G+1 first vertex of each member (device)
     const unsigned long long *set_off; // G+1 first pair of each member's batch (device)
     unsigned long long *set_counts;    // 2G per-member counts of this call (device)
+    // segmented deletes (set_G segments of one batch, set_vbase unused): the
+    // segment that first names each batch key, one word per arena word;
+    // NULL otherwise
+    uint32_t *seg_own;
 };
+
+// Segment of pair i: the last s with off[s] <= i (off has G+1 entries).
+__device__ __forceinline__ uint32_t segment_of(const unsigned long long *off, uint32_t G, unsigned long long i) {
+    uint32_t lo = 0, hi = G;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (off[mid] <= i) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
 
 // Largest number of members of a graph set (per-CTA shared histograms).
 constexpr uint32_t SET_MAX_G = 1024;

@@ -578,6 +578,13 @@ __global__ void __launch_bounds__(256) k_plan_member(GraphView g) {
     }
 }
 
+// Segmented deletes: one removed entry for the segment that owns its key
+// (shared histogram, flushed to the per-segment counts by the kernel).
+__device__ __forceinline__ void seg_count(uint32_t *hist, uint32_t own, uint32_t G, Dev *dev) {
+    if (own < G) atomicAdd(&hist[own], 1u);
+    else latch_status(dev, 5u /* GV_ERR_STATE */);
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(256) k_arena_init(GraphView g) {
     // hash region -> EMPTY; query hit flags of both regions -> 0 (list
@@ -593,6 +600,7 @@ __global__ void __launch_bounds__(256) k_arena_init(GraphView g) {
             const unsigned long long i = g.hbase + (k - (Q ? lused : 0ull));
             g.arena[i] = EMPTY_KEY;
             if (Q) g.found[i] = 0u;
+            if (MODE == MODE_DELETE && g.seg_own) g.seg_own[i] = NIL;
         }
     }
 }
@@ -685,6 +693,17 @@ __global__ void __launch_bounds__(256) k_scatter_member(GraphView g, const uint3
                 if (pos[j] == NIL) latch_status(g.dev, 5u /* GV_ERR_STATE */);
             }
         }
+        if (MODE == MODE_DELETE && g.seg_own) {
+            // segmented delete: each key's owner is the first segment naming it
+#pragma unroll
+            for (int j = 0; j < PP; ++j) {
+                if (pos[j] != NIL) {
+                    const uint32_t sg = segment_of(g.set_off, g.set_G, i0 + j * stride);
+                    if (hs[j] == 0) g.seg_own[pos[j]] = sg;
+                    else atomicMin(g.seg_own + pos[j], sg);
+                }
+            }
+        }
         if (MODE == MODE_QUERY || MODE == MODE_DEDUP) {
 #pragma unroll
             for (int j = 0; j < PP; ++j) {
@@ -712,7 +731,9 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
     __shared__ uint32_t s_free[8][64];
     __shared__ uint32_t s_bid[8][32];
     __shared__ uint32_t s_hkey[8][2 * LIST_MAX];
-    __shared__ uint32_t s_hfound[8][(MODE == MODE_QUERY) ? 2 * LIST_MAX : 1];
+    // queries: hit flag per list key; segmented deletes: owner segment per key
+    __shared__ uint32_t s_hfound[8][(MODE == MODE_QUERY || MODE == MODE_DELETE) ? 2 * LIST_MAX : 1];
+    const bool segd = MODE == MODE_DELETE && g.seg_own != nullptr;
     __shared__ uint32_t s_mhist[(MODE == MODE_QUERY) ? 1 : SET_MAX_G];
     if (MODE != MODE_QUERY && g.set_G) {
         for (uint32_t i = threadIdx.x; i < g.set_G; i += blockDim.x) s_mhist[i] = 0;
@@ -752,6 +773,7 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
                 for (uint32_t j = lane; j <= hmask; j += 32) {
                     hk[j] = EMPTY_KEY;
                     if (MODE == MODE_QUERY) hf[j] = 0u;
+                    if (segd) hf[j] = NIL;
                 }
                 __syncwarp();
                 for (uint32_t j = lane; j < a.x; j += 32) {
@@ -762,6 +784,7 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
                         if (old == EMPTY_KEY || old == v) break;
                         h = (h + 1) & hmask;
                     }
+                    if (segd) atomicMin(&hf[h], g.seg_own[a.y + j]);
                 }
             }
         }
@@ -798,6 +821,7 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
                             if (k == e[j]) {
                                 hitm |= 1u << j;
                                 if (MODE == MODE_QUERY) hf[h] = 1u;
+                                if (segd) seg_count(s_mhist, hf[h], g.set_G, dev);
                                 break;
                             }
                             if (k == EMPTY_KEY) break;
@@ -831,6 +855,7 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
                             if (k != NIL) {
                                 hitm |= 1u << j;
                                 if (MODE == MODE_QUERY) g.found[a.y + bk[j] * HB + half * 4 + k] = 1u;
+                                if (segd) seg_count(s_mhist, g.seg_own[a.y + bk[j] * HB + half * 4 + k], g.set_G, dev);
                                 break;
                             }
                             if (w.w == EMPTY_KEY) break;  // the prefix ended in this half
@@ -901,7 +926,7 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
                     const uint32_t u = g.t_vid[t];
                     g.sent[u] = make_uint4(degn, nbn, nbn ? root : NIL, nbn ? lastb : NIL);
                     removed += deg - degn;
-                    if (g.set_G) atomicAdd(&s_mhist[member_of(g.set_vbase, g.set_G, u)], deg - degn);
+                    if (g.set_G && !g.seg_own) atomicAdd(&s_mhist[member_of(g.set_vbase, g.set_G, u)], deg - degn);
                 }
             }
         } else {
@@ -1007,6 +1032,11 @@ __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
                         for (int j = 0; j < (int)TINY_M; ++j) hm |= (uint32_t)(d[j] == e[jj]) << j;
                         hit = hm != 0;
                         if (MODE == MODE_QUERY) qhit |= hm;
+                        if (MODE == MODE_DELETE && hit && g.seg_own) {
+                            uint32_t own = NIL;
+                            for (uint32_t r = hm; r; r &= r - 1) own = min(own, g.seg_own[aoff + __ffs(r) - 1]);
+                            seg_count(s_mhist, own, g.set_G, dev);
+                        }
                     }
                     if (MODE != MODE_QUERY && !hit) {
                         if (w != x + jj) {
@@ -1038,7 +1068,7 @@ __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
             const uint32_t u = g.t_vid[t];
             g.sent[u] = make_uint4(w, nbn, nbn ? root : NIL, nbn ? bl.get(nbn - 1) : NIL);
             removed += deg - w;
-            if (g.set_G) atomicAdd(&s_mhist[member_of(g.set_vbase, g.set_G, u)], deg - w);
+            if (g.set_G && !g.seg_own) atomicAdd(&s_mhist[member_of(g.set_vbase, g.set_G, u)], deg - w);
         }
     }
     if (MODE != MODE_QUERY) {
@@ -1124,7 +1154,7 @@ __global__ void __launch_bounds__(256) k_vscan(GraphView g) {
             const uint32_t u = g.t_vid[t];
             g.sent[u] = make_uint4(degn, nbn, nbn ? root : NIL, lastb);
             removed += deg - degn;
-            if (g.set_G) atomicAdd(&s_mhist[member_of(g.set_vbase, g.set_G, u)], deg - degn);
+            if (g.set_G && !g.seg_own) atomicAdd(&s_mhist[member_of(g.set_vbase, g.set_G, u)], deg - degn);
         }
     }
     if (lane == 0 && removed) atomicAdd(&dev->call_a, removed);
@@ -1711,6 +1741,20 @@ cudaError_t launch_segment_counts(const GraphView &g, const uint32_t *src, const
     k_segment_counts<<<(int)blocks, 256, 0, lc.stream>>>(g, src, dst, n);
     return cudaGetLastError();
 }
+// After a segmented insert: its totals {inserted, rejected} are {0, 0} only
+// when the call was a no-op (pool exhausted); then every segment gets {0, 0}.
+__global__ void k_segment_noop_check(GraphView g, const unsigned long long *tot, unsigned long long n) {
+    if (tot[0] != 0 || tot[1] != 0 || n == 0) return;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * g.set_G; i += gridDim.x * blockDim.x)
+        g.set_counts[i] = 0;
+}
+
+cudaError_t launch_segment_noop_check(const GraphView &g, const unsigned long long *tot, unsigned long long n,
+                                      const LaunchCfg &lc) {
+    k_segment_noop_check<<<(2 * g.set_G + 255) / 256, 256, 0, lc.stream>>>(g, tot, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_set_insert_counts(const GraphView &g, const LaunchCfg &lc) {
     k_set_insert_counts<<<(g.set_G + 255) / 256, 256, 0, lc.stream>>>(g);
     return cudaGetLastError();

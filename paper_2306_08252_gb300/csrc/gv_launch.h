@@ -135,6 +135,8 @@ cudaError_t launch_bfs_level(const GraphView &g, uint32_t aib, const uint32_t *c
 cudaError_t launch_pagerank(const GraphView &g, uint32_t aib, uint32_t iterations, double damping, double *r,
                             double *c, double *acc, double *scal, unsigned long long *N, uint2 *items,
                             uint32_t *nitems, const LaunchCfg &lc);
+cudaError_t launch_segment_noop_check(const GraphView &g, const unsigned long long *tot, unsigned long long n,
+                                      const LaunchCfg &lc);
 cudaError_t launch_finalize_count_only(const GraphView &g, const LaunchCfg &lc);
 cudaError_t launch_validate(const GraphView &g, uint32_t *owner_bits,
                             unsigned long long *violations, const LaunchCfg &lc);

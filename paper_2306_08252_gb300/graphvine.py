@@ -90,6 +90,7 @@ SIGNATURES = {
     "gv_profile_phase_name": ([c_u32], ctypes.c_char_p),
     "gv_degree_offsets_noalloc": ([c_vp, c_vp, c_u32, c_vp, c_vp], ctypes.c_int),
     "gv_insert_edges_segmented": ([c_vp, c_vp, c_vp, c_u64, c_vp, c_u32, c_vp, c_vp], ctypes.c_int),
+    "gv_delete_edges_segmented": ([c_vp, c_vp, c_vp, c_u64, c_vp, c_u32, c_vp, c_vp], ctypes.c_int),
     "gv_set_create": ([ctypes.POINTER(gv_config), c_u32, c_vp, c_vp, ctypes.POINTER(c_vp)], ctypes.c_int),
     "gv_set_insert_edges": ([c_vp, c_vp, c_vp, c_u64, c_vp, c_vp, c_vp], ctypes.c_int),
     "gv_set_delete_edges": ([c_vp, c_vp, c_vp, c_u64, c_vp, c_vp, c_vp], ctypes.c_int),
@@ -270,6 +271,11 @@ def gv_degree_offsets_noalloc(g, d_vids, d_offsets, stream=None):
 def gv_insert_edges_segmented(g, d_src, d_dst, d_offsets, nseg, d_counts, stream=None):
     return check(load().gv_insert_edges_segmented(g, ptr(d_src), ptr(d_dst), _len(d_src), ptr(d_offsets), nseg,
                                                   ptr(d_counts), stream), "gv_insert_edges_segmented")
+
+
+def gv_delete_edges_segmented(g, d_src, d_dst, d_offsets, nseg, d_counts, stream=None):
+    return check(load().gv_delete_edges_segmented(g, ptr(d_src), ptr(d_dst), _len(d_src), ptr(d_offsets), nseg,
+                                                  ptr(d_counts), stream), "gv_delete_edges_segmented")
 
 
 def gv_profile(g, enable):

@@ -10,9 +10,10 @@ order:
   request's result is the one it would get alone, in order);
 * consecutive query requests merge into one query batch (each request gets
   its slice of the answers; no update separates them);
-* a delete request runs alone (a merged delete could attribute removed
-  copies of a pair named by two requests differently from running them in
-  order).
+* consecutive delete requests merge into one segmented delete (the library
+  removes the union of their pairs, which is what the requests do one after
+  another, and credits each removed entry to the first request that names
+  its pair, which is what that request alone would have removed).
 
 Up to `slots` runs are in flight on one stream, each with its own pinned
 host and device buffers: host-to-device copy, the library call, the
@@ -103,8 +104,6 @@ class Server:
         head = queue[0]
         if len(head) > self.cap:
             raise ValueError(f"request of {len(head)} pairs exceeds the merge capacity {self.cap}")
-        if head.kind == DELETE:
-            return [queue.popleft()]
         run, n = [], 0
         while queue and queue[0].kind == head.kind and len(run) < self.max_reqs and n + len(queue[0]) <= self.cap:
             r = queue.popleft()
@@ -137,8 +136,10 @@ class Server:
                                              slot.d_off[:len(run) + 1], len(run), slot.d_cnt, s)
                 slot.h_cnt[:2 * len(run)].copy_(slot.d_cnt[:2 * len(run)], non_blocking=True)
             elif slot.kind == DELETE:
-                gv.gv_delete_edges(self.g.handle, slot.d_src[:n], slot.d_dst[:n], slot.d_cnt[:2], s)
-                slot.h_cnt[:2].copy_(slot.d_cnt[:2], non_blocking=True)
+                slot.d_off[:len(run) + 1].copy_(slot.h_off[:len(run) + 1], non_blocking=True)
+                gv.gv_delete_edges_segmented(self.g.handle, slot.d_src[:n], slot.d_dst[:n],
+                                             slot.d_off[:len(run) + 1], len(run), slot.d_cnt, s)
+                slot.h_cnt[:2 * len(run)].copy_(slot.d_cnt[:2 * len(run)], non_blocking=True)
             else:
                 gv.gv_query_edges(self.g.handle, slot.d_src[:n], slot.d_dst[:n], slot.d_out[:max(n, 1)], s)
                 if n:
@@ -151,15 +152,13 @@ class Server:
     def _finish(self, slot, now):
         run = slot.reqs
         self.completed += len(run)
-        if slot.kind == INSERT:
+        if slot.kind in (INSERT, DELETE):
             cnt = slot.h_cnt.numpy()[:2 * len(run)].reshape(-1, 2)
             for r, c in zip(run, cnt):
                 r.result = (int(c[0]), int(c[1]))
-            self.reserved_blocks -= slot.blocks
-            self.free_blocks -= slot.blocks  # conservative until the next refresh
-        elif slot.kind == DELETE:
-            c = slot.h_cnt.numpy()[:2]
-            run[0].result = (int(c[0]), int(c[1]))
+            if slot.kind == INSERT:
+                self.reserved_blocks -= slot.blocks
+                self.free_blocks -= slot.blocks  # conservative until the next refresh
         else:
             out = slot.h_out.numpy()[:slot.n]
             a = 0

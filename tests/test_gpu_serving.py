@@ -75,3 +75,52 @@ def test_served_results_equal_alone(realtime):
     finally:
         served_graph.close()
         alone_graph.close()
+
+
+@pytest.mark.parametrize("C", [4, 16])
+def test_segmented_delete_equals_deletes_in_order(C):
+    # one call over several delete batches: per-segment {deleted, rejected}
+    # equal those of the batches applied one call each, in order, including
+    # pairs named by several segments (credited to the first), pairs named
+    # twice inside a segment, absent and invalid pairs, a hub source whose
+    # batch set is a global hash set, tiny and multi-item adjacencies
+    import torch
+    import paper_2306_08252_gb300 as gv
+    from gpu_util import Pair
+    scale, nv = 12, 1 << 12
+    rng = np.random.default_rng(61)
+    bs, bd = W.rmat_pairs(61, 0, 50_000, scale)
+    hub = rng.integers(0, nv, 20_000).astype(np.uint32)
+    bs = np.concatenate([bs, np.zeros_like(hub), bs[:3000]])
+    bd = np.concatenate([bd, hub, bd[:3000]])
+    p = Pair(nv, C=C, pool_bytes=64 << 20)
+    try:
+        p.bulk(bs, bd)
+        segs = []
+        for k in range(7):
+            pick = rng.integers(0, bs.size, int(rng.integers(1, 6000)))
+            s, d = bs[pick], bd[pick]
+            if k == 2:
+                s = np.concatenate([s, [nv, 3]]).astype(np.uint32)
+                d = np.concatenate([d, [1, nv + 5]]).astype(np.uint32)
+            if k == 4:
+                s = np.concatenate([s, np.zeros(900, dtype=np.uint32)])
+                d = np.concatenate([d, hub[:900]])
+            if k == 5:
+                s, d = np.concatenate([s, segs[1][0]]), np.concatenate([d, segs[1][1]])
+            segs.append((s.astype(np.uint32), d.astype(np.uint32)))
+        segs.append((np.zeros(0, dtype=np.uint32), np.zeros(0, dtype=np.uint32)))
+        off = np.zeros(len(segs) + 1, dtype=np.int64)
+        off[1:] = np.cumsum([a.size for a, _ in segs])
+        src = np.concatenate([a for a, _ in segs])
+        dst = np.concatenate([b for _, b in segs])
+        cnt = torch.zeros(2 * len(segs), dtype=torch.int64, device="cuda")
+        gv.gv_delete_edges_segmented(p.g.handle, dev_u32(src), dev_u32(dst), torch.from_numpy(off).cuda(),
+                                     len(segs), cnt)
+        got = cnt.cpu().numpy().reshape(-1, 2)
+        exp = np.array([p.o.delete_edges(a, b) for a, b in segs])
+        np.testing.assert_array_equal(got, exp)
+        assert exp[:, 0].sum() > 0 and exp[2, 1] == 2
+        p.check()
+    finally:
+        p.close()
