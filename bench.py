@@ -521,7 +521,9 @@ def run_serving(args):
     """Serving: RMAT 2^24 vertices / 2^28 edges resident on the device;
     requests of mixed kind (40% insert, 40% delete of base edges, 20% query),
     sizes log-uniform in 1..1M, Poisson arrivals at 50% and 90% of the
-    measured saturated capacity; the first 10% of each stream is warm-up.
+    measured saturated capacity (a second stream of the same size and
+    mix, every request present at time 0); the first 10% of each stream is
+    warm-up.
     Latency = completion observed by the loop - arrival."""
     import torch
     import workloads as W
@@ -534,7 +536,7 @@ def run_serving(args):
     t_gen = time.perf_counter()
     bs, bd = W.rmat_pairs(5, 0, edges, scale)
     reqs, gaps = W.serving_requests(5, bs, bd, scale, args.requests)
-    cap_reqs, _ = W.serving_requests(6, bs, bd, scale, max(args.requests // 10, 100))
+    cap_reqs, _ = W.serving_requests(6, bs, bd, scale, args.requests)
     t_gen = time.perf_counter() - t_gen
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
     blocks = edges // C * 2 + (1 << scale) + (1 << 22)
@@ -548,7 +550,7 @@ def run_serving(args):
     server.run(crs, realtime=False)
     cap = len(crs) / (time.perf_counter() - t0)
     levels = []
-    for load in (0.5, 0.9):
+    for load in (0.5, 0.7, 0.9):
         rate = load * cap
         arrivals = np.cumsum(gaps) / rate
         rs = [serve.Request(k, a, b, t) for (k, a, b), t in zip(reqs, arrivals)]

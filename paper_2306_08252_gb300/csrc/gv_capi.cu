@@ -90,6 +90,8 @@ struct gv_graph {
     uint64_t dict_bytes = 0;
     bool any_vertex_deleted = false;
     unsigned long long used_ub = 0;  // upper bound of blocks in use (pool growth policy)
+    cudaStream_t side = nullptr;     // second stream: concurrent mark tiers
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // analytics scratch: items, two frontiers, counters, PageRank vectors
     unsigned long long an_icap = 0, an_vcap = 0;
     uint2 *an_items = nullptr;
@@ -204,6 +206,9 @@ LaunchCfg lcfg(const gv_graph *g, cudaStream_t s) {
     lc.num_sms = g->num_sms;
     lc.stream = s;
     lc.prof = const_cast<gv::Prof *>(&g->prof);
+    lc.side = g->side;
+    lc.fork = g->ev_fork;
+    lc.join = g->ev_join;
     return lc;
 }
 
@@ -761,6 +766,16 @@ gv_status gv_create(const gv_config *cfg, uint32_t num_vertices, void *stream, g
     }
     cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
     if (g->num_sms <= 0) g->num_sms = 1;
+    // without them the two mark tiers simply run one after the other
+    if (cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        if (g->side) cudaStreamDestroy(g->side);
+        if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+        g->side = nullptr;
+        g->ev_fork = g->ev_join = nullptr;
+    }
     g->flags = c.flags;
     g->item_blocks_cfg = c.item_blocks;
     if (c.dense_shift) g->dense_shift = std::min<uint32_t>(c.dense_shift, 31);
@@ -821,6 +836,12 @@ gv_status gv_destroy(gv_graph *g) {
         for (auto e : g->prof.pool) cudaEventDestroy(e);
         if (g->h_small) cudaFreeHost(g->h_small);
         if (g->h_dev) cudaFreeHost(g->h_dev);
+        if (g->side) {
+            cudaStreamSynchronize(g->side);
+            cudaStreamDestroy(g->side);
+        }
+        if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+        if (g->ev_join) cudaEventDestroy(g->ev_join);
         cudaGetLastError();
     }
     delete g;

@@ -45,7 +45,8 @@ struct Dev {
     unsigned int status;            // latched device status (gv_status), sticky
     unsigned int abort;             // set when this call must not mutate the graph
     unsigned int n_tiny;            // touched sources handled one per thread
-    unsigned int pad[2];
+    unsigned int n_mitems;          // work items of multi-item sources (top of the item array)
+    unsigned int pad;
     unsigned long long harena_used; // words of the arena's hash region used
 };
 

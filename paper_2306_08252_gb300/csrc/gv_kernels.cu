@@ -504,6 +504,7 @@ __global__ void __launch_bounds__(256) k_finalize_insert(GraphView g, unsigned l
         dev->call_a = dev->call_b = dev->call_c = 0;
         dev->n_touched = 0;
         dev->n_items = 0;
+        dev->n_mitems = 0;
         dev->n_tiny = 0;
         dev->arena_used = 0;
         dev->harena_used = 0;
@@ -522,6 +523,30 @@ __device__ __forceinline__ void emit_items(const GraphView &g, uint32_t t, uint3
     for (uint32_t c = 0; c < ni; ++c) g.items[item0 + c] = make_uint2(t, c);
 }
 
+// First work item of a source with ni items, for every thread of the block
+// (all threads call): single-item sources count up from the bottom of the
+// item array, multi-item sources down from the top (so the kernels that
+// handle only multi-item sources visit only their items).
+__device__ __forceinline__ uint32_t alloc_items(const GraphView &g, uint32_t ni, uint32_t *s_lo, uint32_t *s_hi) {
+    uint32_t ltot, htot;
+    const uint32_t lex = block_excl_scan(ni == 1 ? 1u : 0u, &ltot);
+    const uint32_t hex = block_excl_scan(ni > 1 ? ni : 0u, &htot);
+    if (threadIdx.x == 0) {
+        *s_lo = ltot ? atomicAdd(&g.dev->n_items, ltot) : 0u;
+        *s_hi = htot ? atomicAdd(&g.dev->n_mitems, htot) : 0u;
+    }
+    __syncthreads();
+    if (ni == 1) return *s_lo + lex;
+    if (ni > 1) return (uint32_t)(g.max_items - (*s_hi + hex + ni));
+    return 0u;
+}
+
+// Work item of virtual index vi over both regions ([0, nlo) bottom, then the
+// nhi top items).
+__device__ __forceinline__ uint32_t item_at(const GraphView &g, uint32_t vi, uint32_t nlo, uint32_t nhi) {
+    return vi < nlo ? vi : (uint32_t)(g.max_items - nhi + (vi - nlo));
+}
+
 // Per touched source: arena words for its batch destinations (a list up to
 // LIST_MAX entries, else a hash set), and either the tiny tier (one thread,
 // tiny adjacency and few batch entries) or work items of IB blocks.
@@ -531,7 +556,7 @@ __global__ void __launch_bounds__(256) k_plan_member(GraphView g) {
     const uint32_t IB = g.IB;
     const uint32_t tiny_deg = min(TINY_DEG, TINY_NB * g.C);
     __shared__ unsigned long long s_aw, s_hw;
-    __shared__ uint32_t s_ai, s_at;
+    __shared__ uint32_t s_ai, s_am, s_at;
     for (uint32_t base = blockIdx.x * blockDim.x; base < nt; base += gridDim.x * blockDim.x) {
         const uint32_t t = base + threadIdx.x;
         uint32_t m = 0, lw = 0, hw = 0, ni = 0, tiny = 0;
@@ -551,20 +576,17 @@ __global__ void __launch_bounds__(256) k_plan_member(GraphView g) {
                 else ni = (s.y + IB - 1) / IB;
             }
         }
-        uint32_t lt, ht, itot, ttot;
+        uint32_t lt, ht, ttot;
         const uint32_t lex = block_excl_scan(lw, &lt);
         const uint32_t hex = block_excl_scan(hw, &ht);
-        const uint32_t iex = block_excl_scan(ni, &itot);
         const uint32_t tex = block_excl_scan(tiny, &ttot);
         if (threadIdx.x == 0) {
             s_aw = lt ? atomicAdd(&g.dev->arena_used, (unsigned long long)lt) : 0ull;
             s_hw = ht ? atomicAdd(&g.dev->harena_used, (unsigned long long)ht) : 0ull;
-            s_ai = itot ? atomicAdd(&g.dev->n_items, itot) : 0u;
             s_at = ttot ? atomicAdd(&g.dev->n_tiny, ttot) : 0u;
         }
-        __syncthreads();
+        const uint32_t item0 = alloc_items(g, ni, &s_ai, &s_am);
         if (t < nt) {
-            const uint32_t item0 = s_ai + iex;
             // hash sets are powers of two >= HB words, so their offsets stay
             // multiples of HB words: every bucket is sector-aligned
             const uint32_t aoff = hw ? (uint32_t)(g.hbase + s_hw + hex) : (uint32_t)(s_aw + lex);
@@ -721,7 +743,8 @@ __global__ void __launch_bounds__(256) k_scatter_member(GraphView g, const uint3
 template <int MODE>
 __global__ void __launch_bounds__(256) k_mark(GraphView g) {
     Dev *dev = g.dev;
-    const uint32_t nitems = dev->n_items;
+    const uint32_t nlo = dev->n_items, nhi = dev->n_mitems;
+    const uint32_t nitems = nlo + nhi;
     const uint32_t lane = lane_id();
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -730,7 +753,7 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
     const unsigned long long qbb = qmod(dev->q_back, P);
     __shared__ uint32_t s_free[8][64];
     __shared__ uint32_t s_bid[8][32];
-    __shared__ uint32_t s_hkey[8][2 * LIST_MAX];
+    __shared__ __align__(16) uint32_t s_hkey[8][2 * LIST_MAX];
     // queries: hit flag per list key; segmented deletes: owner segment per key
     __shared__ uint32_t s_hfound[8][(MODE == MODE_QUERY || MODE == MODE_DELETE) ? 2 * LIST_MAX : 1];
     const bool segd = MODE == MODE_DELETE && g.seg_own != nullptr;
@@ -741,7 +764,8 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
     }
     FreeStage fs{s_free[threadIdx.x >> 5], 0u};
     unsigned long long removed = 0;  // entries deleted by this warp (lane 0)
-    for (uint32_t it = warp; it < nitems; it += nwarps) {
+    for (uint32_t vi = warp; vi < nitems; vi += nwarps) {
+        const uint32_t it = item_at(g, vi, nlo, nhi);
         const uint2 itm = g.items[it];
         const uint32_t t = itm.x, c = itm.y;
         const uint4 a = g.t_a[t];
@@ -761,16 +785,19 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
         uint32_t *sb_ids = s_bid[threadIdx.x >> 5];
         sb_ids[lane] = bid;
         // Batch list of this source (<= LIST_MAX entries): a shared hash set
-        // of hmask + 1 slots (a power of two >= 2m, at least 64) per warp.
+        // per warp of nsb buckets of 4 slots (nsb * 4 a power of two >= 2m,
+        // at least 64 slots).  A key takes the first empty slot of its home
+        // bucket (then of the next ones), so occupied slots are a prefix of
+        // each bucket and a lookup is one 16-byte shared load.
         bool listmode = false;
-        uint32_t hmask = 63;
+        uint32_t nsb = 16;
         uint32_t *hk = s_hkey[threadIdx.x >> 5];
         uint32_t *hf = s_hfound[threadIdx.x >> 5];
         if (MODE == MODE_DELETE || MODE == MODE_QUERY) {
             listmode = (a.z == 0);
             if (listmode) {
-                while (hmask + 1 < 2 * a.x) hmask = 2 * hmask + 1;
-                for (uint32_t j = lane; j <= hmask; j += 32) {
+                while (4 * nsb < 2 * a.x) nsb *= 2;
+                for (uint32_t j = lane; j < 4 * nsb; j += 32) {
                     hk[j] = EMPTY_KEY;
                     if (MODE == MODE_QUERY) hf[j] = 0u;
                     if (segd) hf[j] = NIL;
@@ -778,11 +805,13 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
                 __syncwarp();
                 for (uint32_t j = lane; j < a.x; j += 32) {
                     const uint32_t v = g.arena[a.y + j];
-                    uint32_t h = hidx(v, hmask + 1);
-                    for (;;) {
+                    uint32_t h = 4 * hidx(v, nsb);
+                    // at most 2m keys in 4 * nsb >= 2m slots: a free or equal
+                    // slot exists, so the walk ends within 4 * nsb steps
+                    for (uint32_t step = 0; step < 4 * nsb; ++step) {
                         const uint32_t old = atomicCAS(&hk[h], EMPTY_KEY, v);
                         if (old == EMPTY_KEY || old == v) break;
-                        h = (h + 1) & hmask;
+                        h = (h + 1) & (4 * nsb - 1);
                     }
                     if (segd) atomicMin(&hf[h], g.seg_own[a.y + j]);
                 }
@@ -815,17 +844,19 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     if ((vmask >> j) & 1u) {
-                        uint32_t h = hidx(e[j], hmask + 1);
-                        for (;;) {
-                            const uint32_t k = hk[h];
-                            if (k == e[j]) {
+                        uint32_t b = hidx(e[j], nsb);
+                        for (uint32_t step = 0; step < nsb; ++step) {
+                            const uint4 w = *reinterpret_cast<const uint4 *>(hk + 4 * b);
+                            const uint32_t k = w.x == e[j] ? 0u : w.y == e[j] ? 1u : w.z == e[j] ? 2u
+                                             : w.w == e[j] ? 3u : NIL;
+                            if (k != NIL) {
                                 hitm |= 1u << j;
-                                if (MODE == MODE_QUERY) hf[h] = 1u;
-                                if (segd) seg_count(s_mhist, hf[h], g.set_G, dev);
+                                if (MODE == MODE_QUERY) hf[4 * b + k] = 1u;
+                                if (segd) seg_count(s_mhist, hf[4 * b + k], g.set_G, dev);
                                 break;
                             }
-                            if (k == EMPTY_KEY) break;
-                            h = (h + 1) & hmask;
+                            if (w.w == EMPTY_KEY) break;  // the bucket's prefix ended
+                            b = (b + 1) & (nsb - 1);
                         }
                     }
                 }
@@ -903,9 +934,9 @@ __global__ void __launch_bounds__(256) k_mark(GraphView g) {
             if (listmode) {
                 for (uint32_t j = lane; j < a.x; j += 32) {
                     const uint32_t v = g.arena[a.y + j];
-                    uint32_t h = hidx(v, hmask + 1);
-                    while (hk[h] != v) h = (h + 1) & hmask;
-                    if (hf[h]) g.found[a.y + j] = 1u;
+                    uint32_t h = 4 * hidx(v, nsb);
+                    for (uint32_t step = 0; step < 4 * nsb && hk[h] != v; ++step) h = (h + 1) & (4 * nsb - 1);
+                    if (hk[h] == v && hf[h]) g.found[a.y + j] = 1u;
                 }
             }
             __syncwarp();
@@ -1087,7 +1118,6 @@ __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
 template <int MODE>
 __global__ void __launch_bounds__(256) k_vscan(GraphView g) {
     Dev *dev = g.dev;
-    const uint32_t nt = dev->n_touched;
     const uint32_t lane = lane_id();
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -1098,7 +1128,13 @@ __global__ void __launch_bounds__(256) k_vscan(GraphView g) {
         __syncthreads();
     }
     unsigned long long removed = 0;
-    for (uint32_t t = warp; t < nt; t += nwarps) {
+    // multi-item sources own the top nhi items; visit each source once, at
+    // its first item
+    const uint32_t nhi = dev->n_mitems;
+    for (uint32_t vi = warp; vi < nhi; vi += nwarps) {
+        const uint2 first = g.items[g.max_items - nhi + vi];
+        if (first.y != 0) continue;
+        const uint32_t t = first.x;
         const uint4 b = g.t_b[t];
         const uint32_t ni = b.w;
         if (ni <= 1) continue;
@@ -1169,7 +1205,7 @@ __global__ void __launch_bounds__(256) k_vscan(GraphView g) {
 template <int MODE>
 __global__ void __launch_bounds__(256) k_move(GraphView g) {
     Dev *dev = g.dev;
-    const uint32_t nitems = dev->n_items;
+    const uint32_t nhi = dev->n_mitems;  // items of multi-item sources (top region)
     const uint32_t lane = lane_id();
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -1178,7 +1214,8 @@ __global__ void __launch_bounds__(256) k_move(GraphView g) {
     const unsigned long long qbb = qmod(dev->q_back, P);
     __shared__ uint32_t s_free[8][64];
     FreeStage fs{s_free[threadIdx.x >> 5], 0u};
-    for (uint32_t it = warp; it < nitems; it += nwarps) {
+    for (uint32_t vi = warp; vi < nhi; vi += nwarps) {
+        const uint32_t it = (uint32_t)(g.max_items - nhi + vi);
         const uint2 itm = g.items[it];
         const uint32_t t = itm.x, c = itm.y;
         const uint4 b = g.t_b[t];
@@ -1292,6 +1329,7 @@ __global__ void __launch_bounds__(256) k_finalize_member(GraphView g, unsigned l
         dev->call_a = dev->call_b = dev->call_c = 0;
         dev->n_touched = 0;
         dev->n_items = 0;
+        dev->n_mitems = 0;
         dev->n_tiny = 0;
         dev->arena_used = 0;
         dev->harena_used = 0;
@@ -1388,6 +1426,7 @@ __global__ void k_reset_lists(GraphView g) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         g.dev->n_touched = 0;
         g.dev->n_items = 0;
+        g.dev->n_mitems = 0;
         g.dev->n_tiny = 0;
     }
 }
@@ -1398,7 +1437,7 @@ __global__ void __launch_bounds__(256) k_plan_vdel_in(GraphView g) {
     const uint32_t nv = g.nv;
     const uint32_t IB = g.IB;
     const uint32_t tiny_deg = min(TINY_DEG, TINY_NB * g.C);
-    __shared__ uint32_t s_at, s_ai, s_an;
+    __shared__ uint32_t s_at, s_ai, s_am, s_an;
     for (uint32_t base = blockIdx.x * blockDim.x; base < nv; base += gridDim.x * blockDim.x) {
         const uint32_t u = base + threadIdx.x;
         uint32_t take = 0, ni = 0, tiny = 0;
@@ -1411,19 +1450,16 @@ __global__ void __launch_bounds__(256) k_plan_vdel_in(GraphView g) {
                 else ni = (s.y + IB - 1) / IB;
             }
         }
-        uint32_t ttot, itot, ntot;
+        uint32_t ttot, ntot;
         const uint32_t tex = block_excl_scan(take, &ttot);
-        const uint32_t iex = block_excl_scan(ni, &itot);
         const uint32_t nex = block_excl_scan(tiny, &ntot);
         if (threadIdx.x == 0) {
             s_at = ttot ? atomicAdd(&g.dev->n_touched, ttot) : 0u;
-            s_ai = itot ? atomicAdd(&g.dev->n_items, itot) : 0u;
             s_an = ntot ? atomicAdd(&g.dev->n_tiny, ntot) : 0u;
         }
-        __syncthreads();
+        const uint32_t item0 = alloc_items(g, ni, &s_ai, &s_am);
         if (take) {
             const uint32_t t = s_at + tex;
-            const uint32_t item0 = s_ai + iex;
             g.t_vid[t] = u;
             g.t_b[t] = make_uint4(s.x, s.y, s.z, ni);
             g.t_a[t] = make_uint4(0, 0, 0, item0);
@@ -1450,6 +1486,7 @@ __global__ void __launch_bounds__(256) k_finalize_vdel(GraphView g, const uint32
         dev->call_a = dev->call_b = dev->call_c = 0;
         dev->n_touched = 0;
         dev->n_items = 0;
+        dev->n_mitems = 0;
         dev->n_tiny = 0;
         dev->arena_used = 0;
         dev->harena_used = 0;
@@ -1668,11 +1705,26 @@ static void member_tail(const GraphView &g0, const uint32_t *src, const uint32_t
         PhaseScope ps(lc, del ? PH_DEL_SCATTER : PH_QRY_SCATTER);
         k_scatter_member<MODE><<<grid_for(n, 256 * PP, cap), 256, 0, lc.stream>>>(g, src, dst, n);
     }
+    // The two tiers touch disjoint sources (their blocks, sentinels and list
+    // ranges) and share only atomically updated counters, so the thread-per-
+    // source tier runs on the graph's second stream beside the warp tier.
+    const bool fork = lc.side && lc.fork && lc.join;
+    if (fork) {
+        cudaEventRecord(lc.fork, lc.stream);
+        cudaStreamWaitEvent(lc.side, lc.fork, 0);
+        LaunchCfg ls = lc;
+        ls.stream = lc.side;
+        PhaseScope ps(ls, del ? PH_DEL_MARK_TINY : PH_QRY_MARK_TINY);
+        k_mark_tiny<MODE><<<gt, 256, 0, lc.side>>>(g);
+    }
     {
         PhaseScope ps(lc, del ? PH_DEL_MARK : PH_QRY_MARK);
         k_mark<MODE><<<gi, 256, 0, lc.stream>>>(g);
     }
-    {
+    if (fork) {
+        cudaEventRecord(lc.join, lc.side);
+        cudaStreamWaitEvent(lc.stream, lc.join, 0);
+    } else {
         PhaseScope ps(lc, del ? PH_DEL_MARK_TINY : PH_QRY_MARK_TINY);
         k_mark_tiny<MODE><<<gt, 256, 0, lc.stream>>>(g);
     }
@@ -1711,8 +1763,17 @@ cudaError_t launch_vertex_delete(const GraphView &g, const uint32_t *ids, uint32
     k_free_items<<<gi, 256, 0, lc.stream>>>(g);
     k_reset_lists<<<1, 32, 0, lc.stream>>>(g);
     k_plan_vdel_in<<<grid_for(g.nv, 256, cap), 256, 0, lc.stream>>>(g);
+    // disjoint tiers, as in deletes: the thread-per-source one on the side stream
+    const bool fork = lc.side && lc.fork && lc.join;
+    if (fork) {
+        cudaEventRecord(lc.fork, lc.stream);
+        cudaStreamWaitEvent(lc.side, lc.fork, 0);
+        k_mark_tiny<MODE_VDEL><<<grid_for(g.nv, 256, cap), 256, 0, lc.side>>>(g);
+        cudaEventRecord(lc.join, lc.side);
+    }
     k_mark<MODE_VDEL><<<gi, 256, 0, lc.stream>>>(g);
-    k_mark_tiny<MODE_VDEL><<<grid_for(g.nv, 256, cap), 256, 0, lc.stream>>>(g);
+    if (fork) cudaStreamWaitEvent(lc.stream, lc.join, 0);
+    else k_mark_tiny<MODE_VDEL><<<grid_for(g.nv, 256, cap), 256, 0, lc.stream>>>(g);
     k_vscan<MODE_VDEL><<<grid_for(g.nv, 8, cap), 256, 0, lc.stream>>>(g);
     k_move<MODE_VDEL><<<gi, 256, 0, lc.stream>>>(g);
     k_finalize_vdel<<<grid_for(k, 256, cap), 256, 0, lc.stream>>>(g, ids, k);

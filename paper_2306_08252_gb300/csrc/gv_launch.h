@@ -45,6 +45,10 @@ struct LaunchCfg {
     int num_sms;
     cudaStream_t stream;
     Prof *prof = nullptr;
+    // optional second stream of the graph and a fork/join event pair: the
+    // two mark tiers (warp items, thread-per-source) run concurrently
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 // Records a start event now and a stop event when the scope ends.
