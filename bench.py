@@ -520,7 +520,7 @@ def run_batched(args):
 def run_serving(args):
     """Serving: RMAT 2^24 vertices / 2^28 edges resident on the device;
     requests of mixed kind (40% insert, 40% delete of base edges, 20% query),
-    sizes log-uniform in 1..1M, Poisson arrivals at 50% and 90% of the
+    sizes log-uniform in 1..1M, Poisson arrivals at 50%, 70% and 90% of the
     measured saturated capacity (a second stream of the same size and
     mix, every request present at time 0); the first 10% of each stream is
     warm-up.
