@@ -181,18 +181,20 @@ def byte_model(g, batch, qry, inserted, deleted, newblocks):
     qry_b = 9 * qry[0].size + 4 * int(deg64[qs].sum())
     del_b = 8 * s.size + 4 * int(deg64[us].sum()) + 32 * us.size + 4 * newblocks
 
-    def tiers(src_ids):
+    def tiers(src_ids, tiny_deg, tiny_nb):
+        # thread-per-source tier: <= tiny_nb blocks, <= min(tiny_deg, tiny_nb*C)
+        # entries, <= 16 batch entries (deletes 128 / 8, queries 64 / 4)
         m = np.bincount(src_ids, minlength=nv)
         touched = m > 0
         nb = (deg64 + C - 1) // C
-        tiny = touched & (deg64 > 0) & (deg64 <= min(64, 4 * C)) & (nb <= 4) & (m <= 16)
+        tiny = touched & (deg64 > 0) & (deg64 <= min(tiny_deg, tiny_nb * C)) & (nb <= tiny_nb) & (m <= 16)
         big = touched & (deg64 > 0) & ~tiny
         return (4 * int(deg64[big].sum()) + 4 * int(m[big].sum()),
                 4 * int(deg64[tiny].sum()) + 4 * int(m[tiny].sum()))
 
-    dmark, dtiny = tiers(s[ok])
+    dmark, dtiny = tiers(s[ok], 128, 8)
     qok = (qry[0] < nv) & (qry[1] < nv)
-    qmark, qtiny = tiers(qry[0][qok])
+    qmark, qtiny = tiers(qry[0][qok], 64, 4)
     scan = 4 * (1 << int(np.ceil(np.log2(max(nv, 1)))))
     kernels = {
         "insert.count": 12 * s.size, "insert.touched": scan, "insert.scatter": 16 * inserted,
