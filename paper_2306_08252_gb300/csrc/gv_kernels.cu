@@ -663,17 +663,20 @@ __global__ void __launch_bounds__(256) k_scatter_member(GraphView g, const uint3
                 g.arena[pos[j]] = v[j];
             }
         }
-        // bucketed hash sets: read the first half of the home bucket of every
-        // pair (L2, not a possibly stale L1 line), then claim the first empty
-        // slot by CAS; occupied slots stay a prefix of each bucket
-        uint4 b0[PP];
+        // bucketed hash sets: read the home bucket of every pair (both
+        // halves in flight together; L2, not a possibly stale L1 line), then
+        // claim its first empty slot by CAS; occupied slots stay a prefix of
+        // each bucket
+        uint4 b0[PP], b1[PP];
         uint32_t bk[PP];
         uint32_t rep = 0;  // set-semantics inserts: bit j = pair j claimed its slot
 #pragma unroll
         for (int j = 0; j < PP; ++j) {
             if (r[j] != NIL && hs[j] != 0) {
                 bk[j] = hidx(v[j], hs[j] / HB);
-                b0[j] = __ldcg(reinterpret_cast<const uint4 *>(g.arena + aoff[j] + bk[j] * HB));
+                const uint4 *bp = reinterpret_cast<const uint4 *>(g.arena + aoff[j] + bk[j] * HB);
+                b0[j] = __ldcg(bp);
+                b1[j] = __ldcg(bp + 1);
             }
         }
 #pragma unroll
@@ -681,36 +684,37 @@ __global__ void __launch_bounds__(256) k_scatter_member(GraphView g, const uint3
             if (r[j] != NIL && hs[j] != 0) {
                 const uint32_t nbk = hs[j] / HB;
                 uint32_t *tab = g.arena + aoff[j];
-                uint32_t b = bk[j], half = 0;
-                uint4 w = b0[j];
-                // each pass ends, moves on by half a bucket, or rereads after
+                uint32_t b = bk[j];
+                uint32_t w[HB] = {b0[j].x, b0[j].y, b0[j].z, b0[j].w, b1[j].x, b1[j].y, b1[j].z, b1[j].w};
+                // each pass ends, moves to the next bucket, or rereads after
                 // losing a slot to another insert (which filled that slot):
-                // 2 * nbk * 5 passes bound the loop
-                for (uint32_t probe = 0; probe < 10 * nbk; ++probe) {
-                    const uint32_t hit = w.x == v[j] ? 0u : w.y == v[j] ? 1u : w.z == v[j] ? 2u
-                                       : w.w == v[j] ? 3u : NIL;
+                // (HB + 1) * nbk passes bound the loop
+                for (uint32_t probe = 0; probe < (HB + 1) * nbk; ++probe) {
+                    uint32_t hit = NIL, empty = NIL;
+#pragma unroll
+                    for (uint32_t k = 0; k < HB; ++k) {
+                        if (hit == NIL && w[k] == v[j]) hit = k;
+                        if (empty == NIL && w[k] == EMPTY_KEY) empty = k;
+                    }
                     if (hit != NIL) {
-                        pos[j] = aoff[j] + b * HB + half * 4 + hit;
+                        pos[j] = aoff[j] + b * HB + hit;
                         break;
                     }
-                    const uint32_t empty = w.x == EMPTY_KEY ? 0u : w.y == EMPTY_KEY ? 1u : w.z == EMPTY_KEY ? 2u
-                                         : w.w == EMPTY_KEY ? 3u : NIL;
                     if (empty != NIL) {
-                        const uint32_t slot = b * HB + half * 4 + empty;
-                        const uint32_t old = atomicCAS(&tab[slot], EMPTY_KEY, v[j]);
+                        const uint32_t old = atomicCAS(&tab[b * HB + empty], EMPTY_KEY, v[j]);
                         if (old == EMPTY_KEY || old == v[j]) {
-                            pos[j] = aoff[j] + slot;
+                            pos[j] = aoff[j] + b * HB + empty;
                             if (MODE == MODE_DEDUP && old == EMPTY_KEY) rep |= 1u << j;
                             break;
                         }
-                        // lost the slot: reread this half
-                    } else if (half == 0) {
-                        half = 1;
+                        // lost the slot: reread this bucket
                     } else {
-                        half = 0;
                         b = (b + 1) & (nbk - 1);
                     }
-                    w = __ldcg(reinterpret_cast<const uint4 *>(tab + b * HB + half * 4));
+                    const uint4 *bp = reinterpret_cast<const uint4 *>(tab + b * HB);
+                    const uint4 x0 = __ldcg(bp), x1 = __ldcg(bp + 1);
+                    w[0] = x0.x; w[1] = x0.y; w[2] = x0.z; w[3] = x0.w;
+                    w[4] = x1.x; w[5] = x1.y; w[6] = x1.z; w[7] = x1.w;
                 }
                 if (pos[j] == NIL) latch_status(g.dev, 5u /* GV_ERR_STATE */);
             }
@@ -1042,9 +1046,15 @@ __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
             act = false;
         }
         uint32_t d[TINY_M];
+        // 64-bit signature of the batch entries (bit hidx(v, 64) per entry):
+        // a stored entry whose bit is clear is in no batch entry, which
+        // spares the 16 comparisons for most entries
+        unsigned long long sig = 0;
 #pragma unroll
-        for (int j = 0; j < (int)TINY_M; ++j)
+        for (int j = 0; j < (int)TINY_M; ++j) {
             d[j] = (MODE != MODE_VDEL && act && (uint32_t)j < m) ? g.arena[aoff + j] : EMPTY_KEY;
+            if (d[j] != EMPTY_KEY) sig |= 1ull << hidx(d[j], 64);
+        }
         uint32_t qhit = 0;
         uint32_t w = 0;
         for (uint32_t x = 0; act && x < deg; x += 4) {
@@ -1059,8 +1069,10 @@ __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
                         hit = (g.dead[e[jj] >> 5] >> (e[jj] & 31u)) & 1u;
                     } else {
                         uint32_t hm = 0;
+                        if ((sig >> hidx(e[jj], 64)) & 1ull) {
 #pragma unroll
-                        for (int j = 0; j < (int)TINY_M; ++j) hm |= (uint32_t)(d[j] == e[jj]) << j;
+                            for (int j = 0; j < (int)TINY_M; ++j) hm |= (uint32_t)(d[j] == e[jj]) << j;
+                        }
                         hit = hm != 0;
                         if (MODE == MODE_QUERY) qhit |= hm;
                         if (MODE == MODE_DELETE && hit && g.seg_own) {
