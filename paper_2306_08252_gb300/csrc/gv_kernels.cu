@@ -745,7 +745,7 @@ __global__ void __launch_bounds__(256) k_scatter_member(GraphView g, const uint3
 
 // One warp per work item (see the file comment).
 template <int MODE>
-__global__ void __launch_bounds__(256) k_mark(GraphView g) {
+__global__ void __launch_bounds__(256, 4) k_mark(GraphView g) {
     Dev *dev = g.dev;
     const uint32_t nlo = dev->n_items, nhi = dev->n_mitems;
     const uint32_t nitems = nlo + nhi;
