@@ -827,6 +827,30 @@ __global__ void __launch_bounds__(256, 4) k_mark(GraphView g) {
         const uint32_t nquads = (nslots + 3) >> 2;
         const bool single = (ni == 1);
         uint32_t running = 0;
+        // Hash-set sources: when the set is small next to this item (a
+        // coalesced read of it costs at most a quarter of the random probes),
+        // a per-warp bitmap of its keys (one bit per key, in the list table's
+        // shared space) turns most misses into one shared-memory test
+        bool filt = false;
+        if ((MODE == MODE_DELETE || MODE == MODE_QUERY) && !listmode && a.z != 0 && a.z <= FILT_MAX_WORDS &&
+            a.z <= 8u * nslots) {
+            filt = true;
+            uint4 *bm4 = reinterpret_cast<uint4 *>(hk);
+            for (uint32_t j = lane; j < FILT_BITS / 128; j += 32) bm4[j] = make_uint4(0u, 0u, 0u, 0u);
+            __syncwarp();
+            for (uint32_t j = lane * 4; j < a.z; j += 128) {
+                const uint4 t4 = *reinterpret_cast<const uint4 *>(g.arena + a.y + j);
+                const uint32_t tw[4] = {t4.x, t4.y, t4.z, t4.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (tw[k] != EMPTY_KEY) {
+                        const uint32_t bit = hidx(tw[k], FILT_BITS);
+                        atomicOr(&hk[bit >> 5], 1u << (bit & 31u));
+                    }
+                }
+            }
+            __syncwarp();
+        }
         for (uint32_t q0 = 0; q0 < nquads; q0 += 32) {
             const uint32_t q = q0 + lane;
             const bool qv = q < nquads;
@@ -872,16 +896,24 @@ __global__ void __launch_bounds__(256, 4) k_mark(GraphView g) {
                 // next bucket, only past four occupied slots without the key
                 const uint32_t *tab = g.arena + a.y;
                 const uint32_t nbk = a.z / HB;
+                uint32_t need = vmask;  // entries that may be in the set
+                if (filt) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const uint32_t bit = hidx(e[j], FILT_BITS);
+                        if (!((hk[bit >> 5] >> (bit & 31u)) & 1u)) need &= ~(1u << j);
+                    }
+                }
                 uint4 x0[4];
                 uint32_t bk[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     bk[j] = hidx(e[j], nbk);
-                    if ((vmask >> j) & 1u) x0[j] = *reinterpret_cast<const uint4 *>(tab + bk[j] * HB);
+                    if ((need >> j) & 1u) x0[j] = *reinterpret_cast<const uint4 *>(tab + bk[j] * HB);
                 }
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    if ((vmask >> j) & 1u) {
+                    if ((need >> j) & 1u) {
                         uint4 w = x0[j];
                         uint32_t half = 0;  // 0: slots 0-3 of bucket bk[j]; 1: slots 4-7
                         for (uint32_t probe = 0; probe < 2 * nbk; ++probe) {
@@ -1057,36 +1089,51 @@ __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
         }
         uint32_t qhit = 0;
         uint32_t w = 0;
-        for (uint32_t x = 0; act && x < deg; x += 4) {
-            const uint32_t bi = divc(g.cmul, x);
-            const uint4 e4 = ld_stream4(reinterpret_cast<const uint4 *>(g.data + (size_t)bl.get(bi) * C + (x - bi * C)));
-            const uint32_t e[4] = {e4.x, e4.y, e4.z, e4.w};
+        // Two quads of stored entries in flight per step: both are read
+        // before either is processed, which is safe because the stable
+        // in-place compaction writes only to slots w <= the slot being read.
+        for (uint32_t x0 = 0; act && x0 < deg; x0 += 8) {
+            uint4 eq[2];
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-                if (x + jj < deg) {
-                    bool hit;
-                    if (MODE == MODE_VDEL) {
-                        hit = (g.dead[e[jj] >> 5] >> (e[jj] & 31u)) & 1u;
-                    } else {
-                        uint32_t hm = 0;
-                        if ((sig >> hidx(e[jj], 64)) & 1ull) {
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t x = x0 + 4 * h;
+                eq[h] = make_uint4(NIL, NIL, NIL, NIL);
+                if (x < deg) {
+                    const uint32_t bi = divc(g.cmul, x);
+                    eq[h] = ld_stream4(reinterpret_cast<const uint4 *>(g.data + (size_t)bl.get(bi) * C + (x - bi * C)));
+                }
+            }
 #pragma unroll
-                            for (int j = 0; j < (int)TINY_M; ++j) hm |= (uint32_t)(d[j] == e[jj]) << j;
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t x = x0 + 4 * h;
+                const uint32_t e[4] = {eq[h].x, eq[h].y, eq[h].z, eq[h].w};
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    if (x + jj < deg) {
+                        bool hit;
+                        if (MODE == MODE_VDEL) {
+                            hit = (g.dead[e[jj] >> 5] >> (e[jj] & 31u)) & 1u;
+                        } else {
+                            uint32_t hm = 0;
+                            if ((sig >> hidx(e[jj], 64)) & 1ull) {
+#pragma unroll
+                                for (int j = 0; j < (int)TINY_M; ++j) hm |= (uint32_t)(d[j] == e[jj]) << j;
+                            }
+                            hit = hm != 0;
+                            if (MODE == MODE_QUERY) qhit |= hm;
+                            if (MODE == MODE_DELETE && hit && g.seg_own) {
+                                uint32_t own = NIL;
+                                for (uint32_t r = hm; r; r &= r - 1) own = min(own, g.seg_own[aoff + __ffs(r) - 1]);
+                                seg_count(s_mhist, own, g.set_G, dev);
+                            }
                         }
-                        hit = hm != 0;
-                        if (MODE == MODE_QUERY) qhit |= hm;
-                        if (MODE == MODE_DELETE && hit && g.seg_own) {
-                            uint32_t own = NIL;
-                            for (uint32_t r = hm; r; r &= r - 1) own = min(own, g.seg_own[aoff + __ffs(r) - 1]);
-                            seg_count(s_mhist, own, g.set_G, dev);
+                        if (MODE != MODE_QUERY && !hit) {
+                            if (w != x + jj) {
+                                const uint32_t wi = divc(g.cmul, w);
+                                g.data[(size_t)bl.get(wi) * C + (w - wi * C)] = e[jj];
+                            }
+                            ++w;
                         }
-                    }
-                    if (MODE != MODE_QUERY && !hit) {
-                        if (w != x + jj) {
-                            const uint32_t wi = divc(g.cmul, w);
-                            g.data[(size_t)bl.get(wi) * C + (w - wi * C)] = e[jj];
-                        }
-                        ++w;
                     }
                 }
             }
