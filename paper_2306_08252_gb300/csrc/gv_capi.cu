@@ -766,12 +766,8 @@ gv_status gv_create(const gv_config *cfg, uint32_t num_vertices, void *stream, g
     }
     cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
     if (g->num_sms <= 0) g->num_sms = 1;
-    // without them the two mark tiers simply run one after the other; the
-    // side stream (the short, latency-bound thread-per-source tier) gets the
-    // highest priority so that its blocks are placed before the warp tier's
-    int prio_least = 0, prio_greatest = 0;
-    cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
-    if (cudaStreamCreateWithPriority(&g->side, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
+    // without them the two mark tiers simply run one after the other
+    if (cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();

@@ -148,12 +148,6 @@ __host__ __device__ __forceinline__ uint32_t dedup_words(uint32_t m) {
     return h;
 }
 
-// Per-warp key bitmap of a hash-set source in the delete / query mark
-// (the list table's shared space: 2 * LIST_MAX words), used for sets of at
-// most FILT_MAX_WORDS words (<= 2048 keys: under 12% false positives).
-constexpr uint32_t FILT_BITS = 32 * 2 * LIST_MAX;
-constexpr uint32_t FILT_MAX_WORDS = 4096;
-
 // Tiny adjacencies (one thread per source): at most TINY_DEG entries in at
 // most TINY_NB blocks, at most TINY_M batch entries.
 constexpr uint32_t TINY_DEG = 128;

@@ -827,30 +827,6 @@ __global__ void __launch_bounds__(256, 4) k_mark(GraphView g) {
         const uint32_t nquads = (nslots + 3) >> 2;
         const bool single = (ni == 1);
         uint32_t running = 0;
-        // Hash-set sources: when the set is small next to this item (a
-        // coalesced read of it costs at most a quarter of the random probes),
-        // a per-warp bitmap of its keys (one bit per key, in the list table's
-        // shared space) turns most misses into one shared-memory test
-        bool filt = false;
-        if ((MODE == MODE_DELETE || MODE == MODE_QUERY) && !listmode && a.z != 0 && a.z <= FILT_MAX_WORDS &&
-            a.z <= 8u * nslots) {
-            filt = true;
-            uint4 *bm4 = reinterpret_cast<uint4 *>(hk);
-            for (uint32_t j = lane; j < FILT_BITS / 128; j += 32) bm4[j] = make_uint4(0u, 0u, 0u, 0u);
-            __syncwarp();
-            for (uint32_t j = lane * 4; j < a.z; j += 128) {
-                const uint4 t4 = *reinterpret_cast<const uint4 *>(g.arena + a.y + j);
-                const uint32_t tw[4] = {t4.x, t4.y, t4.z, t4.w};
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if (tw[k] != EMPTY_KEY) {
-                        const uint32_t bit = hidx(tw[k], FILT_BITS);
-                        atomicOr(&hk[bit >> 5], 1u << (bit & 31u));
-                    }
-                }
-            }
-            __syncwarp();
-        }
         for (uint32_t q0 = 0; q0 < nquads; q0 += 32) {
             const uint32_t q = q0 + lane;
             const bool qv = q < nquads;
@@ -896,14 +872,7 @@ __global__ void __launch_bounds__(256, 4) k_mark(GraphView g) {
                 // next bucket, only past four occupied slots without the key
                 const uint32_t *tab = g.arena + a.y;
                 const uint32_t nbk = a.z / HB;
-                uint32_t need = vmask;  // entries that may be in the set
-                if (filt) {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const uint32_t bit = hidx(e[j], FILT_BITS);
-                        if (!((hk[bit >> 5] >> (bit & 31u)) & 1u)) need &= ~(1u << j);
-                    }
-                }
+                const uint32_t need = vmask;
                 uint4 x0[4];
                 uint32_t bk[4];
 #pragma unroll
