@@ -92,6 +92,7 @@ __global__ void k_bfs_seed(GraphView g, uint32_t source, uint32_t *dist, uint32_
         ctr[0] = live ? 1u : 0u;  // frontier size
         ctr[1] = 0;               // items
         ctr[2] = 0;               // next frontier size
+        ctr[3] = live ? 1u : 0u;  // levels reached so far
     }
 }
 
@@ -138,9 +139,12 @@ __global__ void __launch_bounds__(256) k_bfs_expand(GraphView g, const uint2 *__
     }
 }
 
-// Next frontier becomes the current one: ctr = {frontier, items, next}.
-__global__ void k_bfs_advance(uint32_t *ctr) {
+// Next frontier becomes the current one: ctr = {frontier, items, next,
+// levels}.  A level with an empty frontier changes nothing, so the host may
+// launch several levels between two reads of the frontier size.
+__global__ void k_bfs_advance(uint32_t *ctr, uint32_t level) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
+        if (ctr[2]) ctr[3] = level + 2;
         ctr[0] = ctr[2];
         ctr[1] = 0;
         ctr[2] = 0;
@@ -161,7 +165,7 @@ cudaError_t launch_bfs_level(const GraphView &g, uint32_t aib, const uint32_t *c
     const int grid = lc.num_sms * GRID_MULT;
     k_an_items<<<grid, 256, 0, lc.stream>>>(g, cur, ctr, aib, items, ctr + 1);
     k_bfs_expand<<<grid, 256, 0, lc.stream>>>(g, items, ctr + 1, aib, dist, level, next, ctr + 2);
-    k_bfs_advance<<<1, 32, 0, lc.stream>>>(ctr);
+    k_bfs_advance<<<1, 32, 0, lc.stream>>>(ctr, level);
     return cudaGetLastError();
 }
 

@@ -1322,17 +1322,20 @@ gv_status gv_bfs(gv_graph *g, uint32_t source, uint32_t *dist, uint32_t *h_level
     const uint32_t aib = analytics_item_blocks(g);
     GV_CK(gv::launch_bfs_seed(v, source, (uint32_t *)dd, g->an_cur, g->an_ctr, lcfg(g, s)));
     uint32_t *cur = g->an_cur, *nxt = g->an_next;
-    uint32_t levels = 0;
-    for (uint32_t level = 0;; ++level) {
-        // frontier size of this level (one read per level)
-        GV_CK(cudaMemcpyAsync(g->h_small, g->an_ctr, 4, cudaMemcpyDeviceToHost, s));
+    // Levels go out in groups of kGroup between two reads of the frontier
+    // size (levels past the last one find an empty frontier and do nothing),
+    // so a search of L levels synchronises about L / kGroup times.
+    constexpr uint32_t kGroup = 4;
+    for (uint32_t level = 0; level <= g->nv;) {
+        for (uint32_t k = 0; k < kGroup; ++k, ++level) {
+            GV_CK(gv::launch_bfs_level(v, aib, cur, nxt, g->an_items, g->an_ctr, (uint32_t *)dd, level, lcfg(g, s)));
+            std::swap(cur, nxt);
+        }
+        GV_CK(cudaMemcpyAsync(g->h_small, g->an_ctr, 16, cudaMemcpyDeviceToHost, s));
         GV_CK(cudaStreamSynchronize(s));
-        const uint32_t nf = (uint32_t)(g->h_small[0] & 0xFFFFFFFFull);
-        if (nf == 0) break;
-        levels = level + 1;
-        GV_CK(gv::launch_bfs_level(v, aib, cur, nxt, g->an_items, g->an_ctr, (uint32_t *)dd, level, lcfg(g, s)));
-        std::swap(cur, nxt);
+        if ((uint32_t)(g->h_small[0] & 0xFFFFFFFFull) == 0) break;  // frontier empty
     }
+    const uint32_t levels = (uint32_t)(g->h_small[1] >> 32);  // ctr[3]
     if (hd) {
         GV_CK(cudaMemcpyAsync(dist, dd, (size_t)g->nv * 4, cudaMemcpyDeviceToHost, s));
         GV_CK(cudaStreamSynchronize(s));

@@ -998,8 +998,13 @@ struct Blocks8 {
 
 template <int MODE>
 __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
+    // Vertex deletes visit every vertex id directly (no touched list: the
+    // incoming-edge pass covers all live vertices); other modes visit the
+    // planned tiny sources.
+    constexpr bool DIRECT = MODE == MODE_VDEL;
     Dev *dev = g.dev;
-    const uint32_t ntiny = dev->n_tiny;
+    const uint32_t ntiny = DIRECT ? g.nv : dev->n_tiny;
+    const uint32_t tiny_deg = min(TINY_DEG, TINY_NB * g.C);
     const uint32_t C = g.C;
     const unsigned long long P = g.P;
     const unsigned long long qbb = qmod(dev->q_back, P);
@@ -1017,7 +1022,16 @@ __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
         const uint32_t k = base + lane_id();
         bool act = k < ntiny;
         uint32_t t = 0, deg = 0, nb = 0, root = NIL, m = 0, aoff = 0;
-        if (act) {
+        if (DIRECT) {
+            if (act) act = g.alive[k] != 0;
+            if (act) {
+                const uint4 sv = g.sent[k];
+                deg = sv.x;
+                nb = sv.y;
+                root = sv.z;
+                act = deg > 0 && deg <= tiny_deg && nb <= TINY_NB;
+            }
+        } else if (act) {
             t = g.t_tiny[k];
             const uint4 a = g.t_a[t];
             const uint4 b = g.t_b[t];
@@ -1124,7 +1138,7 @@ __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
             if (fr && h >= 2 && h / 2 <= nbn) g.links[2ull * bl.b[h / 2 - 1] + (h & 1u)] = NIL;
         }
         if (changed) {
-            const uint32_t u = g.t_vid[t];
+            const uint32_t u = DIRECT ? k : g.t_vid[t];
             g.sent[u] = make_uint4(w, nbn, nbn ? root : NIL, nbn ? bl.get(nbn - 1) : NIL);
             removed += deg - w;
             if (g.set_G && !g.seg_own) atomicAdd(&s_mhist[member_of(g.set_vbase, g.set_G, u)], deg - w);
@@ -1465,33 +1479,29 @@ __global__ void __launch_bounds__(256) k_plan_vdel_in(GraphView g) {
     const uint32_t nv = g.nv;
     const uint32_t IB = g.IB;
     const uint32_t tiny_deg = min(TINY_DEG, TINY_NB * g.C);
-    __shared__ uint32_t s_at, s_ai, s_am, s_an;
+    __shared__ uint32_t s_at, s_ai, s_am;
     for (uint32_t base = blockIdx.x * blockDim.x; base < nv; base += gridDim.x * blockDim.x) {
         const uint32_t u = base + threadIdx.x;
-        uint32_t take = 0, ni = 0, tiny = 0;
+        uint32_t take = 0, ni = 0;
         uint4 s = make_uint4(0, 0, NIL, NIL);
         if (u < nv && g.alive[u]) {
             s = g.sent[u];
-            if (s.x) {
+            // tiny adjacencies are handled by k_mark_tiny straight from the
+            // dictionary; only the others become touched sources with items
+            if (s.x && !(s.x <= tiny_deg && s.y <= TINY_NB)) {
                 take = 1;
-                if (s.x <= tiny_deg && s.y <= TINY_NB) tiny = 1;
-                else ni = (s.y + IB - 1) / IB;
+                ni = (s.y + IB - 1) / IB;
             }
         }
-        uint32_t ttot, ntot;
+        uint32_t ttot;
         const uint32_t tex = block_excl_scan(take, &ttot);
-        const uint32_t nex = block_excl_scan(tiny, &ntot);
-        if (threadIdx.x == 0) {
-            s_at = ttot ? atomicAdd(&g.dev->n_touched, ttot) : 0u;
-            s_an = ntot ? atomicAdd(&g.dev->n_tiny, ntot) : 0u;
-        }
+        if (threadIdx.x == 0) s_at = ttot ? atomicAdd(&g.dev->n_touched, ttot) : 0u;
         const uint32_t item0 = alloc_items(g, ni, &s_ai, &s_am);
         if (take) {
             const uint32_t t = s_at + tex;
             g.t_vid[t] = u;
             g.t_b[t] = make_uint4(s.x, s.y, s.z, ni);
             g.t_a[t] = make_uint4(0, 0, 0, item0);
-            if (tiny) g.t_tiny[s_an + nex] = t;
             emit_items(g, t, item0, ni);
         }
         __syncthreads();
