@@ -708,13 +708,53 @@ def run_rows(args):
     reached = dist.cpu().numpy().view(np.uint32) != 0xFFFFFFFF
     trav = int(deg0[reached].sum())
     row("f2-bfs", f"BFS from vertex {src} ({int(reached.sum())} reached)", trav, "traversed edges", ms,
-        8 * trav + 16 * int(reached.sum()) + 4 * nv, timer="CUDA events (one host read per level)")
+        8 * trav + 16 * int(reached.sum()) + 4 * nv, timer="CUDA events (one host read per four levels)")
     rank = torch.zeros(nv, dtype=torch.float64, device="cuda")
     iters = 10
     ms = timed(lambda: gv.gv_pagerank(g.handle, iters, 0.85, rank, stream.cuda_stream), n=3)
     row("f2-pagerank", f"PageRank, {iters} iterations", iters * E, "edge visits", ms,
         iters * (4 * E + 8 * E + 48 * nv))
     g.close()
+
+    # f1: set-semantics insert of the 10M batch (half of it already stored)
+    # on a GV_DEDUP graph: membership pass over the stored blocks + insert
+    gd = gv.Graph(nv, block_capacity=C, pool_bytes=POOL_BYTES, flags=gv.GV_DEDUP)
+    gd.reserve(max(BATCH, BASE_EDGES))
+    gd.bulk_build(d_bs, d_bd, cnt)
+    half = BATCH // 2
+    d_h, d_hd = t(us[:half]), t(ud[:half])
+    d_s, d_d = t(us), t(ud)
+    gd.insert_edges(d_h, d_hd, cnt)  # the first half is stored before every timed call
+    torch.cuda.synchronize()
+    degd, _ = gd.degrees()
+    srcs = np.unique(us)
+    ms = timed(lambda: gd.insert_edges(d_s, d_d, cnt), post=lambda: (gd.delete_edges(d_s, d_d, cnt),
+                                                                     gd.insert_edges(d_h, d_hd, cnt)))
+    gd.insert_edges(d_s, d_d, cnt)
+    added = int(cnt[0].item())
+    row("f1-dedup", f"set-semantics insert of {BATCH} pairs ({added} new)", BATCH, "edges", ms,
+        12 * BATCH + 4 * int(degd.astype(np.int64)[srcs].sum()) + 32 * srcs.size)
+    gd.close()
+
+    # f4: bulk build into a pool of 1/8 of the blocks it needs, grown by
+    # GV_GROW in 25% steps (allocation and copies inside the timed call)
+    need_blocks = int(((np.bincount(bs, minlength=nv) + C - 1) // C).sum())
+    small = (need_blocks // 8) * (4 * C + 12)
+    holder3 = {}
+
+    def mk3():
+        if "g" in holder3:
+            holder3["g"].close()
+        holder3["g"] = gv.Graph(nv, block_capacity=C, pool_bytes=small, flags=gv.GV_GROW)
+        holder3["g"].reserve(BASE_EDGES)
+        torch.cuda.synchronize()
+
+    ms = timed(lambda: holder3["g"].bulk_build(d_bs, d_bd, cnt), pre=mk3, n=3)
+    grown = holder3["g"].stats()
+    row("f4-grow", f"bulk build with pool growth ({small >> 20} MiB -> {grown['pool_bytes'] >> 20} MiB)",
+        bs.size, "edges", ms, 12 * bs.size + 16 * nv, pool_bytes_final=grown["pool_bytes"],
+        device_bytes=grown["device_bytes"], timer="CUDA events (growth allocations and copies included)")
+    holder3["g"].close()
 
     # a9 / a10 on the uniform 2^22 graph
     er = W.er_mixed(3, rounds=0)

@@ -193,6 +193,7 @@ GraphView view(const gv_graph *g) {
     v.qpos = g->qpos;
     v.dead = g->dead;
     v.max_items = g->icap;
+    v.tiny_cap = g->tcap;
     v.arena_cap = g->acap;
     v.set_G = 0;
     v.set_vbase = nullptr;

@@ -46,7 +46,7 @@ struct Dev {
     unsigned int abort;             // set when this call must not mutate the graph
     unsigned int n_tiny;            // touched sources handled one per thread
     unsigned int n_mitems;          // work items of multi-item sources (top of the item array)
-    unsigned int pad;
+    unsigned int n_tiny_hi;         // tiny sources with more than TINY_SPLIT entries (top of t_tiny)
     unsigned long long harena_used; // words of the arena's hash region used
 };
 
@@ -92,6 +92,7 @@ struct GraphView {
     uint8_t *pflag;         // set-semantics insert: 1 if the pair claimed its value's slot
     uint32_t *dead;         // vertex delete: bitmap of deleted ids
     unsigned long long max_items;
+    unsigned long long tiny_cap;       // entries of t_tiny (touched capacity)
     unsigned long long arena_cap;
     // graph sets (many member graphs in one structure); set_G == 0 otherwise
     uint32_t set_G;                    // members
@@ -153,6 +154,10 @@ __host__ __device__ __forceinline__ uint32_t dedup_words(uint32_t m) {
 constexpr uint32_t TINY_DEG = 128;
 constexpr uint32_t TINY_NB = 8;
 constexpr uint32_t TINY_M = 16;
+// Tiny sources of up to TINY_SPLIT entries are listed from the bottom of
+// t_tiny, larger ones from the top, so that a warp's 32 threads walk
+// adjacencies of similar length (loop trip counts diverge less).
+constexpr uint32_t TINY_SPLIT = 32;
 // Queries only read: their thread-per-source tier stops at four blocks (a
 // longer serial walk costs more than a warp item saves).
 constexpr uint32_t TINY_DEG_Q = 64;

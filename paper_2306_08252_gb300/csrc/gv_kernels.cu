@@ -506,6 +506,7 @@ __global__ void __launch_bounds__(256) k_finalize_insert(GraphView g, unsigned l
         dev->n_items = 0;
         dev->n_mitems = 0;
         dev->n_tiny = 0;
+        dev->n_tiny_hi = 0;
         dev->arena_used = 0;
         dev->harena_used = 0;
         dev->free_total = 0;
@@ -556,7 +557,7 @@ __global__ void __launch_bounds__(256) k_plan_member(GraphView g) {
     const uint32_t IB = g.IB;
     const uint32_t tiny_deg = min(TINY_DEG, TINY_NB * g.C);
     __shared__ unsigned long long s_aw, s_hw;
-    __shared__ uint32_t s_ai, s_am, s_at;
+    __shared__ uint32_t s_ai, s_am, s_at, s_ath;
     for (uint32_t base = blockIdx.x * blockDim.x; base < nt; base += gridDim.x * blockDim.x) {
         const uint32_t t = base + threadIdx.x;
         uint32_t m = 0, lw = 0, hw = 0, ni = 0, tiny = 0;
@@ -576,14 +577,17 @@ __global__ void __launch_bounds__(256) k_plan_member(GraphView g) {
                 else ni = (s.y + IB - 1) / IB;
             }
         }
-        uint32_t lt, ht, ttot;
+        const uint32_t tlo = tiny && s.x <= TINY_SPLIT, thi = tiny && s.x > TINY_SPLIT;
+        uint32_t lt, ht, ttot, tthi;
         const uint32_t lex = block_excl_scan(lw, &lt);
         const uint32_t hex = block_excl_scan(hw, &ht);
-        const uint32_t tex = block_excl_scan(tiny, &ttot);
+        const uint32_t tex = block_excl_scan(tlo, &ttot);
+        const uint32_t thx = block_excl_scan(thi, &tthi);
         if (threadIdx.x == 0) {
             s_aw = lt ? atomicAdd(&g.dev->arena_used, (unsigned long long)lt) : 0ull;
             s_hw = ht ? atomicAdd(&g.dev->harena_used, (unsigned long long)ht) : 0ull;
             s_at = ttot ? atomicAdd(&g.dev->n_tiny, ttot) : 0u;
+            s_ath = tthi ? atomicAdd(&g.dev->n_tiny_hi, tthi) : 0u;
         }
         const uint32_t item0 = alloc_items(g, ni, &s_ai, &s_am);
         if (t < nt) {
@@ -593,7 +597,8 @@ __global__ void __launch_bounds__(256) k_plan_member(GraphView g) {
             g.t_a[t] = make_uint4(m, aoff, hw, item0);
             g.t_b[t] = make_uint4(s.x, s.y, s.z, ni);
             g.vinfo[vslot(g.vmask, g.t_vid[t])] = make_uint4(m, aoff, hw, 0u);
-            if (tiny) g.t_tiny[s_at + tex] = t;
+            if (tlo) g.t_tiny[s_at + tex] = t;
+            if (thi) g.t_tiny[g.tiny_cap - 1 - (s_ath + thx)] = t;
             emit_items(g, t, item0, ni);
         }
         __syncthreads();
@@ -1003,7 +1008,8 @@ __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
     // planned tiny sources.
     constexpr bool DIRECT = MODE == MODE_VDEL;
     Dev *dev = g.dev;
-    const uint32_t ntiny = DIRECT ? g.nv : dev->n_tiny;
+    const uint32_t nlo = DIRECT ? g.nv : dev->n_tiny, nhi = DIRECT ? 0u : dev->n_tiny_hi;
+    const uint32_t ntiny = nlo + nhi;
     const uint32_t tiny_deg = min(TINY_DEG, TINY_NB * g.C);
     const uint32_t C = g.C;
     const unsigned long long P = g.P;
@@ -1032,7 +1038,7 @@ __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
                 act = deg > 0 && deg <= tiny_deg && nb <= TINY_NB;
             }
         } else if (act) {
-            t = g.t_tiny[k];
+            t = g.t_tiny[k < nlo ? k : (uint32_t)(g.tiny_cap - nhi + (k - nlo))];
             const uint4 a = g.t_a[t];
             const uint4 b = g.t_b[t];
             deg = b.x;
@@ -1373,6 +1379,7 @@ __global__ void __launch_bounds__(256) k_finalize_member(GraphView g, unsigned l
         dev->n_items = 0;
         dev->n_mitems = 0;
         dev->n_tiny = 0;
+        dev->n_tiny_hi = 0;
         dev->arena_used = 0;
         dev->harena_used = 0;
         dev->free_total = 0;
@@ -1470,6 +1477,7 @@ __global__ void k_reset_lists(GraphView g) {
         g.dev->n_items = 0;
         g.dev->n_mitems = 0;
         g.dev->n_tiny = 0;
+        g.dev->n_tiny_hi = 0;
     }
 }
 
@@ -1526,6 +1534,7 @@ __global__ void __launch_bounds__(256) k_finalize_vdel(GraphView g, const uint32
         dev->n_items = 0;
         dev->n_mitems = 0;
         dev->n_tiny = 0;
+        dev->n_tiny_hi = 0;
         dev->arena_used = 0;
         dev->harena_used = 0;
         dev->free_total = 0;
