@@ -547,22 +547,33 @@ def run_serving(args):
     cap_reqs, _ = W.serving_requests(6, bs, bd, scale, args.requests)
     t_gen = time.perf_counter() - t_gen
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
+    d_bs, d_bd = dev(bs), dev(bd)
     blocks = edges // C * 2 + (1 << scale) + (1 << 22)
-    g = gv.Graph(1 << scale, block_capacity=C, pool_bytes=int(blocks * (4 * C + 12)))
-    g.bulk_build(dev(bs), dev(bd))
-    g.sync()
-    server = serve.Server(g, C, slots=4, merge_pairs=2_000_000, max_reqs=1024)
+    state = {}
+
+    def fresh():
+        """Every measurement starts from the same bulk-built graph (a stream
+        of 10,000 requests inserts ~3e8 pairs on top of the base)."""
+        if "g" in state:
+            state["g"].close()
+        g = gv.Graph(1 << scale, block_capacity=C, pool_bytes=int(blocks * (4 * C + 12)), flags=gv.GV_GROW)
+        g.bulk_build(d_bs, d_bd)
+        assert g.sync() == 0
+        state["g"] = g
+        return serve.Server(g, C, slots=4, merge_pairs=2_000_000, max_reqs=1024)
+
     # saturated capacity (all requests present at time 0)
+    server = fresh()
     crs = [serve.Request(k, a, b, 0.0) for k, a, b in cap_reqs]
     t0 = time.perf_counter()
     server.run(crs, realtime=False)
     cap = len(crs) / (time.perf_counter() - t0)
     levels = []
     for load in (0.5, 0.7, 0.9):
+        server = fresh()
         rate = load * cap
         arrivals = np.cumsum(gaps) / rate
         rs = [serve.Request(k, a, b, t) for (k, a, b), t in zip(reqs, arrivals)]
-        runs0, merged0 = server.runs, server.merged_requests
         server.run(rs, realtime=True)
         skip = len(rs) // 10
         meas = [r for r in rs[skip:] if r.status == gv.GV_OK]
@@ -571,9 +582,10 @@ def run_serving(args):
         lat = serve.latency_stats(rs, skip=skip)
         levels.append({"load": load, "rate_req_per_s": rate, "p50_ms": lat["p50_ms"], "p99_ms": lat["p99_ms"],
                        "mean_ms": lat["mean_ms"], "updates_per_s": upd / span, "requests": len(rs),
-                       "warmup_requests": skip, "runs": server.runs - runs0,
-                       "requests_per_run": (server.merged_requests - merged0) / max(server.runs - runs0, 1),
+                       "warmup_requests": skip, "runs": server.runs,
+                       "requests_per_run": server.merged_requests / max(server.runs, 1),
                        "failed": sum(1 for r in rs if r.status != gv.GV_OK)})
+    g = state["g"]
     assert g.sync() == 0
     st = g.stats()
     g.close()
@@ -583,7 +595,8 @@ def run_serving(args):
            "config": {"workload": f"RMAT scale {scale} ({1 << scale} vertices, {edges} edges), C={C}; "
                                   f"{args.requests} requests, 40/40/20 insert/delete/query, sizes log-uniform 1..1M",
                       "slots": 4, "merge_pairs": 2_000_000, "generation_s": t_gen},
-           "capacity_req_per_s": cap, "levels": levels, "final_edges": st["num_edges"]}
+           "capacity_req_per_s": cap, "levels": levels, "final_edges": st["num_edges"],
+           "final_pool_bytes": st["pool_bytes"]}
     print(json.dumps(res), flush=True)
     return 0
 

@@ -20,8 +20,10 @@ host and device buffers: host-to-device copy, the library call, the
 device-to-host copy of the results and an event.  An insert run is admitted
 only if its worst-case block demand (ceil(B / C) + B new blocks for B pairs)
 fits the free blocks of the pool as last known; otherwise the loop drains
-the in-flight runs, refreshes the pool counters and tries again (a request
-that still does not fit fails with an out-of-memory result).
+the in-flight runs, refreshes the pool counters and tries again.  A run that
+still does not fit fails with an out-of-memory result, unless the graph was
+created with GV_GROW: then it is launched and the library grows the pool
+before inserting.
 
 Latency of a request = completion (its run's event observed by the loop)
 minus its arrival time.
@@ -89,6 +91,7 @@ class Server:
         self.inflight = collections.deque()
         graph.reserve(self.cap)
         st = graph.stats()
+        self.grow = bool(st["flags"] & gv.GV_GROW)
         self.nv = st["num_vertices"]
         self.free_blocks = st["pool_blocks_free"]
         self.reserved_blocks = 0
@@ -205,7 +208,7 @@ class Server:
                             self.inflight[0].event.synchronize()
                             self._finish(self.inflight.popleft(), time.perf_counter() - t0)
                         self._refresh_pool()
-                        if need > self.free_blocks:
+                        if need > self.free_blocks and not self.grow:
                             for r in run:
                                 r.status = gv.GV_ERR_OUT_OF_MEMORY
                                 r.done = time.perf_counter() - t0
