@@ -1768,21 +1768,25 @@ static void member_tail(const GraphView &g0, const uint32_t *src, const uint32_t
         PhaseScope ps(lc, del ? PH_DEL_MARK : PH_QRY_MARK);
         k_mark<MODE><<<gi, 256, 0, lc.stream>>>(g);
     }
-    if (fork) {
-        cudaEventRecord(lc.join, lc.side);
-        cudaStreamWaitEvent(lc.stream, lc.join, 0);
-    } else {
+    if (!fork) {
         PhaseScope ps(lc, del ? PH_DEL_MARK_TINY : PH_QRY_MARK_TINY);
         k_mark_tiny<MODE><<<gt, 256, 0, lc.stream>>>(g);
     }
     if (del) {
+        // the hole filling of multi-item sources does not touch tiny sources
+        // either: the side stream joins only before the finalize
         {
             PhaseScope ps(lc, PH_DEL_VSCAN);
             k_vscan<MODE><<<grid_for(tcap, 8, cap), 256, 0, lc.stream>>>(g);
         }
         PhaseScope ps(lc, PH_DEL_MOVE);
         k_move<MODE><<<gi, 256, 0, lc.stream>>>(g);
-    } else {
+    }
+    if (fork) {
+        cudaEventRecord(lc.join, lc.side);
+        cudaStreamWaitEvent(lc.stream, lc.join, 0);
+    }
+    if (!del) {
         PhaseScope ps(lc, PH_QRY_OUT);
         k_query_out<<<grid_for(n, 256, cap), 256, 0, lc.stream>>>(g, n, qout);
     }
@@ -1819,10 +1823,10 @@ cudaError_t launch_vertex_delete(const GraphView &g, const uint32_t *ids, uint32
         cudaEventRecord(lc.join, lc.side);
     }
     k_mark<MODE_VDEL><<<gi, 256, 0, lc.stream>>>(g);
-    if (fork) cudaStreamWaitEvent(lc.stream, lc.join, 0);
-    else k_mark_tiny<MODE_VDEL><<<grid_for(g.nv, 256, cap), 256, 0, lc.stream>>>(g);
+    if (!fork) k_mark_tiny<MODE_VDEL><<<grid_for(g.nv, 256, cap), 256, 0, lc.stream>>>(g);
     k_vscan<MODE_VDEL><<<grid_for(g.nv, 8, cap), 256, 0, lc.stream>>>(g);
     k_move<MODE_VDEL><<<gi, 256, 0, lc.stream>>>(g);
+    if (fork) cudaStreamWaitEvent(lc.stream, lc.join, 0);
     k_finalize_vdel<<<grid_for(k, 256, cap), 256, 0, lc.stream>>>(g, ids, k);
     return cudaGetLastError();
 }
