@@ -135,8 +135,10 @@ enum Mode : int { MODE_INSERT = 0, MODE_DELETE = 1, MODE_QUERY = 2, MODE_VDEL = 
 // A source's batch destinations are kept as a plain list up to LIST_MAX
 // entries (tested through a shared-memory hash set built per work item) and
 // as a bucketed hash set in the arena above it: buckets of HB = 8 words (one
-// 32-byte sector), so an insert or a lookup reads its whole bucket in one
-// round trip and only a full bucket sends it to the next one.
+// 32-byte sector) whose occupied slots are always a prefix.  An insert reads
+// its whole home bucket in one round trip (two 16-byte loads in flight); a
+// lookup reads the first half and goes on only past four occupied slots; only
+// a full bucket sends either to the next one.
 constexpr uint32_t LIST_MAX = 256;
 constexpr uint32_t HB = 8;
 

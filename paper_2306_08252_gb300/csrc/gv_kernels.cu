@@ -3,11 +3,13 @@
 // Every batch operation (insert, delete, query) starts by grouping the batch
 // by source vertex on the device.  The paper converts each batch to CSR on
 // the host before copying it over ("Initialization and batch updates"); here
-// a counting pass aggregates each tile of pairs in a shared-memory hash table
-// and adds one count per (tile, source) into a per-vertex counter, so hub
-// vertices do not serialise on one global atomic per edge.  The first source
-// to see a zero count appends itself to the call's touched list, which plays
-// the role of the CSR row list.
+// a counting pass gives every valid pair its rank among its source's pairs:
+// large batches take one atomic per pair on the source's counter (its return
+// value is the rank) and list the touched sources afterwards by a scan of the
+// counters; small batches aggregate each tile in a shared-memory table first
+// (one atomic per (tile, source)) and list touched sources on the fly.  The
+// touched list plays the role of the CSR row list; per-vertex counters are
+// indexed through a bijective scramble of the id (see vslot).
 //
 // Insert (Algorithm 1) then runs per touched source:
 //   plan    block demand need(u) = ceil(max(0, cnt - space) / C) with
@@ -20,23 +22,27 @@
 //           k = nblocks + 1 + j hangs under heap index k/2 on side k&1 (the
 //           bit-string rule, Figure 4); an old parent is found by walking the
 //           tree from the root along the bits of k/2.
-//   scatter each pair gets rank r among its source's batch pairs (per-tile
-//           rank + one atomic cursor per (tile, source)); r < space goes to
-//           the last block at slot deg mod C + r, the rest to new block
-//           (r - space) / C, slot (r - space) mod C.
+//   scatter pair of rank r: r < space goes to the last block at slot
+//           deg mod C + r, the rest to new block (r - space) / C, slot
+//           (r - space) mod C; no atomics.
 //   final   sentinels updated; the queue front advances by the blocks popped.
 //
 // Delete (Algorithm 2) and query (Algorithm 3) share one membership pipeline:
-//   plan    per touched source: its batch destinations go to a list (<= 32
-//           entries) or an open-addressing hash set (> 32) in an arena; its
-//           blocks are cut into work items of IB blocks (IB * C <= 512 slots).
-//   scatter batch destinations into the lists / hash sets.
+//   plan    per touched source: its batch destinations go to a list (<= 256
+//           entries) or a bucketed hash set in an arena; small adjacencies
+//           (a few blocks, <= 16 batch entries) go to the thread-per-source
+//           tier, the others are cut into work items of IB blocks
+//           (IB * C <= 512 slots).
+//   scatter batch destinations into the lists (plain store at the rank) or
+//           the hash sets (CAS into the first empty slot of the home bucket).
 //   mark    one warp per item: resolve the item's block ids by walking the
-//           CBT, stream the entries with 16-byte loads, test membership
-//           (binary search over a warp-sorted list, or a hash probe).  Query
-//           sets hit flags.  Delete compacts single-item adjacencies in place
-//           (stable) and frees their emptied tail blocks; multi-item
-//           adjacencies record a survivor bitmask per item.
+//           CBT, stream the entries with 16-byte loads, test membership (a
+//           per-warp shared hash set built from the list, or the arena hash
+//           set).  Query sets hit flags.  Delete compacts single-item
+//           adjacencies in place (stable) and frees their emptied tail blocks;
+//           multi-item adjacencies record a survivor bitmask per item.  The
+//           thread-per-source tier does the same for small adjacencies, with
+//           the batch entries in registers, on a second stream.
 //   vscan   per multi-item source: new degree = survivors; per item the
 //           number of holes below the new degree and of survivors at or above
 //           it, prefix-summed over the source's items.
