@@ -1715,7 +1715,9 @@ cudaError_t launch_insert_tail(const GraphView &g, const uint32_t *src, const ui
                                unsigned long long n, unsigned long long tcap,
                                unsigned long long *counts, const LaunchCfg &lc) {
     const int cap = lc.num_sms * GRID_MULT;
-    const int gt = grid_for(tcap, 256, cap);
+    // a batch of n pairs touches at most n sources: small batches launch
+    // small grids (grid-stride loops cover any count)
+    const int gt = grid_for(tcap < n ? tcap : n, 256, cap);
     {
         PhaseScope ps(lc, PH_INS_PLAN);
         k_plan_insert<<<gt, 256, 0, lc.stream>>>(g);
@@ -1743,8 +1745,11 @@ static void member_tail(const GraphView &g0, const uint32_t *src, const uint32_t
     GraphView g = g0;
     g.hbase = (uint32_t)((n + 63) / 64 * 64);  // lists below (at most n words), hash sets above
     const int cap = lc.num_sms * GRID_MULT;
-    const int gt = grid_for(tcap, 256, cap);
-    const int gi = lc.num_sms * GRID_MULT;  // warp-per-item kernels: 8 warps per CTA
+    // grids follow the batch: at most n touched sources; work items start at
+    // one per source (grid-stride loops cover sources with many items)
+    const unsigned long long nt = tcap < n ? tcap : n;
+    const int gt = grid_for(nt, 256, cap);
+    const int gi = grid_for(4 * nt + 256, 8, lc.num_sms * GRID_MULT);  // warp-per-item kernels: 8 warps per CTA
     const bool del = MODE == MODE_DELETE;
     {
         PhaseScope ps(lc, del ? PH_DEL_PLAN : PH_QRY_PLAN);
@@ -1783,7 +1788,7 @@ static void member_tail(const GraphView &g0, const uint32_t *src, const uint32_t
         // either: the side stream joins only before the finalize
         {
             PhaseScope ps(lc, PH_DEL_VSCAN);
-            k_vscan<MODE><<<grid_for(tcap, 8, cap), 256, 0, lc.stream>>>(g);
+            k_vscan<MODE><<<grid_for(nt, 8, cap), 256, 0, lc.stream>>>(g);
         }
         PhaseScope ps(lc, PH_DEL_MOVE);
         k_move<MODE><<<gi, 256, 0, lc.stream>>>(g);
@@ -1889,8 +1894,9 @@ cudaError_t launch_dedup_insert_prepare(const GraphView &g0, const uint32_t *src
     GraphView g = g0;
     g.hbase = 0;
     const int cap = lc.num_sms * GRID_MULT;
-    const int gt = grid_for(tcap, 256, cap);
-    const int gi = lc.num_sms * GRID_MULT;
+    const unsigned long long nt = tcap < n ? tcap : n;
+    const int gt = grid_for(nt, 256, cap);
+    const int gi = grid_for(4 * nt + 256, 8, cap);
     k_plan_member<MODE_DEDUP><<<gt, 256, 0, lc.stream>>>(g);
     k_arena_init<MODE_DEDUP><<<grid_for(8 * n + 64, 256, cap), 256, 0, lc.stream>>>(g);
     k_scatter_member<MODE_DEDUP><<<grid_for(n, 256 * PP, cap), 256, 0, lc.stream>>>(g, src, dst, n);
