@@ -31,6 +31,7 @@ minus its arrival time.
 from __future__ import annotations
 
 import collections
+import gc
 import time
 
 import numpy as np
@@ -185,6 +186,17 @@ class Server:
         realtime=False treats every request as arrived at time 0 (saturated
         capacity measurement)."""
         reqs = list(requests)
+        # no cyclic garbage collection while serving: a full collection over
+        # the request objects stalls the loop for tens of milliseconds
+        gc_was_on = gc.isenabled()
+        gc.disable()
+        try:
+            return self._run(reqs, realtime)
+        finally:
+            if gc_was_on:
+                gc.enable()
+
+    def _run(self, reqs, realtime):
         q = collections.deque()
         i = 0
         t0 = time.perf_counter()
