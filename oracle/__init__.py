@@ -57,6 +57,8 @@ def _get():
                 "orc_pop_ranges": ([p, u32, p, p], None),
                 "orc_insert_block_demand": ([u64, u64, u32], u64),
                 "orc_bfs": ([p, u32, p], u32),
+                "orc_insert_edges_weighted": ([p, p, p, p, u64, p, p], None),
+                "orc_neighbors_weighted": ([p, p, u32, p, p, p, u64], u64),
                 "orc_pagerank": ([p, u32, ctypes.c_double, p], None),
             }
             for name, (args, res) in sig.items():
@@ -104,6 +106,24 @@ class OracleGraph:
         self._lib.orc_insert_edges(self._g, s.ctypes.data, d.ctypes.data, s.size,
                                    a[0:].ctypes.data, a[1:].ctypes.data)
         return int(a[0]), int(a[1])
+
+    def insert_edges_weighted(self, src, dst, w):
+        s, d, ww = _u32(src), _u32(dst), _u32(w)
+        a = np.zeros(2, dtype=np.uint64)
+        self._lib.orc_insert_edges_weighted(self._g, s.ctypes.data, d.ctypes.data, ww.ctypes.data, s.size,
+                                            a[0:].ctypes.data, a[1:].ctypes.data)
+        return int(a[0]), int(a[1])
+
+    def neighbors_weighted(self, vids):
+        """(offsets, nbrs, weights) in canonical (v, w) order per vertex."""
+        v = _u32(vids)
+        off = np.zeros(v.size + 1, dtype=np.uint64)
+        tot = int(self._lib.orc_neighbors_weighted(self._g, v.ctypes.data, v.size, off.ctypes.data, None, None, 0))
+        nb = np.zeros(max(tot, 1), dtype=np.uint32)
+        wt = np.zeros(max(tot, 1), dtype=np.uint32)
+        self._lib.orc_neighbors_weighted(self._g, v.ctypes.data, v.size, off.ctypes.data, nb.ctypes.data,
+                                         wt.ctypes.data, tot)
+        return off, nb[:tot], wt[:tot]
 
     def bulk_build(self, src, dst):
         return self.insert_edges(src, dst)

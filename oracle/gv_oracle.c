@@ -6,7 +6,9 @@
  * Processing on GPUs", sections "Dynamic vertex updates", "Dynamic edge
  * updates" and "Querying operations"; Algorithms 1, 2 and 3).  It keeps one
  * sorted array of destination ids per source vertex plus an alive flag per
- * vertex and applies one operation at a time, in call order.  There is no
+ * vertex and applies one operation at a time, in call order.  An entry may
+ * carry a 32-bit payload (a weight; 0 for unweighted inserts) that stays
+ * with it through deletes and compaction.  There is no
  * blocking, no block pool, no tree: only the result the paper's structure
  * must reproduce.
  *
@@ -35,7 +37,8 @@
 #define ORC_DEDUP 1u
 
 typedef struct {
-    uint32_t *v;     /* sorted destination ids (multiset) */
+    uint32_t *v;     /* destination ids, sorted by (v, w) (multiset) */
+    uint32_t *w;     /* 32-bit payload (weight) of each entry; 0 when unweighted */
     uint64_t n;
     uint64_t cap;
 } orc_adj;
@@ -64,7 +67,20 @@ static void adj_reserve(orc_adj *a, uint64_t need) {
     uint64_t c = a->cap ? a->cap : 4;
     while (c < need) c *= 2;
     a->v = (uint32_t *)realloc(a->v, c * sizeof(uint32_t));
+    a->w = (uint32_t *)realloc(a->w, c * sizeof(uint32_t));
     a->cap = c;
+}
+
+/* Sorts an adjacency by (v, w): the canonical order of its entries. */
+static void adj_sort(orc_adj *a) {
+    uint64_t *k = (uint64_t *)malloc((a->n ? a->n : 1) * sizeof(uint64_t));
+    for (uint64_t i = 0; i < a->n; ++i) k[i] = ((uint64_t)a->v[i] << 32) | a->w[i];
+    qsort(k, a->n, sizeof(uint64_t), cmp_u64);
+    for (uint64_t i = 0; i < a->n; ++i) {
+        a->v[i] = (uint32_t)(k[i] >> 32);
+        a->w[i] = (uint32_t)(k[i] & 0xFFFFFFFFu);
+    }
+    free(k);
 }
 
 /* 1 if x occurs in the sorted array a[0..n). */
@@ -100,7 +116,10 @@ orc_graph *orc_create(uint32_t nv, uint32_t flags) {
 
 void orc_destroy(orc_graph *g) {
     if (!g) return;
-    for (uint32_t i = 0; i < g->cap; ++i) free(g->adj[i].v);
+    for (uint32_t i = 0; i < g->cap; ++i) {
+        free(g->adj[i].v);
+        free(g->adj[i].w);
+    }
     free(g->adj);
     free(g->alive);
     free(g);
@@ -130,39 +149,71 @@ static uint64_t *sorted_valid_keys(const orc_graph *g, const uint32_t *src, cons
     return k;
 }
 
+typedef struct {
+    uint32_t u, v, w;
+} orc_triple;
+
+static int cmp_triple(const void *a, const void *b) {
+    const orc_triple *x = (const orc_triple *)a, *y = (const orc_triple *)b;
+    if (x->u != y->u) return (x->u > y->u) - (x->u < y->u);
+    if (x->v != y->v) return (x->v > y->v) - (x->v < y->v);
+    return (x->w > y->w) - (x->w < y->w);
+}
+
 /*
  * insert_edges (Algorithm 1): every valid (u, v) is appended to u's
- * adjacency.  Under ORC_DEDUP the pair is added only when v is not yet in
- * adj[u] and was not already added by this batch.
+ * adjacency, with its payload w (0 when w is NULL).  Under ORC_DEDUP the
+ * pair is added only when v is not yet in adj[u] and was not already added
+ * by this batch.  The batch's valid pairs are sorted by (u, v, w) first (the
+ * CSR form the paper assumes for a batch, "Initialization and batch
+ * updates").
  */
-void orc_insert_edges(orc_graph *g, const uint32_t *src, const uint32_t *dst, uint64_t n,
-                      uint64_t *inserted, uint64_t *rejected) {
-    uint64_t m, rej, ins = 0;
-    uint64_t *k = sorted_valid_keys(g, src, dst, n, &m, &rej);
+void orc_insert_edges_weighted(orc_graph *g, const uint32_t *src, const uint32_t *dst, const uint32_t *w,
+                               uint64_t n, uint64_t *inserted, uint64_t *rejected) {
+    orc_triple *k = (orc_triple *)malloc((n ? n : 1) * sizeof(orc_triple));
+    uint64_t m = 0, rej = 0, ins = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        if (valid_pair(g, src[i], dst[i])) {
+            k[m].u = src[i];
+            k[m].v = dst[i];
+            k[m].w = w ? w[i] : 0u;
+            ++m;
+        } else {
+            ++rej;
+        }
+    }
+    qsort(k, m, sizeof(orc_triple), cmp_triple);
     uint64_t i = 0;
     while (i < m) {
-        uint32_t u = (uint32_t)(k[i] >> 32);
+        uint32_t u = k[i].u;
         uint64_t j = i;
-        while (j < m && (uint32_t)(k[j] >> 32) == u) ++j;
+        while (j < m && k[j].u == u) ++j;
         orc_adj *a = &g->adj[u];
         uint64_t old_n = a->n;
         adj_reserve(a, a->n + (j - i));
         for (uint64_t t = i; t < j; ++t) {
-            uint32_t v = (uint32_t)(k[t] & 0xFFFFFFFFu);
+            uint32_t v = k[t].v;
             if (g->flags & ORC_DEDUP) {
                 if (sorted_contains(a->v, old_n, v)) continue;          /* already in the graph */
                 if (a->n > old_n && a->v[a->n - 1] == v) continue;     /* already added (batch sorted) */
             }
-            a->v[a->n++] = v;
+            a->v[a->n] = v;
+            a->w[a->n] = k[t].w;
+            ++a->n;
             ++ins;
         }
-        qsort(a->v, a->n, sizeof(uint32_t), cmp_u32);
+        adj_sort(a);
         i = j;
     }
     free(k);
     g->num_edges += ins;
     if (inserted) *inserted = ins;
     if (rejected) *rejected = rej;
+}
+
+void orc_insert_edges(orc_graph *g, const uint32_t *src, const uint32_t *dst, uint64_t n,
+                      uint64_t *inserted, uint64_t *rejected) {
+    orc_insert_edges_weighted(g, src, dst, NULL, n, inserted, rejected);
 }
 
 /*
@@ -185,8 +236,12 @@ void orc_delete_edges(orc_graph *g, const uint32_t *src, const uint32_t *dst, ui
         orc_adj *a = &g->adj[u];
         uint64_t w = 0;
         for (uint64_t r = 0; r < a->n; ++r) {
-            if (sorted_contains(dset, nd, a->v[r])) ++del;
-            else a->v[w++] = a->v[r];
+            if (sorted_contains(dset, nd, a->v[r])) {
+                ++del;
+            } else {
+                a->w[w] = a->w[r];
+                a->v[w++] = a->v[r];
+            }
         }
         a->n = w;
         i = j;
@@ -242,8 +297,12 @@ uint32_t orc_delete_vertices(orc_graph *g, const uint32_t *ids, uint32_t k) {
         orc_adj *a = &g->adj[u];
         uint64_t w = 0;
         for (uint64_t r = 0; r < a->n; ++r) {
-            if (gone[a->v[r]]) g->num_edges -= 1;
-            else a->v[w++] = a->v[r];
+            if (gone[a->v[r]]) {
+                g->num_edges -= 1;
+            } else {
+                a->w[w] = a->w[r];
+                a->v[w++] = a->v[r];
+            }
         }
         a->n = w;
     }
@@ -279,6 +338,20 @@ uint64_t orc_neighbors(const orc_graph *g, const uint32_t *vids, uint32_t n, uin
         uint32_t u = vids[i];
         if (u < g->nv && g->alive[u] && g->adj[u].n)
             memcpy(nbrs + offsets[i], g->adj[u].v, g->adj[u].n * sizeof(uint32_t));
+    }
+    return tot;
+}
+
+/* neighbors with payloads: as orc_neighbors, plus wts[] aligned with nbrs
+ * (entries in (v, w) order). */
+uint64_t orc_neighbors_weighted(const orc_graph *g, const uint32_t *vids, uint32_t n, uint64_t *offsets,
+                                uint32_t *nbrs, uint32_t *wts, uint64_t cap) {
+    uint64_t tot = orc_neighbors(g, vids, n, offsets, nbrs, cap);
+    if (tot > cap || !nbrs || !wts) return tot;
+    for (uint32_t i = 0; i < n; ++i) {
+        uint32_t u = vids[i];
+        if (u < g->nv && g->alive[u] && g->adj[u].n)
+            memcpy(wts + offsets[i], g->adj[u].w, g->adj[u].n * sizeof(uint32_t));
     }
     return tot;
 }
