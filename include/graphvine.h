@@ -70,6 +70,11 @@ typedef enum gv_status {
  * ids are kept.  Library-owned pools only (pool_mem must be NULL); a failed
  * allocation keeps the old pool. */
 #define GV_GROW 2u
+/* Weighted entries: every stored entry carries a 32-bit payload (a weight,
+ * or any 32-bit value) that moves with it through deletes and compaction.
+ * The pool then holds 8*C + 12 bytes per block.  Excludes GV_DEDUP (which of
+ * several repeated pairs a set-semantics batch keeps is not defined). */
+#define GV_WEIGHTED 4u
 
 typedef struct gv_config {
     /* C, the number of edge entries per edge block (multiple of 4, 4..512).
@@ -77,7 +82,7 @@ typedef struct gv_config {
      * vertices with non-zero degree in the first edge batch, rounded up to a
      * multiple of 4; fixed from then on. */
     uint32_t block_capacity;
-    uint32_t flags;          /* GV_DEDUP | GV_GROW, or 0 */
+    uint32_t flags;          /* GV_DEDUP | GV_GROW | GV_WEIGHTED, or 0 */
     /* Bytes reserved for the edge-block pool: block storage (4*C bytes per
      * block), tree links (8 bytes per block) and the edge queue (4 bytes per
      * block).  0 = half of the free device memory ("Edge Queue": at least
@@ -300,6 +305,25 @@ const char *gv_profile_phase_name(uint32_t phase);
  */
 gv_status gv_insert_edges_segmented(gv_graph *g, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,
                                     const uint64_t *d_offsets, uint32_t nseg, uint64_t *d_counts, void *stream);
+
+/*
+ * gv_insert_edges_weighted -- gv_insert_edges on a graph created with
+ * GV_WEIGHTED, each pair with its 32-bit payload w[i] (device or host, n
+ * entries).  Plain gv_insert_edges (and gv_bulk_build) on such a graph store
+ * payload 0.  Deletes remove entries by (u, v) whatever their payload.  The
+ * paper's entries are plain destination ids; weighted entries are its
+ * "future work" extension (weighted edge entries).
+ * Errors: GV_ERR_INVALID_ARG on an unweighted graph or a graph set.
+ */
+gv_status gv_insert_edges_weighted(gv_graph *g, const uint32_t *src, const uint32_t *dst, const uint32_t *w,
+                                   uint64_t n, uint64_t *d_counts, void *stream);
+
+/*
+ * gv_neighbors_weighted -- gv_neighbors with the payloads: weights[k] belongs
+ * to nbrs[k] (same layout and capacity rules).  Weighted graphs only.
+ */
+gv_status gv_neighbors_weighted(gv_graph *g, const uint32_t *vids, uint32_t n, uint64_t *offsets, uint32_t *nbrs,
+                                uint32_t *weights, uint64_t nbr_capacity, uint64_t *total, void *stream);
 
 /*
  * gv_delete_edges_segmented -- one delete call for nseg consecutive batches

@@ -48,6 +48,7 @@ struct gv_graph {
     void *pool_alloc = nullptr;
     uint64_t pool_bytes = 0;
     uint32_t *data = nullptr, *links = nullptr, *queue = nullptr;
+    uint32_t *wdata = nullptr;  // per-slot payloads (GV_WEIGHTED), parallel to data
     // dictionary and vertex scratch
     uint4 *sent = nullptr;
     uint8_t *alive = nullptr;
@@ -160,6 +161,7 @@ GraphView view(const gv_graph *g) {
     v.sent = g->sent;
     v.alive = g->alive;
     v.data = g->data;
+    v.wdata = g->wdata;
     v.links = g->links;
     v.queue = g->queue;
     v.dev = g->dev;
@@ -383,7 +385,8 @@ gv_status setup_pool(gv_graph *g, uint32_t C, cudaStream_t s) {
         GV_CK(cudaMemGetInfo(&fr, &tot));
         bytes = fr / 2;  // "Edge Queue": at least half of the GPU memory
     }
-    const uint64_t per_block = 4ull * C + 8 + 4;
+    const bool weighted = (g->flags & GV_WEIGHTED) != 0;
+    const uint64_t per_block = 4ull * C * (weighted ? 2 : 1) + 8 + 4;
     unsigned long long P = bytes / per_block;
     // leave room for alignment padding between the three arrays
     while (P > 0 && P * per_block + 512 > bytes) --P;
@@ -406,6 +409,10 @@ gv_status setup_pool(gv_graph *g, uint32_t C, cudaStream_t s) {
     uint64_t off = 0;
     g->data = reinterpret_cast<uint32_t *>(base + off);
     off = align(off + P * C * 4ull);
+    if (weighted) {
+        g->wdata = reinterpret_cast<uint32_t *>(base + off);
+        off = align(off + P * C * 4ull);
+    }
     g->links = reinterpret_cast<uint32_t *>(base + off);
     off = align(off + P * 8ull);
     g->queue = reinterpret_cast<uint32_t *>(base + off);
@@ -470,7 +477,9 @@ gv_status grow_pool(gv_graph *g, unsigned long long P2, unsigned long long qf, u
                     cudaStream_t s) {
     auto align = [](uint64_t x) { return (x + 255) & ~255ull; };
     const uint64_t C = g->C;
-    const uint64_t off_links = align(P2 * C * 4ull);
+    const bool weighted = g->wdata != nullptr;
+    const uint64_t off_w = align(P2 * C * 4ull);
+    const uint64_t off_links = weighted ? align(off_w + P2 * C * 4ull) : off_w;
     const uint64_t off_queue = align(off_links + P2 * 8ull);
     const uint64_t bytes = off_queue + P2 * 4ull;
     void *p = nullptr;
@@ -480,10 +489,12 @@ gv_status grow_pool(gv_graph *g, unsigned long long P2, unsigned long long qf, u
     }
     char *base = static_cast<char *>(p);
     uint32_t *data2 = reinterpret_cast<uint32_t *>(base);
+    uint32_t *w2 = weighted ? reinterpret_cast<uint32_t *>(base + off_w) : nullptr;
     uint32_t *links2 = reinterpret_cast<uint32_t *>(base + off_links);
     uint32_t *queue2 = reinterpret_cast<uint32_t *>(base + off_queue);
     const unsigned long long nfree = qb - qf;
     GV_CK(cudaMemcpyAsync(data2, g->data, g->P * C * 4ull, cudaMemcpyDeviceToDevice, s));
+    if (weighted) GV_CK(cudaMemcpyAsync(w2, g->wdata, g->P * C * 4ull, cudaMemcpyDeviceToDevice, s));
     GV_CK(cudaMemcpyAsync(links2, g->links, g->P * 8ull, cudaMemcpyDeviceToDevice, s));
     GV_CK(gv::launch_grow_queue(g->queue, g->P, qf, nfree, queue2, P2, lcfg(g, s)));
     g->h_small[2] = 0;
@@ -494,6 +505,7 @@ gv_status grow_pool(gv_graph *g, unsigned long long P2, unsigned long long qf, u
     cudaFree(g->pool_alloc);
     g->pool_alloc = p;
     g->data = data2;
+    g->wdata = w2;
     g->links = links2;
     g->queue = queue2;
     g->P = P2;
@@ -532,15 +544,16 @@ gv_status maybe_grow(gv_graph *g, uint64_t n, cudaStream_t s) {
 }
 
 gv_status insert_impl(gv_graph *g, const uint32_t *src, const uint32_t *dst, uint64_t n,
-                      uint64_t *counts, cudaStream_t s) {
+                      uint64_t *counts, cudaStream_t s, const uint32_t *wts = nullptr) {
     if (!g) return GV_ERR_INVALID_ARG;
     if (n > kMaxBatch) return GV_ERR_INVALID_ARG;
     if (n > 0 && (!src || !dst)) return GV_ERR_INVALID_ARG;
     DeviceGuard dg(g->device);
     g->last_stream = s;
-    const void *dsrc = src, *ddst = dst;
+    const void *dsrc = src, *ddst = dst, *dwts = wts;
     GV_TRY(input_ptr(g, 0, src, n * 4, s, &dsrc));
     GV_TRY(input_ptr(g, 1, dst, n * 4, s, &ddst));
+    if (wts) GV_TRY(input_ptr(g, 3, wts, n * 4, s, &dwts));
     void *dcounts = counts;
     bool host_counts = false;
     if (counts) GV_TRY(output_ptr(g, 2, counts, 16, &dcounts, &host_counts));
@@ -573,7 +586,7 @@ gv_status insert_impl(gv_graph *g, const uint32_t *src, const uint32_t *dst, uin
             return insert_impl(g, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, counts, s);
         }
         GV_CK(gv::launch_insert_tail(v2, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, g->tcap,
-                                     (unsigned long long *)dcounts, lcfg(g, s)));
+                                     (unsigned long long *)dcounts, lcfg(g, s), (const uint32_t *)dwts));
     } else if ((g->flags & GV_DEDUP) && n > 0) {
         // set semantics: membership pass over the batch, mask of the pairs
         // that add a new value, then the plain insert of the masked batch
@@ -607,7 +620,7 @@ gv_status insert_impl(gv_graph *g, const uint32_t *src, const uint32_t *dst, uin
             GraphView v = view(g);
             GV_CK(gv::launch_count(gv::MODE_INSERT, v, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, lcfg(g, s)));
             GV_CK(gv::launch_insert_tail(v, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, g->tcap,
-                                         (unsigned long long *)dcounts, lcfg(g, s)));
+                                         (unsigned long long *)dcounts, lcfg(g, s), (const uint32_t *)dwts));
         }
     }
     if (host_counts) {
@@ -678,7 +691,7 @@ gv_status member_impl(gv_graph *g, int mode, const uint32_t *src, const uint32_t
 }
 
 gv_status neighbors_impl(gv_graph *g, const uint32_t *vids, uint32_t n, uint64_t *offsets, uint32_t *nbrs,
-                         uint64_t cap, uint64_t *total, cudaStream_t s, bool all) {
+                         uint64_t cap, uint64_t *total, cudaStream_t s, bool all, uint32_t *wts = nullptr) {
     if (!g || !total || !offsets) return GV_ERR_INVALID_ARG;
     if (n > 0 && !all && !vids) return GV_ERR_INVALID_ARG;
     DeviceGuard dg(g->device);
@@ -714,15 +727,17 @@ gv_status neighbors_impl(gv_graph *g, const uint32_t *vids, uint32_t n, uint64_t
     if (*total > cap) return GV_ERR_INVALID_ARG;
     if (*total == 0 || g->C == 0) return check_launch();
     if (!nbrs) return GV_ERR_INVALID_ARG;
-    void *dn = nbrs;
-    bool hn = false;
+    void *dn = nbrs, *dw = wts;
+    bool hn = false, hw = false;
     GV_TRY(output_ptr(g, 2, nbrs, (size_t)*total * 4, &dn, &hn));
+    if (wts) GV_TRY(output_ptr(g, 4, wts, (size_t)*total * 4, &dw, &hw));
     GV_TRY(ensure_touched(g, n));
     GV_TRY(ensure_items(g, item_bound(g, n)));
     v = view(g);
     GV_CK(gv::launch_neighbor_copy(v, (const uint32_t *)dv, n, (const unsigned long long *)doff, (uint32_t *)dn,
-                                   lcfg(g, s)));
+                                   lcfg(g, s), (uint32_t *)dw));
     if (hn) GV_CK(cudaMemcpyAsync(nbrs, dn, (size_t)*total * 4, cudaMemcpyDeviceToHost, s));
+    if (hw) GV_CK(cudaMemcpyAsync(wts, dw, (size_t)*total * 4, cudaMemcpyDeviceToHost, s));
     GV_CK(cudaStreamSynchronize(s));
     return check_launch();
 }
@@ -753,7 +768,10 @@ gv_status gv_create(const gv_config *cfg, uint32_t num_vertices, void *stream, g
     if (cfg) c = *cfg;
     if (c.block_capacity != 0 && (c.block_capacity < 4 || c.block_capacity > 512 || c.block_capacity % 4))
         return GV_ERR_INVALID_ARG;
-    if (c.flags & ~(GV_DEDUP | GV_GROW)) return GV_ERR_INVALID_ARG;
+    if (c.flags & ~(GV_DEDUP | GV_GROW | GV_WEIGHTED)) return GV_ERR_INVALID_ARG;
+    // which of several repeated (u, v) a set-semantics batch keeps is not
+    // defined, so their payloads would be: the two flags exclude each other
+    if ((c.flags & GV_DEDUP) && (c.flags & GV_WEIGHTED)) return GV_ERR_INVALID_ARG;
     if ((c.flags & GV_GROW) && c.pool_mem) return GV_ERR_INVALID_ARG;  // a caller-owned pool cannot grow
     if (c.pool_mem && c.pool_bytes == 0) return GV_ERR_INVALID_ARG;
     if (num_vertices > 0x7FFFFFFFu) return GV_ERR_INVALID_ARG;
@@ -1182,6 +1200,20 @@ gv_status gv_insert_edges_segmented(gv_graph *g, const uint32_t *d_src, const ui
     // an insert that ran out of pool blocks is a no-op: every segment {0, 0}
     GV_CK(gv::launch_segment_noop_check(v, g->dtmp, n, lcfg(g, s)));
     return check_launch();
+}
+
+gv_status gv_insert_edges_weighted(gv_graph *g, const uint32_t *src, const uint32_t *dst, const uint32_t *w,
+                                   uint64_t n, uint64_t *d_counts, void *stream) {
+    if (!g || (n > 0 && !w)) return GV_ERR_INVALID_ARG;
+    if (!(g->flags & GV_WEIGHTED) || g->set_G) return GV_ERR_INVALID_ARG;
+    return insert_impl(g, src, dst, n, d_counts, static_cast<cudaStream_t>(stream), w);
+}
+
+gv_status gv_neighbors_weighted(gv_graph *g, const uint32_t *vids, uint32_t n, uint64_t *offsets, uint32_t *nbrs,
+                                uint32_t *weights, uint64_t nbr_capacity, uint64_t *total, void *stream) {
+    if (!g || !(g->flags & GV_WEIGHTED)) return GV_ERR_INVALID_ARG;
+    return neighbors_impl(g, vids, n, offsets, nbrs, nbr_capacity, total, static_cast<cudaStream_t>(stream), false,
+                          weights);
 }
 
 gv_status gv_delete_edges_segmented(gv_graph *g, const uint32_t *d_src, const uint32_t *d_dst, uint64_t n,

@@ -55,6 +55,7 @@ struct GraphView {
     uint4 *sent;
     uint8_t *alive;
     uint32_t *data;
+    uint32_t *wdata;  // per-slot 32-bit payload (weights), parallel to data; NULL when unweighted
     uint32_t *links;
     uint32_t *queue;
     Dev *dev;

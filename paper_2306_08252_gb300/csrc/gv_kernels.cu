@@ -414,6 +414,7 @@ __global__ void __launch_bounds__(256) k_link_insert(GraphView g) {
 // recorded by the plan in the source's vinfo record.
 __global__ void __launch_bounds__(256) k_scatter_insert(GraphView g, const uint32_t *__restrict__ src,
                                                         const uint32_t *__restrict__ dst,
+                                                        const uint32_t *__restrict__ wts,
                                                         unsigned long long n) {
     if (g.dev->abort) return;
     const unsigned long long P = g.P;
@@ -457,8 +458,13 @@ __global__ void __launch_bounds__(256) k_scatter_insert(GraphView g, const uint3
 #pragma unroll
         for (int j = 0; j < PP; ++j) {
             if (r[j] != NIL) {
-                if (blk[j] < P) g.data[(size_t)blk[j] * C + ln[j]] = v[j];
-                else latch_status(g.dev, 5u /* GV_ERR_STATE */);
+                if (blk[j] < P) {
+                    const size_t slot = (size_t)blk[j] * C + ln[j];
+                    g.data[slot] = v[j];
+                    if (g.wdata) g.wdata[slot] = wts ? ld_stream(wts + i0 + j * stride) : 0u;
+                } else {
+                    latch_status(g.dev, 5u /* GV_ERR_STATE */);
+                }
             }
         }
     }
@@ -844,8 +850,14 @@ __global__ void __launch_bounds__(256, 4) k_mark(GraphView g) {
             const uint32_t x = q << 2;
             const uint32_t lb = divc(g.cmul, x);
             uint4 e4 = make_uint4(EMPTY_KEY, EMPTY_KEY, EMPTY_KEY, EMPTY_KEY);
-            if (qv) e4 = ld_stream4(reinterpret_cast<const uint4 *>(g.data + (size_t)sb_ids[lb] * C + (x - lb * C)));
+            const size_t qoff = (size_t)sb_ids[lb] * C + (x - lb * C);
+            if (qv) e4 = ld_stream4(reinterpret_cast<const uint4 *>(g.data + qoff));
             const uint32_t e[4] = {e4.x, e4.y, e4.z, e4.w};
+            // payloads of a weighted graph move with their entries: read in
+            // the same round as the entries, before any compaction write
+            uint4 w4 = make_uint4(0u, 0u, 0u, 0u);
+            if (MODE != MODE_QUERY && single && g.wdata && qv)
+                w4 = ld_stream4(reinterpret_cast<const uint4 *>(g.wdata + qoff));
             uint32_t vmask = 0;  // bit j: entry j is a stored entry of this item
 #pragma unroll
             for (int j = 0; j < 4; ++j)
@@ -925,12 +937,15 @@ __global__ void __launch_bounds__(256, 4) k_mark(GraphView g) {
                 // Stable in-place compaction: targets never pass the slot
                 // being read, and each round reads before it writes.
                 uint32_t w = running + ex;
+                const uint32_t ew[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     if ((surv >> j) & 1u) {
                         if (w != x + j) {
                             const uint32_t tq = divc(g.cmul, w);
-                            g.data[(size_t)sb_ids[tq] * C + (w - tq * C)] = e[j];
+                            const size_t to = (size_t)sb_ids[tq] * C + (w - tq * C);
+                            g.data[to] = e[j];
+                            if (g.wdata) g.wdata[to] = ew[j];
                         }
                         ++w;
                     }
@@ -1125,7 +1140,14 @@ __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
                         if (MODE != MODE_QUERY && !hit) {
                             if (w != x + jj) {
                                 const uint32_t wi = divc(g.cmul, w);
-                                g.data[(size_t)bl.get(wi) * C + (w - wi * C)] = e[jj];
+                                const size_t to = (size_t)bl.get(wi) * C + (w - wi * C);
+                                g.data[to] = e[jj];
+                                if (g.wdata) {
+                                    // one thread owns the adjacency and no write has reached
+                                    // slot x + jj yet: its payload is still in place
+                                    const uint32_t bi = divc(g.cmul, x);
+                                    g.wdata[to] = g.wdata[(size_t)bl.get(bi) * C + (x - bi * C) + jj];
+                                }
                             }
                             ++w;
                         }
@@ -1325,9 +1347,10 @@ __global__ void __launch_bounds__(256) k_move(GraphView g) {
                     if (pos != NIL) {
                         const uint32_t pq = divc(g.cmul, pos), xq = divc(g.cmul, x);
                         const uint32_t srcb = g.it_bid[(size_t)(item0 + cs) * IB + pq];
-                        const uint32_t val = g.data[(size_t)srcb * C + (pos - pq * C)];
-                        const uint32_t dstb = bids[xq];
-                        g.data[(size_t)dstb * C + (x - xq * C)] = val;
+                        const size_t from = (size_t)srcb * C + (pos - pq * C);
+                        const size_t to = (size_t)bids[xq] * C + (x - xq * C);
+                        g.data[to] = g.data[from];
+                        if (g.wdata) g.wdata[to] = g.wdata[from];
                     } else {
                         latch_status(dev, 5u /* GV_ERR_STATE */);
                     }
@@ -1713,7 +1736,7 @@ cudaError_t launch_count_rejects(const GraphView &g, const uint32_t *src, const 
 
 cudaError_t launch_insert_tail(const GraphView &g, const uint32_t *src, const uint32_t *dst,
                                unsigned long long n, unsigned long long tcap,
-                               unsigned long long *counts, const LaunchCfg &lc) {
+                               unsigned long long *counts, const LaunchCfg &lc, const uint32_t *wts) {
     const int cap = lc.num_sms * GRID_MULT;
     // a batch of n pairs touches at most n sources: small batches launch
     // small grids (grid-stride loops cover any count)
@@ -1729,7 +1752,7 @@ cudaError_t launch_insert_tail(const GraphView &g, const uint32_t *src, const ui
     }
     {
         PhaseScope ps(lc, PH_INS_SCATTER);
-        k_scatter_insert<<<grid_for(n, 256 * PP, cap), 256, 0, lc.stream>>>(g, src, dst, n);
+        k_scatter_insert<<<grid_for(n, 256 * PP, cap), 256, 0, lc.stream>>>(g, src, dst, wts, n);
     }
     {
         PhaseScope ps(lc, PH_INS_FINALIZE);

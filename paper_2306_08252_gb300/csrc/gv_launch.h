@@ -90,7 +90,8 @@ cudaError_t launch_count_rejects(const GraphView &g, const uint32_t *src, const 
 // Insert: plan (block demand, pop offsets), link (CBT), scatter (slots), finalize.
 cudaError_t launch_insert_tail(const GraphView &g, const uint32_t *src, const uint32_t *dst,
                                unsigned long long n, unsigned long long tcap,
-                               unsigned long long *counts, const LaunchCfg &lc);
+                               unsigned long long *counts, const LaunchCfg &lc,
+                               const uint32_t *wts = nullptr);  // per-pair payloads of a weighted graph
 // Delete / query: plan, arena init, scatter into membership sets, mark,
 // (delete) vscan + move, finalize; (query) result gather.
 cudaError_t launch_member_tail(int mode, const GraphView &g, const uint32_t *src,
@@ -113,7 +114,8 @@ cudaError_t launch_neighbor_offsets(const GraphView &g, const uint32_t *vids, ui
                                     const LaunchCfg &lc);
 cudaError_t launch_neighbor_copy(const GraphView &g, const uint32_t *vids, uint32_t n,
                                  const unsigned long long *offsets, uint32_t *nbrs,
-                                 const LaunchCfg &lc);
+                                 const LaunchCfg &lc,
+                                 uint32_t *wts = nullptr);
 cudaError_t launch_degrees(const GraphView &g, uint32_t *deg, uint8_t *alive,
                            const LaunchCfg &lc);
 cudaError_t launch_iota(uint32_t *out, uint32_t first, uint32_t k, const LaunchCfg &lc);

@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(256) k_nbr_plan(GraphView g, const uint32_t *_
 
 // One warp per item: copy the item's slots in heap (storage) order.
 __global__ void __launch_bounds__(256) k_nbr_copy(GraphView g, const unsigned long long *__restrict__ offsets,
-                                                  uint32_t *__restrict__ nbrs) {
+                                                  uint32_t *__restrict__ nbrs, uint32_t *__restrict__ wts) {
     const uint32_t nitems = g.dev->n_items;
     const uint32_t lane = lane_id();
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -184,17 +184,28 @@ __global__ void __launch_bounds__(256) k_nbr_copy(GraphView g, const unsigned lo
         const uint32_t nslots = min(nblk * C, b.x - sbase);
         const uint32_t nquads = (nslots + 3) >> 2;
         uint32_t *out = nbrs + offsets[itm.x] + sbase;
+        uint32_t *wout = wts ? wts + offsets[itm.x] + sbase : nullptr;
         for (uint32_t q0 = 0; q0 < nquads; q0 += 32) {
             const uint32_t q = q0 + lane;
             const uint32_t x = q << 2;
             const uint32_t lb = divc(g.cmul, x);
             const uint32_t myb = __shfl_sync(FULL, bid, lb & 31u);
             if (q < nquads) {
-                const uint4 e4 = *reinterpret_cast<const uint4 *>(g.data + (size_t)myb * C + (x - lb * C));
+                const size_t qoff = (size_t)myb * C + (x - lb * C);
+                const uint4 e4 = *reinterpret_cast<const uint4 *>(g.data + qoff);
                 const uint32_t e[4] = {e4.x, e4.y, e4.z, e4.w};
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
                     if (x + j < nslots) out[x + j] = e[j];
+                if (wout) {
+                    // payloads of a weighted graph (0 for an unweighted one)
+                    uint4 w4 = make_uint4(0u, 0u, 0u, 0u);
+                    if (g.wdata) w4 = *reinterpret_cast<const uint4 *>(g.wdata + qoff);
+                    const uint32_t w[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (x + j < nslots) wout[x + j] = w[j];
+                }
             }
         }
     }
@@ -353,11 +364,12 @@ cudaError_t launch_neighbor_offsets(const GraphView &g, const uint32_t *vids, ui
 }
 
 cudaError_t launch_neighbor_copy(const GraphView &g, const uint32_t *vids, uint32_t n,
-                                 const unsigned long long *offsets, uint32_t *nbrs, const LaunchCfg &lc) {
+                                 const unsigned long long *offsets, uint32_t *nbrs, const LaunchCfg &lc,
+                                 uint32_t *wts) {
     if (n == 0) return cudaSuccess;
     PhaseScope ps(lc, PH_NEIGHBORS);
     k_nbr_plan<<<grid_for(n, 256, lc.num_sms * 8), 256, 0, lc.stream>>>(g, vids, n);
-    k_nbr_copy<<<lc.num_sms * 8, 256, 0, lc.stream>>>(g, offsets, nbrs);
+    k_nbr_copy<<<lc.num_sms * 8, 256, 0, lc.stream>>>(g, offsets, nbrs, wts);
     k_clear_items<<<1, 32, 0, lc.stream>>>(g);
     return cudaGetLastError();
 }

@@ -24,6 +24,7 @@ GV_ERR_TIMEOUT = 4
 GV_ERR_STATE = 5
 GV_DEDUP = 1
 GV_GROW = 2
+GV_WEIGHTED = 4
 
 c_u32, c_u64, c_vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p
 
@@ -91,6 +92,9 @@ SIGNATURES = {
     "gv_degree_offsets_noalloc": ([c_vp, c_vp, c_u32, c_vp, c_vp], ctypes.c_int),
     "gv_insert_edges_segmented": ([c_vp, c_vp, c_vp, c_u64, c_vp, c_u32, c_vp, c_vp], ctypes.c_int),
     "gv_delete_edges_segmented": ([c_vp, c_vp, c_vp, c_u64, c_vp, c_u32, c_vp, c_vp], ctypes.c_int),
+    "gv_insert_edges_weighted": ([c_vp, c_vp, c_vp, c_vp, c_u64, c_vp, c_vp], ctypes.c_int),
+    "gv_neighbors_weighted": ([c_vp, c_vp, c_u32, c_vp, c_vp, c_vp, c_u64, ctypes.POINTER(c_u64), c_vp],
+                              ctypes.c_int),
     "gv_set_create": ([ctypes.POINTER(gv_config), c_u32, c_vp, c_vp, ctypes.POINTER(c_vp)], ctypes.c_int),
     "gv_set_insert_edges": ([c_vp, c_vp, c_vp, c_u64, c_vp, c_vp, c_vp], ctypes.c_int),
     "gv_set_delete_edges": ([c_vp, c_vp, c_vp, c_u64, c_vp, c_vp, c_vp], ctypes.c_int),
@@ -271,6 +275,21 @@ def gv_degree_offsets_noalloc(g, d_vids, d_offsets, stream=None):
 def gv_insert_edges_segmented(g, d_src, d_dst, d_offsets, nseg, d_counts, stream=None):
     return check(load().gv_insert_edges_segmented(g, ptr(d_src), ptr(d_dst), _len(d_src), ptr(d_offsets), nseg,
                                                   ptr(d_counts), stream), "gv_insert_edges_segmented")
+
+
+def gv_insert_edges_weighted(g, src, dst, w, counts=None, stream=None):
+    _check_u32(src, "src")
+    _check_u32(dst, "dst")
+    _check_u32(w, "w")
+    return check(load().gv_insert_edges_weighted(g, ptr(src), ptr(dst), ptr(w), _len(src), ptr(counts), stream),
+                 "gv_insert_edges_weighted")
+
+
+def gv_neighbors_weighted(g, vids, offsets, nbrs, weights, nbr_capacity, stream=None):
+    total = c_u64(0)
+    code = load().gv_neighbors_weighted(g, ptr(vids), _len(vids), ptr(offsets), ptr(nbrs), ptr(weights),
+                                        nbr_capacity, ctypes.byref(total), stream)
+    return code, total.value
 
 
 def gv_delete_edges_segmented(g, d_src, d_dst, d_offsets, nseg, d_counts, stream=None):
@@ -454,6 +473,20 @@ class Graph:
         code, total = gv_neighbors(self.handle, vids, off, nb, nb.size, self._s())
         check(code, "gv_neighbors")
         return off, nb[:total]
+
+    def insert_edges_weighted(self, src, dst, w, counts=None):
+        return gv_insert_edges_weighted(self.handle, src, dst, w, counts, self._s())
+
+    def neighbors_weighted(self, vids):
+        """(offsets, nbrs, weights) of the listed vertices, storage order."""
+        vids = np.ascontiguousarray(vids, dtype=np.uint32)
+        off = np.zeros(vids.size + 1, dtype=np.uint64)
+        code, total = gv_neighbors_weighted(self.handle, vids, off, None, None, 0, self._s())
+        nb = np.zeros(max(total, 1), dtype=np.uint32)
+        wt = np.zeros(max(total, 1), dtype=np.uint32)
+        code, total = gv_neighbors_weighted(self.handle, vids, off, nb, wt, nb.size, self._s())
+        check(code, "gv_neighbors_weighted")
+        return off, nb[:total], wt[:total]
 
     def bfs(self, source, dist=None):
         """(dist, levels): uint32 distances (0xFFFFFFFF = unreached); `dist`
