@@ -749,6 +749,24 @@ def run_rows(args):
         12 * BATCH + 4 * int(degd.astype(np.int64)[srcs].sum()) + 32 * srcs.size)
     gd.close()
 
+    # f3 (weighted entries): insert the 10M batch with payloads and delete it
+    # again on a GV_WEIGHTED graph (payloads move with every compaction)
+    gw = gv.Graph(nv, block_capacity=C, pool_bytes=POOL_BYTES, flags=gv.GV_WEIGHTED)
+    gw.reserve(max(BATCH, BASE_EDGES))
+    gw.bulk_build(d_bs, d_bd, cnt)
+    d_w = t(np.arange(BATCH, dtype=np.uint32))
+    ms_i = timed(lambda: gw.insert_edges_weighted(d_s, d_d, d_w, cnt), post=lambda: gw.delete_edges(d_s, d_d, cnt))
+    gw.insert_edges_weighted(d_s, d_d, d_w, cnt)
+    torch.cuda.synchronize()
+    degw, _ = gw.degrees()
+    gw.delete_edges(d_s, d_d, cnt)
+    ms_d = timed(lambda: gw.delete_edges(d_s, d_d, cnt), pre=lambda: gw.insert_edges_weighted(d_s, d_d, d_w, cnt))
+    srcs = np.unique(us)
+    row("f3-weighted-insert", f"weighted insert of {BATCH} pairs", BATCH, "edges", ms_i, 16 * BATCH + 32 * srcs.size)
+    row("f3-weighted-delete", f"delete of the {BATCH} weighted pairs", BATCH, "edges", ms_d,
+        8 * BATCH + 8 * int(degw.astype(np.int64)[srcs].sum()) + 32 * srcs.size)
+    gw.close()
+
     # f4: bulk build into a pool of 1/8 of the blocks it needs, grown by
     # GV_GROW in 25% steps (allocation and copies inside the timed call)
     need_blocks = int(((np.bincount(bs, minlength=nv) + C - 1) // C).sum())
