@@ -387,10 +387,20 @@ gv_status setup_pool(gv_graph *g, uint32_t C, cudaStream_t s) {
     }
     const bool weighted = (g->flags & GV_WEIGHTED) != 0;
     const uint64_t per_block = 4ull * C * (weighted ? 2 : 1) + 8 + 4;
+    // End of the laid-out arrays for P blocks: slots, payloads (weighted
+    // graphs), links and queue, each starting on a 256-byte boundary.  The
+    // largest P whose layout fits in `bytes` is taken (every array must lie
+    // inside the allocation: the queue is written in full below).
+    auto layout_end = [&](unsigned long long P) {
+        auto al = [](uint64_t x) { return (x + 255) & ~255ull; };
+        uint64_t off = al(P * C * 4ull);
+        if (weighted) off = al(off + P * C * 4ull);
+        off = al(off + P * 8ull);
+        return off + P * 4ull;
+    };
     unsigned long long P = bytes / per_block;
-    // leave room for alignment padding between the three arrays
-    while (P > 0 && P * per_block + 512 > bytes) --P;
     if (P > 0xFFFFFFFEull) P = 0xFFFFFFFEull;
+    while (P > 0 && layout_end(P) > bytes) --P;
     if (P == 0) return GV_ERR_INVALID_ARG;
     char *base = nullptr;
     if (g->pool_mem_cfg) {
@@ -416,6 +426,7 @@ gv_status setup_pool(gv_graph *g, uint32_t C, cudaStream_t s) {
     g->links = reinterpret_cast<uint32_t *>(base + off);
     off = align(off + P * 8ull);
     g->queue = reinterpret_cast<uint32_t *>(base + off);
+    if (off + P * 4ull > bytes) return GV_ERR_STATE;  // cannot happen: P was fitted to this layout
     g->P = P;
     g->pool_bytes = bytes;
     GV_CK(gv::launch_init_queue(g->queue, P, lcfg(g, s)));
