@@ -124,3 +124,29 @@ def test_segmented_delete_equals_deletes_in_order(C):
         p.check()
     finally:
         p.close()
+
+
+def test_segmented_insert_pool_exhaustion_is_a_noop():
+    # a merged insert that does not fit the pool changes nothing and reports
+    # {0, 0} for every request; the exhaustion is latched for gv_sync
+    import torch
+    import paper_2306_08252_gb300 as gv
+    from gpu_util import Pair
+    nv, C = 2000, 8
+    p = Pair(nv, C=C, pool_bytes=600 * (4 * C + 12))
+    try:
+        bs, bd = W.uniform_pairs(81, 0, 1000, nv)
+        p.bulk(bs, bd)
+        p.check()
+        segs = [W.uniform_pairs(81, 1 + k, 3000, nv) for k in range(3)]
+        off = np.zeros(4, dtype=np.int64)
+        off[1:] = np.cumsum([a.size for a, _ in segs])
+        cnt = torch.full((6,), 7, dtype=torch.int64, device="cuda")
+        gv.gv_insert_edges_segmented(p.g.handle, dev_u32(np.concatenate([a for a, _ in segs])),
+                                     dev_u32(np.concatenate([b for _, b in segs])), torch.from_numpy(off).cuda(),
+                                     3, cnt)
+        assert cnt.cpu().tolist() == [0] * 6
+        assert gv.gv_sync(p.g.handle) == gv.GV_ERR_OUT_OF_MEMORY
+        p.check()  # unchanged: still equal to the oracle, which saw only the bulk build
+    finally:
+        p.close()
