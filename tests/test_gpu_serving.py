@@ -135,7 +135,7 @@ def test_segmented_insert_pool_exhaustion_is_a_noop():
     nv, C = 2000, 8
     p = Pair(nv, C=C, pool_bytes=600 * (4 * C + 12))
     try:
-        bs, bd = W.uniform_pairs(81, 0, 1000, nv)
+        bs, bd = W.uniform_pairs(81, 0, 300, nv)  # ~290 sources: about half of the ~600 blocks
         p.bulk(bs, bd)
         p.check()
         segs = [W.uniform_pairs(81, 1 + k, 3000, nv) for k in range(3)]
