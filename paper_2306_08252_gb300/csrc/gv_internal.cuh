@@ -328,38 +328,6 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
     return r;  // valid in thread 0
 }
 
-// Bitonic sort of 32 (key, payload) pairs held one per lane, ascending keys.
-__device__ __forceinline__ void warp_sort_pairs(uint32_t &key, uint32_t &pay) {
-    uint32_t lane = lane_id();
-#pragma unroll
-    for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            uint32_t ok = __shfl_xor_sync(FULL, key, j);
-            uint32_t op = __shfl_xor_sync(FULL, pay, j);
-            bool up = (lane & k) == 0;
-            bool lower = (lane & j) == 0;
-            bool take = lower ? (up ? ok < key : ok > key) : (up ? ok > key : ok < key);
-            if (take) {
-                key = ok;
-                pay = op;
-            }
-        }
-    }
-}
-
-// Branchless lower bound among 32 ascending keys held one per lane: the
-// returned position p satisfies key[p-1] < e <= key[p] whenever e <= key[31];
-// the caller tests key[p] == e for membership.  All lanes must call.
-__device__ __forceinline__ uint32_t warp_lower_bound(uint32_t skey, uint32_t e) {
-    uint32_t pos = 0;
-#pragma unroll
-    for (uint32_t step = 16; step >= 1; step >>= 1) {
-        uint32_t probe = __shfl_sync(FULL, skey, pos + step - 1);
-        if (probe < e) pos += step;
-    }
-    return pos;
-}
 
 // Open-addressing hash set in a global arena region of `hsize` (power of two)
 // words: insert, returning the slot of `v`.

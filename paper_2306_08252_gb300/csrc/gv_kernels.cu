@@ -412,6 +412,7 @@ __global__ void __launch_bounds__(256) k_link_insert(GraphView g) {
 // Pair i of source u with rank r goes to slot deg(u) + r: the free slots of
 // the last block first, then the new blocks popped for u at queue offset
 // recorded by the plan in the source's vinfo record.
+template <bool WEIGHTED>
 __global__ void __launch_bounds__(256) k_scatter_insert(GraphView g, const uint32_t *__restrict__ src,
                                                         const uint32_t *__restrict__ dst,
                                                         const uint32_t *__restrict__ wts,
@@ -461,7 +462,7 @@ __global__ void __launch_bounds__(256) k_scatter_insert(GraphView g, const uint3
                 if (blk[j] < P) {
                     const size_t slot = (size_t)blk[j] * C + ln[j];
                     g.data[slot] = v[j];
-                    if (g.wdata) g.wdata[slot] = wts ? ld_stream(wts + i0 + j * stride) : 0u;
+                    if (WEIGHTED) g.wdata[slot] = wts ? ld_stream(wts + i0 + j * stride) : 0u;
                 } else {
                     latch_status(g.dev, 5u /* GV_ERR_STATE */);
                 }
@@ -761,7 +762,7 @@ __global__ void __launch_bounds__(256) k_scatter_member(GraphView g, const uint3
 }
 
 // One warp per work item (see the file comment).
-template <int MODE>
+template <int MODE, bool WEIGHTED = false>
 __global__ void __launch_bounds__(256, 4) k_mark(GraphView g) {
     Dev *dev = g.dev;
     const uint32_t nlo = dev->n_items, nhi = dev->n_mitems;
@@ -856,7 +857,7 @@ __global__ void __launch_bounds__(256, 4) k_mark(GraphView g) {
             // payloads of a weighted graph move with their entries: read in
             // the same round as the entries, before any compaction write
             uint4 w4 = make_uint4(0u, 0u, 0u, 0u);
-            if (MODE != MODE_QUERY && single && g.wdata && qv)
+            if (WEIGHTED && MODE != MODE_QUERY && single && qv)
                 w4 = ld_stream4(reinterpret_cast<const uint4 *>(g.wdata + qoff));
             uint32_t vmask = 0;  // bit j: entry j is a stored entry of this item
 #pragma unroll
@@ -945,7 +946,7 @@ __global__ void __launch_bounds__(256, 4) k_mark(GraphView g) {
                             const uint32_t tq = divc(g.cmul, w);
                             const size_t to = (size_t)sb_ids[tq] * C + (w - tq * C);
                             g.data[to] = e[j];
-                            if (g.wdata) g.wdata[to] = ew[j];
+                            if (WEIGHTED) g.wdata[to] = ew[j];
                         }
                         ++w;
                     }
@@ -1752,7 +1753,8 @@ cudaError_t launch_insert_tail(const GraphView &g, const uint32_t *src, const ui
     }
     {
         PhaseScope ps(lc, PH_INS_SCATTER);
-        k_scatter_insert<<<grid_for(n, 256 * PP, cap), 256, 0, lc.stream>>>(g, src, dst, wts, n);
+        if (g.wdata) k_scatter_insert<true><<<grid_for(n, 256 * PP, cap), 256, 0, lc.stream>>>(g, src, dst, wts, n);
+        else k_scatter_insert<false><<<grid_for(n, 256 * PP, cap), 256, 0, lc.stream>>>(g, src, dst, wts, n);
     }
     {
         PhaseScope ps(lc, PH_INS_FINALIZE);
@@ -1800,7 +1802,8 @@ static void member_tail(const GraphView &g0, const uint32_t *src, const uint32_t
     }
     {
         PhaseScope ps(lc, del ? PH_DEL_MARK : PH_QRY_MARK);
-        k_mark<MODE><<<gi, 256, 0, lc.stream>>>(g);
+        if (MODE != MODE_QUERY && g.wdata) k_mark<MODE, true><<<gi, 256, 0, lc.stream>>>(g);
+        else k_mark<MODE><<<gi, 256, 0, lc.stream>>>(g);
     }
     if (!fork) {
         PhaseScope ps(lc, del ? PH_DEL_MARK_TINY : PH_QRY_MARK_TINY);
@@ -1856,7 +1859,8 @@ cudaError_t launch_vertex_delete(const GraphView &g, const uint32_t *ids, uint32
         k_mark_tiny<MODE_VDEL><<<grid_for(g.nv, 256, cap), 256, 0, lc.side>>>(g);
         cudaEventRecord(lc.join, lc.side);
     }
-    k_mark<MODE_VDEL><<<gi, 256, 0, lc.stream>>>(g);
+    if (g.wdata) k_mark<MODE_VDEL, true><<<gi, 256, 0, lc.stream>>>(g);
+    else k_mark<MODE_VDEL><<<gi, 256, 0, lc.stream>>>(g);
     if (!fork) k_mark_tiny<MODE_VDEL><<<grid_for(g.nv, 256, cap), 256, 0, lc.stream>>>(g);
     k_vscan<MODE_VDEL><<<grid_for(g.nv, 8, cap), 256, 0, lc.stream>>>(g);
     k_move<MODE_VDEL><<<gi, 256, 0, lc.stream>>>(g);
