@@ -2,7 +2,8 @@
 // and PageRank.  The paper names analytics on the dynamic structure as
 // future work ("Conclusion and future work"); the definitions are the
 // textbook ones (level-synchronous BFS; PageRank power iteration with
-// damping, dangling mass spread over all live vertices).
+// damping, dangling mass spread over all live vertices, gathered over an
+// incoming-edge CSR built once per call).
 //
 // Both read adjacencies the way the delete and query pipelines do: work
 // items of up to AIB blocks of one vertex, one warp per item, block ids by
@@ -211,9 +212,12 @@ __global__ void __launch_bounds__(256) k_pr_contrib(GraphView g, const double *_
     }
 }
 
-// Every stored entry (u, v) adds u's share to v's accumulator.
-__global__ void __launch_bounds__(256) k_pr_push(GraphView g, const uint2 *__restrict__ items, const uint32_t *nitems,
-                                                 uint32_t aib, const double *__restrict__ c, double *acc) {
+// Incoming-edge CSR of the stored graph, built once per PageRank call so
+// that every iteration gathers (no atomic per entry): in-degrees by one
+// atomic per stored entry, an exclusive scan into offsets, then each entry
+// (u, v) placed in v's segment at an atomically claimed position.
+__global__ void __launch_bounds__(256) k_pr_indeg(GraphView g, const uint2 *__restrict__ items,
+                                                  const uint32_t *nitems, uint32_t aib, uint32_t *indeg) {
     __shared__ uint32_t s_bid[8][32];
     const uint32_t n = *nitems;
     const uint32_t lane = lane_id();
@@ -222,19 +226,146 @@ __global__ void __launch_bounds__(256) k_pr_push(GraphView g, const uint2 *__res
     const uint32_t nv = g.nv;
     for (uint32_t it = warp; it < n; it += nwarps) {
         const uint2 itm = items[it];
-        const double cu = c[itm.x];
         bool bad = false;
         const bool ok = for_item_entries(g, itm.x, itm.y, aib, s_bid[threadIdx.x >> 5], [&](uint4 e4, uint32_t vm) {
             const uint32_t e[4] = {e4.x, e4.y, e4.z, e4.w};
 #pragma unroll
             for (uint32_t j = 0; j < 4; ++j) {
                 if ((vm >> j) & 1u) {
-                    if (e[j] < nv) atomicAdd(acc + e[j], cu);
+                    if (e[j] < nv) atomicAdd(indeg + e[j], 1u);
                     else bad = true;
                 }
             }
         });
         if ((!ok || bad) && lane == 0) latch_status(g.dev, 5u /* GV_ERR_STATE */);
+    }
+}
+
+constexpr uint32_t PR_CHUNK = 1024;  // entries per scan chunk (256 threads x 4)
+
+// Chunk sums of x[0..n).
+__global__ void __launch_bounds__(256) k_pr_chunk_sums(const uint32_t *__restrict__ x, uint32_t n,
+                                                       unsigned long long *part) {
+    const uint32_t base = blockIdx.x * PR_CHUNK;
+    unsigned long long t = 0;
+    for (uint32_t k = threadIdx.x; k < PR_CHUNK; k += blockDim.x)
+        if (base + k < n) t += x[base + k];
+    t = block_sum_u64(t);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// Exclusive scan of the chunk sums in place; part[nchunks] = total.  One
+// block; each thread scans a contiguous run of chunks.
+__global__ void __launch_bounds__(1024) k_pr_scan_parts(unsigned long long *part, uint32_t nchunks) {
+    __shared__ unsigned long long s_run[1024];
+    const uint32_t per = (nchunks + blockDim.x - 1) / blockDim.x;
+    const uint32_t lo = threadIdx.x * per, hi = min(nchunks, lo + per);
+    unsigned long long run = 0;
+    for (uint32_t c = lo; c < hi; ++c) run += part[c];
+    s_run[threadIdx.x] = run;
+    __syncthreads();
+    if (threadIdx.x == 0) {  // scan of the per-thread runs (1024 values)
+        unsigned long long acc = 0;
+        for (uint32_t i = 0; i < blockDim.x; ++i) {
+            const unsigned long long v = s_run[i];
+            s_run[i] = acc;
+            acc += v;
+        }
+        part[nchunks] = acc;
+    }
+    __syncthreads();
+    unsigned long long acc = s_run[threadIdx.x];
+    for (uint32_t c = lo; c < hi; ++c) {
+        const unsigned long long v = part[c];
+        part[c] = acc;
+        acc += v;
+    }
+}
+
+// off[i] = exclusive prefix sum of x at i (i < n); off[n] = total.
+__global__ void __launch_bounds__(256) k_pr_scan_apply(const uint32_t *__restrict__ x, uint32_t n,
+                                                       const unsigned long long *__restrict__ part,
+                                                       uint32_t nchunks, unsigned long long *off) {
+    const uint32_t base = blockIdx.x * PR_CHUNK;
+    uint32_t v[4];
+    uint32_t loc = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t k = base + threadIdx.x * 4 + j;
+        v[j] = k < n ? x[k] : 0u;
+        loc += v[j];
+    }
+    uint32_t tot;
+    const uint32_t ex = block_excl_scan(loc, &tot);
+    unsigned long long run = part[blockIdx.x] + ex;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t k = base + threadIdx.x * 4 + j;
+        if (k < n) off[k] = run;
+        run += v[j];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) off[n] = part[nchunks];
+}
+
+__global__ void __launch_bounds__(256) k_pr_fill(GraphView g, const uint2 *__restrict__ items,
+                                                 const uint32_t *nitems, uint32_t aib,
+                                                 const unsigned long long *__restrict__ off, uint32_t *cursor,
+                                                 uint32_t *in_src, uint32_t *in_dst, unsigned long long ecap) {
+    __shared__ uint32_t s_bid[8][32];
+    const uint32_t n = *nitems;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t nv = g.nv;
+    for (uint32_t it = warp; it < n; it += nwarps) {
+        const uint2 itm = items[it];
+        const uint32_t u = itm.x;
+        for_item_entries(g, u, itm.y, aib, s_bid[threadIdx.x >> 5], [&](uint4 e4, uint32_t vm) {
+            const uint32_t e[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+            for (uint32_t j = 0; j < 4; ++j) {
+                if (((vm >> j) & 1u) && e[j] < nv) {
+                    const unsigned long long pos = off[e[j]] + atomicAdd(cursor + e[j], 1u);
+                    if (pos < ecap) {  // the entry count read by the host bounds the arrays
+                        in_src[pos] = u;
+                        in_dst[pos] = e[j];
+                    } else {
+                        latch_status(g.dev, 5u /* GV_ERR_STATE */);
+                    }
+                }
+            }
+        });
+    }
+}
+
+// acc(v) += sum of c(u) over v's incoming entries.  Entries are taken 32 at
+// a time by a warp in CSR order, so equal destinations sit in consecutive
+// lanes: a segmented sum by shuffles leaves each segment's total in its
+// first lane, which adds it with one atomic (one or a few per warp round
+// instead of one per entry).
+__global__ void __launch_bounds__(256) k_pr_gather(const uint32_t *__restrict__ in_src,
+                                                   const uint32_t *__restrict__ in_dst,
+                                                   const unsigned long long *total, const double *__restrict__ c,
+                                                   double *acc, unsigned long long ecap) {
+    const unsigned long long E = min(*total, ecap);
+    const uint32_t lane = lane_id();
+    const unsigned long long warp = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    for (unsigned long long k0 = warp * 32; k0 < E; k0 += nwarps * 32) {
+        const unsigned long long k = k0 + lane;
+        uint32_t key = NIL;
+        double s = 0.0;
+        if (k < E) {
+            key = ld_stream(in_dst + k);
+            s = c[ld_stream(in_src + k)];
+        }
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const double o = __shfl_down_sync(FULL, s, d);
+            const uint32_t ok = __shfl_down_sync(FULL, key, d);
+            if (lane + d < 32 && ok == key) s += o;
+        }
+        const uint32_t prev = __shfl_up_sync(FULL, key, 1);
+        if (key != NIL && (lane == 0 || prev != key)) atomicAdd(acc + key, s);
     }
 }
 
@@ -252,20 +383,31 @@ __global__ void __launch_bounds__(256) k_pr_update(GraphView g, double *r, const
 
 cudaError_t launch_pagerank(const GraphView &g, uint32_t aib, uint32_t iterations, double damping, double *r,
                             double *c, double *acc, double *scal, unsigned long long *N, uint2 *items,
-                            uint32_t *nitems, const LaunchCfg &lc) {
+                            uint32_t *nitems, uint32_t *cursor, unsigned long long *in_off,
+                            unsigned long long *part, uint32_t *in_src, uint32_t *in_dst, unsigned long long ecap,
+                            const LaunchCfg &lc) {
     PhaseScope ps(lc, PH_ANALYTICS);
     const int grid = lc.num_sms * GRID_MULT;
     const int gnv = grid_for(g.nv ? g.nv : 1, 256, grid);
+    const uint32_t nchunks = (g.nv + PR_CHUNK - 1) / PR_CHUNK;
     cudaMemsetAsync(N, 0, 8, lc.stream);
     cudaMemsetAsync(nitems, 0, 4, lc.stream);
     cudaMemsetAsync(scal, 0, 2 * sizeof(double), lc.stream);
+    cudaMemsetAsync(cursor, 0, (size_t)g.nv * 4, lc.stream);
     k_pr_count<<<gnv, 256, 0, lc.stream>>>(g, N);
     k_pr_start<<<gnv, 256, 0, lc.stream>>>(g, r, N);
     k_an_items<<<grid, 256, 0, lc.stream>>>(g, nullptr, nullptr, aib, items, nitems);
+    // incoming CSR: in-degrees -> offsets -> entries placed per destination
+    k_pr_indeg<<<grid, 256, 0, lc.stream>>>(g, items, nitems, aib, cursor);
+    k_pr_chunk_sums<<<nchunks, 256, 0, lc.stream>>>(cursor, g.nv, part);
+    k_pr_scan_parts<<<1, 1024, 0, lc.stream>>>(part, nchunks);
+    k_pr_scan_apply<<<nchunks, 256, 0, lc.stream>>>(cursor, g.nv, part, nchunks, in_off);
+    cudaMemsetAsync(cursor, 0, (size_t)g.nv * 4, lc.stream);
+    k_pr_fill<<<grid, 256, 0, lc.stream>>>(g, items, nitems, aib, in_off, cursor, in_src, in_dst, ecap);
     for (uint32_t it = 0; it < iterations; ++it) {
         const uint32_t slot = it & 1u;
         k_pr_contrib<<<gnv, 256, 0, lc.stream>>>(g, r, c, acc, scal + slot);
-        k_pr_push<<<grid, 256, 0, lc.stream>>>(g, items, nitems, aib, c, acc);
+        k_pr_gather<<<grid, 256, 0, lc.stream>>>(in_src, in_dst, in_off + g.nv, c, acc, ecap);
         k_pr_update<<<gnv, 256, 0, lc.stream>>>(g, r, acc, scal, slot, N, damping);
     }
     return cudaGetLastError();

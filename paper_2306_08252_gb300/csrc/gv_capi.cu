@@ -99,6 +99,11 @@ struct gv_graph {
     uint32_t *an_cur = nullptr, *an_next = nullptr, *an_ctr = nullptr;
     double *pr_c = nullptr, *pr_acc = nullptr, *pr_scal = nullptr;
     unsigned long long *pr_n = nullptr;
+    // PageRank's incoming-edge CSR: per-vertex cursor, offsets, chunk sums,
+    // source and destination of every entry
+    unsigned long long pr_vcap = 0, pr_ecap = 0;
+    uint32_t *pr_cursor = nullptr, *pr_src = nullptr, *pr_dst = nullptr;
+    unsigned long long *pr_off = nullptr, *pr_part = nullptr;
     // graph set: members' vertex ranges (set_G == 0 for a plain graph)
     uint32_t set_G = 0;
     uint32_t *set_vbase = nullptr;          // device, G+1
@@ -858,6 +863,7 @@ gv_status gv_destroy(gv_graph *g) {
         dfree(g->pflag); dfree(g->dsrc2); dfree(g->dtmp);
         dfree(g->an_items); dfree(g->an_cur); dfree(g->an_next); dfree(g->an_ctr);
         dfree(g->pr_c); dfree(g->pr_acc); dfree(g->pr_scal); dfree(g->pr_n);
+        dfree(g->pr_cursor); dfree(g->pr_src); dfree(g->pr_dst); dfree(g->pr_off); dfree(g->pr_part);
         for (auto &b : g->stage.buf) dfree(b.p);
         for (auto &r : g->prof.recs) {
             cudaEventDestroy(r.a);
@@ -1395,11 +1401,33 @@ gv_status gv_pagerank(gv_graph *g, uint32_t iterations, double damping, double *
     g->last_stream = s;
     if (g->nv == 0) return GV_OK;
     GV_TRY(ensure_analytics(g, true));
+    // incoming-edge CSR scratch: sized by the vertex count and by the stored
+    // entries (read once from the device)
+    GV_CK(cudaMemcpyAsync(g->h_small, &g->dev->num_edges, 8, cudaMemcpyDeviceToHost, s));
+    GV_CK(cudaStreamSynchronize(s));
+    const unsigned long long E = std::max<unsigned long long>(g->h_small[0], 1);
+    if (g->nv > g->pr_vcap || !g->pr_vcap) {
+        dfree(g->pr_cursor); dfree(g->pr_off); dfree(g->pr_part);
+        g->pr_vcap = 0;
+        const unsigned long long cap = std::max<unsigned long long>(g->nv, 1024);
+        GV_TRY(dalloc(&g->pr_cursor, cap, &g->scratch_bytes));
+        GV_TRY(dalloc(&g->pr_off, cap + 1, &g->scratch_bytes));
+        GV_TRY(dalloc(&g->pr_part, cap / 1024 + 2, &g->scratch_bytes));
+        g->pr_vcap = cap;
+    }
+    if (E > g->pr_ecap || !g->pr_ecap) {
+        dfree(g->pr_src); dfree(g->pr_dst);
+        g->pr_ecap = 0;
+        GV_TRY(dalloc(&g->pr_src, E, &g->scratch_bytes));
+        GV_TRY(dalloc(&g->pr_dst, E, &g->scratch_bytes));
+        g->pr_ecap = E;
+    }
     void *dr = rank;
     bool hr = false;
     GV_TRY(output_ptr(g, 0, rank, (size_t)g->nv * 8, &dr, &hr));
     GV_CK(gv::launch_pagerank(view(g), analytics_item_blocks(g), iterations, damping, (double *)dr, g->pr_c,
-                              g->pr_acc, g->pr_scal, g->pr_n, g->an_items, g->an_ctr + 1, lcfg(g, s)));
+                              g->pr_acc, g->pr_scal, g->pr_n, g->an_items, g->an_ctr + 1, g->pr_cursor, g->pr_off,
+                              g->pr_part, g->pr_src, g->pr_dst, g->pr_ecap, lcfg(g, s)));
     if (hr) {
         GV_CK(cudaMemcpyAsync(rank, dr, (size_t)g->nv * 8, cudaMemcpyDeviceToHost, s));
         GV_CK(cudaStreamSynchronize(s));

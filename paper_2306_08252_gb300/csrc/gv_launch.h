@@ -140,7 +140,9 @@ cudaError_t launch_bfs_level(const GraphView &g, uint32_t aib, const uint32_t *c
                              uint32_t *ctr, uint32_t *dist, uint32_t level, const LaunchCfg &lc);
 cudaError_t launch_pagerank(const GraphView &g, uint32_t aib, uint32_t iterations, double damping, double *r,
                             double *c, double *acc, double *scal, unsigned long long *N, uint2 *items,
-                            uint32_t *nitems, const LaunchCfg &lc);
+                            uint32_t *nitems, uint32_t *cursor, unsigned long long *in_off,
+                            unsigned long long *part, uint32_t *in_src, uint32_t *in_dst, unsigned long long ecap,
+                            const LaunchCfg &lc);
 cudaError_t launch_segment_noop_check(const GraphView &g, const unsigned long long *tot, unsigned long long n,
                                       const LaunchCfg &lc);
 cudaError_t launch_finalize_count_only(const GraphView &g, const LaunchCfg &lc);
