@@ -787,14 +787,48 @@ def run_rows(args):
         device_bytes=grown["device_bytes"], timer="CUDA events (growth allocations and copies included)")
     holder3["g"].close()
 
-    # a9 / a10 on the uniform 2^22 graph
-    er = W.er_mixed(3, rounds=0)
+    # a9 / a10 on the uniform 2^22 graph, and its mixed round (1M uniform
+    # inserts, then 1M deletes: half stored pairs, half absent ones)
+    er = W.er_mixed(3, rounds=1)
     nv2 = er["nv"]
     es, ed = er["bulk"]
     vdel = next(op for op in er["ops"] if op.kind == "vdel").ids
+    ins_op = er["ops"][0]
+    del_op = er["ops"][1]
     d_es, d_ed = t(es), t(ed)
     d_ids = t(vdel)
     holder2 = {}
+
+    ge = gv.Graph(nv2, block_capacity=4, pool_bytes=1 << 30)
+    ge.reserve(max(es.size, 1 << 20))
+    ge.bulk_build(d_es, d_ed, cnt)
+    d_is, d_id = t(ins_op.src), t(ins_op.dst)
+    d_ds, d_dd = t(del_op.src), t(del_op.dst)
+    ge.insert_edges(d_is, d_id, cnt)
+    torch.cuda.synchronize()
+    dege, _ = ge.degrees()
+    ge.delete_edges(d_is, d_id, cnt)
+    srcs = np.unique(ins_op.src)
+    ms = timed(lambda: ge.insert_edges(d_is, d_id, cnt), post=lambda: ge.delete_edges(d_is, d_id, cnt))
+    row("a2-a4 ER", f"uniform insert of {ins_op.src.size} pairs (2^22 vertices, 16.7M edges, C=4)",
+        ins_op.src.size, "edges", ms, 12 * ins_op.src.size + 32 * srcs.size + 12 * ins_op.src.size // 4)
+    ge.close()
+    dsrc = np.unique(del_op.src)
+    deg_er = np.bincount(es, minlength=nv2).astype(np.int64)
+    holder_e = {}
+
+    def mk_e():  # every timed delete starts from the bulk-built graph
+        if "g" in holder_e:
+            holder_e["g"].close()
+        holder_e["g"] = gv.Graph(nv2, block_capacity=4, pool_bytes=1 << 30)
+        holder_e["g"].reserve(max(es.size, 1 << 20))
+        holder_e["g"].bulk_build(d_es, d_ed, cnt)
+        torch.cuda.synchronize()
+
+    ms = timed(lambda: holder_e["g"].delete_edges(d_ds, d_dd, cnt), pre=mk_e, n=3)
+    holder_e["g"].close()
+    row("a6 ER", f"mixed delete of {del_op.src.size} pairs (half stored, half absent)", del_op.src.size, "edges",
+        ms, 8 * del_op.src.size + 4 * int(deg_er[dsrc].sum()) + 32 * dsrc.size)
 
     spare = t(np.setdiff1d(np.arange(nv2 - 64, nv2, dtype=np.uint32), vdel)[:1])
 
