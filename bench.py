@@ -804,10 +804,6 @@ def run_rows(args):
     ge.bulk_build(d_es, d_ed, cnt)
     d_is, d_id = t(ins_op.src), t(ins_op.dst)
     d_ds, d_dd = t(del_op.src), t(del_op.dst)
-    ge.insert_edges(d_is, d_id, cnt)
-    torch.cuda.synchronize()
-    dege, _ = ge.degrees()
-    ge.delete_edges(d_is, d_id, cnt)
     srcs = np.unique(ins_op.src)
     ms = timed(lambda: ge.insert_edges(d_is, d_id, cnt), post=lambda: ge.delete_edges(d_is, d_id, cnt))
     row("a2-a4 ER", f"uniform insert of {ins_op.src.size} pairs (2^22 vertices, 16.7M edges, C=4)",
