@@ -1746,7 +1746,7 @@ cudaError_t launch_insert_tail(const GraphView &g, const uint32_t *src, const ui
         PhaseScope ps(lc, PH_INS_PLAN);
         k_plan_insert<<<gt, 256, 0, lc.stream>>>(g);
     }
-    const unsigned long long max_pops = n / g.C + tcap + 1;
+    const unsigned long long max_pops = n / g.C + (tcap < n ? tcap : n) + 1;  // new blocks: <= n/C + sources
     {
         PhaseScope ps(lc, PH_INS_LINK);
         k_link_insert<<<grid_for(max_pops, 256, cap), 256, 0, lc.stream>>>(g);
@@ -1790,8 +1790,10 @@ static void member_tail(const GraphView &g0, const uint32_t *src, const uint32_t
     }
     // The two tiers touch disjoint sources (their blocks, sentinels and list
     // ranges) and share only atomically updated counters, so the thread-per-
-    // source tier runs on the graph's second stream beside the warp tier.
-    const bool fork = lc.side && lc.fork && lc.join;
+    // source tier runs on the graph's second stream beside the warp tier --
+    // for large batches: below FORK_MIN_PAIRS the fork and join cost more
+    // than the overlap saves.
+    const bool fork = lc.side && lc.fork && lc.join && n >= FORK_MIN_PAIRS;
     if (fork) {
         cudaEventRecord(lc.fork, lc.stream);
         cudaStreamWaitEvent(lc.side, lc.fork, 0);
