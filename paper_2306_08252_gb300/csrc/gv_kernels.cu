@@ -1774,7 +1774,7 @@ static void member_tail(const GraphView &g0, const uint32_t *src, const uint32_t
     // one per source (grid-stride loops cover sources with many items)
     const unsigned long long nt = tcap < n ? tcap : n;
     const int gt = grid_for(nt, 256, cap);
-    const int gi = grid_for(4 * nt + 256, 8, lc.num_sms * GRID_MULT);  // warp-per-item kernels: 8 warps per CTA
+    const int gi = grid_for(nt + 256, 8, lc.num_sms * GRID_MULT);  // warp-per-item kernels: 8 warps per CTA
     const bool del = MODE == MODE_DELETE;
     {
         PhaseScope ps(lc, del ? PH_DEL_PLAN : PH_QRY_PLAN);
@@ -1925,7 +1925,7 @@ cudaError_t launch_dedup_insert_prepare(const GraphView &g0, const uint32_t *src
     const int cap = lc.num_sms * GRID_MULT;
     const unsigned long long nt = tcap < n ? tcap : n;
     const int gt = grid_for(nt, 256, cap);
-    const int gi = grid_for(4 * nt + 256, 8, cap);
+    const int gi = grid_for(nt + 256, 8, cap);
     k_plan_member<MODE_DEDUP><<<gt, 256, 0, lc.stream>>>(g);
     k_arena_init<MODE_DEDUP><<<grid_for(8 * n + 64, 256, cap), 256, 0, lc.stream>>>(g);
     k_scatter_member<MODE_DEDUP><<<grid_for(n, 256 * PP, cap), 256, 0, lc.stream>>>(g, src, dst, n);
