@@ -583,9 +583,9 @@ __global__ void __launch_bounds__(256) k_plan_member(GraphView g) {
             else if (m <= LIST_MAX) lw = m;
             else hw = member_words(m);
             if (s.y > 0) {
-                const bool small = MODE == MODE_QUERY
+                const bool small = !g.no_tiny && (MODE == MODE_QUERY
                     ? (s.x <= min(TINY_DEG_Q, TINY_NB_Q * g.C) && s.y <= TINY_NB_Q && m <= TINY_M)
-                    : (MODE != MODE_DEDUP && s.x <= tiny_deg && s.y <= TINY_NB && m <= TINY_M);
+                    : (MODE != MODE_DEDUP && s.x <= tiny_deg && s.y <= TINY_NB && m <= TINY_M));
                 if (small) tiny = 1;
                 else ni = (s.y + IB - 1) / IB;
             }
@@ -1769,6 +1769,9 @@ static void member_tail(const GraphView &g0, const uint32_t *src, const uint32_t
                         uint8_t *qout, const LaunchCfg &lc) {
     GraphView g = g0;
     g.hbase = (uint32_t)((n + 63) / 64 * 64);  // lists below (at most n words), hash sets above
+    // Small batches touch few sources: one warp per source is shorter than a
+    // thread walking a whole small adjacency (and saves the tier's launch).
+    g.no_tiny = n < TINY_MIN_PAIRS ? 1u : 0u;
     const int cap = lc.num_sms * GRID_MULT;
     // grids follow the batch: at most n touched sources; work items start at
     // one per source (grid-stride loops cover sources with many items)
@@ -1793,7 +1796,7 @@ static void member_tail(const GraphView &g0, const uint32_t *src, const uint32_t
     // source tier runs on the graph's second stream beside the warp tier --
     // for large batches: below FORK_MIN_PAIRS the fork and join cost more
     // than the overlap saves.
-    const bool fork = lc.side && lc.fork && lc.join && n >= FORK_MIN_PAIRS;
+    const bool fork = lc.side && lc.fork && lc.join && n >= FORK_MIN_PAIRS && !g.no_tiny;
     if (fork) {
         cudaEventRecord(lc.fork, lc.stream);
         cudaStreamWaitEvent(lc.side, lc.fork, 0);
@@ -1807,7 +1810,7 @@ static void member_tail(const GraphView &g0, const uint32_t *src, const uint32_t
         if (MODE != MODE_QUERY && g.wdata) k_mark<MODE, true><<<gi, 256, 0, lc.stream>>>(g);
         else k_mark<MODE><<<gi, 256, 0, lc.stream>>>(g);
     }
-    if (!fork) {
+    if (!fork && !g.no_tiny) {
         PhaseScope ps(lc, del ? PH_DEL_MARK_TINY : PH_QRY_MARK_TINY);
         k_mark_tiny<MODE><<<gt, 256, 0, lc.stream>>>(g);
     }
