@@ -67,7 +67,6 @@ struct GraphView {
     uint32_t vmask;         // dictionary capacity - 1 (capacity is a power of two)
     unsigned long long cmul;  // ceil(2^40 / C): x / C == (x * cmul) >> 40 for x < 2^31
     uint32_t dense_shift;   // batches with n >= nv >> dense_shift use per-pair counting
-    uint32_t no_tiny;       // 1: every source goes to warp work items (small batches)
     // vertex-indexed scratch (zero between calls), indexed by vslot(u)
     uint32_t *vcnt;         // batch entries per source
     uint4 *vinfo;           // per-source plan record read by the scatters (one 16-byte load per pair)

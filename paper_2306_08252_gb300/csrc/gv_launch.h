@@ -72,10 +72,7 @@ struct PhaseScope {
 };
 
 // Group-by-source counting pass over a pair batch (all modes).
-// Batches of at least this many pairs run the two mark tiers concurrently.
-constexpr unsigned long long FORK_MIN_PAIRS = 1ull << 20;
-// Batches below this many pairs use the warp tier for every source.
-constexpr unsigned long long TINY_MIN_PAIRS = 1ull << 15;
+
 
 // Blocks for `work` units at `per_block` units per block, at least 1 and at
 // most `cap` (grid-stride kernels cover the rest).
