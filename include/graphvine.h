@@ -23,7 +23,10 @@
  *     as void*; NULL = the legacy default stream).  Calls on one graph must
  *     be ordered by the caller (one stream, or explicit dependencies): the
  *     graph's scratch memory is shared by its calls.  Different graphs are
- *     independent and may be used from different threads.
+ *     independent and may be used from different threads.  Inside a call the
+ *     library may fork part of the work onto a second stream it owns; that
+ *     work joins back onto `stream` before the call's last kernel, so the
+ *     ordering on `stream` (and stream capture into a CUDA graph) holds.
  *   - The return value reports host-detectable errors at once (NULL graph,
  *     NULL array with n > 0, n too large, CUDA launch or allocation failure).
  *     Errors found on the device (edge pool exhausted, structure
@@ -38,6 +41,8 @@
  *     delete removes every stored copy of each (u, v) it names (Algorithm 2
  *     marks every matching entry).  With GV_DEDUP an insert adds a pair only
  *     if it is not stored yet and not already added by the same batch.
+ *   - With GV_WEIGHTED every entry carries a 32-bit payload that stays with
+ *     it; deletes match (u, v) whatever the payload.
  */
 #ifndef GRAPHVINE_H
 #define GRAPHVINE_H
