@@ -91,8 +91,9 @@ struct gv_graph {
     uint64_t dict_bytes = 0;
     bool any_vertex_deleted = false;
     unsigned long long used_ub = 0;  // upper bound of blocks in use (pool growth policy)
-    cudaStream_t side = nullptr;     // second stream: concurrent mark tiers
+    cudaStream_t side = nullptr;     // second stream: concurrent mark tiers, staging copies
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_stage[5] = {};    // staging pipeline: start + one per piece
     // analytics scratch: items, two frontiers, counters, PageRank vectors
     unsigned long long an_icap = 0, an_vcap = 0;
     uint2 *an_items = nullptr;
@@ -559,6 +560,48 @@ gv_status maybe_grow(gv_graph *g, uint64_t n, cudaStream_t s) {
     return GV_OK;
 }
 
+// Host-array batches of at least kPipeMin pairs are staged in kPipePieces
+// pieces on the graph's second stream, and each piece is counted on the call
+// stream as soon as it has landed: the counting pass overlaps the copies of
+// the later pieces.  (Counting is order-independent: ranks come from atomics.)
+constexpr uint64_t kPipeMin = 1ull << 20;
+constexpr int kPipePieces = 4;
+
+bool can_pipeline(const gv_graph *g, const uint32_t *src, const uint32_t *dst, uint64_t n) {
+    if (n < kPipeMin || !g->side || g->C == 0) return false;
+    for (auto e : g->ev_stage)
+        if (!e) return false;
+    return is_host_ptr(src) && is_host_ptr(dst);
+}
+
+// Stages src/dst (host arrays) into the staging slots 0/1 and runs the
+// counting pass of `mode` over them, piece by piece.
+gv_status stage_and_count(gv_graph *g, int mode, const uint32_t *src, const uint32_t *dst, uint64_t n,
+                          cudaStream_t s, const void **dsrc, const void **ddst) {
+    void *d0 = nullptr, *d1 = nullptr;
+    GV_TRY(stage_buf(g, 0, n * 4, &d0));
+    GV_TRY(stage_buf(g, 1, n * 4, &d1));
+    // the copies must not overwrite staging buffers that earlier work on s reads
+    GV_CK(cudaEventRecord(g->ev_stage[0], s));
+    GV_CK(cudaStreamWaitEvent(g->side, g->ev_stage[0], 0));
+    const GraphView v = view(g);
+    for (int k = 0; k < kPipePieces; ++k) {
+        const uint64_t lo = n * k / kPipePieces, hi = n * (k + 1) / kPipePieces;
+        GV_CK(cudaMemcpyAsync(static_cast<uint32_t *>(d0) + lo, src + lo, (hi - lo) * 4, cudaMemcpyHostToDevice,
+                              g->side));
+        GV_CK(cudaMemcpyAsync(static_cast<uint32_t *>(d1) + lo, dst + lo, (hi - lo) * 4, cudaMemcpyHostToDevice,
+                              g->side));
+        GV_CK(cudaEventRecord(g->ev_stage[k + 1], g->side));
+        GV_CK(cudaStreamWaitEvent(s, g->ev_stage[k + 1], 0));
+        GV_CK(gv::launch_count_range(mode, v, static_cast<const uint32_t *>(d0), static_cast<const uint32_t *>(d1), n,
+                                     lo, hi, lcfg(g, s)));
+    }
+    GV_CK(gv::launch_count_finish(mode, v, n, lcfg(g, s)));
+    *dsrc = d0;
+    *ddst = d1;
+    return GV_OK;
+}
+
 gv_status insert_impl(gv_graph *g, const uint32_t *src, const uint32_t *dst, uint64_t n,
                       uint64_t *counts, cudaStream_t s, const uint32_t *wts = nullptr) {
     if (!g) return GV_ERR_INVALID_ARG;
@@ -567,8 +610,11 @@ gv_status insert_impl(gv_graph *g, const uint32_t *src, const uint32_t *dst, uin
     DeviceGuard dg(g->device);
     g->last_stream = s;
     const void *dsrc = src, *ddst = dst, *dwts = wts;
-    GV_TRY(input_ptr(g, 0, src, n * 4, s, &dsrc));
-    GV_TRY(input_ptr(g, 1, dst, n * 4, s, &ddst));
+    const bool pipe = !(g->flags & GV_DEDUP) && can_pipeline(g, src, dst, n);
+    if (!pipe) {
+        GV_TRY(input_ptr(g, 0, src, n * 4, s, &dsrc));
+        GV_TRY(input_ptr(g, 1, dst, n * 4, s, &ddst));
+    }
     if (wts) GV_TRY(input_ptr(g, 3, wts, n * 4, s, &dwts));
     void *dcounts = counts;
     bool host_counts = false;
@@ -634,7 +680,8 @@ gv_status insert_impl(gv_graph *g, const uint32_t *src, const uint32_t *dst, uin
             if (counts) GV_CK(cudaMemsetAsync(dcounts, 0, 16, s));
         } else {
             GraphView v = view(g);
-            GV_CK(gv::launch_count(gv::MODE_INSERT, v, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, lcfg(g, s)));
+            if (pipe) GV_TRY(stage_and_count(g, gv::MODE_INSERT, src, dst, n, s, &dsrc, &ddst));
+            else GV_CK(gv::launch_count(gv::MODE_INSERT, v, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, lcfg(g, s)));
             GV_CK(gv::launch_insert_tail(v, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, g->tcap,
                                          (unsigned long long *)dcounts, lcfg(g, s), (const uint32_t *)dwts));
         }
@@ -690,14 +737,18 @@ gv_status member_impl(gv_graph *g, int mode, const uint32_t *src, const uint32_t
         return check_launch();
     }
     const void *dsrc = src, *ddst = dst;
-    GV_TRY(input_ptr(g, 0, src, n * 4, s, &dsrc));
-    GV_TRY(input_ptr(g, 1, dst, n * 4, s, &ddst));
+    const bool pipe = can_pipeline(g, src, dst, n);
+    if (!pipe) {
+        GV_TRY(input_ptr(g, 0, src, n * 4, s, &dsrc));
+        GV_TRY(input_ptr(g, 1, dst, n * 4, s, &ddst));
+    }
     void *dq = qout;
     bool hq = false;
     if (mode == gv::MODE_QUERY) GV_TRY(output_ptr(g, 3, qout, n, &dq, &hq));
     GV_TRY(ensure_batch(g, n, mode));
     GraphView v = view(g);
-    GV_CK(gv::launch_count(mode, v, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, lcfg(g, s)));
+    if (pipe) GV_TRY(stage_and_count(g, mode, src, dst, n, s, &dsrc, &ddst));
+    else GV_CK(gv::launch_count(mode, v, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, lcfg(g, s)));
     GV_CK(gv::launch_member_tail(mode, v, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, g->tcap,
                                  (unsigned long long *)dcounts, (uint8_t *)dq, lcfg(g, s)));
     if (host_counts) GV_CK(cudaMemcpyAsync(counts, dcounts, 16, cudaMemcpyDeviceToHost, s));
@@ -811,6 +862,11 @@ gv_status gv_create(const gv_config *cfg, uint32_t num_vertices, void *stream, g
         g->side = nullptr;
         g->ev_fork = g->ev_join = nullptr;
     }
+    for (auto &e : g->ev_stage)
+        if (g->side && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            e = nullptr;
+        }
     g->flags = c.flags;
     g->item_blocks_cfg = c.item_blocks;
     if (c.dense_shift) g->dense_shift = std::min<uint32_t>(c.dense_shift, 31);
@@ -878,6 +934,8 @@ gv_status gv_destroy(gv_graph *g) {
         }
         if (g->ev_fork) cudaEventDestroy(g->ev_fork);
         if (g->ev_join) cudaEventDestroy(g->ev_join);
+        for (auto e : g->ev_stage)
+            if (e) cudaEventDestroy(e);
         cudaGetLastError();
     }
     delete g;

@@ -1699,25 +1699,30 @@ cudaError_t launch_set_insert_counts(const GraphView &g, const LaunchCfg &lc);
 // ------------------------------------------------------------------ launch
 
 
-cudaError_t launch_count(int mode, const GraphView &g, const uint32_t *src, const uint32_t *dst,
-                         unsigned long long n, const LaunchCfg &lc) {
+// Counting pass over pairs [lo, hi) of a batch of n_total pairs (the path --
+// per-pair atomics or per-tile aggregation -- follows n_total, so the
+// pieces of one batch all take the same one).
+cudaError_t launch_count_range(int mode, const GraphView &g0, const uint32_t *src, const uint32_t *dst,
+                               unsigned long long n_total, unsigned long long lo, unsigned long long hi,
+                               const LaunchCfg &lc) {
     const int ph = mode == MODE_INSERT ? PH_INS_COUNT : mode == MODE_DELETE ? PH_DEL_COUNT : PH_QRY_COUNT;
-    if (n >= ((unsigned long long)g.nv >> g.dense_shift)) {
-        // large batch: per-pair atomics, then a pass over all vertices
+    if (hi <= lo) return cudaSuccess;
+    GraphView g = g0;
+    g.prank = g0.prank + lo;  // ranks are written at the pair's index
+    src += lo;
+    dst += lo;
+    const unsigned long long n = hi - lo;
+    PhaseScope ps(lc, ph);
+    if (n_total >= ((unsigned long long)g.nv >> g.dense_shift)) {
+        // large batch: per-pair atomics (the touched list follows the pass)
         const int grid = grid_for(n, 256 * 8, lc.num_sms * GRID_MULT);
-        {
-            PhaseScope ps(lc, ph);
-            switch (mode) {
-            case MODE_INSERT: k_count_direct<MODE_INSERT><<<grid, 256, 0, lc.stream>>>(g, src, dst, n); break;
-            case MODE_DELETE: k_count_direct<MODE_DELETE><<<grid, 256, 0, lc.stream>>>(g, src, dst, n); break;
-            default: k_count_direct<MODE_QUERY><<<grid, 256, 0, lc.stream>>>(g, src, dst, n); break;
-            }
+        switch (mode) {
+        case MODE_INSERT: k_count_direct<MODE_INSERT><<<grid, 256, 0, lc.stream>>>(g, src, dst, n); break;
+        case MODE_DELETE: k_count_direct<MODE_DELETE><<<grid, 256, 0, lc.stream>>>(g, src, dst, n); break;
+        default: k_count_direct<MODE_QUERY><<<grid, 256, 0, lc.stream>>>(g, src, dst, n); break;
         }
-        PhaseScope ps(lc, ph + 1);  // the touched-list phase follows each count phase
-        k_touched_scan<<<grid_for(g.vmask + 1ull, 1024, lc.num_sms * GRID_MULT), 256, 0, lc.stream>>>(g);
     } else {
         // small batch: per-tile aggregation, touched list appended on the fly
-        PhaseScope ps(lc, ph);
         const int grid = grid_for(n, AGG_TILE, lc.num_sms * GRID_MULT);
         switch (mode) {
         case MODE_INSERT: k_count<MODE_INSERT><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
@@ -1726,6 +1731,24 @@ cudaError_t launch_count(int mode, const GraphView &g, const uint32_t *src, cons
         }
     }
     return cudaGetLastError();
+}
+
+// After every piece of a batch is counted: the touched list of a large
+// batch (a pass over the vertex counters).
+cudaError_t launch_count_finish(int mode, const GraphView &g, unsigned long long n_total, const LaunchCfg &lc) {
+    const int ph = mode == MODE_INSERT ? PH_INS_COUNT : mode == MODE_DELETE ? PH_DEL_COUNT : PH_QRY_COUNT;
+    if (n_total >= ((unsigned long long)g.nv >> g.dense_shift)) {
+        PhaseScope ps(lc, ph + 1);  // the touched-list phase follows each count phase
+        k_touched_scan<<<grid_for(g.vmask + 1ull, 1024, lc.num_sms * GRID_MULT), 256, 0, lc.stream>>>(g);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count(int mode, const GraphView &g, const uint32_t *src, const uint32_t *dst,
+                         unsigned long long n, const LaunchCfg &lc) {
+    cudaError_t e = launch_count_range(mode, g, src, dst, n, 0, n, lc);
+    if (e != cudaSuccess) return e;
+    return launch_count_finish(mode, g, n, lc);
 }
 
 cudaError_t launch_count_rejects(const GraphView &g, const uint32_t *src, const uint32_t *dst,

@@ -83,6 +83,10 @@ inline int grid_for(unsigned long long work, int per_block, int cap) {
     return (int)g;
 }
 
+cudaError_t launch_count_range(int mode, const GraphView &g, const uint32_t *src, const uint32_t *dst,
+                               unsigned long long n_total, unsigned long long lo, unsigned long long hi,
+                               const LaunchCfg &lc);
+cudaError_t launch_count_finish(int mode, const GraphView &g, unsigned long long n_total, const LaunchCfg &lc);
 cudaError_t launch_count(int mode, const GraphView &g, const uint32_t *src, const uint32_t *dst,
                          unsigned long long n, const LaunchCfg &lc);
 // Rejected-pair count only (batches that cannot match any stored edge).

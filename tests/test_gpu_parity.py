@@ -375,3 +375,36 @@ def test_pool_growth_rejects_caller_owned_pool():
     buf = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
     with pytest.raises(gv.GraphVineError):
         gv.Graph(1024, block_capacity=16, pool_bytes=buf.numel(), pool_mem=buf, flags=gv.GV_GROW)
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_large_host_batches_staged_in_pieces(pinned):
+    # host arrays of >= 2^20 pairs are staged in pieces, each counted as it
+    # lands: results equal the oracle's, for inserts, queries and deletes
+    # (pinned and pageable host memory)
+    import torch
+    scale, nv = 16, 1 << 16
+    bs, bd = W.rmat_pairs(91, 0, 200_000, scale)
+    s, d = W.rmat_pairs(91, 1, (1 << 20) + 12345, scale)
+    p = Pair(nv, C=8, pool_bytes=256 << 20)
+    try:
+        p.bulk(bs, bd)
+        host = (lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).pin_memory()) if pinned \
+            else (lambda a: np.ascontiguousarray(a, dtype=np.uint32))
+        hs, hd = host(s), host(d)
+        cnt = np.zeros(2, dtype=np.uint64)
+        p.g.insert_edges(hs, hd, cnt)
+        assert tuple(int(x) for x in cnt) == p.o.insert_edges(s, d)
+        p.check(full=False)
+        out = np.zeros(s.size, dtype=np.uint8)
+        p.g.query_edges(hs, hd, out)
+        np.testing.assert_array_equal(out, p.o.query_edges(s, d))
+        half_s, half_d = host(s[: s.size // 2 + 7]), host(d[: d.size // 2 + 7])
+        ks = np.concatenate([s[: s.size // 2 + 7], bs[:10]])
+        kd = np.concatenate([d[: d.size // 2 + 7], bd[:10]])
+        p.g.delete_edges(host(ks), host(kd), cnt)
+        assert tuple(int(x) for x in cnt) == p.o.delete_edges(ks, kd)
+        del half_s, half_d
+        p.check()
+    finally:
+        p.close()
