@@ -399,12 +399,10 @@ def test_large_host_batches_staged_in_pieces(pinned):
         out = np.zeros(s.size, dtype=np.uint8)
         p.g.query_edges(hs, hd, out)
         np.testing.assert_array_equal(out, p.o.query_edges(s, d))
-        half_s, half_d = host(s[: s.size // 2 + 7]), host(d[: d.size // 2 + 7])
         ks = np.concatenate([s[: s.size // 2 + 7], bs[:10]])
         kd = np.concatenate([d[: d.size // 2 + 7], bd[:10]])
         p.g.delete_edges(host(ks), host(kd), cnt)
         assert tuple(int(x) for x in cnt) == p.o.delete_edges(ks, kd)
-        del half_s, half_d
         p.check()
     finally:
         p.close()
