@@ -762,6 +762,74 @@ __global__ void __launch_bounds__(256) k_scatter_member(GraphView g, const uint3
 }
 
 // One warp per work item (see the file comment).
+// Per multi-item source (one warp, all lanes call): the new degree is the
+// sum of the items' survivors; per item, the holes below the new degree and
+// the survivors at or above it, prefix-summed over the source's items
+// (it_H, it_S); the sentinel gets the new degree and block count.  Reads go
+// through L2: the items were written by other warps of the same kernel when
+// this runs fused into k_mark.
+__device__ __forceinline__ void vscan_source(const GraphView &g, uint32_t t, uint32_t *s_mhist,
+                                             unsigned long long &removed) {
+    const uint32_t lane = lane_id();
+    const uint32_t C = g.C, IB = g.IB, SPI = IB * C;
+    const uint4 b = g.t_b[t];
+    const uint32_t ni = b.w;
+    const uint32_t item0 = g.t_a[t].w;
+    const uint32_t deg = b.x, root = b.z;
+    uint32_t tot = 0;
+    for (uint32_t c = lane; c < ni; c += 32) tot += __ldcg(g.it_cnt + item0 + c);
+    const uint32_t degn = warp_sum(tot);
+    uint32_t carryH = 0, carryS = 0;
+    for (uint32_t c0 = 0; c0 < ni; c0 += 32) {
+        const uint32_t c = c0 + lane;
+        uint32_t h = 0, s = 0;
+        if (c < ni) {
+            const uint32_t sb = c * SPI;
+            const uint32_t len = min(SPI, deg - sb);
+            const uint32_t cnt = __ldcg(g.it_cnt + item0 + c);
+            if (sb + len <= degn) {
+                h = len - cnt;
+            } else if (sb >= degn) {
+                s = cnt;
+            } else {
+                const uint32_t split = degn - sb;
+                const uint32_t *mk = g.it_mask + (size_t)(item0 + c) * MASK_WORDS;
+                uint32_t below = 0;
+                for (uint32_t w = 0; w * 32 < split; ++w) {
+                    uint32_t word = __ldcg(mk + w);
+                    const uint32_t nbits = split - w * 32;
+                    if (nbits < 32) word &= (1u << nbits) - 1u;
+                    below += __popc(word);
+                }
+                h = split - below;
+                s = cnt - below;
+            }
+        }
+        uint32_t th, ts;
+        const uint32_t eh = warp_excl_scan(h, &th);
+        const uint32_t es = warp_excl_scan(s, &ts);
+        if (c < ni) {
+            g.it_H[item0 + c] = carryH + eh;
+            g.it_S[item0 + c] = carryS + es;
+        }
+        carryH += th;
+        carryS += ts;
+    }
+    if (lane == 0) {
+        g.t_a[t].x = degn;
+        const uint32_t nbn = divc(g.cmul, degn + C - 1);
+        uint32_t lastb = NIL;
+        if (nbn) {
+            const uint32_t k = nbn - 1;
+            lastb = __ldcg(g.it_bid + (size_t)(item0 + k / IB) * IB + (k % IB));
+        }
+        const uint32_t u = g.t_vid[t];
+        g.sent[u] = make_uint4(degn, nbn, nbn ? root : NIL, lastb);
+        removed += deg - degn;
+        if (g.set_G && !g.seg_own) atomicAdd(&s_mhist[member_of(g.set_vbase, g.set_G, u)], deg - degn);
+    }
+}
+
 template <int MODE, bool WEIGHTED = false>
 __global__ void __launch_bounds__(256, 4) k_mark(GraphView g) {
     Dev *dev = g.dev;
@@ -995,6 +1063,22 @@ __global__ void __launch_bounds__(256, 4) k_mark(GraphView g) {
         } else {
             if (lane < nblk) g.it_bid[(size_t)it * IB + lane] = bid;
             if (lane == 0) g.it_cnt[it] = running;
+            if (MODE == MODE_DELETE) {
+                // the warp that finishes a source's last item runs the
+                // source's scan step (its counter: the .w word of the
+                // source's vinfo record, zeroed by the plan)
+                __syncwarp();
+                __threadfence();
+                uint32_t last = 0;
+                if (lane == 0) {
+                    uint32_t *done = reinterpret_cast<uint32_t *>(&g.vinfo[vslot(g.vmask, g.t_vid[t])]) + 3;
+                    last = atomicAdd(done, 1u) == ni - 1;
+                }
+                if (__shfl_sync(FULL, last, 0)) {
+                    __threadfence();
+                    vscan_source(g, t, s_mhist, removed);
+                }
+            }
         }
     }
     if (MODE != MODE_QUERY) {
@@ -1192,13 +1276,14 @@ __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
 }
 
 // One warp per multi-item source.
+// One warp per multi-item source (vertex deletes; edge deletes run the same
+// step fused into k_mark, by the warp that finishes a source's last item).
 template <int MODE>
 __global__ void __launch_bounds__(256) k_vscan(GraphView g) {
     Dev *dev = g.dev;
     const uint32_t lane = lane_id();
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    const uint32_t C = g.C, IB = g.IB, SPI = IB * C;
     __shared__ uint32_t s_mhist[SET_MAX_G];
     if (g.set_G) {
         for (uint32_t i = threadIdx.x; i < g.set_G; i += blockDim.x) s_mhist[i] = 0;
@@ -1212,63 +1297,8 @@ __global__ void __launch_bounds__(256) k_vscan(GraphView g) {
         const uint2 first = g.items[g.max_items - nhi + vi];
         if (first.y != 0) continue;
         const uint32_t t = first.x;
-        const uint4 b = g.t_b[t];
-        const uint32_t ni = b.w;
-        if (ni <= 1) continue;
-        const uint32_t item0 = g.t_a[t].w;
-        const uint32_t deg = b.x, root = b.z;
-        uint32_t tot = 0;
-        for (uint32_t c = lane; c < ni; c += 32) tot += g.it_cnt[item0 + c];
-        const uint32_t degn = warp_sum(tot);
-        uint32_t carryH = 0, carryS = 0;
-        for (uint32_t c0 = 0; c0 < ni; c0 += 32) {
-            const uint32_t c = c0 + lane;
-            uint32_t h = 0, s = 0;
-            if (c < ni) {
-                const uint32_t sb = c * SPI;
-                const uint32_t len = min(SPI, deg - sb);
-                const uint32_t cnt = g.it_cnt[item0 + c];
-                if (sb + len <= degn) {
-                    h = len - cnt;
-                } else if (sb >= degn) {
-                    s = cnt;
-                } else {
-                    const uint32_t split = degn - sb;
-                    const uint32_t *mk = g.it_mask + (size_t)(item0 + c) * MASK_WORDS;
-                    uint32_t below = 0;
-                    for (uint32_t w = 0; w * 32 < split; ++w) {
-                        uint32_t word = mk[w];
-                        const uint32_t nbits = split - w * 32;
-                        if (nbits < 32) word &= (1u << nbits) - 1u;
-                        below += __popc(word);
-                    }
-                    h = split - below;
-                    s = cnt - below;
-                }
-            }
-            uint32_t th, ts;
-            const uint32_t eh = warp_excl_scan(h, &th);
-            const uint32_t es = warp_excl_scan(s, &ts);
-            if (c < ni) {
-                g.it_H[item0 + c] = carryH + eh;
-                g.it_S[item0 + c] = carryS + es;
-            }
-            carryH += th;
-            carryS += ts;
-        }
-        if (lane == 0) {
-            g.t_a[t].x = degn;
-            const uint32_t nbn = divc(g.cmul, degn + C - 1);
-            uint32_t lastb = NIL;
-            if (nbn) {
-                const uint32_t k = nbn - 1;
-                lastb = g.it_bid[(size_t)(item0 + k / IB) * IB + (k % IB)];
-            }
-            const uint32_t u = g.t_vid[t];
-            g.sent[u] = make_uint4(degn, nbn, nbn ? root : NIL, lastb);
-            removed += deg - degn;
-            if (g.set_G && !g.seg_own) atomicAdd(&s_mhist[member_of(g.set_vbase, g.set_G, u)], deg - degn);
-        }
+        if (g.t_b[t].w <= 1) continue;
+        vscan_source(g, t, s_mhist, removed);
     }
     if (lane == 0 && removed) atomicAdd(&dev->call_a, removed);
     if (g.set_G) {
@@ -1345,11 +1375,12 @@ __global__ void __launch_bounds__(256) k_move(GraphView g) {
                         }
                         r -= pc;
                     }
-                    if (pos != NIL) {
-                        const uint32_t pq = divc(g.cmul, pos), xq = divc(g.cmul, x);
-                        const uint32_t srcb = g.it_bid[(size_t)(item0 + cs) * IB + pq];
+                    const uint32_t pq = pos != NIL ? divc(g.cmul, pos) : 0u, xq = divc(g.cmul, x);
+                    const uint32_t srcb = pos != NIL ? g.it_bid[(size_t)(item0 + cs) * IB + pq] : NIL;
+                    const uint32_t dstb = bids[xq];
+                    if (pos != NIL && srcb < P && dstb < P) {
                         const size_t from = (size_t)srcb * C + (pos - pq * C);
-                        const size_t to = (size_t)bids[xq] * C + (x - xq * C);
+                        const size_t to = (size_t)dstb * C + (x - xq * C);
                         g.data[to] = g.data[from];
                         if (g.wdata) g.wdata[to] = g.wdata[from];
                     } else {
@@ -1837,10 +1868,7 @@ static void member_tail(const GraphView &g0, const uint32_t *src, const uint32_t
     if (del) {
         // the hole filling of multi-item sources does not touch tiny sources
         // either: the side stream joins only before the finalize
-        {
-            PhaseScope ps(lc, PH_DEL_VSCAN);
-            k_vscan<MODE><<<grid_for(nt, 8, cap), 256, 0, lc.stream>>>(g);
-        }
+        // (the per-source scan step ran inside k_mark)
         PhaseScope ps(lc, PH_DEL_MOVE);
         k_move<MODE><<<gi, 256, 0, lc.stream>>>(g);
     }
