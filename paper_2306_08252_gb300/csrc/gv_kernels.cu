@@ -765,9 +765,7 @@ __global__ void __launch_bounds__(256) k_scatter_member(GraphView g, const uint3
 // Per multi-item source (one warp, all lanes call): the new degree is the
 // sum of the items' survivors; per item, the holes below the new degree and
 // the survivors at or above it, prefix-summed over the source's items
-// (it_H, it_S); the sentinel gets the new degree and block count.  Reads go
-// through L2: the items were written by other warps of the same kernel when
-// this runs fused into k_mark.
+// (it_H, it_S); the sentinel gets the new degree and block count.
 __device__ __forceinline__ void vscan_source(const GraphView &g, uint32_t t, uint32_t *s_mhist,
                                              unsigned long long &removed) {
     const uint32_t lane = lane_id();
@@ -1063,22 +1061,6 @@ __global__ void __launch_bounds__(256, 4) k_mark(GraphView g) {
         } else {
             if (lane < nblk) g.it_bid[(size_t)it * IB + lane] = bid;
             if (lane == 0) g.it_cnt[it] = running;
-            if (MODE == MODE_DELETE) {
-                // the warp that finishes a source's last item runs the
-                // source's scan step (its counter: the .w word of the
-                // source's vinfo record, zeroed by the plan)
-                __syncwarp();
-                __threadfence();
-                uint32_t last = 0;
-                if (lane == 0) {
-                    uint32_t *done = reinterpret_cast<uint32_t *>(&g.vinfo[vslot(g.vmask, g.t_vid[t])]) + 3;
-                    last = atomicAdd(done, 1u) == ni - 1;
-                }
-                if (__shfl_sync(FULL, last, 0)) {
-                    __threadfence();
-                    vscan_source(g, t, s_mhist, removed);
-                }
-            }
         }
     }
     if (MODE != MODE_QUERY) {
@@ -1276,8 +1258,7 @@ __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
 }
 
 // One warp per multi-item source.
-// One warp per multi-item source (vertex deletes; edge deletes run the same
-// step fused into k_mark, by the warp that finishes a source's last item).
+// One warp per multi-item source.
 template <int MODE>
 __global__ void __launch_bounds__(256) k_vscan(GraphView g) {
     Dev *dev = g.dev;
@@ -1868,7 +1849,10 @@ static void member_tail(const GraphView &g0, const uint32_t *src, const uint32_t
     if (del) {
         // the hole filling of multi-item sources does not touch tiny sources
         // either: the side stream joins only before the finalize
-        // (the per-source scan step ran inside k_mark)
+        {
+            PhaseScope ps(lc, PH_DEL_VSCAN);
+            k_vscan<MODE><<<grid_for(nt, 8, cap), 256, 0, lc.stream>>>(g);
+        }
         PhaseScope ps(lc, PH_DEL_MOVE);
         k_move<MODE><<<gi, 256, 0, lc.stream>>>(g);
     }
