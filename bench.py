@@ -155,6 +155,25 @@ class ClockSampler:
 
 # -------------------------------------------------------------- byte model
 
+def max_over_ranks(values, world, device="cpu"):
+    """Per-figure maximum over the ranks of the job (one all_reduce of a
+    float64 vector on `device`); the values themselves at world size 1."""
+    values = [float(v) for v in values]
+    if world <= 1:
+        return values
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Whole-job throughput: every rank processed `units_per_rank` units and
+    the job took `ms` (the slowest rank's time)."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def byte_model(g, batch, qry, inserted, deleted, newblocks):
     """Algorithmic bytes.
 
@@ -343,18 +362,14 @@ def run_ours(args, rank, world, local_rank):
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": e_ms / args.steps, "timer": "host wall clock around synchronised calls"}
 
-    # max over ranks
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-        if e2e:
-            te = torch.tensor([e2e["ms_per_step"]], device=dev)
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-            e2e["value"] = world * args.steps * (inserted + deleted) / (float(te.item()) * args.steps / 1e3)
-            e2e["ms_per_step"] = float(te.item())
+    # the slowest rank's times; every rank processed the same units
+    mx = max_over_ranks([total_ms] + ([e2e["ms_per_step"]] if e2e else []), world, dev)
+    total_ms = mx[0]
+    if e2e:
+        e2e["ms_per_step"] = mx[1]
+        e2e["value"] = whole_job_rate(args.steps * (inserted + deleted), world, mx[1] * args.steps)
 
-    value = world * upd_done / (total_ms / 1e3)
+    value = whole_job_rate(upd_done, world, total_ms)
     pk, pk_kind = peaks()
     hbm = float(pk.get("hbm_gbs", 6800.0))
     # dominant kernel phase = largest device time in the timed region among
