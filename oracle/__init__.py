@@ -60,6 +60,7 @@ def _get():
                 "orc_insert_edges_weighted": ([p, p, p, p, u64, p, p], None),
                 "orc_neighbors_weighted": ([p, p, u32, p, p, p, u64], u64),
                 "orc_pagerank": ([p, u32, ctypes.c_double, p], None),
+                "orc_sssp": ([p, u32, ctypes.c_int, p], u32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -178,6 +179,13 @@ class OracleGraph:
         r = np.zeros(max(self.num_vertices, 1), dtype=np.float64)
         self._lib.orc_pagerank(self._g, iterations, damping, r.ctypes.data)
         return r[:self.num_vertices]
+
+    def sssp(self, source: int, weighted: bool = False):
+        """(dist[nv] uint64, reached); entry length = payload if weighted
+        else 1; unreached = 2^64 - 1."""
+        dist = np.zeros(max(self.num_vertices, 1), dtype=np.uint64)
+        r = int(self._lib.orc_sssp(self._g, source, 1 if weighted else 0, dist.ctypes.data))
+        return dist[:self.num_vertices], r
 
     def export_csr(self):
         nv = self.num_vertices

@@ -517,3 +517,74 @@ void orc_pagerank(const orc_graph *g, uint32_t iterations, double damping, doubl
     }
     free(acc);
 }
+
+/*
+ * orc_sssp: single-source shortest path lengths (Dijkstra's algorithm with a
+ * binary heap and lazy deletion), the third analytic the paper's future work
+ * names beside BFS.  The length of a stored entry (u, v) is its payload when
+ * `weighted` is non-zero, else 1 (so the result equals orc_bfs's distances).
+ * dist[source] = 0 if the source is alive; dist[v] = min over stored entries
+ * (u, v) of dist[u] + length; unreached (and every vertex when the source is
+ * dead) = UINT64_MAX.  Returns the number of reached vertices.
+ */
+typedef struct {
+    uint64_t d;
+    uint32_t v;
+} orc_heap_item;
+
+static void heap_push(orc_heap_item *h, uint64_t *n, orc_heap_item x) {
+    uint64_t i = (*n)++;
+    while (i > 0) {
+        const uint64_t p = (i - 1) / 2;
+        if (h[p].d <= x.d) break;
+        h[i] = h[p];
+        i = p;
+    }
+    h[i] = x;
+}
+
+static orc_heap_item heap_pop(orc_heap_item *h, uint64_t *n) {
+    const orc_heap_item top = h[0];
+    const orc_heap_item last = h[--(*n)];
+    uint64_t i = 0;
+    for (;;) {
+        uint64_t c = 2 * i + 1;
+        if (c >= *n) break;
+        if (c + 1 < *n && h[c + 1].d < h[c].d) ++c;
+        if (last.d <= h[c].d) break;
+        h[i] = h[c];
+        i = c;
+    }
+    if (*n > 0) h[i] = last;
+    return top;
+}
+
+uint32_t orc_sssp(const orc_graph *g, uint32_t source, int weighted, uint64_t *dist) {
+    for (uint32_t v = 0; v < g->nv; ++v) dist[v] = UINT64_MAX;
+    if (source >= g->nv || !g->alive[source]) return 0;
+    /* one heap entry per improvement: at most num_edges + 1 */
+    orc_heap_item *h = (orc_heap_item *)malloc(sizeof(orc_heap_item) * (g->num_edges + 1));
+    uint8_t *done = (uint8_t *)calloc(g->nv, 1);
+    uint64_t n = 0;
+    uint32_t reached = 0;
+    dist[source] = 0;
+    heap_push(h, &n, (orc_heap_item){0, source});
+    while (n > 0) {
+        const orc_heap_item x = heap_pop(h, &n);
+        if (done[x.v] || x.d != dist[x.v]) continue;
+        done[x.v] = 1;
+        ++reached;
+        const orc_adj *a = &g->adj[x.v];
+        for (uint64_t j = 0; j < a->n; ++j) {
+            const uint32_t v = a->v[j];
+            const uint64_t nd = x.d + (weighted ? (uint64_t)a->w[j] : 1u);
+            if (nd < dist[v]) {
+                dist[v] = nd;
+                heap_push(h, &n, (orc_heap_item){nd, v});
+            }
+        }
+    }
+    free(h);
+    free(done);
+    return reached;
+}
