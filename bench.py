@@ -744,6 +744,40 @@ def run_rows(args):
         iters * (4 * E + 8 * E + 48 * nv))
     g.close()
 
+    # f2 (shortest paths): the base graph with a 32-bit length per entry,
+    # lengths spread over [0, 1000) by a multiplicative hash of the position
+    gs = gv.Graph(nv, block_capacity=C, pool_bytes=POOL_BYTES, flags=gv.GV_WEIGHTED)
+    gs.reserve(BASE_EDGES)
+    d_bw = t((np.arange(bs.size, dtype=np.uint64) * 2654435761 % 1000).astype(np.uint32))
+    gs.insert_edges_weighted(d_bs, d_bd, d_bw, cnt)
+    sdist = torch.zeros(nv, dtype=torch.int64, device="cuda")
+    rounds = []
+    ms = timed(lambda: rounds.append(gv.gv_sssp(gs.handle, src, sdist, stream.cuda_stream)), n=3)
+    sreached = sdist.cpu().numpy().view(np.uint64) != np.uint64(0xFFFFFFFFFFFFFFFF)
+    strav = int(deg0[sreached].sum())
+    row("f2-sssp", f"shortest paths from vertex {src}, lengths in [0, 1000) ({int(sreached.sum())} reached, "
+        f"{rounds[-1]} relaxation rounds)", strav, "traversed edges", ms,
+        16 * strav + 16 * int(sreached.sum()) + 12 * nv, timer="CUDA events (one host read per four rounds)")
+    gs.close()
+
+    # f3 (dynamic edge-block size): re-block the base graph from C to the
+    # paper's rule over its degrees (and back, untimed, before each repeat)
+    gr = gv.Graph(nv, block_capacity=C, pool_bytes=POOL_BYTES)
+    gr.bulk_build(d_bs, d_bd, cnt)
+    torch.cuda.synchronize()
+    used_c = gr.stats()["pool_blocks_used"]
+    c_rule = gr.reblock(0)
+    used_r = gr.stats()["pool_blocks_used"]
+    ms = timed(lambda: gr.reblock(c_rule), pre=lambda: gr.reblock(C))
+    E0 = int(deg0.sum())
+    P_r = gr.stats()["pool_blocks"]
+    row("f3-reblock", f"re-block {E0} entries from C={C} to C={c_rule} (the block-size rule over current degrees)",
+        E0, "entries", ms, 8 * E0 + 32 * nv + 8 * used_r + 4 * P_r,
+        timer="CUDA events (the call synchronises twice: degree totals, slot total)",
+        footprint={"slots_allocated_at_C": used_c * C, "slots_allocated_at_rule": used_r * c_rule,
+                   "entries": E0, "block_capacity_rule": c_rule})
+    gr.close()
+
     # f1: set-semantics insert of the 10M batch (half of it already stored)
     # on a GV_DEDUP graph: membership pass over the stored blocks + insert
     gd = gv.Graph(nv, block_capacity=C, pool_bytes=POOL_BYTES, flags=gv.GV_DEDUP)

@@ -415,13 +415,37 @@ gv_status gv_set_member_neighbors(gv_graph *set, uint32_t member, uint64_t *offs
 gv_status gv_degree_offsets_noalloc(gv_graph *g, const uint32_t *d_vids, uint32_t n, uint64_t *d_offsets,
                                     void *stream);
 
+/*
+ * gv_reblock -- change the edge-block size C of a built graph ("dynamically
+ * changing the edge block size", the paper's future work: the average
+ * degree, and with it the best C, drifts over many batch updates).  Every
+ * stored entry (with its payload) stays; only the blocking changes: each
+ * vertex gets ceil(deg / C) blocks of the new size, taken as one contiguous
+ * run of the pool, and the pool memory (the same bytes: library-owned,
+ * grown, or the caller's pool_mem) is laid out again for the new C.
+ *   block_capacity  the new C: a multiple of 4 in [4, 512], or 0 for the
+ *                   paper's rule over the current degrees ("Initialization":
+ *                   the average degree of the vertices with at least one
+ *                   entry, rounded up to a multiple of 4, at least 4).
+ *   h_block_capacity optional host uint32: the C now in use.
+ * Returns GV_ERR_STATE if no edge batch has fixed C yet, a latched device
+ * error if one is pending, GV_ERR_OUT_OF_MEMORY if the entries do not fit
+ * the pool at the new size or the scratch cannot be allocated -- all three
+ * before anything changes -- and GV_ERR_CUDA if a copy fails after the
+ * layout was switched (the graph is then undefined).
+ * Scratch: device arrays of 4 bytes per slot of the new layout (8 on a
+ * weighted graph) plus 8 bytes per vertex, freed before the call returns.
+ * Synchronises `stream` (it reads the degree totals).
+ */
+gv_status gv_reblock(gv_graph *g, uint32_t block_capacity, uint32_t *h_block_capacity, void *stream);
+
 /* gv_status_string -- a static, human-readable name for a status code. */
 const char *gv_status_string(gv_status s);
 
 /*
  * Graph analytics over the stored structure.  The paper lists analytics on
  * the dynamic structure as future work ("Conclusion and future work") and
- * defines none; both calls compute the textbook quantities, reading each
+ * defines none; these calls compute the textbook quantities, reading each
  * adjacency through its tree of edge blocks as the delete and query paths do.
  *
  * gv_bfs -- unweighted single-source distances (level-synchronous
@@ -432,9 +456,28 @@ const char *gv_status_string(gv_status s);
  *             dist[v] = length of a shortest path of stored edges, and
  *             0xFFFFFFFF for unreached vertices.
  *   h_levels  optional host uint32: number of distinct finite distances.
- * Synchronises `stream` once per level (it reads the frontier size).
+ * Synchronises `stream` once per four levels (it reads the frontier size).
  */
 gv_status gv_bfs(gv_graph *g, uint32_t source, uint32_t *dist, uint32_t *h_levels, void *stream);
+
+/*
+ * gv_sssp -- single-source shortest path lengths (the paper's future work
+ * names shortest paths beside BFS).  The length of a stored entry is its
+ * 32-bit payload on a graph created with GV_WEIGHTED (0 for entries inserted
+ * without one) and 1 otherwise, so on an unweighted graph the result equals
+ * gv_bfs's distances.  Computed by Bellman-Ford rounds over a frontier of
+ * vertices whose distance fell; the distances are unique, the number of
+ * rounds depends on the order of the atomic minima.
+ *   source    a vertex id < the vertex count (else GV_ERR_INVALID_ARG); a
+ *             deleted source reaches nothing.
+ *   dist      n uint64 (device or host), n = vertex count: dist[source] = 0,
+ *             dist[v] = minimum over paths of stored entries of the summed
+ *             lengths, and 0xFFFFFFFFFFFFFFFF for unreached vertices.
+ *   h_rounds  optional host uint32: relaxation rounds that had a non-empty
+ *             frontier.
+ * Synchronises `stream` once per four rounds (it reads the frontier size).
+ */
+gv_status gv_sssp(gv_graph *g, uint32_t source, uint64_t *dist, uint32_t *h_rounds, void *stream);
 
 /*
  * gv_pagerank -- `iterations` steps of PageRank power iteration in fp64 over

@@ -1,11 +1,13 @@
-// Graph analytics over the stored structure: breadth-first search distances
-// and PageRank.  The paper names analytics on the dynamic structure as
-// future work ("Conclusion and future work"); the definitions are the
-// textbook ones (level-synchronous BFS; PageRank power iteration with
-// damping, dangling mass spread over all live vertices, gathered over an
-// incoming-edge CSR built once per call).
+// Graph analytics over the stored structure: breadth-first search
+// distances, single-source shortest paths and PageRank.  The paper names
+// analytics on the dynamic structure (BFS, shortest paths) as future work
+// ("Conclusion and future work"); the definitions are the textbook ones
+// (level-synchronous BFS; Bellman-Ford shortest paths over a frontier of
+// improved vertices; PageRank power iteration with damping, dangling mass
+// spread over all live vertices, gathered over an incoming-edge CSR built
+// once per call).
 //
-// Both read adjacencies the way the delete and query pipelines do: work
+// All read adjacencies the way the delete and query pipelines do: work
 // items of up to AIB blocks of one vertex, one warp per item, block ids by
 // lane-parallel walks of the vertex's complete binary tree ("Dynamic edge
 // inserts", bit-string rule), entries by 16-byte streaming loads.
@@ -16,10 +18,11 @@ namespace gv {
 
 namespace {
 
-// Calls f(e4, vm) once per round of 32 quads of the item's stored entries
-// (all lanes call it: f may use warp collectives); vm bit j = entry j of the
-// lane's quad is a stored entry.  Returns false if a tree walk left the pool.
-template <typename F>
+// Calls f(e4, vm) -- f(e4, w4, vm) with WTS, w4 the entries' payloads --
+// once per round of 32 quads of the item's stored entries (all lanes call
+// it: f may use warp collectives); vm bit j = entry j of the lane's quad is a
+// stored entry.  Returns false if a tree walk left the pool.
+template <bool WTS = false, typename F>
 __device__ __forceinline__ bool for_item_entries(const GraphView &g, uint32_t u, uint32_t c, uint32_t aib,
                                                  uint32_t *sb, F &&f) {
     const uint4 s = g.sent[u];
@@ -40,16 +43,22 @@ __device__ __forceinline__ bool for_item_entries(const GraphView &g, uint32_t u,
     for (uint32_t q0 = 0; q0 < nquads; q0 += 32) {
         const uint32_t q = q0 + lane;
         uint4 e4 = make_uint4(NIL, NIL, NIL, NIL);
+        uint4 w4 = make_uint4(0, 0, 0, 0);
         uint32_t vm = 0;
         if (q < nquads) {
             const uint32_t x = q << 2;
             const uint32_t lb = divc(g.cmul, x);
-            e4 = ld_stream4(reinterpret_cast<const uint4 *>(g.data + (size_t)sb[lb] * C + (x - lb * C)));
+            const size_t off = (size_t)sb[lb] * C + (x - lb * C);
+            e4 = ld_stream4(reinterpret_cast<const uint4 *>(g.data + off));
+            if constexpr (WTS) w4 = ld_stream4(reinterpret_cast<const uint4 *>(g.wdata + off));
 #pragma unroll
             for (uint32_t j = 0; j < 4; ++j)
                 if (x + j < nslots) vm |= 1u << j;
         }
-        f(e4, vm);
+        if constexpr (WTS)
+            f(e4, w4, vm);
+        else
+            f(e4, vm);
     }
     __syncwarp();
     return true;
@@ -167,6 +176,108 @@ cudaError_t launch_bfs_level(const GraphView &g, uint32_t aib, const uint32_t *c
     k_an_items<<<grid, 256, 0, lc.stream>>>(g, cur, ctr, aib, items, ctr + 1);
     k_bfs_expand<<<grid, 256, 0, lc.stream>>>(g, items, ctr + 1, aib, dist, level, next, ctr + 2);
     k_bfs_advance<<<1, 32, 0, lc.stream>>>(ctr, level);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------ single-source shortest paths
+
+// Frontier Bellman-Ford with atomic minima: the frontier of round r holds
+// the vertices whose distance fell in round r - 1; each of their stored
+// entries (u, v) offers dist[u] + length to v (payload on a weighted graph,
+// 1 otherwise), taken by a 64-bit atomicMin.  A vertex whose distance fell
+// joins the next frontier once per round (stamp[v] = r + 1 by exchange).
+// Distances are lengths of real paths and every fall is propagated, so the
+// fixpoint is the shortest-path distance whatever the order of the minima;
+// with non-negative lengths it is reached within nv rounds.
+
+__global__ void k_sssp_seed(GraphView g, uint32_t source, unsigned long long *dist, uint32_t *cur, uint32_t *ctr) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const bool live = source < g.nv && g.alive[source];
+        if (live) {
+            dist[source] = 0ull;
+            cur[0] = source;
+        }
+        ctr[0] = live ? 1u : 0u;  // frontier size
+        ctr[1] = 0;               // items
+        ctr[2] = 0;               // next frontier size
+        ctr[3] = live ? 1u : 0u;  // rounds with a non-empty frontier
+    }
+}
+
+template <bool WEIGHTED>
+__global__ void __launch_bounds__(256) k_sssp_relax(GraphView g, const uint2 *__restrict__ items,
+                                                    const uint32_t *nitems, uint32_t aib, unsigned long long *dist,
+                                                    uint32_t *stamp, uint32_t round, uint32_t *next,
+                                                    uint32_t *nnext) {
+    __shared__ uint32_t s_bid[8][32];
+    const uint32_t n = *nitems;
+    const uint32_t lane = lane_id();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t nv = g.nv;
+    for (uint32_t it = warp; it < n; it += nwarps) {
+        const uint2 itm = items[it];
+        const unsigned long long du = __ldcg(dist + itm.x);
+        bool bad = false;
+        auto relax = [&](uint4 e4, uint4 w4, uint32_t vm) {
+            const uint32_t e[4] = {e4.x, e4.y, e4.z, e4.w};
+            const uint32_t w[4] = {w4.x, w4.y, w4.z, w4.w};
+            uint32_t push = 0;
+#pragma unroll
+            for (uint32_t j = 0; j < 4; ++j) {
+                if ((vm >> j) & 1u) {
+                    const uint32_t v = e[j];
+                    const unsigned long long nd = du + (WEIGHTED ? (unsigned long long)w[j] : 1ull);
+                    if (v >= nv) {
+                        bad = true;
+                    } else if (nd < __ldcg(dist + v) && nd < atomicMin(dist + v, nd) &&
+                               atomicExch(stamp + v, round + 1) != round + 1) {
+                        push |= 1u << j;
+                    }
+                }
+            }
+            uint32_t tot;
+            const uint32_t ex = warp_excl_scan(__popc(push), &tot);
+            uint32_t base = 0;
+            if (lane == 0 && tot) base = atomicAdd(nnext, tot);
+            base = __shfl_sync(FULL, base, 0);
+            uint32_t o = base + ex;
+#pragma unroll
+            for (uint32_t j = 0; j < 4; ++j)
+                if ((push >> j) & 1u) next[o++] = e[j];
+        };
+        bool ok;
+        if constexpr (WEIGHTED)
+            ok = for_item_entries<true>(g, itm.x, itm.y, aib, s_bid[threadIdx.x >> 5], relax);
+        else
+            ok = for_item_entries(g, itm.x, itm.y, aib, s_bid[threadIdx.x >> 5],
+                                  [&](uint4 e4, uint32_t vm) { relax(e4, make_uint4(1, 1, 1, 1), vm); });
+        if ((!ok || bad) && lane == 0) latch_status(g.dev, 5u /* GV_ERR_STATE */);
+    }
+}
+
+cudaError_t launch_sssp_seed(const GraphView &g, uint32_t source, unsigned long long *dist, uint32_t *stamp,
+                             uint32_t *cur, uint32_t *ctr, const LaunchCfg &lc) {
+    PhaseScope ps(lc, PH_ANALYTICS);
+    if (g.nv) {
+        cudaMemsetAsync(dist, 0xFF, (size_t)g.nv * 8, lc.stream);
+        cudaMemsetAsync(stamp, 0, (size_t)g.nv * 4, lc.stream);
+    }
+    k_sssp_seed<<<1, 32, 0, lc.stream>>>(g, source, dist, cur, ctr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sssp_round(const GraphView &g, uint32_t aib, const uint32_t *cur, uint32_t *next, uint2 *items,
+                              uint32_t *ctr, unsigned long long *dist, uint32_t *stamp, uint32_t round,
+                              const LaunchCfg &lc) {
+    PhaseScope ps(lc, PH_ANALYTICS);
+    const int grid = lc.num_sms * GRID_MULT;
+    k_an_items<<<grid, 256, 0, lc.stream>>>(g, cur, ctr, aib, items, ctr + 1);
+    if (g.wdata)
+        k_sssp_relax<true><<<grid, 256, 0, lc.stream>>>(g, items, ctr + 1, aib, dist, stamp, round, next, ctr + 2);
+    else
+        k_sssp_relax<false><<<grid, 256, 0, lc.stream>>>(g, items, ctr + 1, aib, dist, stamp, round, next, ctr + 2);
+    k_bfs_advance<<<1, 32, 0, lc.stream>>>(ctr, round);
     return cudaGetLastError();
 }
 

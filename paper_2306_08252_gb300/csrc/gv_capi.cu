@@ -98,6 +98,8 @@ struct gv_graph {
     unsigned long long an_icap = 0, an_vcap = 0;
     uint2 *an_items = nullptr;
     uint32_t *an_cur = nullptr, *an_next = nullptr, *an_ctr = nullptr;
+    uint32_t *an_stamp = nullptr;  // shortest paths: round in which a vertex last joined the frontier
+    unsigned long long *rb_stats = nullptr;  // edge-block resize: {entries, non-empty vertices}
     double *pr_c = nullptr, *pr_acc = nullptr, *pr_scal = nullptr;
     unsigned long long *pr_n = nullptr;
     // PageRank's incoming-edge CSR: per-vertex cursor, offsets, chunk sums,
@@ -379,12 +381,59 @@ unsigned long long item_bound(const gv_graph *g, unsigned long long touched) {
     return touched + (g->IB ? (g->P + g->IB - 1) / g->IB : 0) + 1;
 }
 
+// End of the laid-out pool arrays for P blocks of C slots: slots, payloads
+// (weighted graphs), links and queue, each starting on a 256-byte boundary.
+uint64_t layout_end(unsigned long long P, uint32_t C, bool weighted) {
+    auto al = [](uint64_t x) { return (x + 255) & ~255ull; };
+    uint64_t off = al(P * C * 4ull);
+    if (weighted) off = al(off + P * C * 4ull);
+    off = al(off + P * 8ull);
+    return off + P * 4ull;
+}
+
+// The largest block count whose layout fits in `bytes` (every array must lie
+// inside the allocation: the queue is written in full).
+unsigned long long fit_blocks(uint64_t bytes, uint32_t C, bool weighted) {
+    const uint64_t per_block = 4ull * C * (weighted ? 2 : 1) + 8 + 4;
+    unsigned long long P = bytes / per_block;
+    if (P > 0xFFFFFFFEull) P = 0xFFFFFFFEull;
+    while (P > 0 && layout_end(P, C, weighted) > bytes) --P;
+    return P;
+}
+
+// Points the graph's pool arrays into `base` for P blocks of C slots; false
+// if that layout does not fit in `bytes`.
+bool lay_out_pool(gv_graph *g, char *base, uint64_t bytes, uint32_t C, unsigned long long P) {
+    const bool weighted = (g->flags & GV_WEIGHTED) != 0;
+    if (layout_end(P, C, weighted) > bytes) return false;
+    auto align = [](uint64_t x) { return (x + 255) & ~255ull; };
+    uint64_t off = 0;
+    g->data = reinterpret_cast<uint32_t *>(base + off);
+    off = align(off + P * C * 4ull);
+    g->wdata = nullptr;
+    if (weighted) {
+        g->wdata = reinterpret_cast<uint32_t *>(base + off);
+        off = align(off + P * C * 4ull);
+    }
+    g->links = reinterpret_cast<uint32_t *>(base + off);
+    off = align(off + P * 8ull);
+    g->queue = reinterpret_cast<uint32_t *>(base + off);
+    g->C = C;
+    g->P = P;
+    return true;
+}
+
+// Blocks per work item of the delete / query pipelines: up to 512 slots.
+void set_item_blocks(gv_graph *g) {
+    g->IB = std::min<uint32_t>(32, std::max<uint32_t>(1, 512 / g->C));
+    if (g->item_blocks_cfg) g->IB = std::min<uint32_t>(g->IB, g->item_blocks_cfg);
+}
+
 // Pool: one allocation holding block storage, links and the edge queue.
 gv_status setup_pool(gv_graph *g, uint32_t C, cudaStream_t s) {
     if (C < 4 || C > 512 || (C % 4) != 0) return GV_ERR_INVALID_ARG;
     g->C = C;
-    g->IB = std::min<uint32_t>(32, std::max<uint32_t>(1, 512 / C));
-    if (g->item_blocks_cfg) g->IB = std::min<uint32_t>(g->IB, g->item_blocks_cfg);
+    set_item_blocks(g);
     uint64_t bytes = g->pool_bytes_cfg;
     if (bytes == 0) {
         size_t fr = 0, tot = 0;
@@ -392,21 +441,7 @@ gv_status setup_pool(gv_graph *g, uint32_t C, cudaStream_t s) {
         bytes = fr / 2;  // "Edge Queue": at least half of the GPU memory
     }
     const bool weighted = (g->flags & GV_WEIGHTED) != 0;
-    const uint64_t per_block = 4ull * C * (weighted ? 2 : 1) + 8 + 4;
-    // End of the laid-out arrays for P blocks: slots, payloads (weighted
-    // graphs), links and queue, each starting on a 256-byte boundary.  The
-    // largest P whose layout fits in `bytes` is taken (every array must lie
-    // inside the allocation: the queue is written in full below).
-    auto layout_end = [&](unsigned long long P) {
-        auto al = [](uint64_t x) { return (x + 255) & ~255ull; };
-        uint64_t off = al(P * C * 4ull);
-        if (weighted) off = al(off + P * C * 4ull);
-        off = al(off + P * 8ull);
-        return off + P * 4ull;
-    };
-    unsigned long long P = bytes / per_block;
-    if (P > 0xFFFFFFFEull) P = 0xFFFFFFFEull;
-    while (P > 0 && layout_end(P) > bytes) --P;
+    const unsigned long long P = fit_blocks(bytes, C, weighted);
     if (P == 0) return GV_ERR_INVALID_ARG;
     char *base = nullptr;
     if (g->pool_mem_cfg) {
@@ -421,19 +456,7 @@ gv_status setup_pool(gv_graph *g, uint32_t C, cudaStream_t s) {
         g->pool_alloc = p;
         base = static_cast<char *>(p);
     }
-    auto align = [](uint64_t x) { return (x + 255) & ~255ull; };
-    uint64_t off = 0;
-    g->data = reinterpret_cast<uint32_t *>(base + off);
-    off = align(off + P * C * 4ull);
-    if (weighted) {
-        g->wdata = reinterpret_cast<uint32_t *>(base + off);
-        off = align(off + P * C * 4ull);
-    }
-    g->links = reinterpret_cast<uint32_t *>(base + off);
-    off = align(off + P * 8ull);
-    g->queue = reinterpret_cast<uint32_t *>(base + off);
-    if (off + P * 4ull > bytes) return GV_ERR_STATE;  // cannot happen: P was fitted to this layout
-    g->P = P;
+    if (!lay_out_pool(g, base, bytes, C, P)) return GV_ERR_STATE;  // cannot happen: P was fitted
     g->pool_bytes = bytes;
     GV_CK(gv::launch_init_queue(g->queue, P, lcfg(g, s)));
     // Dev: queue holds every block
@@ -917,7 +940,7 @@ gv_status gv_destroy(gv_graph *g) {
         dfree(g->owner_bits); dfree(g->vres);
         dfree(g->set_vbase); dfree(g->set_src); dfree(g->set_dst);
         dfree(g->pflag); dfree(g->dsrc2); dfree(g->dtmp);
-        dfree(g->an_items); dfree(g->an_cur); dfree(g->an_next); dfree(g->an_ctr);
+        dfree(g->an_items); dfree(g->an_cur); dfree(g->an_next); dfree(g->an_ctr); dfree(g->an_stamp); dfree(g->rb_stats);
         dfree(g->pr_c); dfree(g->pr_acc); dfree(g->pr_scal); dfree(g->pr_n);
         dfree(g->pr_cursor); dfree(g->pr_src); dfree(g->pr_dst); dfree(g->pr_off); dfree(g->pr_part);
         for (auto &b : g->stage.buf) dfree(b.p);
@@ -1065,6 +1088,119 @@ gv_status gv_reserve(gv_graph *g, uint64_t max_batch) {
         GV_TRY(stage_buf(g, slot, max_batch * 4 + 64, &d));
     }
     return GV_OK;
+}
+
+gv_status gv_reblock(gv_graph *g, uint32_t block_capacity, uint32_t *h_block_capacity, void *stream) {
+    if (!g) return GV_ERR_INVALID_ARG;
+    if (block_capacity && (block_capacity < 4 || block_capacity > 512 || block_capacity % 4)) return GV_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (g->C == 0) return GV_ERR_STATE;  // nothing laid out yet: the first edge batch fixes C
+    // a latched device error is reported first; nothing changes
+    GV_CK(cudaStreamSynchronize(g->last_stream));
+    g->last_stream = s;
+    GV_CK(cudaMemcpyAsync(&g->h_small[0], &g->dev->status, 4, cudaMemcpyDeviceToHost, s));
+    GV_CK(cudaStreamSynchronize(s));
+    const unsigned int st0 = (unsigned int)(g->h_small[0] & 0xFFFFFFFFull);
+    if (st0) return static_cast<gv_status>(st0);
+    const uint32_t n = g->nv;
+    const bool weighted = (g->flags & GV_WEIGHTED) != 0;
+
+    // 1. the new C: given, or the paper's rule over the current degrees
+    if (!g->rb_stats) GV_TRY(dalloc(&g->rb_stats, 2, &g->scratch_bytes));
+    GV_CK(gv::launch_degree_stats(view(g), g->rb_stats, lcfg(g, s)));
+    GV_CK(cudaMemcpyAsync(&g->h_small[0], g->rb_stats, 16, cudaMemcpyDeviceToHost, s));
+    GV_CK(cudaStreamSynchronize(s));
+    const uint32_t C2 = block_capacity ? block_capacity : rule_capacity(g->h_small[0], g->h_small[1]);
+    const unsigned long long P2 = fit_blocks(g->pool_bytes, C2, weighted);
+
+    // 2. slot offsets of the new layout (each vertex's degree rounded up to
+    // whole blocks of C2): the run of u starts at block slots[u] / C2
+    unsigned long long *slots = nullptr;
+    uint32_t *nd = nullptr, *nw = nullptr;
+    auto release = [&]() {
+        dfree(slots);
+        dfree(nd);
+        dfree(nw);
+    };
+    void *dv = nullptr;
+    GV_TRY(stage_buf(g, 0, (size_t)n * 4 + 4, &dv));
+    GV_CK(gv::launch_iota((uint32_t *)dv, 0, n, lcfg(g, s)));
+    const unsigned long long nchunks = ((unsigned long long)n + 1023) / 1024;
+    if (nchunks + 1 > g->pcap) {
+        dfree(g->partials);
+        g->pcap = 0;
+        GV_TRY(dalloc(&g->partials, nchunks + 1, &g->scratch_bytes));
+        g->pcap = nchunks + 1;
+    }
+    uint64_t acct = 0;
+    GV_TRY(dalloc(&slots, (size_t)n + 1, &acct));
+    gv_status st = GV_OK;
+    if (gv::launch_neighbor_offsets(view(g), (const uint32_t *)dv, n, slots, g->partials, lcfg(g, s), C2) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(&g->h_small[0], slots + n, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        release();
+        return GV_ERR_CUDA;
+    }
+    const unsigned long long T = g->h_small[0];  // slots of the new layout
+    const unsigned long long nb2 = T / C2;
+    if (nb2 > P2) {  // the entries do not fit the pool at this block size
+        release();
+        return GV_ERR_OUT_OF_MEMORY;
+    }
+    if (nb2 > 0xFFFFFFFEull) {
+        release();
+        return GV_ERR_OUT_OF_MEMORY;
+    }
+
+    // 3. every entry (and payload) copied to its place in the new layout,
+    // read through the old trees
+    if ((st = dalloc(&nd, std::max<unsigned long long>(T, 4), &acct)) != GV_OK ||
+        (weighted && (st = dalloc(&nw, std::max<unsigned long long>(T, 4), &acct)) != GV_OK) ||
+        (st = ensure_touched(g, n)) != GV_OK || (st = ensure_items(g, item_bound(g, n))) != GV_OK) {
+        release();
+        return st;
+    }
+    // the unused tail slots of each run's last block hold NIL
+    if (cudaMemsetAsync(nd, 0xFF, T * 4ull, s) != cudaSuccess ||
+        (n && gv::launch_neighbor_copy(view(g), (const uint32_t *)dv, n, slots, nd, lcfg(g, s), nw) != cudaSuccess)) {
+        release();
+        return GV_ERR_CUDA;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        release();
+        return GV_ERR_CUDA;
+    }
+
+    // 4. the same pool memory laid out for C2: slots back in place, trees
+    // and sentinels over the runs, the queue holding the blocks past them
+    char *base = reinterpret_cast<char *>(g->data);
+    if (!lay_out_pool(g, base, g->pool_bytes, C2, P2)) {
+        release();
+        return GV_ERR_STATE;  // cannot happen: P2 was fitted to this layout
+    }
+    set_item_blocks(g);
+    const GraphView v = view(g);
+    bool ok = true;
+    if (T) ok = ok && cudaMemcpyAsync(g->data, nd, T * 4ull, cudaMemcpyDeviceToDevice, s) == cudaSuccess;
+    if (T && weighted) ok = ok && cudaMemcpyAsync(g->wdata, nw, T * 4ull, cudaMemcpyDeviceToDevice, s) == cudaSuccess;
+    ok = ok && gv::launch_reblock_place(v, slots, lcfg(g, s)) == cudaSuccess;
+    ok = ok && gv::launch_init_queue(g->queue, P2, lcfg(g, s)) == cudaSuccess;
+    g->h_small[2] = nb2;
+    g->h_small[3] = P2;
+    ok = ok && cudaMemcpyAsync(&g->dev->q_front, &g->h_small[2], 8, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(&g->dev->q_back, &g->h_small[3], 8, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
+    release();
+    if (!ok) return GV_ERR_CUDA;
+    g->used_ub = nb2;
+    // work-item scratch is sized by the blocks per item, which follow C
+    dfree(g->items); dfree(g->it_mask); dfree(g->it_cnt); dfree(g->it_H); dfree(g->it_S); dfree(g->it_bid);
+    g->icap = 0;
+    GV_TRY(ensure_items(g, item_bound(g, 1024)));
+    if (h_block_capacity) *h_block_capacity = C2;
+    return check_launch();
 }
 
 gv_status gv_sync(gv_graph *g) {
@@ -1388,7 +1524,7 @@ uint32_t analytics_item_blocks(const gv_graph *g) {
     return g->C ? std::min<uint32_t>(32, std::max<uint32_t>(1, 512 / g->C)) : 32;
 }
 
-gv_status ensure_analytics(gv_graph *g, bool pagerank) {
+gv_status ensure_analytics(gv_graph *g, bool pagerank, bool sssp = false) {
     const uint32_t aib = analytics_item_blocks(g);
     const unsigned long long items = (unsigned long long)g->nv + (g->P + aib - 1) / aib + 1;
     if (items > g->an_icap || !g->an_icap) {
@@ -1399,13 +1535,14 @@ gv_status ensure_analytics(gv_graph *g, bool pagerank) {
     }
     const unsigned long long nv = std::max<unsigned long long>(g->nv, 1);
     if (nv > g->an_vcap || !g->an_vcap) {
-        dfree(g->an_cur); dfree(g->an_next); dfree(g->pr_c); dfree(g->pr_acc);
+        dfree(g->an_cur); dfree(g->an_next); dfree(g->pr_c); dfree(g->pr_acc); dfree(g->an_stamp);
         g->an_vcap = 0;
         GV_TRY(dalloc(&g->an_cur, nv, &g->scratch_bytes));
         GV_TRY(dalloc(&g->an_next, nv, &g->scratch_bytes));
         g->an_vcap = nv;
     }
     if (!g->an_ctr) GV_TRY(dalloc(&g->an_ctr, 4, &g->scratch_bytes));
+    if (sssp && !g->an_stamp) GV_TRY(dalloc(&g->an_stamp, g->an_vcap, &g->scratch_bytes));
     if (pagerank) {
         if (!g->pr_c) GV_TRY(dalloc(&g->pr_c, g->an_vcap, &g->scratch_bytes));
         if (!g->pr_acc) GV_TRY(dalloc(&g->pr_acc, g->an_vcap, &g->scratch_bytes));
@@ -1449,6 +1586,43 @@ gv_status gv_bfs(gv_graph *g, uint32_t source, uint32_t *dist, uint32_t *h_level
         GV_CK(cudaStreamSynchronize(s));
     }
     if (h_levels) *h_levels = levels;
+    return check_launch();
+}
+
+gv_status gv_sssp(gv_graph *g, uint32_t source, uint64_t *dist, uint32_t *h_rounds, void *stream) {
+    if (!g || !dist || source >= g->nv) return GV_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    g->last_stream = s;
+    GV_TRY(ensure_analytics(g, false, true));
+    void *dd = dist;
+    bool hd = false;
+    GV_TRY(output_ptr(g, 0, dist, (size_t)g->nv * 8, &dd, &hd));
+    const GraphView v = view(g);
+    const uint32_t aib = analytics_item_blocks(g);
+    unsigned long long *ddist = static_cast<unsigned long long *>(dd);
+    GV_CK(gv::launch_sssp_seed(v, source, ddist, g->an_stamp, g->an_cur, g->an_ctr, lcfg(g, s)));
+    uint32_t *cur = g->an_cur, *nxt = g->an_next;
+    // rounds go out in groups between two reads of the frontier size, as
+    // the BFS levels do; with non-negative lengths round nv finds an empty
+    // frontier
+    constexpr uint32_t kGroup = 4;
+    for (uint32_t round = 0; round <= g->nv;) {
+        for (uint32_t k = 0; k < kGroup; ++k, ++round) {
+            GV_CK(gv::launch_sssp_round(v, aib, cur, nxt, g->an_items, g->an_ctr, ddist, g->an_stamp, round,
+                                        lcfg(g, s)));
+            std::swap(cur, nxt);
+        }
+        GV_CK(cudaMemcpyAsync(g->h_small, g->an_ctr, 16, cudaMemcpyDeviceToHost, s));
+        GV_CK(cudaStreamSynchronize(s));
+        if ((uint32_t)(g->h_small[0] & 0xFFFFFFFFull) == 0) break;  // frontier empty
+    }
+    const uint32_t rounds = (uint32_t)(g->h_small[1] >> 32);  // ctr[3]
+    if (hd) {
+        GV_CK(cudaMemcpyAsync(dist, dd, (size_t)g->nv * 8, cudaMemcpyDeviceToHost, s));
+        GV_CK(cudaStreamSynchronize(s));
+    }
+    if (h_rounds) *h_rounds = rounds;
     return check_launch();
 }
 

@@ -115,9 +115,15 @@ cudaError_t launch_copy_dictionary(uint4 *dst_sent, uint8_t *dst_alive, const ui
 // Edge queue initialisation: queue[i] = i.
 cudaError_t launch_init_queue(uint32_t *queue, unsigned long long P, const LaunchCfg &lc);
 // Neighbour lists: offsets (exclusive scan of degrees), then copy.
+// offsets[i] = sum over vids[0 .. i-1] of the degree (rounded up to a
+// multiple of round_to when that is non-zero); offsets[n] = the total.
 cudaError_t launch_neighbor_offsets(const GraphView &g, const uint32_t *vids, uint32_t n,
                                     unsigned long long *offsets, unsigned long long *partials,
-                                    const LaunchCfg &lc);
+                                    const LaunchCfg &lc, uint32_t round_to = 0);
+// Edge-block resize: res[0..1] = {entries, non-empty live vertices}; then the
+// trees and sentinels over contiguous block runs starting at slots[u] / C.
+cudaError_t launch_degree_stats(const GraphView &g, unsigned long long *res, const LaunchCfg &lc);
+cudaError_t launch_reblock_place(const GraphView &g, const unsigned long long *slots, const LaunchCfg &lc);
 cudaError_t launch_neighbor_copy(const GraphView &g, const uint32_t *vids, uint32_t n,
                                  const unsigned long long *offsets, uint32_t *nbrs,
                                  const LaunchCfg &lc,
@@ -144,6 +150,11 @@ cudaError_t launch_bfs_seed(const GraphView &g, uint32_t source, uint32_t *dist,
                             const LaunchCfg &lc);
 cudaError_t launch_bfs_level(const GraphView &g, uint32_t aib, const uint32_t *cur, uint32_t *next, uint2 *items,
                              uint32_t *ctr, uint32_t *dist, uint32_t level, const LaunchCfg &lc);
+cudaError_t launch_sssp_seed(const GraphView &g, uint32_t source, unsigned long long *dist, uint32_t *stamp,
+                             uint32_t *cur, uint32_t *ctr, const LaunchCfg &lc);
+cudaError_t launch_sssp_round(const GraphView &g, uint32_t aib, const uint32_t *cur, uint32_t *next, uint2 *items,
+                              uint32_t *ctr, unsigned long long *dist, uint32_t *stamp, uint32_t round,
+                              const LaunchCfg &lc);
 cudaError_t launch_pagerank(const GraphView &g, uint32_t aib, uint32_t iterations, double damping, double *r,
                             double *c, double *acc, double *scal, unsigned long long *N, uint2 *items,
                             uint32_t *nitems, uint32_t *cursor, unsigned long long *in_off,

@@ -48,18 +48,22 @@ constexpr int SCAN_T = 256;
 constexpr int SCAN_PER = 4;
 constexpr int SCAN_CHUNK = SCAN_T * SCAN_PER;
 
-__device__ __forceinline__ uint32_t vid_degree(const GraphView &g, uint32_t u) {
-    return (u < g.nv && g.alive[u]) ? g.sent[u].x : 0u;
+// Degree of a requested vertex (0 for invalid or deleted ids), rounded up to
+// a multiple of `round_to` when that is non-zero (slots of whole blocks).
+__device__ __forceinline__ unsigned long long vid_degree(const GraphView &g, uint32_t u, uint32_t round_to) {
+    const unsigned long long d = (u < g.nv && g.alive[u]) ? g.sent[u].x : 0u;
+    return round_to ? (d + round_to - 1) / round_to * round_to : d;
 }
 
 // Per-chunk sums of the requested vertices' degrees.
 __global__ void __launch_bounds__(SCAN_T) k_nbr_partials(GraphView g, const uint32_t *__restrict__ vids,
-                                                         uint32_t n, unsigned long long *partials) {
+                                                         uint32_t n, uint32_t round_to,
+                                                         unsigned long long *partials) {
     const uint32_t chunk = blockIdx.x;
     unsigned long long s = 0;
     for (int j = 0; j < SCAN_PER; ++j) {
         const uint32_t i = chunk * SCAN_CHUNK + j * SCAN_T + threadIdx.x;
-        if (i < n) s += vid_degree(g, vids[i]);
+        if (i < n) s += vid_degree(g, vids[i], round_to);
     }
     s = block_sum_u64(s);
     if (threadIdx.x == 0) partials[chunk] = s;
@@ -103,7 +107,8 @@ __global__ void __launch_bounds__(1024) k_nbr_scan_partials(unsigned long long *
 
 // offsets[i] = chunk prefix + exclusive scan inside the chunk; offsets[n] = total.
 __global__ void __launch_bounds__(SCAN_T) k_nbr_apply(GraphView g, const uint32_t *__restrict__ vids,
-                                                      uint32_t n, const unsigned long long *partials,
+                                                      uint32_t n, uint32_t round_to,
+                                                      const unsigned long long *partials,
                                                       uint32_t nchunks, unsigned long long *offsets) {
     const uint32_t chunk = blockIdx.x;
     // thread-local run over SCAN_PER consecutive elements
@@ -111,7 +116,7 @@ __global__ void __launch_bounds__(SCAN_T) k_nbr_apply(GraphView g, const uint32_
     unsigned long long s = 0;
     for (int j = 0; j < SCAN_PER; ++j) {
         const uint32_t i = chunk * SCAN_CHUNK + threadIdx.x * SCAN_PER + j;
-        v[j] = i < n ? vid_degree(g, vids[i]) : 0ull;
+        v[j] = i < n ? vid_degree(g, vids[i], round_to) : 0ull;
         s += v[j];
     }
     __shared__ unsigned long long s_w[SCAN_T / 32];
@@ -213,6 +218,59 @@ __global__ void __launch_bounds__(256) k_nbr_copy(GraphView g, const unsigned lo
 
 __global__ void k_clear_items(GraphView g) {
     if (threadIdx.x == 0 && blockIdx.x == 0) g.dev->n_items = 0;
+}
+
+// ------------------------------------------------------ edge-block resize
+
+// res[0] += stored entries of live vertices, res[1] += live vertices with at
+// least one entry (the paper's block-size rule, "Initialization").
+__global__ void __launch_bounds__(256) k_degree_stats(GraphView g, unsigned long long *res) {
+    unsigned long long e = 0, nz = 0;
+    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < g.nv; u += gridDim.x * blockDim.x) {
+        const uint32_t d = g.alive[u] ? g.sent[u].x : 0u;
+        e += d;
+        nz += d ? 1u : 0u;
+    }
+    e = block_sum_u64(e);
+    nz = block_sum_u64(nz);
+    if (threadIdx.x == 0) {
+        if (e) atomicAdd(&res[0], e);
+        if (nz) atomicAdd(&res[1], nz);
+    }
+}
+
+// Rebuilt trees over a contiguous run of blocks per vertex, one warp per
+// vertex: slots[u] = first slot of u's run (a multiple of C), the run's
+// blocks are heap positions 1 .. nblocks in id order, so block k's children
+// are the run's blocks 2k and 2k + 1 ("Dynamic edge inserts": heap-numbered
+// complete binary tree); the entries were already copied to the run.
+__global__ void __launch_bounds__(256) k_reblock_place(GraphView g, const unsigned long long *__restrict__ slots) {
+    const uint32_t lane = lane_id();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t C = g.C;
+    for (uint32_t u = warp; u < g.nv; u += nwarps) {
+        const uint32_t deg = g.alive[u] ? g.sent[u].x : 0u;
+        const uint32_t nb = (deg + C - 1) / C;
+        const uint32_t base = (uint32_t)(slots[u] / C);
+        if (lane == 0) g.sent[u] = make_uint4(deg, nb, nb ? base : NIL, nb ? base + nb - 1 : NIL);
+        for (uint32_t k = 1 + lane; k <= nb; k += 32) {
+            const uint32_t b = base + k - 1;
+            g.links[2ull * b] = 2ull * k <= nb ? base + 2 * k - 1 : NIL;
+            g.links[2ull * b + 1] = 2ull * k + 1 <= nb ? base + 2 * k : NIL;
+        }
+    }
+}
+
+cudaError_t launch_degree_stats(const GraphView &g, unsigned long long *res, const LaunchCfg &lc) {
+    cudaMemsetAsync(res, 0, 2 * sizeof(unsigned long long), lc.stream);
+    if (g.nv) k_degree_stats<<<grid_for(g.nv, 256, lc.num_sms * 8), 256, 0, lc.stream>>>(g, res);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reblock_place(const GraphView &g, const unsigned long long *slots, const LaunchCfg &lc) {
+    if (g.nv) k_reblock_place<<<grid_for(32ull * g.nv, 256, lc.num_sms * 16), 256, 0, lc.stream>>>(g, slots);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------- self-check
@@ -349,7 +407,7 @@ cudaError_t launch_degrees(const GraphView &g, uint32_t *deg, uint8_t *alive, co
 
 cudaError_t launch_neighbor_offsets(const GraphView &g, const uint32_t *vids, uint32_t n,
                                     unsigned long long *offsets, unsigned long long *partials,
-                                    const LaunchCfg &lc) {
+                                    const LaunchCfg &lc, uint32_t round_to) {
     const uint32_t nchunks = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
     if (nchunks == 0) {
         cudaMemsetAsync(offsets, 0, sizeof(unsigned long long), lc.stream);
@@ -357,9 +415,9 @@ cudaError_t launch_neighbor_offsets(const GraphView &g, const uint32_t *vids, ui
         return cudaGetLastError();
     }
     PhaseScope ps(lc, PH_NEIGHBORS);
-    k_nbr_partials<<<nchunks, SCAN_T, 0, lc.stream>>>(g, vids, n, partials);
+    k_nbr_partials<<<nchunks, SCAN_T, 0, lc.stream>>>(g, vids, n, round_to, partials);
     k_nbr_scan_partials<<<1, 1024, 0, lc.stream>>>(partials, nchunks);
-    k_nbr_apply<<<nchunks, SCAN_T, 0, lc.stream>>>(g, vids, n, partials, nchunks, offsets);
+    k_nbr_apply<<<nchunks, SCAN_T, 0, lc.stream>>>(g, vids, n, round_to, partials, nchunks, offsets);
     return cudaGetLastError();
 }
 

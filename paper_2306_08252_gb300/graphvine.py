@@ -79,6 +79,8 @@ SIGNATURES = {
     "gv_export_csr": ([c_vp, c_vp, c_vp, c_u64, ctypes.POINTER(c_u64), c_vp], ctypes.c_int),
     "gv_degrees": ([c_vp, c_vp, c_vp, c_vp], ctypes.c_int),
     "gv_bfs": ([c_vp, c_u32, c_vp, ctypes.POINTER(c_u32), c_vp], ctypes.c_int),
+    "gv_sssp": ([c_vp, c_u32, c_vp, ctypes.POINTER(c_u32), c_vp], ctypes.c_int),
+    "gv_reblock": ([c_vp, c_u32, ctypes.POINTER(c_u32), c_vp], ctypes.c_int),
     "gv_pagerank": ([c_vp, c_u32, ctypes.c_double, c_vp, c_vp], ctypes.c_int),
     "gv_reserve": ([c_vp, c_u64], ctypes.c_int),
     "gv_sync": ([c_vp], ctypes.c_int),
@@ -237,6 +239,22 @@ def gv_bfs(g, source, dist, stream=None):
     levels = c_u32(0)
     check(load().gv_bfs(g, source, ptr(dist), ctypes.byref(levels), stream), "gv_bfs")
     return levels.value
+
+
+def gv_reblock(g, block_capacity=0, stream=None):
+    """Re-block every adjacency at `block_capacity` (0: the paper's rule over
+    the current degrees); returns the block capacity now in use."""
+    c = c_u32(0)
+    check(load().gv_reblock(g, block_capacity, ctypes.byref(c), stream), "gv_reblock")
+    return c.value
+
+
+def gv_sssp(g, source, dist, stream=None):
+    """Shortest path lengths from `source` into `dist` (uint64 per vertex);
+    returns the number of relaxation rounds."""
+    rounds = c_u32(0)
+    check(load().gv_sssp(g, source, ptr(dist), ctypes.byref(rounds), stream), "gv_sssp")
+    return rounds.value
 
 
 def gv_pagerank(g, iterations, damping, rank, stream=None):
@@ -495,6 +513,19 @@ class Graph:
             dist = np.zeros(max(self.stats()["num_vertices"], 1), dtype=np.uint32)
         levels = gv_bfs(self.handle, source, dist, self._s())
         return dist, levels
+
+    def reblock(self, block_capacity=0):
+        """Change the edge-block size in place (0: the paper's rule over the
+        current degrees); returns the new block capacity."""
+        return gv_reblock(self.handle, block_capacity, self._s())
+
+    def sssp(self, source, dist=None):
+        """(dist, rounds): uint64 path lengths (2^64 - 1 = unreached); entry
+        length = payload on a weighted graph, else 1."""
+        if dist is None:
+            dist = np.zeros(max(self.stats()["num_vertices"], 1), dtype=np.uint64)
+        rounds = gv_sssp(self.handle, source, dist, self._s())
+        return dist, rounds
 
     def pagerank(self, iterations, damping=0.85, rank=None):
         if rank is None:
