@@ -771,11 +771,15 @@ def run_rows(args):
     ms = timed(lambda: gr.reblock(c_rule), pre=lambda: gr.reblock(C))
     E0 = int(deg0.sum())
     P_r = gr.stats()["pool_blocks"]
+    c_min = gr.reblock(gv.GV_REBLOCK_MIN_FOOTPRINT)
+    used_m = gr.stats()["pool_blocks_used"]
     row("f3-reblock", f"re-block {E0} entries from C={C} to C={c_rule} (the block-size rule over current degrees)",
         E0, "entries", ms, 8 * E0 + 32 * nv + 8 * used_r + 4 * P_r,
         timer="CUDA events (the call synchronises twice: degree totals, slot total)",
-        footprint={"slots_allocated_at_C": used_c * C, "slots_allocated_at_rule": used_r * c_rule,
-                   "entries": E0, "block_capacity_rule": c_rule})
+        footprint={"entries": E0, "bytes_per_block": "4C slots + 12 links and queue",
+                   "at_C": {"C": C, "blocks": used_c, "bytes": used_c * (4 * C + 12)},
+                   "at_rule": {"C": c_rule, "blocks": used_r, "bytes": used_r * (4 * c_rule + 12)},
+                   "at_min_footprint": {"C": c_min, "blocks": used_m, "bytes": used_m * (4 * c_min + 12)}})
     gr.close()
 
     # f1: set-semantics insert of the 10M batch (half of it already stored)

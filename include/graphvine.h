@@ -423,10 +423,16 @@ gv_status gv_degree_offsets_noalloc(gv_graph *g, const uint32_t *d_vids, uint32_
  * vertex gets ceil(deg / C) blocks of the new size, taken as one contiguous
  * run of the pool, and the pool memory (the same bytes: library-owned,
  * grown, or the caller's pool_mem) is laid out again for the new C.
- *   block_capacity  the new C: a multiple of 4 in [4, 512], or 0 for the
+ *   block_capacity  the new C: a multiple of 4 in [4, 512]; 0 for the
  *                   paper's rule over the current degrees ("Initialization":
  *                   the average degree of the vertices with at least one
- *                   entry, rounded up to a multiple of 4, at least 4).
+ *                   entry, rounded up to a multiple of 4, at least 4); or
+ *                   GV_REBLOCK_MIN_FOOTPRINT for the C of least pool
+ *                   footprint over the current degrees: a block costs 4C
+ *                   bytes of slots (8C on a weighted graph) plus 12 bytes of
+ *                   links and queue entry, a vertex of degree d holds
+ *                   ceil(d / C) blocks, and the C in {4, 8, ..., 512} of
+ *                   least total wins (the smallest on ties).
  *   h_block_capacity optional host uint32: the C now in use.
  * Returns GV_ERR_STATE if no edge batch has fixed C yet, a latched device
  * error if one is pending, GV_ERR_OUT_OF_MEMORY if the entries do not fit
@@ -437,6 +443,7 @@ gv_status gv_degree_offsets_noalloc(gv_graph *g, const uint32_t *d_vids, uint32_
  * weighted graph) plus 8 bytes per vertex, freed before the call returns.
  * Synchronises `stream` (it reads the degree totals).
  */
+#define GV_REBLOCK_MIN_FOOTPRINT 1u
 gv_status gv_reblock(gv_graph *g, uint32_t block_capacity, uint32_t *h_block_capacity, void *stream);
 
 /* gv_status_string -- a static, human-readable name for a status code. */

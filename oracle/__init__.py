@@ -53,6 +53,7 @@ def _get():
                 "orc_dictionary_capacity": ([u64], u64),
                 "orc_blocks_for_degree": ([u64, u32], u64),
                 "orc_block_capacity_rule": ([p, u32], u32),
+                "orc_min_footprint_capacity": ([p, u32, ctypes.c_int], u32),
                 "orc_cbt_path": ([u64, ctypes.c_char_p], u32),
                 "orc_pop_ranges": ([p, u32, p, p], None),
                 "orc_insert_block_demand": ([u64, u64, u32], u64),
@@ -208,6 +209,11 @@ def blocks_for_degree(deg: int, C: int) -> int:
 def block_capacity_rule(deg) -> int:
     d = _u32(deg)
     return int(_get().orc_block_capacity_rule(d.ctypes.data, d.size))
+
+
+def min_footprint_capacity(deg, weighted: bool = False) -> int:
+    d = _u32(deg)
+    return int(_get().orc_min_footprint_capacity(d.ctypes.data, d.size, 1 if weighted else 0))
 
 
 def cbt_path(k: int) -> str:

@@ -403,6 +403,29 @@ uint32_t orc_block_capacity_rule(const uint32_t *deg, uint32_t nv) {
 }
 
 /*
+ * Block size of least pool footprint (the paper's future work: changing the
+ * edge-block size to cut the internal fragmentation of the blocks).  A block
+ * of C slots costs 4C bytes of slots (8C with a 32-bit payload per slot)
+ * plus 12 bytes of tree links and queue entry; a vertex of degree d holds
+ * ceil(d / C) blocks.  Returns the C in {4, 8, ..., 512} of least total
+ * bytes over the given degrees, the smallest such C on ties.
+ */
+uint32_t orc_min_footprint_capacity(const uint32_t *deg, uint32_t nv, int weighted) {
+    uint32_t best_c = 4;
+    uint64_t best = UINT64_MAX;
+    for (uint32_t c = 4; c <= 512; c += 4) {
+        uint64_t blocks = 0;
+        for (uint32_t u = 0; u < nv; ++u) blocks += ((uint64_t)deg[u] + c - 1) / c;
+        const uint64_t bytes = blocks * (4ull * c * (weighted ? 2u : 1u) + 12u);
+        if (bytes < best) {
+            best = bytes;
+            best_c = c;
+        }
+    }
+    return best_c;
+}
+
+/*
  * Bit string placing the k-th block (1-based) of a complete binary tree
  * (section "Dynamic edge inserts"): the binary form of k without its leading
  * 1; '0' = go left, '1' = go right, the last step names the side on which

@@ -99,7 +99,7 @@ struct gv_graph {
     uint2 *an_items = nullptr;
     uint32_t *an_cur = nullptr, *an_next = nullptr, *an_ctr = nullptr;
     uint32_t *an_stamp = nullptr;  // shortest paths: round in which a vertex last joined the frontier
-    unsigned long long *rb_stats = nullptr;  // edge-block resize: {entries, non-empty vertices}
+    unsigned long long *rb_stats = nullptr;  // edge-block resize: degree totals / blocks per candidate C
     double *pr_c = nullptr, *pr_acc = nullptr, *pr_scal = nullptr;
     unsigned long long *pr_n = nullptr;
     // PageRank's incoming-edge CSR: per-vertex cursor, offsets, chunk sums,
@@ -1092,7 +1092,9 @@ gv_status gv_reserve(gv_graph *g, uint64_t max_batch) {
 
 gv_status gv_reblock(gv_graph *g, uint32_t block_capacity, uint32_t *h_block_capacity, void *stream) {
     if (!g) return GV_ERR_INVALID_ARG;
-    if (block_capacity && (block_capacity < 4 || block_capacity > 512 || block_capacity % 4)) return GV_ERR_INVALID_ARG;
+    if (block_capacity && block_capacity != GV_REBLOCK_MIN_FOOTPRINT &&
+        (block_capacity < 4 || block_capacity > 512 || block_capacity % 4))
+        return GV_ERR_INVALID_ARG;
     DeviceGuard dg(g->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (g->C == 0) return GV_ERR_STATE;  // nothing laid out yet: the first edge batch fixes C
@@ -1106,12 +1108,31 @@ gv_status gv_reblock(gv_graph *g, uint32_t block_capacity, uint32_t *h_block_cap
     const uint32_t n = g->nv;
     const bool weighted = (g->flags & GV_WEIGHTED) != 0;
 
-    // 1. the new C: given, or the paper's rule over the current degrees
-    if (!g->rb_stats) GV_TRY(dalloc(&g->rb_stats, 2, &g->scratch_bytes));
-    GV_CK(gv::launch_degree_stats(view(g), g->rb_stats, lcfg(g, s)));
-    GV_CK(cudaMemcpyAsync(&g->h_small[0], g->rb_stats, 16, cudaMemcpyDeviceToHost, s));
-    GV_CK(cudaStreamSynchronize(s));
-    const uint32_t C2 = block_capacity ? block_capacity : rule_capacity(g->h_small[0], g->h_small[1]);
+    // 1. the new C: given, the paper's rule over the current degrees, or the
+    // size of least pool footprint (blocks at every candidate size counted
+    // on the device, bytes compared here; the smallest C wins ties)
+    if (!g->rb_stats) GV_TRY(dalloc(&g->rb_stats, 128, &g->scratch_bytes));
+    uint32_t C2 = block_capacity;
+    if (block_capacity == GV_REBLOCK_MIN_FOOTPRINT) {
+        std::vector<unsigned long long> blocks(128);
+        GV_CK(gv::launch_footprint_blocks(view(g), g->rb_stats, lcfg(g, s)));
+        GV_CK(cudaMemcpyAsync(blocks.data(), g->rb_stats, 128 * 8, cudaMemcpyDeviceToHost, s));
+        GV_CK(cudaStreamSynchronize(s));
+        unsigned long long best = ~0ull;
+        for (uint32_t i = 0; i < 128; ++i) {
+            const uint32_t c = 4 * (i + 1);
+            const unsigned long long bytes = blocks[i] * (4ull * c * (weighted ? 2 : 1) + 12);
+            if (bytes < best) {
+                best = bytes;
+                C2 = c;
+            }
+        }
+    } else if (block_capacity == 0) {
+        GV_CK(gv::launch_degree_stats(view(g), g->rb_stats, lcfg(g, s)));
+        GV_CK(cudaMemcpyAsync(&g->h_small[0], g->rb_stats, 16, cudaMemcpyDeviceToHost, s));
+        GV_CK(cudaStreamSynchronize(s));
+        C2 = rule_capacity(g->h_small[0], g->h_small[1]);
+    }
     const unsigned long long P2 = fit_blocks(g->pool_bytes, C2, weighted);
 
     // 2. slot offsets of the new layout (each vertex's degree rounded up to

@@ -123,6 +123,8 @@ cudaError_t launch_neighbor_offsets(const GraphView &g, const uint32_t *vids, ui
 // Edge-block resize: res[0..1] = {entries, non-empty live vertices}; then the
 // trees and sentinels over contiguous block runs starting at slots[u] / C.
 cudaError_t launch_degree_stats(const GraphView &g, unsigned long long *res, const LaunchCfg &lc);
+// res[i] = blocks the live vertices would hold at C = 4 (i + 1), i < 128.
+cudaError_t launch_footprint_blocks(const GraphView &g, unsigned long long *res, const LaunchCfg &lc);
 cudaError_t launch_reblock_place(const GraphView &g, const unsigned long long *slots, const LaunchCfg &lc);
 cudaError_t launch_neighbor_copy(const GraphView &g, const uint32_t *vids, uint32_t n,
                                  const unsigned long long *offsets, uint32_t *nbrs,

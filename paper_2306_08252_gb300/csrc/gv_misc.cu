@@ -262,6 +262,47 @@ __global__ void __launch_bounds__(256) k_reblock_place(GraphView g, const unsign
     }
 }
 
+// res[i] += sum over live vertices of ceil(deg / C_i), C_i = 4 (i + 1), for
+// the 128 block sizes 4 .. 512.  Each lane owns four sizes (i = lane,
+// lane + 32, + 64, + 96) and walks the degrees of 32 vertices at a time
+// (shuffled from the lane that loaded them); sums meet in shared memory and
+// then in `res`, 128 atomics per CTA.
+__global__ void __launch_bounds__(256) k_footprint_blocks(GraphView g, unsigned long long *res) {
+    __shared__ unsigned long long s_acc[128];
+    for (uint32_t i = threadIdx.x; i < 128; i += blockDim.x) s_acc[i] = 0;
+    __syncthreads();
+    const uint32_t lane = lane_id();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    unsigned long long acc[4] = {0, 0, 0, 0};
+    for (uint32_t base = warp * 32; base < g.nv; base += nwarps * 32) {
+        const uint32_t u = base + lane;
+        const uint32_t d = (u < g.nv && g.alive[u]) ? g.sent[u].x : 0u;
+        for (uint32_t j = 0; j < 32; ++j) {
+            const uint32_t dj = __shfl_sync(FULL, d, j);
+            if (dj == 0) continue;
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) {
+                const uint32_t c = 4u * (lane + 32u * k + 1u);
+                const uint32_t q = dj / c;
+                acc[k] += q + (dj - q * c != 0u);
+            }
+        }
+    }
+#pragma unroll
+    for (uint32_t k = 0; k < 4; ++k)
+        if (acc[k]) atomicAdd(&s_acc[lane + 32u * k], acc[k]);
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < 128; i += blockDim.x)
+        if (s_acc[i]) atomicAdd(&res[i], s_acc[i]);
+}
+
+cudaError_t launch_footprint_blocks(const GraphView &g, unsigned long long *res, const LaunchCfg &lc) {
+    cudaMemsetAsync(res, 0, 128 * sizeof(unsigned long long), lc.stream);
+    if (g.nv) k_footprint_blocks<<<grid_for(g.nv, 256, lc.num_sms * 4), 256, 0, lc.stream>>>(g, res);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_degree_stats(const GraphView &g, unsigned long long *res, const LaunchCfg &lc) {
     cudaMemsetAsync(res, 0, 2 * sizeof(unsigned long long), lc.stream);
     if (g.nv) k_degree_stats<<<grid_for(g.nv, 256, lc.num_sms * 8), 256, 0, lc.stream>>>(g, res);

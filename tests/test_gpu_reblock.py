@@ -3,7 +3,8 @@
 Re-blocking changes only the layout: after it every vertex's entries (and
 payloads), degrees, counts and query answers still equal the oracle's, the
 structure passes the self-check, C is the requested one (or the paper's
-rule over the current degrees, as the oracle computes it) and the pool
+rule, or the size of least footprint, over the current degrees, as the
+oracle computes them) and the pool
 holds exactly sum_u ceil(deg(u) / C) blocks in use.  Later updates go on
 matching the oracle.
 """
@@ -38,14 +39,18 @@ def _updates(p, seed, scale, nv, k=6000):
 
 @pytest.mark.parametrize("C0", [4, 16])
 def test_reblock_sequence_keeps_graph(C0):
+    import paper_2306_08252_gb300 as gv
     scale, nv = 12, 1 << 12
     p = Pair(nv, C=C0, pool_bytes=64 << 20)
     try:
         bs, bd = W.rmat_pairs(91, 0, 40000, scale)
         p.bulk(bs, bd)
-        for i, C in enumerate([8, 64, 4, 512, 0, 12]):
+        for i, C in enumerate([8, 64, 4, 512, 0, 12, gv.GV_REBLOCK_MIN_FOOTPRINT]):
             got = p.g.reblock(C)
-            exp = C if C else oracle.block_capacity_rule(p.o.degrees())
+            if C == gv.GV_REBLOCK_MIN_FOOTPRINT:
+                exp = oracle.min_footprint_capacity(p.o.degrees())
+            else:
+                exp = C if C else oracle.block_capacity_rule(p.o.degrees())
             assert got == exp
             _check_layout(p, exp)
             _updates(p, 92 + i, scale, nv)
@@ -67,8 +72,11 @@ def test_reblock_weighted_payloads_follow():
         w = rng.integers(0, 1 << 32, s.size, dtype=np.uint64).astype(np.uint32)
         p.g.insert_edges_weighted(dev_u32(s), dev_u32(d), dev_u32(w), cnt)
         assert tuple(int(x) for x in cnt.cpu().tolist()) == p.o.insert_edges_weighted(s, d, w)
-        for C in (32, 4, 0):
-            C = p.g.reblock(C)
+        for C in (32, 4, 0, gv.GV_REBLOCK_MIN_FOOTPRINT):
+            got = p.g.reblock(C)
+            if C == gv.GV_REBLOCK_MIN_FOOTPRINT:
+                assert got == oracle.min_footprint_capacity(p.o.degrees(), weighted=True)
+            C = got
             _check_layout(p, C)
             vids = np.arange(nv, dtype=np.uint32)
             off, nb, wt = p.g.neighbors_weighted(vids)
@@ -124,13 +132,13 @@ def test_reblock_caller_pool_grown_pool_and_empty():
         g.close()
         o.close()
     # a pool that grew (GV_GROW) keeps its grown size through the resize
-    p = Pair(nv, C=4, pool_bytes=1 << 20, flags=gv.GV_GROW)
+    p = Pair(nv, C=4, pool_bytes=256 << 10, flags=gv.GV_GROW)
     try:
         for r in range(4):
             s, d = W.rmat_pairs(97, r, 20000, 11)
             p.insert(s, d)
         grown = p.g.stats()["pool_bytes"]
-        assert grown > 1 << 20
+        assert grown > 256 << 10
         C = p.g.reblock(0)
         _check_layout(p, C)
         assert p.g.stats()["pool_bytes"] == grown
@@ -160,10 +168,12 @@ def test_reblock_caller_pool_grown_pool_and_empty():
 
 
 def test_reblock_full_size_rmat():
+    import paper_2306_08252_gb300 as gv
     bs, bd = W.rmat_graph(2, 20, 1 << 24)
     p = Pair(1 << 20, C=16, pool_bytes=1 << 30)
     try:
         p.bulk(bs, bd)
+        assert p.g.reblock(gv.GV_REBLOCK_MIN_FOOTPRINT) == oracle.min_footprint_capacity(p.o.degrees())
         C = p.g.reblock(0)
         assert C == oracle.block_capacity_rule(p.o.degrees())
         p.check(full=False)

@@ -359,3 +359,25 @@ def test_block_capacity_rule():
     assert oracle.block_capacity_rule([0, 0, 0]) == 4
     assert oracle.block_capacity_rule([1, 1, 2]) == 4      # at least 4
     assert oracle.block_capacity_rule([17, 18]) == 20      # ceil(17.5) = 18 -> multiple of 4
+
+
+def test_min_footprint_capacity():
+    # closed forms: equal degrees that are a multiple of 4 (<= 512) are met
+    # exactly by C = that degree (no empty slot, one block each)
+    for d in (4, 8, 36, 200, 512):
+        assert oracle.min_footprint_capacity([d] * 7) == d
+        assert oracle.min_footprint_capacity([d] * 7, weighted=True) == d
+    assert oracle.min_footprint_capacity([0, 0]) == 4  # nothing stored: every C ties
+    # degree 1 everywhere: C = 4 (one block of the smallest size each)
+    assert oracle.min_footprint_capacity([1] * 50) == 4
+    # brute force over the candidates, written out with numpy
+    rng = np.random.default_rng(7)
+    for trial in range(40):
+        nv = int(rng.integers(1, 60))
+        deg = rng.zipf(1.6, nv).clip(0, 5000) * rng.integers(0, 2, nv)
+        for weighted in (False, True):
+            C = np.arange(4, 513, 4)
+            blocks = (-(-deg[None, :].astype(np.int64) // C[:, None])).sum(axis=1)
+            cost = blocks * (4 * C * (2 if weighted else 1) + 12)
+            exp = int(C[np.flatnonzero(cost == cost.min())[0]])
+            assert oracle.min_footprint_capacity(deg, weighted) == exp
