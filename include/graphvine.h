@@ -440,7 +440,8 @@ gv_status gv_degree_offsets_noalloc(gv_graph *g, const uint32_t *d_vids, uint32_
  * before anything changes -- and GV_ERR_CUDA if a copy fails after the
  * layout was switched (the graph is then undefined).
  * Scratch: device arrays of 4 bytes per slot of the new layout (8 on a
- * weighted graph) plus 8 bytes per vertex, freed before the call returns.
+ * weighted graph) plus 8 bytes per vertex, taken from the device's
+ * stream-ordered allocator on `stream` and freed before the call returns.
  * Synchronises `stream` (it reads the degree totals).
  */
 #define GV_REBLOCK_MIN_FOOTPRINT 1u

@@ -71,6 +71,7 @@ struct gv_graph {
     uint32_t *t_owner = nullptr;
     // items
     unsigned long long icap = 0;
+    uint32_t ib_alloc = 0;  // blocks per item the work-item arrays were sized for
     uint2 *items = nullptr;
     uint32_t *it_mask = nullptr, *it_cnt = nullptr, *it_H = nullptr, *it_S = nullptr, *it_bid = nullptr;
     // arena
@@ -353,6 +354,7 @@ gv_status ensure_items(gv_graph *g, unsigned long long need) {
     GV_TRY(dalloc(&g->it_H, cap, &g->scratch_bytes));
     GV_TRY(dalloc(&g->it_S, cap, &g->scratch_bytes));
     GV_TRY(dalloc(&g->it_bid, cap * (g->IB ? g->IB : 32), &g->scratch_bytes));
+    g->ib_alloc = g->IB ? g->IB : 32;
     g->icap = cap;
     return GV_OK;
 }
@@ -1137,12 +1139,23 @@ gv_status gv_reblock(gv_graph *g, uint32_t block_capacity, uint32_t *h_block_cap
 
     // 2. slot offsets of the new layout (each vertex's degree rounded up to
     // whole blocks of C2): the run of u starts at block slots[u] / C2
+    // temporaries from the stream-ordered allocator (no device-wide sync)
     unsigned long long *slots = nullptr;
     uint32_t *nd = nullptr, *nw = nullptr;
+    auto tmp_alloc = [&](auto **p, size_t count) {
+        if (cudaMallocAsync(reinterpret_cast<void **>(p), count * sizeof(**p), s) != cudaSuccess) {
+            cudaGetLastError();
+            *p = nullptr;
+            return GV_ERR_OUT_OF_MEMORY;
+        }
+        return GV_OK;
+    };
     auto release = [&]() {
-        dfree(slots);
-        dfree(nd);
-        dfree(nw);
+        if (slots) cudaFreeAsync(slots, s);
+        if (nd) cudaFreeAsync(nd, s);
+        if (nw) cudaFreeAsync(nw, s);
+        slots = nullptr;
+        nd = nw = nullptr;
     };
     void *dv = nullptr;
     GV_TRY(stage_buf(g, 0, (size_t)n * 4 + 4, &dv));
@@ -1154,8 +1167,7 @@ gv_status gv_reblock(gv_graph *g, uint32_t block_capacity, uint32_t *h_block_cap
         GV_TRY(dalloc(&g->partials, nchunks + 1, &g->scratch_bytes));
         g->pcap = nchunks + 1;
     }
-    uint64_t acct = 0;
-    GV_TRY(dalloc(&slots, (size_t)n + 1, &acct));
+    GV_TRY(tmp_alloc(&slots, (size_t)n + 1));
     gv_status st = GV_OK;
     if (gv::launch_neighbor_offsets(view(g), (const uint32_t *)dv, n, slots, g->partials, lcfg(g, s), C2) !=
             cudaSuccess ||
@@ -1177,8 +1189,8 @@ gv_status gv_reblock(gv_graph *g, uint32_t block_capacity, uint32_t *h_block_cap
 
     // 3. every entry (and payload) copied to its place in the new layout,
     // read through the old trees
-    if ((st = dalloc(&nd, std::max<unsigned long long>(T, 4), &acct)) != GV_OK ||
-        (weighted && (st = dalloc(&nw, std::max<unsigned long long>(T, 4), &acct)) != GV_OK) ||
+    if ((st = tmp_alloc(&nd, std::max<unsigned long long>(T, 4))) != GV_OK ||
+        (weighted && (st = tmp_alloc(&nw, std::max<unsigned long long>(T, 4))) != GV_OK) ||
         (st = ensure_touched(g, n)) != GV_OK || (st = ensure_items(g, item_bound(g, n))) != GV_OK) {
         release();
         return st;
@@ -1212,13 +1224,12 @@ gv_status gv_reblock(gv_graph *g, uint32_t block_capacity, uint32_t *h_block_cap
     g->h_small[3] = P2;
     ok = ok && cudaMemcpyAsync(&g->dev->q_front, &g->h_small[2], 8, cudaMemcpyHostToDevice, s) == cudaSuccess;
     ok = ok && cudaMemcpyAsync(&g->dev->q_back, &g->h_small[3], 8, cudaMemcpyHostToDevice, s) == cudaSuccess;
-    ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
     release();
+    ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
     if (!ok) return GV_ERR_CUDA;
     g->used_ub = nb2;
     // work-item scratch is sized by the blocks per item, which follow C
-    dfree(g->items); dfree(g->it_mask); dfree(g->it_cnt); dfree(g->it_H); dfree(g->it_S); dfree(g->it_bid);
-    g->icap = 0;
+    if (g->IB > g->ib_alloc) g->icap = 0;  // forces a new allocation
     GV_TRY(ensure_items(g, item_bound(g, 1024)));
     if (h_block_capacity) *h_block_capacity = C2;
     return check_launch();
