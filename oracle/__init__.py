@@ -1,7 +1,10 @@
 """ctypes wrapper of the CPU oracle (gv_oracle.c) -- TEST INFRASTRUCTURE ONLY.
 
 Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
-leg may import this package.  The GPU library never loads it.
+leg may import this package.  The GPU library never loads it.  The same
+library carries the parallel CPU baseline (gv_cpu_parallel.c: the oracle's
+algorithm over all host cores with OpenMP), used only to time a multi-core
+CPU beside the GPU path.
 """
 from __future__ import annotations
 
@@ -14,6 +17,8 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gv_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "gv_cpu_parallel.c")]
+_DEPS = _SRCS + [os.path.join(_HERE, "gv_oracle_internal.h")]
 _LIB = os.path.join(_HERE, "libgv_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -23,9 +28,9 @@ DEDUP = 1
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc into an in-tree shared library."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(f) for f in _DEPS):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fopenmp", "-shared", "-fPIC", "-o", tmp] + _SRCS)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -62,6 +67,9 @@ def _get():
                 "orc_neighbors_weighted": ([p, p, u32, p, p, p, u64], u64),
                 "orc_pagerank": ([p, u32, ctypes.c_double, p], None),
                 "orc_sssp": ([p, u32, ctypes.c_int, p], u32),
+                "orc_par_insert_edges": ([p, p, p, u64, ctypes.c_int, p, p], None),
+                "orc_par_delete_edges": ([p, p, p, u64, ctypes.c_int, p, p], None),
+                "orc_par_query_edges": ([p, p, p, u64, ctypes.c_int, p], None),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -141,6 +149,27 @@ class OracleGraph:
         s, d = _u32(src), _u32(dst)
         out = np.zeros(s.size, dtype=np.uint8)
         self._lib.orc_query_edges(self._g, s.ctypes.data, d.ctypes.data, s.size, out.ctypes.data)
+        return out
+
+    # parallel CPU baseline: the same results over `threads` host cores
+    def par_insert_edges(self, src, dst, threads: int):
+        s, d = _u32(src), _u32(dst)
+        a = np.zeros(2, dtype=np.uint64)
+        self._lib.orc_par_insert_edges(self._g, s.ctypes.data, d.ctypes.data, s.size, threads,
+                                       a[0:].ctypes.data, a[1:].ctypes.data)
+        return int(a[0]), int(a[1])
+
+    def par_delete_edges(self, src, dst, threads: int):
+        s, d = _u32(src), _u32(dst)
+        a = np.zeros(2, dtype=np.uint64)
+        self._lib.orc_par_delete_edges(self._g, s.ctypes.data, d.ctypes.data, s.size, threads,
+                                       a[0:].ctypes.data, a[1:].ctypes.data)
+        return int(a[0]), int(a[1])
+
+    def par_query_edges(self, src, dst, threads: int) -> np.ndarray:
+        s, d = _u32(src), _u32(dst)
+        out = np.zeros(s.size, dtype=np.uint8)
+        self._lib.orc_par_query_edges(self._g, s.ctypes.data, d.ctypes.data, s.size, threads, out.ctypes.data)
         return out
 
     def insert_vertices(self, k: int) -> np.ndarray:

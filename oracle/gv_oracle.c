@@ -34,23 +34,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define ORC_DEDUP 1u
-
-typedef struct {
-    uint32_t *v;     /* destination ids, sorted by (v, w) (multiset) */
-    uint32_t *w;     /* 32-bit payload (weight) of each entry; 0 when unweighted */
-    uint64_t n;
-    uint64_t cap;
-} orc_adj;
-
-typedef struct orc_graph {
-    uint32_t nv;        /* vertex ids in [0, nv) exist */
-    uint32_t cap;       /* allocated vertex slots */
-    uint32_t flags;
-    uint8_t *alive;
-    orc_adj *adj;
-    uint64_t num_edges;
-} orc_graph;
+#include "gv_oracle_internal.h"
 
 static int cmp_u32(const void *a, const void *b) {
     uint32_t x = *(const uint32_t *)a, y = *(const uint32_t *)b;
@@ -62,7 +46,7 @@ static int cmp_u64(const void *a, const void *b) {
     return (x > y) - (x < y);
 }
 
-static void adj_reserve(orc_adj *a, uint64_t need) {
+void adj_reserve(orc_adj *a, uint64_t need) {
     if (need <= a->cap) return;
     uint64_t c = a->cap ? a->cap : 4;
     while (c < need) c *= 2;
@@ -72,7 +56,7 @@ static void adj_reserve(orc_adj *a, uint64_t need) {
 }
 
 /* Sorts an adjacency by (v, w): the canonical order of its entries. */
-static void adj_sort(orc_adj *a) {
+void adj_sort(orc_adj *a) {
     uint64_t *k = (uint64_t *)malloc((a->n ? a->n : 1) * sizeof(uint64_t));
     for (uint64_t i = 0; i < a->n; ++i) k[i] = ((uint64_t)a->v[i] << 32) | a->w[i];
     qsort(k, a->n, sizeof(uint64_t), cmp_u64);
@@ -84,7 +68,7 @@ static void adj_sort(orc_adj *a) {
 }
 
 /* 1 if x occurs in the sorted array a[0..n). */
-static int sorted_contains(const uint32_t *a, uint64_t n, uint32_t x) {
+int sorted_contains(const uint32_t *a, uint64_t n, uint32_t x) {
     uint64_t lo = 0, hi = n;
     while (lo < hi) {
         uint64_t mid = lo + (hi - lo) / 2;
@@ -125,7 +109,7 @@ void orc_destroy(orc_graph *g) {
     free(g);
 }
 
-static int valid_pair(const orc_graph *g, uint32_t u, uint32_t v) {
+int valid_pair(const orc_graph *g, uint32_t u, uint32_t v) {
     return u < g->nv && v < g->nv && g->alive[u] && g->alive[v];
 }
 
@@ -149,11 +133,7 @@ static uint64_t *sorted_valid_keys(const orc_graph *g, const uint32_t *src, cons
     return k;
 }
 
-typedef struct {
-    uint32_t u, v, w;
-} orc_triple;
-
-static int cmp_triple(const void *a, const void *b) {
+int cmp_triple(const void *a, const void *b) {
     const orc_triple *x = (const orc_triple *)a, *y = (const orc_triple *)b;
     if (x->u != y->u) return (x->u > y->u) - (x->u < y->u);
     if (x->v != y->v) return (x->v > y->v) - (x->v < y->v);
