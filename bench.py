@@ -115,6 +115,34 @@ def host_cores():
         return os.cpu_count() or 1
 
 
+def cpu_model():
+    """The host CPU as /proc/cpuinfo names it (model name, or the Arm
+    implementer/part codes), with the machine architecture."""
+    import platform
+    name = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read()
+        for key in ("model name", "Model Name", "Hardware"):
+            for line in info.splitlines():
+                if line.split(":")[0].strip() == key:
+                    name = line.split(":", 1)[1].strip()
+                    break
+            if name:
+                break
+        if not name:
+            kv = {}
+            for line in info.splitlines():
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    kv.setdefault(k.strip(), v.strip())
+            if "CPU implementer" in kv:
+                name = f"implementer {kv['CPU implementer']} part {kv.get('CPU part', '?')}"
+    except OSError:
+        pass
+    return f"{name or 'unknown'} ({platform.machine()})"
+
+
 def parallel_cpu_rate(base, upd, qry, threads, budget_s=10.0, max_steps=3):
     """The oracle's sorted-vector algorithm run over `threads` host cores
     (OpenMP over source buckets) on the whole step: insert the full batch,
@@ -1001,7 +1029,7 @@ def main():
                                          f"delete them, on the full bulk-built graph ({secs:.1f} s)"}
         cores = host_cores()
         v, steps, secs = parallel_cpu_rate(base, upd, qry, cores)
-        res["cpu_parallel"] = {"value": v, "unit": UNIT, "cores": cores,
+        res["cpu_parallel"] = {"value": v, "unit": UNIT, "cores": cores, "cpu": cpu_model(),
                                "kind": "the oracle's sorted-vector algorithm, OpenMP over source buckets",
                                "sample": f"{steps} full steps (insert the 10M batch, 1M queries, delete the batch) "
                                          f"on the full bulk-built graph ({secs:.1f} s)"}
