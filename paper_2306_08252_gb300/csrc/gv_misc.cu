@@ -239,29 +239,6 @@ __global__ void __launch_bounds__(256) k_degree_stats(GraphView g, unsigned long
     }
 }
 
-// Rebuilt trees over a contiguous run of blocks per vertex, one warp per
-// vertex: slots[u] = first slot of u's run (a multiple of C), the run's
-// blocks are heap positions 1 .. nblocks in id order, so block k's children
-// are the run's blocks 2k and 2k + 1 ("Dynamic edge inserts": heap-numbered
-// complete binary tree); the entries were already copied to the run.
-__global__ void __launch_bounds__(256) k_reblock_place(GraphView g, const unsigned long long *__restrict__ slots) {
-    const uint32_t lane = lane_id();
-    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    const uint32_t C = g.C;
-    for (uint32_t u = warp; u < g.nv; u += nwarps) {
-        const uint32_t deg = g.alive[u] ? g.sent[u].x : 0u;
-        const uint32_t nb = (deg + C - 1) / C;
-        const uint32_t base = (uint32_t)(slots[u] / C);
-        if (lane == 0) g.sent[u] = make_uint4(deg, nb, nb ? base : NIL, nb ? base + nb - 1 : NIL);
-        for (uint32_t k = 1 + lane; k <= nb; k += 32) {
-            const uint32_t b = base + k - 1;
-            g.links[2ull * b] = 2ull * k <= nb ? base + 2 * k - 1 : NIL;
-            g.links[2ull * b + 1] = 2ull * k + 1 <= nb ? base + 2 * k : NIL;
-        }
-    }
-}
-
 // res[i] += sum over live vertices of ceil(deg / C_i), C_i = 4 (i + 1), for
 // the 128 block sizes 4 .. 512.  Each lane owns four sizes (i = lane,
 // lane + 32, + 64, + 96) and walks the degrees of 32 vertices at a time
@@ -275,17 +252,27 @@ __global__ void __launch_bounds__(256) k_footprint_blocks(GraphView g, unsigned 
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     unsigned long long acc[4] = {0, 0, 0, 0};
+    unsigned long long mag[4];
+#pragma unroll
+    for (uint32_t k = 0; k < 4; ++k) {
+        const unsigned long long c = 4u * (lane + 32u * k + 1u);
+        mag[k] = ((1ull << 40) + c - 1) / c;
+    }
     for (uint32_t base = warp * 32; base < g.nv; base += nwarps * 32) {
         const uint32_t u = base + lane;
         const uint32_t d = (u < g.nv && g.alive[u]) ? g.sent[u].x : 0u;
         for (uint32_t j = 0; j < 32; ++j) {
             const uint32_t dj = __shfl_sync(FULL, d, j);
             if (dj == 0) continue;
+            // ceil(dj / c) = floor((dj - 1) / c) + 1 for dj > 0; the quotient
+            // by multiply-shift (x * ceil(2^40 / c)) >> 40, exact for
+            // x < 2^31 and c <= 512, else a division
 #pragma unroll
             for (uint32_t k = 0; k < 4; ++k) {
-                const uint32_t c = 4u * (lane + 32u * k + 1u);
-                const uint32_t q = dj / c;
-                acc[k] += q + (dj - q * c != 0u);
+                const uint32_t x = dj - 1u;
+                const uint32_t q = x < 0x80000000u ? (uint32_t)(((unsigned long long)x * mag[k]) >> 40)
+                                                   : x / (4u * (lane + 32u * k + 1u));
+                acc[k] += q + 1u;
             }
         }
     }
@@ -303,6 +290,54 @@ cudaError_t launch_footprint_blocks(const GraphView &g, unsigned long long *res,
     return cudaGetLastError();
 }
 
+// Rebuilt trees over a contiguous run of blocks per vertex: slots[u] = first
+// slot of u's run (a multiple of C); the run's blocks are heap positions
+// 1 .. nblocks in id order, so block k's children are the run's blocks 2k
+// and 2k + 1 ("Dynamic edge inserts": heap-numbered complete binary tree);
+// the entries were already copied to the run.  A warp takes 32 consecutive
+// vertices (one sentinel per lane, coalesced) and then strides over the
+// concatenation of their runs, so every lane writes links whatever the
+// degree mix; a block finds its vertex by a 5-step search of the warp's
+// exclusive scan of block counts.
+__global__ void __launch_bounds__(256) k_reblock_place(GraphView g, const unsigned long long *__restrict__ slots) {
+    const uint32_t lane = lane_id();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t C = g.C;
+    for (uint32_t vbase = warp * 32; vbase < g.nv; vbase += nwarps * 32) {
+        const uint32_t u = vbase + lane;
+        uint32_t nb = 0, base = 0;
+        if (u < g.nv) {
+            const uint32_t deg = g.alive[u] ? g.sent[u].x : 0u;
+            nb = (deg + C - 1) / C;
+            base = (uint32_t)(slots[u] / C);
+            g.sent[u] = make_uint4(deg, nb, nb ? base : NIL, nb ? base + nb - 1 : NIL);
+        }
+        uint32_t total;
+        const uint32_t ex = warp_excl_scan(nb, &total);
+        for (uint32_t i0 = 0; i0 < total; i0 += 32) {
+            const uint32_t i = i0 + lane;
+            // owner: the largest lane j with ex_j <= i (lanes with no block
+            // share their successor's offset and lose to it)
+            uint32_t j = 0;
+#pragma unroll
+            for (uint32_t step = 16; step >= 1; step >>= 1) {
+                const uint32_t e = __shfl_sync(FULL, ex, (j + step) & 31u);
+                if (j + step < 32 && e <= i) j += step;
+            }
+            const uint32_t jb = __shfl_sync(FULL, base, j);
+            const uint32_t jn = __shfl_sync(FULL, nb, j);
+            const uint32_t je = __shfl_sync(FULL, ex, j);
+            if (i < total) {
+                const uint32_t k = i - je + 1;  // heap index within the run
+                const uint32_t b = jb + k - 1;
+                g.links[2ull * b] = 2ull * k <= jn ? jb + 2 * k - 1 : NIL;
+                g.links[2ull * b + 1] = 2ull * k + 1 <= jn ? jb + 2 * k : NIL;
+            }
+        }
+    }
+}
+
 cudaError_t launch_degree_stats(const GraphView &g, unsigned long long *res, const LaunchCfg &lc) {
     cudaMemsetAsync(res, 0, 2 * sizeof(unsigned long long), lc.stream);
     if (g.nv) k_degree_stats<<<grid_for(g.nv, 256, lc.num_sms * 8), 256, 0, lc.stream>>>(g, res);
@@ -310,7 +345,7 @@ cudaError_t launch_degree_stats(const GraphView &g, unsigned long long *res, con
 }
 
 cudaError_t launch_reblock_place(const GraphView &g, const unsigned long long *slots, const LaunchCfg &lc) {
-    if (g.nv) k_reblock_place<<<grid_for(32ull * g.nv, 256, lc.num_sms * 16), 256, 0, lc.stream>>>(g, slots);
+    if (g.nv) k_reblock_place<<<grid_for(g.nv, 256, lc.num_sms * 16), 256, 0, lc.stream>>>(g, slots);
     return cudaGetLastError();
 }
 
