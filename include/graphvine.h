@@ -439,9 +439,10 @@ gv_status gv_degree_offsets_noalloc(gv_graph *g, const uint32_t *d_vids, uint32_
  * the pool at the new size or the scratch cannot be allocated -- all three
  * before anything changes -- and GV_ERR_CUDA if a copy fails after the
  * layout was switched (the graph is then undefined).
- * Scratch: device arrays of 4 bytes per slot of the new layout (8 on a
- * weighted graph) plus 8 bytes per vertex, taken from the device's
- * stream-ordered allocator on `stream` and freed before the call returns.
+ * Scratch: 4 bytes per slot of the new layout (8 on a weighted graph) in
+ * the graph's delete/query scratch, plus 12 bytes per vertex in its staging
+ * buffers; like all of the graph's scratch it grows when needed and is kept
+ * until gv_destroy.
  * Synchronises `stream` (it reads the degree totals).
  */
 #define GV_REBLOCK_MIN_FOOTPRINT 1u

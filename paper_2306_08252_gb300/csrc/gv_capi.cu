@@ -1138,25 +1138,13 @@ gv_status gv_reblock(gv_graph *g, uint32_t block_capacity, uint32_t *h_block_cap
     const unsigned long long P2 = fit_blocks(g->pool_bytes, C2, weighted);
 
     // 2. slot offsets of the new layout (each vertex's degree rounded up to
-    // whole blocks of C2): the run of u starts at block slots[u] / C2
-    // temporaries from the stream-ordered allocator (no device-wide sync)
+    // whole blocks of C2): the run of u starts at block slots[u] / C2.
+    // Scratch is the graph's own, kept between calls: the vertex list and
+    // the run offsets in staging buffers, the new slots (and payloads) in the
+    // membership arena and its parallel array (per-call scratch of deletes
+    // and queries).
     unsigned long long *slots = nullptr;
     uint32_t *nd = nullptr, *nw = nullptr;
-    auto tmp_alloc = [&](auto **p, size_t count) {
-        if (cudaMallocAsync(reinterpret_cast<void **>(p), count * sizeof(**p), s) != cudaSuccess) {
-            cudaGetLastError();
-            *p = nullptr;
-            return GV_ERR_OUT_OF_MEMORY;
-        }
-        return GV_OK;
-    };
-    auto release = [&]() {
-        if (slots) cudaFreeAsync(slots, s);
-        if (nd) cudaFreeAsync(nd, s);
-        if (nw) cudaFreeAsync(nw, s);
-        slots = nullptr;
-        nd = nw = nullptr;
-    };
     void *dv = nullptr;
     GV_TRY(stage_buf(g, 0, (size_t)n * 4 + 4, &dv));
     GV_CK(gv::launch_iota((uint32_t *)dv, 0, n, lcfg(g, s)));
@@ -1167,52 +1155,33 @@ gv_status gv_reblock(gv_graph *g, uint32_t block_capacity, uint32_t *h_block_cap
         GV_TRY(dalloc(&g->partials, nchunks + 1, &g->scratch_bytes));
         g->pcap = nchunks + 1;
     }
-    GV_TRY(tmp_alloc(&slots, (size_t)n + 1));
-    gv_status st = GV_OK;
-    if (gv::launch_neighbor_offsets(view(g), (const uint32_t *)dv, n, slots, g->partials, lcfg(g, s), C2) !=
-            cudaSuccess ||
-        cudaMemcpyAsync(&g->h_small[0], slots + n, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) {
-        release();
-        return GV_ERR_CUDA;
-    }
+    void *ds = nullptr;
+    GV_TRY(stage_buf(g, 1, ((size_t)n + 1) * 8, &ds));
+    slots = static_cast<unsigned long long *>(ds);
+    GV_CK(gv::launch_neighbor_offsets(view(g), (const uint32_t *)dv, n, slots, g->partials, lcfg(g, s), C2));
+    GV_CK(cudaMemcpyAsync(&g->h_small[0], slots + n, 8, cudaMemcpyDeviceToHost, s));
+    GV_CK(cudaStreamSynchronize(s));
     const unsigned long long T = g->h_small[0];  // slots of the new layout
     const unsigned long long nb2 = T / C2;
-    if (nb2 > P2) {  // the entries do not fit the pool at this block size
-        release();
-        return GV_ERR_OUT_OF_MEMORY;
-    }
-    if (nb2 > 0xFFFFFFFEull) {
-        release();
-        return GV_ERR_OUT_OF_MEMORY;
-    }
+    // the entries must fit the pool at this block size
+    if (nb2 > P2 || nb2 > 0xFFFFFFFEull) return GV_ERR_OUT_OF_MEMORY;
 
     // 3. every entry (and payload) copied to its place in the new layout,
     // read through the old trees
-    if ((st = tmp_alloc(&nd, std::max<unsigned long long>(T, 4))) != GV_OK ||
-        (weighted && (st = tmp_alloc(&nw, std::max<unsigned long long>(T, 4))) != GV_OK) ||
-        (st = ensure_touched(g, n)) != GV_OK || (st = ensure_items(g, item_bound(g, n))) != GV_OK) {
-        release();
-        return st;
-    }
+    GV_TRY(ensure_arena(g, std::max<unsigned long long>(T, 4), false, 0));
+    GV_TRY(ensure_touched(g, n));
+    GV_TRY(ensure_items(g, item_bound(g, n)));
+    nd = g->arena;
+    nw = weighted ? g->found : nullptr;
     // the unused tail slots of each run's last block hold NIL
-    if (cudaMemsetAsync(nd, 0xFF, T * 4ull, s) != cudaSuccess ||
-        (n && gv::launch_neighbor_copy(view(g), (const uint32_t *)dv, n, slots, nd, lcfg(g, s), nw) != cudaSuccess)) {
-        release();
-        return GV_ERR_CUDA;
-    }
-    if (cudaStreamSynchronize(s) != cudaSuccess) {
-        release();
-        return GV_ERR_CUDA;
-    }
+    GV_CK(cudaMemsetAsync(nd, 0xFF, T * 4ull, s));
+    if (n) GV_CK(gv::launch_neighbor_copy(view(g), (const uint32_t *)dv, n, slots, nd, lcfg(g, s), nw));
+    GV_CK(cudaStreamSynchronize(s));
 
     // 4. the same pool memory laid out for C2: slots back in place, trees
     // and sentinels over the runs, the queue holding the blocks past them
     char *base = reinterpret_cast<char *>(g->data);
-    if (!lay_out_pool(g, base, g->pool_bytes, C2, P2)) {
-        release();
-        return GV_ERR_STATE;  // cannot happen: P2 was fitted to this layout
-    }
+    if (!lay_out_pool(g, base, g->pool_bytes, C2, P2)) return GV_ERR_STATE;  // cannot happen: P2 was fitted
     set_item_blocks(g);
     const GraphView v = view(g);
     bool ok = true;
@@ -1224,7 +1193,6 @@ gv_status gv_reblock(gv_graph *g, uint32_t block_capacity, uint32_t *h_block_cap
     g->h_small[3] = P2;
     ok = ok && cudaMemcpyAsync(&g->dev->q_front, &g->h_small[2], 8, cudaMemcpyHostToDevice, s) == cudaSuccess;
     ok = ok && cudaMemcpyAsync(&g->dev->q_back, &g->h_small[3], 8, cudaMemcpyHostToDevice, s) == cudaSuccess;
-    release();
     ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
     if (!ok) return GV_ERR_CUDA;
     g->used_ub = nb2;
