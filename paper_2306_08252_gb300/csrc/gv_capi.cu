@@ -1187,7 +1187,8 @@ gv_status gv_reblock(gv_graph *g, uint32_t block_capacity, uint32_t *h_block_cap
     bool ok = true;
     if (T) ok = ok && cudaMemcpyAsync(g->data, nd, T * 4ull, cudaMemcpyDeviceToDevice, s) == cudaSuccess;
     if (T && weighted) ok = ok && cudaMemcpyAsync(g->wdata, nw, T * 4ull, cudaMemcpyDeviceToDevice, s) == cudaSuccess;
-    ok = ok && gv::launch_reblock_place(v, slots, lcfg(g, s)) == cudaSuccess;
+    // long runs are listed in the touched-vertex scratch (n entries), counted in rb_stats[0]
+    ok = ok && gv::launch_reblock_place(v, slots, g->t_vid, g->rb_stats, lcfg(g, s)) == cudaSuccess;
     ok = ok && gv::launch_init_queue(g->queue, P2, lcfg(g, s)) == cudaSuccess;
     g->h_small[2] = nb2;
     g->h_small[3] = P2;

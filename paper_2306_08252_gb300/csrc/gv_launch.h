@@ -125,7 +125,10 @@ cudaError_t launch_neighbor_offsets(const GraphView &g, const uint32_t *vids, ui
 cudaError_t launch_degree_stats(const GraphView &g, unsigned long long *res, const LaunchCfg &lc);
 // res[i] = blocks the live vertices would hold at C = 4 (i + 1), i < 128.
 cudaError_t launch_footprint_blocks(const GraphView &g, unsigned long long *res, const LaunchCfg &lc);
-cudaError_t launch_reblock_place(const GraphView &g, const unsigned long long *slots, const LaunchCfg &lc);
+// big: scratch of one id per vertex (the runs longer than a thread writes
+// alone), nbig: one counter
+cudaError_t launch_reblock_place(const GraphView &g, const unsigned long long *slots, uint32_t *big,
+                                 unsigned long long *nbig, const LaunchCfg &lc);
 cudaError_t launch_neighbor_copy(const GraphView &g, const uint32_t *vids, uint32_t n,
                                  const unsigned long long *offsets, uint32_t *nbrs,
                                  const LaunchCfg &lc,

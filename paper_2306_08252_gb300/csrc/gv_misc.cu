@@ -294,46 +294,46 @@ cudaError_t launch_footprint_blocks(const GraphView &g, unsigned long long *res,
 // slot of u's run (a multiple of C); the run's blocks are heap positions
 // 1 .. nblocks in id order, so block k's children are the run's blocks 2k
 // and 2k + 1 ("Dynamic edge inserts": heap-numbered complete binary tree);
-// the entries were already copied to the run.  A warp takes 32 consecutive
-// vertices (one sentinel per lane, coalesced) and then strides over the
-// concatenation of their runs, so every lane writes links whatever the
-// degree mix; a block finds its vertex by a 5-step search of the warp's
-// exclusive scan of block counts.
-__global__ void __launch_bounds__(256) k_reblock_place(GraphView g, const unsigned long long *__restrict__ slots) {
-    const uint32_t lane = lane_id();
-    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+// the entries were already copied to the run.  One thread per vertex writes
+// the sentinel and the links of a run of up to PLACE_SMALL blocks; longer
+// runs (the hubs of a skewed graph) are listed for k_reblock_big, which
+// spreads each over a whole CTA.
+constexpr uint32_t PLACE_SMALL = 32;
+
+__global__ void __launch_bounds__(256) k_reblock_place(GraphView g, const unsigned long long *__restrict__ slots,
+                                                       uint32_t *big, unsigned long long *nbig) {
     const uint32_t C = g.C;
-    for (uint32_t vbase = warp * 32; vbase < g.nv; vbase += nwarps * 32) {
-        const uint32_t u = vbase + lane;
-        uint32_t nb = 0, base = 0;
-        if (u < g.nv) {
-            const uint32_t deg = g.alive[u] ? g.sent[u].x : 0u;
-            nb = (deg + C - 1) / C;
-            base = (uint32_t)(slots[u] / C);
-            g.sent[u] = make_uint4(deg, nb, nb ? base : NIL, nb ? base + nb - 1 : NIL);
+    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < g.nv; u += gridDim.x * blockDim.x) {
+        const uint32_t deg = g.alive[u] ? g.sent[u].x : 0u;
+        const uint32_t nb = (deg + C - 1) / C;
+        const uint32_t base = (uint32_t)(slots[u] / C);
+        g.sent[u] = make_uint4(deg, nb, nb ? base : NIL, nb ? base + nb - 1 : NIL);
+        if (nb > PLACE_SMALL) {
+            big[atomicAdd(nbig, 1ull)] = u;
+            continue;
         }
-        uint32_t total;
-        const uint32_t ex = warp_excl_scan(nb, &total);
-        for (uint32_t i0 = 0; i0 < total; i0 += 32) {
-            const uint32_t i = i0 + lane;
-            // owner: the largest lane j with ex_j <= i (lanes with no block
-            // share their successor's offset and lose to it)
-            uint32_t j = 0;
-#pragma unroll
-            for (uint32_t step = 16; step >= 1; step >>= 1) {
-                const uint32_t e = __shfl_sync(FULL, ex, (j + step) & 31u);
-                if (j + step < 32 && e <= i) j += step;
-            }
-            const uint32_t jb = __shfl_sync(FULL, base, j);
-            const uint32_t jn = __shfl_sync(FULL, nb, j);
-            const uint32_t je = __shfl_sync(FULL, ex, j);
-            if (i < total) {
-                const uint32_t k = i - je + 1;  // heap index within the run
-                const uint32_t b = jb + k - 1;
-                g.links[2ull * b] = 2ull * k <= jn ? jb + 2 * k - 1 : NIL;
-                g.links[2ull * b + 1] = 2ull * k + 1 <= jn ? jb + 2 * k : NIL;
-            }
+        for (uint32_t k = 1; k <= nb; ++k) {
+            const uint32_t b = base + k - 1;
+            g.links[2ull * b] = 2 * k <= nb ? base + 2 * k - 1 : NIL;
+            g.links[2ull * b + 1] = 2 * k + 1 <= nb ? base + 2 * k : NIL;
+        }
+    }
+}
+
+// Links of the long runs, one CTA per listed vertex.
+__global__ void __launch_bounds__(256) k_reblock_big(GraphView g, const unsigned long long *__restrict__ slots,
+                                                     const uint32_t *__restrict__ big,
+                                                     const unsigned long long *nbig) {
+    const uint32_t C = g.C;
+    const uint32_t n = (uint32_t)*nbig;
+    for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
+        const uint32_t u = big[i];
+        const uint32_t nb = g.sent[u].y;
+        const uint32_t base = (uint32_t)(slots[u] / C);
+        for (uint32_t k = 1 + threadIdx.x; k <= nb; k += blockDim.x) {
+            const uint32_t b = base + k - 1;
+            g.links[2ull * b] = 2ull * k <= nb ? base + 2 * k - 1 : NIL;
+            g.links[2ull * b + 1] = 2ull * k + 1 <= nb ? base + 2 * k : NIL;
         }
     }
 }
@@ -344,8 +344,13 @@ cudaError_t launch_degree_stats(const GraphView &g, unsigned long long *res, con
     return cudaGetLastError();
 }
 
-cudaError_t launch_reblock_place(const GraphView &g, const unsigned long long *slots, const LaunchCfg &lc) {
-    if (g.nv) k_reblock_place<<<grid_for(g.nv, 256, lc.num_sms * 16), 256, 0, lc.stream>>>(g, slots);
+cudaError_t launch_reblock_place(const GraphView &g, const unsigned long long *slots, uint32_t *big,
+                                 unsigned long long *nbig, const LaunchCfg &lc) {
+    cudaMemsetAsync(nbig, 0, sizeof(unsigned long long), lc.stream);
+    if (g.nv) {
+        k_reblock_place<<<grid_for(g.nv, 256, lc.num_sms * 16), 256, 0, lc.stream>>>(g, slots, big, nbig);
+        k_reblock_big<<<lc.num_sms * 4, 256, 0, lc.stream>>>(g, slots, big, nbig);
+    }
     return cudaGetLastError();
 }
 
