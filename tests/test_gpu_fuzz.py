@@ -1,7 +1,8 @@
 """Random operation sequences on the GPU against the oracle, checked after
-every call: edge inserts (multiset and set semantics), deletes, segmented
-deletes, queries, vertex inserts and deletes, pool growth, BFS, for several
-block capacities and graph sizes.  Seeded; every case is reproducible."""
+every call: edge inserts (multiset and set semantics, weighted), deletes,
+segmented deletes, queries, vertex inserts and deletes, pool growth, BFS,
+shortest paths, edge-block resizes, for several block capacities and graph
+sizes.  Seeded; every case is reproducible."""
 import numpy as np
 import pytest
 
@@ -20,7 +21,8 @@ def _pairs(rng, n, nv, hub_frac=0.3):
     return s, d
 
 
-@pytest.mark.parametrize("seed,C,flags", [(1, 4, 0), (2, 8, 0), (3, 16, 1), (4, 12, 2), (5, 32, 3), (6, 0, 0)])
+@pytest.mark.parametrize("seed,C,flags", [(1, 4, 0), (2, 8, 0), (3, 16, 1), (4, 12, 2), (5, 32, 3), (6, 0, 0),
+                                          (7, 8, 4), (8, 20, 6)])
 def test_random_operation_sequences(seed, C, flags):
     import torch
     import paper_2306_08252_gb300 as gv
@@ -34,10 +36,17 @@ def test_random_operation_sequences(seed, C, flags):
         p.check()
         stored_s, stored_d = bs, bd
         for step in range(25):
-            op = rng.choice(["insert", "delete", "query", "segdel", "vdel", "vins", "bfs"],
-                            p=[0.3, 0.25, 0.15, 0.1, 0.07, 0.07, 0.06])
+            op = rng.choice(["insert", "delete", "query", "segdel", "vdel", "vins", "bfs", "sssp", "reblock"],
+                            p=[0.28, 0.22, 0.13, 0.09, 0.06, 0.06, 0.05, 0.05, 0.06])
             n_now = p.o.num_vertices
-            if op == "insert":
+            if op == "insert" and flags & gv.GV_WEIGHTED and rng.random() < 0.6:
+                s, d = _pairs(rng, int(rng.integers(0, 15000)), n_now)
+                w = rng.integers(0, 1 << 32, s.size, dtype=np.uint64).astype(np.uint32)
+                cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+                p.g.insert_edges_weighted(dev_u32(s), dev_u32(d), dev_u32(w), cnt)
+                assert tuple(int(x) for x in cnt.cpu().tolist()) == p.o.insert_edges_weighted(s, d, w)
+                stored_s, stored_d = np.concatenate([stored_s, s]), np.concatenate([stored_d, d])
+            elif op == "insert":
                 s, d = _pairs(rng, int(rng.integers(0, 15000)), n_now)
                 if s.size and rng.random() < 0.5:  # repeat stored pairs
                     k = rng.integers(0, stored_s.size, s.size // 3)
@@ -76,6 +85,23 @@ def test_random_operation_sequences(seed, C, flags):
                 odist, olv = p.o.bfs(src)
                 np.testing.assert_array_equal(dist[:n_now], odist)
                 assert lv == olv
+            elif op == "sssp":
+                src = int(rng.integers(0, n_now))
+                dist, _ = p.g.sssp(src)
+                odist, _ = p.o.sssp(src, bool(flags & gv.GV_WEIGHTED))
+                np.testing.assert_array_equal(dist[:n_now], odist)
+            elif op == "reblock":
+                before = p.g.stats()["block_capacity"]
+                want = int(rng.choice([0, gv.GV_REBLOCK_MIN_FOOTPRINT, 4, 8, 12, 16, 24, 32, 64, 128]))
+                try:
+                    got = p.g.reblock(want)
+                except gv.GraphVineError as e:
+                    # only a resize that does not fit the pool may fail; nothing changes
+                    assert e.code == gv.GV_ERR_OUT_OF_MEMORY
+                    got = before
+                assert p.g.stats()["block_capacity"] == got
+                deg = p.o.degrees().astype(np.int64)
+                assert p.g.stats()["pool_blocks_used"] == int(((deg + got - 1) // got).sum())
             p.check()
     finally:
         p.close()
