@@ -650,8 +650,12 @@ def run_serving(args):
         upd = sum(len(r) for r in meas if r.kind in (serve.INSERT, serve.DELETE))
         span = max(r.done for r in meas) - min(r.arrival for r in meas)
         lat = serve.latency_stats(rs, skip=skip)
+        worst = max(meas, key=lambda r: r.done - r.arrival)
         levels.append({"load": load, "rate_req_per_s": rate, "p50_ms": lat["p50_ms"], "p99_ms": lat["p99_ms"],
-                       "mean_ms": lat["mean_ms"], "updates_per_s": upd / span, "requests": len(rs),
+                       "mean_ms": lat["mean_ms"], "max_ms": lat["max_ms"],
+                       "worst": {"arrival_s": worst.arrival - rs[0].arrival, "kind": worst.kind,
+                                 "pairs": len(worst)},
+                       "updates_per_s": upd / span, "requests": len(rs),
                        "warmup_requests": skip, "runs": server.runs,
                        "requests_per_run": server.merged_requests / max(server.runs, 1),
                        "failed": sum(1 for r in rs if r.status != gv.GV_OK)})
