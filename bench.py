@@ -415,7 +415,7 @@ def run_ours(args, rank, world, local_rank):
         d2h = args.queries + 32
         e2e = {"value": args.steps * (inserted + deleted) / (e_ms / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "ms_per_step": e_ms / args.steps, "timer": "host wall clock around synchronised calls"}
+               "ms_per_step": e_ms / args.steps, "timer": "host wall clock from the first call of the step to the device synchronisation after its last"}
 
     # the slowest rank's times; every rank processed the same units
     mx = max_over_ranks([total_ms] + ([e2e["ms_per_step"]] if e2e else []), world, dev)

@@ -13,10 +13,20 @@
  *   - Array arguments are plain pointers.  Unless an entry point says
  *     otherwise, an array may live in device memory (cudaMalloc, a torch CUDA
  *     tensor) or in host memory (pinned or pageable).  Host arrays are copied
- *     to and from library-owned device staging buffers on `stream`; a call
- *     with a host OUTPUT array synchronises `stream` before it returns.
- *   - The caller owns every array it passes; it must stay valid until the
- *     call's work on `stream` has completed.  The library owns the graph
+ *     to and from library-owned device staging buffers.  The edge batches of
+ *     gv_bulk_build, gv_insert_edges, gv_insert_edges_weighted,
+ *     gv_delete_edges and gv_query_edges are copied on a copy stream the library owns, into one
+ *     of three rotating staging sets, so that a call's copies overlap the
+ *     kernels of the calls before it; `stream` waits for them.  Their host
+ *     OUTPUT arrays (counts, query results) are written in stream order: a
+ *     page-locked output holds its values once `stream` has reached the
+ *     end of the call (synchronise `stream`, or gv_sync, before reading it);
+ *     a pageable output is complete when the call returns.  Other calls with
+ *     a host output array synchronise `stream` before they return.
+ *   - The caller owns every array it passes; it must stay valid, and a host
+ *     input unchanged, until the call's work on `stream` has completed (a
+ *     pageable host input may be reused once the call returns).  The
+ *     library owns the graph
  *     state, the block pool (unless gv_config.pool_mem is given) and its
  *     scratch memory.
  *   - Calls are asynchronous and ordered on `stream` (a cudaStream_t, passed

@@ -33,6 +33,18 @@ struct Staging {
     DevBuf buf[6];
 };
 
+// One staging set for the host inputs of a batch call (sources,
+// destinations, payloads) and the events that order it: one per piece
+// landed, and one when the call that read it has finished with it.
+constexpr int kInSets = 3;
+constexpr int kPipePieces = 4;
+struct InSet {
+    DevBuf src, dst, wts;
+    cudaEvent_t piece[kPipePieces] = {};
+    cudaEvent_t free_ev = nullptr;
+    bool used = false;
+};
+
 }  // namespace
 
 struct gv_graph {
@@ -94,7 +106,12 @@ struct gv_graph {
     unsigned long long used_ub = 0;  // upper bound of blocks in use (pool growth policy)
     cudaStream_t side = nullptr;     // second stream: concurrent mark tiers, staging copies
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    cudaEvent_t ev_stage[5] = {};    // staging pipeline: start + one per piece
+    // host input staging: kInSets rotating sets of device buffers filled on
+    // the copy stream; a set's free event is recorded on the call stream
+    // after the last kernel of the call that read it
+    cudaStream_t copy = nullptr;
+    InSet in_sets[kInSets];
+    uint32_t in_round = 0;
     // analytics scratch: items, two frontiers, counters, PageRank vectors
     unsigned long long an_icap = 0, an_vcap = 0;
     uint2 *an_items = nullptr;
@@ -585,45 +602,96 @@ gv_status maybe_grow(gv_graph *g, uint64_t n, cudaStream_t s) {
     return GV_OK;
 }
 
-// Host-array batches of at least kPipeMin pairs are staged in kPipePieces
-// pieces on the graph's second stream, and each piece is counted on the call
+// Host-array batches are staged into the next of kInSets rotating sets of
+// device buffers on the graph's copy stream, so that a call's copies can run
+// while the kernels of earlier calls still read their own sets; the call
+// stream waits for the copies, and a set is refilled only after the call
+// that read it recorded its free event.  Batches of at least kPipeMin pairs
+// are copied in kPipePieces pieces and each piece is counted on the call
 // stream as soon as it has landed: the counting pass overlaps the copies of
-// the later pieces.  (Counting is order-independent: ranks come from atomics.)
+// the later pieces (counting is order-independent: ranks come from atomics).
 constexpr uint64_t kPipeMin = 1ull << 20;
-constexpr int kPipePieces = 4;
 
-bool can_pipeline(const gv_graph *g, const uint32_t *src, const uint32_t *dst, uint64_t n) {
-    if (n < kPipeMin || !g->side || g->C == 0) return false;
-    for (auto e : g->ev_stage)
-        if (!e) return false;
-    return is_host_ptr(src) && is_host_ptr(dst);
+gv_status set_buf(DevBuf &b, size_t bytes, void **out) {
+    if (b.bytes < bytes) {
+        if (b.p) cudaFree(b.p);  // synchronises the device: no copy or kernel still uses it
+        b.p = nullptr;
+        b.bytes = 0;
+        const size_t want = std::max(bytes, (size_t)4096);
+        if (cudaMalloc(&b.p, want) != cudaSuccess) {
+            cudaGetLastError();
+            return GV_ERR_OUT_OF_MEMORY;
+        }
+        b.bytes = want;
+    }
+    *out = b.p;
+    return GV_OK;
 }
 
-// Stages src/dst (host arrays) into the staging slots 0/1 and runs the
-// counting pass of `mode` over them, piece by piece.
-gv_status stage_and_count(gv_graph *g, int mode, const uint32_t *src, const uint32_t *dst, uint64_t n,
-                          cudaStream_t s, const void **dsrc, const void **ddst) {
-    void *d0 = nullptr, *d1 = nullptr;
-    GV_TRY(stage_buf(g, 0, n * 4, &d0));
-    GV_TRY(stage_buf(g, 1, n * 4, &d1));
-    // the copies must not overwrite staging buffers that earlier work on s reads
-    GV_CK(cudaEventRecord(g->ev_stage[0], s));
-    GV_CK(cudaStreamWaitEvent(g->side, g->ev_stage[0], 0));
+// Device views of a batch's inputs (host arrays staged, device arrays as
+// they are); with `count`, also the counting pass of `mode`.  *set_out = the
+// staging set used (-1: none); the caller records its free event on `s`
+// after the call's last launch.
+gv_status stage_batch(gv_graph *g, int mode, const uint32_t *src, const uint32_t *dst, const uint32_t *wts,
+                      uint64_t n, cudaStream_t s, bool count, const void **dsrc, const void **ddst,
+                      const void **dwts, int *set_out) {
+    *set_out = -1;
+    *dsrc = src;
+    *ddst = dst;
+    if (dwts) *dwts = wts;
+    const bool hs = is_host_ptr(src), hd = is_host_ptr(dst), hw = wts && is_host_ptr(wts);
     const GraphView v = view(g);
-    for (int k = 0; k < kPipePieces; ++k) {
-        const uint64_t lo = n * k / kPipePieces, hi = n * (k + 1) / kPipePieces;
-        GV_CK(cudaMemcpyAsync(static_cast<uint32_t *>(d0) + lo, src + lo, (hi - lo) * 4, cudaMemcpyHostToDevice,
-                              g->side));
-        GV_CK(cudaMemcpyAsync(static_cast<uint32_t *>(d1) + lo, dst + lo, (hi - lo) * 4, cudaMemcpyHostToDevice,
-                              g->side));
-        GV_CK(cudaEventRecord(g->ev_stage[k + 1], g->side));
-        GV_CK(cudaStreamWaitEvent(s, g->ev_stage[k + 1], 0));
-        GV_CK(gv::launch_count_range(mode, v, static_cast<const uint32_t *>(d0), static_cast<const uint32_t *>(d1), n,
-                                     lo, hi, lcfg(g, s)));
+    if (!hs && !hd && !hw) {
+        if (count) GV_CK(gv::launch_count(mode, v, src, dst, n, lcfg(g, s)));
+        return GV_OK;
     }
-    GV_CK(gv::launch_count_finish(mode, v, n, lcfg(g, s)));
-    *dsrc = d0;
-    *ddst = d1;
+    const int k = (int)(g->in_round++ % kInSets);
+    InSet &set = g->in_sets[k];
+    void *bs = nullptr, *bd = nullptr, *bw = nullptr;
+    if (hs) GV_TRY(set_buf(set.src, n * 4, &bs));
+    if (hd) GV_TRY(set_buf(set.dst, n * 4, &bd));
+    if (hw) GV_TRY(set_buf(set.wts, n * 4, &bw));
+    const bool async = g->copy && set.free_ev;  // a set with free_ev has all its events
+    cudaStream_t cs = async ? g->copy : s;
+    if (async && set.used) GV_CK(cudaStreamWaitEvent(cs, set.free_ev, 0));
+    const uint32_t *ss = hs ? static_cast<const uint32_t *>(bs) : src;
+    const uint32_t *sd = hd ? static_cast<const uint32_t *>(bd) : dst;
+    const int pieces = (count && n >= kPipeMin && g->C != 0) ? kPipePieces : 1;
+    for (int p = 0; p < pieces; ++p) {
+        const uint64_t lo = n * p / pieces, hi = n * (p + 1) / pieces;
+        if (hi > lo) {
+            if (hs) GV_CK(cudaMemcpyAsync(static_cast<uint32_t *>(bs) + lo, src + lo, (hi - lo) * 4,
+                                          cudaMemcpyHostToDevice, cs));
+            if (hd) GV_CK(cudaMemcpyAsync(static_cast<uint32_t *>(bd) + lo, dst + lo, (hi - lo) * 4,
+                                          cudaMemcpyHostToDevice, cs));
+            if (hw) GV_CK(cudaMemcpyAsync(static_cast<uint32_t *>(bw) + lo, wts + lo, (hi - lo) * 4,
+                                          cudaMemcpyHostToDevice, cs));
+        }
+        if (async) {
+            GV_CK(cudaEventRecord(set.piece[p], cs));
+            GV_CK(cudaStreamWaitEvent(s, set.piece[p], 0));
+        }
+        if (count && pieces > 1) GV_CK(gv::launch_count_range(mode, v, ss, sd, n, lo, hi, lcfg(g, s)));
+    }
+    if (count) {
+        if (pieces > 1) GV_CK(gv::launch_count_finish(mode, v, n, lcfg(g, s)));
+        else GV_CK(gv::launch_count(mode, v, ss, sd, n, lcfg(g, s)));
+    }
+    set.used = true;
+    // free once the kernels launched so far are done; the caller records it
+    // again after its last launch (an error return in between still leaves
+    // the set guarded by this record)
+    if (async) GV_CK(cudaEventRecord(set.free_ev, s));
+    *set_out = k;
+    *dsrc = ss;
+    *ddst = sd;
+    if (dwts) *dwts = hw ? bw : wts;
+    return GV_OK;
+}
+
+// The staging set of a call is free once the call stream reaches this point.
+gv_status release_set(gv_graph *g, int set, cudaStream_t s) {
+    if (set >= 0 && g->in_sets[set].free_ev) GV_CK(cudaEventRecord(g->in_sets[set].free_ev, s));
     return GV_OK;
 }
 
@@ -635,12 +703,14 @@ gv_status insert_impl(gv_graph *g, const uint32_t *src, const uint32_t *dst, uin
     DeviceGuard dg(g->device);
     g->last_stream = s;
     const void *dsrc = src, *ddst = dst, *dwts = wts;
-    const bool pipe = !(g->flags & GV_DEDUP) && can_pipeline(g, src, dst, n);
-    if (!pipe) {
+    // the plain insert of a laid-out graph stages host inputs on the copy
+    // stream (stage_batch); the first batch and set semantics copy them here
+    const bool plain = g->C != 0 && !(g->flags & GV_DEDUP) && n > 0;
+    if (!plain) {
         GV_TRY(input_ptr(g, 0, src, n * 4, s, &dsrc));
         GV_TRY(input_ptr(g, 1, dst, n * 4, s, &ddst));
+        if (wts) GV_TRY(input_ptr(g, 3, wts, n * 4, s, &dwts));
     }
-    if (wts) GV_TRY(input_ptr(g, 3, wts, n * 4, s, &dwts));
     void *dcounts = counts;
     bool host_counts = false;
     if (counts) GV_TRY(output_ptr(g, 2, counts, 16, &dcounts, &host_counts));
@@ -704,17 +774,15 @@ gv_status insert_impl(gv_graph *g, const uint32_t *src, const uint32_t *dst, uin
         if (n == 0) {
             if (counts) GV_CK(cudaMemsetAsync(dcounts, 0, 16, s));
         } else {
-            GraphView v = view(g);
-            if (pipe) GV_TRY(stage_and_count(g, gv::MODE_INSERT, src, dst, n, s, &dsrc, &ddst));
-            else GV_CK(gv::launch_count(gv::MODE_INSERT, v, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, lcfg(g, s)));
-            GV_CK(gv::launch_insert_tail(v, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, g->tcap,
+            int set = -1;
+            GV_TRY(stage_batch(g, gv::MODE_INSERT, src, dst, wts, n, s, true, &dsrc, &ddst, &dwts, &set));
+            GV_CK(gv::launch_insert_tail(view(g), (const uint32_t *)dsrc, (const uint32_t *)ddst, n, g->tcap,
                                          (unsigned long long *)dcounts, lcfg(g, s), (const uint32_t *)dwts));
+            GV_TRY(release_set(g, set, s));
         }
     }
-    if (host_counts) {
-        GV_CK(cudaMemcpyAsync(counts, dcounts, 16, cudaMemcpyDeviceToHost, s));
-        GV_CK(cudaStreamSynchronize(s));
-    }
+    // host counts land in stream order (a pageable target completes here)
+    if (host_counts) GV_CK(cudaMemcpyAsync(counts, dcounts, 16, cudaMemcpyDeviceToHost, s));
     return check_launch();
 }
 
@@ -762,23 +830,18 @@ gv_status member_impl(gv_graph *g, int mode, const uint32_t *src, const uint32_t
         return check_launch();
     }
     const void *dsrc = src, *ddst = dst;
-    const bool pipe = can_pipeline(g, src, dst, n);
-    if (!pipe) {
-        GV_TRY(input_ptr(g, 0, src, n * 4, s, &dsrc));
-        GV_TRY(input_ptr(g, 1, dst, n * 4, s, &ddst));
-    }
     void *dq = qout;
     bool hq = false;
     if (mode == gv::MODE_QUERY) GV_TRY(output_ptr(g, 3, qout, n, &dq, &hq));
     GV_TRY(ensure_batch(g, n, mode));
-    GraphView v = view(g);
-    if (pipe) GV_TRY(stage_and_count(g, mode, src, dst, n, s, &dsrc, &ddst));
-    else GV_CK(gv::launch_count(mode, v, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, lcfg(g, s)));
-    GV_CK(gv::launch_member_tail(mode, v, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, g->tcap,
+    int set = -1;
+    GV_TRY(stage_batch(g, mode, src, dst, nullptr, n, s, true, &dsrc, &ddst, nullptr, &set));
+    GV_CK(gv::launch_member_tail(mode, view(g), (const uint32_t *)dsrc, (const uint32_t *)ddst, n, g->tcap,
                                  (unsigned long long *)dcounts, (uint8_t *)dq, lcfg(g, s)));
+    GV_TRY(release_set(g, set, s));
+    // host outputs land in stream order (a pageable target completes here)
     if (host_counts) GV_CK(cudaMemcpyAsync(counts, dcounts, 16, cudaMemcpyDeviceToHost, s));
     if (hq) GV_CK(cudaMemcpyAsync(qout, dq, n, cudaMemcpyDeviceToHost, s));
-    if (host_counts || hq) GV_CK(cudaStreamSynchronize(s));
     return check_launch();
 }
 
@@ -887,11 +950,25 @@ gv_status gv_create(const gv_config *cfg, uint32_t num_vertices, void *stream, g
         g->side = nullptr;
         g->ev_fork = g->ev_join = nullptr;
     }
-    for (auto &e : g->ev_stage)
-        if (g->side && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+    // copy stream and staging events; without them host inputs are copied
+    // on the call stream
+    if (cudaStreamCreateWithFlags(&g->copy, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        g->copy = nullptr;
+    }
+    for (auto &set : g->in_sets) {
+        bool ok = g->copy && cudaEventCreateWithFlags(&set.free_ev, cudaEventDisableTiming) == cudaSuccess;
+        for (auto &e : set.piece) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
             cudaGetLastError();
-            e = nullptr;
+            if (set.free_ev) cudaEventDestroy(set.free_ev);
+            for (auto &e : set.piece) {
+                if (e) cudaEventDestroy(e);
+                e = nullptr;
+            }
+            set.free_ev = nullptr;  // this set copies on the call stream
         }
+    }
     g->flags = c.flags;
     g->item_blocks_cfg = c.item_blocks;
     if (c.dense_shift) g->dense_shift = std::min<uint32_t>(c.dense_shift, 31);
@@ -959,8 +1036,18 @@ gv_status gv_destroy(gv_graph *g) {
         }
         if (g->ev_fork) cudaEventDestroy(g->ev_fork);
         if (g->ev_join) cudaEventDestroy(g->ev_join);
-        for (auto e : g->ev_stage)
-            if (e) cudaEventDestroy(e);
+        if (g->copy) {
+            cudaStreamSynchronize(g->copy);
+            cudaStreamDestroy(g->copy);
+        }
+        for (auto &set : g->in_sets) {
+            dfree(set.src.p);
+            dfree(set.dst.p);
+            dfree(set.wts.p);
+            if (set.free_ev) cudaEventDestroy(set.free_ev);
+            for (auto e : set.piece)
+                if (e) cudaEventDestroy(e);
+        }
         cudaGetLastError();
     }
     delete g;

@@ -406,3 +406,68 @@ def test_large_host_batches_staged_in_pieces(pinned):
         p.check()
     finally:
         p.close()
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_host_batches_in_flight_stream_order(weighted):
+    # host-array calls issued back to back without a synchronisation: their
+    # copies run on the library's copy stream into rotating staging sets
+    # while earlier calls compute; page-locked outputs land in stream order.
+    # Seven calls cycle through the sets twice (a set is refilled only after
+    # the call that read it); one pinned input pair is reused by an insert
+    # and a later delete; large batches take the piecewise path.
+    import torch
+    import paper_2306_08252_gb300 as gv
+    scale, nv = 14, 1 << 14
+    flags = gv.GV_WEIGHTED if weighted else 0
+    p = Pair(nv, C=8, pool_bytes=256 << 20, flags=flags)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).pin_memory()
+    try:
+        bs, bd = W.rmat_pairs(77, 0, 100_000, scale)
+        p.bulk(bs, bd)
+        a_s, a_d = W.rmat_pairs(77, 1, (1 << 20) + 999, scale)     # piecewise staging
+        b_s, b_d = W.rmat_pairs(77, 2, 30_000, scale)
+        q_s = np.concatenate([a_s[:50_000], b_s[:10_000]])
+        q_d = np.concatenate([a_d[:50_000], b_d[:10_000]])
+        rng = np.random.default_rng(77)
+        a_w = rng.integers(0, 1 << 32, a_s.size, dtype=np.uint64).astype(np.uint32)
+        ha_s, ha_d, hb_s, hb_d = pin(a_s), pin(a_d), pin(b_s), pin(b_d)
+        hq_s, hq_d, ha_w = pin(q_s), pin(q_d), pin(a_w)
+        cnts = [torch.zeros(2, dtype=torch.int64).pin_memory() for _ in range(5)]
+        outs = [torch.zeros(q_s.size, dtype=torch.uint8).pin_memory() for _ in range(2)]
+        g = p.g
+        if weighted:
+            g.insert_edges_weighted(ha_s, ha_d, ha_w, cnts[0])
+        else:
+            g.insert_edges(ha_s, ha_d, cnts[0])
+        g.query_edges(hq_s, hq_d, outs[0])
+        g.insert_edges(hb_s, hb_d, cnts[1])
+        g.delete_edges(ha_s, ha_d, cnts[2])                          # reuses the first call's pinned input
+        g.query_edges(hq_s, hq_d, outs[1])
+        g.delete_edges(hb_s[:7_000], hb_d[:7_000], cnts[3])
+        g.insert_edges(ha_s[:5_000], ha_d[:5_000], cnts[4])
+        torch.cuda.synchronize()
+        o = p.o
+        exp0 = o.insert_edges_weighted(a_s, a_d, a_w) if weighted else o.insert_edges(a_s, a_d)
+        expq0 = o.query_edges(q_s, q_d)
+        exp1 = o.insert_edges(b_s, b_d)
+        exp2 = o.delete_edges(a_s, a_d)
+        expq1 = o.query_edges(q_s, q_d)
+        exp3 = o.delete_edges(b_s[:7_000], b_d[:7_000])
+        exp4 = o.insert_edges(a_s[:5_000], a_d[:5_000])
+        got = [tuple(int(x) for x in c.tolist()) for c in cnts]
+        assert got == [exp0, exp1, exp2, exp3, exp4]
+        np.testing.assert_array_equal(outs[0].numpy(), expq0)
+        np.testing.assert_array_equal(outs[1].numpy(), expq1)
+        p.check()
+        if weighted:
+            vids = np.arange(nv, dtype=np.uint32)
+            off, nb, wt = g.neighbors_weighted(vids)
+            ooff, onb, owt = o.neighbors_weighted(vids)
+            np.testing.assert_array_equal(off, ooff)
+            seg = np.repeat(np.arange(nv), np.diff(off.astype(np.int64)))
+            order = np.lexsort((wt, nb, seg))
+            np.testing.assert_array_equal(nb[order], onb)
+            np.testing.assert_array_equal(wt[order], owt)
+    finally:
+        p.close()
