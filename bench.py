@@ -752,6 +752,35 @@ def run_rows(args):
 
     ms = timed(lambda: holder["g"].bulk_build(d_bs, d_bd, cnt), pre=mk, n=3)
     row("a5", "bulk build", bs.size, "edges", ms, 12 * bs.size + 16 * nv)
+
+    # f4 (memory footprint, the paper's Table 5): device memory of the
+    # structure after the bulk build, and after one insert batch of 100K / 1M
+    # / 10M pairs on top of it (fresh graph each): the library's own
+    # allocations, the part of the pool in use, and the drop of free device
+    # memory reported by the driver (which includes the whole pool
+    # reservation)
+    fp = []
+    batches = {B: (t(us[:B]), t(ud[:B])) for B in (100_000, 1_000_000, 10_000_000)}
+    for B in (0, 100_000, 1_000_000, 10_000_000):
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        gf = gv.Graph(nv, block_capacity=C, pool_bytes=POOL_BYTES)
+        gf.bulk_build(d_bs, d_bd, cnt)
+        if B:
+            gf.insert_edges(batches[B][0], batches[B][1], cnt)
+        torch.cuda.synchronize()
+        free1 = torch.cuda.mem_get_info()[0]
+        st = gf.stats()
+        used = st["pool_blocks_used"] * (4 * C + 12)
+        fp.append({"batch": B or "bulk only", "entries": st["num_edges"], "pool_blocks_used": st["pool_blocks_used"],
+                   "pool_in_use_bytes": used, "bytes_per_entry": used / max(st["num_edges"], 1),
+                   "library_device_bytes": st["device_bytes"], "pool_reserved_bytes": st["pool_bytes"],
+                   "driver_free_drop_bytes": free0 - free1})
+        gf.close()
+    del batches
+    rows.append({"row": "f4-footprint", "what": "device memory after bulk build (+ one insert batch), C=16, "
+                 "2 GiB pool", "footprint": fp})
+    print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
     g = holder["g"]
     deg0, _ = g.degrees()
     deg0 = deg0.astype(np.int64)
