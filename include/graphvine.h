@@ -485,12 +485,8 @@ gv_status gv_bfs(gv_graph *g, uint32_t source, uint32_t *dist, uint32_t *h_level
  * 32-bit payload on a graph created with GV_WEIGHTED (0 for entries inserted
  * without one) and 1 otherwise, so on an unweighted graph the result equals
  * gv_bfs's distances.  Computed by Bellman-Ford rounds over a frontier of
- * vertices whose distance fell, in distance bands of width delta (a
- * near-far split: falls at or past the band limit wait on a pile until the
- * frontier of the band is exhausted); on a weighted graph delta is the mean
- * length of the source's entries (at least 1), on an unweighted one there is
- * no band.  The distances are unique; the number of rounds depends on delta
- * and on the order of the atomic minima.
+ * vertices whose distance fell; the distances are unique, the number of
+ * rounds depends on the order of the atomic minima.
  *   source    a vertex id < the vertex count (else GV_ERR_INVALID_ARG); a
  *             deleted source reaches nothing.
  *   dist      n uint64 (device or host), n = vertex count: dist[source] = 0,
@@ -501,12 +497,6 @@ gv_status gv_bfs(gv_graph *g, uint32_t source, uint32_t *dist, uint32_t *h_level
  * Synchronises `stream` once per four rounds (it reads the frontier size).
  */
 gv_status gv_sssp(gv_graph *g, uint32_t source, uint64_t *dist, uint32_t *h_rounds, void *stream);
-
-/* gv_sssp_delta -- gv_sssp with the band width given: 0 = automatic (as
- * gv_sssp), 0xFFFFFFFFFFFFFFFF = no band (plain frontier Bellman-Ford), any
- * other value = that width (weighted graphs; unweighted ones use no band). */
-gv_status gv_sssp_delta(gv_graph *g, uint32_t source, uint64_t delta, uint64_t *dist, uint32_t *h_rounds,
-                        void *stream);
 
 /*
  * gv_pagerank -- `iterations` steps of PageRank power iteration in fp64 over

@@ -181,46 +181,16 @@ cudaError_t launch_bfs_level(const GraphView &g, uint32_t aib, const uint32_t *c
 
 // ------------------------------------------------ single-source shortest paths
 
-// Frontier Bellman-Ford with atomic minima, in distance bands (a near-far
-// split of the frontier): an entry (u, v) of a frontier vertex offers
-// dist[u] + length to v (payload on a weighted graph, 1 otherwise), taken by
-// a 64-bit atomicMin.  A vertex whose distance fell below the band limit T
-// joins the next frontier (once per round: stamp[v] = r + 1 by exchange);
-// one whose distance fell to T or more goes on the far pile (once per pile:
-// fstamp[v] = pile epoch by exchange, so a pile never holds more than |V|
-// entries), and the pile's least offered distance is kept.  When a round
-// leaves the next frontier empty, the band moves up to
-// T' = max(T + delta, least offered distance + 1) and the pile is split by
-// each vertex's current distance d: d < T means it was relaxed at d already
-// (every fall below T joined a frontier, and no frontier is left), so it is
-// dropped; d < T' joins the next frontier; the rest form the next pile.
-// Distances are lengths of real paths and every fall is relaxed in some
-// round, so the fixpoint is the shortest-path distance whatever the order
-// of the minima; bands only bound how often a vertex is relaxed again.  With
-// T = infinity (unit lengths, or a caller's delta of 2^64 - 1) it is plain
-// frontier Bellman-Ford.
+// Frontier Bellman-Ford with atomic minima: the frontier of round r holds
+// the vertices whose distance fell in round r - 1; each of their stored
+// entries (u, v) offers dist[u] + length to v (payload on a weighted graph,
+// 1 otherwise), taken by a 64-bit atomicMin.  A vertex whose distance fell
+// joins the next frontier once per round (stamp[v] = r + 1 by exchange).
+// Distances are lengths of real paths and every fall is propagated, so the
+// fixpoint is the shortest-path distance whatever the order of the minima;
+// with non-negative lengths it is reached within nv rounds.
 
-__device__ __forceinline__ unsigned long long sat_add(unsigned long long a, unsigned long long b) {
-    return a > ~0ull - b ? ~0ull : a + b;
-}
-
-// New band limit when the next frontier is empty and the pile is not.
-__device__ __forceinline__ unsigned long long band_limit(const SsspState *st, uint32_t p) {
-    const unsigned long long t = sat_add(st->T, st->delta);
-    const unsigned long long m = sat_add(st->far_min[p], 1ull);
-    return t > m ? t : m;
-}
-
-__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
-    for (int off = 16; off; off >>= 1) {
-        const unsigned long long y = __shfl_xor_sync(FULL, v, off);
-        v = y < v ? y : v;
-    }
-    return v;
-}
-
-__global__ void k_sssp_seed(GraphView g, uint32_t source, unsigned long long *dist, uint32_t *cur, uint32_t *ctr,
-                            SsspState *st, unsigned long long delta) {
+__global__ void k_sssp_seed(GraphView g, uint32_t source, unsigned long long *dist, uint32_t *cur, uint32_t *ctr) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         const bool live = source < g.nv && g.alive[source];
         if (live) {
@@ -229,18 +199,8 @@ __global__ void k_sssp_seed(GraphView g, uint32_t source, unsigned long long *di
         }
         ctr[0] = live ? 1u : 0u;  // frontier size
         ctr[1] = 0;               // items
-        ctr[2] = 0;               // next frontier size (relaxation)
+        ctr[2] = 0;               // next frontier size
         ctr[3] = live ? 1u : 0u;  // rounds with a non-empty frontier
-        ctr[4] = 0;               // next frontier size (pile split)
-        // round 0 relaxes the source with no band; the mean length of its
-        // entries sets an automatic delta (delta == 0)
-        st->T = ~0ull;
-        st->delta = delta;
-        st->far_n[0] = st->far_n[1] = 0;
-        st->far_min[0] = st->far_min[1] = ~0ull;
-        st->len_sum = st->len_cnt = 0;
-        st->parity = 0;
-        st->epoch = 1;  // fstamp is cleared to 0
     }
 }
 
@@ -248,18 +208,13 @@ template <bool WEIGHTED>
 __global__ void __launch_bounds__(256) k_sssp_relax(GraphView g, const uint2 *__restrict__ items,
                                                     const uint32_t *nitems, uint32_t aib, unsigned long long *dist,
                                                     uint32_t *stamp, uint32_t round, uint32_t *next,
-                                                    uint32_t *nnext, SsspState *st, uint32_t *fstamp,
-                                                    uint32_t *far_v, unsigned long long fcap) {
+                                                    uint32_t *nnext) {
     __shared__ uint32_t s_bid[8][32];
     const uint32_t n = *nitems;
     const uint32_t lane = lane_id();
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t nv = g.nv;
-    const unsigned long long T = st->T;
-    const uint32_t p = st->parity, epoch = st->epoch;
-    uint32_t *fv = far_v + p * fcap;
-    unsigned long long lsum = 0, lcnt = 0;  // round 0: lengths of the source's entries
     for (uint32_t it = warp; it < n; it += nwarps) {
         const uint2 itm = items[it];
         const unsigned long long du = __ldcg(dist + itm.x);
@@ -267,26 +222,17 @@ __global__ void __launch_bounds__(256) k_sssp_relax(GraphView g, const uint2 *__
         auto relax = [&](uint4 e4, uint4 w4, uint32_t vm) {
             const uint32_t e[4] = {e4.x, e4.y, e4.z, e4.w};
             const uint32_t w[4] = {w4.x, w4.y, w4.z, w4.w};
-            uint32_t push = 0, fpush = 0;
-            unsigned long long fmin = ~0ull;
+            uint32_t push = 0;
 #pragma unroll
             for (uint32_t j = 0; j < 4; ++j) {
                 if ((vm >> j) & 1u) {
                     const uint32_t v = e[j];
                     const unsigned long long nd = du + (WEIGHTED ? (unsigned long long)w[j] : 1ull);
-                    if (round == 0) {
-                        lsum += WEIGHTED ? w[j] : 1u;
-                        ++lcnt;
-                    }
                     if (v >= nv) {
                         bad = true;
-                    } else if (nd < __ldcg(dist + v) && nd < atomicMin(dist + v, nd)) {
-                        if (nd >= T) {
-                            fmin = nd < fmin ? nd : fmin;
-                            if (atomicExch(fstamp + v, epoch) != epoch) fpush |= 1u << j;
-                        } else if (atomicExch(stamp + v, round + 1) != round + 1) {
-                            push |= 1u << j;
-                        }
+                    } else if (nd < __ldcg(dist + v) && nd < atomicMin(dist + v, nd) &&
+                               atomicExch(stamp + v, round + 1) != round + 1) {
+                        push |= 1u << j;
                     }
                 }
             }
@@ -299,24 +245,6 @@ __global__ void __launch_bounds__(256) k_sssp_relax(GraphView g, const uint2 *__
 #pragma unroll
             for (uint32_t j = 0; j < 4; ++j)
                 if ((push >> j) & 1u) next[o++] = e[j];
-            // far pile: warp-aggregated append; the least offered distance
-            // by one atomic per warp
-            fmin = warp_min_u64(fmin);
-            uint32_t ftot;
-            const uint32_t fex = warp_excl_scan(__popc(fpush), &ftot);
-            unsigned long long fb = 0;
-            if (lane == 0) {
-                if (fmin != ~0ull) atomicMin(&st->far_min[p], fmin);
-                if (ftot) fb = atomicAdd(&st->far_n[p], (unsigned long long)ftot);
-            }
-            fb = __shfl_sync(FULL, fb, 0);
-            unsigned long long fo = fb + fex;
-#pragma unroll
-            for (uint32_t j = 0; j < 4; ++j)
-                if ((fpush >> j) & 1u) {
-                    if (fo < fcap) fv[fo] = e[j];  // at most |V| <= fcap: one entry per vertex and pile
-                    ++fo;
-                }
         };
         bool ok;
         if constexpr (WEIGHTED)
@@ -326,132 +254,30 @@ __global__ void __launch_bounds__(256) k_sssp_relax(GraphView g, const uint2 *__
                                   [&](uint4 e4, uint32_t vm) { relax(e4, make_uint4(1, 1, 1, 1), vm); });
         if ((!ok || bad) && lane == 0) latch_status(g.dev, 5u /* GV_ERR_STATE */);
     }
-    if (round == 0) {
-        lsum = warp_sum_u64(lsum);
-        lcnt = warp_sum_u64(lcnt);
-        if (lane == 0 && lcnt) {
-            atomicAdd(&st->len_sum, lsum);
-            atomicAdd(&st->len_cnt, lcnt);
-        }
-    }
-}
-
-// Pile split, when the round left the next frontier empty (the condition
-// reads only values this kernel does not change): see the comment above.
-__global__ void __launch_bounds__(256) k_sssp_split(GraphView g, const unsigned long long *__restrict__ dist,
-                                                    uint32_t *stamp, uint32_t round, uint32_t *next, uint32_t *ctr,
-                                                    SsspState *st, uint32_t *fstamp, uint32_t *far_v,
-                                                    unsigned long long fcap) {
-    const uint32_t p = st->parity;
-    const unsigned long long nfar = st->far_n[p];
-    if (ctr[2] != 0 || nfar == 0) return;
-    const unsigned long long T = st->T, Tn = band_limit(st, p);
-    const uint32_t next_epoch = st->epoch + 1;
-    const unsigned long long cnt = nfar < fcap ? nfar : fcap;
-    const uint32_t *fv = far_v + p * fcap;
-    uint32_t *kv = far_v + (p ^ 1u) * fcap;
-    const uint32_t lane = lane_id();
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    // warp-aligned trips: every lane of a warp takes part in the collectives
-    for (unsigned long long i0 = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) & ~31ull; i0 < cnt;
-         i0 += stride) {
-        const unsigned long long i = i0 + lane;
-        uint32_t v = 0;
-        unsigned long long d = ~0ull;
-        bool near = false, keep = false;
-        if (i < cnt) {
-            v = fv[i];
-            if (v < g.nv) {
-                d = __ldcg(dist + v);
-                if (d >= T) {  // below T: relaxed at d already
-                    if (d < Tn) {
-                        near = atomicExch(stamp + v, round + 1) != round + 1;
-                    } else {
-                        keep = true;
-                        fstamp[v] = next_epoch;
-                    }
-                }
-            }
-        }
-        const uint32_t nb = __ballot_sync(FULL, near), kb = __ballot_sync(FULL, keep);
-        const unsigned long long mn = warp_min_u64(keep ? d : ~0ull);
-        uint32_t nbase = 0;
-        unsigned long long kbase = 0;
-        if (lane == 0) {
-            if (nb) nbase = atomicAdd(&ctr[4], (uint32_t)__popc(nb));
-            if (kb) {
-                kbase = atomicAdd(&st->far_n[p ^ 1u], (unsigned long long)__popc(kb));
-                atomicMin(&st->far_min[p ^ 1u], mn);
-            }
-        }
-        nbase = __shfl_sync(FULL, nbase, 0);
-        kbase = __shfl_sync(FULL, kbase, 0);
-        const uint32_t below = (1u << lane) - 1u;
-        if (near) next[nbase + __popc(nb & below)] = v;
-        if (keep) {
-            const unsigned long long o = kbase + __popc(kb & below);
-            if (o < fcap) kv[o] = v;
-        }
-    }
-}
-
-// End of a round: band and pile bookkeeping, then the next frontier becomes
-// the current one: ctr = {frontier, items, next (relaxation), rounds, next
-// (split)}.
-__global__ void k_sssp_advance(uint32_t *ctr, SsspState *st, uint32_t round, unsigned long long delta_mult) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        const uint32_t p = st->parity;
-        if (round == 0) {
-            // first band: delta from the source's entries unless given
-            if (st->delta == 0) {
-                const unsigned long long mean = st->len_cnt ? st->len_sum / st->len_cnt : 1ull;
-                st->delta = mean * delta_mult > 0 ? mean * delta_mult : 1ull;
-            }
-            if (st->delta != ~0ull) st->T = st->delta;
-        } else if (ctr[2] == 0 && st->far_n[p] > 0) {
-            st->T = band_limit(st, p);
-            st->far_n[p] = 0;
-            st->far_min[p] = ~0ull;
-            st->parity = p ^ 1u;
-            st->epoch += 1;
-        }
-        const uint32_t nxt = ctr[2] + ctr[4];
-        if (nxt) ctr[3] = round + 2;
-        ctr[0] = nxt;
-        ctr[1] = 0;
-        ctr[2] = 0;
-        ctr[4] = 0;
-    }
 }
 
 cudaError_t launch_sssp_seed(const GraphView &g, uint32_t source, unsigned long long *dist, uint32_t *stamp,
-                             uint32_t *fstamp, uint32_t *cur, uint32_t *ctr, SsspState *st,
-                             unsigned long long delta, const LaunchCfg &lc) {
+                             uint32_t *cur, uint32_t *ctr, const LaunchCfg &lc) {
     PhaseScope ps(lc, PH_ANALYTICS);
     if (g.nv) {
         cudaMemsetAsync(dist, 0xFF, (size_t)g.nv * 8, lc.stream);
         cudaMemsetAsync(stamp, 0, (size_t)g.nv * 4, lc.stream);
-        cudaMemsetAsync(fstamp, 0, (size_t)g.nv * 4, lc.stream);
     }
-    k_sssp_seed<<<1, 32, 0, lc.stream>>>(g, source, dist, cur, ctr, st, delta);
+    k_sssp_seed<<<1, 32, 0, lc.stream>>>(g, source, dist, cur, ctr);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sssp_round(const GraphView &g, uint32_t aib, const uint32_t *cur, uint32_t *next, uint2 *items,
                               uint32_t *ctr, unsigned long long *dist, uint32_t *stamp, uint32_t round,
-                              SsspState *st, uint32_t *fstamp, uint32_t *far_v, unsigned long long fcap,
-                              unsigned long long delta_mult, const LaunchCfg &lc) {
+                              const LaunchCfg &lc) {
     PhaseScope ps(lc, PH_ANALYTICS);
     const int grid = lc.num_sms * GRID_MULT;
     k_an_items<<<grid, 256, 0, lc.stream>>>(g, cur, ctr, aib, items, ctr + 1);
     if (g.wdata)
-        k_sssp_relax<true><<<grid, 256, 0, lc.stream>>>(g, items, ctr + 1, aib, dist, stamp, round, next, ctr + 2,
-                                                        st, fstamp, far_v, fcap);
+        k_sssp_relax<true><<<grid, 256, 0, lc.stream>>>(g, items, ctr + 1, aib, dist, stamp, round, next, ctr + 2);
     else
-        k_sssp_relax<false><<<grid, 256, 0, lc.stream>>>(g, items, ctr + 1, aib, dist, stamp, round, next, ctr + 2,
-                                                         st, fstamp, far_v, fcap);
-    k_sssp_split<<<grid, 256, 0, lc.stream>>>(g, dist, stamp, round, next, ctr, st, fstamp, far_v, fcap);
-    k_sssp_advance<<<1, 32, 0, lc.stream>>>(ctr, st, round, delta_mult);
+        k_sssp_relax<false><<<grid, 256, 0, lc.stream>>>(g, items, ctr + 1, aib, dist, stamp, round, next, ctr + 2);
+    k_bfs_advance<<<1, 32, 0, lc.stream>>>(ctr, round);
     return cudaGetLastError();
 }
 

@@ -117,10 +117,6 @@ struct gv_graph {
     uint2 *an_items = nullptr;
     uint32_t *an_cur = nullptr, *an_next = nullptr, *an_ctr = nullptr;
     uint32_t *an_stamp = nullptr;  // shortest paths: round in which a vertex last joined the frontier
-    gv::SsspState *sp_state = nullptr;      // shortest paths: band and far-pile state
-    uint32_t *sp_far_v = nullptr;           // far piles: vertex ids, two parities of sp_fcap
-    uint32_t *sp_fstamp = nullptr;          // per vertex: epoch of the pile that holds it
-    unsigned long long sp_fcap = 0;
     unsigned long long *rb_stats = nullptr;  // edge-block resize: degree totals / blocks per candidate C
     double *pr_c = nullptr, *pr_acc = nullptr, *pr_scal = nullptr;
     unsigned long long *pr_n = nullptr;
@@ -1024,7 +1020,6 @@ gv_status gv_destroy(gv_graph *g) {
         dfree(g->set_vbase); dfree(g->set_src); dfree(g->set_dst);
         dfree(g->pflag); dfree(g->dsrc2); dfree(g->dtmp);
         dfree(g->an_items); dfree(g->an_cur); dfree(g->an_next); dfree(g->an_ctr); dfree(g->an_stamp); dfree(g->rb_stats);
-        dfree(g->sp_state); dfree(g->sp_far_v); dfree(g->sp_fstamp);
         dfree(g->pr_c); dfree(g->pr_acc); dfree(g->pr_scal); dfree(g->pr_n);
         dfree(g->pr_cursor); dfree(g->pr_src); dfree(g->pr_dst); dfree(g->pr_off); dfree(g->pr_part);
         for (auto &b : g->stage.buf) dfree(b.p);
@@ -1629,24 +1624,13 @@ gv_status ensure_analytics(gv_graph *g, bool pagerank, bool sssp = false) {
     const unsigned long long nv = std::max<unsigned long long>(g->nv, 1);
     if (nv > g->an_vcap || !g->an_vcap) {
         dfree(g->an_cur); dfree(g->an_next); dfree(g->pr_c); dfree(g->pr_acc); dfree(g->an_stamp);
-        dfree(g->sp_far_v); dfree(g->sp_fstamp);
         g->an_vcap = 0;
         GV_TRY(dalloc(&g->an_cur, nv, &g->scratch_bytes));
         GV_TRY(dalloc(&g->an_next, nv, &g->scratch_bytes));
         g->an_vcap = nv;
     }
-    if (!g->an_ctr) GV_TRY(dalloc(&g->an_ctr, 8, &g->scratch_bytes));
-    if (sssp) {
-        if (!g->an_stamp) GV_TRY(dalloc(&g->an_stamp, g->an_vcap, &g->scratch_bytes));
-        if (!g->sp_state) GV_TRY(dalloc(&g->sp_state, 1, &g->scratch_bytes));
-        // far piles: two parities of an_vcap vertex ids (a pile holds a
-        // vertex at most once), and the per-vertex pile stamp
-        if (!g->sp_far_v) {
-            g->sp_fcap = g->an_vcap;
-            GV_TRY(dalloc(&g->sp_far_v, 2 * g->sp_fcap, &g->scratch_bytes));
-            GV_TRY(dalloc(&g->sp_fstamp, g->an_vcap, &g->scratch_bytes));
-        }
-    }
+    if (!g->an_ctr) GV_TRY(dalloc(&g->an_ctr, 4, &g->scratch_bytes));
+    if (sssp && !g->an_stamp) GV_TRY(dalloc(&g->an_stamp, g->an_vcap, &g->scratch_bytes));
     if (pagerank) {
         if (!g->pr_c) GV_TRY(dalloc(&g->pr_c, g->an_vcap, &g->scratch_bytes));
         if (!g->pr_acc) GV_TRY(dalloc(&g->pr_acc, g->an_vcap, &g->scratch_bytes));
@@ -1693,8 +1677,7 @@ gv_status gv_bfs(gv_graph *g, uint32_t source, uint32_t *dist, uint32_t *h_level
     return check_launch();
 }
 
-gv_status gv_sssp_delta(gv_graph *g, uint32_t source, uint64_t delta, uint64_t *dist, uint32_t *h_rounds,
-                        void *stream) {
+gv_status gv_sssp(gv_graph *g, uint32_t source, uint64_t *dist, uint32_t *h_rounds, void *stream) {
     if (!g || !dist || source >= g->nv) return GV_ERR_INVALID_ARG;
     DeviceGuard dg(g->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1706,44 +1689,29 @@ gv_status gv_sssp_delta(gv_graph *g, uint32_t source, uint64_t delta, uint64_t *
     const GraphView v = view(g);
     const uint32_t aib = analytics_item_blocks(g);
     unsigned long long *ddist = static_cast<unsigned long long *>(dd);
-    // unit lengths: plain rounds are breadth-first search, no band needed
-    const unsigned long long d0 = g->wdata ? delta : ~0ull;
-    GV_CK(gv::launch_sssp_seed(v, source, ddist, g->an_stamp, g->sp_fstamp, g->an_cur, g->an_ctr, g->sp_state, d0,
-                               lcfg(g, s)));
+    GV_CK(gv::launch_sssp_seed(v, source, ddist, g->an_stamp, g->an_cur, g->an_ctr, lcfg(g, s)));
     uint32_t *cur = g->an_cur, *nxt = g->an_next;
-    // rounds go out in groups between two reads of the frontier size and
-    // the far pile, as the BFS levels do.  Every round relaxes a frontier or
-    // empties part of the pile, so the loop ends; the cap only guards it.
+    // rounds go out in groups between two reads of the frontier size, as
+    // the BFS levels do; with non-negative lengths round nv finds an empty
+    // frontier
     constexpr uint32_t kGroup = 4;
-    constexpr unsigned long long kDeltaMult = 1;  // automatic band width = mean length of the source's entries
-    const unsigned long long cap = 64ull * ((unsigned long long)g->nv + 1024);
-    uint32_t rounds_done = 0;
-    for (unsigned long long round = 0;;) {
-        if (round > cap) return GV_ERR_STATE;
+    for (uint32_t round = 0; round <= g->nv;) {
         for (uint32_t k = 0; k < kGroup; ++k, ++round) {
-            GV_CK(gv::launch_sssp_round(v, aib, cur, nxt, g->an_items, g->an_ctr, ddist, g->an_stamp,
-                                        (uint32_t)round, g->sp_state, g->sp_fstamp, g->sp_far_v, g->sp_fcap,
-                                        kDeltaMult, lcfg(g, s)));
+            GV_CK(gv::launch_sssp_round(v, aib, cur, nxt, g->an_items, g->an_ctr, ddist, g->an_stamp, round,
+                                        lcfg(g, s)));
             std::swap(cur, nxt);
         }
-        gv::SsspState hs;
         GV_CK(cudaMemcpyAsync(g->h_small, g->an_ctr, 16, cudaMemcpyDeviceToHost, s));
-        GV_CK(cudaMemcpyAsync(&hs, g->sp_state, sizeof(hs), cudaMemcpyDeviceToHost, s));
         GV_CK(cudaStreamSynchronize(s));
-        const uint32_t frontier = (uint32_t)(g->h_small[0] & 0xFFFFFFFFull);
-        rounds_done = (uint32_t)(g->h_small[1] >> 32);  // ctr[3]
-        if (frontier == 0 && hs.far_n[hs.parity] == 0) break;
+        if ((uint32_t)(g->h_small[0] & 0xFFFFFFFFull) == 0) break;  // frontier empty
     }
+    const uint32_t rounds = (uint32_t)(g->h_small[1] >> 32);  // ctr[3]
     if (hd) {
         GV_CK(cudaMemcpyAsync(dist, dd, (size_t)g->nv * 8, cudaMemcpyDeviceToHost, s));
         GV_CK(cudaStreamSynchronize(s));
     }
-    if (h_rounds) *h_rounds = rounds_done;
+    if (h_rounds) *h_rounds = rounds;
     return check_launch();
-}
-
-gv_status gv_sssp(gv_graph *g, uint32_t source, uint64_t *dist, uint32_t *h_rounds, void *stream) {
-    return gv_sssp_delta(g, source, 0, dist, h_rounds, stream);
 }
 
 gv_status gv_pagerank(gv_graph *g, uint32_t iterations, double damping, double *rank, void *stream) {

@@ -155,22 +155,11 @@ cudaError_t launch_bfs_seed(const GraphView &g, uint32_t source, uint32_t *dist,
                             const LaunchCfg &lc);
 cudaError_t launch_bfs_level(const GraphView &g, uint32_t aib, const uint32_t *cur, uint32_t *next, uint2 *items,
                              uint32_t *ctr, uint32_t *dist, uint32_t level, const LaunchCfg &lc);
-// Shortest paths: band limit and width, far piles (count and least offered
-// distance per parity), round-0 length statistics, pile parity and epoch.
-struct SsspState {
-    unsigned long long T, delta;
-    unsigned long long far_n[2], far_min[2];
-    unsigned long long len_sum, len_cnt;
-    uint32_t parity, epoch;
-};
-// ctr: 8 uint32 {frontier, items, next, rounds, next from the pile split, -}
 cudaError_t launch_sssp_seed(const GraphView &g, uint32_t source, unsigned long long *dist, uint32_t *stamp,
-                             uint32_t *fstamp, uint32_t *cur, uint32_t *ctr, SsspState *st,
-                             unsigned long long delta, const LaunchCfg &lc);
+                             uint32_t *cur, uint32_t *ctr, const LaunchCfg &lc);
 cudaError_t launch_sssp_round(const GraphView &g, uint32_t aib, const uint32_t *cur, uint32_t *next, uint2 *items,
                               uint32_t *ctr, unsigned long long *dist, uint32_t *stamp, uint32_t round,
-                              SsspState *st, uint32_t *fstamp, uint32_t *far_v, unsigned long long fcap,
-                              unsigned long long delta_mult, const LaunchCfg &lc);
+                              const LaunchCfg &lc);
 cudaError_t launch_pagerank(const GraphView &g, uint32_t aib, uint32_t iterations, double damping, double *r,
                             double *c, double *acc, double *scal, unsigned long long *N, uint2 *items,
                             uint32_t *nitems, uint32_t *cursor, unsigned long long *in_off,

@@ -81,7 +81,6 @@ SIGNATURES = {
     "gv_degrees": ([c_vp, c_vp, c_vp, c_vp], ctypes.c_int),
     "gv_bfs": ([c_vp, c_u32, c_vp, ctypes.POINTER(c_u32), c_vp], ctypes.c_int),
     "gv_sssp": ([c_vp, c_u32, c_vp, ctypes.POINTER(c_u32), c_vp], ctypes.c_int),
-    "gv_sssp_delta": ([c_vp, c_u32, ctypes.c_uint64, c_vp, ctypes.POINTER(c_u32), c_vp], ctypes.c_int),
     "gv_reblock": ([c_vp, c_u32, ctypes.POINTER(c_u32), c_vp], ctypes.c_int),
     "gv_pagerank": ([c_vp, c_u32, ctypes.c_double, c_vp, c_vp], ctypes.c_int),
     "gv_reserve": ([c_vp, c_u64], ctypes.c_int),
@@ -251,15 +250,11 @@ def gv_reblock(g, block_capacity=0, stream=None):
     return c.value
 
 
-def gv_sssp(g, source, dist, stream=None, delta=None):
+def gv_sssp(g, source, dist, stream=None):
     """Shortest path lengths from `source` into `dist` (uint64 per vertex);
-    returns the number of relaxation rounds.  `delta`: band width (None or 0
-    = automatic, 2^64 - 1 = no band)."""
+    returns the number of relaxation rounds."""
     rounds = c_u32(0)
-    if delta is None:
-        check(load().gv_sssp(g, source, ptr(dist), ctypes.byref(rounds), stream), "gv_sssp")
-    else:
-        check(load().gv_sssp_delta(g, source, delta, ptr(dist), ctypes.byref(rounds), stream), "gv_sssp_delta")
+    check(load().gv_sssp(g, source, ptr(dist), ctypes.byref(rounds), stream), "gv_sssp")
     return rounds.value
 
 
@@ -525,13 +520,12 @@ class Graph:
         current degrees); returns the new block capacity."""
         return gv_reblock(self.handle, block_capacity, self._s())
 
-    def sssp(self, source, dist=None, delta=None):
+    def sssp(self, source, dist=None):
         """(dist, rounds): uint64 path lengths (2^64 - 1 = unreached); entry
-        length = payload on a weighted graph, else 1; `delta` = band width
-        (None: automatic)."""
+        length = payload on a weighted graph, else 1."""
         if dist is None:
             dist = np.zeros(max(self.stats()["num_vertices"], 1), dtype=np.uint64)
-        rounds = gv_sssp(self.handle, source, dist, self._s(), delta)
+        rounds = gv_sssp(self.handle, source, dist, self._s())
         return dist, rounds
 
     def pagerank(self, iterations, damping=0.85, rank=None):

@@ -110,25 +110,3 @@ def test_sssp_full_size_weighted_rmat():
         _check(p, [0, 12345], True)
     finally:
         p.close()
-
-
-@pytest.mark.parametrize("delta", [1, 3, 40, 1000, 0xFFFFFFFFFFFFFFFF])
-def test_sssp_band_widths(delta):
-    # every band width gives the same distances: 1 (a band per distance
-    # value), small and large widths, and no band at all
-    import paper_2306_08252_gb300 as gv
-    scale, nv = 11, 1 << 11
-    rng = np.random.default_rng(830)
-    p = Pair(nv, C=8, pool_bytes=64 << 20, flags=gv.GV_WEIGHTED)
-    try:
-        bs, bd = W.rmat_pairs(83, 0, 30000, scale)
-        _winsert(p, bs, bd, rng.integers(0, 200, bs.size).astype(np.uint32))
-        s, d = W.uniform_pairs(83, 1, 5000, nv)
-        _winsert(p, s, d, rng.integers(0, 0xFFFFFFFF, s.size, dtype=np.uint64, endpoint=True).astype(np.uint32))
-        p.delete(bs[:3000], bd[:3000])
-        for src in (0, 5, 1000):
-            dist, rounds = p.g.sssp(src, delta=delta)
-            np.testing.assert_array_equal(dist[:nv], p.o.sssp(src, True)[0])
-        assert p.g.sync() == 0
-    finally:
-        p.close()
