@@ -362,28 +362,23 @@ __global__ void __launch_bounds__(256) k_plan_insert(GraphView g) {
     }
 }
 
-// Links the popped blocks into their sources' trees (Figure 4's bit-string
-// rule) and, in the same grid, writes each touched source's new sentinel
-// (degree, block count, root of an empty source, last block) and clears its
-// counter.  Reading an old root for a walk while the sentinel pass rewrites
-// it is safe: the root only changes for a source that had no block, and
-// such a source's parents are all new blocks.
 __global__ void __launch_bounds__(256) k_link_insert(GraphView g) {
     Dev *dev = g.dev;
     const unsigned long long total = dev->alloc_total;
     const unsigned long long qf = dev->q_front, qb = dev->q_back;
-    // Edge queue exhausted: the whole call becomes a no-op.
-    const bool abort = total > qb - qf;
-    if (abort && blockIdx.x == 0 && threadIdx.x == 0) {
-        dev->abort = 1u;
-        latch_status(dev, 2u /* GV_ERR_OUT_OF_MEMORY */);
+    if (total > qb - qf) {
+        // Edge queue exhausted: the whole call becomes a no-op.
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            dev->abort = 1u;
+            latch_status(dev, 2u /* GV_ERR_OUT_OF_MEMORY */);
+        }
+        return;
     }
     const unsigned long long P = g.P;
     const unsigned long long qbase = qmod(qf, P);
     const uint32_t C = g.C;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
-    for (unsigned long long j = tid; !abort && j < total; j += stride) {
+    for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < total;
+         j += (unsigned long long)gridDim.x * blockDim.x) {
         const uint32_t t = g.t_owner[j];
         const uint4 a = g.t_a[t];
         const uint32_t deg = a.x, off = a.z, need = a.w;
@@ -411,80 +406,23 @@ __global__ void __launch_bounds__(256) k_link_insert(GraphView g) {
             g.links[2ull * pid + (k & 1u)] = id;
         }
     }
-    const uint32_t nt = dev->n_touched;
-    for (unsigned long long t = tid; t < nt; t += stride) {
-        const uint32_t u = g.t_vid[t];
-        const uint32_t vs = vslot(g.vmask, u);
-        if (!abort) {
-            const uint32_t cnt = g.vcnt[vs];
-            const uint4 a = g.t_a[t];
-            const uint32_t deg = a.x, off = a.z, need = a.w;
-            const uint32_t nb = divc(g.cmul, deg + C - 1);
-            uint4 snew = g.sent[u];
-            snew.x = deg + cnt;
-            snew.y = nb + need;
-            if (need) {
-                if (nb == 0) snew.z = g.queue[ring(qbase, off, P)];
-                snew.w = g.queue[ring(qbase, off + need - 1, P)];
-            }
-            g.sent[u] = snew;
-        }
-        g.vcnt[vs] = 0;
-    }
-}
-
-// End of an insert call (one thread, after every other CTA of the last
-// kernel): edge and queue counters unless the call aborted, the caller's
-// {inserted, rejected}, per-call scratch counters reset.
-__device__ __forceinline__ void close_insert(Dev *dev, unsigned long long n, bool abort,
-                                             unsigned long long *counts) {
-    unsigned long long rej = dev->call_b;
-    unsigned long long ins = n - rej;
-    if (abort) {
-        ins = 0;
-        rej = 0;
-    } else {
-        dev->q_front += dev->alloc_total;
-        dev->num_edges += ins;
-        dev->tot_ins += ins;
-        dev->tot_rej += rej;
-    }
-    if (counts) {
-        counts[0] = ins;
-        counts[1] = rej;
-    }
-    dev->alloc_total = 0;
-    dev->call_a = dev->call_b = dev->call_c = 0;
-    dev->n_touched = 0;
-    dev->n_items = 0;
-    dev->n_mitems = 0;
-    dev->n_tiny = 0;
-    dev->n_tiny_hi = 0;
-    dev->arena_used = 0;
-    dev->harena_used = 0;
-    dev->free_total = 0;
-    dev->abort = 0;
-    dev->done_ctas = 0;
 }
 
 // Insert scatter: one pass over the pairs, no aggregation and no atomics.
 // Pair i of source u with rank r goes to slot deg(u) + r: the free slots of
 // the last block first, then the new blocks popped for u at queue offset
 // recorded by the plan in the source's vinfo record.
-// Its last CTA closes the call: edge and queue counters, the caller's
-// {inserted, rejected}, per-call scratch counters reset.
 template <bool WEIGHTED>
 __global__ void __launch_bounds__(256) k_scatter_insert(GraphView g, const uint32_t *__restrict__ src,
                                                         const uint32_t *__restrict__ dst,
                                                         const uint32_t *__restrict__ wts,
-                                                        unsigned long long n, unsigned long long *counts) {
-    Dev *dev = g.dev;
-    const bool abort = dev->abort != 0;
+                                                        unsigned long long n) {
+    if (g.dev->abort) return;
     const unsigned long long P = g.P;
-    const unsigned long long qbase = qmod(dev->q_front, P);
+    const unsigned long long qbase = qmod(g.dev->q_front, P);
     const uint32_t C = g.C;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long i0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; !abort && i0 < n;
+    for (unsigned long long i0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i0 < n;
          i0 += stride * PP) {
         uint32_t r[PP], u[PP], v[PP];
 #pragma unroll
@@ -531,7 +469,63 @@ __global__ void __launch_bounds__(256) k_scatter_insert(GraphView g, const uint3
             }
         }
     }
-    if (last_cta(dev) && threadIdx.x == 0) close_insert(dev, n, abort, counts);
+}
+
+__global__ void __launch_bounds__(256) k_finalize_insert(GraphView g, unsigned long long n,
+                                                         unsigned long long *counts) {
+    Dev *dev = g.dev;
+    const uint32_t nt = dev->n_touched;
+    const bool abort = dev->abort != 0;
+    const unsigned long long P = g.P;
+    const unsigned long long qbase = qmod(dev->q_front, P);
+    const uint32_t C = g.C;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+        const uint32_t u = g.t_vid[t];
+        const uint32_t cnt = g.vcnt[vslot(g.vmask, u)];
+        if (!abort) {
+            const uint4 a = g.t_a[t];
+            const uint32_t deg = a.x, off = a.z, need = a.w;
+            const uint32_t nb = divc(g.cmul, deg + C - 1);
+            uint4 s = g.sent[u];
+            s.x = deg + cnt;
+            s.y = nb + need;
+            if (need) {
+                if (nb == 0) s.z = g.queue[ring(qbase, off, P)];
+                s.w = g.queue[ring(qbase, off + need - 1, P)];
+            }
+            g.sent[u] = s;
+        }
+        g.vcnt[vslot(g.vmask, u)] = 0;
+    }
+    if (last_cta(dev) && threadIdx.x == 0) {
+        unsigned long long rej = dev->call_b;
+        unsigned long long ins = n - rej;
+        if (abort) {
+            ins = 0;
+            rej = 0;
+        } else {
+            dev->q_front += dev->alloc_total;
+            dev->num_edges += ins;
+            dev->tot_ins += ins;
+            dev->tot_rej += rej;
+        }
+        if (counts) {
+            counts[0] = ins;
+            counts[1] = rej;
+        }
+        dev->alloc_total = 0;
+        dev->call_a = dev->call_b = dev->call_c = 0;
+        dev->n_touched = 0;
+        dev->n_items = 0;
+        dev->n_mitems = 0;
+        dev->n_tiny = 0;
+        dev->n_tiny_hi = 0;
+        dev->arena_used = 0;
+        dev->harena_used = 0;
+        dev->free_total = 0;
+        dev->abort = 0;
+        dev->done_ctas = 0;
+    }
 }
 
 // ------------------------------------------------------ membership pipeline
@@ -1789,17 +1783,17 @@ cudaError_t launch_insert_tail(const GraphView &g, const uint32_t *src, const ui
     }
     const unsigned long long max_pops = n / g.C + (tcap < n ? tcap : n) + 1;  // new blocks: <= n/C + sources
     {
-        // links of the new blocks, then the touched sources' sentinels (at
-        // most min(tcap, n) <= max_pops of them: the same grid covers both)
         PhaseScope ps(lc, PH_INS_LINK);
         k_link_insert<<<grid_for(max_pops, 256, cap), 256, 0, lc.stream>>>(g);
     }
     {
-        // the scatter's last CTA also closes the call (counters)
         PhaseScope ps(lc, PH_INS_SCATTER);
-        const int gs = grid_for(n, 256 * PP, cap);
-        if (g.wdata) k_scatter_insert<true><<<gs, 256, 0, lc.stream>>>(g, src, dst, wts, n, counts);
-        else k_scatter_insert<false><<<gs, 256, 0, lc.stream>>>(g, src, dst, wts, n, counts);
+        if (g.wdata) k_scatter_insert<true><<<grid_for(n, 256 * PP, cap), 256, 0, lc.stream>>>(g, src, dst, wts, n);
+        else k_scatter_insert<false><<<grid_for(n, 256 * PP, cap), 256, 0, lc.stream>>>(g, src, dst, wts, n);
+    }
+    {
+        PhaseScope ps(lc, PH_INS_FINALIZE);
+        k_finalize_insert<<<gt, 256, 0, lc.stream>>>(g, n, counts);
     }
     return cudaGetLastError();
 }
