@@ -802,6 +802,36 @@ def run_rows(args):
         row("a6", f"delete batch of {B}", B, "edges", ms_d,
             8 * B + 4 * int(deg1.astype(np.int64)[srcs].sum()) + 32 * srcs.size + 4 * newb)
 
+    # small batches replayed from CUDA graphs: the same insert and delete
+    # calls captured once (scratch sized before the capture), so the launch
+    # sequence runs without host launch gaps
+    g.reserve(max(BATCH, BASE_EDGES))
+    for B in (1_000, 10_000):
+        s, d = t(us[:B]), t(ud[:B])
+        srcs = np.unique(us[:B])
+        ci = torch.zeros(2, dtype=torch.int64, device="cuda")
+        cd = torch.zeros(2, dtype=torch.int64, device="cuda")
+        g.insert_edges(s, d, ci)
+        g.delete_edges(s, d, cd)
+        torch.cuda.synchronize()
+        exp_i, exp_d = tuple(ci.tolist()), tuple(cd.tolist())
+        gi, gdl = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gi, capture_error_mode="relaxed"):
+            g.insert_edges(s, d, ci)
+        with torch.cuda.graph(gdl, capture_error_mode="relaxed"):
+            g.delete_edges(s, d, cd)
+        ci.zero_()
+        cd.zero_()
+        ms_i = timed(gi.replay, post=gdl.replay)
+        ms_d = timed(gdl.replay, pre=gi.replay)
+        torch.cuda.synchronize()
+        assert tuple(ci.tolist()) == exp_i and tuple(cd.tolist()) == exp_d and g.sync() == 0
+        row("a2-a4 graph", f"insert batch of {B}, replayed from a CUDA graph", B, "edges", ms_i,
+            12 * B + 32 * srcs.size)
+        row("a6 graph", f"delete batch of {B}, replayed from a CUDA graph", B, "edges", ms_d,
+            8 * B + 4 * int(deg0[srcs].sum() + B) + 32 * srcs.size)
+        del gi, gdl
+
     # a7: 1M queries (half present) on the base graph
     d_qs, d_qd = t(qs), t(qd)
     out = torch.zeros(qs.size, dtype=torch.uint8, device="cuda")
