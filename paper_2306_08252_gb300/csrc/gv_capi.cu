@@ -775,9 +775,14 @@ gv_status insert_impl(gv_graph *g, const uint32_t *src, const uint32_t *dst, uin
             if (counts) GV_CK(cudaMemsetAsync(dcounts, 0, 16, s));
         } else {
             int set = -1;
-            GV_TRY(stage_batch(g, gv::MODE_INSERT, src, dst, wts, n, s, true, &dsrc, &ddst, &dwts, &set));
-            GV_CK(gv::launch_insert_tail(view(g), (const uint32_t *)dsrc, (const uint32_t *)ddst, n, g->tcap,
-                                         (unsigned long long *)dcounts, lcfg(g, s), (const uint32_t *)dwts));
+            const bool small = n <= gv::small_insert_max();
+            GV_TRY(stage_batch(g, gv::MODE_INSERT, src, dst, wts, n, s, !small, &dsrc, &ddst, &dwts, &set));
+            if (small)
+                GV_CK(gv::launch_insert_small(view(g), (const uint32_t *)dsrc, (const uint32_t *)ddst,
+                                              (const uint32_t *)dwts, n, (unsigned long long *)dcounts, lcfg(g, s)));
+            else
+                GV_CK(gv::launch_insert_tail(view(g), (const uint32_t *)dsrc, (const uint32_t *)ddst, n, g->tcap,
+                                             (unsigned long long *)dcounts, lcfg(g, s), (const uint32_t *)dwts));
             GV_TRY(release_set(g, set, s));
         }
     }
@@ -1762,7 +1767,7 @@ static const char *kPhaseNames[gv::PH_COUNT] = {
     "delete.mark",    "delete.mark_tiny", "delete.vscan",  "delete.move",      "delete.finalize",
     "query.count",    "query.touched",  "query.plan",      "query.arena",      "query.scatter",
     "query.mark",     "query.mark_tiny", "query.out",      "query.finalize",
-    "vertex_delete",  "neighbors",      "other",          "analytics"};
+    "vertex_delete",  "neighbors",      "other",          "analytics",      "insert.small"};
 
 uint32_t gv_profile_num_phases(void) { return gv::PH_COUNT; }
 

@@ -528,6 +528,198 @@ __global__ void __launch_bounds__(256) k_finalize_insert(GraphView g, unsigned l
     }
 }
 
+// ------------------------------------------- small insert batches, one CTA
+
+// An insert of at most SMALL_INS pairs in one kernel of one CTA: the chain
+// of five dependent kernels of the general path (count, plan, link,
+// scatter, finalize) is what a small batch waits for, not its work.  The
+// same steps, separated by barriers instead of launches: pairs grouped by
+// source in a shared hash table (a returning shared atomic gives each pair
+// its rank), block demand per source and one block scan for the queue
+// offsets (Figure 3), the pool check before any write (an exhausted queue
+// makes the call a no-op), then the new blocks linked at heap indices
+// nblocks + 1 .. (Figure 4's bit-string rule) and the pairs written at slot
+// deg + rank, and last the sentinels and the call's counters.
+constexpr uint32_t SMALL_INS = 2048;
+constexpr uint32_t SMALL_HS = 2 * SMALL_INS;  // hash slots (a power of two)
+constexpr uint32_t SMALL_THREADS = 1024;
+constexpr size_t SMALL_SMEM = SMALL_HS * 3 * 4 + SMALL_INS * (4 + 16 + 4 + 4 + 4 + 4 + 4);
+
+template <bool WEIGHTED>
+__global__ void __launch_bounds__(SMALL_THREADS, 1) k_insert_small(GraphView g, const uint32_t *__restrict__ src,
+                                                                  const uint32_t *__restrict__ dst,
+                                                                  const uint32_t *__restrict__ wts,
+                                                                  uint32_t n, unsigned long long *counts) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    uint32_t *hk = sm;                                    // [SMALL_HS] source id per slot
+    uint32_t *hc = hk + SMALL_HS;                         // [SMALL_HS] pairs per slot
+    uint32_t *ht = hc + SMALL_HS;                         // [SMALL_HS] touched index per slot
+    uint4 *ta = reinterpret_cast<uint4 *>(ht + SMALL_HS); // [SMALL_INS] sentinel before the call
+    uint32_t *tu = reinterpret_cast<uint32_t *>(ta + SMALL_INS);  // [SMALL_INS] source id
+    uint32_t *tslot = tu + SMALL_INS;                     // [SMALL_INS] hash slot
+    uint32_t *tneed = tslot + SMALL_INS;                  // [SMALL_INS] new blocks
+    uint32_t *toff = tneed + SMALL_INS;                   // [SMALL_INS] queue offset of the new blocks
+    uint32_t *pslot = toff + SMALL_INS;                   // [SMALL_INS] hash slot per pair (NIL: rejected)
+    uint32_t *prank = pslot + SMALL_INS;                  // [SMALL_INS] rank per pair
+    __shared__ uint32_t s_nt, s_rej, s_abort;
+    __shared__ unsigned long long s_qbase;
+    Dev *dev = g.dev;
+    const uint32_t tid = threadIdx.x, C = g.C;
+    const unsigned long long P = g.P;
+    for (uint32_t h = tid; h < SMALL_HS; h += SMALL_THREADS) {
+        hk[h] = EMPTY_KEY;
+        hc[h] = 0;
+    }
+    if (tid == 0) {
+        s_nt = 0;
+        s_rej = 0;
+    }
+    __syncthreads();
+    // 1. group by source
+    uint32_t rej = 0;
+    for (uint32_t i = tid; i < n; i += SMALL_THREADS) {
+        const uint32_t u = src[i], v = dst[i];
+        const bool ok = u < g.nv && v < g.nv && (g.all_alive || (g.alive[u] && g.alive[v]));
+        if (!ok) {
+            ++rej;
+            pslot[i] = NIL;
+            continue;
+        }
+        uint32_t h = hidx(u, SMALL_HS);
+        // at most n <= SMALL_HS / 2 keys: a free or equal slot exists
+        for (uint32_t step = 0; step < SMALL_HS; ++step) {
+            const uint32_t old = atomicCAS(&hk[h], EMPTY_KEY, u);
+            if (old == EMPTY_KEY) {
+                const uint32_t t = atomicAdd(&s_nt, 1u);
+                ht[h] = t;
+                tu[t] = u;
+                tslot[t] = h;
+                break;
+            }
+            if (old == u) break;
+            h = (h + 1) & (SMALL_HS - 1);
+        }
+        pslot[i] = h;
+        prank[i] = atomicAdd(&hc[h], 1u);
+    }
+    if (rej) atomicAdd(&s_rej, rej);
+    __syncthreads();
+    const uint32_t nt = s_nt;
+    // 2. block demand and queue offsets (two touched sources per thread)
+    uint32_t need2[2] = {0, 0};
+    for (uint32_t k = 0; k < 2; ++k) {
+        const uint32_t t = 2 * tid + k;
+        if (t < nt) {
+            const uint4 st = g.sent[tu[t]];
+            ta[t] = st;
+            const uint32_t cnt = hc[tslot[t]];
+            const uint32_t space = st.y * C - st.x;
+            need2[k] = cnt > space ? divc(g.cmul, cnt - space + C - 1) : 0u;
+            tneed[t] = need2[k];
+        }
+    }
+    uint32_t total;
+    const uint32_t base = block_excl_scan(need2[0] + need2[1], &total);
+    if (2 * tid < nt) toff[2 * tid] = base;
+    if (2 * tid + 1 < nt) toff[2 * tid + 1] = base + need2[0];
+    // 3. pool check before any write
+    if (tid == 0) {
+        const unsigned long long qf = dev->q_front, qb = dev->q_back;
+        s_abort = total > qb - qf ? 1u : 0u;
+        s_qbase = qmod(qf, P);
+        if (s_abort) {
+            latch_status(dev, 2u /* GV_ERR_OUT_OF_MEMORY */);
+            if (counts) {
+                counts[0] = 0;
+                counts[1] = 0;
+            }
+        }
+    }
+    __syncthreads();
+    if (s_abort) return;
+    const unsigned long long qbase = s_qbase;
+    // 4. links of the new blocks, and the pairs' slots
+    for (uint32_t j = tid; j < total; j += SMALL_THREADS) {
+        // owner: the last touched source whose offset is <= j
+        uint32_t lo = 0, hi = nt;  // toff[lo] <= j < toff[hi] (toff[nt] = total)
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (toff[mid] <= j) lo = mid;
+            else hi = mid;
+        }
+        const uint32_t t = lo;
+        const uint4 st = ta[t];
+        const uint32_t nb = st.y, need = tneed[t], off = toff[t];
+        const uint32_t k = nb + 1 + (j - off);  // heap index of this block
+        const uint32_t nbn = nb + need;
+        const uint32_t id = g.queue[ring(qbase, j, P)];
+        if (id >= P) {
+            latch_status(dev, 5u /* GV_ERR_STATE */);
+            continue;
+        }
+        if (2ull * k > nbn) g.links[2ull * id] = NIL;
+        if (2ull * k + 1 > nbn) g.links[2ull * id + 1] = NIL;
+        if (k > 1) {
+            const uint32_t p = k >> 1;
+            const uint32_t pid =
+                p > nb ? g.queue[ring(qbase, off + (p - nb - 1), P)] : cbt_walk(g.links, P, st.z, p);
+            if (pid >= P) {
+                latch_status(dev, 5u /* GV_ERR_STATE */);
+                continue;
+            }
+            g.links[2ull * pid + (k & 1u)] = id;
+        }
+    }
+    for (uint32_t i = tid; i < n; i += SMALL_THREADS) {
+        const uint32_t h = pslot[i];
+        if (h == NIL) continue;
+        const uint32_t t = ht[h], r = prank[i];
+        const uint4 st = ta[t];
+        const uint32_t deg = st.x, nb = st.y;
+        const uint32_t space = nb * C - deg;
+        uint32_t blk, ln;
+        if (r < space) {
+            blk = st.w;
+            ln = deg - (nb - 1) * C + r;
+        } else {
+            const uint32_t q = r - space;
+            const uint32_t jb = divc(g.cmul, q);
+            ln = q - jb * C;
+            blk = g.queue[ring(qbase, toff[t] + jb, P)];
+        }
+        if (blk < P) {
+            const size_t slot = (size_t)blk * C + ln;
+            g.data[slot] = dst[i];
+            if (WEIGHTED) g.wdata[slot] = wts ? wts[i] : 0u;
+        } else {
+            latch_status(dev, 5u /* GV_ERR_STATE */);
+        }
+    }
+    // 5. sentinels and counters
+    for (uint32_t t = tid; t < nt; t += SMALL_THREADS) {
+        uint4 st = ta[t];
+        const uint32_t need = tneed[t], off = toff[t], nb = st.y;
+        st.x += hc[tslot[t]];
+        st.y = nb + need;
+        if (need) {
+            if (nb == 0) st.z = g.queue[ring(qbase, off, P)];
+            st.w = g.queue[ring(qbase, off + need - 1, P)];
+        }
+        g.sent[tu[t]] = st;
+    }
+    if (tid == 0) {
+        const unsigned long long r2 = s_rej, ins = n - r2;
+        dev->q_front += total;
+        dev->num_edges += ins;
+        dev->tot_ins += ins;
+        dev->tot_rej += r2;
+        if (counts) {
+            counts[0] = ins;
+            counts[1] = r2;
+        }
+    }
+}
+
 // ------------------------------------------------------ membership pipeline
 
 // Items over the blocks of one touched source: t_b[t] = {deg, nblocks, root,
@@ -1769,6 +1961,30 @@ cudaError_t launch_count_rejects(const GraphView &g, const uint32_t *src, const 
     k_count_rejects<<<grid_for(n, 256, lc.num_sms * GRID_MULT), 256, 0, lc.stream>>>(g, src, dst, n, rejected);
     return cudaGetLastError();
 }
+
+cudaError_t launch_insert_small(const GraphView &g, const uint32_t *src, const uint32_t *dst, const uint32_t *wts,
+                                unsigned long long n, unsigned long long *counts, const LaunchCfg &lc) {
+    if (n == 0 || n > SMALL_INS) return cudaErrorInvalidValue;
+    // the shared-memory opt-in is per function and device
+    static bool attr_set[64][2] = {};
+    int devc = 0;
+    if (cudaGetDevice(&devc) != cudaSuccess || devc < 0 || devc >= 64) return cudaErrorInvalidDevice;
+    const int w = g.wdata ? 1 : 0;
+    if (!attr_set[devc][w]) {
+        const cudaError_t e = w ? cudaFuncSetAttribute(k_insert_small<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)SMALL_SMEM)
+                                : cudaFuncSetAttribute(k_insert_small<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)SMALL_SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set[devc][w] = true;
+    }
+    PhaseScope ps(lc, PH_INS_SMALL);
+    if (w) k_insert_small<true><<<1, SMALL_THREADS, SMALL_SMEM, lc.stream>>>(g, src, dst, wts, (uint32_t)n, counts);
+    else k_insert_small<false><<<1, SMALL_THREADS, SMALL_SMEM, lc.stream>>>(g, src, dst, wts, (uint32_t)n, counts);
+    return cudaGetLastError();
+}
+
+uint32_t small_insert_max() { return SMALL_INS; }
 
 cudaError_t launch_insert_tail(const GraphView &g, const uint32_t *src, const uint32_t *dst,
                                unsigned long long n, unsigned long long tcap,

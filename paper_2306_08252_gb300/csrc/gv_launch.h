@@ -16,7 +16,7 @@ enum Phase : int {
     PH_DEL_VSCAN, PH_DEL_MOVE, PH_DEL_FINALIZE,
     PH_QRY_COUNT, PH_QRY_TOUCHED, PH_QRY_PLAN, PH_QRY_ARENA, PH_QRY_SCATTER, PH_QRY_MARK, PH_QRY_MARK_TINY,
     PH_QRY_OUT, PH_QRY_FINALIZE,
-    PH_VDEL, PH_NEIGHBORS, PH_OTHER, PH_ANALYTICS,
+    PH_VDEL, PH_NEIGHBORS, PH_OTHER, PH_ANALYTICS, PH_INS_SMALL,
     PH_COUNT
 };
 
@@ -93,6 +93,11 @@ cudaError_t launch_count(int mode, const GraphView &g, const uint32_t *src, cons
 cudaError_t launch_count_rejects(const GraphView &g, const uint32_t *src, const uint32_t *dst,
                                  unsigned long long n, unsigned long long *rejected,
                                  const LaunchCfg &lc);
+// Insert of at most small_insert_max() pairs in one kernel of one CTA
+// (grouping included: no counting pass before it).
+cudaError_t launch_insert_small(const GraphView &g, const uint32_t *src, const uint32_t *dst, const uint32_t *wts,
+                                unsigned long long n, unsigned long long *counts, const LaunchCfg &lc);
+uint32_t small_insert_max();
 // Insert: plan (block demand, pop offsets), link (CBT), scatter (slots), finalize.
 cudaError_t launch_insert_tail(const GraphView &g, const uint32_t *src, const uint32_t *dst,
                                unsigned long long n, unsigned long long tcap,

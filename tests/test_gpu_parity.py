@@ -168,7 +168,8 @@ def test_empty_degenerate_and_duplicates():
         p.close()
 
 
-def test_pool_exhaustion_is_a_noop():
+@pytest.mark.parametrize("big", [5000, 1500])  # the general path and the one-CTA small-batch path
+def test_pool_exhaustion_is_a_noop(big):
     import paper_2306_08252_gb300 as gv
     nv = 256
     # pool of ~200 blocks of C=4
@@ -178,7 +179,7 @@ def test_pool_exhaustion_is_a_noop():
         p.insert(s, d)
         p.check()
         before = p.g.export_csr()
-        s2, d2 = W.uniform_pairs(4, 1, 5000, nv)
+        s2, d2 = W.uniform_pairs(4, 1, big, nv)
         p.g.insert_edges(dev_u32(s2), dev_u32(d2), p.counts)
         assert p.g.__class__  # call returns; error is latched on the device
         code = gv.gv_sync(p.g.handle)
@@ -471,3 +472,45 @@ def test_host_batches_in_flight_stream_order(weighted):
             np.testing.assert_array_equal(wt[order], owt)
     finally:
         p.close()
+
+
+
+@pytest.mark.parametrize("C", [4, 12, 64])
+def test_small_insert_path_matches_general_path(C):
+    # batches of at most 2,048 pairs take the one-CTA insert; sizes around
+    # that bound, skewed sources (one source with more pairs than a block
+    # and a new tree), invalid and dead ids, weighted and plain
+    import paper_2306_08252_gb300 as gv
+    rng = np.random.default_rng(40 + C)
+    nv = 3000
+    for flags in (0, gv.GV_WEIGHTED):
+        p = Pair(nv, C=C, pool_bytes=64 << 20, flags=flags)
+        try:
+            bs, bd = W.rmat_pairs(40 + C, 0, 20000, 11)
+            p.bulk(bs, bd)
+            p.vdel(np.array([3, 7, 2999], dtype=np.uint32))
+            for n in (1, 2, 31, 700, 2047, 2048, 2049, 4000):
+                s = rng.integers(0, nv + 3, n).astype(np.uint32)
+                d = rng.integers(0, nv + 3, n).astype(np.uint32)
+                s[: n // 3] = 1                      # a hub of this batch
+                s[n // 3: n // 3 + n // 10] = 2500  # a source with few or no blocks yet
+                if flags:
+                    import torch
+                    w = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
+                    cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+                    p.g.insert_edges_weighted(dev_u32(s), dev_u32(d), dev_u32(w), cnt)
+                    assert tuple(int(x) for x in cnt.cpu().tolist()) == p.o.insert_edges_weighted(s, d, w)
+                else:
+                    p.insert(s, d)
+                p.check()
+            if flags:
+                vids = np.arange(nv, dtype=np.uint32)
+                off, nb, wt = p.g.neighbors_weighted(vids)
+                ooff, onb, owt = p.o.neighbors_weighted(vids)
+                np.testing.assert_array_equal(off, ooff)
+                seg = np.repeat(np.arange(nv), np.diff(off.astype(np.int64)))
+                order = np.lexsort((wt, nb, seg))
+                np.testing.assert_array_equal(nb[order], onb)
+                np.testing.assert_array_equal(wt[order], owt)
+        finally:
+            p.close()
