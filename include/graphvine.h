@@ -178,7 +178,9 @@ gv_status gv_bulk_build(gv_graph *g, const uint32_t *src, const uint32_t *dst, u
  * new edges fill the free slots of its last block, then blocks popped from
  * the edge queue at offsets given by a prefix sum of per-source block demand
  * (Figure 3); each new block hangs in the source's CBT at the place the bit
- * string of its 1-based index names (Figure 4).
+ * string of its 1-based index names (Figure 4).  A batch of at most 2,048
+ * pairs (without GV_DEDUP) runs all of it in one kernel of one thread block
+ * (grouping in shared memory); larger ones in a chain of grid-wide kernels.
  *   src, dst  n uint32 endpoints each (device or host), any order, any
  *             duplicates.
  *   d_counts  optional, 2 uint64 (device or host): {inserted, rejected}.
