@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--queries", type=int, default=QUERIES)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay of the step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=10_000)
     ap.add_argument("--serve-scale", type=int, default=24)
@@ -387,6 +388,31 @@ def run_ours(args, rank, world, local_rank):
     assert g.sync() == 0
     gpu_launches = int(sum(c for _, c in phases.values()))
 
+    # ---------------- the same step replayed from a CUDA graph (captured once):
+    # same calls, same work; the library's launch sequence without host
+    # launch latency between kernels
+    graph = None
+    if not args.no_graph:
+        ref_counts = counts.clone()
+        cg = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(cg, capture_error_mode="relaxed"):
+            step()
+        cg.replay()
+        torch.cuda.synchronize()
+        gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            gev[i][0].record(stream)
+            cg.replay()
+            gev[i][1].record(stream)
+        torch.cuda.synchronize()
+        assert torch.equal(counts, ref_counts) and g.sync() == 0
+        g_ms = float(sum(a.elapsed_time(b) for a, b in gev))
+        g_ms = max_over_ranks([g_ms], world, dev)[0]
+        graph = {"value": whole_job_rate(upd_done, world, g_ms), "unit": UNIT, "ms_per_step": g_ms / args.steps,
+                 "timer": "CUDA events around each replay of the captured step"}
+        del cg
+
     # ---------------- end to end: host (pinned) inputs and outputs, through the C ABI
     e2e = None
     if not args.no_e2e:
@@ -463,6 +489,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": gpu_launches,
         "clocks": clocks,
         "e2e": e2e,
+        "graph_replay": graph,
         "counts_per_step": {"inserted": inserted, "deleted": deleted},
     }
     g.close()
