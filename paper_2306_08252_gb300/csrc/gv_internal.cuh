@@ -212,6 +212,12 @@ static_assert(VSCRAMBLE * VSCRAMBLE_INV == 1u, "scramble inverse");
 __device__ __forceinline__ uint32_t vslot(uint32_t vmask, uint32_t u) { return (u * VSCRAMBLE) & vmask; }
 __device__ __forceinline__ uint32_t vslot_inv(uint32_t vmask, uint32_t i) { return (i * VSCRAMBLE_INV) & vmask; }
 
+// Programmatic dependent launch: a kernel launched with the attribute may be
+// scheduled while its predecessor on the stream drains; it waits here,
+// before touching anything the predecessor wrote, until that grid has
+// completed and its memory is visible.  A no-op for an ordinary launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ void latch_status(Dev *dev, unsigned int code) {
     atomicCAS(&dev->status, 0u, code);
 }

@@ -167,6 +167,7 @@ template <int MODE>
 __global__ void __launch_bounds__(AGG_THREADS) k_count(GraphView g, const uint32_t *__restrict__ src,
                                                        const uint32_t *__restrict__ dst,
                                                        unsigned long long n) {
+    pdl_wait();
     __shared__ uint32_t keys[AGG_H];
     __shared__ uint32_t cnt[AGG_H];
     __shared__ uint32_t s_tbase;
@@ -245,6 +246,7 @@ template <int MODE>
 __global__ void __launch_bounds__(256) k_count_direct(GraphView g, const uint32_t *__restrict__ src,
                                                       const uint32_t *__restrict__ dst,
                                                       unsigned long long n) {
+    pdl_wait();
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     unsigned long long rej = 0;
     for (unsigned long long i0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i0 < n;
@@ -290,6 +292,7 @@ __global__ void __launch_bounds__(256) k_count_direct(GraphView g, const uint32_
 // Touched list after a direct count: every vertex with a non-zero count
 // (vertex order within each chunk; one atomic per CTA chunk).
 __global__ void __launch_bounds__(256) k_touched_scan(GraphView g) {
+    pdl_wait();
     const uint32_t ncap = g.vmask + 1;
     __shared__ uint32_t s_base;
     for (uint32_t base = blockIdx.x * blockDim.x * 4; base < ncap; base += gridDim.x * blockDim.x * 4) {
@@ -322,6 +325,7 @@ __global__ void __launch_bounds__(256) k_touched_scan(GraphView g) {
 __global__ void __launch_bounds__(256) k_count_rejects(GraphView g, const uint32_t *__restrict__ src,
                                                        const uint32_t *__restrict__ dst,
                                                        unsigned long long n, unsigned long long *rejected) {
+    pdl_wait();
     unsigned long long rej = 0;
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x)
@@ -333,6 +337,7 @@ __global__ void __launch_bounds__(256) k_count_rejects(GraphView g, const uint32
 // ------------------------------------------------------------------ insert
 
 __global__ void __launch_bounds__(256) k_plan_insert(GraphView g) {
+    pdl_wait();
     const uint32_t nt = g.dev->n_touched;
     const uint32_t C = g.C;
     __shared__ unsigned long long s_base;
@@ -363,6 +368,7 @@ __global__ void __launch_bounds__(256) k_plan_insert(GraphView g) {
 }
 
 __global__ void __launch_bounds__(256) k_link_insert(GraphView g) {
+    pdl_wait();
     Dev *dev = g.dev;
     const unsigned long long total = dev->alloc_total;
     const unsigned long long qf = dev->q_front, qb = dev->q_back;
@@ -417,6 +423,7 @@ __global__ void __launch_bounds__(256) k_scatter_insert(GraphView g, const uint3
                                                         const uint32_t *__restrict__ dst,
                                                         const uint32_t *__restrict__ wts,
                                                         unsigned long long n) {
+    pdl_wait();
     if (g.dev->abort) return;
     const unsigned long long P = g.P;
     const unsigned long long qbase = qmod(g.dev->q_front, P);
@@ -473,6 +480,7 @@ __global__ void __launch_bounds__(256) k_scatter_insert(GraphView g, const uint3
 
 __global__ void __launch_bounds__(256) k_finalize_insert(GraphView g, unsigned long long n,
                                                          unsigned long long *counts) {
+    pdl_wait();
     Dev *dev = g.dev;
     const uint32_t nt = dev->n_touched;
     const bool abort = dev->abort != 0;
@@ -550,6 +558,7 @@ __global__ void __launch_bounds__(SMALL_THREADS, 1) k_insert_small(GraphView g, 
                                                                   const uint32_t *__restrict__ dst,
                                                                   const uint32_t *__restrict__ wts,
                                                                   uint32_t n, unsigned long long *counts) {
+    pdl_wait();
     extern __shared__ __align__(16) uint32_t sm[];
     uint32_t *hk = sm;                                    // [SMALL_HS] source id per slot
     uint32_t *hc = hk + SMALL_HS;                         // [SMALL_HS] pairs per slot
@@ -758,6 +767,7 @@ __device__ __forceinline__ uint32_t item_at(const GraphView &g, uint32_t vi, uin
 // tiny adjacency and few batch entries) or work items of IB blocks.
 template <int MODE>
 __global__ void __launch_bounds__(256) k_plan_member(GraphView g) {
+    pdl_wait();
     const uint32_t nt = g.dev->n_touched;
     const uint32_t IB = g.IB;
     const uint32_t tiny_deg = min(TINY_DEG, TINY_NB * g.C);
@@ -819,6 +829,7 @@ __device__ __forceinline__ void seg_count(uint32_t *hist, uint32_t own, uint32_t
 
 template <int MODE>
 __global__ void __launch_bounds__(256) k_arena_init(GraphView g) {
+    pdl_wait();
     // hash region -> EMPTY; query hit flags of both regions -> 0 (list
     // entries are all overwritten by the scatter)
     const unsigned long long lused = g.dev->arena_used, hused = g.dev->harena_used;
@@ -844,6 +855,7 @@ template <int MODE>
 __global__ void __launch_bounds__(256) k_scatter_member(GraphView g, const uint32_t *__restrict__ src,
                                                         const uint32_t *__restrict__ dst,
                                                         unsigned long long n) {
+    pdl_wait();
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long i0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i0 < n;
          i0 += stride * PP) {
@@ -1022,6 +1034,7 @@ __device__ __forceinline__ void vscan_source(const GraphView &g, uint32_t t, uin
 
 template <int MODE, bool WEIGHTED = false>
 __global__ void __launch_bounds__(256, 4) k_mark(GraphView g) {
+    pdl_wait();
     Dev *dev = g.dev;
     const uint32_t nlo = dev->n_items, nhi = dev->n_mitems;
     const uint32_t nitems = nlo + nhi;
@@ -1283,6 +1296,7 @@ struct Blocks8 {
 
 template <int MODE>
 __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
+    pdl_wait();
     // Vertex deletes visit every vertex id directly (no touched list: the
     // incoming-edge pass covers all live vertices); other modes visit the
     // planned tiny sources.
@@ -1453,6 +1467,7 @@ __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
 // One warp per multi-item source.
 template <int MODE>
 __global__ void __launch_bounds__(256) k_vscan(GraphView g) {
+    pdl_wait();
     Dev *dev = g.dev;
     const uint32_t lane = lane_id();
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1484,6 +1499,7 @@ __global__ void __launch_bounds__(256) k_vscan(GraphView g) {
 // One warp per item of a multi-item source.
 template <int MODE>
 __global__ void __launch_bounds__(256) k_move(GraphView g) {
+    pdl_wait();
     Dev *dev = g.dev;
     const uint32_t nhi = dev->n_mitems;  // items of multi-item sources (top region)
     const uint32_t lane = lane_id();
@@ -1580,6 +1596,7 @@ __global__ void __launch_bounds__(256) k_move(GraphView g) {
 }
 
 __global__ void __launch_bounds__(256) k_query_out(GraphView g, unsigned long long n, uint8_t *out) {
+    pdl_wait();
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         const uint32_t p = g.qpos[i];
@@ -1589,6 +1606,7 @@ __global__ void __launch_bounds__(256) k_query_out(GraphView g, unsigned long lo
 
 template <int MODE>
 __global__ void __launch_bounds__(256) k_finalize_member(GraphView g, unsigned long long *counts) {
+    pdl_wait();
     Dev *dev = g.dev;
     const uint32_t nt = dev->n_touched;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
@@ -1626,6 +1644,7 @@ __global__ void __launch_bounds__(256) k_finalize_member(GraphView g, unsigned l
 
 __global__ void __launch_bounds__(256) k_vdel_mark(GraphView g, const uint32_t *__restrict__ ids,
                                                    uint32_t k) {
+    pdl_wait();
     for (uint32_t base = blockIdx.x * blockDim.x; base < k; base += gridDim.x * blockDim.x) {
         const uint32_t i = base + threadIdx.x;
         bool own = false;
@@ -1648,6 +1667,7 @@ __global__ void __launch_bounds__(256) k_vdel_mark(GraphView g, const uint32_t *
 
 // Deleted vertices: their blocks become items to free; sentinels cleared.
 __global__ void __launch_bounds__(256) k_plan_vfree(GraphView g) {
+    pdl_wait();
     const uint32_t nt = g.dev->n_touched;
     const uint32_t IB = g.IB;
     __shared__ uint32_t s_ai;
@@ -1679,6 +1699,7 @@ __global__ void __launch_bounds__(256) k_plan_vfree(GraphView g) {
 }
 
 __global__ void __launch_bounds__(256) k_free_items(GraphView g) {
+    pdl_wait();
     Dev *dev = g.dev;
     const uint32_t nitems = dev->n_items;
     const uint32_t lane = lane_id();
@@ -1706,6 +1727,7 @@ __global__ void __launch_bounds__(256) k_free_items(GraphView g) {
 // Between the two phases of a vertex delete: the touched list and the item
 // list are rebuilt for the incoming-edge pass.
 __global__ void k_reset_lists(GraphView g) {
+    pdl_wait();
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         g.dev->n_touched = 0;
         g.dev->n_items = 0;
@@ -1718,6 +1740,7 @@ __global__ void k_reset_lists(GraphView g) {
 // Every live vertex with edges becomes a touched source of the incoming-edge
 // pass (its entries are tested against the deleted-id bitmap).
 __global__ void __launch_bounds__(256) k_plan_vdel_in(GraphView g) {
+    pdl_wait();
     const uint32_t nv = g.nv;
     const uint32_t IB = g.IB;
     const uint32_t tiny_deg = min(TINY_DEG, TINY_NB * g.C);
@@ -1752,6 +1775,7 @@ __global__ void __launch_bounds__(256) k_plan_vdel_in(GraphView g) {
 
 __global__ void __launch_bounds__(256) k_finalize_vdel(GraphView g, const uint32_t *__restrict__ ids,
                                                        uint32_t k) {
+    pdl_wait();
     Dev *dev = g.dev;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
         const uint32_t id = ids[i];
@@ -1786,6 +1810,7 @@ __global__ void __launch_bounds__(256) k_finalize_vdel(GraphView g, const uint32
 __global__ void __launch_bounds__(256) k_dedup_select(GraphView g, const uint32_t *__restrict__ src,
                                                       unsigned long long n, uint32_t *src2,
                                                       unsigned long long *cnt) {
+    pdl_wait();
     unsigned long long k = 0;
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
@@ -1799,6 +1824,7 @@ __global__ void __launch_bounds__(256) k_dedup_select(GraphView g, const uint32_
 }
 
 __global__ void k_copy_rejects(Dev *dev, unsigned long long *tmp) {
+    pdl_wait();
     if (threadIdx.x == 0 && blockIdx.x == 0) tmp[0] = dev->call_b;
 }
 
@@ -1807,6 +1833,7 @@ __global__ void k_copy_rejects(Dev *dev, unsigned long long *tmp) {
 // repeats) is taken back out of the running total.
 __global__ void k_dedup_counts(Dev *dev, const unsigned long long *tmp, unsigned long long n,
                                unsigned long long *counts) {
+    pdl_wait();
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         // tmp[0] = rejected by the grouping pass, tmp[2..3] = {inserted, rejected} of the insert
         const unsigned long long ins = tmp[2], rej2 = tmp[3], rej = tmp[0];
@@ -1828,6 +1855,7 @@ __global__ void k_dedup_counts(Dev *dev, const unsigned long long *tmp, unsigned
 __global__ void __launch_bounds__(256) k_set_remap(GraphView g, const uint32_t *__restrict__ src,
                                                    const uint32_t *__restrict__ dst, unsigned long long n,
                                                    uint32_t *gsrc, uint32_t *gdst) {
+    pdl_wait();
     __shared__ unsigned long long s_off[SET_MAX_G + 1];
     __shared__ uint32_t s_base[SET_MAX_G + 1];
     __shared__ uint32_t s_rej[SET_MAX_G];
@@ -1863,6 +1891,7 @@ __global__ void __launch_bounds__(256) k_set_remap(GraphView g, const uint32_t *
 // ranges, offsets in set_off; multiset inserts insert every valid pair).
 __global__ void __launch_bounds__(256) k_segment_counts(GraphView g, const uint32_t *__restrict__ src,
                                                         const uint32_t *__restrict__ dst, unsigned long long n) {
+    pdl_wait();
     __shared__ unsigned long long s_off[SET_MAX_G + 1];
     __shared__ uint32_t s_rej[SET_MAX_G];
     const uint32_t G = g.set_G;
@@ -1892,6 +1921,7 @@ __global__ void __launch_bounds__(256) k_segment_counts(GraphView g, const uint3
 
 // Inserted pairs per member (multiset): its batch size minus its rejects.
 __global__ void k_set_insert_counts(GraphView g) {
+    pdl_wait();
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < g.set_G; i += gridDim.x * blockDim.x)
         g.set_counts[2 * i] = (g.set_off[i + 1] - g.set_off[i]) - g.set_counts[2 * i + 1];
 }
@@ -1921,17 +1951,17 @@ cudaError_t launch_count_range(int mode, const GraphView &g0, const uint32_t *sr
         // large batch: per-pair atomics (the touched list follows the pass)
         const int grid = grid_for(n, 256 * 8, lc.num_sms * GRID_MULT);
         switch (mode) {
-        case MODE_INSERT: k_count_direct<MODE_INSERT><<<grid, 256, 0, lc.stream>>>(g, src, dst, n); break;
-        case MODE_DELETE: k_count_direct<MODE_DELETE><<<grid, 256, 0, lc.stream>>>(g, src, dst, n); break;
-        default: k_count_direct<MODE_QUERY><<<grid, 256, 0, lc.stream>>>(g, src, dst, n); break;
+        case MODE_INSERT: launch_pdl(k_count_direct<MODE_INSERT>, grid, 256, 0, lc.stream, g, src, dst, n); break;
+        case MODE_DELETE: launch_pdl(k_count_direct<MODE_DELETE>, grid, 256, 0, lc.stream, g, src, dst, n); break;
+        default: launch_pdl(k_count_direct<MODE_QUERY>, grid, 256, 0, lc.stream, g, src, dst, n); break;
         }
     } else {
         // small batch: per-tile aggregation, touched list appended on the fly
         const int grid = grid_for(n, AGG_TILE, lc.num_sms * GRID_MULT);
         switch (mode) {
-        case MODE_INSERT: k_count<MODE_INSERT><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
-        case MODE_DELETE: k_count<MODE_DELETE><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
-        default: k_count<MODE_QUERY><<<grid, AGG_THREADS, 0, lc.stream>>>(g, src, dst, n); break;
+        case MODE_INSERT: launch_pdl(k_count<MODE_INSERT>, grid, AGG_THREADS, 0, lc.stream, g, src, dst, n); break;
+        case MODE_DELETE: launch_pdl(k_count<MODE_DELETE>, grid, AGG_THREADS, 0, lc.stream, g, src, dst, n); break;
+        default: launch_pdl(k_count<MODE_QUERY>, grid, AGG_THREADS, 0, lc.stream, g, src, dst, n); break;
         }
     }
     return cudaGetLastError();
@@ -1943,7 +1973,7 @@ cudaError_t launch_count_finish(int mode, const GraphView &g, unsigned long long
     const int ph = mode == MODE_INSERT ? PH_INS_COUNT : mode == MODE_DELETE ? PH_DEL_COUNT : PH_QRY_COUNT;
     if (n_total >= ((unsigned long long)g.nv >> g.dense_shift)) {
         PhaseScope ps(lc, ph + 1);  // the touched-list phase follows each count phase
-        k_touched_scan<<<grid_for(g.vmask + 1ull, 1024, lc.num_sms * GRID_MULT), 256, 0, lc.stream>>>(g);
+        launch_pdl(k_touched_scan, grid_for(g.vmask + 1ull, 1024, lc.num_sms * GRID_MULT), 256, 0, lc.stream, g);
     }
     return cudaGetLastError();
 }
@@ -1958,7 +1988,7 @@ cudaError_t launch_count(int mode, const GraphView &g, const uint32_t *src, cons
 cudaError_t launch_count_rejects(const GraphView &g, const uint32_t *src, const uint32_t *dst,
                                  unsigned long long n, unsigned long long *rejected,
                                  const LaunchCfg &lc) {
-    k_count_rejects<<<grid_for(n, 256, lc.num_sms * GRID_MULT), 256, 0, lc.stream>>>(g, src, dst, n, rejected);
+    launch_pdl(k_count_rejects, grid_for(n, 256, lc.num_sms * GRID_MULT), 256, 0, lc.stream, g, src, dst, n, rejected);
     return cudaGetLastError();
 }
 
@@ -1979,8 +2009,8 @@ cudaError_t launch_insert_small(const GraphView &g, const uint32_t *src, const u
         attr_set[devc][w] = true;
     }
     PhaseScope ps(lc, PH_INS_SMALL);
-    if (w) k_insert_small<true><<<1, SMALL_THREADS, SMALL_SMEM, lc.stream>>>(g, src, dst, wts, (uint32_t)n, counts);
-    else k_insert_small<false><<<1, SMALL_THREADS, SMALL_SMEM, lc.stream>>>(g, src, dst, wts, (uint32_t)n, counts);
+    if (w) launch_pdl(k_insert_small<true>, 1, SMALL_THREADS, SMALL_SMEM, lc.stream, g, src, dst, wts, (uint32_t)n, counts);
+    else launch_pdl(k_insert_small<false>, 1, SMALL_THREADS, SMALL_SMEM, lc.stream, g, src, dst, wts, (uint32_t)n, counts);
     return cudaGetLastError();
 }
 
@@ -1995,21 +2025,21 @@ cudaError_t launch_insert_tail(const GraphView &g, const uint32_t *src, const ui
     const int gt = grid_for(tcap < n ? tcap : n, 256, cap);
     {
         PhaseScope ps(lc, PH_INS_PLAN);
-        k_plan_insert<<<gt, 256, 0, lc.stream>>>(g);
+        launch_pdl(k_plan_insert, gt, 256, 0, lc.stream, g);
     }
     const unsigned long long max_pops = n / g.C + (tcap < n ? tcap : n) + 1;  // new blocks: <= n/C + sources
     {
         PhaseScope ps(lc, PH_INS_LINK);
-        k_link_insert<<<grid_for(max_pops, 256, cap), 256, 0, lc.stream>>>(g);
+        launch_pdl(k_link_insert, grid_for(max_pops, 256, cap), 256, 0, lc.stream, g);
     }
     {
         PhaseScope ps(lc, PH_INS_SCATTER);
-        if (g.wdata) k_scatter_insert<true><<<grid_for(n, 256 * PP, cap), 256, 0, lc.stream>>>(g, src, dst, wts, n);
-        else k_scatter_insert<false><<<grid_for(n, 256 * PP, cap), 256, 0, lc.stream>>>(g, src, dst, wts, n);
+        if (g.wdata) launch_pdl(k_scatter_insert<true>, grid_for(n, 256 * PP, cap), 256, 0, lc.stream, g, src, dst, wts, n);
+        else launch_pdl(k_scatter_insert<false>, grid_for(n, 256 * PP, cap), 256, 0, lc.stream, g, src, dst, wts, n);
     }
     {
         PhaseScope ps(lc, PH_INS_FINALIZE);
-        k_finalize_insert<<<gt, 256, 0, lc.stream>>>(g, n, counts);
+        launch_pdl(k_finalize_insert, gt, 256, 0, lc.stream, g, n, counts);
     }
     return cudaGetLastError();
 }
@@ -2030,15 +2060,15 @@ static void member_tail(const GraphView &g0, const uint32_t *src, const uint32_t
     const bool del = MODE == MODE_DELETE;
     {
         PhaseScope ps(lc, del ? PH_DEL_PLAN : PH_QRY_PLAN);
-        k_plan_member<MODE><<<gt, 256, 0, lc.stream>>>(g);
+        launch_pdl(k_plan_member<MODE>, gt, 256, 0, lc.stream, g);
     }
     {
         PhaseScope ps(lc, del ? PH_DEL_ARENA : PH_QRY_ARENA);
-        k_arena_init<MODE><<<grid_for(5 * n + 64, 256, cap), 256, 0, lc.stream>>>(g);
+        launch_pdl(k_arena_init<MODE>, grid_for(5 * n + 64, 256, cap), 256, 0, lc.stream, g);
     }
     {
         PhaseScope ps(lc, del ? PH_DEL_SCATTER : PH_QRY_SCATTER);
-        k_scatter_member<MODE><<<grid_for(n, 256 * PP, cap), 256, 0, lc.stream>>>(g, src, dst, n);
+        launch_pdl(k_scatter_member<MODE>, grid_for(n, 256 * PP, cap), 256, 0, lc.stream, g, src, dst, n);
     }
     // The two tiers touch disjoint sources (their blocks, sentinels and list
     // ranges) and share only atomically updated counters, so the thread-per-
@@ -2055,34 +2085,38 @@ static void member_tail(const GraphView &g0, const uint32_t *src, const uint32_t
     }
     {
         PhaseScope ps(lc, del ? PH_DEL_MARK : PH_QRY_MARK);
-        if (MODE != MODE_QUERY && g.wdata) k_mark<MODE, true><<<gi, 256, 0, lc.stream>>>(g);
-        else k_mark<MODE><<<gi, 256, 0, lc.stream>>>(g);
+        if (MODE != MODE_QUERY && g.wdata) launch_pdl(k_mark<MODE, true>, gi, 256, 0, lc.stream, g);
+        else launch_pdl(k_mark<MODE>, gi, 256, 0, lc.stream, g);
     }
     if (!fork) {
         PhaseScope ps(lc, del ? PH_DEL_MARK_TINY : PH_QRY_MARK_TINY);
-        k_mark_tiny<MODE><<<gt, 256, 0, lc.stream>>>(g);
+        launch_pdl(k_mark_tiny<MODE>, gt, 256, 0, lc.stream, g);
     }
     if (del) {
         // the hole filling of multi-item sources does not touch tiny sources
         // either: the side stream joins only before the finalize
         {
             PhaseScope ps(lc, PH_DEL_VSCAN);
-            k_vscan<MODE><<<grid_for(nt, 8, cap), 256, 0, lc.stream>>>(g);
+            launch_pdl(k_vscan<MODE>, grid_for(nt, 8, cap), 256, 0, lc.stream, g);
         }
         PhaseScope ps(lc, PH_DEL_MOVE);
-        k_move<MODE><<<gi, 256, 0, lc.stream>>>(g);
+        launch_pdl(k_move<MODE>, gi, 256, 0, lc.stream, g);
     }
     if (fork) {
         cudaEventRecord(lc.join, lc.side);
         cudaStreamWaitEvent(lc.stream, lc.join, 0);
     }
+    // the first kernel after the join is an ordinary launch: it waits for
+    // the side stream's work through the event, not for one predecessor grid
     if (!del) {
         PhaseScope ps(lc, PH_QRY_OUT);
-        k_query_out<<<grid_for(n, 256, cap), 256, 0, lc.stream>>>(g, n, qout);
+        if (fork) k_query_out<<<grid_for(n, 256, cap), 256, 0, lc.stream>>>(g, n, qout);
+        else launch_pdl(k_query_out, grid_for(n, 256, cap), 256, 0, lc.stream, g, n, qout);
     }
     {
         PhaseScope ps(lc, del ? PH_DEL_FINALIZE : PH_QRY_FINALIZE);
-        k_finalize_member<MODE><<<gt, 256, 0, lc.stream>>>(g, counts);
+        if (fork && del) k_finalize_member<MODE><<<gt, 256, 0, lc.stream>>>(g, counts);
+        else launch_pdl(k_finalize_member<MODE>, gt, 256, 0, lc.stream, g, counts);
     }
 }
 
@@ -2147,6 +2181,7 @@ cudaError_t launch_segment_counts(const GraphView &g, const uint32_t *src, const
 // After a segmented insert: its totals {inserted, rejected} are {0, 0} only
 // when the call was a no-op (pool exhausted); then every segment gets {0, 0}.
 __global__ void k_segment_noop_check(GraphView g, const unsigned long long *tot, unsigned long long n) {
+    pdl_wait();
     if (tot[0] != 0 || tot[1] != 0 || n == 0) return;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * g.set_G; i += gridDim.x * blockDim.x)
         g.set_counts[i] = 0;

@@ -74,6 +74,25 @@ struct PhaseScope {
 // Group-by-source counting pass over a pair batch (all modes).
 
 
+// Launch with programmatic stream serialization: the grid may be scheduled
+// while the previous kernel on the stream drains (every kernel of this
+// library starts with pdl_wait(), so none reads its predecessor's results
+// early).  Errors are left for cudaGetLastError, as with <<<>>>.
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args &&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    (void)cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 // Blocks for `work` units at `per_block` units per block, at least 1 and at
 // most `cap` (grid-stride kernels cover the rest).
 inline int grid_for(unsigned long long work, int per_block, int cap) {
