@@ -71,6 +71,7 @@ __device__ __forceinline__ bool for_item_entries(const GraphView &g, uint32_t u,
 __global__ void __launch_bounds__(256) k_an_items(GraphView g, const uint32_t *__restrict__ list,
                                                   const uint32_t *nlist, uint32_t aib, uint2 *items,
                                                   uint32_t *nitems) {
+    pdl_wait();
     const uint32_t n = list ? *nlist : g.nv;
     __shared__ uint32_t s_base;
     for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
@@ -93,6 +94,7 @@ __global__ void __launch_bounds__(256) k_an_items(GraphView g, const uint32_t *_
 
 // Source of the search: distance 0 and the first frontier, if alive.
 __global__ void k_bfs_seed(GraphView g, uint32_t source, uint32_t *dist, uint32_t *cur, uint32_t *ctr) {
+    pdl_wait();
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         const bool live = source < g.nv && g.alive[source];
         if (live) {
@@ -112,6 +114,7 @@ __global__ void k_bfs_seed(GraphView g, uint32_t source, uint32_t *dist, uint32_
 __global__ void __launch_bounds__(256) k_bfs_expand(GraphView g, const uint2 *__restrict__ items,
                                                     const uint32_t *nitems, uint32_t aib, uint32_t *dist,
                                                     uint32_t level, uint32_t *next, uint32_t *nnext) {
+    pdl_wait();
     __shared__ uint32_t s_bid[8][32];
     const uint32_t n = *nitems;
     const uint32_t lane = lane_id();
@@ -153,6 +156,7 @@ __global__ void __launch_bounds__(256) k_bfs_expand(GraphView g, const uint2 *__
 // levels}.  A level with an empty frontier changes nothing, so the host may
 // launch several levels between two reads of the frontier size.
 __global__ void k_bfs_advance(uint32_t *ctr, uint32_t level) {
+    pdl_wait();
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         if (ctr[2]) ctr[3] = level + 2;
         ctr[0] = ctr[2];
@@ -173,9 +177,9 @@ cudaError_t launch_bfs_level(const GraphView &g, uint32_t aib, const uint32_t *c
                              uint32_t *ctr, uint32_t *dist, uint32_t level, const LaunchCfg &lc) {
     PhaseScope ps(lc, PH_ANALYTICS);
     const int grid = lc.num_sms * GRID_MULT;
-    k_an_items<<<grid, 256, 0, lc.stream>>>(g, cur, ctr, aib, items, ctr + 1);
-    k_bfs_expand<<<grid, 256, 0, lc.stream>>>(g, items, ctr + 1, aib, dist, level, next, ctr + 2);
-    k_bfs_advance<<<1, 32, 0, lc.stream>>>(ctr, level);
+    launch_pdl(k_an_items, grid, 256, 0, lc.stream, g, cur, ctr, aib, items, ctr + 1);
+    launch_pdl(k_bfs_expand, grid, 256, 0, lc.stream, g, items, ctr + 1, aib, dist, level, next, ctr + 2);
+    launch_pdl(k_bfs_advance, 1, 32, 0, lc.stream, ctr, level);
     return cudaGetLastError();
 }
 
@@ -191,6 +195,7 @@ cudaError_t launch_bfs_level(const GraphView &g, uint32_t aib, const uint32_t *c
 // with non-negative lengths it is reached within nv rounds.
 
 __global__ void k_sssp_seed(GraphView g, uint32_t source, unsigned long long *dist, uint32_t *cur, uint32_t *ctr) {
+    pdl_wait();
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         const bool live = source < g.nv && g.alive[source];
         if (live) {
@@ -209,6 +214,7 @@ __global__ void __launch_bounds__(256) k_sssp_relax(GraphView g, const uint2 *__
                                                     const uint32_t *nitems, uint32_t aib, unsigned long long *dist,
                                                     uint32_t *stamp, uint32_t round, uint32_t *next,
                                                     uint32_t *nnext) {
+    pdl_wait();
     __shared__ uint32_t s_bid[8][32];
     const uint32_t n = *nitems;
     const uint32_t lane = lane_id();
@@ -272,12 +278,12 @@ cudaError_t launch_sssp_round(const GraphView &g, uint32_t aib, const uint32_t *
                               const LaunchCfg &lc) {
     PhaseScope ps(lc, PH_ANALYTICS);
     const int grid = lc.num_sms * GRID_MULT;
-    k_an_items<<<grid, 256, 0, lc.stream>>>(g, cur, ctr, aib, items, ctr + 1);
+    launch_pdl(k_an_items, grid, 256, 0, lc.stream, g, cur, ctr, aib, items, ctr + 1);
     if (g.wdata)
-        k_sssp_relax<true><<<grid, 256, 0, lc.stream>>>(g, items, ctr + 1, aib, dist, stamp, round, next, ctr + 2);
+        launch_pdl(k_sssp_relax<true>, grid, 256, 0, lc.stream, g, items, ctr + 1, aib, dist, stamp, round, next, ctr + 2);
     else
-        k_sssp_relax<false><<<grid, 256, 0, lc.stream>>>(g, items, ctr + 1, aib, dist, stamp, round, next, ctr + 2);
-    k_bfs_advance<<<1, 32, 0, lc.stream>>>(ctr, round);
+        launch_pdl(k_sssp_relax<false>, grid, 256, 0, lc.stream, g, items, ctr + 1, aib, dist, stamp, round, next, ctr + 2);
+    launch_pdl(k_bfs_advance, 1, 32, 0, lc.stream, ctr, round);
     return cudaGetLastError();
 }
 
@@ -285,6 +291,7 @@ cudaError_t launch_sssp_round(const GraphView &g, uint32_t aib, const uint32_t *
 
 // N = live vertices (64-bit counter, zeroed by the caller).
 __global__ void __launch_bounds__(256) k_pr_count(GraphView g, unsigned long long *N) {
+    pdl_wait();
     unsigned long long k = 0;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < g.nv; v += gridDim.x * blockDim.x) k += g.alive[v];
     k = block_sum_u64(k);
@@ -292,6 +299,7 @@ __global__ void __launch_bounds__(256) k_pr_count(GraphView g, unsigned long lon
 }
 
 __global__ void __launch_bounds__(256) k_pr_start(GraphView g, double *r, const unsigned long long *N) {
+    pdl_wait();
     const unsigned long long n = *N;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < g.nv; v += gridDim.x * blockDim.x)
         r[v] = (n && g.alive[v]) ? 1.0 / (double)n : 0.0;
@@ -301,6 +309,7 @@ __global__ void __launch_bounds__(256) k_pr_start(GraphView g, double *r, const 
 // the accumulator cleared, and the dangling mass summed into *dang.
 __global__ void __launch_bounds__(256) k_pr_contrib(GraphView g, const double *__restrict__ r, double *c,
                                                     double *acc, double *dang) {
+    pdl_wait();
     __shared__ double s_p[8];
     double dm = 0.0;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < g.nv; v += gridDim.x * blockDim.x) {
@@ -329,6 +338,7 @@ __global__ void __launch_bounds__(256) k_pr_contrib(GraphView g, const double *_
 // (u, v) placed in v's segment at an atomically claimed position.
 __global__ void __launch_bounds__(256) k_pr_indeg(GraphView g, const uint2 *__restrict__ items,
                                                   const uint32_t *nitems, uint32_t aib, uint32_t *indeg) {
+    pdl_wait();
     __shared__ uint32_t s_bid[8][32];
     const uint32_t n = *nitems;
     const uint32_t lane = lane_id();
@@ -357,6 +367,7 @@ constexpr uint32_t PR_CHUNK = 1024;  // entries per scan chunk (256 threads x 4)
 // Chunk sums of x[0..n).
 __global__ void __launch_bounds__(256) k_pr_chunk_sums(const uint32_t *__restrict__ x, uint32_t n,
                                                        unsigned long long *part) {
+    pdl_wait();
     const uint32_t base = blockIdx.x * PR_CHUNK;
     unsigned long long t = 0;
     for (uint32_t k = threadIdx.x; k < PR_CHUNK; k += blockDim.x)
@@ -368,6 +379,7 @@ __global__ void __launch_bounds__(256) k_pr_chunk_sums(const uint32_t *__restric
 // Exclusive scan of the chunk sums in place; part[nchunks] = total.  One
 // block; each thread scans a contiguous run of chunks.
 __global__ void __launch_bounds__(1024) k_pr_scan_parts(unsigned long long *part, uint32_t nchunks) {
+    pdl_wait();
     __shared__ unsigned long long s_run[1024];
     const uint32_t per = (nchunks + blockDim.x - 1) / blockDim.x;
     const uint32_t lo = threadIdx.x * per, hi = min(nchunks, lo + per);
@@ -397,6 +409,7 @@ __global__ void __launch_bounds__(1024) k_pr_scan_parts(unsigned long long *part
 __global__ void __launch_bounds__(256) k_pr_scan_apply(const uint32_t *__restrict__ x, uint32_t n,
                                                        const unsigned long long *__restrict__ part,
                                                        uint32_t nchunks, unsigned long long *off) {
+    pdl_wait();
     const uint32_t base = blockIdx.x * PR_CHUNK;
     uint32_t v[4];
     uint32_t loc = 0;
@@ -422,6 +435,7 @@ __global__ void __launch_bounds__(256) k_pr_fill(GraphView g, const uint2 *__res
                                                  const uint32_t *nitems, uint32_t aib,
                                                  const unsigned long long *__restrict__ off, uint32_t *cursor,
                                                  uint32_t *in_src, uint32_t *in_dst, unsigned long long ecap) {
+    pdl_wait();
     __shared__ uint32_t s_bid[8][32];
     const uint32_t n = *nitems;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -457,6 +471,7 @@ __global__ void __launch_bounds__(256) k_pr_gather(const uint32_t *__restrict__ 
                                                    const uint32_t *__restrict__ in_dst,
                                                    const unsigned long long *total, const double *__restrict__ c,
                                                    double *acc, unsigned long long ecap) {
+    pdl_wait();
     const unsigned long long E = min(*total, ecap);
     const uint32_t lane = lane_id();
     const unsigned long long warp = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) >> 5;
@@ -485,6 +500,7 @@ __global__ void __launch_bounds__(256) k_pr_gather(const uint32_t *__restrict__ 
 __global__ void __launch_bounds__(256) k_pr_update(GraphView g, double *r, const double *__restrict__ acc,
                                                    double *dang, uint32_t slot, const unsigned long long *N,
                                                    double damping) {
+    pdl_wait();
     const double n = (double)*N;
     const double dm = dang[slot];
     if (blockIdx.x == 0 && threadIdx.x == 0) dang[slot ^ 1u] = 0.0;
@@ -505,21 +521,22 @@ cudaError_t launch_pagerank(const GraphView &g, uint32_t aib, uint32_t iteration
     cudaMemsetAsync(nitems, 0, 4, lc.stream);
     cudaMemsetAsync(scal, 0, 2 * sizeof(double), lc.stream);
     cudaMemsetAsync(cursor, 0, (size_t)g.nv * 4, lc.stream);
+    // kernels right after a memset are ordinary launches
     k_pr_count<<<gnv, 256, 0, lc.stream>>>(g, N);
-    k_pr_start<<<gnv, 256, 0, lc.stream>>>(g, r, N);
-    k_an_items<<<grid, 256, 0, lc.stream>>>(g, nullptr, nullptr, aib, items, nitems);
+    launch_pdl(k_pr_start, gnv, 256, 0, lc.stream, g, r, N);
+    launch_pdl(k_an_items, grid, 256, 0, lc.stream, g, nullptr, nullptr, aib, items, nitems);
     // incoming CSR: in-degrees -> offsets -> entries placed per destination
-    k_pr_indeg<<<grid, 256, 0, lc.stream>>>(g, items, nitems, aib, cursor);
-    k_pr_chunk_sums<<<nchunks, 256, 0, lc.stream>>>(cursor, g.nv, part);
-    k_pr_scan_parts<<<1, 1024, 0, lc.stream>>>(part, nchunks);
-    k_pr_scan_apply<<<nchunks, 256, 0, lc.stream>>>(cursor, g.nv, part, nchunks, in_off);
+    launch_pdl(k_pr_indeg, grid, 256, 0, lc.stream, g, items, nitems, aib, cursor);
+    launch_pdl(k_pr_chunk_sums, nchunks, 256, 0, lc.stream, cursor, g.nv, part);
+    launch_pdl(k_pr_scan_parts, 1, 1024, 0, lc.stream, part, nchunks);
+    launch_pdl(k_pr_scan_apply, nchunks, 256, 0, lc.stream, cursor, g.nv, part, nchunks, in_off);
     cudaMemsetAsync(cursor, 0, (size_t)g.nv * 4, lc.stream);
     k_pr_fill<<<grid, 256, 0, lc.stream>>>(g, items, nitems, aib, in_off, cursor, in_src, in_dst, ecap);
     for (uint32_t it = 0; it < iterations; ++it) {
         const uint32_t slot = it & 1u;
-        k_pr_contrib<<<gnv, 256, 0, lc.stream>>>(g, r, c, acc, scal + slot);
-        k_pr_gather<<<grid, 256, 0, lc.stream>>>(in_src, in_dst, in_off + g.nv, c, acc, ecap);
-        k_pr_update<<<gnv, 256, 0, lc.stream>>>(g, r, acc, scal, slot, N, damping);
+        launch_pdl(k_pr_contrib, gnv, 256, 0, lc.stream, g, r, c, acc, scal + slot);
+        launch_pdl(k_pr_gather, grid, 256, 0, lc.stream, in_src, in_dst, in_off + g.nv, c, acc, ecap);
+        launch_pdl(k_pr_update, gnv, 256, 0, lc.stream, g, r, acc, scal, slot, N, damping);
     }
     return cudaGetLastError();
 }
