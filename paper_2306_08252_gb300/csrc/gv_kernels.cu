@@ -2134,10 +2134,10 @@ cudaError_t launch_vertex_delete(const GraphView &g, const uint32_t *ids, uint32
     const int gi = lc.num_sms * GRID_MULT;
     PhaseScope ps(lc, PH_VDEL);
     k_vdel_mark<<<grid_for(k, 256, cap), 256, 0, lc.stream>>>(g, ids, k);
-    k_plan_vfree<<<grid_for(k, 256, cap), 256, 0, lc.stream>>>(g);
-    k_free_items<<<gi, 256, 0, lc.stream>>>(g);
-    k_reset_lists<<<1, 32, 0, lc.stream>>>(g);
-    k_plan_vdel_in<<<grid_for(g.nv, 256, cap), 256, 0, lc.stream>>>(g);
+    launch_pdl(k_plan_vfree, grid_for(k, 256, cap), 256, 0, lc.stream, g);
+    launch_pdl(k_free_items, gi, 256, 0, lc.stream, g);
+    launch_pdl(k_reset_lists, 1, 32, 0, lc.stream, g);
+    launch_pdl(k_plan_vdel_in, grid_for(g.nv, 256, cap), 256, 0, lc.stream, g);
     // disjoint tiers, as in deletes: the thread-per-source one on the side stream
     const bool fork = lc.side && lc.fork && lc.join;
     if (fork) {
@@ -2146,11 +2146,11 @@ cudaError_t launch_vertex_delete(const GraphView &g, const uint32_t *ids, uint32
         k_mark_tiny<MODE_VDEL><<<grid_for(g.nv, 256, cap), 256, 0, lc.side>>>(g);
         cudaEventRecord(lc.join, lc.side);
     }
-    if (g.wdata) k_mark<MODE_VDEL, true><<<gi, 256, 0, lc.stream>>>(g);
-    else k_mark<MODE_VDEL><<<gi, 256, 0, lc.stream>>>(g);
-    if (!fork) k_mark_tiny<MODE_VDEL><<<grid_for(g.nv, 256, cap), 256, 0, lc.stream>>>(g);
-    k_vscan<MODE_VDEL><<<grid_for(g.nv, 8, cap), 256, 0, lc.stream>>>(g);
-    k_move<MODE_VDEL><<<gi, 256, 0, lc.stream>>>(g);
+    if (g.wdata) launch_pdl(k_mark<MODE_VDEL, true>, gi, 256, 0, lc.stream, g);
+    else launch_pdl(k_mark<MODE_VDEL>, gi, 256, 0, lc.stream, g);
+    if (!fork) launch_pdl(k_mark_tiny<MODE_VDEL>, grid_for(g.nv, 256, cap), 256, 0, lc.stream, g);
+    launch_pdl(k_vscan<MODE_VDEL>, grid_for(g.nv, 8, cap), 256, 0, lc.stream, g);
+    launch_pdl(k_move<MODE_VDEL>, gi, 256, 0, lc.stream, g);
     if (fork) cudaStreamWaitEvent(lc.stream, lc.join, 0);
     k_finalize_vdel<<<grid_for(k, 256, cap), 256, 0, lc.stream>>>(g, ids, k);
     return cudaGetLastError();
@@ -2189,12 +2189,12 @@ __global__ void k_segment_noop_check(GraphView g, const unsigned long long *tot,
 
 cudaError_t launch_segment_noop_check(const GraphView &g, const unsigned long long *tot, unsigned long long n,
                                       const LaunchCfg &lc) {
-    k_segment_noop_check<<<(2 * g.set_G + 255) / 256, 256, 0, lc.stream>>>(g, tot, n);
+    launch_pdl(k_segment_noop_check, (2 * g.set_G + 255) / 256, 256, 0, lc.stream, g, tot, n);
     return cudaGetLastError();
 }
 
 cudaError_t launch_set_insert_counts(const GraphView &g, const LaunchCfg &lc) {
-    k_set_insert_counts<<<(g.set_G + 255) / 256, 256, 0, lc.stream>>>(g);
+    launch_pdl(k_set_insert_counts, (g.set_G + 255) / 256, 256, 0, lc.stream, g);
     return cudaGetLastError();
 }
 }  // namespace gv
@@ -2212,18 +2212,18 @@ cudaError_t launch_dedup_insert_prepare(const GraphView &g0, const uint32_t *src
     const unsigned long long nt = tcap < n ? tcap : n;
     const int gt = grid_for(nt, 256, cap);
     const int gi = grid_for(4 * nt + 256, 8, cap);
-    k_plan_member<MODE_DEDUP><<<gt, 256, 0, lc.stream>>>(g);
-    k_arena_init<MODE_DEDUP><<<grid_for(8 * n + 64, 256, cap), 256, 0, lc.stream>>>(g);
-    k_scatter_member<MODE_DEDUP><<<grid_for(n, 256 * PP, cap), 256, 0, lc.stream>>>(g, src, dst, n);
-    k_mark<MODE_QUERY><<<gi, 256, 0, lc.stream>>>(g);
-    k_dedup_select<<<grid_for(n, 256, cap), 256, 0, lc.stream>>>(g, src, n, src2, tmp + 1);
-    k_copy_rejects<<<1, 32, 0, lc.stream>>>(g.dev, tmp);
-    k_finalize_member<MODE_QUERY><<<gt, 256, 0, lc.stream>>>(g, nullptr);
+    launch_pdl(k_plan_member<MODE_DEDUP>, gt, 256, 0, lc.stream, g);
+    launch_pdl(k_arena_init<MODE_DEDUP>, grid_for(8 * n + 64, 256, cap), 256, 0, lc.stream, g);
+    launch_pdl(k_scatter_member<MODE_DEDUP>, grid_for(n, 256 * PP, cap), 256, 0, lc.stream, g, src, dst, n);
+    launch_pdl(k_mark<MODE_QUERY>, gi, 256, 0, lc.stream, g);
+    launch_pdl(k_dedup_select, grid_for(n, 256, cap), 256, 0, lc.stream, g, src, n, src2, tmp + 1);
+    launch_pdl(k_copy_rejects, 1, 32, 0, lc.stream, g.dev, tmp);
+    launch_pdl(k_finalize_member<MODE_QUERY>, gt, 256, 0, lc.stream, g, nullptr);
     return cudaGetLastError();
 }
 cudaError_t launch_dedup_counts(Dev *dev, const unsigned long long *tmp, unsigned long long n,
                                 unsigned long long *counts, const LaunchCfg &lc) {
-    k_dedup_counts<<<1, 32, 0, lc.stream>>>(dev, tmp, n, counts);
+    launch_pdl(k_dedup_counts, 1, 32, 0, lc.stream, dev, tmp, n, counts);
     return cudaGetLastError();
 }
 }  // namespace gv
@@ -2232,7 +2232,7 @@ namespace gv {
 // Clears the per-call state of a counting pass whose batch is not applied
 // (the first batch of a set-semantics graph, counted only to fix C).
 cudaError_t launch_finalize_count_only(const GraphView &g, const LaunchCfg &lc) {
-    k_finalize_member<MODE_QUERY><<<grid_for(g.nv, 256, lc.num_sms * GRID_MULT), 256, 0, lc.stream>>>(g, nullptr);
+    launch_pdl(k_finalize_member<MODE_QUERY>, grid_for(g.nv, 256, lc.num_sms * GRID_MULT), 256, 0, lc.stream, g, nullptr);
     return cudaGetLastError();
 }
 }  // namespace gv

@@ -7,6 +7,7 @@ namespace gv {
 // Sentinel attach ("Dynamic vertex updates": one thread per vertex attaches
 // an empty edge sentinel).
 __global__ void __launch_bounds__(256) k_init_vertices(GraphView g, uint32_t from, uint32_t to) {
+    pdl_wait();
     for (uint32_t u = from + blockIdx.x * blockDim.x + threadIdx.x; u < to; u += gridDim.x * blockDim.x) {
         g.sent[u] = make_uint4(0, 0, NIL, NIL);
         g.alive[u] = 1;
@@ -17,6 +18,7 @@ __global__ void __launch_bounds__(256) k_init_vertices(GraphView g, uint32_t fro
 __global__ void __launch_bounds__(256) k_copy_dictionary(uint4 *dst_sent, uint8_t *dst_alive,
                                                          const uint4 *src_sent, const uint8_t *src_alive,
                                                          uint32_t n) {
+    pdl_wait();
     for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
         dst_sent[u] = src_sent[u];
         dst_alive[u] = src_alive[u];
@@ -25,17 +27,20 @@ __global__ void __launch_bounds__(256) k_copy_dictionary(uint4 *dst_sent, uint8_
 
 // Edge queue: every pool block id, in order ("Edge Queue").
 __global__ void __launch_bounds__(256) k_init_queue(uint32_t *queue, unsigned long long P) {
+    pdl_wait();
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < P;
          i += (unsigned long long)gridDim.x * blockDim.x)
         queue[i] = (uint32_t)i;
 }
 
 __global__ void __launch_bounds__(256) k_iota(uint32_t *out, uint32_t first, uint32_t k) {
+    pdl_wait();
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x)
         out[i] = first + i;
 }
 
 __global__ void __launch_bounds__(256) k_degrees(GraphView g, uint32_t *deg, uint8_t *alive) {
+    pdl_wait();
     for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < g.nv; u += gridDim.x * blockDim.x) {
         deg[u] = g.sent[u].x;
         if (alive) alive[u] = g.alive[u];
@@ -59,6 +64,7 @@ __device__ __forceinline__ unsigned long long vid_degree(const GraphView &g, uin
 __global__ void __launch_bounds__(SCAN_T) k_nbr_partials(GraphView g, const uint32_t *__restrict__ vids,
                                                          uint32_t n, uint32_t round_to,
                                                          unsigned long long *partials) {
+    pdl_wait();
     const uint32_t chunk = blockIdx.x;
     unsigned long long s = 0;
     for (int j = 0; j < SCAN_PER; ++j) {
@@ -71,6 +77,7 @@ __global__ void __launch_bounds__(SCAN_T) k_nbr_partials(GraphView g, const uint
 
 // Exclusive scan of the chunk sums by one CTA.
 __global__ void __launch_bounds__(1024) k_nbr_scan_partials(unsigned long long *partials, uint32_t nchunks) {
+    pdl_wait();
     __shared__ unsigned long long s_carry;
     __shared__ unsigned long long s_w[32];
     if (threadIdx.x == 0) s_carry = 0;
@@ -110,6 +117,7 @@ __global__ void __launch_bounds__(SCAN_T) k_nbr_apply(GraphView g, const uint32_
                                                       uint32_t n, uint32_t round_to,
                                                       const unsigned long long *partials,
                                                       uint32_t nchunks, unsigned long long *offsets) {
+    pdl_wait();
     const uint32_t chunk = blockIdx.x;
     // thread-local run over SCAN_PER consecutive elements
     unsigned long long v[SCAN_PER];
@@ -140,6 +148,7 @@ __global__ void __launch_bounds__(SCAN_T) k_nbr_apply(GraphView g, const uint32_
 
 // Items over the requested vertices' blocks (touched index = request index).
 __global__ void __launch_bounds__(256) k_nbr_plan(GraphView g, const uint32_t *__restrict__ vids, uint32_t n) {
+    pdl_wait();
     const uint32_t IB = g.IB;
     __shared__ uint32_t s_ai;
     for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
@@ -169,6 +178,7 @@ __global__ void __launch_bounds__(256) k_nbr_plan(GraphView g, const uint32_t *_
 // One warp per item: copy the item's slots in heap (storage) order.
 __global__ void __launch_bounds__(256) k_nbr_copy(GraphView g, const unsigned long long *__restrict__ offsets,
                                                   uint32_t *__restrict__ nbrs, uint32_t *__restrict__ wts) {
+    pdl_wait();
     const uint32_t nitems = g.dev->n_items;
     const uint32_t lane = lane_id();
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -217,6 +227,7 @@ __global__ void __launch_bounds__(256) k_nbr_copy(GraphView g, const unsigned lo
 }
 
 __global__ void k_clear_items(GraphView g) {
+    pdl_wait();
     if (threadIdx.x == 0 && blockIdx.x == 0) g.dev->n_items = 0;
 }
 
@@ -225,6 +236,7 @@ __global__ void k_clear_items(GraphView g) {
 // res[0] += stored entries of live vertices, res[1] += live vertices with at
 // least one entry (the paper's block-size rule, "Initialization").
 __global__ void __launch_bounds__(256) k_degree_stats(GraphView g, unsigned long long *res) {
+    pdl_wait();
     unsigned long long e = 0, nz = 0;
     for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < g.nv; u += gridDim.x * blockDim.x) {
         const uint32_t d = g.alive[u] ? g.sent[u].x : 0u;
@@ -245,6 +257,7 @@ __global__ void __launch_bounds__(256) k_degree_stats(GraphView g, unsigned long
 // (shuffled from the lane that loaded them); sums meet in shared memory and
 // then in `res`, 128 atomics per CTA.
 __global__ void __launch_bounds__(256) k_footprint_blocks(GraphView g, unsigned long long *res) {
+    pdl_wait();
     __shared__ unsigned long long s_acc[128];
     for (uint32_t i = threadIdx.x; i < 128; i += blockDim.x) s_acc[i] = 0;
     __syncthreads();
@@ -302,6 +315,7 @@ constexpr uint32_t PLACE_SMALL = 32;
 
 __global__ void __launch_bounds__(256) k_reblock_place(GraphView g, const unsigned long long *__restrict__ slots,
                                                        uint32_t *big, unsigned long long *nbig) {
+    pdl_wait();
     const uint32_t C = g.C;
     for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < g.nv; u += gridDim.x * blockDim.x) {
         const uint32_t deg = g.alive[u] ? g.sent[u].x : 0u;
@@ -324,6 +338,7 @@ __global__ void __launch_bounds__(256) k_reblock_place(GraphView g, const unsign
 __global__ void __launch_bounds__(256) k_reblock_big(GraphView g, const unsigned long long *__restrict__ slots,
                                                      const uint32_t *__restrict__ big,
                                                      const unsigned long long *nbig) {
+    pdl_wait();
     const uint32_t C = g.C;
     const uint32_t n = (uint32_t)*nbig;
     for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
@@ -349,7 +364,7 @@ cudaError_t launch_reblock_place(const GraphView &g, const unsigned long long *s
     cudaMemsetAsync(nbig, 0, sizeof(unsigned long long), lc.stream);
     if (g.nv) {
         k_reblock_place<<<grid_for(g.nv, 256, lc.num_sms * 16), 256, 0, lc.stream>>>(g, slots, big, nbig);
-        k_reblock_big<<<lc.num_sms * 4, 256, 0, lc.stream>>>(g, slots, big, nbig);
+        launch_pdl(k_reblock_big, lc.num_sms * 4, 256, 0, lc.stream, g, slots, big, nbig);
     }
     return cudaGetLastError();
 }
@@ -377,6 +392,7 @@ __device__ __forceinline__ uint32_t cbt_walk_checked(const uint32_t *links, unsi
 
 __global__ void __launch_bounds__(256) k_validate_vertices(GraphView g, uint32_t *owner,
                                                            unsigned long long *res) {
+    pdl_wait();
     const uint32_t lane = lane_id();
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -418,6 +434,7 @@ __global__ void __launch_bounds__(256) k_validate_vertices(GraphView g, uint32_t
 
 __global__ void __launch_bounds__(256) k_validate_queue(GraphView g, uint32_t *owner,
                                                         unsigned long long *res) {
+    pdl_wait();
     const unsigned long long qf = g.dev->q_front, qb = g.dev->q_back, P = g.P;
     if (P == 0) return;
     unsigned long long viol = 0, cnt = 0;
@@ -463,6 +480,7 @@ cudaError_t launch_init_queue(uint32_t *queue, unsigned long long P, const Launc
 // 0 .. free-1, then the new ids P .. P2-1.
 __global__ void k_grow_queue(const uint32_t *__restrict__ q, unsigned long long P, unsigned long long qf,
                              unsigned long long nfree, uint32_t *__restrict__ q2, unsigned long long P2) {
+    pdl_wait();
     const unsigned long long tot = nfree + (P2 - P);
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < tot;
          i += (unsigned long long)gridDim.x * blockDim.x)
@@ -497,8 +515,8 @@ cudaError_t launch_neighbor_offsets(const GraphView &g, const uint32_t *vids, ui
     }
     PhaseScope ps(lc, PH_NEIGHBORS);
     k_nbr_partials<<<nchunks, SCAN_T, 0, lc.stream>>>(g, vids, n, round_to, partials);
-    k_nbr_scan_partials<<<1, 1024, 0, lc.stream>>>(partials, nchunks);
-    k_nbr_apply<<<nchunks, SCAN_T, 0, lc.stream>>>(g, vids, n, round_to, partials, nchunks, offsets);
+    launch_pdl(k_nbr_scan_partials, 1, 1024, 0, lc.stream, partials, nchunks);
+    launch_pdl(k_nbr_apply, nchunks, SCAN_T, 0, lc.stream, g, vids, n, round_to, partials, nchunks, offsets);
     return cudaGetLastError();
 }
 
@@ -508,15 +526,15 @@ cudaError_t launch_neighbor_copy(const GraphView &g, const uint32_t *vids, uint3
     if (n == 0) return cudaSuccess;
     PhaseScope ps(lc, PH_NEIGHBORS);
     k_nbr_plan<<<grid_for(n, 256, lc.num_sms * 8), 256, 0, lc.stream>>>(g, vids, n);
-    k_nbr_copy<<<lc.num_sms * 8, 256, 0, lc.stream>>>(g, offsets, nbrs, wts);
-    k_clear_items<<<1, 32, 0, lc.stream>>>(g);
+    launch_pdl(k_nbr_copy, lc.num_sms * 8, 256, 0, lc.stream, g, offsets, nbrs, wts);
+    launch_pdl(k_clear_items, 1, 32, 0, lc.stream, g);
     return cudaGetLastError();
 }
 
 cudaError_t launch_validate(const GraphView &g, uint32_t *owner_bits, unsigned long long *res,
                             const LaunchCfg &lc) {
     k_validate_vertices<<<lc.num_sms * 8, 256, 0, lc.stream>>>(g, owner_bits, res);
-    k_validate_queue<<<lc.num_sms * 8, 256, 0, lc.stream>>>(g, owner_bits, res);
+    launch_pdl(k_validate_queue, lc.num_sms * 8, 256, 0, lc.stream, g, owner_bits, res);
     return cudaGetLastError();
 }
 
