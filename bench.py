@@ -736,7 +736,7 @@ def run_rows(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
-    reps = max(args.steps, 3)
+    reps = max(args.steps, 10)  # median of at least 10 repeats after a warm-up call
     rows = []
 
     def timed(fn, pre=None, post=None, n=reps):
@@ -794,7 +794,7 @@ def run_rows(args):
         holder["g"].reserve(max(BATCH, BASE_EDGES))
         torch.cuda.synchronize()
 
-    ms = timed(lambda: holder["g"].bulk_build(d_bs, d_bd, cnt), pre=mk, n=3)
+    ms = timed(lambda: holder["g"].bulk_build(d_bs, d_bd, cnt), pre=mk)
     row("a5", "bulk build", bs.size, "edges", ms, 12 * bs.size + 16 * nv)
 
     # f4 (memory footprint, the paper's Table 5): device memory of the
@@ -894,14 +894,14 @@ def run_rows(args):
     # next rows: BFS from the largest hub, PageRank (10 iterations)
     dist = torch.zeros(nv, dtype=torch.int32, device="cuda")
     src = int(np.argmax(deg0))
-    ms = timed(lambda: gv.gv_bfs(g.handle, src, dist, stream.cuda_stream), n=3)
+    ms = timed(lambda: gv.gv_bfs(g.handle, src, dist, stream.cuda_stream))
     reached = dist.cpu().numpy().view(np.uint32) != 0xFFFFFFFF
     trav = int(deg0[reached].sum())
     row("f2-bfs", f"BFS from vertex {src} ({int(reached.sum())} reached)", trav, "traversed edges", ms,
         8 * trav + 16 * int(reached.sum()) + 4 * nv, timer="CUDA events (one host read per four levels)")
     rank = torch.zeros(nv, dtype=torch.float64, device="cuda")
     iters = 10
-    ms = timed(lambda: gv.gv_pagerank(g.handle, iters, 0.85, rank, stream.cuda_stream), n=3)
+    ms = timed(lambda: gv.gv_pagerank(g.handle, iters, 0.85, rank, stream.cuda_stream))
     row("f2-pagerank", f"PageRank, {iters} iterations", iters * E, "edge visits", ms,
         iters * (4 * E + 8 * E + 48 * nv))
     g.close()
@@ -914,7 +914,7 @@ def run_rows(args):
     gs.insert_edges_weighted(d_bs, d_bd, d_bw, cnt)
     sdist = torch.zeros(nv, dtype=torch.int64, device="cuda")
     rounds = []
-    ms = timed(lambda: rounds.append(gv.gv_sssp(gs.handle, src, sdist, stream.cuda_stream)), n=3)
+    ms = timed(lambda: rounds.append(gv.gv_sssp(gs.handle, src, sdist, stream.cuda_stream)))
     sreached = sdist.cpu().numpy().view(np.uint64) != np.uint64(0xFFFFFFFFFFFFFFFF)
     strav = int(deg0[sreached].sum())
     row("f2-sssp", f"shortest paths from vertex {src}, lengths in [0, 1000) ({int(sreached.sum())} reached, "
@@ -995,7 +995,7 @@ def run_rows(args):
         holder3["g"].reserve(BASE_EDGES)
         torch.cuda.synchronize()
 
-    ms = timed(lambda: holder3["g"].bulk_build(d_bs, d_bd, cnt), pre=mk3, n=3)
+    ms = timed(lambda: holder3["g"].bulk_build(d_bs, d_bd, cnt), pre=mk3)
     grown = holder3["g"].stats()
     row("f4-grow", f"bulk build with pool growth ({small >> 20} MiB -> {grown['pool_bytes'] >> 20} MiB)",
         bs.size, "edges", ms, 12 * bs.size + 16 * nv, pool_bytes_final=grown["pool_bytes"],
@@ -1036,7 +1036,7 @@ def run_rows(args):
         holder_e["g"].bulk_build(d_es, d_ed, cnt)
         torch.cuda.synchronize()
 
-    ms = timed(lambda: holder_e["g"].delete_edges(d_ds, d_dd, cnt), pre=mk_e, n=3)
+    ms = timed(lambda: holder_e["g"].delete_edges(d_ds, d_dd, cnt), pre=mk_e)
     holder_e["g"].close()
     row("a6 ER", f"mixed delete of {del_op.src.size} pairs (half stored, half absent)", del_op.src.size, "edges",
         ms, 8 * del_op.src.size + 4 * int(deg_er[dsrc].sum()) + 32 * dsrc.size)
@@ -1053,13 +1053,13 @@ def run_rows(args):
             holder2["g"].delete_vertices(spare)
         torch.cuda.synchronize()
 
-    ms = timed(lambda: holder2["g"].delete_vertices(d_ids), pre=mk2, n=3)
+    ms = timed(lambda: holder2["g"].delete_vertices(d_ids), pre=mk2)
     E2 = int(es.size)
     row("a10", f"delete {vdel.size} vertices (outgoing and incoming edges)", vdel.size, "vertices", ms,
         4 * E2 + 16 * vdel.size + 16 * nv2 // 8)
     k = 65_536
     newids = torch.zeros(k, dtype=torch.int32, device="cuda")
-    ms = timed(lambda: holder2["g"].insert_vertices(k, newids), pre=lambda: mk2(False), n=3)
+    ms = timed(lambda: holder2["g"].insert_vertices(k, newids), pre=lambda: mk2(False))
     row("a9", f"insert {k} vertices (dictionary doubling from 2^22)", k, "vertices", ms,
         2 * 17 * nv2 + 17 * k + 4 * k, timer="CUDA events (the dictionary's new allocation included)")
     holder2["g"].close()
