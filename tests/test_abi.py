@@ -82,3 +82,11 @@ def test_multiply_shift_division_by_block_capacity_is_exact():
         xs += [k * C + r for k in (1, 7, 1 << 20, (1 << 31) // C - 1) for r in (0, C - 1)]
         for x in xs:
             assert (x * M) >> 40 == x // C, (C, x)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # no CPU fallback: without the CUDA library every entry point raises
+    import paper_2306_08252_gb300.graphvine as gvb
+    monkeypatch.setattr(gvb, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        gvb.load(str(tmp_path / "libgraphvine.so"))
