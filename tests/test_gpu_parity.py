@@ -514,55 +514,3 @@ def test_small_insert_path_matches_general_path(C):
                 np.testing.assert_array_equal(wt[order], owt)
         finally:
             p.close()
-
-
-@pytest.mark.parametrize("n", [1500, 60_000])  # the one-CTA insert and the general path
-def test_plain_calls_captured_in_a_cuda_graph(n):
-    # insert / query / delete calls on a plain graph captured once and
-    # replayed (the second stream and the programmatic dependent launches
-    # are part of the capture): every replay gives the counts and query bits
-    # of the calls made directly, and the graph ends equal to the oracle's
-    import torch
-    scale, nv = 13, 1 << 13
-    p = Pair(nv, C=8, pool_bytes=128 << 20)
-    try:
-        bs, bd = W.rmat_pairs(66, 0, 50_000, scale)
-        p.bulk(bs, bd)
-        s, d = W.rmat_pairs(66, 1, n, scale)
-        qs = np.concatenate([s[: n // 2], bs[:1000]])
-        qd = np.concatenate([d[: n // 2], bd[:1000]])
-        ds, dd, dqs, dqd = dev_u32(s), dev_u32(d), dev_u32(qs), dev_u32(qd)
-        p.g.reserve(max(n, 50_000))
-        ci = torch.zeros(2, dtype=torch.int64, device="cuda")
-        cd = torch.zeros(2, dtype=torch.int64, device="cuda")
-        out = torch.zeros(qs.size, dtype=torch.uint8, device="cuda")
-        # direct calls first (they also size the scratch), then the capture
-        p.g.insert_edges(ds, dd, ci)
-        p.g.query_edges(dqs, dqd, out)
-        p.g.delete_edges(ds, dd, cd)
-        torch.cuda.synchronize()
-        exp = (tuple(ci.tolist()), out.cpu().numpy().copy(), tuple(cd.tolist()))
-        assert exp[0] == p.o.insert_edges(s, d)
-        np.testing.assert_array_equal(exp[1], p.o.query_edges(qs, qd))
-        assert exp[2] == p.o.delete_edges(s, d)
-        step = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(step, capture_error_mode="relaxed"):
-            p.g.insert_edges(ds, dd, ci)
-            p.g.query_edges(dqs, dqd, out)
-            p.g.delete_edges(ds, dd, cd)
-        for _ in range(3):
-            ci.zero_(); cd.zero_(); out.zero_()
-            step.replay()
-            torch.cuda.synchronize()
-            assert tuple(ci.tolist()) == exp[0] and tuple(cd.tolist()) == exp[2]
-            np.testing.assert_array_equal(out.cpu().numpy(), exp[1])
-        p.check()  # the batch's pairs are gone again, as in the oracle
-        ins = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(ins, capture_error_mode="relaxed"):
-            p.g.insert_edges(ds, dd, ci)
-        ins.replay()
-        torch.cuda.synchronize()
-        assert tuple(ci.tolist()) == p.o.insert_edges(s, d)
-        p.check()
-    finally:
-        p.close()
