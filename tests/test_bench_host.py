@@ -1,0 +1,51 @@
+"""Host arithmetic of the benchmark, on the CPU: the algorithmic-byte model
+(per operation and per kernel, with the split between the two mark tiers)
+against hand-computed values on a small graph state."""
+import types
+
+import numpy as np
+
+import bench
+
+
+def _fake_graph(deg):
+    return types.SimpleNamespace(degrees=lambda: (np.asarray(deg, dtype=np.uint32), None))
+
+
+def test_byte_model_closed_forms():
+    C = bench.BLOCK
+    deg = np.zeros(64, dtype=np.int64)
+    deg[1] = 10          # tiny: <= 8 blocks, <= 128 entries
+    deg[2] = 200         # warp tier (more than 128 entries)
+    deg[3] = 5           # tiny for deletes, but 20 batch entries: warp tier
+    src = np.array([1] * 3 + [2] * 4 + [3] * 20 + [70, 5], dtype=np.uint32)  # 70 is out of range
+    dst = np.array([7] * (src.size - 2) + [1, 99], dtype=np.uint32)          # 99 out of range
+    qs = np.array([1, 2, 2, 9, 80], dtype=np.uint32)
+    qd = np.array([3, 3, 4, 5, 6], dtype=np.uint32)
+    m = bench.byte_model(_fake_graph(deg), (src, dst), (qs, qd), inserted=27, deleted=27, newblocks=3)
+    valid = (src < 64) & (dst < 64)
+    us = np.unique(src[valid])                  # 1, 2, 3 (5's pair has dst 99)
+    assert list(us) == [1, 2, 3]
+    assert m["insert"] == 12 * 27 + 32 * 3 + 12 * 3
+    assert m["query"] == 9 * 5 + 4 * (10 + 200 + 0)  # distinct queried sources 1, 2, 9
+    assert m["delete"] == 8 * src.size + 4 * (10 + 200 + 5) + 32 * 3 + 4 * 3
+    k = m["kernels"]
+    # delete tiers: source 1 tiny (10 entries, 3 batch entries); 2 and 3 in the warp tier
+    assert k["delete.mark_tiny"] == 4 * 10 + 4 * 3
+    assert k["delete.mark"] == 4 * (200 + 5) + 4 * (4 + 20)
+    # the two tiers cover every stored entry and batch entry of the touched sources
+    assert k["delete.mark"] + k["delete.mark_tiny"] == 4 * (10 + 200 + 5) + 4 * 27
+    # query tiers (tiny: <= 4 blocks, <= 64 entries): 1 tiny, 2 warp, 9 has no entries
+    assert k["query.mark_tiny"] == 4 * 10 + 4 * 1
+    assert k["query.mark"] == 4 * 200 + 4 * 2
+    assert k["insert.count"] == 12 * src.size and k["insert.scatter"] == 16 * 27
+    assert k["delete.scatter"] == 16 * src.size and k["query.scatter"] == 16 * qs.size
+    assert k["insert.touched"] == 4 * 64  # the counter array of the dictionary's capacity
+    assert m["step"] == m["insert"] + m["query"] + m["delete"]
+    assert C == 16
+
+
+def test_whole_job_rate_and_config():
+    assert bench.whole_job_rate(10, 4, 2.0) == 10 * 4 / 2e-3
+    cfg = bench.config_dict(types.SimpleNamespace(batch=bench.BATCH, queries=bench.QUERIES, gpus=1), 1)
+    assert "workload" in cfg and str(bench.BATCH) in cfg["workload"]
