@@ -15,9 +15,10 @@
  *     tensor) or in host memory (pinned or pageable).  Host arrays are copied
  *     to and from library-owned device staging buffers.  The edge batches of
  *     gv_bulk_build, gv_insert_edges, gv_insert_edges_weighted,
- *     gv_delete_edges and gv_query_edges are copied on a copy stream the library owns, into one
- *     of three rotating staging sets, so that a call's copies overlap the
- *     kernels of the calls before it; `stream` waits for them.  Their host
+ *     gv_delete_edges and gv_query_edges are copied on a copy stream the
+ *     library owns, into one of three rotating staging sets, so that a
+ *     call's copies overlap the kernels of the calls before it; `stream`
+ *     waits for them.  Their host
  *     OUTPUT arrays (counts, query results) are written in stream order: a
  *     page-locked output holds its values once `stream` has reached the
  *     end of the call (synchronise `stream`, or gv_sync, before reading it);
@@ -26,9 +27,8 @@
  *   - The caller owns every array it passes; it must stay valid, and a host
  *     input unchanged, until the call's work on `stream` has completed (a
  *     pageable host input may be reused once the call returns).  The
- *     library owns the graph
- *     state, the block pool (unless gv_config.pool_mem is given) and its
- *     scratch memory.
+ *     library owns the graph state, the block pool (unless
+ *     gv_config.pool_mem is given) and its scratch memory.
  *   - Calls are asynchronous and ordered on `stream` (a cudaStream_t, passed
  *     as void*; NULL = the legacy default stream).  Calls on one graph must
  *     be ordered by the caller (one stream, or explicit dependencies): the
@@ -37,6 +37,9 @@
  *     library may fork part of the work onto a second stream it owns; that
  *     work joins back onto `stream` before the call's last kernel, so the
  *     ordering on `stream` (and stream capture into a CUDA graph) holds.
+ *     Consecutive kernels of a call are launched with programmatic stream
+ *     serialization: each may be scheduled while its predecessor drains and
+ *     waits, at its first instruction, for the predecessor's results.
  *   - The return value reports host-detectable errors at once (NULL graph,
  *     NULL array with n > 0, n too large, CUDA launch or allocation failure).
  *     Errors found on the device (edge pool exhausted, structure
