@@ -90,3 +90,36 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(gvb, "_lib", None)
     with pytest.raises(RuntimeError, match="missing"):
         gvb.load(str(tmp_path / "libgraphvine.so"))
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    # a C99 caller: the header compiles without C++ (-pedantic, warnings as
+    # errors), links against the library and makes calls that need no GPU
+    import os
+    import shutil
+    import subprocess
+    from paper_2306_08252_gb300 import build as b
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "caller.c"
+    src.write_text(
+        '#include "graphvine.h"\n'
+        "#include <stdio.h>\n"
+        "#include <string.h>\n"
+        "int main(void) {\n"
+        "    gv_graph *g = (gv_graph *)0;\n"
+        "    if (gv_create((const gv_config *)0, 16, (void *)0, (gv_graph **)0) != GV_ERR_INVALID_ARG) return 1;\n"
+        "    if (gv_sync(g) != GV_ERR_INVALID_ARG) return 2;\n"
+        "    if (gv_destroy(g) != GV_OK) return 3;\n"
+        "    if (strcmp(gv_status_string(GV_ERR_OUT_OF_MEMORY), \"\") == 0) return 4;\n"
+        "    printf(\"%s\\n\", gv_status_string(GV_OK));\n"
+        "    return 0;\n"
+        "}\n")
+    exe = tmp_path / "caller"
+    libdir = os.path.dirname(b.LIB)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(root, "include"),
+                    str(src), "-L", libdir, "-lgraphvine", f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, (r.returncode, r.stderr)
+    assert r.stdout.strip()
