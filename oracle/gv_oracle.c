@@ -369,7 +369,9 @@ uint64_t orc_blocks_for_degree(uint64_t deg, uint32_t C) { return (deg + C - 1) 
  * Edge-block size rule (section "Initialization"): the average degree of the
  * vertices with non-zero degree in the first batch.  Rounding is not stated;
  * the reading taken: ceil of the average, rounded up to a multiple of 4, at
- * least 4 (so that blocks hold whole 16-byte vectors).
+ * least 4 (so that blocks hold whole 16-byte vectors) and at most 512 (the
+ * paper bounds neither end; 512 slots is the largest block the structure
+ * takes, so a mean degree above 512 gives C = 512).
  */
 uint32_t orc_block_capacity_rule(const uint32_t *deg, uint32_t nv) {
     uint64_t sum = 0, nz = 0;
@@ -378,7 +380,7 @@ uint32_t orc_block_capacity_rule(const uint32_t *deg, uint32_t nv) {
     uint64_t avg = (sum + nz - 1) / nz;
     uint64_t c = (avg + 3) / 4 * 4;
     if (c < 4) c = 4;
-    if (c > 1024) c = 1024;
+    if (c > 512) c = 512;
     return (uint32_t)c;
 }
 

@@ -30,6 +30,33 @@ def test_tiny_uniform_config_every_batch():
         p.close()
 
 
+def test_rule_capacity_above_512():
+    """The paper's C rule on a first batch whose mean non-zero degree is past
+    512: both sides take the largest block (512 slots); then a second batch,
+    a delete spanning several blocks per source and the full CSR."""
+    import oracle
+    nv = 256
+    rng = np.random.default_rng(5)
+    srcs = np.repeat(np.arange(0, nv, 4, dtype=np.uint32), 700)  # 64 sources, 700 entries each
+    dsts = rng.integers(0, nv, srcs.size).astype(np.uint32)
+    p = Pair(nv, C=0, pool_bytes=32 << 20)
+    try:
+        p.bulk(srcs, dsts)
+        st = p.check()
+        rule = oracle.block_capacity_rule(np.bincount(srcs, minlength=nv))
+        assert rule == 512
+        assert st["block_capacity"] == rule
+        s2 = rng.integers(0, nv, 5000).astype(np.uint32)
+        d2 = rng.integers(0, nv, 5000).astype(np.uint32)
+        p.insert(s2, d2)
+        p.check()
+        p.delete(np.concatenate([srcs[::3], s2[:100]]), np.concatenate([dsts[::3], d2[:100]]))
+        p.check()
+        p.query(srcs[::5], dsts[::5])
+    finally:
+        p.close()
+
+
 @pytest.mark.parametrize("C", [4, 8, 16, 20, 64, 0])
 def test_rmat_skewed_batches(C):
     scale, nv = 12, 1 << 12

@@ -359,6 +359,12 @@ def test_block_capacity_rule():
     assert oracle.block_capacity_rule([0, 0, 0]) == 4
     assert oracle.block_capacity_rule([1, 1, 2]) == 4      # at least 4
     assert oracle.block_capacity_rule([17, 18]) == 20      # ceil(17.5) = 18 -> multiple of 4
+    # the upper end: a mean non-zero degree past 512 gives the largest block
+    assert oracle.block_capacity_rule([508]) == 508
+    assert oracle.block_capacity_rule([509]) == 512        # 509 -> 512 by the rounding
+    assert oracle.block_capacity_rule([513]) == 512        # 516 by the rounding, then the cap
+    assert oracle.block_capacity_rule([2000, 3000, 0]) == 512
+    assert oracle.block_capacity_rule([1] * 10 + [100000]) == 512  # ceil(100010 / 11) = 9092
 
 
 def test_min_footprint_capacity():
