@@ -86,24 +86,31 @@ def config_dict(args, n):
 
 # ------------------------------------------------------------ CPU baseline
 
-def oracle_sample_rate(base, upd, qry, budget_s=12.0, sample=1_000_000, qsample=100_000, max_steps=None):
-    """The oracle (single thread, as it stands) on a bounded sample of the
-    step: insert `sample` edges of the batch, query `qsample`, delete them."""
+def oracle_sample_rate(base, upd, qry, budget_s=12.0, warmup=1):
+    """The oracle (single thread, as it stands) on whole steps of the
+    workload: insert the full batch, answer every query, delete the batch,
+    on the full bulk-built graph; `warmup` untimed steps first (the first
+    delete also removes the base graph's copies of batch pairs), then steps
+    until `budget_s` of timed work (at least one)."""
     import oracle
     o = oracle.OracleGraph(1 << SCALE)
     o.bulk_build(*base)
-    s, d = upd[0][:sample], upd[1][:sample]
-    qs, qd = qry[0][:qsample], qry[1][:qsample]
+
+    def ostep():
+        ins, _ = o.insert_edges(*upd)
+        o.query_edges(*qry)
+        dele, _ = o.delete_edges(*upd)
+        return ins + dele
+
+    for _ in range(warmup):
+        ostep()
     done = 0
     t_total = 0.0
     steps = 0
-    while (t_total < budget_s and (max_steps is None or steps < max_steps)) or steps == 0:
+    while t_total < budget_s or steps == 0:
         t0 = time.perf_counter()
-        ins, _ = o.insert_edges(s, d)
-        o.query_edges(qs, qd)
-        dele, _ = o.delete_edges(s, d)
+        done += ostep()
         t_total += time.perf_counter() - t0
-        done += ins + dele
         steps += 1
     o.close()
     return done / t_total, steps, t_total
@@ -1091,16 +1098,15 @@ def main():
             return 0
         base, upd, qry = workload(args.batch, args.queries)
         import oracle
-        sample, qsample = 1_000_000, 100_000
         o = oracle.OracleGraph(1 << SCALE)
         o.bulk_build(*base)
-        s, d = upd[0][:sample], upd[1][:sample]
-        qs, qd = qry[0][:qsample], qry[1][:qsample]
 
+        # every step is the whole step of the GPU arm's config: insert the
+        # full batch, answer every query, delete the batch
         def ostep():
-            a, _ = o.insert_edges(s, d)
-            o.query_edges(qs, qd)
-            b, _ = o.delete_edges(s, d)
+            a, _ = o.insert_edges(*upd)
+            o.query_edges(*qry)
+            b, _ = o.delete_edges(*upd)
             return a + b
 
         for _ in range(args.warmup):
@@ -1111,14 +1117,16 @@ def main():
             done += ostep()
         dt = time.perf_counter() - t0
         v = done / dt
+        o.close()
         a = argparse.Namespace(**vars(args))
         res = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
                "data": "synthetic", "config": config_dict(a, world),
                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"per step: insert {sample} edges of the batch, query {qsample}, "
-                                          f"delete the {sample}, on the full bulk-built graph"},
+                                "sample": f"{args.steps} whole steps after {args.warmup} untimed ones: insert the "
+                                          f"{args.batch}-edge batch, {args.queries} queries, delete the batch, "
+                                          f"on the full bulk-built graph"},
                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(res), flush=True)
         return 0
@@ -1132,8 +1140,9 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         v, steps, secs = oracle_sample_rate(base, upd, qry)
         res["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                               "sample": f"{steps} steps of insert 1,000,000 edges of the batch + query 100,000 + "
-                                         f"delete them, on the full bulk-built graph ({secs:.1f} s)"}
+                               "sample": f"{steps} whole steps after one untimed step: insert the {args.batch}-edge "
+                                         f"batch, {args.queries} queries, delete the batch, on the full bulk-built "
+                                         f"graph ({secs:.1f} s timed)"}
         cores = host_cores()
         v, steps, secs = parallel_cpu_rate(base, upd, qry, cores)
         res["cpu_parallel"] = {"value": v, "unit": UNIT, "cores": cores, "cpu": cpu_model(),
