@@ -405,11 +405,10 @@ gv_status gv_set_member_neighbors(gv_graph *set, uint32_t member, uint64_t *offs
  * gv_degree_offsets_noalloc -- CSR offsets of the listed vertices' current
  * out-degrees, computed without allocating any memory.  The paper has no
  * counterpart; this entry point exists for callers that cannot allocate
- * device memory at the point of the call: code that runs while a stream is
- * being captured into a CUDA graph (cudaMalloc and cudaFree are not allowed
- * there), serving loops that must not stall on an allocation (cudaFree
- * synchronises the whole device), and processes whose device memory is
- * owned by another allocator.
+ * device memory at the point of the call: serving loops that must not stall
+ * on an allocation (cudaFree synchronises the whole device), processes whose
+ * device memory is all held by another allocator (a framework's caching
+ * allocator), and code that runs under a fixed device-memory budget.
  *   d_vids     n uint32 vertex ids, DEVICE memory only.
  *   n          at most 67,108,864 (2^26); larger n returns GV_ERR_INVALID_ARG
  *              and does nothing.
@@ -425,7 +424,11 @@ gv_status gv_set_member_neighbors(gv_graph *set, uint32_t member, uint64_t *offs
  * overlaps on the GPU -- on different streams without ordering, from any
  * graph -- race on it and must be serialised by the caller.  The first call
  * on each device looks up the array's device address (cudaGetSymbolAddress),
- * so make that first call before any stream capture begins.
+ * and so does the first call after the device's context was replaced (for
+ * example by cudaDeviceReset); make that first call before any stream
+ * capture begins.  An error already pending in the CUDA runtime when the
+ * call starts (from the caller's own launches) is returned as GV_ERR_CUDA
+ * and left pending, not cleared.
  */
 gv_status gv_degree_offsets_noalloc(gv_graph *g, const uint32_t *d_vids, uint32_t n, uint64_t *d_offsets,
                                     void *stream);

@@ -4,6 +4,7 @@
 // pool, scratch), staging of host arrays, and the launch sequence of each
 // operation.  Every step of an operation runs in the kernels of
 // gv_kernels.cu / gv_misc.cu; nothing here touches graph data on the host.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -1365,35 +1366,66 @@ gv_status gv_validate(gv_graph *g, uint64_t *violations, void *stream) {
 // library-allocated memory, so the call performs no allocation at all.  Every
 // GPU that loads this library holds the array (512 KiB) until the process
 // exits.  In host code `g_noalloc_partials` is only a host-side stand-in for
-// the symbol: its device address is taken once per device, with that device
-// current, by cudaGetSymbolAddress on the first call made on that device.
+// the symbol: its device address is taken by cudaGetSymbolAddress, with the
+// device current, on the first call made on that device, and taken again
+// only if the device's context has been replaced since (cudaDeviceReset
+// destroys the context and the module with it, so an address cached from the
+// old context would point at freed memory).
 
 }  // extern "C"
 
 namespace {
-constexpr uint32_t kNoAllocScanChunk = 1024;                           // ids per scan chunk (gv_misc.cu)
-constexpr uint32_t kNoAllocMaxVertices = 1u << 26;                     // ids per call
-constexpr uint32_t kNoAllocChunks = kNoAllocMaxVertices / kNoAllocScanChunk;
+constexpr uint32_t kNoAllocMaxVertices = 1u << 26;  // ids per call
+constexpr uint32_t kNoAllocChunks = (kNoAllocMaxVertices + gv::SCAN_CHUNK - 1) / gv::SCAN_CHUNK;
+// launch_neighbor_offsets writes one chunk sum per SCAN_CHUNK ids plus the
+// total: the array must hold that many for the largest call accepted
+static_assert((unsigned long long)kNoAllocChunks * gv::SCAN_CHUNK >= kNoAllocMaxVertices,
+              "scratch array too small for the largest call");
 constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void *g_noalloc_addr[kNoAllocMaxDevices] = {};
+CUcontext g_noalloc_ctx[kNoAllocMaxDevices] = {};
 }  // namespace
 
 static __device__ __align__(256) unsigned long long g_noalloc_partials[kNoAllocChunks + 1];
 
 namespace {
+// The driver's current context of the calling thread, through the runtime's
+// driver entry point (no link against the driver library); nullptr if the
+// entry point is unavailable.
+CUcontext current_context() {
+    using Fn = CUresult (*)(CUcontext *);
+    static Fn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        return reinterpret_cast<Fn>(p);
+    }();
+    CUcontext c = nullptr;
+    if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+    return c;
+}
+
 // Device address of the scratch array on `dev` (which must be current).
 gv_status noalloc_scratch(int dev, unsigned long long **out) {
     if (dev < 0 || dev >= kNoAllocMaxDevices) return GV_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
+    const CUcontext ctx = current_context();
+    // without a context handle to compare, look the address up on every call
+    if (!g_noalloc_addr[dev] || ctx == nullptr || ctx != g_noalloc_ctx[dev]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
         if (e != cudaSuccess || p == nullptr) {
-            cudaGetLastError();
+            cudaGetLastError();  // this call's own error (no error was pending at entry)
+            g_noalloc_addr[dev] = nullptr;
             return GV_ERR_CUDA;
         }
         g_noalloc_addr[dev] = p;
+        g_noalloc_ctx[dev] = ctx;
     }
     *out = static_cast<unsigned long long *>(g_noalloc_addr[dev]);
     return GV_OK;
@@ -1407,6 +1439,8 @@ gv_status gv_degree_offsets_noalloc(gv_graph *g, const uint32_t *d_vids, uint32_
     if (!g || !d_offsets || (n > 0 && !d_vids)) return GV_ERR_INVALID_ARG;
     if (n > kNoAllocMaxVertices) return GV_ERR_INVALID_ARG;
     DeviceGuard dg(g->device);
+    // an error the caller's own work left pending is reported, not cleared
+    if (cudaPeekAtLastError() != cudaSuccess) return GV_ERR_CUDA;
     // Host arrays would need staging buffers, i.e. an allocation.
     if (is_host_ptr(d_offsets) || (n > 0 && is_host_ptr(d_vids))) return GV_ERR_INVALID_ARG;
     unsigned long long *scratch = nullptr;

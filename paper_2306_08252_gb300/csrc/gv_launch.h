@@ -220,6 +220,12 @@ constexpr int AGG_SPT = AGG_H / AGG_THREADS;     // hash slots per thread
 constexpr int PP = GV_PP;                        // pairs per thread per step (streaming kernels)
 constexpr int GRID_MULT = GV_GRID_MULT;          // CTAs per SM of grid-stride kernels
 constexpr int MASK_WORDS = 16;                   // survivor bits per item (512 slots)
+// Neighbour-offset scan: SCAN_T threads per CTA, SCAN_PER ids each; one
+// chunk sum per SCAN_CHUNK ids (launch_neighbor_offsets' `partials` holds
+// ceil(n / SCAN_CHUNK) + 1 of them).
+constexpr int SCAN_T = 256;
+constexpr int SCAN_PER = 4;
+constexpr int SCAN_CHUNK = SCAN_T * SCAN_PER;
 static_assert(AGG_H >= 2 * AGG_TILE, "aggregation table must be at most half full");
 static_assert(AGG_SPT <= 32 && AGG_SPT % 2 == 0, "slots per thread");
 static_assert(AGG_TILE <= (1 << (32 - AGG_HBITS)), "slot and rank must pack into 32 bits");

@@ -49,10 +49,6 @@ __global__ void __launch_bounds__(256) k_degrees(GraphView g, uint32_t *deg, uin
 
 // ------------------------------------------------------------- neighbours
 
-constexpr int SCAN_T = 256;
-constexpr int SCAN_PER = 4;
-constexpr int SCAN_CHUNK = SCAN_T * SCAN_PER;
-
 // Degree of a requested vertex (0 for invalid or deleted ids), rounded up to
 // a multiple of `round_to` when that is non-zero (slots of whole blocks).
 __device__ __forceinline__ unsigned long long vid_degree(const GraphView &g, uint32_t u, uint32_t round_to) {
@@ -509,9 +505,9 @@ cudaError_t launch_neighbor_offsets(const GraphView &g, const uint32_t *vids, ui
                                     const LaunchCfg &lc, uint32_t round_to) {
     const uint32_t nchunks = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
     if (nchunks == 0) {
-        cudaMemsetAsync(offsets, 0, sizeof(unsigned long long), lc.stream);
-        cudaMemsetAsync(partials, 0, sizeof(unsigned long long), lc.stream);
-        return cudaGetLastError();
+        cudaError_t e = cudaMemsetAsync(offsets, 0, sizeof(unsigned long long), lc.stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(partials, 0, sizeof(unsigned long long), lc.stream);
+        return e;
     }
     PhaseScope ps(lc, PH_NEIGHBORS);
     k_nbr_partials<<<nchunks, SCAN_T, 0, lc.stream>>>(g, vids, n, round_to, partials);

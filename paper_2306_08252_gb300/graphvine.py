@@ -544,12 +544,3 @@ class Graph:
         check(code, "gv_export_csr")
         return off, nb[:total]
 
-    def canonical_csr(self):
-        """Export with each adjacency sorted (storage order is unspecified)."""
-        off, nb = self.export_csr()
-        nb = nb.copy()
-        for u in range(off.size - 1):
-            a, b = int(off[u]), int(off[u + 1])
-            if b - a > 1:
-                nb[a:b].sort()
-        return off, nb
