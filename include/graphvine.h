@@ -93,6 +93,12 @@ typedef enum gv_status {
  * The pool then holds 8*C + 12 bytes per block.  Excludes GV_DEDUP (which of
  * several repeated pairs a set-semantics batch keeps is not defined). */
 #define GV_WEIGHTED 4u
+/* Large batches (see dense_shift below) of plain inserts, deletes and
+ * queries are grouped by source with a radix partition of the source ids
+ * (no per-pair global atomic); with this flag they take the per-pair atomic
+ * scheme instead (kept for comparison and as the path of dictionaries of
+ * more than 2^24 vertices). */
+#define GV_ATOMIC_GROUPING 8u
 
 typedef struct gv_config {
     /* C, the number of edge entries per edge block (multiple of 4, 4..512).
@@ -100,7 +106,7 @@ typedef struct gv_config {
      * vertices with non-zero degree in the first edge batch, rounded up to a
      * multiple of 4; fixed from then on. */
     uint32_t block_capacity;
-    uint32_t flags;          /* GV_DEDUP | GV_GROW | GV_WEIGHTED, or 0 */
+    uint32_t flags;          /* GV_DEDUP | GV_GROW | GV_WEIGHTED | GV_ATOMIC_GROUPING, or 0 */
     /* Bytes reserved for the edge-block pool: block storage (4*C bytes per
      * block), tree links (8 bytes per block) and the edge queue (4 bytes per
      * block).  0 = half of the free device memory ("Edge Queue": at least
@@ -117,8 +123,12 @@ typedef struct gv_config {
      * warp handles per work item in deletes and queries (1 .. min(32, 512/C);
      * default the maximum) -- fewer blocks put more warps on a long
      * adjacency.  dense_shift: batches of n pairs with n >= vertices >> s
-     * are grouped with one atomic per pair plus a pass over all vertices,
-     * smaller ones with per-tile aggregation (default s = 3). */
+     * (dictionary capacity) are grouped by a radix partition of the source
+     * ids (bucket by the high bits, then a counting sort of each chunk of a
+     * bucket by the low bits) plus a pass over all vertices -- or, with
+     * GV_ATOMIC_GROUPING, set semantics or graph sets, one atomic per pair
+     * plus that pass -- smaller ones with per-tile aggregation (default
+     * s = 3). */
     uint32_t item_blocks;
     uint32_t dense_shift;
     uint32_t reserved;

@@ -126,6 +126,13 @@ struct gv_graph {
     unsigned long long pr_vcap = 0, pr_ecap = 0;
     uint32_t *pr_cursor = nullptr, *pr_src = nullptr, *pr_dst = nullptr;
     unsigned long long *pr_off = nullptr, *pr_part = nullptr;
+    // grouped path of large batches: partitioned pairs, per-CTA bucket
+    // counts, bucket totals and bases, chunk list, block-wide tier groups
+    unsigned long long gp_ncap = 0, gp_acap = 0, gp_hcap = 0, gp_ccap = 0, gp_icap = 0;
+    uint32_t *gp_src = nullptr, *gp_dst = nullptr, *gp_aux = nullptr, *gp_hist = nullptr;
+    uint32_t *gp_btot = nullptr, *gp_bbase = nullptr;
+    uint4 *gp_chunks = nullptr;
+    uint2 *grp_items = nullptr;
     // graph set: members' vertex ranges (set_G == 0 for a plain graph)
     uint32_t set_G = 0;
     uint32_t *set_vbase = nullptr;          // device, G+1
@@ -512,6 +519,71 @@ gv_status ensure_batch(gv_graph *g, uint64_t n, int mode) {
     return GV_OK;
 }
 
+// Does a plain batch call of n pairs take the grouped path?  Large batches
+// (the dense threshold) on dictionaries of at most GP_BMAX * GP_WMAX
+// vertices, unless the graph asked for the per-pair atomic grouping.
+bool use_grouped(const gv_graph *g, uint64_t n) {
+    if (g->flags & GV_ATOMIC_GROUPING) return false;
+    if (g->set_G || g->C == 0 || n == 0) return false;
+    if ((unsigned long long)g->vcap > (unsigned long long)gv::GP_BMAX * gv::GP_WMAX) return false;
+    return n >= ((unsigned long long)g->nv >> g->dense_shift);
+}
+
+template <typename T>
+gv_status grow_buf(T **p, unsigned long long *cap, unsigned long long need, uint64_t *acct) {
+    if (need <= *cap && *cap) return GV_OK;
+    const unsigned long long c = std::max<unsigned long long>(need, std::max<unsigned long long>(2 * *cap, 1024));
+    dfree(*p);
+    *cap = 0;
+    GV_TRY(dalloc(p, c, acct));
+    *cap = c;
+    return GV_OK;
+}
+
+// Scratch of a grouped call of n pairs (aux: a word per pair travels with it).
+gv_status ensure_group(gv_graph *g, uint64_t n, bool aux, unsigned long long items) {
+    uint32_t ctas = 0;
+    unsigned long long len = 0;
+    gv::group_shape(n, g->num_sms, &ctas, &len);
+    if (n > g->gp_ncap || !g->gp_ncap) {
+        const unsigned long long c = std::max<unsigned long long>(n, std::max<unsigned long long>(2 * g->gp_ncap, 4096));
+        dfree(g->gp_src);
+        dfree(g->gp_dst);
+        g->gp_ncap = 0;
+        GV_TRY(dalloc(&g->gp_src, c, &g->scratch_bytes));
+        GV_TRY(dalloc(&g->gp_dst, c, &g->scratch_bytes));
+        g->gp_ncap = c;
+    }
+    if (aux) GV_TRY(grow_buf(&g->gp_aux, &g->gp_acap, n, &g->scratch_bytes));
+    GV_TRY(grow_buf(&g->gp_hist, &g->gp_hcap, (unsigned long long)ctas * gv::GP_BMAX, &g->scratch_bytes));
+    GV_TRY(grow_buf(&g->gp_chunks, &g->gp_ccap, n / gv::GP_CHUNK + gv::GP_BMAX + 1, &g->scratch_bytes));
+    if (!g->gp_btot) GV_TRY(dalloc(&g->gp_btot, gv::GP_BMAX, &g->scratch_bytes));
+    if (!g->gp_bbase) GV_TRY(dalloc(&g->gp_bbase, gv::GP_BMAX, &g->scratch_bytes));
+    if (items) GV_TRY(grow_buf(&g->grp_items, &g->gp_icap, items, &g->scratch_bytes));
+    return GV_OK;
+}
+
+// The graph's view for a grouped call of n pairs.
+GraphView grouped_view(const gv_graph *g, uint64_t n) {
+    GraphView v = view(g);
+    v.grouped = 1;
+    uint32_t sh = 0;
+    while ((g->vcap >> sh) > gv::GP_BMAX) ++sh;
+    v.gb_shift = sh;
+    v.gb_n = g->vcap >> sh;
+    gv::group_shape(n, g->num_sms, &v.gp_ctas, &v.gp_len);
+    v.gp_src = g->gp_src;
+    v.gp_dst = g->gp_dst;
+    v.gp_aux = g->gp_aux;
+    v.gp_hist = g->gp_hist;
+    v.gp_btot = g->gp_btot;
+    v.gp_bbase = g->gp_bbase;
+    v.gp_chunks = g->gp_chunks;
+    v.gcur = g->vtid;  // the touched-index array is free during a grouped call
+    v.grp_items = g->grp_items;
+    return v;
+}
+
 gv_status check_launch() {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return GV_ERR_CUDA;
@@ -633,17 +705,30 @@ gv_status set_buf(DevBuf &b, size_t bytes, void **out) {
 // they are); with `count`, also the counting pass of `mode`.  *set_out = the
 // staging set used (-1: none); the caller records its free event on `s`
 // after the call's last launch.
-gv_status stage_batch(gv_graph *g, int mode, const uint32_t *src, const uint32_t *dst, const uint32_t *wts,
-                      uint64_t n, cudaStream_t s, bool count, const void **dsrc, const void **ddst,
-                      const void **dwts, int *set_out) {
+gv_status stage_batch(gv_graph *g, const GraphView &v, int mode, const uint32_t *src, const uint32_t *dst,
+                      const uint32_t *wts, uint64_t n, cudaStream_t s, bool count, const void **dsrc,
+                      const void **ddst, const void **dwts, int *set_out) {
     *set_out = -1;
     *dsrc = src;
     *ddst = dst;
     if (dwts) *dwts = wts;
     const bool hs = is_host_ptr(src), hd = is_host_ptr(dst), hw = wts && is_host_ptr(wts);
-    const GraphView v = view(g);
+    const bool grp = v.grouped != 0;
+    // counting of pairs [lo, hi) as soon as they are on the device, and the
+    // rest of the grouping once all of them are
+    auto count_range = [&](const uint32_t *cs, const uint32_t *cd, uint64_t lo, uint64_t hi) {
+        return grp ? gv::launch_group_hist(mode, v, cs, cd, n, lo, hi, lcfg(g, s))
+                   : gv::launch_count_range(mode, v, cs, cd, n, lo, hi, lcfg(g, s));
+    };
+    auto count_finish = [&](const uint32_t *cs, const uint32_t *cd, const uint32_t *cw) {
+        return grp ? gv::launch_group_finish(mode, v, cs, cd, cw, n, lcfg(g, s))
+                   : gv::launch_count_finish(mode, v, n, lcfg(g, s));
+    };
     if (!hs && !hd && !hw) {
-        if (count) GV_CK(gv::launch_count(mode, v, src, dst, n, lcfg(g, s)));
+        if (count) {
+            GV_CK(count_range(src, dst, 0, n));
+            GV_CK(count_finish(src, dst, wts));
+        }
         return GV_OK;
     }
     const int k = (int)(g->in_round++ % kInSets);
@@ -657,9 +742,15 @@ gv_status stage_batch(gv_graph *g, int mode, const uint32_t *src, const uint32_t
     if (async && set.used) GV_CK(cudaStreamWaitEvent(cs, set.free_ev, 0));
     const uint32_t *ss = hs ? static_cast<const uint32_t *>(bs) : src;
     const uint32_t *sd = hd ? static_cast<const uint32_t *>(bd) : dst;
+    const uint32_t *sw = hw ? static_cast<const uint32_t *>(bw) : wts;
     const int pieces = (count && n >= kPipeMin && g->C != 0) ? kPipePieces : 1;
     for (int p = 0; p < pieces; ++p) {
-        const uint64_t lo = n * p / pieces, hi = n * (p + 1) / pieces;
+        uint64_t lo = n * p / pieces, hi = n * (p + 1) / pieces;
+        if (grp) {
+            // piece boundaries on whole partition-CTA ranges
+            lo = std::min<uint64_t>(n, lo / v.gp_len * v.gp_len);
+            hi = p + 1 == pieces ? n : std::min<uint64_t>(n, hi / v.gp_len * v.gp_len);
+        }
         if (hi > lo) {
             if (hs) GV_CK(cudaMemcpyAsync(static_cast<uint32_t *>(bs) + lo, src + lo, (hi - lo) * 4,
                                           cudaMemcpyHostToDevice, cs));
@@ -672,11 +763,11 @@ gv_status stage_batch(gv_graph *g, int mode, const uint32_t *src, const uint32_t
             GV_CK(cudaEventRecord(set.piece[p], cs));
             GV_CK(cudaStreamWaitEvent(s, set.piece[p], 0));
         }
-        if (count && pieces > 1) GV_CK(gv::launch_count_range(mode, v, ss, sd, n, lo, hi, lcfg(g, s)));
+        if (count && pieces > 1) GV_CK(count_range(ss, sd, lo, hi));
     }
     if (count) {
-        if (pieces > 1) GV_CK(gv::launch_count_finish(mode, v, n, lcfg(g, s)));
-        else GV_CK(gv::launch_count(mode, v, ss, sd, n, lcfg(g, s)));
+        if (pieces == 1) GV_CK(count_range(ss, sd, 0, n));
+        GV_CK(count_finish(ss, sd, sw));
     }
     set.used = true;
     // free once the kernels launched so far are done; the caller records it
@@ -686,7 +777,7 @@ gv_status stage_batch(gv_graph *g, int mode, const uint32_t *src, const uint32_t
     *set_out = k;
     *dsrc = ss;
     *ddst = sd;
-    if (dwts) *dwts = hw ? bw : wts;
+    if (dwts) *dwts = sw;
     return GV_OK;
 }
 
@@ -777,12 +868,15 @@ gv_status insert_impl(gv_graph *g, const uint32_t *src, const uint32_t *dst, uin
         } else {
             int set = -1;
             const bool small = n <= gv::small_insert_max();
-            GV_TRY(stage_batch(g, gv::MODE_INSERT, src, dst, wts, n, s, !small, &dsrc, &ddst, &dwts, &set));
+            const bool grp = !small && use_grouped(g, n);
+            if (grp) GV_TRY(ensure_group(g, n, g->wdata != nullptr, 0));
+            const GraphView v = grp ? grouped_view(g, n) : view(g);
+            GV_TRY(stage_batch(g, v, gv::MODE_INSERT, src, dst, wts, n, s, !small, &dsrc, &ddst, &dwts, &set));
             if (small)
-                GV_CK(gv::launch_insert_small(view(g), (const uint32_t *)dsrc, (const uint32_t *)ddst,
+                GV_CK(gv::launch_insert_small(v, (const uint32_t *)dsrc, (const uint32_t *)ddst,
                                               (const uint32_t *)dwts, n, (unsigned long long *)dcounts, lcfg(g, s)));
             else
-                GV_CK(gv::launch_insert_tail(view(g), (const uint32_t *)dsrc, (const uint32_t *)ddst, n, g->tcap,
+                GV_CK(gv::launch_insert_tail(v, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, g->tcap,
                                              (unsigned long long *)dcounts, lcfg(g, s), (const uint32_t *)dwts));
             GV_TRY(release_set(g, set, s));
         }
@@ -840,9 +934,15 @@ gv_status member_impl(gv_graph *g, int mode, const uint32_t *src, const uint32_t
     bool hq = false;
     if (mode == gv::MODE_QUERY) GV_TRY(output_ptr(g, 3, qout, n, &dq, &hq));
     GV_TRY(ensure_batch(g, n, mode));
+    const bool grp = use_grouped(g, n);
+    if (grp) {
+        const unsigned long long touched = std::min<unsigned long long>(n, g->nv ? g->nv : 1);
+        GV_TRY(ensure_group(g, n, mode == gv::MODE_QUERY, item_bound(g, touched)));
+    }
+    const GraphView v = grp ? grouped_view(g, n) : view(g);
     int set = -1;
-    GV_TRY(stage_batch(g, mode, src, dst, nullptr, n, s, true, &dsrc, &ddst, nullptr, &set));
-    GV_CK(gv::launch_member_tail(mode, view(g), (const uint32_t *)dsrc, (const uint32_t *)ddst, n, g->tcap,
+    GV_TRY(stage_batch(g, v, mode, src, dst, nullptr, n, s, true, &dsrc, &ddst, nullptr, &set));
+    GV_CK(gv::launch_member_tail(mode, v, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, g->tcap,
                                  (unsigned long long *)dcounts, (uint8_t *)dq, lcfg(g, s)));
     GV_TRY(release_set(g, set, s));
     // host outputs land in stream order (a pageable target completes here)
@@ -929,7 +1029,7 @@ gv_status gv_create(const gv_config *cfg, uint32_t num_vertices, void *stream, g
     if (cfg) c = *cfg;
     if (c.block_capacity != 0 && (c.block_capacity < 4 || c.block_capacity > 512 || c.block_capacity % 4))
         return GV_ERR_INVALID_ARG;
-    if (c.flags & ~(GV_DEDUP | GV_GROW | GV_WEIGHTED)) return GV_ERR_INVALID_ARG;
+    if (c.flags & ~(GV_DEDUP | GV_GROW | GV_WEIGHTED | GV_ATOMIC_GROUPING)) return GV_ERR_INVALID_ARG;
     // which of several repeated (u, v) a set-semantics batch keeps is not
     // defined, so their payloads would be: the two flags exclude each other
     if ((c.flags & GV_DEDUP) && (c.flags & GV_WEIGHTED)) return GV_ERR_INVALID_ARG;
@@ -1028,6 +1128,8 @@ gv_status gv_destroy(gv_graph *g) {
         dfree(g->an_items); dfree(g->an_cur); dfree(g->an_next); dfree(g->an_ctr); dfree(g->an_stamp); dfree(g->rb_stats);
         dfree(g->pr_c); dfree(g->pr_acc); dfree(g->pr_scal); dfree(g->pr_n);
         dfree(g->pr_cursor); dfree(g->pr_src); dfree(g->pr_dst); dfree(g->pr_off); dfree(g->pr_part);
+        dfree(g->gp_src); dfree(g->gp_dst); dfree(g->gp_aux); dfree(g->gp_hist);
+        dfree(g->gp_btot); dfree(g->gp_bbase); dfree(g->gp_chunks); dfree(g->grp_items);
         for (auto &b : g->stage.buf) dfree(b.p);
         for (auto &r : g->prof.recs) {
             cudaEventDestroy(r.a);
@@ -1801,7 +1903,10 @@ static const char *kPhaseNames[gv::PH_COUNT] = {
     "delete.mark",    "delete.mark_tiny", "delete.vscan",  "delete.move",      "delete.finalize",
     "query.count",    "query.touched",  "query.plan",      "query.arena",      "query.scatter",
     "query.mark",     "query.mark_tiny", "query.out",      "query.finalize",
-    "vertex_delete",  "neighbors",      "other",          "analytics",      "insert.small"};
+    "vertex_delete",  "neighbors",      "other",          "analytics",      "insert.small",
+    "insert.partition", "insert.vertex_count", "insert.place",
+    "delete.partition", "delete.vertex_count", "delete.place", "delete.mark_cta",
+    "query.partition",  "query.vertex_count",  "query.place",  "query.mark_cta"};
 
 uint32_t gv_profile_num_phases(void) { return gv::PH_COUNT; }
 

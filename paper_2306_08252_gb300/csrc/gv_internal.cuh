@@ -48,6 +48,10 @@ struct Dev {
     unsigned int n_mitems;          // work items of multi-item sources (top of the item array)
     unsigned int n_tiny_hi;         // tiny sources with more than TINY_SPLIT entries (top of t_tiny)
     unsigned long long harena_used; // words of the arena's hash region used
+    // grouped path (large batches): chunks of the partitioned batch, and
+    // work groups of the block-wide membership tier
+    unsigned int n_chunks;
+    unsigned int n_groups;
 };
 
 // Everything a kernel needs to know about one graph (passed by value).
@@ -104,7 +108,42 @@ struct GraphView {
     // segment that first names each batch key, one word per arena word;
     // NULL otherwise
     uint32_t *seg_own;
+    // Grouped path (large plain batches): the batch is grouped by source on
+    // the device by a radix partition (bucket = u >> gb_shift) and a
+    // counting sort per chunk of a bucket; per-vertex scratch is then indexed
+    // by the vertex id itself (no scramble: no per-pair atomics remain).
+    uint32_t grouped;           // 1 during a grouped call
+    uint32_t gb_shift;          // log2(vertices per bucket)
+    uint32_t gb_n;              // buckets (vcap >> gb_shift)
+    uint32_t gp_ctas;           // CTAs of the partition passes
+    unsigned long long gp_len;  // pairs per partition CTA (a multiple of 1024)
+    uint32_t *gp_src;           // partitioned pairs, bucket by bucket
+    uint32_t *gp_dst;
+    uint32_t *gp_aux;           // query: original index; weighted insert: payload
+    uint32_t *gp_hist;          // [gp_ctas][gb_n]: counts, then prefixes over the CTAs
+    uint32_t *gp_btot;          // [gb_n] valid pairs per bucket
+    uint32_t *gp_bbase;         // [gb_n] first partitioned position of each bucket
+    uint4 *gp_chunks;           // {start, length, bucket, -} per chunk
+    uint32_t *gcur;             // per vertex: its segment start, advanced by the placement
+    uint2 *grp_items;           // block-wide membership tier: {touched index, first item}
 };
+
+// Grouped path limits and sizes.
+constexpr uint32_t GP_BMAX = 4096;     // buckets at most (shared counters of a partition CTA)
+constexpr uint32_t GP_WMAX = 4096;     // vertices per bucket at most (shared counters of a chunk CTA)
+constexpr uint32_t GP_CHUNK = 4096;    // pairs per chunk
+constexpr uint32_t GP_THREADS = 512;   // threads of the partition and chunk CTAs
+constexpr uint32_t GP_VPC = 4096;      // vertices per CTA of the per-vertex scan (>= GP_WMAX)
+// Sources with more batch entries than LIST_MAX go to the block-wide
+// membership tier: CT_GI work items per CTA share one shared-memory hash set
+// of the source's batch entries, built CT_KEYS keys at a time.
+constexpr uint32_t CT_GI = 8;
+constexpr uint32_t CT_SLOTS = 8192;
+constexpr uint32_t CT_KEYS = CT_SLOTS / 2;
+constexpr uint32_t CT_FLAG = 0xFFFFFFFFu;  // t_a[t].z of a block-wide-tier source
+
+// Index of vertex u in the per-call vertex scratch (vcnt, vinfo).
+__device__ __forceinline__ uint32_t vidx(const GraphView &g, uint32_t u);
 
 // Segment of pair i: the last s with off[s] <= i (off has G+1 entries).
 __device__ __forceinline__ uint32_t segment_of(const unsigned long long *off, uint32_t G, unsigned long long i) {
@@ -210,6 +249,7 @@ constexpr uint32_t VSCRAMBLE_INV = inverse_odd(VSCRAMBLE);
 static_assert(VSCRAMBLE * VSCRAMBLE_INV == 1u, "scramble inverse");
 
 __device__ __forceinline__ uint32_t vslot(uint32_t vmask, uint32_t u) { return (u * VSCRAMBLE) & vmask; }
+__device__ __forceinline__ uint32_t vidx(const GraphView &g, uint32_t u) { return g.grouped ? u : vslot(g.vmask, u); }
 __device__ __forceinline__ uint32_t vslot_inv(uint32_t vmask, uint32_t i) { return (i * VSCRAMBLE_INV) & vmask; }
 
 // Programmatic dependent launch: a kernel launched with the attribute may be
@@ -376,6 +416,82 @@ __device__ __forceinline__ bool last_cta(Dev *dev) {
     __syncthreads();
     if (s_last) __threadfence();
     return s_last;
+}
+
+// Position off past base in a ring of P slots (base < P, off <= P).
+__device__ __forceinline__ unsigned long long ring(unsigned long long base, unsigned long long off,
+                                                   unsigned long long P) {
+    unsigned long long q = base + off;
+    return q >= P ? q - P : q;
+}
+
+// Freed block ids of one warp, staged in shared memory and pushed onto the
+// edge queue 32 at a time with one atomic on the call's free counter (the
+// queue positions are q_back + counter, published by the finalize kernel).
+struct FreeStage {
+    uint32_t *buf;  // 64 ids: this warp's slice of shared memory
+    uint32_t n;     // ids held (warp-uniform)
+
+    __device__ __forceinline__ void flush(uint32_t cnt, Dev *dev, uint32_t *queue, unsigned long long qbb,
+                                          unsigned long long P) {
+        unsigned long long base = 0;
+        if (lane_id() == 0 && cnt) base = atomicAdd(&dev->free_total, (unsigned long long)cnt);
+        base = __shfl_sync(FULL, base, 0);
+        if (lane_id() < cnt) queue[ring(qbb, base + lane_id(), P)] = buf[lane_id()];
+        __syncwarp();
+    }
+
+    // All 32 lanes call; lanes with `want` add `id`.
+    __device__ __forceinline__ void push(bool want, uint32_t id, Dev *dev, uint32_t *queue, unsigned long long qbb,
+                                         unsigned long long P) {
+        const uint32_t lane = lane_id();
+        const unsigned bal = __ballot_sync(FULL, want);
+        if (want) buf[n + __popc(bal & ((1u << lane) - 1u))] = id;
+        n += __popc(bal);
+        __syncwarp();
+        if (n >= 32) {
+            flush(32, dev, queue, qbb, P);
+            const uint32_t rem = n - 32;
+            const uint32_t x = lane < rem ? buf[32 + lane] : 0u;
+            __syncwarp();
+            if (lane < rem) buf[lane] = x;
+            __syncwarp();
+            n = rem;
+        }
+    }
+};
+
+// ------------------------------------------------------------ work items
+
+// Items over the blocks of one touched source: t_b[t] = {deg, nblocks, root,
+// items}; t_a[t].w = first item.  Returns nothing; writes the item list.
+__device__ __forceinline__ void emit_items(const GraphView &g, uint32_t t, uint32_t item0,
+                                           uint32_t ni) {
+    for (uint32_t c = 0; c < ni; ++c) g.items[item0 + c] = make_uint2(t, c);
+}
+
+// First work item of a source with ni items, for every thread of the block
+// (all threads call): single-item sources count up from the bottom of the
+// item array, multi-item sources down from the top (so the kernels that
+// handle only multi-item sources visit only their items).
+__device__ __forceinline__ uint32_t alloc_items(const GraphView &g, uint32_t ni, uint32_t *s_lo, uint32_t *s_hi) {
+    uint32_t ltot, htot;
+    const uint32_t lex = block_excl_scan(ni == 1 ? 1u : 0u, &ltot);
+    const uint32_t hex = block_excl_scan(ni > 1 ? ni : 0u, &htot);
+    if (threadIdx.x == 0) {
+        *s_lo = ltot ? atomicAdd(&g.dev->n_items, ltot) : 0u;
+        *s_hi = htot ? atomicAdd(&g.dev->n_mitems, htot) : 0u;
+    }
+    __syncthreads();
+    if (ni == 1) return *s_lo + lex;
+    if (ni > 1) return (uint32_t)(g.max_items - (*s_hi + hex + ni));
+    return 0u;
+}
+
+// Work item of virtual index vi over both regions ([0, nlo) bottom, then the
+// nhi top items).
+__device__ __forceinline__ uint32_t item_at(const GraphView &g, uint32_t vi, uint32_t nlo, uint32_t nhi) {
+    return vi < nlo ? vi : (uint32_t)(g.max_items - nhi + (vi - nlo));
 }
 
 }  // namespace gv

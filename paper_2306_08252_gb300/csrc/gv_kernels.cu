@@ -79,48 +79,6 @@ __device__ __forceinline__ uint32_t agg_insert(uint32_t *keys, uint32_t *cnt, ui
     return h;
 }
 
-__device__ __forceinline__ unsigned long long ring(unsigned long long base, unsigned long long off,
-                                                   unsigned long long P) {
-    unsigned long long q = base + off;
-    return q >= P ? q - P : q;
-}
-
-// Freed block ids of one warp, staged in shared memory and pushed onto the
-// edge queue 32 at a time with one atomic on the call's free counter (the
-// queue positions are q_back + counter, published by the finalize kernel).
-struct FreeStage {
-    uint32_t *buf;  // 64 ids: this warp's slice of shared memory
-    uint32_t n;     // ids held (warp-uniform)
-
-    __device__ __forceinline__ void flush(uint32_t cnt, Dev *dev, uint32_t *queue, unsigned long long qbb,
-                                          unsigned long long P) {
-        unsigned long long base = 0;
-        if (lane_id() == 0 && cnt) base = atomicAdd(&dev->free_total, (unsigned long long)cnt);
-        base = __shfl_sync(FULL, base, 0);
-        if (lane_id() < cnt) queue[ring(qbb, base + lane_id(), P)] = buf[lane_id()];
-        __syncwarp();
-    }
-
-    // All 32 lanes call; lanes with `want` add `id`.
-    __device__ __forceinline__ void push(bool want, uint32_t id, Dev *dev, uint32_t *queue, unsigned long long qbb,
-                                         unsigned long long P) {
-        const uint32_t lane = lane_id();
-        const unsigned bal = __ballot_sync(FULL, want);
-        if (want) buf[n + __popc(bal & ((1u << lane) - 1u))] = id;
-        n += __popc(bal);
-        __syncwarp();
-        if (n >= 32) {
-            flush(32, dev, queue, qbb, P);
-            const uint32_t rem = n - 32;
-            const uint32_t x = lane < rem ? buf[32 + lane] : 0u;
-            __syncwarp();
-            if (lane < rem) buf[lane] = x;
-            __syncwarp();
-            n = rem;
-        }
-    }
-};
-
 // ---------------------------------------------------------------- grouping
 
 // Loads one tile's pairs and their validity with every global load issued
@@ -489,7 +447,7 @@ __global__ void __launch_bounds__(256) k_finalize_insert(GraphView g, unsigned l
     const uint32_t C = g.C;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
         const uint32_t u = g.t_vid[t];
-        const uint32_t cnt = g.vcnt[vslot(g.vmask, u)];
+        const uint32_t cnt = g.vcnt[vidx(g, u)];
         if (!abort) {
             const uint4 a = g.t_a[t];
             const uint32_t deg = a.x, off = a.z, need = a.w;
@@ -503,7 +461,7 @@ __global__ void __launch_bounds__(256) k_finalize_insert(GraphView g, unsigned l
             }
             g.sent[u] = s;
         }
-        g.vcnt[vslot(g.vmask, u)] = 0;
+        g.vcnt[vidx(g, u)] = 0;
     }
     if (last_cta(dev) && threadIdx.x == 0) {
         unsigned long long rej = dev->call_b;
@@ -530,6 +488,8 @@ __global__ void __launch_bounds__(256) k_finalize_insert(GraphView g, unsigned l
         dev->n_tiny_hi = 0;
         dev->arena_used = 0;
         dev->harena_used = 0;
+        dev->n_chunks = 0;
+        dev->n_groups = 0;
         dev->free_total = 0;
         dev->abort = 0;
         dev->done_ctas = 0;
@@ -730,37 +690,6 @@ __global__ void __launch_bounds__(SMALL_THREADS, 1) k_insert_small(GraphView g, 
 }
 
 // ------------------------------------------------------ membership pipeline
-
-// Items over the blocks of one touched source: t_b[t] = {deg, nblocks, root,
-// items}; t_a[t].w = first item.  Returns nothing; writes the item list.
-__device__ __forceinline__ void emit_items(const GraphView &g, uint32_t t, uint32_t item0,
-                                           uint32_t ni) {
-    for (uint32_t c = 0; c < ni; ++c) g.items[item0 + c] = make_uint2(t, c);
-}
-
-// First work item of a source with ni items, for every thread of the block
-// (all threads call): single-item sources count up from the bottom of the
-// item array, multi-item sources down from the top (so the kernels that
-// handle only multi-item sources visit only their items).
-__device__ __forceinline__ uint32_t alloc_items(const GraphView &g, uint32_t ni, uint32_t *s_lo, uint32_t *s_hi) {
-    uint32_t ltot, htot;
-    const uint32_t lex = block_excl_scan(ni == 1 ? 1u : 0u, &ltot);
-    const uint32_t hex = block_excl_scan(ni > 1 ? ni : 0u, &htot);
-    if (threadIdx.x == 0) {
-        *s_lo = ltot ? atomicAdd(&g.dev->n_items, ltot) : 0u;
-        *s_hi = htot ? atomicAdd(&g.dev->n_mitems, htot) : 0u;
-    }
-    __syncthreads();
-    if (ni == 1) return *s_lo + lex;
-    if (ni > 1) return (uint32_t)(g.max_items - (*s_hi + hex + ni));
-    return 0u;
-}
-
-// Work item of virtual index vi over both regions ([0, nlo) bottom, then the
-// nhi top items).
-__device__ __forceinline__ uint32_t item_at(const GraphView &g, uint32_t vi, uint32_t nlo, uint32_t nhi) {
-    return vi < nlo ? vi : (uint32_t)(g.max_items - nhi + (vi - nlo));
-}
 
 // Per touched source: arena words for its batch destinations (a list up to
 // LIST_MAX entries, else a hash set), and either the tiny tier (one thread,
@@ -1062,6 +991,7 @@ __global__ void __launch_bounds__(256, 4) k_mark(GraphView g) {
         const uint2 itm = g.items[it];
         const uint32_t t = itm.x, c = itm.y;
         const uint4 a = g.t_a[t];
+        if (a.z == CT_FLAG) continue;  // a source of the block-wide tier (k_mark_cta)
         const uint4 b = g.t_b[t];
         const uint32_t deg = b.x, nb = b.y, root = b.z, ni = b.w;
         const uint32_t kb = c * IB;
@@ -1611,7 +1541,7 @@ __global__ void __launch_bounds__(256) k_finalize_member(GraphView g, unsigned l
     const uint32_t nt = dev->n_touched;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
         const uint32_t u = g.t_vid[t];
-        g.vcnt[vslot(g.vmask, u)] = 0;
+        g.vcnt[vidx(g, u)] = 0;
     }
     if (last_cta(dev) && threadIdx.x == 0) {
         if (MODE == MODE_DELETE) {
@@ -1634,6 +1564,8 @@ __global__ void __launch_bounds__(256) k_finalize_member(GraphView g, unsigned l
         dev->n_tiny_hi = 0;
         dev->arena_used = 0;
         dev->harena_used = 0;
+        dev->n_chunks = 0;
+        dev->n_groups = 0;
         dev->free_total = 0;
         dev->abort = 0;
         dev->done_ctas = 0;
@@ -1795,6 +1727,8 @@ __global__ void __launch_bounds__(256) k_finalize_vdel(GraphView g, const uint32
         dev->n_tiny_hi = 0;
         dev->arena_used = 0;
         dev->harena_used = 0;
+        dev->n_chunks = 0;
+        dev->n_groups = 0;
         dev->free_total = 0;
         dev->abort = 0;
         dev->done_ctas = 0;
@@ -2025,14 +1959,19 @@ cudaError_t launch_insert_tail(const GraphView &g, const uint32_t *src, const ui
     const int gt = grid_for(tcap < n ? tcap : n, 256, cap);
     {
         PhaseScope ps(lc, PH_INS_PLAN);
-        launch_pdl(k_plan_insert, gt, 256, 0, lc.stream, g);
+        if (g.grouped) launch_gp_plan_insert(g, gt, lc);
+        else launch_pdl(k_plan_insert, gt, 256, 0, lc.stream, g);
     }
     const unsigned long long max_pops = n / g.C + (tcap < n ? tcap : n) + 1;  // new blocks: <= n/C + sources
     {
         PhaseScope ps(lc, PH_INS_LINK);
         launch_pdl(k_link_insert, grid_for(max_pops, 256, cap), 256, 0, lc.stream, g);
     }
-    {
+    if (g.grouped) {
+        // the grouped batch goes straight from its chunks into the slots
+        const cudaError_t e = launch_group_place(MODE_INSERT, g, n, lc);
+        if (e != cudaSuccess) return e;
+    } else {
         PhaseScope ps(lc, PH_INS_SCATTER);
         if (g.wdata) launch_pdl(k_scatter_insert<true>, grid_for(n, 256 * PP, cap), 256, 0, lc.stream, g, src, dst, wts, n);
         else launch_pdl(k_scatter_insert<false>, grid_for(n, 256 * PP, cap), 256, 0, lc.stream, g, src, dst, wts, n);
@@ -2058,15 +1997,19 @@ static void member_tail(const GraphView &g0, const uint32_t *src, const uint32_t
     const int gt = grid_for(nt, 256, cap);
     const int gi = grid_for(4 * nt + 256, 8, lc.num_sms * GRID_MULT);  // warp-per-item kernels: 8 warps per CTA
     const bool del = MODE == MODE_DELETE;
-    {
+    if (g.grouped) {
+        // the grouping already placed every source's batch list in the arena
         PhaseScope ps(lc, del ? PH_DEL_PLAN : PH_QRY_PLAN);
-        launch_pdl(k_plan_member<MODE>, gt, 256, 0, lc.stream, g);
-    }
-    {
-        PhaseScope ps(lc, del ? PH_DEL_ARENA : PH_QRY_ARENA);
-        launch_pdl(k_arena_init<MODE>, grid_for(5 * n + 64, 256, cap), 256, 0, lc.stream, g);
-    }
-    {
+        launch_gp_plan_member(MODE, g, gt, lc);
+    } else {
+        {
+            PhaseScope ps(lc, del ? PH_DEL_PLAN : PH_QRY_PLAN);
+            launch_pdl(k_plan_member<MODE>, gt, 256, 0, lc.stream, g);
+        }
+        {
+            PhaseScope ps(lc, del ? PH_DEL_ARENA : PH_QRY_ARENA);
+            launch_pdl(k_arena_init<MODE>, grid_for(5 * n + 64, 256, cap), 256, 0, lc.stream, g);
+        }
         PhaseScope ps(lc, del ? PH_DEL_SCATTER : PH_QRY_SCATTER);
         launch_pdl(k_scatter_member<MODE>, grid_for(n, 256 * PP, cap), 256, 0, lc.stream, g, src, dst, n);
     }
@@ -2088,6 +2031,9 @@ static void member_tail(const GraphView &g0, const uint32_t *src, const uint32_t
         if (MODE != MODE_QUERY && g.wdata) launch_pdl(k_mark<MODE, true>, gi, 256, 0, lc.stream, g);
         else launch_pdl(k_mark<MODE>, gi, 256, 0, lc.stream, g);
     }
+    // sources with more than LIST_MAX batch entries (grouped path only):
+    // disjoint from the warp tier's sources
+    if (g.grouped) launch_mark_cta(MODE, g, nt, lc);
     if (!fork) {
         PhaseScope ps(lc, del ? PH_DEL_MARK_TINY : PH_QRY_MARK_TINY);
         launch_pdl(k_mark_tiny<MODE>, gt, 256, 0, lc.stream, g);

@@ -112,6 +112,69 @@ def test_hub_deletes_across_many_items():
         p.close()
 
 
+@pytest.mark.parametrize("weighted", [False, True])
+def test_hub_batch_lists_past_one_shared_slice(weighted):
+    """Sources with more batch entries than one shared-memory slice of the
+    block-wide membership tier (several slices per group of work items), a
+    single-item source with more than 256 batch entries (compacted in place
+    by that tier), queries with repeats; plain and weighted graphs."""
+    import paper_2306_08252_gb300 as gv
+    nv = 20000
+    rng = np.random.default_rng(11)
+    hub_d = rng.integers(0, nv, 300_000).astype(np.uint32)
+    small_d = rng.integers(0, nv, 400).astype(np.uint32)  # source 7: one work item at C = 16
+    other_s = rng.integers(8, nv, 60_000).astype(np.uint32)
+    other_d = rng.integers(0, nv, 60_000).astype(np.uint32)
+    bs = np.concatenate([np.zeros(hub_d.size, np.uint32), np.full(400, 7, np.uint32), other_s])
+    bd = np.concatenate([hub_d, small_d, other_d])
+    p = Pair(nv, C=16, pool_bytes=96 << 20, flags=gv.GV_WEIGHTED if weighted else 0)
+    try:
+        p.bulk(bs, bd)
+        p.check()
+        # queries: 12,000 on the hub (present and absent, repeated), 300 on source 7
+        qd = np.concatenate([hub_d[:6000], rng.integers(0, nv, 6000).astype(np.uint32), small_d[:150],
+                             rng.integers(0, nv, 150).astype(np.uint32)])
+        qs = np.concatenate([np.zeros(12000, np.uint32), np.full(300, 7, np.uint32)])
+        p.query(qs, qd)
+        # deletes: 11,000 distinct destinations on the hub (three slices), 300
+        # on source 7 (half present), plus scattered other pairs
+        dh = rng.choice(nv, size=11000, replace=False).astype(np.uint32)
+        d7 = np.concatenate([small_d[:150], rng.integers(0, nv, 150).astype(np.uint32)])
+        ds = np.concatenate([np.zeros(dh.size, np.uint32), np.full(300, 7, np.uint32), other_s[:5000]])
+        dd = np.concatenate([dh, d7, other_d[:5000]])
+        p.delete(ds, dd)
+        p.check()
+        p.query(qs, qd)
+        p.insert(np.zeros(5000, np.uint32), rng.integers(0, nv, 5000).astype(np.uint32))
+        p.delete(np.zeros(dh.size, np.uint32), dh)
+        p.check()
+    finally:
+        p.close()
+
+
+@pytest.mark.parametrize("C", [4, 16])
+def test_rmat_batches_atomic_grouping(C):
+    """Large batches through the per-pair atomic grouping (GV_ATOMIC_GROUPING)
+    give the same results as the oracle, like the radix-partition grouping."""
+    import paper_2306_08252_gb300 as gv
+    scale, nv = 12, 1 << 12
+    bs, bd = W.rmat_pairs(22, 0, 65536, scale)
+    p = Pair(nv, C=C, pool_bytes=64 << 20, flags=gv.GV_ATOMIC_GROUPING)
+    try:
+        p.bulk(bs, bd)
+        p.check()
+        for r, b in enumerate([5000, 20000]):
+            s, d = W.rmat_pairs(22, 100 + r, b, scale)
+            p.insert(s, d)
+            p.check()
+            qs, qd = W.rmat_queries(22, scale, 4000, s, d, r)
+            p.query(qs, qd)
+            p.delete(np.concatenate([s, bs[:1000]]), np.concatenate([d, bd[:1000]]))
+            p.check()
+    finally:
+        p.close()
+
+
 def test_queries_with_invalid_and_dead_ids():
     nv = 2000
     bs, bd = W.uniform_pairs(9, 0, 30000, nv)
