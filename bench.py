@@ -59,6 +59,11 @@ def parse():
                     help="rmat: the single-graph step (default); batched: many member graphs, "
                          "one captured launch sequence vs one launch sequence per graph")
     ap.add_argument("--graphs", type=int, default=256)
+    ap.add_argument("--scale", type=int, default=SCALE,
+                    help="RMAT scale of the graph (16 * 2^scale base edges); the default is the "
+                         "measured workload, smaller scales are for profiling captures")
+    ap.add_argument("--grouping", default="atomic", choices=["atomic", "radix"],
+                    help="grouping of large batches: one atomic per pair (default) or the radix partition")
     return ap.parse_args()
 
 
@@ -246,11 +251,14 @@ def byte_model(g, batch, qry, inserted, deleted, newblocks):
     entry of each touched source + 32 B per touched source + 4 B per freed
     block (entries moved by compaction are not counted: a lower bound).
 
-    Per kernel (its compulsory traffic): counting passes read the pairs and
-    write one rank per pair (12 B/pair); the touched scan reads the counter
-    array; scatters read pair + rank and write one 4-byte entry (16 B/pair);
-    mark kernels read every stored entry of the sources they own and their
-    batch entries (4 B each)."""
+    Per kernel (its compulsory traffic): the partition passes read the pairs
+    once (8 B/pair; the partitioned copy is grouping scratch); the grouping
+    by vertex writes one 4-byte batch-list entry per pair (deletes, queries;
+    for inserts the grouped destination); the insert's slot pass writes one
+    4-byte entry per inserted pair; mark kernels (thread-per-source, warp and
+    block-wide tiers) read every stored entry of the sources they own and
+    their batch entries (4 B each).  The per-pair atomic grouping (the
+    default) has its counting passes at 12 B/pair and scatters at 16 B/pair."""
     s, d = batch
     deg, _ = g.degrees()  # state after the insert = state the query and delete see
     nv = deg.size
@@ -265,25 +273,33 @@ def byte_model(g, batch, qry, inserted, deleted, newblocks):
 
     def tiers(src_ids, tiny_deg, tiny_nb):
         # thread-per-source tier: <= tiny_nb blocks, <= min(tiny_deg, tiny_nb*C)
-        # entries, <= 16 batch entries (deletes 128 / 8, queries 64 / 4)
+        # entries, <= 16 batch entries (deletes 128 / 8, queries 64 / 4); the
+        # others: warp tier up to 256 batch entries, block-wide tier above
         m = np.bincount(src_ids, minlength=nv)
         touched = m > 0
         nb = (deg64 + C - 1) // C
         tiny = touched & (deg64 > 0) & (deg64 <= min(tiny_deg, tiny_nb * C)) & (nb <= tiny_nb) & (m <= 16)
         big = touched & (deg64 > 0) & ~tiny
-        return (4 * int(deg64[big].sum()) + 4 * int(m[big].sum()),
-                4 * int(deg64[tiny].sum()) + 4 * int(m[tiny].sum()))
+        warp = big & (m <= 256)
+        cta = big & (m > 256)
+        f = lambda sel: 4 * int(deg64[sel].sum()) + 4 * int(m[sel].sum())
+        return f(warp), f(cta), f(tiny)
 
-    dmark, dtiny = tiers(s[ok], 128, 8)
+    dmark, dcta, dtiny = tiers(s[ok], 128, 8)
     qok = (qry[0] < nv) & (qry[1] < nv)
-    qmark, qtiny = tiers(qry[0][qok], 64, 4)
+    qmark, qcta, qtiny = tiers(qry[0][qok], 64, 4)
     scan = 4 * (1 << int(np.ceil(np.log2(max(nv, 1)))))
+    nq = int(qok.sum())
     kernels = {
+        "insert.partition": 8 * s.size, "insert.group": 4 * inserted, "insert.slots": 4 * inserted,
+        "delete.partition": 8 * s.size, "delete.group": 4 * int(ok.sum()),
+        "delete.mark": dmark, "delete.mark_cta": dcta, "delete.mark_tiny": dtiny,
+        "query.partition": 8 * qry[0].size, "query.group": 4 * nq,
+        "query.mark": qmark, "query.mark_cta": qcta, "query.mark_tiny": qtiny,
+        # per-pair atomic grouping (the default)
         "insert.count": 12 * s.size, "insert.touched": scan, "insert.scatter": 16 * inserted,
         "delete.count": 12 * s.size, "delete.touched": scan, "delete.scatter": 16 * s.size,
-        "delete.mark": dmark, "delete.mark_tiny": dtiny,
         "query.count": 12 * qry[0].size, "query.touched": scan, "query.scatter": 16 * qry[0].size,
-        "query.mark": qmark, "query.mark_tiny": qtiny,
     }
     return {"insert": ins_b, "query": qry_b, "delete": del_b, "step": ins_b + qry_b + del_b,
             "touched_sources": int(us.size), "kernels": kernels}
@@ -336,7 +352,8 @@ def run_ours(args, rank, world, local_rank):
     d_out = torch.zeros(args.queries, dtype=torch.uint8, device=dev)
     counts = torch.zeros(4, dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream()
-    g = gv.Graph(1 << SCALE, block_capacity=C, pool_bytes=POOL_BYTES)
+    g = gv.Graph(1 << SCALE, block_capacity=C, pool_bytes=POOL_BYTES,
+                 flags=gv.GV_RADIX_GROUPING if args.grouping == "radix" else 0)
     g.reserve(max(args.batch, BASE_EDGES))
     g.bulk_build(d_bs, d_bs.new_empty(0) if False else d_bd, counts[:2])
     g.sync()
@@ -1082,7 +1099,10 @@ def run_rows(args):
 
 
 def main():
+    global SCALE, BASE_EDGES
     args = parse()
+    if args.scale != SCALE:
+        SCALE, BASE_EDGES = args.scale, 16 << args.scale
     if args.workload == "rows":
         return run_rows(args)
     if args.workload == "batched":

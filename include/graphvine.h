@@ -94,11 +94,16 @@ typedef enum gv_status {
  * several repeated pairs a set-semantics batch keeps is not defined). */
 #define GV_WEIGHTED 4u
 /* Large batches (see dense_shift below) of plain inserts, deletes and
- * queries are grouped by source with a radix partition of the source ids
- * (no per-pair global atomic); with this flag they take the per-pair atomic
- * scheme instead (kept for comparison and as the path of dictionaries of
- * more than 2^24 vertices). */
-#define GV_ATOMIC_GROUPING 8u
+ * queries are grouped by source with one atomic per pair on the source's
+ * counter.  With this flag they are grouped instead by a radix partition of
+ * the source ids (no per-pair global atomic; dictionaries of at most 2^24
+ * vertices): the batch becomes contiguous per-source runs, inserts write
+ * each source's new entries as consecutive slots and deletes and queries
+ * test stored entries against the runs (sources of more than 256 and at
+ * most 4096 batch entries through a shared-memory hash set per CTA).  Same
+ * results; measured slower on the 10M-edge RMAT step (1.32 against 1.14
+ * ms), so not the default. */
+#define GV_RADIX_GROUPING 8u
 
 typedef struct gv_config {
     /* C, the number of edge entries per edge block (multiple of 4, 4..512).
@@ -106,7 +111,7 @@ typedef struct gv_config {
      * vertices with non-zero degree in the first edge batch, rounded up to a
      * multiple of 4; fixed from then on. */
     uint32_t block_capacity;
-    uint32_t flags;          /* GV_DEDUP | GV_GROW | GV_WEIGHTED | GV_ATOMIC_GROUPING, or 0 */
+    uint32_t flags;          /* GV_DEDUP | GV_GROW | GV_WEIGHTED | GV_RADIX_GROUPING, or 0 */
     /* Bytes reserved for the edge-block pool: block storage (4*C bytes per
      * block), tree links (8 bytes per block) and the edge queue (4 bytes per
      * block).  0 = half of the free device memory ("Edge Queue": at least
@@ -123,12 +128,11 @@ typedef struct gv_config {
      * warp handles per work item in deletes and queries (1 .. min(32, 512/C);
      * default the maximum) -- fewer blocks put more warps on a long
      * adjacency.  dense_shift: batches of n pairs with n >= vertices >> s
-     * (dictionary capacity) are grouped by a radix partition of the source
-     * ids (bucket by the high bits, then a counting sort of each chunk of a
-     * bucket by the low bits) plus a pass over all vertices -- or, with
-     * GV_ATOMIC_GROUPING, set semantics or graph sets, one atomic per pair
-     * plus that pass -- smaller ones with per-tile aggregation (default
-     * s = 3). */
+     * (dictionary capacity) are grouped with one atomic per pair plus a pass
+     * over all vertices (or, with GV_RADIX_GROUPING, by a radix partition of
+     * the source ids: buckets by the high bits, then a counting sort of each
+     * chunk of a bucket by the low bits), smaller ones with per-tile
+     * aggregation (default s = 3). */
     uint32_t item_blocks;
     uint32_t dense_shift;
     uint32_t reserved;

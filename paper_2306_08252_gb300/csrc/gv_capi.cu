@@ -128,9 +128,10 @@ struct gv_graph {
     unsigned long long *pr_off = nullptr, *pr_part = nullptr;
     // grouped path of large batches: partitioned pairs, per-CTA bucket
     // counts, bucket totals and bases, chunk list, block-wide tier groups
-    unsigned long long gp_ncap = 0, gp_acap = 0, gp_hcap = 0, gp_ccap = 0, gp_icap = 0;
+    unsigned long long gp_ncap = 0, gp_acap = 0, gp_hcap = 0, gp_ccap = 0, gp_icap = 0, gp_rcap = 0, go_cap = 0;
     uint32_t *gp_src = nullptr, *gp_dst = nullptr, *gp_aux = nullptr, *gp_hist = nullptr;
-    uint32_t *gp_btot = nullptr, *gp_bbase = nullptr;
+    uint32_t *gp_btot = nullptr, *gp_bbase = nullptr, *gp_mbkt = nullptr, *gp_rows = nullptr;
+    uint32_t *go_src = nullptr, *go_dst = nullptr, *go_aux = nullptr;
     uint4 *gp_chunks = nullptr;
     uint2 *grp_items = nullptr;
     // graph set: members' vertex ranges (set_G == 0 for a plain graph)
@@ -521,9 +522,9 @@ gv_status ensure_batch(gv_graph *g, uint64_t n, int mode) {
 
 // Does a plain batch call of n pairs take the grouped path?  Large batches
 // (the dense threshold) on dictionaries of at most GP_BMAX * GP_WMAX
-// vertices, unless the graph asked for the per-pair atomic grouping.
+// vertices, when the graph asked for the radix-partition grouping.
 bool use_grouped(const gv_graph *g, uint64_t n) {
-    if (g->flags & GV_ATOMIC_GROUPING) return false;
+    if (!(g->flags & GV_RADIX_GROUPING)) return false;
     if (g->set_G || g->C == 0 || n == 0) return false;
     if ((unsigned long long)g->vcap > (unsigned long long)gv::GP_BMAX * gv::GP_WMAX) return false;
     return n >= ((unsigned long long)g->nv >> g->dense_shift);
@@ -540,8 +541,9 @@ gv_status grow_buf(T **p, unsigned long long *cap, unsigned long long need, uint
     return GV_OK;
 }
 
-// Scratch of a grouped call of n pairs (aux: a word per pair travels with it).
-gv_status ensure_group(gv_graph *g, uint64_t n, bool aux, unsigned long long items) {
+// Scratch of a grouped call of n pairs (aux: a word per pair travels with
+// it; out: the insert's grouped copy; items: block-wide tier groups).
+gv_status ensure_group(gv_graph *g, uint64_t n, bool aux, bool out, unsigned long long items) {
     uint32_t ctas = 0;
     unsigned long long len = 0;
     gv::group_shape(n, g->num_sms, &ctas, &len);
@@ -555,10 +557,31 @@ gv_status ensure_group(gv_graph *g, uint64_t n, bool aux, unsigned long long ite
         g->gp_ncap = c;
     }
     if (aux) GV_TRY(grow_buf(&g->gp_aux, &g->gp_acap, n, &g->scratch_bytes));
+    if (out && (n > g->go_cap || !g->go_cap)) {
+        const unsigned long long c = std::max<unsigned long long>(n, std::max<unsigned long long>(2 * g->go_cap, 4096));
+        dfree(g->go_src);
+        dfree(g->go_dst);
+        dfree(g->go_aux);
+        g->go_cap = 0;
+        GV_TRY(dalloc(&g->go_src, c, &g->scratch_bytes));
+        GV_TRY(dalloc(&g->go_dst, c, &g->scratch_bytes));
+        GV_TRY(dalloc(&g->go_aux, c, &g->scratch_bytes));
+        g->go_cap = c;
+    }
     GV_TRY(grow_buf(&g->gp_hist, &g->gp_hcap, (unsigned long long)ctas * gv::GP_BMAX, &g->scratch_bytes));
     GV_TRY(grow_buf(&g->gp_chunks, &g->gp_ccap, n / gv::GP_CHUNK + gv::GP_BMAX + 1, &g->scratch_bytes));
+    // rows: one per chunk of a bucket of several chunks (at most 2n /
+    // GP_CHUNK), W words each; sized for every batch of at most n pairs
+    // (smaller batches have fewer buckets, so longer rows)
+    unsigned long long rw = 0;
+    for (unsigned long long m = n; m > 0; m /= 2) {
+        const unsigned long long wm = 1ull << gv::group_bucket_shift(m, g->vcap);  // vertices per bucket
+        rw = std::max<unsigned long long>(rw, (2 * (m / gv::GP_CHUNK) + 2) * wm);
+    }
+    GV_TRY(grow_buf(&g->gp_rows, &g->gp_rcap, rw, &g->scratch_bytes));
     if (!g->gp_btot) GV_TRY(dalloc(&g->gp_btot, gv::GP_BMAX, &g->scratch_bytes));
     if (!g->gp_bbase) GV_TRY(dalloc(&g->gp_bbase, gv::GP_BMAX, &g->scratch_bytes));
+    if (!g->gp_mbkt) GV_TRY(dalloc(&g->gp_mbkt, gv::GP_BMAX, &g->scratch_bytes));
     if (items) GV_TRY(grow_buf(&g->grp_items, &g->gp_icap, items, &g->scratch_bytes));
     return GV_OK;
 }
@@ -567,10 +590,8 @@ gv_status ensure_group(gv_graph *g, uint64_t n, bool aux, unsigned long long ite
 GraphView grouped_view(const gv_graph *g, uint64_t n) {
     GraphView v = view(g);
     v.grouped = 1;
-    uint32_t sh = 0;
-    while ((g->vcap >> sh) > gv::GP_BMAX) ++sh;
-    v.gb_shift = sh;
-    v.gb_n = g->vcap >> sh;
+    v.gb_shift = gv::group_bucket_shift(n, g->vcap);
+    v.gb_n = g->vcap >> v.gb_shift;
     gv::group_shape(n, g->num_sms, &v.gp_ctas, &v.gp_len);
     v.gp_src = g->gp_src;
     v.gp_dst = g->gp_dst;
@@ -579,8 +600,15 @@ GraphView grouped_view(const gv_graph *g, uint64_t n) {
     v.gp_btot = g->gp_btot;
     v.gp_bbase = g->gp_bbase;
     v.gp_chunks = g->gp_chunks;
+    v.gp_mbkt = g->gp_mbkt;
+    v.gp_rows = g->gp_rows;
+    v.go_src = g->go_src;
+    v.go_dst = g->go_dst;
+    v.go_aux = g->go_aux;
     v.gcur = g->vtid;  // the touched-index array is free during a grouped call
     v.grp_items = g->grp_items;
+    v.grp_cap = g->gp_icap;
+    v.hbase = (uint32_t)((n + 63) / 64 * 64);  // deletes, queries: batch lists below, hash sets above
     return v;
 }
 
@@ -869,7 +897,7 @@ gv_status insert_impl(gv_graph *g, const uint32_t *src, const uint32_t *dst, uin
             int set = -1;
             const bool small = n <= gv::small_insert_max();
             const bool grp = !small && use_grouped(g, n);
-            if (grp) GV_TRY(ensure_group(g, n, g->wdata != nullptr, 0));
+            if (grp) GV_TRY(ensure_group(g, n, g->wdata != nullptr, true, 0));
             const GraphView v = grp ? grouped_view(g, n) : view(g);
             GV_TRY(stage_batch(g, v, gv::MODE_INSERT, src, dst, wts, n, s, !small, &dsrc, &ddst, &dwts, &set));
             if (small)
@@ -937,7 +965,7 @@ gv_status member_impl(gv_graph *g, int mode, const uint32_t *src, const uint32_t
     const bool grp = use_grouped(g, n);
     if (grp) {
         const unsigned long long touched = std::min<unsigned long long>(n, g->nv ? g->nv : 1);
-        GV_TRY(ensure_group(g, n, mode == gv::MODE_QUERY, item_bound(g, touched)));
+        GV_TRY(ensure_group(g, n, mode == gv::MODE_QUERY, false, item_bound(g, touched)));
     }
     const GraphView v = grp ? grouped_view(g, n) : view(g);
     int set = -1;
@@ -1029,7 +1057,7 @@ gv_status gv_create(const gv_config *cfg, uint32_t num_vertices, void *stream, g
     if (cfg) c = *cfg;
     if (c.block_capacity != 0 && (c.block_capacity < 4 || c.block_capacity > 512 || c.block_capacity % 4))
         return GV_ERR_INVALID_ARG;
-    if (c.flags & ~(GV_DEDUP | GV_GROW | GV_WEIGHTED | GV_ATOMIC_GROUPING)) return GV_ERR_INVALID_ARG;
+    if (c.flags & ~(GV_DEDUP | GV_GROW | GV_WEIGHTED | GV_RADIX_GROUPING)) return GV_ERR_INVALID_ARG;
     // which of several repeated (u, v) a set-semantics batch keeps is not
     // defined, so their payloads would be: the two flags exclude each other
     if ((c.flags & GV_DEDUP) && (c.flags & GV_WEIGHTED)) return GV_ERR_INVALID_ARG;
@@ -1130,6 +1158,7 @@ gv_status gv_destroy(gv_graph *g) {
         dfree(g->pr_cursor); dfree(g->pr_src); dfree(g->pr_dst); dfree(g->pr_off); dfree(g->pr_part);
         dfree(g->gp_src); dfree(g->gp_dst); dfree(g->gp_aux); dfree(g->gp_hist);
         dfree(g->gp_btot); dfree(g->gp_bbase); dfree(g->gp_chunks); dfree(g->grp_items);
+        dfree(g->gp_mbkt); dfree(g->gp_rows); dfree(g->go_src); dfree(g->go_dst); dfree(g->go_aux);
         for (auto &b : g->stage.buf) dfree(b.p);
         for (auto &r : g->prof.recs) {
             cudaEventDestroy(r.a);
@@ -1270,6 +1299,9 @@ gv_status gv_reserve(gv_graph *g, uint64_t max_batch) {
     GV_TRY(ensure_touched(g, std::min<unsigned long long>(max_batch, g->nv ? g->nv : 1)));
     GV_TRY(ensure_owner(g, (g->C ? max_batch / g->C : max_batch) + std::min<unsigned long long>(max_batch, g->nv) + 1));
     if (g->C) GV_TRY(ensure_items(g, item_bound(g, std::min<unsigned long long>(max_batch, g->nv ? g->nv : 1))));
+    if ((g->flags & GV_RADIX_GROUPING) && !g->set_G && max_batch > 0)
+        GV_TRY(ensure_group(g, max_batch, true, true,
+                            g->C ? item_bound(g, std::min<unsigned long long>(max_batch, g->nv ? g->nv : 1)) : 0));
     GV_TRY(ensure_arena(g, 5 * max_batch + 128, true, max_batch));
     GV_TRY(ensure_ranks(g, max_batch));
     if (g->set_G && (max_batch > g->scap || !g->scap)) {
@@ -1904,9 +1936,9 @@ static const char *kPhaseNames[gv::PH_COUNT] = {
     "query.count",    "query.touched",  "query.plan",      "query.arena",      "query.scatter",
     "query.mark",     "query.mark_tiny", "query.out",      "query.finalize",
     "vertex_delete",  "neighbors",      "other",          "analytics",      "insert.small",
-    "insert.partition", "insert.vertex_count", "insert.place",
-    "delete.partition", "delete.vertex_count", "delete.place", "delete.mark_cta",
-    "query.partition",  "query.vertex_count",  "query.place",  "query.mark_cta"};
+    "insert.partition", "insert.group", "insert.slots",
+    "delete.partition", "delete.group", "delete.mark_cta",
+    "query.partition",  "query.group",  "query.mark_cta"};
 
 uint32_t gv_profile_num_phases(void) { return gv::PH_COUNT; }
 

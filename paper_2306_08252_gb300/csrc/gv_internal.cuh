@@ -52,6 +52,9 @@ struct Dev {
     // work groups of the block-wide membership tier
     unsigned int n_chunks;
     unsigned int n_groups;
+    unsigned int n_mbuckets;        // buckets of more than one chunk
+    unsigned int n_grouped;         // valid pairs of the grouped batch
+    unsigned int n_hash;            // grouped path: sources whose batch keys go to an arena hash set
 };
 
 // Everything a kernel needs to know about one graph (passed by value).
@@ -116,28 +119,36 @@ struct GraphView {
     uint32_t gb_shift;          // log2(vertices per bucket)
     uint32_t gb_n;              // buckets (vcap >> gb_shift)
     uint32_t gp_ctas;           // CTAs of the partition passes
-    unsigned long long gp_len;  // pairs per partition CTA (a multiple of 1024)
+    unsigned long long gp_len;  // pairs per partition CTA (a multiple of GP_TILE)
     uint32_t *gp_src;           // partitioned pairs, bucket by bucket
     uint32_t *gp_dst;
     uint32_t *gp_aux;           // query: original index; weighted insert: payload
     uint32_t *gp_hist;          // [gp_ctas][gb_n]: counts, then prefixes over the CTAs
     uint32_t *gp_btot;          // [gb_n] valid pairs per bucket
     uint32_t *gp_bbase;         // [gb_n] first partitioned position of each bucket
-    uint4 *gp_chunks;           // {start, length, bucket, -} per chunk
-    uint32_t *gcur;             // per vertex: its segment start, advanced by the placement
-    uint2 *grp_items;           // block-wide membership tier: {touched index, first item}
+    uint4 *gp_chunks;           // {start, length, bucket, row of a multi-chunk bucket's chunk or NIL}
+    uint32_t *gp_mbkt;          // buckets of more than one chunk
+    uint32_t *gp_rows;          // [row][vertex of the bucket]: a chunk's offset in each vertex's segment
+    uint32_t *go_src;           // insert: the grouped pairs (source order)
+    uint32_t *go_dst;
+    uint32_t *go_aux;
+    uint32_t *gcur;             // per vertex: start of its segment in the grouped order
+    uint2 *grp_items;           // block-wide membership tier: {touched index, first item} from
+                                // the bottom; hash-set sources {touched index, -} from the top
+    unsigned long long grp_cap; // entries of grp_items
 };
 
 // Grouped path limits and sizes.
-constexpr uint32_t GP_BMAX = 4096;     // buckets at most (shared counters of a partition CTA)
-constexpr uint32_t GP_WMAX = 4096;     // vertices per bucket at most (shared counters of a chunk CTA)
-constexpr uint32_t GP_CHUNK = 4096;    // pairs per chunk
+constexpr uint32_t GP_BMAX = 4096;     // buckets at most
+constexpr uint32_t GP_WMAX = 4096;     // vertices per bucket at most
+constexpr uint32_t GP_TILE = 4096;     // pairs per tile of a partition CTA
+constexpr uint32_t GP_CHUNK = 4096;    // pairs per chunk of a bucket
 constexpr uint32_t GP_THREADS = 512;   // threads of the partition and chunk CTAs
-constexpr uint32_t GP_VPC = 4096;      // vertices per CTA of the per-vertex scan (>= GP_WMAX)
+constexpr uint32_t GP_MAXCTAS = 1024;  // partition CTAs at most (rows of the column scan)
 // Sources with more batch entries than LIST_MAX go to the block-wide
 // membership tier: CT_GI work items per CTA share one shared-memory hash set
 // of the source's batch entries, built CT_KEYS keys at a time.
-constexpr uint32_t CT_GI = 8;
+constexpr uint32_t CT_GI = 8;          // items per group = warps per CTA
 constexpr uint32_t CT_SLOTS = 8192;
 constexpr uint32_t CT_KEYS = CT_SLOTS / 2;
 constexpr uint32_t CT_FLAG = 0xFFFFFFFFu;  // t_a[t].z of a block-wide-tier source
@@ -398,6 +409,53 @@ __device__ __forceinline__ uint32_t hash_find(const uint32_t *tab, uint32_t hsiz
         if (cur == v) return h;
         if (cur == EMPTY_KEY) return NIL;
         h = (h + 1) & (hsize - 1);
+    }
+    return NIL;
+}
+
+// Bucketed hash set of nbk buckets of HB words at tab (occupied slots are a
+// prefix of each bucket): insert v, returning its word index in tab (NIL if
+// the table is full, which sizing at twice the keys rules out).  Each pass
+// ends, moves to the next bucket, or rereads after losing a slot to another
+// insert (which filled that slot): (HB + 1) * nbk passes bound the loop.
+__device__ __forceinline__ uint32_t bucket_insert(uint32_t *tab, uint32_t nbk, uint32_t v) {
+    uint32_t b = hidx(v, nbk);
+    for (uint32_t probe = 0; probe < (HB + 1) * nbk; ++probe) {
+        const uint4 *bp = reinterpret_cast<const uint4 *>(tab + b * HB);
+        const uint4 x0 = __ldcg(bp), x1 = __ldcg(bp + 1);
+        const uint32_t w[HB] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+        uint32_t hit = NIL, empty = NIL;
+#pragma unroll
+        for (uint32_t k = 0; k < HB; ++k) {
+            if (hit == NIL && w[k] == v) hit = k;
+            if (empty == NIL && w[k] == EMPTY_KEY) empty = k;
+        }
+        if (hit != NIL) return b * HB + hit;
+        if (empty != NIL) {
+            const uint32_t old = atomicCAS(&tab[b * HB + empty], EMPTY_KEY, v);
+            if (old == EMPTY_KEY || old == v) return b * HB + empty;
+        } else {
+            b = (b + 1) & (nbk - 1);
+        }
+    }
+    return NIL;
+}
+
+// Word index of v in the bucketed hash set (NIL if absent).
+__device__ __forceinline__ uint32_t bucket_find(const uint32_t *tab, uint32_t nbk, uint32_t v) {
+    uint32_t b = hidx(v, nbk);
+    for (uint32_t step = 0; step < nbk; ++step) {
+        const uint4 *bp = reinterpret_cast<const uint4 *>(tab + b * HB);
+        const uint4 x0 = __ldcg(bp), x1 = __ldcg(bp + 1);
+        const uint32_t w[HB] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+        for (uint32_t k = 0; k < HB; ++k)
+            if (w[k] == v) return b * HB + k;
+        if (w[HB - 1] != EMPTY_KEY) {
+            b = (b + 1) & (nbk - 1);
+            continue;
+        }
+        return NIL;  // the bucket's prefix ended without v
     }
     return NIL;
 }

@@ -490,6 +490,7 @@ __global__ void __launch_bounds__(256) k_finalize_insert(GraphView g, unsigned l
         dev->harena_used = 0;
         dev->n_chunks = 0;
         dev->n_groups = 0;
+        dev->n_hash = 0;
         dev->free_total = 0;
         dev->abort = 0;
         dev->done_ctas = 0;
@@ -1566,6 +1567,7 @@ __global__ void __launch_bounds__(256) k_finalize_member(GraphView g, unsigned l
         dev->harena_used = 0;
         dev->n_chunks = 0;
         dev->n_groups = 0;
+        dev->n_hash = 0;
         dev->free_total = 0;
         dev->abort = 0;
         dev->done_ctas = 0;
@@ -1729,6 +1731,7 @@ __global__ void __launch_bounds__(256) k_finalize_vdel(GraphView g, const uint32
         dev->harena_used = 0;
         dev->n_chunks = 0;
         dev->n_groups = 0;
+        dev->n_hash = 0;
         dev->free_total = 0;
         dev->abort = 0;
         dev->done_ctas = 0;
@@ -1999,6 +2002,7 @@ static void member_tail(const GraphView &g0, const uint32_t *src, const uint32_t
     const bool del = MODE == MODE_DELETE;
     if (g.grouped) {
         // the grouping already placed every source's batch list in the arena
+        // (and filled the hash sets of sources past CT_KEYS batch entries)
         PhaseScope ps(lc, del ? PH_DEL_PLAN : PH_QRY_PLAN);
         launch_gp_plan_member(MODE, g, gt, lc);
     } else {
@@ -2033,7 +2037,10 @@ static void member_tail(const GraphView &g0, const uint32_t *src, const uint32_t
     }
     // sources with more than LIST_MAX batch entries (grouped path only):
     // disjoint from the warp tier's sources
-    if (g.grouped) launch_mark_cta(MODE, g, nt, lc);
+    if (g.grouped) {
+        launch_mark_cta(MODE, g, nt, lc);
+        if (!del) launch_gp_hash_found(g, lc);
+    }
     if (!fork) {
         PhaseScope ps(lc, del ? PH_DEL_MARK_TINY : PH_QRY_MARK_TINY);
         launch_pdl(k_mark_tiny<MODE>, gt, 256, 0, lc.stream, g);

@@ -17,11 +17,11 @@ enum Phase : int {
     PH_QRY_COUNT, PH_QRY_TOUCHED, PH_QRY_PLAN, PH_QRY_ARENA, PH_QRY_SCATTER, PH_QRY_MARK, PH_QRY_MARK_TINY,
     PH_QRY_OUT, PH_QRY_FINALIZE,
     PH_VDEL, PH_NEIGHBORS, PH_OTHER, PH_ANALYTICS, PH_INS_SMALL,
-    // grouped path of large batches: radix partition by source, per-vertex
-    // counts and segment starts, placement of each chunk's runs
-    PH_INS_PART, PH_INS_VCOUNT, PH_INS_PLACE,
-    PH_DEL_PART, PH_DEL_VCOUNT, PH_DEL_PLACE, PH_DEL_MARK_CTA,
-    PH_QRY_PART, PH_QRY_VCOUNT, PH_QRY_PLACE, PH_QRY_MARK_CTA,
+    // grouped path of large batches: radix partition by source, grouping of
+    // each bucket by vertex, the insert's slot pass, the block-wide tier
+    PH_INS_PART, PH_INS_GROUP, PH_INS_SLOTS,
+    PH_DEL_PART, PH_DEL_GROUP, PH_DEL_MARK_CTA,
+    PH_QRY_PART, PH_QRY_GROUP, PH_QRY_MARK_CTA,
     PH_COUNT
 };
 
@@ -137,9 +137,11 @@ cudaError_t launch_member_tail(int mode, const GraphView &g, const uint32_t *src
 // per-bucket counts of the partition CTAs whose ranges lie in pairs [lo, hi)
 // (lo a multiple of the range, hi one or n).  launch_group_finish: the rest
 // of the grouping once every pair has landed (and, for deletes and queries,
-// the placement of the batch lists).  launch_group_place: the placement
-// (inserts: straight into the slots, after the plan and the links).
+// the batch lists of deletes and queries).  launch_group_place: the insert's
+// slot pass over the grouped pairs (after the plan and the links).
 void group_shape(unsigned long long n, int num_sms, uint32_t *ctas, unsigned long long *len);
+// log2 of the vertices per bucket of the partition for n pairs, dictionary vcap.
+uint32_t group_bucket_shift(unsigned long long n, uint32_t vcap);
 cudaError_t launch_group_hist(int mode, const GraphView &g, const uint32_t *src, const uint32_t *dst,
                               unsigned long long n, unsigned long long lo, unsigned long long hi,
                               const LaunchCfg &lc);
@@ -149,6 +151,9 @@ cudaError_t launch_group_place(int mode, const GraphView &g, unsigned long long 
 cudaError_t launch_gp_plan_insert(const GraphView &g, int grid, const LaunchCfg &lc);
 cudaError_t launch_gp_plan_member(int mode, const GraphView &g, int grid, const LaunchCfg &lc);
 cudaError_t launch_mark_cta(int mode, const GraphView &g, unsigned long long nt, const LaunchCfg &lc);
+// Grouped queries: the hits of the sources past CT_KEYS batch entries (found
+// in their arena hash sets) copied back to their list entries.
+cudaError_t launch_gp_hash_found(const GraphView &g, const LaunchCfg &lc);
 // Vertex delete: mark dead, free own blocks, remove incoming edges, finalize.
 cudaError_t launch_vertex_delete(const GraphView &g, const uint32_t *ids, uint32_t k,
                                  const LaunchCfg &lc);

@@ -25,7 +25,7 @@ GV_ERR_STATE = 5
 GV_DEDUP = 1
 GV_GROW = 2
 GV_WEIGHTED = 4
-GV_ATOMIC_GROUPING = 8
+GV_RADIX_GROUPING = 8
 GV_REBLOCK_MIN_FOOTPRINT = 1  # gv_reblock: the block size of least pool footprint
 
 c_u32, c_u64, c_vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p

@@ -41,8 +41,27 @@ def test_byte_model_closed_forms():
     assert k["insert.count"] == 12 * src.size and k["insert.scatter"] == 16 * 27
     assert k["delete.scatter"] == 16 * src.size and k["query.scatter"] == 16 * qs.size
     assert k["insert.touched"] == 4 * 64  # the counter array of the dictionary's capacity
+    # grouped path: pairs read once by the partition, one entry per placed pair
+    assert k["insert.partition"] == 8 * src.size and k["query.partition"] == 8 * qs.size
+    assert k["insert.slots"] == 4 * 27 and k["delete.group"] == 4 * int(valid.sum())
+    assert k["query.group"] == 4 * int(((qs < 64) & (qd < 64)).sum())
+    assert k["delete.mark_cta"] == 0 and k["query.mark_cta"] == 0  # no source past 256 batch entries
     assert m["step"] == m["insert"] + m["query"] + m["delete"]
     assert C == 16
+
+
+def test_byte_model_block_wide_tier():
+    deg = np.zeros(32, dtype=np.int64)
+    deg[4] = 1000
+    deg[5] = 600
+    src = np.array([4] * 300 + [5] * 100, dtype=np.uint32)
+    dst = np.arange(400, dtype=np.uint32) % 32
+    m = bench.byte_model(_fake_graph(deg), (src, dst), (src[:10], dst[:10]), inserted=400, deleted=400,
+                         newblocks=0)
+    k = m["kernels"]
+    assert k["delete.mark_cta"] == 4 * 1000 + 4 * 300   # source 4: 300 batch entries
+    assert k["delete.mark"] == 4 * 600 + 4 * 100        # source 5: 100
+    assert k["delete.mark_tiny"] == 0
 
 
 def test_whole_job_rate_and_config():

@@ -21,8 +21,9 @@ def _pairs(rng, n, nv, hub_frac=0.3):
     return s, d
 
 
+# flags: 1 set semantics, 2 pool growth, 4 weighted, 8 radix-partition grouping
 @pytest.mark.parametrize("seed,C,flags", [(1, 4, 0), (2, 8, 0), (3, 16, 1), (4, 12, 2), (5, 32, 3), (6, 0, 0),
-                                          (7, 8, 4), (8, 20, 6)])
+                                          (7, 8, 4), (8, 20, 6), (9, 16, 8), (10, 4, 12), (11, 0, 10)])
 def test_random_operation_sequences(seed, C, flags):
     import torch
     import paper_2306_08252_gb300 as gv

@@ -14,9 +14,11 @@ from gpu_util import Pair, canon, dev_u32
 pytestmark = pytest.mark.gpu
 
 
-def test_tiny_uniform_config_every_batch():
+@pytest.mark.parametrize("radix", [False, True])
+def test_tiny_uniform_config_every_batch(radix):
+    import paper_2306_08252_gb300 as gv
     cfg = W.tiny_uniform()
-    p = Pair(cfg["nv"], C=cfg["block_capacity"], pool_bytes=32 << 20)
+    p = Pair(cfg["nv"], C=cfg["block_capacity"], pool_bytes=32 << 20, flags=gv.GV_RADIX_GROUPING if radix else 0)
     try:
         p.bulk(*cfg["bulk"])
         p.check()
@@ -127,7 +129,7 @@ def test_hub_batch_lists_past_one_shared_slice(weighted):
     other_d = rng.integers(0, nv, 60_000).astype(np.uint32)
     bs = np.concatenate([np.zeros(hub_d.size, np.uint32), np.full(400, 7, np.uint32), other_s])
     bd = np.concatenate([hub_d, small_d, other_d])
-    p = Pair(nv, C=16, pool_bytes=96 << 20, flags=gv.GV_WEIGHTED if weighted else 0)
+    p = Pair(nv, C=16, pool_bytes=96 << 20, flags=(gv.GV_WEIGHTED if weighted else 0) | gv.GV_RADIX_GROUPING)
     try:
         p.bulk(bs, bd)
         p.check()
@@ -152,14 +154,14 @@ def test_hub_batch_lists_past_one_shared_slice(weighted):
         p.close()
 
 
-@pytest.mark.parametrize("C", [4, 16])
-def test_rmat_batches_atomic_grouping(C):
-    """Large batches through the per-pair atomic grouping (GV_ATOMIC_GROUPING)
-    give the same results as the oracle, like the radix-partition grouping."""
+@pytest.mark.parametrize("C", [4, 16, 0])
+def test_rmat_batches_radix_grouping(C):
+    """Large batches through the radix-partition grouping (GV_RADIX_GROUPING)
+    give the oracle's results, like the per-pair atomic grouping."""
     import paper_2306_08252_gb300 as gv
     scale, nv = 12, 1 << 12
     bs, bd = W.rmat_pairs(22, 0, 65536, scale)
-    p = Pair(nv, C=C, pool_bytes=64 << 20, flags=gv.GV_ATOMIC_GROUPING)
+    p = Pair(nv, C=C, pool_bytes=64 << 20, flags=gv.GV_RADIX_GROUPING)
     try:
         p.bulk(bs, bd)
         p.check()
@@ -350,13 +352,16 @@ def test_er_mixed_scaled():
         p.close()
 
 
-def test_rmat_full_size_sampled():
+@pytest.mark.parametrize("radix", [False, True])
+def test_rmat_full_size_sampled(radix):
     """RMAT 2^20 vertices, 16M edges, the 10M insert / 1M query / 10M delete
-    step in the benchmark's launch configuration; every degree and query bit,
-    sampled neighbour lists (top hubs and random vertices)."""
+    step in the benchmark's launch configuration (and through the radix-
+    partition grouping); every degree and query bit, sampled neighbour lists
+    (top hubs and random vertices)."""
+    import paper_2306_08252_gb300 as gv
     scale = 20
     bs, bd = W.rmat_graph(2, scale, 1 << 24)
-    p = Pair(1 << scale, C=16, pool_bytes=1 << 30)
+    p = Pair(1 << scale, C=16, pool_bytes=1 << 30, flags=gv.GV_RADIX_GROUPING if radix else 0)
     try:
         p.bulk(bs, bd)
         p.check(full=False)
