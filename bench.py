@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay of the step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the short batched-form record")
+    ap.add_argument("--no-serving", action="store_true", help="skip the short serving record")
     ap.add_argument("--requests", type=int, default=10_000)
     ap.add_argument("--serve-scale", type=int, default=24)
     ap.add_argument("--workload", default="rmat", choices=["rmat", "batched", "serving", "rows"],
@@ -453,6 +455,43 @@ def run_ours(args, rank, world, local_rank):
                  "timer": "CUDA events around each replay of the captured step"}
         del cg
 
+    # ---------------- the compaction-heavy delete: the first delete of the
+    # batch on a freshly built graph (bulk build + the insert) also removes
+    # the base graph's copies of batch pairs, spread through the adjacencies,
+    # so compaction moves many entries (the steady-state step deletes only
+    # the entries its own insert appended, at the adjacency tails)
+    heavy_ms, heavy_phases, heavy_deleted = [], {}, 0
+    for r in range(3):
+        g2 = gv.Graph(1 << SCALE, block_capacity=C, pool_bytes=POOL_BYTES,
+                      flags=gv.GV_RADIX_GROUPING if args.grouping == "radix" else 0)
+        g2.reserve(max(args.batch, BASE_EDGES))
+        g2.bulk_build(d_bs, d_bd)
+        g2.insert_edges(d_s, d_d)
+        if r == 2:
+            g2.profile_read()
+            g2.profile(True)
+        flush.fill_(r & 0xFF)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g2.delete_edges(d_s, d_d, counts[2:])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        heavy_deleted = int(counts[2].item())
+        if r == 2:
+            g2.profile(False)
+            heavy_phases = {k: v[0] for k, v in g2.profile_read().items() if v[1] and k.startswith("delete.")}
+        else:
+            heavy_ms.append(e0.elapsed_time(e1))
+        assert g2.sync() == 0
+        g2.close()
+    heavy = {"ms": statistics.median(heavy_ms), "deleted": heavy_deleted,
+             "value": heavy_deleted / (statistics.median(heavy_ms) / 1e3), "unit": UNIT,
+             "phases_ms": heavy_phases,
+             "workload": f"delete the {args.batch}-edge batch once, right after the bulk build and its insert "
+                         "(every stored copy of a batch pair goes, base-graph copies included)",
+             "timer": "CUDA events around the call; median of 2, phases from a third with per-kernel events"}
+
     # ---------------- end to end: host (pinned) inputs and outputs, through the C ABI
     e2e = None
     if not args.no_e2e:
@@ -532,12 +571,28 @@ def run_ours(args, rank, world, local_rank):
         "e2e": e2e,
         "graph_replay": graph,
         "counts_per_step": {"inserted": inserted, "deleted": deleted},
+        "latency": {"p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+                    "max_ms": float(max(step_ms)), "samples": len(step_ms),
+                    "of": "one step (the 10M insert, 1M queries, 10M delete), device time per step"},
+        "p50_ms": float(np.percentile(step_ms, 50)),
+        "p99_ms": float(np.percentile(step_ms, 99)),
+        "delete_compaction_heavy": heavy,
     }
     g.close()
     return res, (base, upd, qry)
 
 
 def run_batched(args):
+    print(json.dumps(batched_record(args.graphs, args.steps, args.warmup, tune=True)), flush=True)
+    return 0
+
+
+# configuration of the short batched record in the default line (the
+# autotuner's usual pick for this workload; --workload batched tunes)
+BATCHED_FIXED = {"block_capacity": 16, "item_blocks": 16, "dense_shift": 3}
+
+
+def batched_record(graphs, steps, warmup, tune=True):
     """Many independent RMAT graphs (member sizes log-uniform in 2^10..2^18,
     average degree 8, batches log-uniform in 1..1M): one graph set whose
     insert + delete for all members is captured in one CUDA graph, against
@@ -550,8 +605,11 @@ def run_batched(args):
     from paper_2306_08252_gb300 import autotune
 
     torch.cuda.set_device(0)
-    members = W.batched_rmat(seed=4, graphs=args.graphs)
-    tuned = autotune.tune_set(members, log=lambda m: print(m, file=sys.stderr))
+    members = W.batched_rmat(seed=4, graphs=graphs)
+    if tune:
+        tuned = autotune.tune_set(members, log=lambda m: print(m, file=sys.stderr))
+    else:
+        tuned = dict(BATCHED_FIXED, cached=False)
     C, IBk, DS = tuned["block_capacity"], tuned["item_blocks"], tuned["dense_shift"]
     dev = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).view(dt)).cuda()
     bs, bd, bo = autotune.concat_member_batches(members, "bulk")
@@ -586,12 +644,12 @@ def run_batched(args):
         gs.delete_edges(*b, cd)
     with torch.cuda.graph(rest_g, capture_error_mode="relaxed"):
         gs.delete_edges(*a, cr)
-    for _ in range(max(args.warmup, 1)):
+    for _ in range(max(warmup, 1)):
         step_g.replay()
         rest_g.replay()
     torch.cuda.synchronize()
     t_b = 0.0
-    for i in range(args.steps):
+    for i in range(steps):
         flush.fill_(i & 0xFF)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -624,12 +682,12 @@ def run_batched(args):
                 g.insert_edges(s_, d_, pc[2 * i:2 * i + 2])
                 g.delete_edges(s2, d2, pd[2 * i:2 * i + 2])
 
-    for _ in range(max(args.warmup, 1)):
+    for _ in range(max(warmup, 1)):
         plain_step(False)
         plain_step(True)
     torch.cuda.synchronize()
     t_p = 0.0
-    for i in range(args.steps):
+    for i in range(steps):
         flush.fill_(i & 0xFF)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -644,11 +702,11 @@ def run_batched(args):
             np.array_equal(pd.cpu().numpy().reshape(-1, 2), batched_counts[1]))
     for g, *_ in plain:
         g.close()
-    vb = args.steps * updates / (t_b / 1e3)
-    vp = args.steps * updates / (t_p / 1e3)
+    vb = steps * updates / (t_b / 1e3)
+    vp = steps * updates / (t_p / 1e3)
     res = {"metric": "edge updates/s (batched form: all members in one captured launch sequence)",
-           "value": vb, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": t_b / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "value": vb, "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": warmup,
+           "ms_per_step": t_b / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "u32", "data": "synthetic (seeded RMAT members)",
            "config": {"workload": f"{G} RMAT graphs, vertices log-uniform 2^10..2^18, average degree 8, "
                                   f"insert + delete batches log-uniform 1..1M per member",
@@ -656,14 +714,19 @@ def run_batched(args):
                       "updates_per_step": updates, "tuned": {k: tuned[k] for k in ("block_capacity", "item_blocks",
                                                                                       "dense_shift")},
                       "l2": "flushed before every timed step"},
-           "plain": {"value": vp, "ms_per_step": t_p / args.steps,
+           "plain": {"value": vp, "ms_per_step": t_p / steps,
                      "form": "one graph object per member, insert + delete call per member"},
-           "speedup_vs_plain": vb / vp, "counts_match_plain": bool(same)}
-    print(json.dumps(res), flush=True)
-    return 0
+           "speedup_vs_plain": vb / vp, "counts_match_plain": bool(same),
+           "tuned_here": bool(tune and not tuned.get("cached", False))}
+    return res
 
 
 def run_serving(args):
+    print(json.dumps(serving_record(args.serve_scale, args.requests, (0.5, 0.7, 0.9))), flush=True)
+    return 0
+
+
+def serving_record(scale, requests, loads):
     """Serving: RMAT 2^24 vertices / 2^28 edges resident on the device;
     requests of mixed kind (40% insert, 40% delete of base edges, 20% query),
     sizes log-uniform in 1..1M, Poisson arrivals at 50%, 70% and 90% of the
@@ -677,12 +740,12 @@ def run_serving(args):
     from paper_2306_08252_gb300 import serve
 
     torch.cuda.set_device(0)
-    scale, C = args.serve_scale, 16
+    C = 16
     edges = 1 << (scale + 4)
     t_gen = time.perf_counter()
     bs, bd = W.rmat_pairs(5, 0, edges, scale)
-    reqs, gaps = W.serving_requests(5, bs, bd, scale, args.requests)
-    cap_reqs, _ = W.serving_requests(6, bs, bd, scale, args.requests)
+    reqs, gaps = W.serving_requests(5, bs, bd, scale, requests)
+    cap_reqs, _ = W.serving_requests(6, bs, bd, scale, requests)
     t_gen = time.perf_counter() - t_gen
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
     d_bs, d_bd = dev(bs), dev(bd)
@@ -707,7 +770,7 @@ def run_serving(args):
     server.run(crs, realtime=False)
     cap = len(crs) / (time.perf_counter() - t0)
     levels = []
-    for load in (0.5, 0.7, 0.9):
+    for load in loads:
         server = fresh()
         rate = load * cap
         arrivals = np.cumsum(gaps) / rate
@@ -735,12 +798,11 @@ def run_serving(args):
            "value": levels[-1]["updates_per_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
            "data": "synthetic (seeded RMAT graph and request stream)",
            "config": {"workload": f"RMAT scale {scale} ({1 << scale} vertices, {edges} edges), C={C}; "
-                                  f"{args.requests} requests, 40/40/20 insert/delete/query, sizes log-uniform 1..1M",
+                                  f"{requests} requests, 40/40/20 insert/delete/query, sizes log-uniform 1..1M",
                       "slots": 4, "merge_pairs": 2_000_000, "generation_s": t_gen},
            "capacity_req_per_s": cap, "levels": levels, "final_edges": st["num_edges"],
            "final_pool_bytes": st["pool_bytes"]}
-    print(json.dumps(res), flush=True)
-    return 0
+    return res
 
 
 # ------------------------------------------------------- per-row sweep
@@ -1157,6 +1219,24 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     res, (base, upd, qry) = run_ours(args, rank, world, local_rank)
+    if world == 1 and not args.no_batched:
+        # the batched form, short: the 256-member workload, 3 steps, the
+        # autotuner's usual configuration (no tuning pass)
+        b = batched_record(256, 3, 1, tune=False)
+        res["batched"] = {k: b[k] for k in ("metric", "value", "unit", "ms_per_step", "steps", "config",
+                                            "plain", "speedup_vs_plain", "counts_match_plain")}
+        res["batched_speedup_vs_plain"] = b["speedup_vs_plain"]
+    if world == 1 and not args.no_serving:
+        # the serving loop, short: RMAT scale 20 resident, 2,000 requests,
+        # Poisson arrivals at 70% of the measured capacity
+        sv = serving_record(20, 2000, (0.7,))
+        lv = sv["levels"][0]
+        res["serving"] = {"metric": sv["metric"], "config": sv["config"], "capacity_req_per_s": sv["capacity_req_per_s"],
+                          "load": lv["load"], "p50_ms": lv["p50_ms"], "p99_ms": lv["p99_ms"], "max_ms": lv["max_ms"],
+                          "updates_per_s": lv["updates_per_s"], "requests_per_run": lv["requests_per_run"],
+                          "failed": lv["failed"],
+                          "note": "short form of --workload serving (RMAT scale 24, three load levels)"}
+        res["serving_p99_ms"] = lv["p99_ms"]
     if rank == 0 and not args.no_cpu_baseline:
         v, steps, secs = oracle_sample_rate(base, upd, qry)
         res["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -64,3 +64,12 @@ def test_tiny_config_shape():
             existing = [p for p in pairs if p in base]
             absent = [p for p in pairs if p not in seen]
             assert len(existing) == 512 and len(absent) == 512
+
+
+def test_unique_and_membership_helpers_match_numpy():
+    rng = np.random.default_rng(3)
+    for n in (0, 1, 7, 5000):
+        a = rng.integers(0, 900, n).astype(np.uint64)
+        np.testing.assert_array_equal(W.unique_sorted(a), np.unique(a))
+        b = rng.integers(0, 1200, 2000).astype(np.uint64)
+        np.testing.assert_array_equal(W.in_sorted(b, W.unique_sorted(a)), np.isin(b, a))

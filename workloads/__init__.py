@@ -125,16 +125,37 @@ def unkey(k: np.ndarray):
     return (k >> np.uint64(32)).astype(np.uint32), (k & np.uint64(0xFFFFFFFF)).astype(np.uint32)
 
 
+def unique_sorted(a: np.ndarray) -> np.ndarray:
+    """The distinct values of ``a`` in increasing order (what np.unique
+    returns), by one sort and a comparison of neighbours."""
+    a = np.sort(np.asarray(a), kind="stable")
+    if a.size == 0:
+        return a
+    keep = np.empty(a.size, dtype=bool)
+    keep[0] = True
+    np.not_equal(a[1:], a[:-1], out=keep[1:])
+    return a[keep]
+
+
+def in_sorted(a: np.ndarray, table: np.ndarray) -> np.ndarray:
+    """Membership of every value of ``a`` in the sorted distinct ``table``."""
+    if table.size == 0:
+        return np.zeros(a.size, dtype=bool)
+    pos = np.searchsorted(table, a)
+    pos[pos == table.size] = 0
+    return table[pos] == a
+
+
 def absent_pairs(seed: int, stream: int, n: int, nv: int, exclude_keys: np.ndarray, lo: int = 0):
     """n uniform pairs whose keys are not in ``exclude_keys`` (sorted or not)."""
-    excl = np.unique(exclude_keys)
+    excl = unique_sorted(exclude_keys)
     got = []
     have = 0
     rnd = 0
     while have < n:
         s, d = uniform_pairs(seed, stream * 1000 + rnd, max(2 * (n - have), 64), nv, lo)
         k = keys(s, d)
-        k = k[~np.isin(k, excl)]
+        k = k[~in_sorted(k, excl)]
         got.append(k)
         have += k.size
         rnd += 1
@@ -170,7 +191,7 @@ def tiny_uniform(seed: int = 1, nv: int = 1024, base_edges: int = 8192, rounds: 
     seeded permutation, so each is present when deleted), half are pairs never
     inserted so far (absent)."""
     bs, bd = uniform_pairs(seed, 0, base_edges, nv)
-    base_keys = np.unique(keys(bs, bd))
+    base_keys = unique_sorted(keys(bs, bd))
     perm = shuffled(seed, 1, base_keys)
     seen = [keys(bs, bd)]
     ops = []
@@ -219,7 +240,7 @@ def er_mixed(seed: int = 3, nv: int = 1 << 22, base_edges: int = 16_777_216, rou
     """Erdos-Renyi-style uniform multigraph with mixed rounds, then vertex
     deletes of distinct ids and vertex inserts with out-edges to live ids."""
     bs, bd = uniform_pairs(seed, 0, base_edges, nv)
-    base_keys = np.unique(keys(bs, bd))
+    base_keys = unique_sorted(keys(bs, bd))
     perm = shuffled(seed, 1, base_keys)
     seen = [keys(bs, bd)]
     ops = []
@@ -260,8 +281,8 @@ def batched_rmat(seed: int = 4, graphs: int = 256, xlo: float = 10.0, xhi: float
     ids."""
     xs = xlo + (xhi - xlo) * uniform_f64(seed, 0, graphs)
     ls = np.log(smax) * uniform_f64(seed, 1, graphs)
-    out = []
-    for i in range(graphs):
+
+    def member(i):
         x = float(xs[i])
         nv = max(2, int(round(2.0 ** x)))
         scale = int(np.ceil(np.log2(nv)))
@@ -269,7 +290,7 @@ def batched_rmat(seed: int = 4, graphs: int = 256, xlo: float = 10.0, xhi: float
         bs, bd = rmat_pairs(seed, 100 + i, e, scale, abcd, limit=nv)
         s = max(1, int(round(np.exp(ls[i]))))
         ins_s, ins_d = rmat_pairs(seed, 100_000 + i, s, scale, abcd, limit=nv)
-        base_keys = np.unique(keys(bs, bd))
+        base_keys = unique_sorted(keys(bs, bd))
         ex = shuffled(seed, 200_000 + i, base_keys)[:s // 2]
         es, ed = unkey(ex)
         as_, ad = absent_pairs(seed, 300_000 + i, s - es.size, nv,
@@ -277,8 +298,22 @@ def batched_rmat(seed: int = 4, graphs: int = 256, xlo: float = 10.0, xhi: float
         ds = np.concatenate([es, as_])
         dd = np.concatenate([ed, ad])
         order = shuffled(seed, 400_000 + i, np.arange(ds.size, dtype=np.uint32))
-        out.append({"nv": nv, "bulk": (bs, bd), "insert": (ins_s, ins_d), "delete": (ds[order], dd[order])})
-    return out
+        return {"nv": nv, "bulk": (bs, bd), "insert": (ins_s, ins_d), "delete": (ds[order], dd[order])}
+
+    # members are independent (each draws from its own streams), so they are
+    # generated on host threads (the C generators and numpy's sorts release
+    # the interpreter lock); the result does not depend on the thread count
+    return _parallel_map(member, range(graphs))
+
+
+def _parallel_map(fn, items):
+    from concurrent.futures import ThreadPoolExecutor
+    items = list(items)
+    workers = min(len(items), os.cpu_count() or 1)
+    if workers <= 1:
+        return [fn(i) for i in items]
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        return list(ex.map(fn, items))
 
 
 def concat_member_batches(members, key):
@@ -302,18 +337,19 @@ def serving_requests(seed: int, base_src, base_dst, scale: int, n_requests: int,
     u = uniform_f64(seed, 0, n_requests)
     ls = np.log(smax) * uniform_f64(seed, 1, n_requests)
     gaps = -np.log(1.0 - uniform_f64(seed, 2, n_requests))
-    reqs = []
-    for i in range(n_requests):
+
+    def request(i):
         s = max(1, int(round(np.exp(ls[i]))))
         if u[i] < mix[0]:
             a, b = rmat_pairs(seed, 10_000 + i, s, scale, abcd)
-            reqs.append(("insert", a, b))
-        elif u[i] < mix[0] + mix[1]:
+            return ("insert", a, b)
+        if u[i] < mix[0] + mix[1]:
             idx = sample_indices(seed, 20_000 + i, base_src.size, s)
-            reqs.append(("delete", base_src[idx], base_dst[idx]))
-        else:
-            h = s // 2
-            idx = sample_indices(seed, 30_000 + i, base_src.size, h)
-            a, b = rmat_pairs(seed, 40_000 + i, s - h, scale, abcd)
-            reqs.append(("query", np.concatenate([base_src[idx], a]), np.concatenate([base_dst[idx], b])))
+            return ("delete", base_src[idx], base_dst[idx])
+        h = s // 2
+        idx = sample_indices(seed, 30_000 + i, base_src.size, h)
+        a, b = rmat_pairs(seed, 40_000 + i, s - h, scale, abcd)
+        return ("query", np.concatenate([base_src[idx], a]), np.concatenate([base_dst[idx], b]))
+
+    reqs = _parallel_map(request, range(n_requests))
     return reqs, gaps
