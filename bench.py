@@ -244,7 +244,7 @@ def whole_job_rate(units_per_rank, world, ms):
     return world * units_per_rank / (ms / 1e3)
 
 
-def byte_model(g, batch, qry, inserted, deleted, newblocks):
+def byte_model(g, batch, qry, inserted, deleted, newblocks, radix=False):
     """Algorithmic bytes.
 
     Per operation (the minimum the method must move): insert 12 B/edge +
@@ -276,14 +276,17 @@ def byte_model(g, batch, qry, inserted, deleted, newblocks):
     def tiers(src_ids, tiny_deg, tiny_nb):
         # thread-per-source tier: <= tiny_nb blocks, <= min(tiny_deg, tiny_nb*C)
         # entries, <= 16 batch entries (deletes 128 / 8, queries 64 / 4); the
-        # others: warp tier up to 256 batch entries, block-wide tier above
+        # others: the warp tier, or on the radix path the block-wide tier for
+        # 257..4096 batch entries
         m = np.bincount(src_ids, minlength=nv)
         touched = m > 0
         nb = (deg64 + C - 1) // C
         tiny = touched & (deg64 > 0) & (deg64 <= min(tiny_deg, tiny_nb * C)) & (nb <= tiny_nb) & (m <= 16)
         big = touched & (deg64 > 0) & ~tiny
-        warp = big & (m <= 256)
-        cta = big & (m > 256)
+        # the block-wide tier exists only on the radix-partition path; the
+        # default path's warp tier takes every source that is not tiny
+        cta = big & (m > 256) & (m <= 4096) if radix else np.zeros_like(big)
+        warp = big & ~cta
         f = lambda sel: 4 * int(deg64[sel].sum()) + 4 * int(m[sel].sum())
         return f(warp), f(cta), f(tiny)
 
@@ -383,7 +386,7 @@ def run_ours(args, rank, world, local_rank):
     deleted = int(counts[2].item())
     # degrees as the query/delete of a step see them: re-insert, measure, delete
     g.insert_edges(d_s, d_d, counts[:2])
-    model = byte_model(g, upd, qry, inserted, deleted, newblocks)
+    model = byte_model(g, upd, qry, inserted, deleted, newblocks, radix=args.grouping == "radix")
     g.delete_edges(d_s, d_d, counts[2:])
     torch.cuda.synchronize()
 

@@ -57,11 +57,16 @@ def test_byte_model_block_wide_tier():
     src = np.array([4] * 300 + [5] * 100, dtype=np.uint32)
     dst = np.arange(400, dtype=np.uint32) % 32
     m = bench.byte_model(_fake_graph(deg), (src, dst), (src[:10], dst[:10]), inserted=400, deleted=400,
-                         newblocks=0)
+                         newblocks=0, radix=True)
     k = m["kernels"]
     assert k["delete.mark_cta"] == 4 * 1000 + 4 * 300   # source 4: 300 batch entries
     assert k["delete.mark"] == 4 * 600 + 4 * 100        # source 5: 100
     assert k["delete.mark_tiny"] == 0
+    # the default path has no block-wide tier: the warp tier takes both
+    k = bench.byte_model(_fake_graph(deg), (src, dst), (src[:10], dst[:10]), inserted=400, deleted=400,
+                         newblocks=0)["kernels"]
+    assert k["delete.mark_cta"] == 0
+    assert k["delete.mark"] == 4 * (1000 + 600) + 4 * 400
 
 
 def test_whole_job_rate_and_config():
