@@ -15,9 +15,15 @@ order:
   another, and credits each removed entry to the first request that names
   its pair, which is what that request alone would have removed).
 
-Up to `slots` runs are in flight on one stream, each with its own pinned
-host and device buffers: host-to-device copy, the library call, the
-device-to-host copy of the results and an event.  An insert run is admitted
+Up to `slots` runs are in flight, each with its own pinned host and device
+buffers, on three streams ordered by events: the host-to-device copy of its
+pairs on an upload stream, the library call on the compute stream (after
+the copy's event), the device-to-host copy of its results on a download
+stream (after the call's event), then the run's completion event.  So one
+run's upload and another's download overlap the kernels of the run between
+them.  The calls themselves stay in arrival order on one stream: every call
+on a graph uses the graph's shared per-call device scratch, and update runs
+change the graph the next run reads.  An insert run is admitted
 only if its worst-case block demand (ceil(B / C) + B new blocks for B pairs)
 fits the free blocks of the pool as last known; otherwise the loop drains
 the in-flight runs, refreshes the pool counters and tries again.  A run that
@@ -69,7 +75,9 @@ class _Slot:
         self.h_off = torch.empty(max_reqs + 1, dtype=torch.int64).pin_memory()
         self.h_cnt = torch.empty(2 * max_reqs, dtype=torch.int64).pin_memory()
         self.h_out = torch.empty(cap, dtype=torch.uint8).pin_memory()
-        self.event = torch.cuda.Event()
+        self.copied = torch.cuda.Event()    # pairs on the device (upload stream)
+        self.computed = torch.cuda.Event()  # the library call done (compute stream)
+        self.event = torch.cuda.Event()     # results on the host (download stream)
         self.reqs = []
         self.kind = None
         self.n = 0
@@ -87,6 +95,8 @@ class Server:
         self.cap = int(merge_pairs)
         self.max_reqs = int(max_reqs)
         self.stream = torch.cuda.Stream()
+        self.up = torch.cuda.Stream()
+        self.down = torch.cuda.Stream()
         self.slots = [_Slot(self.cap, self.max_reqs, torch) for _ in range(slots)]
         self.free_slots = collections.deque(self.slots)
         self.inflight = collections.deque()
@@ -129,26 +139,32 @@ class Server:
             hs[a:a + len(r)] = r.src.view(np.int32)
             hd[a:a + len(r)] = r.dst.view(np.int32)
         slot.h_off.numpy()[:len(run) + 1] = offs
-        with torch.cuda.stream(self.stream):
-            s = self.stream.cuda_stream
+        k = len(run)
+        with torch.cuda.stream(self.up):
             if n:
                 slot.d_src[:n].copy_(slot.h_src[:n], non_blocking=True)
                 slot.d_dst[:n].copy_(slot.h_dst[:n], non_blocking=True)
-            if slot.kind == INSERT:
-                slot.d_off[:len(run) + 1].copy_(slot.h_off[:len(run) + 1], non_blocking=True)
-                gv.gv_insert_edges_segmented(self.g.handle, slot.d_src[:n], slot.d_dst[:n],
-                                             slot.d_off[:len(run) + 1], len(run), slot.d_cnt, s)
-                slot.h_cnt[:2 * len(run)].copy_(slot.d_cnt[:2 * len(run)], non_blocking=True)
-            elif slot.kind == DELETE:
-                slot.d_off[:len(run) + 1].copy_(slot.h_off[:len(run) + 1], non_blocking=True)
-                gv.gv_delete_edges_segmented(self.g.handle, slot.d_src[:n], slot.d_dst[:n],
-                                             slot.d_off[:len(run) + 1], len(run), slot.d_cnt, s)
-                slot.h_cnt[:2 * len(run)].copy_(slot.d_cnt[:2 * len(run)], non_blocking=True)
-            else:
-                gv.gv_query_edges(self.g.handle, slot.d_src[:n], slot.d_dst[:n], slot.d_out[:max(n, 1)], s)
-                if n:
-                    slot.h_out[:n].copy_(slot.d_out[:n], non_blocking=True)
-            slot.event.record(self.stream)
+            if slot.kind != QUERY:
+                slot.d_off[:k + 1].copy_(slot.h_off[:k + 1], non_blocking=True)
+            slot.copied.record(self.up)
+        self.stream.wait_event(slot.copied)
+        s = self.stream.cuda_stream
+        if slot.kind == INSERT:
+            gv.gv_insert_edges_segmented(self.g.handle, slot.d_src[:n], slot.d_dst[:n],
+                                         slot.d_off[:k + 1], k, slot.d_cnt, s)
+        elif slot.kind == DELETE:
+            gv.gv_delete_edges_segmented(self.g.handle, slot.d_src[:n], slot.d_dst[:n],
+                                         slot.d_off[:k + 1], k, slot.d_cnt, s)
+        else:
+            gv.gv_query_edges(self.g.handle, slot.d_src[:n], slot.d_dst[:n], slot.d_out[:max(n, 1)], s)
+        slot.computed.record(self.stream)
+        self.down.wait_event(slot.computed)
+        with torch.cuda.stream(self.down):
+            if slot.kind != QUERY:
+                slot.h_cnt[:2 * k].copy_(slot.d_cnt[:2 * k], non_blocking=True)
+            elif n:
+                slot.h_out[:n].copy_(slot.d_out[:n], non_blocking=True)
+            slot.event.record(self.down)
         self.inflight.append(slot)
         self.runs += 1
         self.merged_requests += len(run)
@@ -176,6 +192,7 @@ class Server:
 
     def _refresh_pool(self):
         self.stream.synchronize()
+        self.down.synchronize()
         st = self.g.stats()
         self.free_blocks = st["pool_blocks_free"]
         self.reserved_blocks = 0
@@ -241,6 +258,7 @@ class Server:
                     if wait > 0:
                         time.sleep(min(wait, 0.0005))
         self.stream.synchronize()
+        self.down.synchronize()
         return reqs
 
 
