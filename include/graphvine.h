@@ -135,6 +135,24 @@ typedef struct gv_config {
      * aggregation (default s = 3). */
     uint32_t item_blocks;
     uint32_t dense_shift;
+    /* Hub runs: a per-vertex edge-block size ("Conclusion and future work":
+     * changing the block size; "Performance Evaluation": deletes on graphs
+     * with a large maximum degree pay for the height of the hubs' trees).
+     * hub_shift s in 3..8 (0 = off): a vertex whose first allocation (the
+     * first insert, or bulk build, that gives it entries) takes at least
+     * hub_degree entries (0 = C * 2^s) receives its edge blocks in runs of
+     * R = 2^s contiguous blocks, so that for its tree a block holds C * R
+     * entries: the tree links run heads only and is s levels shallower.  The
+     * vertex keeps runs until it is emptied.  hub_percent (1..90, 0 = 50)
+     * of the pool's blocks, rounded down to whole runs, form the run region,
+     * with its own queue of free runs; an insert that needs more runs than
+     * are free fails like an exhausted pool (GV_ERR_OUT_OF_MEMORY, nothing
+     * changes).  Results never depend on the setting.  Excludes GV_GROW,
+     * GV_RADIX_GROUPING, graph sets and gv_reblock; block ids stay below
+     * 2^31 - 1 (the pool is capped there). */
+    uint32_t hub_shift;
+    uint32_t hub_degree;
+    uint32_t hub_percent;
     uint32_t reserved;
 } gv_config;
 
@@ -153,7 +171,9 @@ typedef struct gv_stats_t {
     uint64_t total_deleted;
     uint64_t total_rejected;
     uint32_t device_status;    /* latched device status (gv_status), cleared by the read */
-    uint32_t reserved;
+    uint32_t hub_shift;        /* log2 of the blocks per run (0: no hub runs) */
+    uint64_t pool_runs;        /* runs of the run region (its blocks count in pool_blocks) */
+    uint64_t pool_runs_free;   /* runs in the run queue (their blocks count in pool_blocks_free) */
 } gv_stats_t;
 
 /*

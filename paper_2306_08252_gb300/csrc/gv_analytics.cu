@@ -32,7 +32,7 @@ __device__ __forceinline__ bool for_item_entries(const GraphView &g, uint32_t u,
     const uint32_t nblk = min(aib, nb - kb);
     const uint32_t lane = lane_id();
     uint32_t bid = NIL;
-    if (lane < nblk) bid = cbt_walk(g.links, g.P, root, kb + 1 + lane);
+    if (lane < nblk) bid = blk_at(g, root, kb + 1 + lane);
     if (__any_sync(FULL, lane < nblk && bid == NIL)) return false;
     sb[lane] = bid;
     __syncwarp();

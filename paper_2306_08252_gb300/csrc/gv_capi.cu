@@ -82,6 +82,13 @@ struct gv_graph {
     unsigned long long *dtmp = nullptr;
     unsigned long long ocap = 0;
     uint32_t *t_owner = nullptr;
+    uint32_t *t_rowner = nullptr;  // hub runs: run pop index -> touched index (ocap entries)
+    // hub runs (per-vertex block size): log2 R (0 = off), the entry count of a
+    // first allocation that makes a source a hub (0 = C << rs), the percent
+    // of the pool in runs, the runs and the ring of free run heads
+    uint32_t rs = 0, hub_deg_cfg = 0, hub_pct = 0;
+    unsigned long long RP = 0;
+    uint32_t *rqueue = nullptr;
     // items
     unsigned long long icap = 0;
     uint32_t ib_alloc = 0;  // blocks per item the work-item arrays were sized for
@@ -236,6 +243,13 @@ GraphView view(const gv_graph *g) {
     v.set_vbase = nullptr;
     v.set_off = nullptr;
     v.set_counts = nullptr;
+    if (g->RP) {
+        v.rs = g->rs;
+        v.hub_deg = g->hub_deg_cfg ? g->hub_deg_cfg : g->C << g->rs;
+        v.RP = g->RP;
+        v.rqueue = g->rqueue;
+        v.t_rowner = g->t_rowner;
+    }
     return v;
 }
 
@@ -363,8 +377,11 @@ gv_status ensure_owner(gv_graph *g, unsigned long long need) {
     if (need <= g->ocap && g->ocap) return GV_OK;
     unsigned long long cap = std::max<unsigned long long>(need, std::max<unsigned long long>(2 * g->ocap, 1024));
     dfree(g->t_owner);
+    dfree(g->t_rowner);
     g->ocap = 0;
     GV_TRY(dalloc(&g->t_owner, cap, &g->scratch_bytes));
+    // run pops of a call are bounded like its block pops (a run holds R >= 1 blocks)
+    if (g->rs) GV_TRY(dalloc(&g->t_rowner, cap, &g->scratch_bytes));
     g->ocap = cap;
     return GV_OK;
 }
@@ -469,8 +486,12 @@ gv_status setup_pool(gv_graph *g, uint32_t C, cudaStream_t s) {
         bytes = fr / 2;  // "Edge Queue": at least half of the GPU memory
     }
     const bool weighted = (g->flags & GV_WEIGHTED) != 0;
-    const unsigned long long P = fit_blocks(bytes, C, weighted);
+    unsigned long long P = fit_blocks(bytes, C, weighted);
+    // with hub runs a root word carries RUN_BIT: block ids stay below 2^31 - 1
+    if (g->rs && P > 0x7FFFFFFEull) P = 0x7FFFFFFEull;
     if (P == 0) return GV_ERR_INVALID_ARG;
+    const unsigned long long RP = g->rs ? (P * g->hub_pct / 100) >> g->rs : 0ull;
+    if (g->rs && RP == 0) return GV_ERR_INVALID_ARG;  // the pool holds no run
     char *base = nullptr;
     if (g->pool_mem_cfg) {
         if (reinterpret_cast<uintptr_t>(g->pool_mem_cfg) % 16 != 0) return GV_ERR_INVALID_ARG;
@@ -486,11 +507,19 @@ gv_status setup_pool(gv_graph *g, uint32_t C, cudaStream_t s) {
     }
     if (!lay_out_pool(g, base, bytes, C, P)) return GV_ERR_STATE;  // cannot happen: P was fitted
     g->pool_bytes = bytes;
-    GV_CK(gv::launch_init_queue(g->queue, P, lcfg(g, s)));
-    // Dev: queue holds every block
-    Dev init;
-    std::memset(&init, 0, sizeof(init));
-    GV_CK(cudaMemcpyAsync(&g->dev->q_back, &P, sizeof(P), cudaMemcpyHostToDevice, s));
+    // Dev: the edge queue holds every block outside the run region [0, H);
+    // the run queue the heads of the region's runs
+    const unsigned long long H = RP << g->rs;
+    GV_CK(gv::launch_init_queue(g->queue, P - H, lcfg(g, s), (uint32_t)H, 1u));
+    g->h_small[4] = P - H;
+    GV_CK(cudaMemcpyAsync(&g->dev->q_back, &g->h_small[4], 8, cudaMemcpyHostToDevice, s));
+    if (RP) {
+        GV_TRY(dalloc(&g->rqueue, RP, &g->scratch_bytes));
+        GV_CK(gv::launch_init_queue(g->rqueue, RP, lcfg(g, s), 0u, 1u << g->rs));
+        g->h_small[5] = RP;
+        GV_CK(cudaMemcpyAsync(&g->dev->rq_back, &g->h_small[5], 8, cudaMemcpyHostToDevice, s));
+        g->RP = RP;
+    }
     GV_CK(cudaStreamSynchronize(s));
     GV_TRY(ensure_items(g, item_bound(g, 1024)));
     return GV_OK;
@@ -524,7 +553,7 @@ gv_status ensure_batch(gv_graph *g, uint64_t n, int mode) {
 // (the dense threshold) on dictionaries of at most GP_BMAX * GP_WMAX
 // vertices, when the graph asked for the radix-partition grouping.
 bool use_grouped(const gv_graph *g, uint64_t n) {
-    if (!(g->flags & GV_RADIX_GROUPING)) return false;
+    if (!(g->flags & GV_RADIX_GROUPING) || g->rs) return false;
     if (g->set_G || g->C == 0 || n == 0) return false;
     if ((unsigned long long)g->vcap > (unsigned long long)gv::GP_BMAX * gv::GP_WMAX) return false;
     return n >= ((unsigned long long)g->nv >> g->dense_shift);
@@ -895,7 +924,8 @@ gv_status insert_impl(gv_graph *g, const uint32_t *src, const uint32_t *dst, uin
             if (counts) GV_CK(cudaMemsetAsync(dcounts, 0, 16, s));
         } else {
             int set = -1;
-            const bool small = n <= gv::small_insert_max();
+            // (hub runs: the one-CTA path takes single blocks only)
+            const bool small = n <= gv::small_insert_max() && !g->rs;
             const bool grp = !small && use_grouped(g, n);
             if (grp) GV_TRY(ensure_group(g, n, g->wdata != nullptr, true, 0));
             const GraphView v = grp ? grouped_view(g, n) : view(g);
@@ -1064,6 +1094,11 @@ gv_status gv_create(const gv_config *cfg, uint32_t num_vertices, void *stream, g
     if ((c.flags & GV_GROW) && c.pool_mem) return GV_ERR_INVALID_ARG;  // a caller-owned pool cannot grow
     if (c.pool_mem && c.pool_bytes == 0) return GV_ERR_INVALID_ARG;
     if (num_vertices > 0x7FFFFFFFu) return GV_ERR_INVALID_ARG;
+    // hub runs: R = 2^s with TINY_NB <= R (a small run adjacency lies in one
+    // run) and s <= 8; excluded with pool growth and the radix grouping
+    if (c.hub_shift != 0 && (c.hub_shift < 3 || c.hub_shift > 8)) return GV_ERR_INVALID_ARG;
+    if (c.hub_shift && (c.flags & (GV_GROW | GV_RADIX_GROUPING))) return GV_ERR_INVALID_ARG;
+    if (c.hub_percent > 90) return GV_ERR_INVALID_ARG;
     gv_graph *g = new (std::nothrow) gv_graph();
     if (!g) return GV_ERR_OUT_OF_MEMORY;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1104,6 +1139,9 @@ gv_status gv_create(const gv_config *cfg, uint32_t num_vertices, void *stream, g
         }
     }
     g->flags = c.flags;
+    g->rs = c.hub_shift;
+    g->hub_deg_cfg = c.hub_degree;
+    g->hub_pct = c.hub_percent ? c.hub_percent : 50;
     g->item_blocks_cfg = c.item_blocks;
     if (c.dense_shift) g->dense_shift = std::min<uint32_t>(c.dense_shift, 31);
     g->pool_bytes_cfg = c.pool_bytes;
@@ -1147,7 +1185,7 @@ gv_status gv_destroy(gv_graph *g) {
         if (g->pool_alloc) cudaFree(g->pool_alloc);
         dfree(g->sent); dfree(g->alive); dfree(g->vcnt); dfree(g->vinfo); dfree(g->vtid); dfree(g->dead);
         dfree(g->dev);
-        dfree(g->t_vid); dfree(g->t_a); dfree(g->t_b); dfree(g->t_owner); dfree(g->t_tiny); dfree(g->prank);
+        dfree(g->t_vid); dfree(g->t_a); dfree(g->t_b); dfree(g->t_owner); dfree(g->t_rowner); dfree(g->rqueue); dfree(g->t_tiny); dfree(g->prank);
         dfree(g->items); dfree(g->it_mask); dfree(g->it_cnt); dfree(g->it_H); dfree(g->it_S); dfree(g->it_bid);
         dfree(g->arena); dfree(g->found); dfree(g->qpos); dfree(g->partials);
         dfree(g->owner_bits); dfree(g->vres);
@@ -1327,6 +1365,7 @@ gv_status gv_reblock(gv_graph *g, uint32_t block_capacity, uint32_t *h_block_cap
     DeviceGuard dg(g->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (g->C == 0) return GV_ERR_STATE;  // nothing laid out yet: the first edge batch fixes C
+    if (g->rs) return GV_ERR_STATE;     // a graph with hub runs keeps its layout
     // a latched device error is reported first; nothing changes
     GV_CK(cudaStreamSynchronize(g->last_stream));
     g->last_stream = s;
@@ -1454,8 +1493,11 @@ gv_status gv_stats(gv_graph *g, gv_stats_t *out) {
     out->flags = g->flags;
     out->num_edges = d.num_edges;
     out->pool_blocks = g->P;
-    out->pool_blocks_free = d.q_back - d.q_front;
+    out->pool_blocks_free = d.q_back - d.q_front + ((d.rq_back - d.rq_front) << g->rs);
     out->pool_blocks_used = g->P - out->pool_blocks_free;
+    out->hub_shift = g->rs;
+    out->pool_runs = g->RP;
+    out->pool_runs_free = d.rq_back - d.rq_front;
     out->pool_bytes = g->pool_bytes;
     uint64_t stage_bytes = 0;
     for (auto &b : g->stage.buf) stage_bytes += b.bytes;
@@ -1720,6 +1762,7 @@ gv_status gv_set_create(const gv_config *cfg, uint32_t num_graphs, const uint32_
                         gv_graph **out) {
     if (!out || num_graphs == 0 || num_graphs > gv::SET_MAX_G || !num_vertices) return GV_ERR_INVALID_ARG;
     if (!cfg || cfg->block_capacity == 0 || (cfg->flags & GV_DEDUP)) return GV_ERR_INVALID_ARG;
+    if (cfg->hub_shift) return GV_ERR_INVALID_ARG;  // hub runs: plain graphs only
     std::vector<uint32_t> base(num_graphs + 1, 0);
     uint64_t tot = 0;
     for (uint32_t i = 0; i < num_graphs; ++i) {

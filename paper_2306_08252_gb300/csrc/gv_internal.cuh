@@ -55,6 +55,10 @@ struct Dev {
     unsigned int n_mbuckets;        // buckets of more than one chunk
     unsigned int n_grouped;         // valid pairs of the grouped batch
     unsigned int n_hash;            // grouped path: sources whose batch keys go to an arena hash set
+    // hub runs (see GraphView::rs): ring of free run heads, and the runs
+    // popped / pushed by the current call
+    unsigned long long rq_front, rq_back;
+    unsigned long long ralloc_total, rfree_total;
 };
 
 // Everything a kernel needs to know about one graph (passed by value).
@@ -136,6 +140,20 @@ struct GraphView {
     uint2 *grp_items;           // block-wide membership tier: {touched index, first item} from
                                 // the bottom; hash-set sources {touched index, -} from the top
     unsigned long long grp_cap; // entries of grp_items
+    // Hub runs (a per-vertex block size): a source whose first allocation
+    // takes at least hub_deg entries gets its blocks in runs of R = 2^rs
+    // contiguous, R-aligned blocks of the run region [0, RP * R) instead of
+    // one at a time, so its blocks are C * R slots long for the tree: the
+    // tree links run heads only (heap index of a run), its height drops by
+    // rs, and every slot computation (degree, slot index, block index in
+    // units of C) stays as for the other sources.  Marked by RUN_BIT in the
+    // sentinel's root word; kept until the source is emptied.  rs == 0: no
+    // runs (the bit is never set).
+    uint32_t rs;
+    uint32_t hub_deg;
+    unsigned long long RP;      // runs in the run region
+    uint32_t *rqueue;           // ring of RP free run heads (block ids, multiples of R)
+    uint32_t *t_rowner;         // insert: run pop index -> touched index
 };
 
 // Grouped path limits and sizes.
@@ -288,6 +306,24 @@ __device__ __forceinline__ uint32_t cbt_walk(const uint32_t *__restrict__ links,
         if (b >= P) return NIL;
     }
     return b;
+}
+
+// Hub runs: the sentinel's root word is the id of the root block, or of the
+// head of the first run with RUN_BIT set (block ids then stay below 2^31 - 1,
+// so that no root word of a run equals NIL).
+constexpr uint32_t RUN_BIT = 0x80000000u;
+
+__device__ __forceinline__ bool is_run(uint32_t rw) { return rw != NIL && (rw & RUN_BIT); }
+
+// Block id of the block at heap index k (k >= 1, in blocks of C slots) of
+// the adjacency whose sentinel root word is rw: a tree walk for a plain
+// adjacency; for a run adjacency a walk to the run holding block k - 1
+// (run heap index ((k - 1) >> rs) + 1), then the offset inside the run.
+__device__ __forceinline__ uint32_t blk_at(const GraphView &g, uint32_t rw, uint32_t k) {
+    if (!is_run(rw)) return cbt_walk(g.links, g.P, rw, k);
+    const uint32_t j = k - 1;
+    const uint32_t h = cbt_walk(g.links, g.P, rw & ~RUN_BIT, (j >> g.rs) + 1);
+    return h == NIL ? NIL : h + (j & ((1u << g.rs) - 1u));
 }
 
 // x mod P for a pool of P blocks (0 for an empty pool).
@@ -481,6 +517,35 @@ __device__ __forceinline__ unsigned long long ring(unsigned long long base, unsi
                                                    unsigned long long P) {
     unsigned long long q = base + off;
     return q >= P ? q - P : q;
+}
+
+// A run freed by a delete goes back onto the run queue at rq_back + the
+// call's run counter (published by the finalize kernel).  Runs return
+// rarely (a hub shrinking by whole runs), so no staging.
+__device__ __forceinline__ void push_run(const GraphView &g, uint32_t head, unsigned long long rqbb) {
+    const unsigned long long pos = atomicAdd(&g.dev->rfree_total, 1ull);
+    g.rqueue[ring(rqbb, pos, g.RP)] = head;
+}
+
+// Delete-side release for a run adjacency (root word rw) shrinking to nbn
+// blocks: the block at heap index k with id bid gives its whole run back
+// when it is the run's head and the run lies past the runs still needed;
+// a kept parent run forgets it.  The walk to the parent passes only kept
+// runs, whose links to kept children no thread clears.
+__device__ __forceinline__ void release_run(const GraphView &g, uint32_t rw, uint32_t k, uint32_t bid,
+                                            uint32_t nbn, unsigned long long rqbb) {
+    const uint32_t j = k - 1, R = 1u << g.rs;
+    if (j & (R - 1u)) return;
+    const uint32_t kr = (j >> g.rs) + 1u;         // heap index of the run
+    const uint32_t nrn = (nbn + R - 1u) >> g.rs;  // runs kept
+    if (kr <= nrn) return;
+    push_run(g, bid, rqbb);
+    const uint32_t pr = kr >> 1;
+    if (kr >= 2u && pr <= nrn) {
+        const uint32_t ph = cbt_walk(g.links, g.P, rw & ~RUN_BIT, pr);
+        if (ph != NIL) g.links[2ull * ph + (kr & 1u)] = NIL;
+        else latch_status(g.dev, 5u /* GV_ERR_STATE */);
+    }
 }
 
 // Freed block ids of one warp, staged in shared memory and pushed onto the

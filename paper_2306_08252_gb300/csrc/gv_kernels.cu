@@ -298,28 +298,48 @@ __global__ void __launch_bounds__(256) k_plan_insert(GraphView g) {
     pdl_wait();
     const uint32_t nt = g.dev->n_touched;
     const uint32_t C = g.C;
-    __shared__ unsigned long long s_base;
+    __shared__ unsigned long long s_base, s_rbase;
     for (uint32_t base = blockIdx.x * blockDim.x; base < nt; base += gridDim.x * blockDim.x) {
         const uint32_t t = base + threadIdx.x;
-        uint32_t need = 0, deg = 0, last = NIL;
+        uint32_t need = 0, rneed = 0, deg = 0, last = NIL;
+        bool run = false;
         if (t < nt) {
             const uint32_t u = g.t_vid[t];
             const uint32_t cnt = g.vcnt[vslot(g.vmask, u)];
             const uint4 s = g.sent[u];
             deg = s.x;
             last = s.w;
-            const uint32_t space = s.y * C - deg;
-            need = cnt > space ? divc(g.cmul, cnt - space + C - 1) : 0u;
+            // a hub: already in runs, or an empty source whose first
+            // allocation takes at least hub_deg entries
+            run = g.rs && (is_run(s.z) || (s.y == 0 && cnt >= g.hub_deg));
+            if (!run) {
+                const uint32_t space = s.y * C - deg;
+                need = cnt > space ? divc(g.cmul, cnt - space + C - 1) : 0u;
+            } else {
+                const uint32_t R = 1u << g.rs;
+                const uint32_t nbn = divc(g.cmul, deg + cnt + C - 1);
+                rneed = ((nbn + R - 1u) >> g.rs) - ((s.y + R - 1u) >> g.rs);
+            }
         }
-        uint32_t tot;
+        uint32_t tot, rtot = 0, rex = 0;
         const uint32_t ex = block_excl_scan(need, &tot);
-        if (threadIdx.x == 0) s_base = tot ? atomicAdd(&g.dev->alloc_total, (unsigned long long)tot) : 0ull;
+        if (g.rs) rex = block_excl_scan(rneed, &rtot);
+        if (threadIdx.x == 0) {
+            s_base = tot ? atomicAdd(&g.dev->alloc_total, (unsigned long long)tot) : 0ull;
+            s_rbase = rtot ? atomicAdd(&g.dev->ralloc_total, (unsigned long long)rtot) : 0ull;
+        }
         __syncthreads();
-        const unsigned long long off = s_base + ex;
-        if (t < nt) {
+        if (t < nt && !run) {
+            const unsigned long long off = s_base + ex;
             g.t_a[t] = make_uint4(deg, last, (uint32_t)off, need);
             g.vinfo[vslot(g.vmask, g.t_vid[t])] = make_uint4(deg, last, (uint32_t)off, 0u);
             for (uint32_t j = 0; j < need; ++j) g.t_owner[off + j] = t;
+        } else if (t < nt) {
+            // run pops: offset into the run queue, count flagged by RUN_BIT
+            const unsigned long long roff = s_rbase + rex;
+            g.t_a[t] = make_uint4(deg, last, (uint32_t)roff, rneed | RUN_BIT);
+            g.vinfo[vslot(g.vmask, g.t_vid[t])] = make_uint4(deg, last, (uint32_t)roff, 1u);
+            for (uint32_t j = 0; j < rneed; ++j) g.t_rowner[roff + j] = t;
         }
         __syncthreads();
     }
@@ -329,8 +349,9 @@ __global__ void __launch_bounds__(256) k_link_insert(GraphView g) {
     pdl_wait();
     Dev *dev = g.dev;
     const unsigned long long total = dev->alloc_total;
+    const unsigned long long rtotal = g.rs ? dev->ralloc_total : 0ull;
     const unsigned long long qf = dev->q_front, qb = dev->q_back;
-    if (total > qb - qf) {
+    if (total > qb - qf || (rtotal && rtotal > dev->rq_back - dev->rq_front)) {
         // Edge queue exhausted: the whole call becomes a no-op.
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             dev->abort = 1u;
@@ -341,8 +362,39 @@ __global__ void __launch_bounds__(256) k_link_insert(GraphView g) {
     const unsigned long long P = g.P;
     const unsigned long long qbase = qmod(qf, P);
     const uint32_t C = g.C;
-    for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < total;
+    const unsigned long long rqbase = rtotal ? qmod(dev->rq_front, g.RP) : 0ull;
+    for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < total + rtotal;
          j += (unsigned long long)gridDim.x * blockDim.x) {
+        if (j >= total) {
+            // a popped run: its head takes run heap index nr + 1 + (its pop
+            // offset) in the tree of run heads, by the same rule as a block
+            const unsigned long long jr = j - total;
+            const uint32_t t = g.t_rowner[jr];
+            const uint4 a = g.t_a[t];
+            const uint32_t deg = a.x, roff = a.z, rneed = a.w & ~RUN_BIT;
+            const uint32_t R = 1u << g.rs;
+            const uint32_t nr = (divc(g.cmul, deg + C - 1) + R - 1u) >> g.rs;
+            const uint32_t k = nr + 1 + (uint32_t)(jr - roff);
+            const uint32_t nrn = nr + rneed;
+            const uint32_t id = g.rqueue[ring(rqbase, jr, g.RP)];
+            if (id >= P) {
+                latch_status(dev, 5u /* GV_ERR_STATE */);
+                continue;
+            }
+            if (2ull * k > nrn) g.links[2ull * id] = NIL;
+            if (2ull * k + 1 > nrn) g.links[2ull * id + 1] = NIL;
+            if (k > 1) {
+                const uint32_t p = k >> 1;
+                const uint32_t pid = p > nr ? g.rqueue[ring(rqbase, roff + (p - nr - 1), g.RP)]
+                                            : cbt_walk(g.links, P, g.sent[g.t_vid[t]].z & ~RUN_BIT, p);
+                if (pid >= P) {
+                    latch_status(dev, 5u /* GV_ERR_STATE */);
+                    continue;
+                }
+                g.links[2ull * pid + (k & 1u)] = id;
+            }
+            continue;
+        }
         const uint32_t t = g.t_owner[j];
         const uint4 a = g.t_a[t];
         const uint32_t deg = a.x, off = a.z, need = a.w;
@@ -385,6 +437,7 @@ __global__ void __launch_bounds__(256) k_scatter_insert(GraphView g, const uint3
     if (g.dev->abort) return;
     const unsigned long long P = g.P;
     const unsigned long long qbase = qmod(g.dev->q_front, P);
+    const unsigned long long rqbase = g.rs ? qmod(g.dev->rq_front, g.RP) : 0ull;
     const uint32_t C = g.C;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long i0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i0 < n;
@@ -397,7 +450,7 @@ __global__ void __launch_bounds__(256) k_scatter_insert(GraphView g, const uint3
             u[j] = i < n ? ld_stream(src + i) : 0u;
             v[j] = i < n ? ld_stream(dst + i) : 0u;
         }
-        uint4 vi[PP];  // {deg, last block, queue offset of the new blocks, -}
+        uint4 vi[PP];  // {deg, last block, queue offset of the new blocks (or runs), 1 for a run source}
 #pragma unroll
         for (int j = 0; j < PP; ++j)
             if (r[j] != NIL) vi[j] = g.vinfo[vslot(g.vmask, u[j])];
@@ -417,7 +470,17 @@ __global__ void __launch_bounds__(256) k_scatter_insert(GraphView g, const uint3
                     const uint32_t q = r[j] - space;
                     const uint32_t jb = divc(g.cmul, q);
                     ln[j] = q - jb * C;
-                    blk[j] = g.queue[ring(qbase, vi[j].z + jb, P)];
+                    if (vi[j].w == 0u) {
+                        blk[j] = g.queue[ring(qbase, vi[j].z + jb, P)];
+                    } else {
+                        // block nb + jb of a run source: still inside its last
+                        // run (contiguous after the last block), or in run
+                        // (nb + jb) >> rs, popped at run offset z + that - nr
+                        const uint32_t J = nb + jb, nr = (nb + (1u << g.rs) - 1u) >> g.rs;
+                        blk[j] = J < (nr << g.rs) ? vi[j].y + 1u + jb
+                                                  : g.rqueue[ring(rqbase, vi[j].z + (J >> g.rs) - nr, g.RP)] +
+                                                        (J & ((1u << g.rs) - 1u));
+                    }
                 }
             }
         }
@@ -444,20 +507,38 @@ __global__ void __launch_bounds__(256) k_finalize_insert(GraphView g, unsigned l
     const bool abort = dev->abort != 0;
     const unsigned long long P = g.P;
     const unsigned long long qbase = qmod(dev->q_front, P);
+    const unsigned long long rqbase = g.rs ? qmod(dev->rq_front, g.RP) : 0ull;
     const uint32_t C = g.C;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
         const uint32_t u = g.t_vid[t];
         const uint32_t cnt = g.vcnt[vidx(g, u)];
         if (!abort) {
             const uint4 a = g.t_a[t];
-            const uint32_t deg = a.x, off = a.z, need = a.w;
+            const uint32_t deg = a.x, off = a.z;
             const uint32_t nb = divc(g.cmul, deg + C - 1);
             uint4 s = g.sent[u];
             s.x = deg + cnt;
-            s.y = nb + need;
-            if (need) {
-                if (nb == 0) s.z = g.queue[ring(qbase, off, P)];
-                s.w = g.queue[ring(qbase, off + need - 1, P)];
+            if (!(a.w & RUN_BIT)) {
+                const uint32_t need = a.w;
+                s.y = nb + need;
+                if (need) {
+                    if (nb == 0) s.z = g.queue[ring(qbase, off, P)];
+                    s.w = g.queue[ring(qbase, off + need - 1, P)];
+                }
+            } else {
+                // run source: the root word is the first run's head with
+                // RUN_BIT; the last block is block nbn - 1, found as in the
+                // scatter
+                const uint32_t R = 1u << g.rs;
+                const uint32_t nbn = divc(g.cmul, deg + cnt + C - 1);
+                const uint32_t nr = (nb + R - 1u) >> g.rs;
+                if (nb == 0) s.z = g.rqueue[ring(rqbase, off, g.RP)] | RUN_BIT;
+                if (nbn > nb) {
+                    const uint32_t J = nbn - 1u;
+                    s.w = J < (nr << g.rs) ? a.y + (J - (nb - 1u))
+                                           : g.rqueue[ring(rqbase, off + (J >> g.rs) - nr, g.RP)] + (J & (R - 1u));
+                }
+                s.y = nbn;
             }
             g.sent[u] = s;
         }
@@ -471,6 +552,7 @@ __global__ void __launch_bounds__(256) k_finalize_insert(GraphView g, unsigned l
             rej = 0;
         } else {
             dev->q_front += dev->alloc_total;
+            dev->rq_front += dev->ralloc_total;
             dev->num_edges += ins;
             dev->tot_ins += ins;
             dev->tot_rej += rej;
@@ -492,6 +574,8 @@ __global__ void __launch_bounds__(256) k_finalize_insert(GraphView g, unsigned l
         dev->n_groups = 0;
         dev->n_hash = 0;
         dev->free_total = 0;
+        dev->ralloc_total = 0;
+        dev->rfree_total = 0;
         dev->abort = 0;
         dev->done_ctas = 0;
     }
@@ -974,6 +1058,7 @@ __global__ void __launch_bounds__(256, 4) k_mark(GraphView g) {
     const uint32_t C = g.C, IB = g.IB;
     const unsigned long long P = g.P;
     const unsigned long long qbb = qmod(dev->q_back, P);
+    const unsigned long long rqbb = g.rs ? qmod(dev->rq_back, g.RP) : 0ull;
     __shared__ uint32_t s_free[8][64];
     __shared__ uint32_t s_bid[8][32];
     __shared__ __align__(16) uint32_t s_hkey[8][2 * LIST_MAX];
@@ -998,7 +1083,7 @@ __global__ void __launch_bounds__(256, 4) k_mark(GraphView g) {
         const uint32_t kb = c * IB;
         const uint32_t nblk = min(IB, nb - kb);
         uint32_t bid = NIL;
-        if (lane < nblk) bid = cbt_walk(g.links, P, root, kb + 1 + lane);
+        if (lane < nblk) bid = blk_at(g, root, kb + 1 + lane);
         if (__any_sync(FULL, lane < nblk && bid == NIL)) {
             if (lane == 0) latch_status(dev, 5u /* GV_ERR_STATE */);
             continue;
@@ -1182,11 +1267,13 @@ __global__ void __launch_bounds__(256, 4) k_mark(GraphView g) {
                 const uint32_t nbn = divc(g.cmul, degn + C - 1);
                 const uint32_t k = lane + 1;
                 const bool fr = lane < nblk && k > nbn;
-                fs.push(fr, bid, dev, g.queue, qbb, P);
+                const bool run = is_run(root);  // a run source returns whole runs
+                fs.push(fr && !run, bid, dev, g.queue, qbb, P);
                 const uint32_t p = k >> 1;
                 const uint32_t pb = __shfl_sync(FULL, bid, (p - 1) & 31u);
                 const uint32_t lastb = __shfl_sync(FULL, bid, (nbn - 1) & 31u);
-                if (fr && p >= 1 && p <= nbn) g.links[2ull * pb + (k & 1u)] = NIL;
+                if (fr && !run && p >= 1 && p <= nbn) g.links[2ull * pb + (k & 1u)] = NIL;
+                if (fr && run) release_run(g, root, k, bid, nbn, rqbb);
                 if (lane == 0) {
                     const uint32_t u = g.t_vid[t];
                     g.sent[u] = make_uint4(degn, nbn, nbn ? root : NIL, nbn ? lastb : NIL);
@@ -1239,6 +1326,7 @@ __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
     const uint32_t C = g.C;
     const unsigned long long P = g.P;
     const unsigned long long qbb = qmod(dev->q_back, P);
+    const unsigned long long rqbb = g.rs ? qmod(dev->rq_back, g.RP) : 0ull;
     __shared__ uint32_t s_free[8][64];
     __shared__ uint32_t s_mhist[(MODE == MODE_QUERY) ? 1 : SET_MAX_G];
     if (MODE != MODE_QUERY && g.set_G) {
@@ -1273,16 +1361,19 @@ __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
             aoff = a.y;
         }
         // heap index h (1-based) lives in bl.b[h-1]; children of h are 2h, 2h+1
+        // (a run source's first TINY_NB blocks all lie in its first run,
+        // R >= TINY_NB: consecutive ids from the head)
+        const bool run = is_run(root);
         Blocks8 bl;
 #pragma unroll
         for (uint32_t h = 0; h < TINY_NB; ++h) bl.b[h] = NIL;
-        bl.b[0] = root;
-        bool bad = act && root >= P;
+        bl.b[0] = run ? root & ~RUN_BIT : root;
+        bool bad = act && bl.b[0] >= P;
 #pragma unroll
         for (uint32_t h = 2; h <= TINY_NB; ++h) {
             if (act && !bad && h <= nb) {
                 const uint32_t parent = bl.b[h / 2 - 1];
-                const uint32_t c = g.links[2ull * parent + (h & 1u)];
+                const uint32_t c = run ? bl.b[0] + (h - 1) : g.links[2ull * parent + (h & 1u)];
                 bl.b[h - 1] = c;
                 if (c >= P) bad = true;
             }
@@ -1372,9 +1463,10 @@ __global__ void __launch_bounds__(256) k_mark_tiny(GraphView g) {
 #pragma unroll
         for (uint32_t h = TINY_NB; h >= 1; --h) {
             const bool fr = changed && h <= nb && h > nbn;
-            fs.push(fr, bl.b[h - 1], dev, g.queue, qbb, P);
-            if (fr && h >= 2 && h / 2 <= nbn) g.links[2ull * bl.b[h / 2 - 1] + (h & 1u)] = NIL;
+            fs.push(fr && !run, bl.b[h - 1], dev, g.queue, qbb, P);
+            if (fr && !run && h >= 2 && h / 2 <= nbn) g.links[2ull * bl.b[h / 2 - 1] + (h & 1u)] = NIL;
         }
+        if (changed && run && nbn == 0) push_run(g, bl.b[0], rqbb);  // emptied: its only run returns
         if (changed) {
             const uint32_t u = DIRECT ? k : g.t_vid[t];
             g.sent[u] = make_uint4(w, nbn, nbn ? root : NIL, nbn ? bl.get(nbn - 1) : NIL);
@@ -1439,6 +1531,7 @@ __global__ void __launch_bounds__(256) k_move(GraphView g) {
     const uint32_t C = g.C, IB = g.IB, SPI = IB * C;
     const unsigned long long P = g.P;
     const unsigned long long qbb = qmod(dev->q_back, P);
+    const unsigned long long rqbb = g.rs ? qmod(dev->rq_back, g.RP) : 0ull;
     __shared__ uint32_t s_free[8][64];
     FreeStage fs{s_free[threadIdx.x >> 5], 0u};
     for (uint32_t vi = warp; vi < nhi; vi += nwarps) {
@@ -1514,8 +1607,10 @@ __global__ void __launch_bounds__(256) k_move(GraphView g) {
         const uint32_t nblk = min(IB, nb - kb);
         const uint32_t k = kb + 1 + lane;
         const bool fr = lane < nblk && k > nbn;
-        fs.push(fr, fr ? bids[lane] : NIL, dev, g.queue, qbb, P);
-        if (fr) {
+        const bool run = is_run(b.z);  // a run source returns whole runs
+        fs.push(fr && !run, fr ? bids[lane] : NIL, dev, g.queue, qbb, P);
+        if (fr && run) release_run(g, b.z, k, bids[lane], nbn, rqbb);
+        if (fr && !run) {
             const uint32_t p = k >> 1;
             if (p >= 1 && p <= nbn) {
                 const uint32_t pb = g.it_bid[(size_t)(item0 + (p - 1) / IB) * IB + (p - 1) % IB];
@@ -1548,6 +1643,7 @@ __global__ void __launch_bounds__(256) k_finalize_member(GraphView g, unsigned l
         if (MODE == MODE_DELETE) {
             const unsigned long long del = dev->call_a, rej = dev->call_b;
             dev->q_back += dev->free_total;
+            dev->rq_back += dev->rfree_total;
             dev->num_edges -= del;
             dev->tot_del += del;
             dev->tot_rej += rej;
@@ -1569,6 +1665,8 @@ __global__ void __launch_bounds__(256) k_finalize_member(GraphView g, unsigned l
         dev->n_groups = 0;
         dev->n_hash = 0;
         dev->free_total = 0;
+        dev->ralloc_total = 0;
+        dev->rfree_total = 0;
         dev->abort = 0;
         dev->done_ctas = 0;
     }
@@ -1642,6 +1740,7 @@ __global__ void __launch_bounds__(256) k_free_items(GraphView g) {
     const uint32_t IB = g.IB;
     const unsigned long long P = g.P;
     const unsigned long long qbb = qmod(dev->q_back, P);
+    const unsigned long long rqbb = g.rs ? qmod(dev->rq_back, g.RP) : 0ull;
     __shared__ uint32_t s_free[8][64];
     FreeStage fs{s_free[threadIdx.x >> 5], 0u};
     for (uint32_t it = warp; it < nitems; it += nwarps) {
@@ -1650,10 +1749,13 @@ __global__ void __launch_bounds__(256) k_free_items(GraphView g) {
         const uint32_t kb = itm.y * IB;
         const uint32_t nblk = min(IB, b.y - kb);
         const bool fr = lane < nblk;
+        const bool run = is_run(b.z);
         uint32_t bid = NIL;
-        if (fr) bid = cbt_walk(g.links, P, b.z, kb + 1 + lane);
+        if (fr) bid = blk_at(g, b.z, kb + 1 + lane);
         if (fr && bid == NIL) latch_status(dev, 5u /* GV_ERR_STATE */);
-        fs.push(fr && bid != NIL, bid, dev, g.queue, qbb, P);
+        fs.push(fr && bid != NIL && !run, bid, dev, g.queue, qbb, P);
+        // a run source: each run's head block returns the run
+        if (fr && bid != NIL && run && ((kb + lane) & ((1u << g.rs) - 1u)) == 0u) push_run(g, bid, rqbb);
     }
     fs.flush(fs.n, dev, g.queue, qbb, P);
 }
@@ -1718,6 +1820,7 @@ __global__ void __launch_bounds__(256) k_finalize_vdel(GraphView g, const uint32
     if (last_cta(dev) && threadIdx.x == 0) {
         const unsigned long long del = dev->call_a;
         dev->q_back += dev->free_total;
+        dev->rq_back += dev->rfree_total;
         dev->num_edges -= del;
         dev->tot_del += del;
         dev->alloc_total = 0;
@@ -1733,6 +1836,8 @@ __global__ void __launch_bounds__(256) k_finalize_vdel(GraphView g, const uint32
         dev->n_groups = 0;
         dev->n_hash = 0;
         dev->free_total = 0;
+        dev->ralloc_total = 0;
+        dev->rfree_total = 0;
         dev->abort = 0;
         dev->done_ctas = 0;
     }

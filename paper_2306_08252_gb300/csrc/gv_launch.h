@@ -164,7 +164,8 @@ cudaError_t launch_init_vertices(const GraphView &g, uint32_t from, uint32_t to,
 cudaError_t launch_copy_dictionary(uint4 *dst_sent, uint8_t *dst_alive, const uint4 *src_sent,
                                    const uint8_t *src_alive, uint32_t n, const LaunchCfg &lc);
 // Edge queue initialisation: queue[i] = i.
-cudaError_t launch_init_queue(uint32_t *queue, unsigned long long P, const LaunchCfg &lc);
+cudaError_t launch_init_queue(uint32_t *queue, unsigned long long n, const LaunchCfg &lc, uint32_t first = 0,
+                              uint32_t step = 1);
 // Neighbour lists: offsets (exclusive scan of degrees), then copy.
 // offsets[i] = sum over vids[0 .. i-1] of the degree (rounded up to a
 // multiple of round_to when that is non-zero); offsets[n] = the total.

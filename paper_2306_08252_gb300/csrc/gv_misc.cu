@@ -26,11 +26,14 @@ __global__ void __launch_bounds__(256) k_copy_dictionary(uint4 *dst_sent, uint8_
 }
 
 // Edge queue: every pool block id, in order ("Edge Queue").
-__global__ void __launch_bounds__(256) k_init_queue(uint32_t *queue, unsigned long long P) {
+// queue[i] = first + i * step for i < n (the free block ids of a fresh pool,
+// or the heads of its runs).
+__global__ void __launch_bounds__(256) k_init_queue(uint32_t *queue, unsigned long long n, uint32_t first,
+                                                    uint32_t step) {
     pdl_wait();
-    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < P;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x)
-        queue[i] = (uint32_t)i;
+        queue[i] = first + (uint32_t)i * step;
 }
 
 __global__ void __launch_bounds__(256) k_iota(uint32_t *out, uint32_t first, uint32_t k) {
@@ -186,7 +189,7 @@ __global__ void __launch_bounds__(256) k_nbr_copy(GraphView g, const unsigned lo
         const uint32_t kb = itm.y * IB;
         const uint32_t nblk = min(IB, b.y - kb);
         uint32_t bid = NIL;
-        if (lane < nblk) bid = cbt_walk(g.links, g.P, b.z, kb + 1 + lane);
+        if (lane < nblk) bid = blk_at(g, b.z, kb + 1 + lane);
         if (__any_sync(FULL, lane < nblk && bid == NIL)) {
             if (lane == 0) latch_status(g.dev, 5u /* GV_ERR_STATE */);
             continue;
@@ -393,21 +396,47 @@ __global__ void __launch_bounds__(256) k_validate_vertices(GraphView g, uint32_t
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t C = g.C;
+    const uint32_t R = 1u << g.rs;
+    const unsigned long long H = g.rs ? (g.RP << g.rs) : 0ull;  // run region [0, H)
     unsigned long long viol = 0, sdeg = 0, snb = 0;
     for (uint32_t u = warp; u < g.nv; u += nwarps) {
         const uint4 s = g.sent[u];
         const uint32_t deg = s.x, nb = s.y;
+        const bool run = is_run(s.z);
+        const uint32_t nr = run ? (nb + R - 1u) >> g.rs : 0u;
         if (lane == 0) {
             sdeg += deg;
-            snb += nb;
+            snb += run ? (unsigned long long)nr << g.rs : nb;  // blocks owned
             if (C == 0 ? (deg != 0 || nb != 0) : (nb != (deg + C - 1) / C)) ++viol;
             if (!g.alive[u] && (deg != 0 || nb != 0)) ++viol;
             if (nb == 0 && (s.z != NIL || s.w != NIL)) ++viol;
+            if (run && g.rs == 0) ++viol;
+        }
+        if (run) {
+            // tree of run heads: each head R-aligned inside the run region,
+            // all R blocks of each run owned once, the last block in the last run
+            const uint32_t head0 = s.z & ~RUN_BIT;
+            for (uint32_t k = 1 + lane; k <= nr; k += 32) {
+                bool bad = false;
+                const uint32_t h = cbt_walk_checked(g.links, g.P, head0, k, bad);
+                if (bad || h >= H || (h & (R - 1u))) {
+                    ++viol;
+                    continue;
+                }
+                for (uint32_t i = 0; i < R; ++i) {
+                    const uint32_t b = h + i, bit = 1u << (b & 31u);
+                    if (atomicOr(&owner[b >> 5], bit) & bit) ++viol;
+                }
+                if (k == nr && s.w != h + ((nb - 1u) & (R - 1u))) ++viol;
+                if (2ull * k > nr && g.links[2ull * h] != NIL) ++viol;
+                if (2ull * k + 1 > nr && g.links[2ull * h + 1] != NIL) ++viol;
+            }
+            continue;
         }
         for (uint32_t k = 1 + lane; k <= nb; k += 32) {
             bool bad = false;
             const uint32_t b = cbt_walk_checked(g.links, g.P, s.z, k, bad);
-            if (bad) {
+            if (bad || b < H) {  // a plain adjacency's blocks lie outside the run region
                 ++viol;
                 continue;
             }
@@ -433,17 +462,37 @@ __global__ void __launch_bounds__(256) k_validate_queue(GraphView g, uint32_t *o
     pdl_wait();
     const unsigned long long qf = g.dev->q_front, qb = g.dev->q_back, P = g.P;
     if (P == 0) return;
+    const unsigned long long H = g.rs ? (g.RP << g.rs) : 0ull;
     unsigned long long viol = 0, cnt = 0;
     for (unsigned long long p = qf + blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; p < qb;
          p += (unsigned long long)gridDim.x * blockDim.x) {
         const uint32_t b = g.queue[p % P];
         ++cnt;
-        if (b >= P) {
+        if (b >= P || b < H) {
             ++viol;
             continue;
         }
         const uint32_t bit = 1u << (b & 31u);
         if (atomicOr(&owner[b >> 5], bit) & bit) ++viol;
+    }
+    if (g.rs) {
+        // free runs: R-aligned heads inside the run region, each covering R
+        // blocks that nothing else owns
+        const uint32_t R = 1u << g.rs;
+        const unsigned long long rqf = g.dev->rq_front, rqb = g.dev->rq_back;
+        for (unsigned long long p = rqf + blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; p < rqb;
+             p += (unsigned long long)gridDim.x * blockDim.x) {
+            const uint32_t h = g.rqueue[p % g.RP];
+            if (h >= H || (h & (R - 1u))) {
+                ++viol;
+                continue;
+            }
+            cnt += R;
+            for (uint32_t i = 0; i < R; ++i) {
+                const uint32_t b = h + i, bit = 1u << (b & 31u);
+                if (atomicOr(&owner[b >> 5], bit) & bit) ++viol;
+            }
+        }
     }
     viol = warp_sum_u64(viol);
     cnt = warp_sum_u64(cnt);
@@ -467,8 +516,9 @@ cudaError_t launch_copy_dictionary(uint4 *dst_sent, uint8_t *dst_alive, const ui
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_queue(uint32_t *queue, unsigned long long P, const LaunchCfg &lc) {
-    k_init_queue<<<grid_for(P, 256, lc.num_sms * 16), 256, 0, lc.stream>>>(queue, P);
+cudaError_t launch_init_queue(uint32_t *queue, unsigned long long n, const LaunchCfg &lc, uint32_t first,
+                              uint32_t step) {
+    if (n) k_init_queue<<<grid_for(n, 256, lc.num_sms * 16), 256, 0, lc.stream>>>(queue, n, first, step);
     return cudaGetLastError();
 }
 

@@ -40,6 +40,9 @@ class gv_config(ctypes.Structure):
         ("vertex_capacity", c_u32),
         ("item_blocks", c_u32),
         ("dense_shift", c_u32),
+        ("hub_shift", c_u32),
+        ("hub_degree", c_u32),
+        ("hub_percent", c_u32),
         ("reserved", c_u32),
     ]
 
@@ -60,7 +63,9 @@ class gv_stats_t(ctypes.Structure):
         ("total_deleted", c_u64),
         ("total_rejected", c_u64),
         ("device_status", c_u32),
-        ("reserved", c_u32),
+        ("hub_shift", c_u32),
+        ("pool_runs", c_u64),
+        ("pool_runs_free", c_u64),
     ]
 
     def as_dict(self):
@@ -178,8 +183,9 @@ def current_stream():
 # -------------------------------------------------------- C-named wrappers
 
 def gv_create(num_vertices, block_capacity=0, pool_bytes=0, pool_mem=None, flags=0, vertex_capacity=0,
-              stream=None, item_blocks=0, dense_shift=0):
-    cfg = gv_config(block_capacity, flags, pool_bytes, ptr(pool_mem), vertex_capacity, item_blocks, dense_shift, 0)
+              stream=None, item_blocks=0, dense_shift=0, hub_shift=0, hub_degree=0, hub_percent=0):
+    cfg = gv_config(block_capacity, flags, pool_bytes, ptr(pool_mem), vertex_capacity, item_blocks, dense_shift,
+                    hub_shift, hub_degree, hub_percent, 0)
     h = c_vp()
     check(load().gv_create(ctypes.byref(cfg), num_vertices, stream, ctypes.byref(h)), "gv_create")
     return h.value
@@ -338,7 +344,7 @@ class GraphSet:
         nv = np.ascontiguousarray(num_vertices, dtype=np.uint32)
         self.num_vertices = nv
         self.stream = stream
-        cfg = gv_config(block_capacity, 0, pool_bytes, None, 0, item_blocks, dense_shift, 0)
+        cfg = gv_config(block_capacity, 0, pool_bytes, None, 0, item_blocks, dense_shift, 0, 0, 0, 0)
         h = c_vp()
         check(load().gv_set_create(ctypes.byref(cfg), nv.size, nv.ctypes.data, self._s(), ctypes.byref(h)),
               "gv_set_create")
@@ -409,11 +415,12 @@ class Graph:
     """A device-resident GraphVine graph (see include/graphvine.h)."""
 
     def __init__(self, num_vertices, block_capacity=0, pool_bytes=0, pool_mem=None, flags=0,
-                 vertex_capacity=0, stream=None, item_blocks=0, dense_shift=0):
+                 vertex_capacity=0, stream=None, item_blocks=0, dense_shift=0, hub_shift=0, hub_degree=0,
+                 hub_percent=0):
         self.stream = stream
         self._pool_ref = pool_mem  # keep a caller-owned pool alive
         self.handle = gv_create(num_vertices, block_capacity, pool_bytes, pool_mem, flags, vertex_capacity,
-                                self._s(), item_blocks, dense_shift)
+                                self._s(), item_blocks, dense_shift, hub_shift, hub_degree, hub_percent)
 
     def _s(self):
         if self.stream is not None:
