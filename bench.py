@@ -40,6 +40,7 @@ C = 16
 BLOCK = C
 POOL_BYTES = 2 << 30
 SEED = 2
+HUB_SHIFT = 4
 
 
 def parse():
@@ -66,6 +67,9 @@ def parse():
                          "measured workload, smaller scales are for profiling captures")
     ap.add_argument("--grouping", default="atomic", choices=["atomic", "radix"],
                     help="grouping of large batches: one atomic per pair (default) or the radix partition")
+    ap.add_argument("--hub-shift", type=int, default=HUB_SHIFT,
+                    help="the hub-runs record: runs of 2^s blocks for vertices whose first allocation takes "
+                         "at least C * 2^s entries (0 skips the record)")
     return ap.parse_args()
 
 
@@ -583,6 +587,96 @@ def run_ours(args, rank, world, local_rank):
     }
     g.close()
     return res, (base, upd, qry)
+
+
+def hub_record(args, dev, base, upd, qry, plain):
+    """The same step on a graph whose hubs hold their blocks in runs of
+    2^s blocks (a per-vertex block size): steps timed as in the main
+    record, the per-kernel phases of a second pass, and the compaction-heavy
+    delete; counts must equal the plain graph's."""
+    import torch
+    import paper_2306_08252_gb300 as gv
+    rs = args.hub_shift
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(dev)
+    d_bs, d_bd = t(base[0]), t(base[1])
+    d_s, d_d = t(upd[0]), t(upd[1])
+    d_qs, d_qd = t(qry[0]), t(qry[1])
+    d_out = torch.zeros(args.queries, dtype=torch.uint8, device=dev)
+    counts = torch.zeros(4, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def make():
+        g = gv.Graph(1 << SCALE, block_capacity=C, pool_bytes=POOL_BYTES, hub_shift=rs)
+        g.reserve(max(args.batch, BASE_EDGES))
+        g.bulk_build(d_bs, d_bd)
+        return g
+
+    g = make()
+    st = g.stats()
+    deg, _ = g.degrees()
+    d64 = deg.astype(np.int64)
+    hub = d64 >= (C << rs)  # every vertex's first allocation was the bulk build
+    owned_plain = int(((d64 + C - 1) // C).sum())
+
+    def step():
+        g.insert_edges(d_s, d_d, counts[:2])
+        g.query_edges(d_qs, d_qd, d_out)
+        g.delete_edges(d_s, d_d, counts[2:])
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    assert g.sync() == 0
+    assert (int(counts[0]), int(counts[2])) == (plain["inserted"], plain["deleted"])
+    steps = max(args.steps // 2, 5)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    g.profile_read()
+    g.profile(True)
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        step()
+    torch.cuda.synchronize()
+    g.profile(False)
+    phases = {k: v[0] / steps for k, v in g.profile_read().items() if v[1]}
+    assert g.sync() == 0 and g.validate() == 0
+    g.close()
+    heavy = []
+    for r in range(3):
+        g2 = make()
+        g2.insert_edges(d_s, d_d)
+        flush.fill_(r & 0xFF)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g2.delete_edges(d_s, d_d, counts[2:])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        heavy.append(e0.elapsed_time(e1))
+        assert int(counts[2]) == plain["heavy_deleted"] and g2.sync() == 0
+        g2.close()
+    step_ms = statistics.median(ms)
+    hv = statistics.median(heavy)
+    keys = ("delete.mark", "delete.mark_tiny", "delete.move", "query.mark", "insert.link", "insert.scatter")
+    return {"hub_shift": rs, "hub_degree": C << rs, "run_blocks": 1 << rs,
+            "hub_vertices": int(hub.sum()), "hub_entries_share": float(d64[hub].sum() / max(d64.sum(), 1)),
+            "max_tree_height_plain": int(np.ceil(np.log2(max(1, (d64.max() + C - 1) // C)))) + 1,
+            "max_tree_height_runs": int(np.ceil(np.log2(max(1, -(-((d64.max() + C - 1) // C) // (1 << rs)))))) + 1,
+            "pool_blocks_used_after_build": st["pool_blocks_used"], "blocks_plain_layout": owned_plain,
+            "ms_per_step": step_ms, "value": (plain["inserted"] + plain["deleted"]) / (step_ms / 1e3), "unit": UNIT,
+            "vs_plain_ms_per_step": plain["p50_ms"], "steps": steps,
+            "phases_ms_per_step": {k: phases[k] for k in keys if k in phases},
+            "plain_phases_ms_per_step": {k: plain["phases"][k] for k in keys if k in plain["phases"]},
+            "delete_compaction_heavy_ms": hv, "plain_delete_compaction_heavy_ms": plain["heavy_ms"],
+            "counts_match_plain": True,
+            "timer": "CUDA events around each step (median), L2 flushed before each; phases from a second pass"}
 
 
 def run_batched(args):
@@ -1222,6 +1316,12 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     res, (base, upd, qry) = run_ours(args, rank, world, local_rank)
+    if world == 1 and args.hub_shift:
+        plain = {"inserted": res["counts_per_step"]["inserted"], "deleted": res["counts_per_step"]["deleted"],
+                 "p50_ms": res["p50_ms"], "phases": res["phases_ms_per_step"],
+                 "heavy_ms": res["delete_compaction_heavy"]["ms"],
+                 "heavy_deleted": res["delete_compaction_heavy"]["deleted"]}
+        res["hub_runs"] = hub_record(args, torch.device("cuda", local_rank), base, upd, qry, plain)
     if world == 1 and not args.no_batched:
         # the batched form, short: the 256-member workload, 3 steps, the
         # autotuner's usual configuration (no tuning pass)
