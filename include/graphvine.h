@@ -147,8 +147,11 @@ typedef struct gv_config {
      * of the pool's blocks, rounded down to whole runs, form the run region,
      * with its own queue of free runs; an insert that needs more runs than
      * are free fails like an exhausted pool (GV_ERR_OUT_OF_MEMORY, nothing
-     * changes).  Results never depend on the setting.  Excludes GV_GROW,
-     * GV_RADIX_GROUPING, graph sets and gv_reblock; block ids stay below
+     * changes).  gv_reblock re-decides every vertex: after it, exactly the
+     * vertices of degree >= the threshold (at the new C) are hubs, so it also
+     * serves to promote vertices that grew past the threshold after their
+     * first allocation.  Results never depend on the setting.  Excludes
+     * GV_GROW, GV_RADIX_GROUPING and graph sets; block ids stay below
      * 2^31 - 1 (the pool is capped there). */
     uint32_t hub_shift;
     uint32_t hub_degree;
@@ -495,6 +498,11 @@ gv_status gv_degree_offsets_noalloc(gv_graph *g, const uint32_t *d_vids, uint32_
  * the graph's delete/query scratch, plus 12 bytes per vertex in its staging
  * buffers; like all of the graph's scratch it grows when needed and is kept
  * until gv_destroy.
+ * With hub runs (gv_config.hub_shift), the run region is laid out again
+ * for the new C with the same share of the pool; every vertex whose degree
+ * reaches the hub threshold at the new C (hub_degree, or C * 2^s) gets its
+ * blocks as whole runs there, every other vertex as plain blocks outside
+ * it; GV_ERR_OUT_OF_MEMORY (nothing changed) if either part does not fit.
  * Synchronises `stream` (it reads the degree totals).
  */
 #define GV_REBLOCK_MIN_FOOTPRINT 1u

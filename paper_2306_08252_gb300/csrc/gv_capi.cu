@@ -1365,7 +1365,6 @@ gv_status gv_reblock(gv_graph *g, uint32_t block_capacity, uint32_t *h_block_cap
     DeviceGuard dg(g->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (g->C == 0) return GV_ERR_STATE;  // nothing laid out yet: the first edge batch fixes C
-    if (g->rs) return GV_ERR_STATE;     // a graph with hub runs keeps its layout
     // a latched device error is reported first; nothing changes
     GV_CK(cudaStreamSynchronize(g->last_stream));
     g->last_stream = s;
@@ -1401,10 +1400,21 @@ gv_status gv_reblock(gv_graph *g, uint32_t block_capacity, uint32_t *h_block_cap
         GV_CK(cudaStreamSynchronize(s));
         C2 = rule_capacity(g->h_small[0], g->h_small[1]);
     }
-    const unsigned long long P2 = fit_blocks(g->pool_bytes, C2, weighted);
+    unsigned long long P2 = fit_blocks(g->pool_bytes, C2, weighted);
+    // hub runs: the run region is laid out again for C2 (the same share of
+    // the pool), and every vertex of degree >= T2 (the hub threshold at C2)
+    // becomes a hub, every other vertex a plain one
+    const bool hubs = g->rs != 0;
+    if (hubs && P2 > 0x7FFFFFFEull) P2 = 0x7FFFFFFEull;
+    const unsigned long long RP2 = hubs ? (P2 * g->hub_pct / 100) >> g->rs : 0ull;
+    const unsigned long long H2 = RP2 << g->rs;
+    const uint32_t T2 = hubs ? (g->hub_deg_cfg ? g->hub_deg_cfg : C2 << g->rs) : 0xFFFFFFFFu;
+    if (hubs && RP2 == 0) return GV_ERR_OUT_OF_MEMORY;
 
     // 2. slot offsets of the new layout (each vertex's degree rounded up to
-    // whole blocks of C2): the run of u starts at block slots[u] / C2.
+    // whole blocks of C2): the run of u starts at block slots[u] / C2.  With
+    // hub runs the scratch holds the hubs' runs (whole runs of 2^s blocks)
+    // first, then the plain vertices'.
     // Scratch is the graph's own, kept between calls: the vertex list and
     // the run offsets in staging buffers, the new slots (and payloads) in the
     // membership arena and its parallel array (per-call scratch of deletes
@@ -1424,13 +1434,33 @@ gv_status gv_reblock(gv_graph *g, uint32_t block_capacity, uint32_t *h_block_cap
     void *ds = nullptr;
     GV_TRY(stage_buf(g, 1, ((size_t)n + 1) * 8, &ds));
     slots = static_cast<unsigned long long *>(ds);
-    GV_CK(gv::launch_neighbor_offsets(view(g), (const uint32_t *)dv, n, slots, g->partials, lcfg(g, s), C2));
-    GV_CK(cudaMemcpyAsync(&g->h_small[0], slots + n, 8, cudaMemcpyDeviceToHost, s));
-    GV_CK(cudaStreamSynchronize(s));
-    const unsigned long long T = g->h_small[0];  // slots of the new layout
+    unsigned long long T = 0, hub_total = 0;  // slots of the new layout, of its hubs' runs
+    if (!hubs) {
+        GV_CK(gv::launch_neighbor_offsets(view(g), (const uint32_t *)dv, n, slots, g->partials, lcfg(g, s), C2));
+        GV_CK(cudaMemcpyAsync(&g->h_small[0], slots + n, 8, cudaMemcpyDeviceToHost, s));
+        GV_CK(cudaStreamSynchronize(s));
+        T = g->h_small[0];
+    } else {
+        void *dh = nullptr;
+        GV_TRY(stage_buf(g, 2, ((size_t)n + 1) * 8, &dh));
+        unsigned long long *hslots = static_cast<unsigned long long *>(dh);
+        GV_CK(gv::launch_reblock_offsets(view(g), (const uint32_t *)dv, n, hslots, g->partials, lcfg(g, s), C2, true,
+                                         T2, g->rs));
+        GV_CK(cudaMemcpyAsync(&g->h_small[0], hslots + n, 8, cudaMemcpyDeviceToHost, s));
+        GV_CK(gv::launch_reblock_offsets(view(g), (const uint32_t *)dv, n, slots, g->partials, lcfg(g, s), C2, false,
+                                         T2, g->rs));
+        GV_CK(cudaMemcpyAsync(&g->h_small[1], slots + n, 8, cudaMemcpyDeviceToHost, s));
+        GV_CK(cudaStreamSynchronize(s));
+        hub_total = g->h_small[0];
+        T = hub_total + g->h_small[1];
+        GV_CK(gv::launch_reblock_merge(view(g), slots, hslots, T2, hub_total, lcfg(g, s)));
+    }
     const unsigned long long nb2 = T / C2;
-    // the entries must fit the pool at this block size
+    const unsigned long long hb2 = hub_total / C2;  // blocks in runs
+    // the entries must fit the pool at this block size (with hub runs: the
+    // plain blocks outside the run region, the hubs' runs inside it)
     if (nb2 > P2 || nb2 > 0xFFFFFFFEull) return GV_ERR_OUT_OF_MEMORY;
+    if (hubs && (nb2 - hb2 > P2 - H2 || hb2 > H2)) return GV_ERR_OUT_OF_MEMORY;
 
     // 3. every entry (and payload) copied to its place in the new layout,
     // read through the old trees
@@ -1446,20 +1476,41 @@ gv_status gv_reblock(gv_graph *g, uint32_t block_capacity, uint32_t *h_block_cap
 
     // 4. the same pool memory laid out for C2: slots back in place, trees
     // and sentinels over the runs, the queue holding the blocks past them
+    uint32_t *rq2 = nullptr;  // the run queue at the new size, allocated before the pool changes
+    if (hubs && RP2 > g->RP) GV_TRY(dalloc(&rq2, RP2, &g->scratch_bytes));
     char *base = reinterpret_cast<char *>(g->data);
     if (!lay_out_pool(g, base, g->pool_bytes, C2, P2)) return GV_ERR_STATE;  // cannot happen: P2 was fitted
     set_item_blocks(g);
+    if (rq2) {
+        dfree(g->rqueue);
+        g->rqueue = rq2;
+    }
+    if (hubs) g->RP = RP2;
     const GraphView v = view(g);
     bool ok = true;
-    if (T) ok = ok && cudaMemcpyAsync(g->data, nd, T * 4ull, cudaMemcpyDeviceToDevice, s) == cudaSuccess;
-    if (T && weighted) ok = ok && cudaMemcpyAsync(g->wdata, nw, T * 4ull, cudaMemcpyDeviceToDevice, s) == cudaSuccess;
+    // hubs' runs at block 0 (the run region), the plain vertices' from block H2
+    const unsigned long long hs = hb2 * C2, ps = T - hs, pdst = H2 * C2;
+    if (hs) ok = ok && cudaMemcpyAsync(g->data, nd, hs * 4ull, cudaMemcpyDeviceToDevice, s) == cudaSuccess;
+    if (ps) ok = ok && cudaMemcpyAsync(g->data + pdst, nd + hs, ps * 4ull, cudaMemcpyDeviceToDevice, s) == cudaSuccess;
+    if (hs && weighted) ok = ok && cudaMemcpyAsync(g->wdata, nw, hs * 4ull, cudaMemcpyDeviceToDevice, s) == cudaSuccess;
+    if (ps && weighted)
+        ok = ok && cudaMemcpyAsync(g->wdata + pdst, nw + hs, ps * 4ull, cudaMemcpyDeviceToDevice, s) == cudaSuccess;
     // long runs are listed in the touched-vertex scratch (n entries), counted in rb_stats[0]
-    ok = ok && gv::launch_reblock_place(v, slots, g->t_vid, g->rb_stats, lcfg(g, s)) == cudaSuccess;
-    ok = ok && gv::launch_init_queue(g->queue, P2, lcfg(g, s)) == cudaSuccess;
-    g->h_small[2] = nb2;
-    g->h_small[3] = P2;
+    ok = ok && gv::launch_reblock_place(v, slots, g->t_vid, g->rb_stats, lcfg(g, s), T2, pdst - hs) == cudaSuccess;
+    // the edge queue: the blocks past the plain runs (outside the run
+    // region); the run queue: the runs past the hubs'
+    ok = ok && gv::launch_init_queue(g->queue, P2 - H2, lcfg(g, s), (uint32_t)H2, 1u) == cudaSuccess;
+    g->h_small[2] = nb2 - hb2;
+    g->h_small[3] = P2 - H2;
     ok = ok && cudaMemcpyAsync(&g->dev->q_front, &g->h_small[2], 8, cudaMemcpyHostToDevice, s) == cudaSuccess;
     ok = ok && cudaMemcpyAsync(&g->dev->q_back, &g->h_small[3], 8, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    if (hubs) {
+        ok = ok && gv::launch_init_queue(g->rqueue, RP2, lcfg(g, s), 0u, 1u << g->rs) == cudaSuccess;
+        g->h_small[4] = hb2 >> g->rs;
+        g->h_small[5] = RP2;
+        ok = ok && cudaMemcpyAsync(&g->dev->rq_front, &g->h_small[4], 8, cudaMemcpyHostToDevice, s) == cudaSuccess;
+        ok = ok && cudaMemcpyAsync(&g->dev->rq_back, &g->h_small[5], 8, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    }
     ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
     if (!ok) return GV_ERR_CUDA;
     g->used_ub = nb2;

@@ -179,8 +179,19 @@ cudaError_t launch_degree_stats(const GraphView &g, unsigned long long *res, con
 cudaError_t launch_footprint_blocks(const GraphView &g, unsigned long long *res, const LaunchCfg &lc);
 // big: scratch of one id per vertex (the runs longer than a thread writes
 // alone), nbig: one counter
+// T: degree from which a vertex is placed in runs (hub runs on), plain_shift:
+// added to a plain vertex's slot offset to give its place in the pool
 cudaError_t launch_reblock_place(const GraphView &g, const unsigned long long *slots, uint32_t *big,
-                                 unsigned long long *nbig, const LaunchCfg &lc);
+                                 unsigned long long *nbig, const LaunchCfg &lc, uint32_t T = 0xFFFFFFFFu,
+                                 unsigned long long plain_shift = 0ull);
+cudaError_t launch_reblock_merge(const GraphView &g, unsigned long long *plain_off, const unsigned long long *hub_off,
+                                 uint32_t T, unsigned long long hub_total, const LaunchCfg &lc);
+// Slot offsets of the edge-block resize of a graph with hub runs: over the
+// plain vertices (degree < T, rounded to round_to) or over the hubs (rounded
+// to whole runs of round_to << rs slots); offsets[n] = total.
+cudaError_t launch_reblock_offsets(const GraphView &g, const uint32_t *vids, uint32_t n, unsigned long long *offsets,
+                                   unsigned long long *partials, const LaunchCfg &lc, uint32_t round_to, bool hubs,
+                                   uint32_t T, uint32_t rs);
 cudaError_t launch_neighbor_copy(const GraphView &g, const uint32_t *vids, uint32_t n,
                                  const unsigned long long *offsets, uint32_t *nbrs,
                                  const LaunchCfg &lc,

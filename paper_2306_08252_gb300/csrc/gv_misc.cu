@@ -59,16 +59,32 @@ __device__ __forceinline__ unsigned long long vid_degree(const GraphView &g, uin
     return round_to ? (d + round_to - 1) / round_to * round_to : d;
 }
 
+// Slots a requested vertex takes in a layout: SEL 0 its degree rounded as
+// above; for the edge-block resize of a graph with hub runs, SEL 1 the same
+// for a plain vertex (degree below T) and 0 for a hub, SEL 2 a hub's degree
+// rounded up to whole runs (round_to << rs slots) and 0 for a plain vertex.
+template <int SEL>
+__device__ __forceinline__ unsigned long long vid_size(const GraphView &g, uint32_t u, uint32_t round_to,
+                                                       uint32_t T, uint32_t rs) {
+    if (SEL == 0) return vid_degree(g, u, round_to);
+    const unsigned long long d = vid_degree(g, u, 0);
+    const bool hub = d > 0 && d >= T;
+    if (SEL == 1 ? hub : !hub) return 0ull;
+    const unsigned long long r = SEL == 2 ? (unsigned long long)round_to << rs : round_to;
+    return (d + r - 1) / r * r;
+}
+
 // Per-chunk sums of the requested vertices' degrees.
+template <int SEL>
 __global__ void __launch_bounds__(SCAN_T) k_nbr_partials(GraphView g, const uint32_t *__restrict__ vids,
-                                                         uint32_t n, uint32_t round_to,
+                                                         uint32_t n, uint32_t round_to, uint32_t T, uint32_t rs,
                                                          unsigned long long *partials) {
     pdl_wait();
     const uint32_t chunk = blockIdx.x;
     unsigned long long s = 0;
     for (int j = 0; j < SCAN_PER; ++j) {
         const uint32_t i = chunk * SCAN_CHUNK + j * SCAN_T + threadIdx.x;
-        if (i < n) s += vid_degree(g, vids[i], round_to);
+        if (i < n) s += vid_size<SEL>(g, vids[i], round_to, T, rs);
     }
     s = block_sum_u64(s);
     if (threadIdx.x == 0) partials[chunk] = s;
@@ -112,8 +128,9 @@ __global__ void __launch_bounds__(1024) k_nbr_scan_partials(unsigned long long *
 }
 
 // offsets[i] = chunk prefix + exclusive scan inside the chunk; offsets[n] = total.
+template <int SEL>
 __global__ void __launch_bounds__(SCAN_T) k_nbr_apply(GraphView g, const uint32_t *__restrict__ vids,
-                                                      uint32_t n, uint32_t round_to,
+                                                      uint32_t n, uint32_t round_to, uint32_t T, uint32_t rs,
                                                       const unsigned long long *partials,
                                                       uint32_t nchunks, unsigned long long *offsets) {
     pdl_wait();
@@ -123,7 +140,7 @@ __global__ void __launch_bounds__(SCAN_T) k_nbr_apply(GraphView g, const uint32_
     unsigned long long s = 0;
     for (int j = 0; j < SCAN_PER; ++j) {
         const uint32_t i = chunk * SCAN_CHUNK + threadIdx.x * SCAN_PER + j;
-        v[j] = i < n ? vid_degree(g, vids[i], round_to) : 0ull;
+        v[j] = i < n ? vid_size<SEL>(g, vids[i], round_to, T, rs) : 0ull;
         s += v[j];
     }
     __shared__ unsigned long long s_w[SCAN_T / 32];
@@ -312,24 +329,38 @@ cudaError_t launch_footprint_blocks(const GraphView &g, unsigned long long *res,
 // spreads each over a whole CTA.
 constexpr uint32_t PLACE_SMALL = 32;
 
+//
+// With hub runs (g.rs != 0) a vertex of degree >= T is a hub: its run starts
+// at slots[u] (R-aligned: hubs fill the run region from block 0 in whole
+// runs) and its tree is one of run heads, the head of run k (1-based) being
+// block base + (k - 1) * R; every other vertex's run starts at slots[u] +
+// plain_shift (the scratch placed the hubs first, the pool puts the plain
+// vertices past the run region).
+__device__ __forceinline__ void place_links(const GraphView &g, uint32_t base, uint32_t n, uint32_t stride,
+                                            uint32_t k) {
+    const uint32_t b = base + (k - 1) * stride;
+    g.links[2ull * b] = 2ull * k <= n ? base + (2 * k - 1) * stride : NIL;
+    g.links[2ull * b + 1] = 2ull * k + 1 <= n ? base + 2 * k * stride : NIL;
+}
+
 __global__ void __launch_bounds__(256) k_reblock_place(GraphView g, const unsigned long long *__restrict__ slots,
-                                                       uint32_t *big, unsigned long long *nbig) {
+                                                       uint32_t *big, unsigned long long *nbig, uint32_t T,
+                                                       unsigned long long plain_shift) {
     pdl_wait();
     const uint32_t C = g.C;
     for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < g.nv; u += gridDim.x * blockDim.x) {
         const uint32_t deg = g.alive[u] ? g.sent[u].x : 0u;
         const uint32_t nb = (deg + C - 1) / C;
-        const uint32_t base = (uint32_t)(slots[u] / C);
-        g.sent[u] = make_uint4(deg, nb, nb ? base : NIL, nb ? base + nb - 1 : NIL);
-        if (nb > PLACE_SMALL) {
+        const bool hub = g.rs && deg > 0 && deg >= T;
+        const uint32_t base = (uint32_t)((hub ? slots[u] : slots[u] + plain_shift) / C);
+        const uint32_t stride = hub ? 1u << g.rs : 1u;          // heads of runs, or blocks
+        const uint32_t n = hub ? (nb + stride - 1) >> g.rs : nb;  // tree nodes
+        g.sent[u] = make_uint4(deg, nb, nb ? (hub ? base | RUN_BIT : base) : NIL, nb ? base + nb - 1 : NIL);
+        if (n > PLACE_SMALL) {
             big[atomicAdd(nbig, 1ull)] = u;
             continue;
         }
-        for (uint32_t k = 1; k <= nb; ++k) {
-            const uint32_t b = base + k - 1;
-            g.links[2ull * b] = 2 * k <= nb ? base + 2 * k - 1 : NIL;
-            g.links[2ull * b + 1] = 2 * k + 1 <= nb ? base + 2 * k : NIL;
-        }
+        for (uint32_t k = 1; k <= n; ++k) place_links(g, base, n, stride, k);
     }
 }
 
@@ -338,18 +369,36 @@ __global__ void __launch_bounds__(256) k_reblock_big(GraphView g, const unsigned
                                                      const uint32_t *__restrict__ big,
                                                      const unsigned long long *nbig) {
     pdl_wait();
-    const uint32_t C = g.C;
     const uint32_t n = (uint32_t)*nbig;
     for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
         const uint32_t u = big[i];
-        const uint32_t nb = g.sent[u].y;
-        const uint32_t base = (uint32_t)(slots[u] / C);
-        for (uint32_t k = 1 + threadIdx.x; k <= nb; k += blockDim.x) {
-            const uint32_t b = base + k - 1;
-            g.links[2ull * b] = 2ull * k <= nb ? base + 2 * k - 1 : NIL;
-            g.links[2ull * b + 1] = 2ull * k + 1 <= nb ? base + 2 * k : NIL;
-        }
+        const uint4 st = g.sent[u];  // written by k_reblock_place
+        const bool hub = is_run(st.z);
+        const uint32_t base = st.z & ~RUN_BIT;
+        const uint32_t stride = hub ? 1u << g.rs : 1u;
+        const uint32_t nodes = hub ? (st.y + stride - 1) >> g.rs : st.y;
+        for (uint32_t k = 1 + threadIdx.x; k <= nodes; k += blockDim.x) place_links(g, base, nodes, stride, k);
     }
+}
+
+// Edge-block resize of a graph with hub runs: one scratch offset per vertex,
+// the hubs' runs first (hub_off), the plain vertices' runs after them
+// (hub_total + plain_off), written over plain_off.
+__global__ void __launch_bounds__(256) k_reblock_merge(GraphView g, unsigned long long *plain_off,
+                                                       const unsigned long long *__restrict__ hub_off, uint32_t T,
+                                                       unsigned long long hub_total) {
+    pdl_wait();
+    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < g.nv; u += gridDim.x * blockDim.x) {
+        const uint32_t deg = g.alive[u] ? g.sent[u].x : 0u;
+        plain_off[u] = (deg > 0 && deg >= T) ? hub_off[u] : hub_total + plain_off[u];
+    }
+}
+
+cudaError_t launch_reblock_merge(const GraphView &g, unsigned long long *plain_off, const unsigned long long *hub_off,
+                                 uint32_t T, unsigned long long hub_total, const LaunchCfg &lc) {
+    if (g.nv) k_reblock_merge<<<grid_for(g.nv, 256, lc.num_sms * 16), 256, 0, lc.stream>>>(g, plain_off, hub_off, T,
+                                                                                            hub_total);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_degree_stats(const GraphView &g, unsigned long long *res, const LaunchCfg &lc) {
@@ -359,10 +408,12 @@ cudaError_t launch_degree_stats(const GraphView &g, unsigned long long *res, con
 }
 
 cudaError_t launch_reblock_place(const GraphView &g, const unsigned long long *slots, uint32_t *big,
-                                 unsigned long long *nbig, const LaunchCfg &lc) {
+                                 unsigned long long *nbig, const LaunchCfg &lc, uint32_t T,
+                                 unsigned long long plain_shift) {
     cudaMemsetAsync(nbig, 0, sizeof(unsigned long long), lc.stream);
     if (g.nv) {
-        k_reblock_place<<<grid_for(g.nv, 256, lc.num_sms * 16), 256, 0, lc.stream>>>(g, slots, big, nbig);
+        k_reblock_place<<<grid_for(g.nv, 256, lc.num_sms * 16), 256, 0, lc.stream>>>(g, slots, big, nbig, T,
+                                                                                      plain_shift);
         launch_pdl(k_reblock_big, lc.num_sms * 4, 256, 0, lc.stream, g, slots, big, nbig);
     }
     return cudaGetLastError();
@@ -560,9 +611,32 @@ cudaError_t launch_neighbor_offsets(const GraphView &g, const uint32_t *vids, ui
         return e;
     }
     PhaseScope ps(lc, PH_NEIGHBORS);
-    k_nbr_partials<<<nchunks, SCAN_T, 0, lc.stream>>>(g, vids, n, round_to, partials);
+    k_nbr_partials<0><<<nchunks, SCAN_T, 0, lc.stream>>>(g, vids, n, round_to, 0u, 0u, partials);
     launch_pdl(k_nbr_scan_partials, 1, 1024, 0, lc.stream, partials, nchunks);
-    launch_pdl(k_nbr_apply, nchunks, SCAN_T, 0, lc.stream, g, vids, n, round_to, partials, nchunks, offsets);
+    launch_pdl(k_nbr_apply<0>, nchunks, SCAN_T, 0, lc.stream, g, vids, n, round_to, 0u, 0u, partials, nchunks,
+               offsets);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reblock_offsets(const GraphView &g, const uint32_t *vids, uint32_t n, unsigned long long *offsets,
+                                   unsigned long long *partials, const LaunchCfg &lc, uint32_t round_to, bool hubs,
+                                   uint32_t T, uint32_t rs) {
+    const uint32_t nchunks = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    if (nchunks == 0) {
+        cudaError_t e = cudaMemsetAsync(offsets, 0, sizeof(unsigned long long), lc.stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(partials, 0, sizeof(unsigned long long), lc.stream);
+        return e;
+    }
+    PhaseScope ps(lc, PH_OTHER);
+    if (hubs) k_nbr_partials<2><<<nchunks, SCAN_T, 0, lc.stream>>>(g, vids, n, round_to, T, rs, partials);
+    else k_nbr_partials<1><<<nchunks, SCAN_T, 0, lc.stream>>>(g, vids, n, round_to, T, rs, partials);
+    launch_pdl(k_nbr_scan_partials, 1, 1024, 0, lc.stream, partials, nchunks);
+    if (hubs)
+        launch_pdl(k_nbr_apply<2>, nchunks, SCAN_T, 0, lc.stream, g, vids, n, round_to, T, rs, partials, nchunks,
+                   offsets);
+    else
+        launch_pdl(k_nbr_apply<1>, nchunks, SCAN_T, 0, lc.stream, g, vids, n, round_to, T, rs, partials, nchunks,
+                   offsets);
     return cudaGetLastError();
 }
 

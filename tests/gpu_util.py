@@ -99,6 +99,18 @@ class Pair:
         self.g.query_edges(dev_u32(s), dev_u32(d), out)
         np.testing.assert_array_equal(out.cpu().numpy(), self.o.query_edges(s, d))
 
+    def reblock(self, C2):
+        """Edge-block resize; with hub runs every vertex is re-decided: a hub
+        iff its degree reaches the threshold at the new C."""
+        c = self.g.reblock(C2)
+        self.C = c
+        if self.rs:
+            d = self.o.degrees().astype(np.int64)
+            T = self.hub_degree or (c << self.rs)
+            self.hub = np.zeros(max(d.size, self.hub.size), dtype=bool)
+            self.hub[:d.size] = (d > 0) & (d >= T)
+        return c
+
     def vdel(self, ids):
         before = self.o.degrees().astype(np.int64)
         self.g.delete_vertices(dev_u32(ids))

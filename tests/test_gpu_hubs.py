@@ -11,7 +11,6 @@ in tests/gpu_util.Pair."""
 import numpy as np
 import pytest
 
-import oracle
 import workloads as W
 from gpu_util import Pair, dev_u32, canon
 
@@ -205,13 +204,47 @@ def test_hub_config_rejected():
         with pytest.raises(gv.GraphVineError) as e:
             gv.Graph(256, block_capacity=8, pool_bytes=4 << 20, **kw)
         assert e.value.code == gv.GV_ERR_INVALID_ARG
-    g = gv.Graph(256, block_capacity=8, pool_bytes=4 << 20, hub_shift=3)
+
+
+@pytest.mark.parametrize("C,C2,rs", [(16, 16, 3), (8, 32, 4), (32, 4, 3), (16, 0, 5)])
+def test_reblock_promotes_grown_vertices_to_runs(C, C2, rs):
+    """Vertices that grew past the threshold after their first allocation
+    stay plain until gv_reblock, which lays out exactly the vertices of
+    degree >= the threshold (at the new C) in runs; the graph keeps working
+    (inserts, deletes, queries, vertex deletes) on the new layout."""
+    scale, nv = 12, 1 << 12
+    p = Pair(nv, C=C, pool_bytes=96 << 20, hub_shift=rs)
     try:
-        s, d = W.uniform_pairs(1, 0, 1000, 256)
-        g.insert_edges(dev_u32(s), dev_u32(d))
-        with pytest.raises(gv.GraphVineError) as e:
-            g.reblock(16)
-        assert e.value.code == gv.GV_ERR_STATE
-        assert g.sync() == 0 and g.validate() == 0
+        # many small batches: most vertices' first allocation is small, so
+        # they grow past the threshold as plain vertices
+        for r in range(6):
+            s, d = W.rmat_pairs(41 + C + rs, r, 8 * nv, scale)
+            p.insert(s, d)
+        p.check()
+        deg = p.o.degrees().astype(np.int64)
+        T = C << rs
+        assert ((deg >= T) & ~p.hub[:deg.size]).any(), "some vertices must have grown past the threshold"
+        p.reblock(C2)
+        st = p.check()
+        d = p.o.degrees().astype(np.int64)[p.hub[:nv]]
+        R = 1 << rs
+        runs_owned = int((((d + p.C - 1) // p.C + R - 1) // R).sum())
+        assert p.hub.any() and st["pool_runs_free"] == st["pool_runs"] - runs_owned
+        bs, bd = W.rmat_pairs(41, 20, 6 * nv, scale)
+        p.insert(bs, bd)
+        p.check()
+        qs, qd = W.rmat_queries(41, scale, 4 * nv, bs, bd, 0)
+        p.query(qs, qd)
+        p.delete(bs[::2], bd[::2])
+        p.check()
+        hubs = np.flatnonzero(p.hub).astype(np.uint32)
+        p.vdel(np.concatenate([hubs[:2], np.array([9, 10], dtype=np.uint32)]))
+        p.check()
+        p.check_sampled(hubs[2:10])
+        # a second resize back to the first size
+        p.reblock(C)
+        p.check()
+        p.delete(bs[1::2], bd[1::2])
+        p.check()
     finally:
-        g.close()
+        p.close()
