@@ -26,7 +26,9 @@ def blocks_owned(deg, hub, C, rs):
     nb = (d + C - 1) // C
     if rs:
         R = 1 << rs
-        nb = np.where(hub[:d.size], (nb + R - 1) // R * R, nb)
+        h = np.zeros(d.size, dtype=bool)
+        h[:min(d.size, hub.size)] = hub[:d.size]
+        nb = np.where(h, (nb + R - 1) // R * R, nb)
     return int(nb.sum())
 
 

@@ -6,7 +6,7 @@ sizes.  Seeded; every case is reproducible."""
 import numpy as np
 import pytest
 
-from gpu_util import Pair, dev_u32
+from gpu_util import Pair, blocks_owned, dev_u32
 
 pytestmark = pytest.mark.gpu
 
@@ -21,16 +21,22 @@ def _pairs(rng, n, nv, hub_frac=0.3):
     return s, d
 
 
-# flags: 1 set semantics, 2 pool growth, 4 weighted, 8 radix-partition grouping
+# flags: 1 set semantics, 2 pool growth, 4 weighted, 8 radix-partition
+# grouping; 16 (this test's own bit) hub runs with a random run size and
+# threshold
 @pytest.mark.parametrize("seed,C,flags", [(1, 4, 0), (2, 8, 0), (3, 16, 1), (4, 12, 2), (5, 32, 3), (6, 0, 0),
-                                          (7, 8, 4), (8, 20, 6), (9, 16, 8), (10, 4, 12), (11, 0, 10)])
+                                          (7, 8, 4), (8, 20, 6), (9, 16, 8), (10, 4, 12), (11, 0, 10),
+                                          (12, 4, 16), (13, 16, 20), (14, 0, 17), (15, 8, 16)])
 def test_random_operation_sequences(seed, C, flags):
     import torch
     import paper_2306_08252_gb300 as gv
     rng = np.random.default_rng(1000 + seed)
     nv = int(rng.integers(300, 3000))
+    hubs = bool(flags & 16)
+    flags &= 15
     pool = (8 << 20) if flags & gv.GV_GROW else (64 << 20)
-    p = Pair(nv, C=C, pool_bytes=pool, flags=flags)
+    hub_kw = dict(hub_shift=int(rng.integers(3, 7)), hub_degree=int(rng.choice([0, 1, 20, 100]))) if hubs else {}
+    p = Pair(nv, C=C, pool_bytes=pool, flags=flags, **hub_kw)
     try:
         bs, bd = _pairs(rng, int(rng.integers(1, 20000)), nv)
         p.bulk(bs, bd)
@@ -44,8 +50,10 @@ def test_random_operation_sequences(seed, C, flags):
                 s, d = _pairs(rng, int(rng.integers(0, 15000)), n_now)
                 w = rng.integers(0, 1 << 32, s.size, dtype=np.uint64).astype(np.uint32)
                 cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+                before = p.o.degrees().astype(np.int64)
                 p.g.insert_edges_weighted(dev_u32(s), dev_u32(d), dev_u32(w), cnt)
                 assert tuple(int(x) for x in cnt.cpu().tolist()) == p.o.insert_edges_weighted(s, d, w)
+                p._hub_update(before)
                 stored_s, stored_d = np.concatenate([stored_s, s]), np.concatenate([stored_d, d])
             elif op == "insert":
                 s, d = _pairs(rng, int(rng.integers(0, 15000)), n_now)
@@ -70,11 +78,13 @@ def test_random_operation_sequences(seed, C, flags):
                 off = np.zeros(len(segs) + 1, dtype=np.int64)
                 off[1:] = np.cumsum([a.size for a, _ in segs])
                 cnt = torch.zeros(2 * len(segs), dtype=torch.int64, device="cuda")
+                before = p.o.degrees().astype(np.int64)
                 gv.gv_delete_edges_segmented(p.g.handle, dev_u32(np.concatenate([a for a, _ in segs])),
                                              dev_u32(np.concatenate([b for _, b in segs])),
                                              torch.from_numpy(off).cuda(), len(segs), cnt)
                 exp = [p.o.delete_edges(a, b) for a, b in segs]
                 np.testing.assert_array_equal(cnt.cpu().numpy().reshape(-1, 2), np.array(exp))
+                p._hub_update(before)
             elif op == "vdel":
                 ids = rng.choice(n_now, int(rng.integers(1, 20)), replace=False).astype(np.uint32)
                 p.vdel(ids)
@@ -95,14 +105,13 @@ def test_random_operation_sequences(seed, C, flags):
                 before = p.g.stats()["block_capacity"]
                 want = int(rng.choice([0, gv.GV_REBLOCK_MIN_FOOTPRINT, 4, 8, 12, 16, 24, 32, 64, 128]))
                 try:
-                    got = p.g.reblock(want)
+                    got = p.reblock(want)  # with hub runs: every vertex re-decided by degree
                 except gv.GraphVineError as e:
                     # only a resize that does not fit the pool may fail; nothing changes
                     assert e.code == gv.GV_ERR_OUT_OF_MEMORY
                     got = before
                 assert p.g.stats()["block_capacity"] == got
-                deg = p.o.degrees().astype(np.int64)
-                assert p.g.stats()["pool_blocks_used"] == int(((deg + got - 1) // got).sum())
+                assert p.g.stats()["pool_blocks_used"] == blocks_owned(p.o.degrees(), p.hub, got, p.rs)
             p.check()
     finally:
         p.close()
