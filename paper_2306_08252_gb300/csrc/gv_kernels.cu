@@ -208,32 +208,32 @@ __global__ void __launch_bounds__(256) k_count_direct(GraphView g, const uint32_
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     unsigned long long rej = 0;
     for (unsigned long long i0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i0 < n;
-         i0 += stride * 8) {
-        uint32_t u[8], v[8];
+         i0 += stride * CD_PER) {
+        uint32_t u[CD_PER], v[CD_PER];
         uint32_t ok = 0;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < CD_PER; ++j) {
             const unsigned long long i = i0 + j * stride;
             u[j] = i < n ? ld_stream(src + i) : NIL;
             v[j] = i < n ? ld_stream(dst + i) : NIL;
             if (u[j] < g.nv && v[j] < g.nv) ok |= 1u << j;
         }
         if (!g.all_alive) {
-            uint8_t au[8], av[8];
+            uint8_t au[CD_PER], av[CD_PER];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
+            for (int j = 0; j < CD_PER; ++j) {
                 au[j] = ((ok >> j) & 1u) ? g.alive[u[j]] : 0;
                 av[j] = ((ok >> j) & 1u) ? g.alive[v[j]] : 0;
             }
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
+            for (int j = 0; j < CD_PER; ++j)
                 if (!(au[j] && av[j])) ok &= ~(1u << j);
         }
-        uint32_t r[8];
+        uint32_t r[CD_PER];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) r[j] = ((ok >> j) & 1u) ? atomicAdd(&g.vcnt[vslot(g.vmask, u[j])], 1u) : NIL;
+        for (int j = 0; j < CD_PER; ++j) r[j] = ((ok >> j) & 1u) ? atomicAdd(&g.vcnt[vslot(g.vmask, u[j])], 1u) : NIL;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < CD_PER; ++j) {
             const unsigned long long i = i0 + j * stride;
             if (i < n) {
                 g.prank[i] = r[j];
@@ -869,30 +869,31 @@ template <int MODE>
 __global__ void __launch_bounds__(256) k_scatter_member(GraphView g, const uint32_t *__restrict__ src,
                                                         const uint32_t *__restrict__ dst,
                                                         unsigned long long n) {
+    constexpr int PPM = PP_MEMBER;
     pdl_wait();
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long i0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i0 < n;
-         i0 += stride * PP) {
-        uint32_t r[PP], u[PP], v[PP];
+         i0 += stride * PPM) {
+        uint32_t r[PPM], u[PPM], v[PPM];
 #pragma unroll
-        for (int j = 0; j < PP; ++j) {
+        for (int j = 0; j < PPM; ++j) {
             const unsigned long long i = i0 + j * stride;
             r[j] = i < n ? ld_stream(g.prank + i) : NIL;
             u[j] = i < n ? ld_stream(src + i) : 0u;
             v[j] = i < n ? ld_stream(dst + i) : 0u;
         }
-        uint32_t aoff[PP], hs[PP];
+        uint32_t aoff[PPM], hs[PPM];
 #pragma unroll
-        for (int j = 0; j < PP; ++j) {
+        for (int j = 0; j < PPM; ++j) {
             if (r[j] != NIL) {
                 const uint4 vi = g.vinfo[vslot(g.vmask, u[j])];
                 aoff[j] = vi.y;
                 hs[j] = vi.z;  // 0: list
             }
         }
-        uint32_t pos[PP];
+        uint32_t pos[PPM];
 #pragma unroll
-        for (int j = 0; j < PP; ++j) {
+        for (int j = 0; j < PPM; ++j) {
             pos[j] = NIL;
             if (r[j] != NIL && hs[j] == 0) {
                 pos[j] = aoff[j] + r[j];
@@ -903,11 +904,11 @@ __global__ void __launch_bounds__(256) k_scatter_member(GraphView g, const uint3
         // halves in flight together; L2, not a possibly stale L1 line), then
         // claim its first empty slot by CAS; occupied slots stay a prefix of
         // each bucket
-        uint4 b0[PP], b1[PP];
-        uint32_t bk[PP];
+        uint4 b0[PPM], b1[PPM];
+        uint32_t bk[PPM];
         uint32_t rep = 0;  // set-semantics inserts: bit j = pair j claimed its slot
 #pragma unroll
-        for (int j = 0; j < PP; ++j) {
+        for (int j = 0; j < PPM; ++j) {
             if (r[j] != NIL && hs[j] != 0) {
                 bk[j] = hidx(v[j], hs[j] / HB);
                 const uint4 *bp = reinterpret_cast<const uint4 *>(g.arena + aoff[j] + bk[j] * HB);
@@ -916,7 +917,7 @@ __global__ void __launch_bounds__(256) k_scatter_member(GraphView g, const uint3
             }
         }
 #pragma unroll
-        for (int j = 0; j < PP; ++j) {
+        for (int j = 0; j < PPM; ++j) {
             if (r[j] != NIL && hs[j] != 0) {
                 const uint32_t nbk = hs[j] / HB;
                 uint32_t *tab = g.arena + aoff[j];
@@ -958,7 +959,7 @@ __global__ void __launch_bounds__(256) k_scatter_member(GraphView g, const uint3
         if (MODE == MODE_DELETE && g.seg_own) {
             // segmented delete: each key's owner is the first segment naming it
 #pragma unroll
-            for (int j = 0; j < PP; ++j) {
+            for (int j = 0; j < PPM; ++j) {
                 if (pos[j] != NIL) {
                     const uint32_t sg = segment_of(g.set_off, g.set_G, i0 + j * stride);
                     if (hs[j] == 0) g.seg_own[pos[j]] = sg;
@@ -968,7 +969,7 @@ __global__ void __launch_bounds__(256) k_scatter_member(GraphView g, const uint3
         }
         if (MODE == MODE_QUERY || MODE == MODE_DEDUP) {
 #pragma unroll
-            for (int j = 0; j < PP; ++j) {
+            for (int j = 0; j < PPM; ++j) {
                 const unsigned long long i = i0 + j * stride;
                 if (i < n) {
                     g.qpos[i] = pos[j];
@@ -1991,7 +1992,7 @@ cudaError_t launch_count_range(int mode, const GraphView &g0, const uint32_t *sr
     PhaseScope ps(lc, ph);
     if (n_total >= ((unsigned long long)g.nv >> g.dense_shift)) {
         // large batch: per-pair atomics (the touched list follows the pass)
-        const int grid = grid_for(n, 256 * 8, lc.num_sms * GRID_MULT);
+        const int grid = grid_for(n, 256 * CD_PER, lc.num_sms * GRID_MULT);
         switch (mode) {
         case MODE_INSERT: launch_pdl(k_count_direct<MODE_INSERT>, grid, 256, 0, lc.stream, g, src, dst, n); break;
         case MODE_DELETE: launch_pdl(k_count_direct<MODE_DELETE>, grid, 256, 0, lc.stream, g, src, dst, n); break;
@@ -2120,7 +2121,7 @@ static void member_tail(const GraphView &g0, const uint32_t *src, const uint32_t
             launch_pdl(k_arena_init<MODE>, grid_for(5 * n + 64, 256, cap), 256, 0, lc.stream, g);
         }
         PhaseScope ps(lc, del ? PH_DEL_SCATTER : PH_QRY_SCATTER);
-        launch_pdl(k_scatter_member<MODE>, grid_for(n, 256 * PP, cap), 256, 0, lc.stream, g, src, dst, n);
+        launch_pdl(k_scatter_member<MODE>, grid_for(n, 256 * PP_MEMBER, cap), 256, 0, lc.stream, g, src, dst, n);
     }
     // The two tiers touch disjoint sources (their blocks, sentinels and list
     // ranges) and share only atomically updated counters, so the thread-per-
@@ -2272,7 +2273,7 @@ cudaError_t launch_dedup_insert_prepare(const GraphView &g0, const uint32_t *src
     const int gi = grid_for(4 * nt + 256, 8, cap);
     launch_pdl(k_plan_member<MODE_DEDUP>, gt, 256, 0, lc.stream, g);
     launch_pdl(k_arena_init<MODE_DEDUP>, grid_for(8 * n + 64, 256, cap), 256, 0, lc.stream, g);
-    launch_pdl(k_scatter_member<MODE_DEDUP>, grid_for(n, 256 * PP, cap), 256, 0, lc.stream, g, src, dst, n);
+    launch_pdl(k_scatter_member<MODE_DEDUP>, grid_for(n, 256 * PP_MEMBER, cap), 256, 0, lc.stream, g, src, dst, n);
     launch_pdl(k_mark<MODE_QUERY>, gi, 256, 0, lc.stream, g);
     launch_pdl(k_dedup_select, grid_for(n, 256, cap), 256, 0, lc.stream, g, src, n, src2, tmp + 1);
     launch_pdl(k_copy_rejects, 1, 32, 0, lc.stream, g.dev, tmp);

@@ -247,6 +247,12 @@ cudaError_t launch_validate(const GraphView &g, uint32_t *owner_bits,
 #ifndef GV_PP
 #define GV_PP 4
 #endif
+#ifndef GV_PP_MEMBER
+#define GV_PP_MEMBER 1
+#endif
+#ifndef GV_CD_PER
+#define GV_CD_PER 8
+#endif
 #ifndef GV_GRID_MULT
 #define GV_GRID_MULT 16
 #endif
@@ -257,6 +263,12 @@ constexpr int AGG_HBITS = GV_AGG_HBITS;
 constexpr int AGG_H = 1 << AGG_HBITS;            // shared hash slots per tile (>= 2 * tile)
 constexpr int AGG_SPT = AGG_H / AGG_THREADS;     // hash slots per thread
 constexpr int PP = GV_PP;                        // pairs per thread per step (streaming kernels)
+// The membership scatter holds more per pair (a plan record, two half
+// buckets): with one pair a thread more CTAs fit an SM, which hides its
+// scattered accesses better than more pairs in flight per thread (on the
+// 10M delete: 141 us at one pair, 166 at two, 200 at four).
+constexpr int PP_MEMBER = GV_PP_MEMBER;
+constexpr int CD_PER = GV_CD_PER;                // pairs per thread per step of the per-pair counting pass
 constexpr int GRID_MULT = GV_GRID_MULT;          // CTAs per SM of grid-stride kernels
 constexpr int MASK_WORDS = 16;                   // survivor bits per item (512 slots)
 // Neighbour-offset scan: SCAN_T threads per CTA, SCAN_PER ids each; one
