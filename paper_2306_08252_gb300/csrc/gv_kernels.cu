@@ -36,7 +36,8 @@
 //   scatter batch destinations into the lists (plain store at the rank) or
 //           the hash sets (CAS into the first empty slot of the home bucket).
 //   mark    one warp per item: resolve the item's block ids by walking the
-//           CBT, stream the entries with 16-byte loads, test membership (a
+//           CBT, stream the entries with 16-byte loads (the next round's in
+//           flight while a round is tested), test membership (a
 //           per-warp shared hash set built from the list, or the arena hash
 //           set).  Query sets hit flags.  Delete compacts single-item
 //           adjacencies in place (stable) and frees their emptied tail blocks;
@@ -1133,14 +1134,29 @@ __global__ void __launch_bounds__(256, 4) k_mark(GraphView g) {
         const uint32_t nquads = (nslots + 3) >> 2;
         const bool single = (ni == 1);
         uint32_t running = 0;
+        // Each round streams 32 quads of the item's entries; the next
+        // round's quad is loaded while this one is tested (software
+        // pipelining: one load latency exposed per item instead of per
+        // round).  Prefetching is safe under compaction: a round's writes
+        // go to slots at or below the slot it reads, never to the next
+        // round's.
+        uint4 e4n = make_uint4(EMPTY_KEY, EMPTY_KEY, EMPTY_KEY, EMPTY_KEY);
+        if (lane < nquads) {
+            const uint32_t xn = lane << 2, lbn = divc(g.cmul, xn);
+            e4n = ld_stream4(reinterpret_cast<const uint4 *>(g.data + (size_t)sb_ids[lbn] * C + (xn - lbn * C)));
+        }
         for (uint32_t q0 = 0; q0 < nquads; q0 += 32) {
             const uint32_t q = q0 + lane;
             const bool qv = q < nquads;
             const uint32_t x = q << 2;
             const uint32_t lb = divc(g.cmul, x);
-            uint4 e4 = make_uint4(EMPTY_KEY, EMPTY_KEY, EMPTY_KEY, EMPTY_KEY);
-            const size_t qoff = (size_t)sb_ids[lb] * C + (x - lb * C);
-            if (qv) e4 = ld_stream4(reinterpret_cast<const uint4 *>(g.data + qoff));
+            const size_t qoff = qv ? (size_t)sb_ids[lb] * C + (x - lb * C) : 0;
+            const uint4 e4 = e4n;
+            e4n = make_uint4(EMPTY_KEY, EMPTY_KEY, EMPTY_KEY, EMPTY_KEY);
+            if (q + 32 < nquads) {
+                const uint32_t xn = (q + 32) << 2, lbn = divc(g.cmul, xn);
+                e4n = ld_stream4(reinterpret_cast<const uint4 *>(g.data + (size_t)sb_ids[lbn] * C + (xn - lbn * C)));
+            }
             const uint32_t e[4] = {e4.x, e4.y, e4.z, e4.w};
             // payloads of a weighted graph move with their entries: read in
             // the same round as the entries, before any compaction write
