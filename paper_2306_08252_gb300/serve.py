@@ -17,7 +17,9 @@ order:
 
 Up to `slots` runs are in flight, each with its own pinned host and device
 buffers, on three streams ordered by events: the host-to-device copy of its
-pairs on an upload stream, the library call on the compute stream (after
+pairs on an upload stream (straight from each request's own memory when the
+request lives in pinned host memory -- `pin_requests` -- else packed into
+the run's pinned buffer first), the library call on the compute stream (after
 the copy's event), the device-to-host copy of its results on a download
 stream (after the call's event), then the run's completion event.  So one
 run's upload and another's download overlap the kernels of the run between
@@ -48,7 +50,7 @@ INSERT, DELETE, QUERY = "insert", "delete", "query"
 
 
 class Request:
-    __slots__ = ("kind", "src", "dst", "arrival", "result", "done", "status")
+    __slots__ = ("kind", "src", "dst", "arrival", "result", "done", "status", "t_src", "t_dst")
 
     def __init__(self, kind, src, dst, arrival=0.0):
         self.kind = kind
@@ -58,9 +60,31 @@ class Request:
         self.result = None
         self.done = None
         self.status = gv.GV_OK
+        self.t_src = self.t_dst = None  # pinned int32 views (pin_requests)
 
     def __len__(self):
         return int(self.src.size)
+
+
+def pin_requests(reqs):
+    """Moves the pairs of `reqs` into one pinned host buffer (as a server
+    that receives requests into registered buffers has them), so that the
+    loop uploads each request straight from its own memory with no packing
+    copy on the host.  Returns the buffer (keep it alive while the requests
+    are served)."""
+    import torch
+    total = sum(len(r) for r in reqs)
+    buf = torch.empty(max(2 * total, 1), dtype=torch.int32).pin_memory()
+    view = buf.numpy()
+    a = 0
+    for r in reqs:
+        n = len(r)
+        view[a:a + n] = r.src.view(np.int32)
+        view[a + n:a + 2 * n] = r.dst.view(np.int32)
+        r.t_src, r.t_dst = buf[a:a + n], buf[a + n:a + 2 * n]
+        r.src, r.dst = view[a:a + n].view(np.uint32), view[a + n:a + 2 * n].view(np.uint32)
+        a += 2 * n
+    return buf
 
 
 class _Slot:
@@ -133,15 +157,22 @@ class Server:
         offs[1:] = np.cumsum([len(r) for r in run])
         n = int(offs[-1])
         slot.n = n
-        hs = slot.h_src.numpy()
-        hd = slot.h_dst.numpy()
-        for r, a in zip(run, offs[:-1]):
-            hs[a:a + len(r)] = r.src.view(np.int32)
-            hd[a:a + len(r)] = r.dst.view(np.int32)
+        pinned = all(r.t_src is not None for r in run)
+        if not pinned:
+            hs = slot.h_src.numpy()
+            hd = slot.h_dst.numpy()
+            for r, a in zip(run, offs[:-1]):
+                hs[a:a + len(r)] = r.src.view(np.int32)
+                hd[a:a + len(r)] = r.dst.view(np.int32)
         slot.h_off.numpy()[:len(run) + 1] = offs
         k = len(run)
         with torch.cuda.stream(self.up):
-            if n:
+            if n and pinned:
+                for r, a in zip(run, offs[:-1]):
+                    if len(r):
+                        slot.d_src[a:a + len(r)].copy_(r.t_src, non_blocking=True)
+                        slot.d_dst[a:a + len(r)].copy_(r.t_dst, non_blocking=True)
+            elif n:
                 slot.d_src[:n].copy_(slot.h_src[:n], non_blocking=True)
                 slot.d_dst[:n].copy_(slot.h_dst[:n], non_blocking=True)
             if slot.kind != QUERY:

@@ -32,8 +32,10 @@ def _alone(g, o, kind, s, d):
     return res
 
 
-@pytest.mark.parametrize("realtime", [False, True])
-def test_served_results_equal_alone(realtime):
+@pytest.mark.parametrize("realtime,pinned", [(False, False), (True, False), (True, True)])
+def test_served_results_equal_alone(realtime, pinned):
+    """pinned: the requests live in pinned host memory and are uploaded
+    straight from it (serve.pin_requests)."""
     import paper_2306_08252_gb300 as gv
     from paper_2306_08252_gb300 import serve
     scale, C = 12, 8
@@ -53,7 +55,9 @@ def test_served_results_equal_alone(realtime):
         o.bulk_build(bs, bd)
         server = serve.Server(served_graph, C, slots=3, merge_pairs=20_000, max_reqs=64)
         rs = [serve.Request(k, a, b, t) for (k, a, b), t in zip(reqs, arrivals)]
+        keep = serve.pin_requests(rs) if pinned else None
         server.run(rs, realtime=realtime)
+        del keep
         assert server.merged_requests == len(rs)
         assert server.runs < len(rs)  # some requests were merged
         for r, (kind, s, d) in zip(rs, reqs):
