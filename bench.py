@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the short batched-form record")
     ap.add_argument("--no-serving", action="store_true", help="skip the short serving record")
     ap.add_argument("--requests", type=int, default=10_000)
+    ap.add_argument("--serve-loop", default="native", choices=["native", "python"],
+                    help="the serving loop: native (gv_serve, the C ABI) or the Python one (serve.Server)")
     ap.add_argument("--serve-scale", type=int, default=24)
     ap.add_argument("--workload", default="rmat", choices=["rmat", "batched", "serving", "rows"],
                     help="rmat: the single-graph step (default); batched: many member graphs, "
@@ -819,11 +821,12 @@ def batched_record(graphs, steps, warmup, tune=True):
 
 
 def run_serving(args):
-    print(json.dumps(serving_record(args.serve_scale, args.requests, (0.5, 0.7, 0.9))), flush=True)
+    print(json.dumps(serving_record(args.serve_scale, args.requests, (0.5, 0.7, 0.9),
+                                    native=args.serve_loop == "native")), flush=True)
     return 0
 
 
-def serving_record(scale, requests, loads):
+def serving_record(scale, requests, loads, native=True):
     """Serving: RMAT 2^24 vertices / 2^28 edges resident on the device;
     requests of mixed kind (40% insert, 40% delete of base edges, 20% query),
     sizes log-uniform in 1..1M, Poisson arrivals at 50%, 70% and 90% of the
@@ -858,24 +861,33 @@ def serving_record(scale, requests, loads):
         g.bulk_build(d_bs, d_bd)
         assert g.sync() == 0
         state["g"] = g
-        return serve.Server(g, C, slots=4, merge_pairs=2_000_000, max_reqs=1024)
+        return g
+
+    def serve_all(g, rs, realtime):
+        """The native loop (gv_serve) or the Python one; (runs, merged)."""
+        if native:
+            st = serve.serve_native(g, rs, slots=4, merge_pairs=2_000_000, max_reqs=1024, realtime=realtime)
+            return st["runs"], st["merged_requests"]
+        server = serve.Server(g, C, slots=4, merge_pairs=2_000_000, max_reqs=1024)
+        server.run(rs, realtime=realtime)
+        return server.runs, server.merged_requests
 
     # saturated capacity (all requests present at time 0)
-    server = fresh()
+    g = fresh()
     crs = [serve.Request(k, a, b, 0.0) for k, a, b in cap_reqs]
     cbuf = serve.pin_requests(crs)  # requests arrive in pinned host memory (registered receive buffers)
     t0 = time.perf_counter()
-    server.run(crs, realtime=False)
+    serve_all(g, crs, False)
     cap = len(crs) / (time.perf_counter() - t0)
     del crs, cbuf
     levels = []
     for load in loads:
-        server = fresh()
+        g = fresh()
         rate = load * cap
         arrivals = np.cumsum(gaps) / rate
         rs = [serve.Request(k, a, b, t) for (k, a, b), t in zip(reqs, arrivals)]
         lbuf = serve.pin_requests(rs)  # freed with the level's requests
-        server.run(rs, realtime=True)
+        runs, merged = serve_all(g, rs, True)
         skip = len(rs) // 10
         meas = [r for r in rs[skip:] if r.status == gv.GV_OK]
         upd = sum(len(r) for r in meas if r.kind in (serve.INSERT, serve.DELETE))
@@ -887,8 +899,8 @@ def serving_record(scale, requests, loads):
                        "worst": {"arrival_s": worst.arrival - rs[0].arrival, "kind": worst.kind,
                                  "pairs": len(worst)},
                        "updates_per_s": upd / span, "requests": len(rs),
-                       "warmup_requests": skip, "runs": server.runs,
-                       "requests_per_run": server.merged_requests / max(server.runs, 1),
+                       "warmup_requests": skip, "runs": runs,
+                       "requests_per_run": merged / max(runs, 1),
                        "failed": sum(1 for r in rs if r.status != gv.GV_OK)})
     g = state["g"]
     assert g.sync() == 0
@@ -900,7 +912,8 @@ def serving_record(scale, requests, loads):
            "config": {"workload": f"RMAT scale {scale} ({1 << scale} vertices, {edges} edges), C={C}; "
                                   f"{requests} requests, 40/40/20 insert/delete/query, sizes log-uniform 1..1M",
                       "slots": 4, "merge_pairs": 2_000_000, "generation_s": t_gen,
-                      "requests_in": "pinned host memory, uploaded straight from each request"},
+                      "requests_in": "pinned host memory, uploaded straight from each request",
+                      "loop": "native (gv_serve)" if native else "python (serve.Server)"},
            "capacity_req_per_s": cap, "levels": levels, "final_edges": st["num_edges"],
            "final_pool_bytes": st["pool_bytes"]}
     return res

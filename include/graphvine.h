@@ -508,6 +508,71 @@ gv_status gv_degree_offsets_noalloc(gv_graph *g, const uint32_t *d_vids, uint32_
 #define GV_REBLOCK_MIN_FOOTPRINT 1u
 gv_status gv_reblock(gv_graph *g, uint32_t block_capacity, uint32_t *h_block_capacity, void *stream);
 
+/*
+ * gv_serve -- continuous batching of a stream of requests on one graph (the
+ * serving form of the batched update path: requests arriving while earlier
+ * work runs are merged into runs whose device work overlaps).  Each request
+ * is an insert, delete or query batch of n (src, dst) pairs with an arrival
+ * time; once arrived, consecutive requests of one kind (at most max_reqs
+ * requests and merge_pairs pairs) form one run: one segmented insert
+ * (gv_insert_edges_segmented), one segmented delete
+ * (gv_delete_edges_segmented) or one query batch, so every request gets the
+ * result it would get alone, applied in arrival order.  Up to `slots` runs
+ * are in flight: the upload of a run's pairs, its call and the download of
+ * its results run on three streams of the loop's own, ordered by events, so
+ * that one run's copies overlap another's kernels.  Calls stay in arrival
+ * order.  An insert run is admitted while its worst-case block demand
+ * (ceil(n / C) blocks plus one per touched source, a whole run per source
+ * with hub runs) fits the free blocks last read; else the loop waits for the
+ * runs in flight and reads the pool again; a run that still does not fit
+ * fails (status GV_ERR_OUT_OF_MEMORY, counts {0, 0}) unless the graph has
+ * GV_GROW.
+ *   reqs     n_reqs requests (host memory, caller-owned): the kind, n, src,
+ *            dst, answers and arrival fields are inputs; status, done and
+ *            counts are outputs.  src and dst in pinned host memory are
+ *            uploaded as they are; other host memory is copied into the
+ *            loop's pinned staging first.  Query answers (1 = stored) go to
+ *            `answers` (n bytes of host memory).
+ *   cfg      NULL for the defaults: slots 4 (1..64), max_reqs 1024
+ *            (1..1024), merge_pairs 2,000,000 (every request must hold at
+ *            most this many pairs); realtime 1 honours the arrival times
+ *            (seconds after the call starts, non-decreasing), 0 treats
+ *            every request as arrived at the start.
+ *   h_stats  optional host uint64[2]: runs launched, requests merged.
+ *   stream   the stream of the library calls (as for every other entry
+ *            point; it stays the graph's stream after the loop).  Uploads
+ *            and downloads run on two streams the loop creates and
+ *            destroys.
+ * Allocates the loop's device and pinned buffers (slots of merge_pairs
+ * pairs) and reserves the graph's scratch for merge_pairs pairs at the
+ * start; frees the loop's buffers before returning.  Returns when every
+ * request has completed (or failed); GV_ERR_INVALID_ARG for a malformed
+ * request or configuration, before anything runs.
+ */
+#define GV_SERVE_INSERT 0u
+#define GV_SERVE_DELETE 1u
+#define GV_SERVE_QUERY 2u
+typedef struct gv_serve_request {
+    uint32_t kind;          /* GV_SERVE_INSERT, GV_SERVE_DELETE or GV_SERVE_QUERY */
+    int32_t status;         /* out: GV_OK, or GV_ERR_OUT_OF_MEMORY for an insert that did not fit */
+    uint64_t n;             /* pairs */
+    const uint32_t *src;    /* n source ids (host) */
+    const uint32_t *dst;    /* n destination ids (host) */
+    uint8_t *answers;       /* queries: n answers (host); unused otherwise */
+    double arrival;         /* seconds after the start of the call */
+    double done;            /* out: when the loop saw the request's run complete (same clock) */
+    uint64_t counts[2];     /* out: inserts and deletes, {done, rejected} */
+} gv_serve_request;
+typedef struct gv_serve_config {
+    uint32_t slots;
+    uint32_t max_reqs;
+    uint64_t merge_pairs;
+    uint32_t realtime;
+    uint32_t reserved;
+} gv_serve_config;
+gv_status gv_serve(gv_graph *g, gv_serve_request *reqs, uint64_t n_reqs, const gv_serve_config *cfg,
+                   uint64_t *h_stats, void *stream);
+
 /* gv_status_string -- a static, human-readable name for a status code. */
 const char *gv_status_string(gv_status s);
 

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgraphvine.so")
 
-SOURCES = ["gv_kernels.cu", "gv_group.cu", "gv_misc.cu", "gv_analytics.cu", "gv_capi.cu"]
+SOURCES = ["gv_kernels.cu", "gv_group.cu", "gv_misc.cu", "gv_analytics.cu", "gv_capi.cu", "gv_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 # Extra nvcc flags (e.g. -DGV_AGG_THREADS=128) for tuning builds.

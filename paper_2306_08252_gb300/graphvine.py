@@ -47,6 +47,30 @@ class gv_config(ctypes.Structure):
     ]
 
 
+class gv_serve_request(ctypes.Structure):
+    _fields_ = [
+        ("kind", c_u32),
+        ("status", ctypes.c_int32),
+        ("n", c_u64),
+        ("src", c_vp),
+        ("dst", c_vp),
+        ("answers", c_vp),
+        ("arrival", ctypes.c_double),
+        ("done", ctypes.c_double),
+        ("counts", c_u64 * 2),
+    ]
+
+
+class gv_serve_config(ctypes.Structure):
+    _fields_ = [
+        ("slots", c_u32),
+        ("max_reqs", c_u32),
+        ("merge_pairs", c_u64),
+        ("realtime", c_u32),
+        ("reserved", c_u32),
+    ]
+
+
 class gv_stats_t(ctypes.Structure):
     _fields_ = [
         ("num_vertices", c_u32),
@@ -94,6 +118,8 @@ SIGNATURES = {
     "gv_stats": ([c_vp, ctypes.POINTER(gv_stats_t)], ctypes.c_int),
     "gv_validate": ([c_vp, ctypes.POINTER(c_u64), c_vp], ctypes.c_int),
     "gv_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "gv_serve": ([c_vp, ctypes.POINTER(gv_serve_request), c_u64, ctypes.POINTER(gv_serve_config), c_vp, c_vp],
+                 ctypes.c_int),
     "gv_profile": ([c_vp, ctypes.c_int], ctypes.c_int),
     "gv_profile_read": ([c_vp, c_vp, c_vp, c_u32], ctypes.c_int),
     "gv_profile_num_phases": ([], c_u32),

@@ -299,3 +299,45 @@ def latency_stats(reqs, skip=0):
         return {"p50_ms": None, "p99_ms": None}
     return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
             "mean_ms": float(lat.mean() * 1e3), "max_ms": float(lat.max() * 1e3)}
+
+
+def serve_native(graph, requests, slots=4, merge_pairs=2_000_000, max_reqs=1024, realtime=True):
+    """The same loop in native code (gv_serve): the C ABI runs admission,
+    run forming, the three streams and the completion polling; this wrapper
+    only builds the request array and copies the results back into the
+    Request objects (result, done, status).  `done` and `arrival` share the
+    loop's clock (seconds after the call started); with realtime=False every
+    arrival counts as 0.  Returns {"runs", "merged_requests"}."""
+    import ctypes
+    reqs = list(requests)
+    arr = (gv.gv_serve_request * max(len(reqs), 1))()
+    answers = []
+    code = {INSERT: 0, DELETE: 1, QUERY: 2}
+    for i, r in enumerate(reqs):
+        q = arr[i]
+        q.kind = code[r.kind]
+        q.n = len(r)
+        q.src = r.src.ctypes.data if len(r) else None
+        q.dst = r.dst.ctypes.data if len(r) else None
+        if r.kind == QUERY:
+            a = np.zeros(max(len(r), 1), dtype=np.uint8)
+            answers.append(a)
+            q.answers = a.ctypes.data
+        else:
+            answers.append(None)
+        if not realtime:
+            r.arrival = 0.0
+        q.arrival = r.arrival
+    cfg = gv.gv_serve_config(slots, max_reqs, merge_pairs, 1 if realtime else 0, 0)
+    stats = (ctypes.c_uint64 * 2)()
+    gv.check(gv.load().gv_serve(graph.handle, arr, len(reqs), ctypes.byref(cfg), stats, graph._s()), "gv_serve")
+    for i, r in enumerate(reqs):
+        q = arr[i]
+        r.status = int(q.status)
+        r.done = float(q.done)
+        if r.kind == QUERY:
+            r.result = answers[i][:len(r)]
+        else:
+            r.result = (int(q.counts[0]), int(q.counts[1]))
+    return {"runs": int(stats[0]), "merged_requests": int(stats[1])}
+

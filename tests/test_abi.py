@@ -126,7 +126,7 @@ def test_header_is_plain_c_and_links(lib, tmp_path):
 
 
 def test_binding_structs_match_header(tmp_path):
-    # the ctypes mirrors of gv_config and gv_stats_t have the header's size
+    # the ctypes mirrors of the header's structs have its size
     # and field offsets (a C program compiled against the header prints them)
     import ctypes
     import os
@@ -137,7 +137,7 @@ def test_binding_structs_match_header(tmp_path):
         pytest.skip("gcc not available")
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     lines = ['#include "graphvine.h"', "#include <stddef.h>", "#include <stdio.h>", "int main(void) {"]
-    for cls, name in [(gvb.gv_config, "gv_config"), (gvb.gv_stats_t, "gv_stats_t")]:
+    for cls, name in [(gvb.gv_config, "gv_config"), (gvb.gv_stats_t, "gv_stats_t"), (gvb.gv_serve_request, "gv_serve_request"), (gvb.gv_serve_config, "gv_serve_config")]:
         lines.append(f'    printf("{name} %zu\\n", sizeof({name}));')
         for f, _ in cls._fields_:
             lines.append(f'    printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
@@ -148,7 +148,7 @@ def test_binding_structs_match_header(tmp_path):
     subprocess.run(["gcc", "-std=c99", "-I", os.path.join(root, "include"), str(src), "-o", str(exe)], check=True)
     out = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
                                                           check=True).stdout.split("\n") if l)
-    for cls, name in [(gvb.gv_config, "gv_config"), (gvb.gv_stats_t, "gv_stats_t")]:
+    for cls, name in [(gvb.gv_config, "gv_config"), (gvb.gv_stats_t, "gv_stats_t"), (gvb.gv_serve_request, "gv_serve_request"), (gvb.gv_serve_config, "gv_serve_config")]:
         assert int(out[name]) == ctypes.sizeof(cls), name
         for f, _ in cls._fields_:
             assert int(out[f"{name}.{f}"]) == getattr(cls, f).offset, (name, f)

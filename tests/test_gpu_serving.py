@@ -32,10 +32,12 @@ def _alone(g, o, kind, s, d):
     return res
 
 
-@pytest.mark.parametrize("realtime,pinned", [(False, False), (True, False), (True, True)])
-def test_served_results_equal_alone(realtime, pinned):
+@pytest.mark.parametrize("realtime,pinned,native", [(False, False, False), (True, False, False), (True, True, False),
+                                                    (False, False, True), (True, False, True), (True, True, True)])
+def test_served_results_equal_alone(realtime, pinned, native):
     """pinned: the requests live in pinned host memory and are uploaded
-    straight from it (serve.pin_requests)."""
+    straight from it (serve.pin_requests); native: the loop of the C ABI
+    (gv_serve) instead of the Python one."""
     import paper_2306_08252_gb300 as gv
     from paper_2306_08252_gb300 import serve
     scale, C = 12, 8
@@ -53,13 +55,18 @@ def test_served_results_equal_alone(realtime, pinned):
         served_graph.bulk_build(dev_u32(bs), dev_u32(bd))
         alone_graph.bulk_build(dev_u32(bs), dev_u32(bd))
         o.bulk_build(bs, bd)
-        server = serve.Server(served_graph, C, slots=3, merge_pairs=20_000, max_reqs=64)
         rs = [serve.Request(k, a, b, t) for (k, a, b), t in zip(reqs, arrivals)]
         keep = serve.pin_requests(rs) if pinned else None
-        server.run(rs, realtime=realtime)
+        if native:
+            st = serve.serve_native(served_graph, rs, slots=3, merge_pairs=20_000, max_reqs=64, realtime=realtime)
+            merged, runs = st["merged_requests"], st["runs"]
+        else:
+            server = serve.Server(served_graph, C, slots=3, merge_pairs=20_000, max_reqs=64)
+            server.run(rs, realtime=realtime)
+            merged, runs = server.merged_requests, server.runs
         del keep
-        assert server.merged_requests == len(rs)
-        assert server.runs < len(rs)  # some requests were merged
+        assert merged == len(rs)
+        assert runs < len(rs)  # some requests were merged
         for r, (kind, s, d) in zip(rs, reqs):
             assert r.status == gv.GV_OK and r.done is not None
             res = _alone(alone_graph, o, kind, s, d)
@@ -154,3 +161,37 @@ def test_segmented_insert_pool_exhaustion_is_a_noop():
         p.check()  # unchanged: still equal to the oracle, which saw only the bulk build
     finally:
         p.close()
+
+
+def test_native_loop_refuses_an_insert_that_cannot_fit():
+    # the native loop's admission: a run whose worst-case block demand does
+    # not fit the free blocks (after draining and reading the pool again)
+    # fails with GV_ERR_OUT_OF_MEMORY and {0, 0}; the other requests run as
+    # if it had not been sent
+    import paper_2306_08252_gb300 as gv
+    from paper_2306_08252_gb300 import serve
+    nv, C = 2000, 8
+    g = gv.Graph(nv, block_capacity=C, pool_bytes=600 * (4 * C + 12))
+    o = oracle.OracleGraph(nv)
+    try:
+        bs, bd = W.uniform_pairs(91, 0, 300, nv)
+        g.bulk_build(dev_u32(bs), dev_u32(bd))
+        o.bulk_build(bs, bd)
+        small = W.uniform_pairs(91, 1, 50, nv)
+        huge = W.uniform_pairs(91, 2, 3000, nv)
+        rs = [serve.Request("insert", *small), serve.Request("query", bs[:100], bd[:100]),
+              serve.Request("insert", *huge), serve.Request("delete", bs[:50], bd[:50])]
+        serve.serve_native(g, rs, slots=2, merge_pairs=4000, max_reqs=8, realtime=False)
+        assert [r.status for r in rs] == [gv.GV_OK, gv.GV_OK, gv.GV_ERR_OUT_OF_MEMORY, gv.GV_OK]
+        assert rs[0].result == o.insert_edges(*small)
+        np.testing.assert_array_equal(rs[1].result, o.query_edges(bs[:100], bd[:100]))
+        assert rs[2].result == (0, 0)
+        assert rs[3].result == o.delete_edges(bs[:50], bd[:50])
+        assert g.sync() == 0 and g.validate() == 0
+        off, nb = g.export_csr()
+        ooff, onb = o.export_csr()
+        np.testing.assert_array_equal(off, ooff)
+        np.testing.assert_array_equal(canon(off, nb), onb)
+    finally:
+        g.close()
+        o.close()

@@ -78,3 +78,14 @@ def test_latency_stats():
     assert st["p50_ms"] == pytest.approx(np.percentile(lat, 50) * 1e3)
     assert st["p99_ms"] == pytest.approx(np.percentile(lat, 99) * 1e3)
     assert st["max_ms"] == pytest.approx(10.0)
+
+
+def test_native_loop_rejects_malformed_requests():
+    # argument checks of gv_serve happen before anything runs (no GPU needed:
+    # a NULL graph is refused first, then malformed requests)
+    import ctypes
+    import paper_2306_08252_gb300.graphvine as gvb
+    lib = gvb.load()
+    arr = (gvb.gv_serve_request * 1)()
+    assert lib.gv_serve(None, arr, 1, None, None, None) == gvb.GV_ERR_INVALID_ARG
+    assert lib.gv_serve(None, None, 0, None, None, None) == gvb.GV_ERR_INVALID_ARG
