@@ -150,8 +150,10 @@ typedef struct gv_config {
      * changes).  gv_reblock re-decides every vertex: after it, exactly the
      * vertices of degree >= the threshold (at the new C) are hubs, so it also
      * serves to promote vertices that grew past the threshold after their
-     * first allocation.  Results never depend on the setting.  Excludes
-     * GV_GROW, GV_RADIX_GROUPING and graph sets; block ids stay below
+     * first allocation.  With GV_GROW the pool grows by single blocks only
+     * (the growth rule applies to the blocks outside the run region, whose
+     * size stays as created).  Results never depend on the setting.
+     * Excludes GV_RADIX_GROUPING and graph sets; block ids stay below
      * 2^31 - 1 (the pool is capped there). */
     uint32_t hub_shift;
     uint32_t hub_degree;

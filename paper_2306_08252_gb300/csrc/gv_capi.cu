@@ -713,7 +713,11 @@ gv_status grow_pool(gv_graph *g, unsigned long long P2, unsigned long long qf, u
 gv_status maybe_grow(gv_graph *g, uint64_t n, cudaStream_t s) {
     if (!(g->flags & GV_GROW) || !g->C || n == 0) return GV_OK;
     const unsigned long long demand = (n + g->C - 1) / g->C + std::min<unsigned long long>(n, g->nv);
-    if (5 * (g->used_ub + demand) <= 4 * g->P) {
+    // with hub runs the policy applies to the blocks outside the run
+    // region, which has a fixed size: growth adds single blocks only
+    const unsigned long long H = g->RP << g->rs;
+    const unsigned long long pmax = g->rs ? 0x7FFFFFFEull : 0xFFFFFFFEull;
+    if (5 * (g->used_ub + demand) <= 4 * (g->P - H)) {
         g->used_ub += demand;
         return GV_OK;
     }
@@ -721,9 +725,9 @@ gv_status maybe_grow(gv_graph *g, uint64_t n, cudaStream_t s) {
     GV_CK(cudaMemcpyAsync(&g->h_small[1], &g->dev->q_back, 8, cudaMemcpyDeviceToHost, s));
     GV_CK(cudaStreamSynchronize(s));
     const unsigned long long qf = g->h_small[0], qb = g->h_small[1];
-    const unsigned long long used = g->P - (qb - qf);
+    const unsigned long long used = g->P - H - (qb - qf);
     unsigned long long P2 = g->P;
-    while (5 * (used + demand) > 4 * P2 && P2 < 0xFFFFFFFEull) P2 = std::min<unsigned long long>(P2 + (P2 + 3) / 4, 0xFFFFFFFEull);
+    while (5 * (used + demand) > 4 * (P2 - H) && P2 < pmax) P2 = std::min<unsigned long long>(P2 + (P2 + 3) / 4, pmax);
     if (P2 > g->P) {
         const gv_status st = grow_pool(g, P2, qf, qb, s);
         if (st != GV_OK && st != GV_ERR_OUT_OF_MEMORY) return st;
@@ -1095,9 +1099,9 @@ gv_status gv_create(const gv_config *cfg, uint32_t num_vertices, void *stream, g
     if (c.pool_mem && c.pool_bytes == 0) return GV_ERR_INVALID_ARG;
     if (num_vertices > 0x7FFFFFFFu) return GV_ERR_INVALID_ARG;
     // hub runs: R = 2^s with TINY_NB <= R (a small run adjacency lies in one
-    // run) and s <= 8; excluded with pool growth and the radix grouping
+    // run) and s <= 8; excluded with the radix grouping
     if (c.hub_shift != 0 && (c.hub_shift < 3 || c.hub_shift > 8)) return GV_ERR_INVALID_ARG;
-    if (c.hub_shift && (c.flags & (GV_GROW | GV_RADIX_GROUPING))) return GV_ERR_INVALID_ARG;
+    if (c.hub_shift && (c.flags & GV_RADIX_GROUPING)) return GV_ERR_INVALID_ARG;
     if (c.hub_percent > 90) return GV_ERR_INVALID_ARG;
     gv_graph *g = new (std::nothrow) gv_graph();
     if (!g) return GV_ERR_OUT_OF_MEMORY;

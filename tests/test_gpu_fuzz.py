@@ -26,7 +26,7 @@ def _pairs(rng, n, nv, hub_frac=0.3):
 # threshold
 @pytest.mark.parametrize("seed,C,flags", [(1, 4, 0), (2, 8, 0), (3, 16, 1), (4, 12, 2), (5, 32, 3), (6, 0, 0),
                                           (7, 8, 4), (8, 20, 6), (9, 16, 8), (10, 4, 12), (11, 0, 10),
-                                          (12, 4, 16), (13, 16, 20), (14, 0, 17), (15, 8, 16)])
+                                          (12, 4, 16), (13, 16, 20), (14, 0, 17), (15, 8, 16), (16, 8, 18)])
 def test_random_operation_sequences(seed, C, flags):
     import torch
     import paper_2306_08252_gb300 as gv

@@ -199,8 +199,8 @@ def test_run_region_exhaustion_is_a_noop():
 
 def test_hub_config_rejected():
     import paper_2306_08252_gb300 as gv
-    for kw in [dict(hub_shift=2), dict(hub_shift=9), dict(hub_shift=3, flags=gv.GV_GROW),
-               dict(hub_shift=3, flags=gv.GV_RADIX_GROUPING), dict(hub_shift=3, hub_percent=91)]:
+    for kw in [dict(hub_shift=2), dict(hub_shift=9), dict(hub_shift=3, flags=gv.GV_RADIX_GROUPING),
+               dict(hub_shift=3, hub_percent=91)]:
         with pytest.raises(gv.GraphVineError) as e:
             gv.Graph(256, block_capacity=8, pool_bytes=4 << 20, **kw)
         assert e.value.code == gv.GV_ERR_INVALID_ARG
@@ -246,5 +246,20 @@ def test_reblock_promotes_grown_vertices_to_runs(C, C2, rs):
         p.check()
         p.delete(bs[1::2], bd[1::2])
         p.check()
+    finally:
+        p.close()
+
+
+def test_hub_runs_with_pool_growth():
+    """GV_GROW with hub runs: the blocks outside the run region grow (the
+    growth rule counts those alone), the run region keeps its size, and the
+    graph stays equal to the oracle through growth."""
+    import paper_2306_08252_gb300 as gv
+    p = Pair(1 << 12, C=8, pool_bytes=4 << 20, flags=gv.GV_GROW, hub_shift=3, hub_percent=90)
+    try:
+        st0 = p.g.stats()
+        _hub_ops(p, 12, 1234, rounds=2)
+        st = p.g.stats()
+        assert st["pool_blocks"] > st0["pool_blocks"] and st["pool_runs"] == st0["pool_runs"]
     finally:
         p.close()
