@@ -65,13 +65,14 @@ def _hub_ops(p, scale, seed, rounds=3):
 
 @pytest.mark.parametrize("C,rs", [(4, 3), (16, 3), (16, 5), (8, 4)])
 def test_hub_runs_match_oracle(C, rs):
+    from test_gpu_analytics import _check
     p = Pair(1 << 12, C=C, pool_bytes=96 << 20, hub_shift=rs)
     try:
         _hub_ops(p, 12, 900 + C + rs)
-        src = 0
-        dist, _ = p.g.bfs(src)
-        odist, _ = p.o.bfs(src)
-        np.testing.assert_array_equal(dist, odist)
+        # BFS and PageRank read every adjacency through the tree of run heads
+        _check(p, [0, 1, 77], iters=(1, 7))
+        dist, _ = p.g.sssp(1)
+        np.testing.assert_array_equal(dist[:p.o.num_vertices], p.o.sssp(1, False)[0])
     finally:
         p.close()
 
