@@ -1002,10 +1002,16 @@ gv_status member_impl(gv_graph *g, int mode, const uint32_t *src, const uint32_t
         GV_TRY(ensure_group(g, n, mode == gv::MODE_QUERY, false, item_bound(g, touched)));
     }
     const GraphView v = grp ? grouped_view(g, n) : view(g);
+    // small batches: grouping, plan and placement in one kernel of one CTA
+    const bool small = !grp && n <= gv::small_member_max();
     int set = -1;
-    GV_TRY(stage_batch(g, v, mode, src, dst, nullptr, n, s, true, &dsrc, &ddst, nullptr, &set));
-    GV_CK(gv::launch_member_tail(mode, v, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, g->tcap,
-                                 (unsigned long long *)dcounts, (uint8_t *)dq, lcfg(g, s)));
+    GV_TRY(stage_batch(g, v, mode, src, dst, nullptr, n, s, !small, &dsrc, &ddst, nullptr, &set));
+    if (small)
+        GV_CK(gv::launch_member_small(mode, v, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, g->tcap,
+                                      (unsigned long long *)dcounts, (uint8_t *)dq, lcfg(g, s)));
+    else
+        GV_CK(gv::launch_member_tail(mode, v, (const uint32_t *)dsrc, (const uint32_t *)ddst, n, g->tcap,
+                                     (unsigned long long *)dcounts, (uint8_t *)dq, lcfg(g, s)));
     GV_TRY(release_set(g, set, s));
     // host outputs land in stream order (a pageable target completes here)
     if (host_counts) GV_CK(cudaMemcpyAsync(counts, dcounts, 16, cudaMemcpyDeviceToHost, s));

@@ -981,6 +981,165 @@ __global__ void __launch_bounds__(256) k_scatter_member(GraphView g, const uint3
     }
 }
 
+// ------------------------------------ small delete / query batches, one CTA
+
+// The front of a plain delete or query of at most SMALL_MEM pairs in one
+// kernel of one CTA, in place of the counting pass, the plan, the arena
+// initialisation and the scatter (four dependent launches that a small batch
+// waits for more than it works in): the batch grouped by source in a shared
+// hash table (a returning shared atomic gives each pair its rank among its
+// source's pairs), then per touched source the plan of the general path
+// (batch list or hash set in the arena, thread-per-source tier or work items,
+// the same thresholds and the same records), the hash sets cleared, and the
+// pairs placed in their lists or sets.  The mark, compaction and finalize
+// kernels of the general path follow unchanged.
+constexpr uint32_t SMALL_MEM = 2048;
+constexpr uint32_t SMALL_MEM_HS = 2 * SMALL_MEM;  // source hash slots (a power of two)
+constexpr uint32_t SMALL_MEM_THREADS = 1024;
+constexpr size_t SMALL_MEM_SMEM = SMALL_MEM_HS * 3 * 4 + SMALL_MEM * 4 * 4 + SMALL_MEM * 2 * 4;
+
+template <int MODE>
+__global__ void __launch_bounds__(SMALL_MEM_THREADS, 1) k_member_small(GraphView g, const uint32_t *__restrict__ src,
+                                                                      const uint32_t *__restrict__ dst, uint32_t n) {
+    pdl_wait();
+    extern __shared__ __align__(16) uint32_t sm[];
+    uint32_t *hk = sm;                      // [SMALL_MEM_HS] source id per slot
+    uint32_t *hc = hk + SMALL_MEM_HS;       // [SMALL_MEM_HS] pairs per slot
+    uint32_t *ht = hc + SMALL_MEM_HS;       // [SMALL_MEM_HS] touched index per slot
+    uint32_t *tu = ht + SMALL_MEM_HS;       // [SMALL_MEM] source id per touched index
+    uint32_t *tslot = tu + SMALL_MEM;       // [SMALL_MEM] hash slot per touched index
+    uint32_t *taoff = tslot + SMALL_MEM;    // [SMALL_MEM] arena offset of the source's list or set
+    uint32_t *thw = taoff + SMALL_MEM;      // [SMALL_MEM] hash-set words (0: a list)
+    uint32_t *pslot = thw + SMALL_MEM;      // [SMALL_MEM] hash slot per pair (NIL: rejected)
+    uint32_t *prk = pslot + SMALL_MEM;      // [SMALL_MEM] rank per pair
+    __shared__ uint32_t s_nt, s_rej;
+    __shared__ unsigned long long s_aw, s_hw;
+    __shared__ uint32_t s_ai, s_am, s_at, s_ath;
+    __shared__ uint32_t s_lused, s_hused;
+    Dev *dev = g.dev;
+    const uint32_t tid = threadIdx.x;
+    for (uint32_t h = tid; h < SMALL_MEM_HS; h += SMALL_MEM_THREADS) {
+        hk[h] = EMPTY_KEY;
+        hc[h] = 0;
+    }
+    if (tid == 0) {
+        s_nt = 0;
+        s_rej = 0;
+        s_lused = 0;
+        s_hused = 0;
+    }
+    __syncthreads();
+    // 1. group by source
+    uint32_t rej = 0;
+    for (uint32_t i = tid; i < n; i += SMALL_MEM_THREADS) {
+        const uint32_t u = src[i], v = dst[i];
+        if (!valid_pair(g, u, v)) {
+            ++rej;
+            pslot[i] = NIL;
+            if (MODE == MODE_QUERY) g.qpos[i] = NIL;
+            continue;
+        }
+        uint32_t h = hidx(u, SMALL_MEM_HS);
+        // at most n <= SMALL_MEM_HS / 2 keys: a free or equal slot exists
+        for (uint32_t step = 0; step < SMALL_MEM_HS; ++step) {
+            const uint32_t old = atomicCAS(&hk[h], EMPTY_KEY, u);
+            if (old == EMPTY_KEY) {
+                const uint32_t t = atomicAdd(&s_nt, 1u);
+                ht[h] = t;
+                tu[t] = u;
+                tslot[t] = h;
+                break;
+            }
+            if (old == u) break;
+            h = (h + 1) & (SMALL_MEM_HS - 1);
+        }
+        pslot[i] = h;
+        prk[i] = atomicAdd(&hc[h], 1u);
+    }
+    if (rej) atomicAdd(&s_rej, rej);
+    __syncthreads();
+    const uint32_t nt = s_nt;
+    // 2. plan per touched source (the general path's k_plan_member)
+    const uint32_t IB = g.IB;
+    const uint32_t tiny_deg = min(TINY_DEG, TINY_NB * g.C);
+    for (uint32_t base = 0; base < nt; base += SMALL_MEM_THREADS) {
+        const uint32_t t = base + tid;
+        uint32_t m = 0, lw = 0, hw = 0, ni = 0, tiny = 0;
+        uint4 s = make_uint4(0, 0, NIL, NIL);
+        if (t < nt) {
+            const uint32_t u = tu[t];
+            m = hc[tslot[t]];
+            s = g.sent[u];
+            if (m <= LIST_MAX) lw = m;
+            else hw = member_words(m);
+            if (s.y > 0) {
+                const bool small = MODE == MODE_QUERY
+                    ? (s.x <= min(TINY_DEG_Q, TINY_NB_Q * g.C) && s.y <= TINY_NB_Q && m <= TINY_M)
+                    : (s.x <= tiny_deg && s.y <= TINY_NB && m <= TINY_M);
+                if (small) tiny = 1;
+                else ni = (s.y + IB - 1) / IB;
+            }
+        }
+        const uint32_t tlo = tiny && s.x <= TINY_SPLIT, thi = tiny && s.x > TINY_SPLIT;
+        uint32_t lt, hts, ttot, tthi;
+        const uint32_t lex = block_excl_scan(lw, &lt);
+        const uint32_t hex = block_excl_scan(hw, &hts);
+        const uint32_t tex = block_excl_scan(tlo, &ttot);
+        const uint32_t thx = block_excl_scan(thi, &tthi);
+        if (tid == 0) {
+            s_aw = lt ? atomicAdd(&dev->arena_used, (unsigned long long)lt) : 0ull;
+            s_hw = hts ? atomicAdd(&dev->harena_used, (unsigned long long)hts) : 0ull;
+            s_at = ttot ? atomicAdd(&dev->n_tiny, ttot) : 0u;
+            s_ath = tthi ? atomicAdd(&dev->n_tiny_hi, tthi) : 0u;
+            s_lused += lt;
+            s_hused += hts;
+        }
+        const uint32_t item0 = alloc_items(g, ni, &s_ai, &s_am);
+        if (t < nt) {
+            const uint32_t aoff = hw ? (uint32_t)(g.hbase + s_hw + hex) : (uint32_t)(s_aw + lex);
+            g.t_vid[t] = tu[t];
+            g.t_a[t] = make_uint4(m, aoff, hw, item0);
+            g.t_b[t] = make_uint4(s.x, s.y, s.z, ni);
+            taoff[t] = aoff;
+            thw[t] = hw;
+            if (tlo) g.t_tiny[s_at + tex] = t;
+            if (thi) g.t_tiny[g.tiny_cap - 1 - (s_ath + thx)] = t;
+            emit_items(g, t, item0, ni);
+        }
+        __syncthreads();
+    }
+    // 3. hash sets empty; query hit flags cleared over both regions
+    const uint32_t lused = s_lused, hused = s_hused;
+    for (uint32_t k = tid; k < hused; k += SMALL_MEM_THREADS) {
+        g.arena[g.hbase + k] = EMPTY_KEY;
+        if (MODE == MODE_QUERY) g.found[g.hbase + k] = 0u;
+    }
+    if (MODE == MODE_QUERY)
+        for (uint32_t k = tid; k < lused; k += SMALL_MEM_THREADS) g.found[k] = 0u;
+    __syncthreads();
+    // 4. batch destinations into the lists (at the pair's rank) or the sets
+    for (uint32_t i = tid; i < n; i += SMALL_MEM_THREADS) {
+        const uint32_t h = pslot[i];
+        if (h == NIL) continue;
+        const uint32_t t = ht[h];
+        const uint32_t v = dst[i];
+        uint32_t pos;
+        if (thw[t] == 0) {
+            pos = taoff[t] + prk[i];
+            g.arena[pos] = v;
+        } else {
+            const uint32_t w = bucket_insert(g.arena + taoff[t], thw[t] / HB, v);
+            pos = w == NIL ? NIL : taoff[t] + w;
+            if (w == NIL) latch_status(dev, 5u /* GV_ERR_STATE */);
+        }
+        if (MODE == MODE_QUERY) g.qpos[i] = pos;
+    }
+    if (tid == 0) {
+        dev->n_touched = nt;
+        if (MODE != MODE_QUERY && s_rej) dev->call_b += s_rej;
+    }
+}
+
 // One warp per work item (see the file comment).
 // Per multi-item source (one warp, all lanes call): the new degree is the
 // sum of the items' survivors; per item, the holes below the new degree and
@@ -997,6 +1156,21 @@ __device__ __forceinline__ void vscan_source(const GraphView &g, uint32_t t, uin
     uint32_t tot = 0;
     for (uint32_t c = lane; c < ni; c += 32) tot += __ldcg(g.it_cnt + item0 + c);
     const uint32_t degn = warp_sum(tot);
+    // The one item that holds position degn (if it starts below it) has
+    // survivors on both sides: those below degn, counted from its survivor
+    // mask by the whole warp at once (lane w reads word w).
+    const uint32_t cs = degn / SPI;
+    uint32_t below_cs = 0;
+    if (cs < ni) {
+        const uint32_t split = degn - cs * SPI;
+        uint32_t word = 0;
+        if (lane < MASK_WORDS && lane * 32 < split) {
+            word = __ldcg(g.it_mask + (size_t)(item0 + cs) * MASK_WORDS + lane);
+            const uint32_t nbits = split - lane * 32;
+            if (nbits < 32) word &= (1u << nbits) - 1u;
+        }
+        below_cs = warp_sum(__popc(word));
+    }
     uint32_t carryH = 0, carryS = 0;
     for (uint32_t c0 = 0; c0 < ni; c0 += 32) {
         const uint32_t c = c0 + lane;
@@ -1010,17 +1184,10 @@ __device__ __forceinline__ void vscan_source(const GraphView &g, uint32_t t, uin
             } else if (sb >= degn) {
                 s = cnt;
             } else {
+                // c == cs: the item straddling degn
                 const uint32_t split = degn - sb;
-                const uint32_t *mk = g.it_mask + (size_t)(item0 + c) * MASK_WORDS;
-                uint32_t below = 0;
-                for (uint32_t w = 0; w * 32 < split; ++w) {
-                    uint32_t word = __ldcg(mk + w);
-                    const uint32_t nbits = split - w * 32;
-                    if (nbits < 32) word &= (1u << nbits) - 1u;
-                    below += __popc(word);
-                }
-                h = split - below;
-                s = cnt - below;
+                h = split - below_cs;
+                s = cnt - below_cs;
             }
         }
         uint32_t th, ts;
@@ -2111,7 +2278,7 @@ cudaError_t launch_insert_tail(const GraphView &g, const uint32_t *src, const ui
 template <int MODE>
 static void member_tail(const GraphView &g0, const uint32_t *src, const uint32_t *dst,
                         unsigned long long n, unsigned long long tcap, unsigned long long *counts,
-                        uint8_t *qout, const LaunchCfg &lc) {
+                        uint8_t *qout, const LaunchCfg &lc, bool small) {
     GraphView g = g0;
     g.hbase = (uint32_t)((n + 63) / 64 * 64);  // lists below (at most n words), hash sets above
 
@@ -2127,6 +2294,10 @@ static void member_tail(const GraphView &g0, const uint32_t *src, const uint32_t
         // (and filled the hash sets of sources past CT_KEYS batch entries)
         PhaseScope ps(lc, del ? PH_DEL_PLAN : PH_QRY_PLAN);
         launch_gp_plan_member(MODE, g, gt, lc);
+    } else if (small) {
+        // one CTA groups, plans and places the batch (k_member_small)
+        PhaseScope ps(lc, del ? PH_DEL_PLAN : PH_QRY_PLAN);
+        launch_pdl(k_member_small<MODE>, 1, SMALL_MEM_THREADS, SMALL_MEM_SMEM, lc.stream, g, src, dst, (uint32_t)n);
     } else {
         {
             PhaseScope ps(lc, del ? PH_DEL_PLAN : PH_QRY_PLAN);
@@ -2198,8 +2369,32 @@ static void member_tail(const GraphView &g0, const uint32_t *src, const uint32_t
 cudaError_t launch_member_tail(int mode, const GraphView &g, const uint32_t *src,
                                const uint32_t *dst, unsigned long long n, unsigned long long tcap,
                                unsigned long long *counts, uint8_t *qout, const LaunchCfg &lc) {
-    if (mode == MODE_DELETE) member_tail<MODE_DELETE>(g, src, dst, n, tcap, counts, qout, lc);
-    else member_tail<MODE_QUERY>(g, src, dst, n, tcap, counts, qout, lc);
+    if (mode == MODE_DELETE) member_tail<MODE_DELETE>(g, src, dst, n, tcap, counts, qout, lc, false);
+    else member_tail<MODE_QUERY>(g, src, dst, n, tcap, counts, qout, lc, false);
+    return cudaGetLastError();
+}
+
+uint64_t small_member_max() { return SMALL_MEM; }
+
+cudaError_t launch_member_small(int mode, const GraphView &g, const uint32_t *src, const uint32_t *dst,
+                                unsigned long long n, unsigned long long tcap, unsigned long long *counts,
+                                uint8_t *qout, const LaunchCfg &lc) {
+    if (n == 0 || n > SMALL_MEM || g.grouped || g.set_G || g.seg_own) return cudaErrorInvalidValue;
+    // the shared-memory opt-in is per function and device
+    static bool attr_set[64][2] = {};
+    int devc = 0;
+    if (cudaGetDevice(&devc) != cudaSuccess || devc < 0 || devc >= 64) return cudaErrorInvalidDevice;
+    const int q = mode == MODE_QUERY ? 1 : 0;
+    if (!attr_set[devc][q]) {
+        const cudaError_t e = q ? cudaFuncSetAttribute(k_member_small<MODE_QUERY>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMALL_MEM_SMEM)
+                                : cudaFuncSetAttribute(k_member_small<MODE_DELETE>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMALL_MEM_SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set[devc][q] = true;
+    }
+    if (mode == MODE_DELETE) member_tail<MODE_DELETE>(g, src, dst, n, tcap, counts, qout, lc, true);
+    else member_tail<MODE_QUERY>(g, src, dst, n, tcap, counts, qout, lc, true);
     return cudaGetLastError();
 }
 

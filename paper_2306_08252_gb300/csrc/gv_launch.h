@@ -132,6 +132,14 @@ cudaError_t launch_insert_tail(const GraphView &g, const uint32_t *src, const ui
 cudaError_t launch_member_tail(int mode, const GraphView &g, const uint32_t *src,
                                const uint32_t *dst, unsigned long long n, unsigned long long tcap,
                                unsigned long long *counts, uint8_t *qout, const LaunchCfg &lc);
+// A plain delete or query of at most small_member_max() pairs with the
+// counting pass, plan, arena initialisation and scatter in one kernel of one
+// CTA (the batch not counted before), then the general path's mark and
+// finalize kernels.
+uint64_t small_member_max();
+cudaError_t launch_member_small(int mode, const GraphView &g, const uint32_t *src, const uint32_t *dst,
+                                unsigned long long n, unsigned long long tcap, unsigned long long *counts,
+                                uint8_t *qout, const LaunchCfg &lc);
 // Grouped path of large plain batches (gv_group.cu).  group_shape: the
 // partition CTAs and their pair range for a batch of n.  launch_group_hist:
 // per-bucket counts of the partition CTAs whose ranges lie in pairs [lo, hi)
