@@ -795,7 +795,6 @@ __global__ void __launch_bounds__(256) k_plan_member(GraphView g) {
         if (t < nt) {
             const uint32_t u = g.t_vid[t];
             m = g.vcnt[vslot(g.vmask, u)];
-            g.vcnt[vslot(g.vmask, u)] = 0;  // read once: cleared here instead of by the finalize
             s = g.sent[u];
             if (MODE == MODE_DEDUP) hw = dedup_words(m);
             else if (m <= LIST_MAX) lw = m;
@@ -1816,19 +1815,13 @@ __global__ void __launch_bounds__(256) k_query_out(GraphView g, unsigned long lo
 }
 
 template <int MODE>
-// reset_counts: the touched sources' batch counters still hold their
-// counts (the grouped path, or a count whose batch is not applied); the
-// plan of the other paths clears each counter as it reads it.
-__global__ void __launch_bounds__(256) k_finalize_member(GraphView g, unsigned long long *counts,
-                                                         bool reset_counts) {
+__global__ void __launch_bounds__(256) k_finalize_member(GraphView g, unsigned long long *counts) {
     pdl_wait();
     Dev *dev = g.dev;
     const uint32_t nt = dev->n_touched;
-    if (reset_counts || g.grouped) {
-        for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
-            const uint32_t u = g.t_vid[t];
-            g.vcnt[vidx(g, u)] = 0;
-        }
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+        const uint32_t u = g.t_vid[t];
+        g.vcnt[vidx(g, u)] = 0;
     }
     if (last_cta(dev) && threadIdx.x == 0) {
         if (MODE == MODE_DELETE) {
@@ -2368,8 +2361,8 @@ static void member_tail(const GraphView &g0, const uint32_t *src, const uint32_t
     }
     {
         PhaseScope ps(lc, del ? PH_DEL_FINALIZE : PH_QRY_FINALIZE);
-        if (fork && del) k_finalize_member<MODE><<<gt, 256, 0, lc.stream>>>(g, counts, false);
-        else launch_pdl(k_finalize_member<MODE>, gt, 256, 0, lc.stream, g, counts, false);
+        if (fork && del) k_finalize_member<MODE><<<gt, 256, 0, lc.stream>>>(g, counts);
+        else launch_pdl(k_finalize_member<MODE>, gt, 256, 0, lc.stream, g, counts);
     }
 }
 
@@ -2495,7 +2488,7 @@ cudaError_t launch_dedup_insert_prepare(const GraphView &g0, const uint32_t *src
     launch_pdl(k_mark<MODE_QUERY>, gi, 256, 0, lc.stream, g);
     launch_pdl(k_dedup_select, grid_for(n, 256, cap), 256, 0, lc.stream, g, src, n, src2, tmp + 1);
     launch_pdl(k_copy_rejects, 1, 32, 0, lc.stream, g.dev, tmp);
-    launch_pdl(k_finalize_member<MODE_QUERY>, gt, 256, 0, lc.stream, g, nullptr, false);
+    launch_pdl(k_finalize_member<MODE_QUERY>, gt, 256, 0, lc.stream, g, nullptr);
     return cudaGetLastError();
 }
 cudaError_t launch_dedup_counts(Dev *dev, const unsigned long long *tmp, unsigned long long n,
@@ -2509,8 +2502,7 @@ namespace gv {
 // Clears the per-call state of a counting pass whose batch is not applied
 // (the first batch of a set-semantics graph, counted only to fix C).
 cudaError_t launch_finalize_count_only(const GraphView &g, const LaunchCfg &lc) {
-    launch_pdl(k_finalize_member<MODE_QUERY>, grid_for(g.nv, 256, lc.num_sms * GRID_MULT), 256, 0, lc.stream, g, nullptr,
-               true);
+    launch_pdl(k_finalize_member<MODE_QUERY>, grid_for(g.nv, 256, lc.num_sms * GRID_MULT), 256, 0, lc.stream, g, nullptr);
     return cudaGetLastError();
 }
 }  // namespace gv
