@@ -1262,6 +1262,22 @@ __global__ void __launch_bounds__(256, 4) k_mark(GraphView g) {
         // that lanes can look up any block without a shuffle.
         uint32_t *sb_ids = s_bid[threadIdx.x >> 5];
         sb_ids[lane] = bid;
+        __syncwarp();
+        const uint32_t sbase = kb * C;
+        const uint32_t nslots = min(nblk * C, deg - sbase);
+        const uint32_t nquads = (nslots + 3) >> 2;
+        // Each round streams 32 quads of the item's entries; the next
+        // round's quad is loaded while this one is tested (software
+        // pipelining: one load latency exposed per item instead of per
+        // round), and the first round's is in flight while the batch list
+        // below is built.  Prefetching is safe under compaction: a round's
+        // writes go to slots at or below the slot it reads, never to the
+        // next round's.
+        uint4 e4n = make_uint4(EMPTY_KEY, EMPTY_KEY, EMPTY_KEY, EMPTY_KEY);
+        if (lane < nquads) {
+            const uint32_t xn = lane << 2, lbn = divc(g.cmul, xn);
+            e4n = ld_stream4(reinterpret_cast<const uint4 *>(g.data + (size_t)sb_ids[lbn] * C + (xn - lbn * C)));
+        }
         // Batch list of this source (<= LIST_MAX entries): a shared hash set
         // per warp of nsb buckets of 4 slots (nsb * 4 a power of two >= 2m,
         // at least 64 slots).  A key takes the first empty slot of its home
@@ -1296,22 +1312,8 @@ __global__ void __launch_bounds__(256, 4) k_mark(GraphView g) {
             }
         }
         __syncwarp();
-        const uint32_t sbase = kb * C;
-        const uint32_t nslots = min(nblk * C, deg - sbase);
-        const uint32_t nquads = (nslots + 3) >> 2;
         const bool single = (ni == 1);
         uint32_t running = 0;
-        // Each round streams 32 quads of the item's entries; the next
-        // round's quad is loaded while this one is tested (software
-        // pipelining: one load latency exposed per item instead of per
-        // round).  Prefetching is safe under compaction: a round's writes
-        // go to slots at or below the slot it reads, never to the next
-        // round's.
-        uint4 e4n = make_uint4(EMPTY_KEY, EMPTY_KEY, EMPTY_KEY, EMPTY_KEY);
-        if (lane < nquads) {
-            const uint32_t xn = lane << 2, lbn = divc(g.cmul, xn);
-            e4n = ld_stream4(reinterpret_cast<const uint4 *>(g.data + (size_t)sb_ids[lbn] * C + (xn - lbn * C)));
-        }
         for (uint32_t q0 = 0; q0 < nquads; q0 += 32) {
             const uint32_t q = q0 + lane;
             const bool qv = q < nquads;
