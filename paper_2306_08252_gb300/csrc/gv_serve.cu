@@ -13,11 +13,12 @@
 //     the requests remove one after another);
 //   * queries merge into one query batch (no update separates them).
 // Up to `slots` runs are in flight, each with its own device buffers, on
-// three streams ordered by events: the upload of its pairs (straight from
-// each request's memory when that is pinned host memory, else packed into the
-// slot's pinned staging first), the library call on the compute stream, and
-// the download of its results, after which the run's completion event fires.
-// Calls stay in arrival order on the one compute stream (every call on a
+// three streams ordered by events: the upload of its pairs on a stream of the
+// loop's own (straight from each request's memory when that is pinned host
+// memory, else packed into the slot's pinned staging first), the library call
+// on the caller's stream, and the download of its results on a second stream
+// of the loop's own, after which the run's completion event fires.
+// Calls stay in arrival order on the caller's stream (every call on a
 // graph shares the graph's per-call scratch, and updates change what the
 // next run reads).  An insert run is admitted only while its worst-case block
 // demand fits the free blocks as last read; otherwise the loop drains the
